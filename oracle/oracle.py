@@ -1,0 +1,225 @@
+"""Python access to the FP64 CPU oracle (``nep_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by ``__graft_entry__.smoke``,
+by the bench's CPU-baseline leg and by ``make_scaler.py``.  It never imports
+the CUDA package; it reads only the seeded inputs module.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBDIR = os.path.join(HERE, "lib")
+LIB = os.path.join(LIBDIR, "libnep_oracle.so")
+SRC = os.path.join(HERE, "nep_oracle.c")
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP) into oracle/lib/."""
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        os.makedirs(LIBDIR, exist_ok=True)
+        tmp = LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared",
+                               "-o", tmp, SRC, "-lm"])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(LIB)
+        dp = C.POINTER(C.c_double)
+        ip = C.POINTER(C.c_int)
+        L.orc_energy_forces_virial.argtypes = [ip, dp, dp, dp, C.c_int, dp, dp, ip, C.c_int,
+                                               dp, dp, dp, dp]
+        L.orc_descriptors.argtypes = [ip, dp, dp, dp, C.c_int, dp, dp, ip, C.c_int, dp]
+        L.orc_forces_subset.argtypes = [ip, dp, dp, dp, C.c_int, dp, dp, ip, C.c_int,
+                                        C.POINTER(C.c_int64), dp, dp]
+        L.orc_md.argtypes = [ip, dp, dp, dp, C.c_int, dp, dp, dp, C.c_int, dp, ip,
+                             C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, dp]
+        L.orc_site.argtypes = [ip, dp, dp, dp, C.c_int, dp, C.c_int, dp, dp, dp, dp, dp]
+        L.orc_neighbor_counts.argtypes = [C.c_int, dp, dp, ip, C.c_double, C.c_int, ip,
+                                          C.c_int, dp]
+        L.orc_cutoff.argtypes = [C.c_double, C.c_double, dp, dp]
+        L.orc_chebyshev.argtypes = [C.c_double, C.c_int, dp, dp]
+        L.orc_basis.argtypes = [C.c_double, C.c_double, C.c_int, dp, dp]
+        L.orc_legendre.argtypes = [C.c_double, C.c_int, dp, dp]
+        L.orc_zbl.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                              dp, dp]
+        L.orc_fourbody_triple.argtypes = [C.c_int, dp, dp]
+        L.orc_fourbody_triple.restype = C.c_double
+        L.orc_n_params.argtypes = [ip]
+        _lib = L
+    return _lib
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def _d(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _i(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _hp(model):
+    ihp = np.array([model.n_max_radial + 1, model.n_max_angular + 1,
+                    model.basis_size_radial + 1, model.basis_size_angular + 1,
+                    model.l_max, model.use_4body, model.n_hidden], dtype=np.int32)
+    dhp = np.array([model.rc_radial, model.rc_angular, float(model.z),
+                    model.zbl_r_inner, model.zbl_r_outer], dtype=np.float64)
+    return ihp, dhp
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with code {rc}")
+
+
+def energy_forces_virial(model, pos, box, pbc, use_grid=True, params=None):
+    """E, F (N,3), W (3,3), U_site (N) of one system."""
+    ihp, dhp = _hp(model)
+    p = _f64(model.params if params is None else params)
+    s = _f64(model.scaler)
+    pos = _f64(pos)
+    n = pos.shape[0]
+    box = _f64(box)
+    pbc = np.ascontiguousarray(pbc, dtype=np.int32)
+    E = np.zeros(1)
+    F = np.zeros((n, 3))
+    W = np.zeros(9)
+    U = np.zeros(n)
+    _check(lib().orc_energy_forces_virial(_i(ihp), _d(dhp), _d(p), _d(s), n, _d(pos), _d(box),
+                                          _i(pbc), int(use_grid), _d(E), _d(F), _d(W), _d(U)),
+           "energy_forces_virial")
+    return float(E[0]), F, W.reshape(3, 3), U
+
+
+def descriptors(model, pos, box, pbc, use_grid=True):
+    """Unscaled descriptors (N, D)."""
+    ihp, dhp = _hp(model)
+    p = _f64(model.params)
+    s = _f64(model.scaler if model.scaler is not None else np.ones(model.dim))
+    pos = _f64(pos)
+    n = pos.shape[0]
+    q = np.zeros((n, model.dim))
+    _check(lib().orc_descriptors(_i(ihp), _d(dhp), _d(p), _d(s), n, _d(pos), _d(_f64(box)),
+                                 _i(np.ascontiguousarray(pbc, dtype=np.int32)), int(use_grid),
+                                 _d(q)), "descriptors")
+    return q
+
+
+def forces_subset(model, pos, box, pbc, idx):
+    """Forces (len(idx), 3) and site energies (len(idx)) of the listed atoms."""
+    ihp, dhp = _hp(model)
+    p = _f64(model.params)
+    s = _f64(model.scaler)
+    pos = _f64(pos)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    F = np.zeros((len(idx), 3))
+    U = np.zeros(len(idx))
+    _check(lib().orc_forces_subset(_i(ihp), _d(dhp), _d(p), _d(s), pos.shape[0], _d(pos),
+                                   _d(_f64(box)), _i(np.ascontiguousarray(pbc, dtype=np.int32)),
+                                   len(idx), idx.ctypes.data_as(C.POINTER(C.c_int64)),
+                                   _d(F), _d(U)), "forces_subset")
+    return F, U
+
+
+def site(model, dR, dA):
+    """U^NEP, q (unscaled), dU/dd for radial and angular neighbour lists of one atom."""
+    ihp, dhp = _hp(model)
+    p = _f64(model.params)
+    s = _f64(model.scaler)
+    dR = _f64(np.reshape(dR, (-1, 3)))
+    dA = _f64(np.reshape(dA, (-1, 3)))
+    U = np.zeros(1)
+    q = np.zeros(model.dim)
+    gR = np.zeros_like(dR)
+    gA = np.zeros_like(dA)
+    _check(lib().orc_site(_i(ihp), _d(dhp), _d(p), _d(s), dR.shape[0], _d(dR), dA.shape[0],
+                          _d(dA), _d(U), _d(q), _d(gR), _d(gA)), "site")
+    return float(U[0]), q, gR, gA
+
+
+def md(model, pos, vel, box, pbc, mass, dt_max, nsteps, d_max=0.0, forces=None,
+       use_grid=True):
+    """Velocity-Verlet NVE; returns (pos, vel, forces, thermo[nsteps, 4])."""
+    ihp, dhp = _hp(model)
+    p = _f64(model.params)
+    s = _f64(model.scaler)
+    pos = _f64(pos).copy()
+    vel = _f64(vel).copy()
+    n = pos.shape[0]
+    F = np.zeros((n, 3)) if forces is None else _f64(forces).copy()
+    thermo = np.zeros((nsteps, 4))
+    _check(lib().orc_md(_i(ihp), _d(dhp), _d(p), _d(s), n, _d(pos), _d(vel), _d(F),
+                        0 if forces is None else 1, _d(_f64(box)),
+                        _i(np.ascontiguousarray(pbc, dtype=np.int32)), float(mass),
+                        float(dt_max), float(d_max), int(nsteps), int(use_grid), _d(thermo)),
+           "md")
+    return pos, vel, F, thermo
+
+
+def neighbor_counts(pos, box, pbc, rc, mode=0, maxn=0):
+    """Per-atom neighbour counts within rc (mode 0 brute force, 1 cell grid)
+    and, if maxn > 0, the sorted neighbour distances (N, maxn)."""
+    pos = _f64(pos)
+    n = pos.shape[0]
+    counts = np.zeros(n, np.int32)
+    dist = np.zeros((n, max(maxn, 1)))
+    _check(lib().orc_neighbor_counts(n, _d(pos), _d(_f64(box)),
+                                     _i(np.ascontiguousarray(pbc, dtype=np.int32)), float(rc),
+                                     int(mode), _i(counts), int(maxn),
+                                     _d(dist) if maxn > 0 else None), "neighbor_counts")
+    return counts, (dist if maxn > 0 else None)
+
+
+def cutoff(r, rc):
+    fc, dfc = np.zeros(1), np.zeros(1)
+    lib().orc_cutoff(float(r), float(rc), _d(fc), _d(dfc))
+    return float(fc[0]), float(dfc[0])
+
+
+def chebyshev(x, K):
+    T, dT = np.zeros(K), np.zeros(K)
+    lib().orc_chebyshev(float(x), int(K), _d(T), _d(dT))
+    return T, dT
+
+
+def basis(r, rc, K):
+    f, df = np.zeros(K), np.zeros(K)
+    lib().orc_basis(float(r), float(rc), int(K), _d(f), _d(df))
+    return f, df
+
+
+def legendre(x, lmax):
+    P, dP = np.zeros(lmax + 1), np.zeros(lmax + 1)
+    lib().orc_legendre(float(x), int(lmax), _d(P), _d(dP))
+    return P, dP
+
+
+def zbl(r, Zi=74.0, Zj=74.0, r1=1.0, r2=2.0):
+    U, dU = np.zeros(1), np.zeros(1)
+    lib().orc_zbl(float(r), float(Zi), float(Zj), float(r1), float(r2), _d(U), _d(dU))
+    return float(U[0]), float(dU[0])
+
+
+def fourbody_triple(g, u):
+    g = _f64(g)
+    u = _f64(np.reshape(u, (-1, 3)))
+    return float(lib().orc_fourbody_triple(len(g), _d(g), _d(u)))
