@@ -1,0 +1,367 @@
+"""Benchmark: NEP-ZBL velocity-Verlet MD throughput (atom-steps/s) on one GB300.
+
+Workload (default): the 8,192,000-atom bcc W slab (160^3 cells, a = 3.165 A,
+periodic in x, y, open in z with 30 A of vacuum each side, 300 K velocities
+from seed 5), random-init NEP-ZBL model (seed 1), FP32 descriptors/network
+with FP64 positions/integrator/energy/virial, NVE at dt = 1 fs.  One "step"
+is one MD step: kick-drift, cell binning, neighbour lists, descriptors,
+network, pair forces + ZBL + virial, kick, thermo -- all in the library's CUDA
+kernels, replayed from captured CUDA graphs.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle (the
+only reference that exists for this method) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2305_08140_gb300 import inputs as I  # noqa: E402
+
+METRIC = "atom-steps/s for NEP-ZBL MD at 1M-8M atoms (FP32 vs plain FP64 GPU path); HBM roofline %"
+UNIT = "atom-steps/s"
+WORKLOAD = ("8,192,000-atom bcc W slab (160x160x160 cells, a=3.165 A), periodic x,y, open z "
+            "with 30 A vacuum each side, 300 K (seed 5), NVE dt=1 fs, random-init NEP-ZBL "
+            "(seed 1: r_c 6/4 A, n_max 4/4, basis 8, l_max 4 + 4-body, 30 neurons, ZBL 1/2 A)")
+
+# FP32 issue rate of GB300 used as the ALU roofline: 152 SMs x 128 FP32 lanes
+# x 2 flop per FMA x SM clock.
+SMS = 152
+FP32_LANES = 128
+
+# Algorithmic work of one force evaluation, per atom and per ordered pair.
+# Counted from the arithmetic the method needs in this formulation (an FMA is
+# 2 flop; sqrt, reciprocal, sincospi and tanh count 1 each):
+#   per radial pair, descriptor pass: distance 8, Chebyshev basis T_0..T_8 ~20,
+#     5 radial functions g_n = f_c (C_n + sum_k h_nk T_k) 5*(18+2) = 100   -> 128
+#   per angular pair, descriptor pass: Chebyshev 20, g_n 100, unit vector 4,
+#     24 harmonics ~60, A_nlm += g_n Y_lm 240                               -> 424
+#   per atom: q (120 squares/adds -> 240), 4-body 5*~60 = 300, network
+#     forward 30x30 FMA 1800 + 30 tanh + 60, backward 30x30 FMA 1800,
+#     adjoint dU/dq -> (b_k, A-bar) ~ 400                                   -> 4630
+#   per radial pair, force pass: distance/unit vector 12, Chebyshev with
+#     derivatives 40, sum_k b_k T_k and b_k T'_k 36, force 10, virial 18,
+#     fixed-point conversion/scatter bookkeeping 6                          -> 122
+#   per angular pair, force pass: Chebyshev with derivatives 40,
+#     g_n and g'_n 190, harmonics 60, G_lm and G'_lm 480, S 96,
+#     gradient polynomial contraction ~200, assembly 12                     -> 1078
+FLOP_ATOM = 4630
+FLOP_PAIR_R = 128 + 122
+FLOP_PAIR_A = 424 + 1078
+# Algorithmic DRAM bytes of the force kernel per atom and per ordered pair:
+# own position (16) + counts (8) + site energy/partials (~1) per atom; per
+# pair the neighbour entry read twice (8) and the 3 x 8-byte force update
+# (read-modify-write 48) -- the neighbour position reads hit L1/L2.
+BYTES_ATOM = 25
+BYTES_PAIR = 56
+
+
+def _measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline_sample(seconds_hint: float = 20.0) -> dict:
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    one velocity-Verlet step of a laterally cut piece of the slab (the full
+    160-cell depth and both free surfaces, 12 x 12 cells across, 46,080 atoms),
+    on every host thread it uses."""
+    from oracle import oracle as O
+    nl = 12
+    pos = I.bcc(nl, nl, 160)
+    pos[:, 2] += 30.0
+    L = nl * I.A_W
+    box = np.array([L, L, 160 * I.A_W + 60.0])
+    pbc = np.array([1, 1, 0], np.int32)
+    vel = I.maxwell_boltzmann(np.random.default_rng(5), len(pos), 300.0)
+    model = I.nep_model(1)
+    # forces at the start are part of the step's work only once
+    t0 = time.perf_counter()
+    O.md(model, pos, vel, box, pbc, I.MASS_W, 1.0, 1)
+    dt = time.perf_counter() - t0
+    n = len(pos)
+    return {"value": n * 2 / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": (f"FP64 oracle velocity-Verlet step of a {nl}x{nl}x160-cell cut of the "
+                       f"slab ({n} atoms, open z, periodic x,y): initial forces + 1 step = 2 "
+                       f"force evaluations in {dt:.1f} s; value counts atom-evaluations/s")}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    nl = 12
+    pos = I.bcc(nl, nl, 160)
+    pos[:, 2] += 30.0
+    L = nl * I.A_W
+    box = np.array([L, L, 160 * I.A_W + 60.0])
+    pbc = np.array([1, 1, 0], np.int32)
+    vel = I.maxwell_boltzmann(np.random.default_rng(5), len(pos), 300.0)
+    model = I.nep_model(1)
+    p, v, F, _ = O.md(model, pos, vel, box, pbc, I.MASS_W, 1.0, max(args.warmup, 0))
+    t0 = time.perf_counter()
+    p, v, F, _ = O.md(model, p, v, box, pbc, I.MASS_W, 1.0, args.steps, forces=F)
+    dt = time.perf_counter() - t0
+    n = len(pos)
+    value = n * args.steps / dt
+    sample = (f"FP64 oracle velocity-Verlet on a {nl}x{nl}x160-cell cut of the slab "
+              f"({n} atoms, open z, periodic x,y), {args.steps} steps")
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2305_08140_gb300 import nepzbl as N
+
+    s = I.c5()
+    n = s.n
+    model = I.nep_model(1)
+    nep = N.NEP(model, "fp32")
+    dev = torch.device("cuda", local)
+    x = N.to_device_soa(s.pos, dev)
+    v = N.to_device_soa(s.vel, dev)
+    st = N.MDState(x, v, s.box, s.pbc, dt_max=1.0)
+    nep.set_option(N.NEP_OPT_GRAPH_CHUNK, 25)
+    stream = torch.cuda.current_stream()
+
+    # warm-up (includes the first force evaluation and graph capture)
+    nep.md(st, max(args.warmup, 1))
+    torch.cuda.synchronize()
+    nep.set_option(N.NEP_OPT_TIMING, 1)
+    # capture every graph length the timed run uses outside the timed region
+    nep.md(st, min(25, args.steps))
+    if args.steps % 25 and args.steps > 25:
+        nep.md(st, args.steps % 25)
+    nep.reset_stats()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    nep.md(st, args.steps, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    stats = nep.stats()
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * n * args.steps / (ms * 1e-3)
+
+    # roofline of the dominant kernel (the force kernel), timed inside the region
+    peaks, peak_kind = _measured_peaks()
+    k_ms = stats["timed_ms"] / max(stats["timed_launches"], 1)
+    pr, pa = stats["pairs_radial"], stats["pairs_angular"]
+    flop = FLOP_ATOM * n + FLOP_PAIR_R * pr + FLOP_PAIR_A * pa
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+    achieved = flop / (k_ms * 1e-3) / 1e12
+    bytes_alg = BYTES_ATOM * n + BYTES_PAIR * pr
+    hbm_achieved = bytes_alg / (k_ms * 1e-3) / 1e9
+    launches = stats["kernel_launches"]
+
+    # FP64 path on the same workload (a few steps)
+    nep.set_option(N.NEP_OPT_TIMING, 0)
+    fp64 = None
+    if not args.skip_fp64:
+        nep64 = N.NEP(model, "fp64")
+        st64 = N.MDState(N.to_device_soa(s.pos, dev), N.to_device_soa(s.vel, dev), s.box, s.pbc,
+                         dt_max=1.0)
+        nep64.set_option(N.NEP_OPT_GRAPH_CHUNK, 2)
+        nep64.md(st64, 1)
+        torch.cuda.synchronize()
+        k64 = 2
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        nep64.md(st64, k64, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64 = {"value": n * k64 / (e0.elapsed_time(e1) * 1e-3), "unit": UNIT, "steps": k64,
+                "dtype": "f64"}
+        nep64.close()
+        del st64
+
+    # end to end through the public API with host buffers: each step copies
+    # x, v, F from pinned host memory, runs one MD step and reads x, v, F and E back
+    k_e2e = max(1, min(args.steps, 10))
+    hx = st.xyz.cpu().pin_memory()
+    hv = st.vel.cpu().pin_memory()
+    hf = st.forces.cpu().pin_memory()
+    dx, dv, df = st.xyz, st.vel, st.forces
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        dx.copy_(hx, non_blocking=True)
+        dv.copy_(hv, non_blocking=True)
+        df.copy_(hf, non_blocking=True)
+        nep.md(st, 1, stream)
+        hx.copy_(dx, non_blocking=True)
+        hv.copy_(dv, non_blocking=True)
+        hf.copy_(df, non_blocking=True)
+        torch.cuda.synchronize()
+        _ = st.potential_energy
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": ws * n * k_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 9 * 8 * n,
+           "d2h_bytes_per_step": 9 * 8 * n + 8, "steps": k_e2e}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.skip_cpu:
+        cpu = cpu_baseline_sample()
+
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded bcc W lattice, random-init NEP-ZBL weights)",
+        "config": {"workload": WORKLOAD, "atoms": n, "precision": "fp32 descriptors/network/forces,"
+                   " fp64 positions/integrator/energy/virial", "parallelism": "replicas" if ws > 1
+                   else "single GPU", "l2": "inputs larger than L2 (state ~0.6 GB, lists ~3 GB)",
+                   "graph_chunk": 25},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "roofline": {"bound": "alu", "kernel": "k_nep (descriptors+network+forces)",
+                     "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": None,
+                     "peak_kind": f"FP32 issue rate {SMS} SMs x {FP32_LANES} lanes x 2 x "
+                                  f"{sm_mhz:.0f} MHz (sm_max_mhz, {peak_kind})",
+                     "kernel_ms": k_ms, "flop_per_launch": flop,
+                     "hbm_achieved_gbs": hbm_achieved, "hbm_peak_gbs": peaks.get("hbm_gbs"),
+                     "hbm_frac": hbm_achieved / float(peaks.get("hbm_gbs", 6800.0)),
+                     "kernel_share": stats["timed_ms"] / ms if ms > 0 else None,
+                     "pairs_radial": pr, "pairs_angular": pa},
+        "fp64_path": fp64,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

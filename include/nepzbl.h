@@ -1,0 +1,185 @@
+/*
+ * nepzbl.h -- C ABI of the GB300 NEP-ZBL library (libnepzbl.so).
+ *
+ * The library evaluates the NEP-ZBL potential of arXiv:2305.08140 and runs
+ * velocity-Verlet molecular dynamics with it on one NVIDIA GPU (sm_103a):
+ *
+ *   E = sum_i U_i,  U_i = U_i^NEP({q_nu^i}) + 1/2 sum_{j != i} U_ZBL(r_ij)   (Eq. 1)
+ *   U_ZBL(r) = e^2/(4 pi eps0) Zi Zj / r * phi(r/a) * f_c(r)                  (Eq. 2)
+ *   phi(x) = 0.32825 e^{-2.54931x} + 0.09219 e^{-0.29182x} + 0.58110 e^{-0.59231x}  (Eq. 3)
+ *   a = 0.46848 / (Zi^0.23 + Zj^0.23)                                         (Eq. 4)
+ *   f_c: Tersoff switch between zbl_r_inner and zbl_r_outer                   (Sec. II.A)
+ *
+ * U^NEP is a one-hidden-layer tanh network of a descriptor with Chebyshev
+ * radial and Legendre angular components (Sec. II.A).  The descriptor read
+ * here (the same contract the tests' FP64 CPU checker follows):
+ *   f_k(r) = (T_k(2 (r/rc - 1)^2 - 1) + 1)/2 * (1 + cos(pi r/rc))/2,
+ *   g_n(r) = sum_k c_nk f_k(r),
+ *   q_n    = sum_j g^R_n(r_ij)                                   (n = 0..n_max_radial)
+ *   q_nl   = sum_j sum_k g^A_n(r_ij) g^A_n(r_ik) P_l(cos theta_ijk) (l = 1..l_max)
+ *   q4_n   = tr(T_n^3), T_n = sum_j g^A_n(r_ij) (u_ij u_ij^T - I/3)
+ *   U^NEP  = sum_mu w1_mu tanh(sum_nu w0_{mu nu} s_nu q_nu - b0_mu) - b1.
+ * Forces F = -dE/dr; virial W_ab = -sum_i sum_j (dU_i/dr_ij)_a (r_ij)_b with
+ * r_ij = r_j - r_i (so P = (2 KE + tr W) / (3 V)).
+ * Units: A, eV, eV/A, amu, fs.
+ *
+ * Memory: every array argument documented "device" is a pointer to GPU
+ * memory owned by the caller (for example a torch tensor's data_ptr); the
+ * library never frees it.  "host" arguments are ordinary CPU memory.  The
+ * library owns its context and all scratch memory (cell lists, neighbour
+ * lists, accumulators, CUDA graphs) and frees it in nep_free.
+ *
+ * Streams: all GPU work of a call is issued on the caller's stream
+ * (cudaStream_t passed as void*, NULL = legacy default stream) and the call
+ * returns after that stream has finished the call's work.  A context must not
+ * be used from two threads at once.
+ *
+ * Errors: every int-returning call returns NEP_OK (0) or a negative
+ * NEP_ERR_* code and never aborts the process; nep_last_error gives a
+ * message.  GPU-side problems (neighbour overflow, non-finite values) are
+ * reported through a device status word read after the stream sync.
+ */
+#ifndef NEPZBL_H
+#define NEPZBL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NEP_OK                 0
+#define NEP_ERR_INVALID_ARG   (-1)  /* bad pointer, size, or parameter */
+#define NEP_ERR_CUDA          (-2)  /* a CUDA runtime call failed */
+#define NEP_ERR_NBR_OVERFLOW  (-3)  /* neighbour capacity exceeded and could not grow */
+#define NEP_ERR_BOX           (-4)  /* box not diagonal, not positive, or too small */
+#define NEP_ERR_NONFINITE     (-5)  /* NaN/Inf in positions, energies or forces */
+#define NEP_ERR_ATOM_LOST     (-6)  /* reserved: atom outside any representable cell */
+#define NEP_ERR_UNSUPPORTED   (-7)  /* model sizes this build was not compiled for */
+
+/* Arithmetic of the force evaluation. */
+#define NEP_FP32  0   /* FP32 descriptors/network/forces; FP64 positions, integrator,
+                         energy and virial sums; deterministic fixed-point force sums */
+#define NEP_FP64  1   /* every step in FP64 (reference path) */
+
+typedef struct nep_ctx nep_ctx;   /* opaque; created by nep_init */
+
+/* Model definition, copied by nep_init (the caller may free it afterwards).
+ * This build supports n_types = 1, n_max_radial = n_max_angular = 4,
+ * basis_size_radial = basis_size_angular = 8, l_max = 4, use_4body = 1,
+ * n_hidden = 30 (descriptor length D = 30, 1051 parameters), with
+ * zbl_r_outer <= rc_angular <= rc_radial. */
+typedef struct nep_params {
+    int32_t n_types;                 /* number of species (1) */
+    int32_t z[4];                    /* nuclear charge Z per species (Eq. 2, 4) */
+    double  mass[4];                 /* mass per species (amu), used by md_step */
+    double  rc_radial;               /* r_c^R (A) */
+    double  rc_angular;              /* r_c^A (A) */
+    double  zbl_r_inner;             /* Tersoff switch inner radius (A) */
+    double  zbl_r_outer;             /* Tersoff switch outer radius (A) */
+    int32_t n_max_radial;            /* radial functions n = 0..n_max_radial */
+    int32_t n_max_angular;           /* angular functions n = 0..n_max_angular */
+    int32_t basis_size_radial;       /* Chebyshev k = 0..basis_size_radial */
+    int32_t basis_size_angular;      /* Chebyshev k = 0..basis_size_angular */
+    int32_t l_max;                   /* Legendre orders l = 1..l_max */
+    int32_t use_4body;               /* 1: append q4_n = tr(T_n^3) */
+    int32_t n_hidden;                /* hidden tanh neurons */
+    const double* params;            /* host, flat: w0[H][D] row-major, b0[H], w1[H], b1,
+                                        cR[nR][KR], cA[nA][KA] */
+    int64_t n_params;                /* length of params */
+    const double* q_scaler;          /* host, length D: s_nu */
+} nep_params;
+
+/* Creates a context for one model.  precision = NEP_FP32 or NEP_FP64.
+ * Selects the current CUDA device.  On success *out owns the context. */
+int nep_init(const nep_params* p, int precision, nep_ctx** out);
+
+/* Frees the context and all memory it owns (NULL is allowed). */
+void nep_free(nep_ctx* ctx);
+
+/* Message of the last error of this context (or of the last failed nep_init
+ * when ctx is NULL).  Valid until the next call on the context. */
+const char* nep_last_error(const nep_ctx* ctx);
+
+/* One force evaluation (Eq. 1-4 and the descriptor above).
+ *   n_atoms      number of atoms (0 allowed; < 2^26)
+ *   xyz          device double[3 * n_atoms], SoA: x[0..n), y[0..n), z[0..n) (A)
+ *   box          host double[9], row-major 3x3 cell; must be diagonal.
+ *                A periodic dimension needs box[d][d] >= 3 * rc_radial.  For an
+ *                open dimension, box[d][d] is the extent [0, L) over which the
+ *                cell grid is laid (atoms outside it are still handled).
+ *   types        device int32[n_atoms] species index (all 0 in this build)
+ *   pbc          host int32[3], 1 periodic, 0 open
+ *   energy       host double[1]: E (eV)
+ *   forces       device double[3 * n_atoms], SoA (eV/A), overwritten
+ *   virial       host double[9], row-major W (eV), or NULL
+ *   site_energy  device double[n_atoms]: U_i (eV), or NULL
+ *   stream       cudaStream_t or NULL
+ * Grows its neighbour capacity and repeats the evaluation when an atom has
+ * more neighbours than fit. */
+int nep_compute(nep_ctx* ctx, int64_t n_atoms, const double* xyz, const double box[9],
+                const int32_t* types, const int32_t pbc[3], double* energy, double* forces,
+                double* virial, double* site_energy, void* stream);
+
+/* State of an MD run.  Pointers are device memory owned by the caller. */
+typedef struct nep_md_state {
+    int64_t n_atoms;
+    double* xyz;            /* device double[3n] SoA positions (A), advanced in place;
+                               periodic coordinates are wrapped into [0, L) */
+    double* vel;            /* device double[3n] SoA velocities (A/fs) */
+    double* forces;         /* device double[3n] SoA forces at xyz (eV/A) */
+    const int32_t* types;   /* device int32[n] */
+    double box[9];          /* host copy of the cell (see nep_compute) */
+    int32_t pbc[3];
+    int32_t forces_valid;   /* in/out: 0 = md_step first computes forces at xyz */
+    double dt_max;          /* time step or its upper limit (fs) */
+    double d_max;           /* > 0: dt = min(dt_max, d_max / max_i |v_i|) before each
+                               step (Sec. II.B); <= 0: fixed dt = dt_max */
+    /* outputs, updated by md_step */
+    double time;            /* accumulated simulated time (fs) */
+    int64_t step;           /* accumulated number of steps */
+    double dt_last;         /* time step of the last step (fs) */
+    double potential_energy;/* E after the last step (eV) */
+    double kinetic_energy;  /* KE after the last step (eV) */
+    double virial[9];       /* W after the last step (eV) */
+} nep_md_state;
+
+/* Advances the state by n_steps velocity-Verlet NVE steps (Sec. II.B):
+ *   v += dt/2 F/m; x += dt v; F = F(x); v += dt/2 F/m.
+ * Steps are replayed from captured CUDA graphs in chunks; if a chunk
+ * overflows the neighbour capacity the chunk is rolled back from a device
+ * copy, the capacity grows and the chunk runs again. */
+int md_step(nep_ctx* ctx, nep_md_state* state, int n_steps, void* stream);
+
+/* Counters of a context (for benchmarks and tests). */
+typedef struct nep_stats {
+    int64_t kernel_launches;    /* kernels launched by this context (graph nodes counted) */
+    int64_t timed_launches;     /* force-kernel launches timed while timing was on */
+    double  timed_ms;           /* their summed duration (CUDA events, ms) */
+    int64_t pairs_radial;       /* ordered pairs r < rc_radial in the last evaluation */
+    int64_t pairs_angular;      /* ordered pairs r < rc_angular in the last evaluation */
+    int32_t max_nbr_radial;     /* largest per-atom count in the last evaluation */
+    int32_t max_nbr_angular;
+    int32_t nbr_capacity;       /* current neighbour slots per atom */
+    int32_t graph_chunk;        /* MD steps per captured graph */
+} nep_stats;
+
+int nep_get_stats(const nep_ctx* ctx, nep_stats* out);
+
+/* Options: NEP_OPT_TIMING (0/1) times every force-kernel launch with CUDA
+ * events (also inside MD graphs); NEP_OPT_GRAPH_CHUNK sets the MD steps per
+ * captured graph (>= 1); NEP_OPT_NBR_CAPACITY sets the neighbour slots per
+ * atom (grows automatically when exceeded). */
+#define NEP_OPT_TIMING        1
+#define NEP_OPT_GRAPH_CHUNK   2
+#define NEP_OPT_NBR_CAPACITY  3
+int nep_set_option(nep_ctx* ctx, int option, int64_t value);
+
+/* Resets the counters of nep_stats (launches, timing). */
+int nep_reset_stats(nep_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NEPZBL_H */

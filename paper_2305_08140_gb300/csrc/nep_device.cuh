@@ -1,0 +1,801 @@
+// nep_device.cuh -- CUDA kernels of one NEP-ZBL force evaluation and of the
+// velocity-Verlet step, templated on the arithmetic type R (float: mixed
+// precision path; double: plain FP64 path).
+//
+// Data layout (all in HBM, owned by the context):
+//   x, v, F        double SoA [3][n] in the caller's atom order
+//   perm[k]        caller index of the k-th atom in cell order
+//   pos4[k]        (x, y, z) relative to the origin of the atom's cell, in R,
+//                  .w = species; k in cell order (16 B per atom for float)
+//   cell_start[c]  first cell-ordered slot of cell c (cells row-major x,y,z)
+//   nbr[s * ld + k]  neighbour slot s of atom k: (m << 5) | stencil code, m in
+//                  cell order; slots [0, na) hold r < rc_A (also radial),
+//                  slots [M - nro, M) hold rc_A <= r < rc_R
+//   facc[a * ld + k] force accumulators in cell order: int64 fixed point
+//                  (2^-32 eV/A) for float, double for double
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nep_math.cuh"
+
+namespace nepk {
+
+constexpr int NR = 5, NA = 5, KR = 9, KA = 9, LM = 4, NLM = 24, H = 30;
+constexpr int D = NR + NA * LM + NA;   // 30
+constexpr int TILE = 128;              // atoms per block of the force kernel
+constexpr int NPART = 10;              // energy + 9 virial components per tile
+
+// status bits
+constexpr int ST_OVERFLOW = 1, ST_NONFINITE = 2, ST_FORCE_RANGE = 4;
+
+template <typename R> struct V4 { using T = float4; };
+template <> struct V4<double> { using T = double4; };
+
+// Model constants passed by value as a kernel argument (constant bank).
+template <typename R>
+struct Model {
+    R w0[H * D];        // w0[mu][nu] * s_nu
+    R b0[H], w1[H], b1;
+    R hR[NR * KR], CR[NR];   // c/2 and sum_k c/2 (radial)
+    R hA[NA * KA], CA[NA];   // angular
+    R rcR2, rcA2, inv_rcR, inv_rcA;
+    R zbl_r2;                // outer switch radius (pair test)
+    double zbl_k;            // e^2/(4 pi eps0) Zi Zj (eV A)
+    double zbl_inv_a;        // 1 / a (Eq. 4)
+    double zbl_r1, zbl_rr2;  // switch radii
+};
+
+// Cell grid and sizes.
+struct Grid {
+    int nc[3];
+    int pbc[3];
+    double lc[3], inv_lc[3];   // cell edge
+    double L[3], invL[3];      // box (periodic wrap)
+    int n;                     // atoms
+    int ld;                    // leading dimension of nbr / facc (atom capacity)
+    int M;                     // neighbour slots per atom
+};
+
+// ----------------------------------------------------------------------------
+// Binning: cell of each atom, slot within the cell (atomic), counting sort
+// ----------------------------------------------------------------------------
+
+__device__ __forceinline__ int cell_coord(double x, int d, const Grid& g, double& xw)
+{
+    if (g.pbc[d]) x -= g.L[d] * floor(x * g.invL[d]);
+    xw = x;
+    int c = (int)floor(x * g.inv_lc[d]);
+    c = c < 0 ? 0 : c;
+    c = c >= g.nc[d] ? g.nc[d] - 1 : c;
+    return c;
+}
+
+__global__ void k_bin_count(Grid g, const double* __restrict__ x, int* __restrict__ cell_of,
+                            int* __restrict__ slot_of, int* __restrict__ count,
+                            int* __restrict__ status)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    double p[3] = {x[i], x[g.n + i], x[2 * g.n + i]};
+    int c[3];
+    bool bad = false;
+    for (int d = 0; d < 3; ++d) {
+        if (!isfinite(p[d])) { bad = true; p[d] = 0.0; }
+        double w;
+        c[d] = cell_coord(p[d], d, g, w);
+    }
+    if (bad) atomicOr(status, ST_NONFINITE);
+    int cell = (c[0] * g.nc[1] + c[1]) * g.nc[2] + c[2];
+    cell_of[i] = cell;
+    slot_of[i] = atomicAdd(&count[cell], 1);
+}
+
+// exclusive scan of count[0..nc) into start[0..nc], 1024 items per block
+constexpr int SCAN_T = 256, SCAN_ITEMS = 4, SCAN_B = SCAN_T * SCAN_ITEMS;
+
+__device__ __forceinline__ int block_excl_scan(int v, int* sh, int& total)
+{
+    // inclusive warp scan
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int s = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += t;
+    }
+    if (lane == 31) sh[w] = s;
+    __syncthreads();
+    if (w == 0) {
+        int nw = blockDim.x >> 5;
+        int t = lane < nw ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += u;
+        }
+        if (lane < nw) sh[lane] = t;
+    }
+    __syncthreads();
+    int before = (w > 0 ? sh[w - 1] : 0);
+    total = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before + s - v;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_blocks(const int* __restrict__ in, int n,
+                                                        int* __restrict__ out,
+                                                        int* __restrict__ block_sums)
+{
+    __shared__ int sh[32];
+    int base = blockIdx.x * SCAN_B + threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS], sum = 0;
+#pragma unroll
+    for (int t = 0; t < SCAN_ITEMS; ++t) {
+        v[t] = (base + t < n) ? in[base + t] : 0;
+        sum += v[t];
+    }
+    int total;
+    int ex = block_excl_scan(sum, sh, total);
+#pragma unroll
+    for (int t = 0; t < SCAN_ITEMS; ++t) {
+        if (base + t < n) out[base + t] = ex;
+        ex += v[t];
+    }
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+// one block: exclusive scan of up to SCAN_B block sums; writes out[n] = total
+__global__ void __launch_bounds__(SCAN_T) k_scan_sums(int* __restrict__ sums, int nb,
+                                                      int* __restrict__ out, int n)
+{
+    __shared__ int sh[32];
+    int base = threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS], sum = 0;
+#pragma unroll
+    for (int t = 0; t < SCAN_ITEMS; ++t) {
+        v[t] = (base + t < nb) ? sums[base + t] : 0;
+        sum += v[t];
+    }
+    int total;
+    int ex = block_excl_scan(sum, sh, total);
+#pragma unroll
+    for (int t = 0; t < SCAN_ITEMS; ++t) {
+        if (base + t < nb) sums[base + t] = ex;
+        ex += v[t];
+    }
+    if (threadIdx.x == 0) out[n] = total;
+}
+
+__global__ void k_scan_add(int* __restrict__ out, int n, const int* __restrict__ sums)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += sums[i / SCAN_B];
+}
+
+__global__ void k_bin_scatter(int n, const int* __restrict__ cell_of,
+                              const int* __restrict__ slot_of, const int* __restrict__ start,
+                              int* __restrict__ perm)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    perm[start[cell_of[i]] + slot_of[i]] = i;
+}
+
+// One thread per cell: order the cell's atoms by caller index (so everything
+// downstream is independent of the atomic slot order) and write their
+// cell-relative positions.
+template <typename R>
+__global__ void k_cell_finalize(Grid g, int ncell, const int* __restrict__ start,
+                                int* __restrict__ perm, const double* __restrict__ x,
+                                const int32_t* __restrict__ types,
+                                typename V4<R>::T* __restrict__ pos4,
+                                int* __restrict__ cell_sorted)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    int b = start[c], e = start[c + 1];
+    for (int s = b + 1; s < e; ++s) {
+        int v = perm[s], t = s;
+        while (t > b && perm[t - 1] > v) { perm[t] = perm[t - 1]; --t; }
+        perm[t] = v;
+    }
+    int cz = c % g.nc[2], cy = (c / g.nc[2]) % g.nc[1], cx = c / (g.nc[2] * g.nc[1]);
+    int cc[3] = {cx, cy, cz};
+    for (int s = b; s < e; ++s) {
+        int i = perm[s];
+        R rel[3];
+        for (int d = 0; d < 3; ++d) {
+            double p = x[d * g.n + i];
+            if (!isfinite(p)) p = 0.0;
+            double w;
+            cell_coord(p, d, g, w);
+            rel[d] = (R)(w - cc[d] * g.lc[d]);
+        }
+        typename V4<R>::T q;
+        q.x = rel[0]; q.y = rel[1]; q.z = rel[2];
+        q.w = (R)types[i];
+        pos4[s] = q;
+        cell_sorted[s] = c;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Neighbour lists: 27-cell stencil, minimum image through the stencil offset
+// ----------------------------------------------------------------------------
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_neighbors(Grid g, R rcR2, R rcA2,
+                                                   const typename V4<R>::T* __restrict__ pos4,
+                                                   const int* __restrict__ cell_sorted,
+                                                   const int* __restrict__ start,
+                                                   int* __restrict__ nbr, int2* __restrict__ cnt,
+                                                   int* __restrict__ status,
+                                                   int* __restrict__ maxc,
+                                                   unsigned long long* __restrict__ pairs)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    int na = 0, nro = 0, sa = 0, sro = 0;
+    if (k < g.n) {
+        typename V4<R>::T p = pos4[k];
+        int c = cell_sorted[k];
+        int cz = c % g.nc[2], cy = (c / g.nc[2]) % g.nc[1], cx = c / (g.nc[2] * g.nc[1]);
+        const int M = g.M;
+        for (int ox = -1; ox <= 1; ++ox) {
+            int X = cx + ox;
+            if (g.pbc[0]) X = (X + g.nc[0]) % g.nc[0];
+            else if (X < 0 || X >= g.nc[0]) continue;
+            R offx = (R)(ox * g.lc[0]);
+            for (int oy = -1; oy <= 1; ++oy) {
+                int Y = cy + oy;
+                if (g.pbc[1]) Y = (Y + g.nc[1]) % g.nc[1];
+                else if (Y < 0 || Y >= g.nc[1]) continue;
+                R offy = (R)(oy * g.lc[1]);
+                for (int oz = -1; oz <= 1; ++oz) {
+                    int Z = cz + oz;
+                    if (g.pbc[2]) Z = (Z + g.nc[2]) % g.nc[2];
+                    else if (Z < 0 || Z >= g.nc[2]) continue;
+                    R offz = (R)(oz * g.lc[2]);
+                    int code = (ox + 1) * 9 + (oy + 1) * 3 + (oz + 1);
+                    int c2 = (X * g.nc[1] + Y) * g.nc[2] + Z;
+                    int e = start[c2 + 1];
+                    for (int m = start[c2]; m < e; ++m) {
+                        if (m == k) continue;
+                        typename V4<R>::T q = pos4[m];
+                        R dx = q.x - p.x + offx, dy = q.y - p.y + offy, dz = q.z - p.z + offz;
+                        R r2 = dx * dx + dy * dy + dz * dz;
+                        if (r2 < rcR2) {
+                            bool ang = r2 < rcA2;
+                            if (sa + sro < M) {
+                                int ent = (m << 5) | code;
+                                if (ang) nbr[(size_t)(sa++) * g.ld + k] = ent;
+                                else nbr[(size_t)(M - 1 - sro++) * g.ld + k] = ent;
+                            }
+                            if (ang) ++na; else ++nro;
+                        }
+                    }
+                }
+            }
+        }
+        cnt[k] = make_int2(sa, sro);
+        if (na + nro > M) atomicOr(status, ST_OVERFLOW);
+    }
+    // statistics: block maxima and pair sums
+    int tot = na + nro;
+    unsigned long long pr = (unsigned long long)tot, pa = (unsigned long long)na;
+    for (int o = 16; o > 0; o >>= 1) {
+        tot = max(tot, __shfl_xor_sync(0xffffffffu, tot, o));
+        na = max(na, __shfl_xor_sync(0xffffffffu, na, o));
+        pr += __shfl_xor_sync(0xffffffffu, pr, o);
+        pa += __shfl_xor_sync(0xffffffffu, pa, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (tot > 0) atomicMax(&maxc[0], tot);
+        if (na > 0) atomicMax(&maxc[1], na);
+        if (pr) atomicAdd(&pairs[0], pr);
+        if (pa) atomicAdd(&pairs[1], pa);
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Force accumulation policy
+// ----------------------------------------------------------------------------
+
+template <typename R> struct Acc;
+
+// FP32 path: 64-bit fixed point with 2^-32 eV/A resolution; integer sums do
+// not depend on the order of the atomics, so the forces are deterministic.
+template <> struct Acc<float> {
+    using T = long long;
+    static constexpr double SCALE = 4294967296.0;
+    __device__ static __forceinline__ long long conv(float f)
+    {
+        return __float2ll_rn(f * 4294967296.0f);
+    }
+    __device__ static __forceinline__ long long convd(double f)
+    {
+        return __double2ll_rn(f * 4294967296.0);
+    }
+    __device__ static __forceinline__ void add(long long* p, long long v)
+    {
+        atomicAdd(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));
+    }
+    __device__ static __forceinline__ double value(long long v) { return (double)v * (1.0 / 4294967296.0); }
+};
+
+template <> struct Acc<double> {
+    using T = double;
+    __device__ static __forceinline__ double conv(double f) { return f; }
+    __device__ static __forceinline__ double convd(double f) { return f; }
+    __device__ static __forceinline__ void add(double* p, double v) { atomicAdd(p, v); }
+    __device__ static __forceinline__ double value(double v) { return v; }
+};
+
+// ZBL pair term of Eq. 2-4 with the Tersoff switch, in FP64: U and dU/dr.
+__device__ __forceinline__ void zbl_pair(double r, double k, double inv_a, double r1, double r2,
+                                         double& U, double& dU)
+{
+    double x = r * inv_a;
+    double e1 = 0.32825 * exp(-2.54931 * x);
+    double e2 = 0.09219 * exp(-0.29182 * x);
+    double e3 = 0.58110 * exp(-0.59231 * x);
+    double phi = e1 + e2 + e3;
+    double dphi = -(2.54931 * e1 + 0.29182 * e2 + 0.59231 * e3);   // d phi / dx
+    double fc = 1.0, dfc = 0.0;
+    if (r >= r1) {
+        double s, c;
+        sincospi((r - r1) / (r2 - r1), &s, &c);
+        fc = 0.5 + 0.5 * c;
+        dfc = -0.5 * M_PI / (r2 - r1) * s;
+    }
+    double inv_r = 1.0 / r;
+    double v = k * inv_r * phi;
+    double dv = -v * inv_r + k * inv_r * dphi * inv_a;
+    U = v * fc;
+    dU = dv * fc + v * dfc;
+}
+
+template <typename R>
+__device__ __forceinline__ void stencil_offset(int code, const Grid& g, R& ox, R& oy, R& oz)
+{
+    int a = code / 9, b = (code / 3) % 3, c = code % 3;
+    ox = (R)((a - 1) * g.lc[0]);
+    oy = (R)((b - 1) * g.lc[1]);
+    oz = (R)((c - 1) * g.lc[2]);
+}
+
+// ----------------------------------------------------------------------------
+// The force kernel: one thread per atom (cell order), 128 atoms per block.
+// Descriptor sums -> network and its backward -> pair forces scattered to
+// both atoms of each pair -> per-tile energy and virial.
+// ----------------------------------------------------------------------------
+
+template <typename R>
+__global__ void __launch_bounds__(TILE) k_nep(const Model<R> P, const Grid g,
+                                              const typename V4<R>::T* __restrict__ pos4,
+                                              const int* __restrict__ nbr,
+                                              const int2* __restrict__ cnt,
+                                              const int* __restrict__ perm,
+                                              const double* __restrict__ x64,
+                                              typename Acc<R>::T* __restrict__ facc,
+                                              double* __restrict__ partials,
+                                              double* __restrict__ site_energy,
+                                              int* __restrict__ status)
+{
+    using A_ = Acc<R>;
+    const int k = blockIdx.x * TILE + threadIdx.x;
+    const int M = g.M;
+    const size_t ld = (size_t)g.ld;
+    double e_site = 0.0;
+    double wv[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) wv[t] = 0.0;
+
+    if (k < g.n) {
+        const typename V4<R>::T pi = pos4[k];
+        const int2 c2 = cnt[k];
+        const int na = c2.x, nro = c2.y;
+
+        // ---------------- descriptor sums ----------------
+        R qR[NR];
+        R A[NA][NLM];
+#pragma unroll
+        for (int n = 0; n < NR; ++n) qR[n] = R(0);
+#pragma unroll
+        for (int n = 0; n < NA; ++n)
+#pragma unroll
+            for (int lm = 0; lm < NLM; ++lm) A[n][lm] = R(0);
+
+        for (int s = 0; s < na + nro; ++s) {
+            const int slot = s < na ? s : M - nro + (s - na);
+            const int ent = nbr[slot * ld + k];
+            const int m = ent >> 5;
+            R ox, oy, oz;
+            stencil_offset(ent & 31, g, ox, oy, oz);
+            const typename V4<R>::T pj = pos4[m];
+            const R dx = pj.x - pi.x + ox, dy = pj.y - pi.y + oy, dz = pj.z - pi.z + oz;
+            const R r = nepm::nep_sqrt(dx * dx + dy * dy + dz * dz);
+            R T[KR], dT[KR], fc, dfc, dxdr;
+            nepm::cheb<KR, false>(r, P.inv_rcR, T, dT, fc, dfc, dxdr);
+#pragma unroll
+            for (int n = 0; n < NR; ++n) {
+                R acc = P.CR[n];
+#pragma unroll
+                for (int kk = 0; kk < KR; ++kk) acc += P.hR[n * KR + kk] * T[kk];
+                qR[n] += fc * acc;
+            }
+            if (s < na) {
+                nepm::cheb<KA, false>(r, P.inv_rcA, T, dT, fc, dfc, dxdr);
+                const R inv_r = R(1) / r;
+                R Y[NLM];
+                nepm::harmonics(dx * inv_r, dy * inv_r, dz * inv_r, Y);
+#pragma unroll
+                for (int n = 0; n < NA; ++n) {
+                    R acc = P.CA[n];
+#pragma unroll
+                    for (int kk = 0; kk < KA; ++kk) acc += P.hA[n * KA + kk] * T[kk];
+                    const R gn = fc * acc;
+#pragma unroll
+                    for (int lm = 0; lm < NLM; ++lm) A[n][lm] += gn * Y[lm];
+                }
+            }
+        }
+
+        // ---------------- network (descriptor consumed on the fly) -----------
+        R h[H];
+#pragma unroll
+        for (int mu = 0; mu < H; ++mu) h[mu] = -P.b0[mu];
+#pragma unroll
+        for (int nu = 0; nu < NR; ++nu)
+#pragma unroll
+            for (int mu = 0; mu < H; ++mu) h[mu] += P.w0[mu * D + nu] * qR[nu];
+#pragma unroll
+        for (int l = 1; l <= LM; ++l) {
+            const int lo = l * l - 1, hi = (l + 1) * (l + 1) - 1;   // harmonic range
+#pragma unroll
+            for (int n = 0; n < NA; ++n) {
+                R q = R(0);
+#pragma unroll
+                for (int lm = lo; lm < hi; ++lm) q += A[n][lm] * A[n][lm];
+                const int nu = NR + (l - 1) * NA + n;
+#pragma unroll
+                for (int mu = 0; mu < H; ++mu) h[mu] += P.w0[mu * D + nu] * q;
+            }
+        }
+#pragma unroll
+        for (int n = 0; n < NA; ++n) {
+            const R q4 = nepm::fourbody(&A[n][3], (R*)nullptr);
+            const int nu = NR + LM * NA + n;
+#pragma unroll
+            for (int mu = 0; mu < H; ++mu) h[mu] += P.w0[mu * D + nu] * q4;
+        }
+        R U = -P.b1;
+#pragma unroll
+        for (int mu = 0; mu < H; ++mu) {
+            const R t = tanh(h[mu]);
+            U += P.w1[mu] * t;
+            h[mu] = P.w1[mu] * (R(1) - t * t);   // dU/dh_mu
+        }
+
+        // ---------------- adjoint: dU/dq -> radial coefficients, dU/dA -------
+        R bR[KR], B0 = R(0);
+#pragma unroll
+        for (int kk = 0; kk < KR; ++kk) bR[kk] = R(0);
+#pragma unroll
+        for (int nu = 0; nu < NR; ++nu) {
+            R a = R(0);
+#pragma unroll
+            for (int mu = 0; mu < H; ++mu) a += h[mu] * P.w0[mu * D + nu];
+            B0 += a * P.CR[nu];
+#pragma unroll
+            for (int kk = 0; kk < KR; ++kk) bR[kk] += a * P.hR[nu * KR + kk];
+        }
+#pragma unroll
+        for (int n = 0; n < NA; ++n) {
+            R a4 = R(0), a2 = R(0);
+#pragma unroll
+            for (int mu = 0; mu < H; ++mu) {
+                a4 += h[mu] * P.w0[mu * D + NR + LM * NA + n];
+                a2 += h[mu] * P.w0[mu * D + NR + NA + n];
+            }
+            R dq4[5];
+            nepm::fourbody(&A[n][3], dq4);
+#pragma unroll
+            for (int t = 0; t < 5; ++t) A[n][3 + t] = R(2) * a2 * A[n][3 + t] + a4 * dq4[t];
+        }
+#pragma unroll
+        for (int l = 1; l <= LM; ++l) {
+            if (l == 2) continue;
+            const int lo = l * l - 1, hi = (l + 1) * (l + 1) - 1;
+#pragma unroll
+            for (int n = 0; n < NA; ++n) {
+                R a = R(0);
+#pragma unroll
+                for (int mu = 0; mu < H; ++mu) a += h[mu] * P.w0[mu * D + NR + (l - 1) * NA + n];
+#pragma unroll
+                for (int lm = lo; lm < hi; ++lm) A[n][lm] *= R(2) * a;
+            }
+        }
+
+        // ---------------- pair forces --------------------------------------
+        typename A_::T fi[3] = {0, 0, 0};
+        R w[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) w[t] = R(0);
+        double ez = 0.0;
+        bool bad = !isfinite(U);
+        const int i_caller = perm[k];
+
+        for (int s = 0; s < na + nro; ++s) {
+            const int slot = s < na ? s : M - nro + (s - na);
+            const int ent = nbr[slot * ld + k];
+            const int m = ent >> 5;
+            R ox, oy, oz;
+            stencil_offset(ent & 31, g, ox, oy, oz);
+            const typename V4<R>::T pj = pos4[m];
+            const R dx = pj.x - pi.x + ox, dy = pj.y - pi.y + oy, dz = pj.z - pi.z + oz;
+            const R r = nepm::nep_sqrt(dx * dx + dy * dy + dz * dz);
+            const R inv_r = R(1) / r;
+            const R ux = dx * inv_r, uy = dy * inv_r, uz = dz * inv_r;
+            R T[KR], dT[KR], fc, dfc, dxdr;
+            // radial: sum_n dU/dq_n g'_n(r)
+            nepm::cheb<KR, true>(r, P.inv_rcR, T, dT, fc, dfc, dxdr);
+            R s1 = B0, s2 = R(0);
+#pragma unroll
+            for (int kk = 0; kk < KR; ++kk) {
+                s1 += bR[kk] * T[kk];
+                s2 += bR[kk] * dT[kk];
+            }
+            R fs = dfc * s1 + fc * dxdr * s2;   // coefficient of u
+            R vx = R(0), vy = R(0), vz = R(0);  // coefficient of 1/r
+            if (s < na) {
+                nepm::cheb<KA, true>(r, P.inv_rcA, T, dT, fc, dfc, dxdr);
+                R gn[NA], dgn[NA];
+#pragma unroll
+                for (int n = 0; n < NA; ++n) {
+                    R a = P.CA[n], b = R(0);
+#pragma unroll
+                    for (int kk = 0; kk < KA; ++kk) {
+                        a += P.hA[n * KA + kk] * T[kk];
+                        b += P.hA[n * KA + kk] * dT[kk];
+                    }
+                    gn[n] = fc * a;
+                    dgn[n] = dfc * a + fc * dxdr * b;
+                }
+                R Y[NLM], G[NLM];
+                nepm::harmonics(ux, uy, uz, Y);
+                R sang = R(0);
+#pragma unroll
+                for (int lm = 0; lm < NLM; ++lm) {
+                    const int l = lm < 3 ? 1 : (lm < 8 ? 2 : (lm < 15 ? 3 : 4));
+                    R gsum = R(0), dsum = R(0);
+#pragma unroll
+                    for (int n = 0; n < NA; ++n) {
+                        gsum += A[n][lm] * gn[n];
+                        dsum += A[n][lm] * dgn[n];
+                    }
+                    G[lm] = gsum;
+                    sang += (dsum - R(l) * inv_r * gsum) * Y[lm];
+                }
+                fs += sang;
+                nepm::harmonics_grad_dot(ux, uy, uz, G, vx, vy, vz);
+            }
+            const R fx = fs * ux + vx * inv_r;
+            const R fy = fs * uy + vy * inv_r;
+            const R fz = fs * uz + vz * inv_r;
+            bad |= !isfinite(fx + fy + fz);
+            typename A_::T cx = A_::conv(fx), cy = A_::conv(fy), cz = A_::conv(fz);
+            // ZBL pair term (Eq. 1-4), FP64 from the FP64 positions
+            if (s < na && r < P.zbl_r2) {
+                double d64[3];
+                if (sizeof(R) == 4) {
+                    const int j_caller = perm[m];
+                    for (int a = 0; a < 3; ++a) {
+                        double t = x64[a * g.n + j_caller] - x64[a * g.n + i_caller];
+                        if (g.pbc[a]) t -= g.L[a] * rint(t * g.invL[a]);
+                        d64[a] = t;
+                    }
+                } else {
+                    d64[0] = (double)dx; d64[1] = (double)dy; d64[2] = (double)dz;
+                }
+                const double r64 = sqrt(d64[0] * d64[0] + d64[1] * d64[1] + d64[2] * d64[2]);
+                if (r64 < P.zbl_rr2) {
+                    double Uz, dUz;
+                    zbl_pair(r64, P.zbl_k, P.zbl_inv_a, P.zbl_r1, P.zbl_rr2, Uz, dUz);
+                    ez += 0.5 * Uz;
+                    const double c = 0.5 * dUz / r64;
+                    const double f3[3] = {c * d64[0], c * d64[1], c * d64[2]};
+                    cx += A_::convd(f3[0]);
+                    cy += A_::convd(f3[1]);
+                    cz += A_::convd(f3[2]);
+                    bad |= !isfinite(c);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+#pragma unroll
+                        for (int b = 0; b < 3; ++b) wv[3 * a + b] -= f3[a] * d64[b];
+                }
+            }
+            fi[0] += cx; fi[1] += cy; fi[2] += cz;
+            A_::add(&facc[m], -cx);
+            A_::add(&facc[ld + m], -cy);
+            A_::add(&facc[2 * ld + m], -cz);
+            w[0] -= fx * dx; w[1] -= fx * dy; w[2] -= fx * dz;
+            w[3] -= fy * dx; w[4] -= fy * dy; w[5] -= fy * dz;
+            w[6] -= fz * dx; w[7] -= fz * dy; w[8] -= fz * dz;
+        }
+        A_::add(&facc[k], fi[0]);
+        A_::add(&facc[ld + k], fi[1]);
+        A_::add(&facc[2 * ld + k], fi[2]);
+        e_site = (double)U + ez;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) wv[t] += (double)w[t];
+        if (site_energy) site_energy[i_caller] = e_site;
+        if (bad) atomicOr(status, ST_NONFINITE);
+    }
+
+    // ---------------- per-tile energy and virial (fixed order) ----------------
+    __shared__ double red[TILE / 32][NPART];
+    double v[NPART];
+    v[0] = e_site;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) v[1 + t] = wv[t];
+#pragma unroll
+    for (int t = 0; t < NPART; ++t)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[t] += __shfl_xor_sync(0xffffffffu, v[t], o);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int t = 0; t < NPART; ++t) red[threadIdx.x >> 5][t] = v[t];
+    __syncthreads();
+    if (threadIdx.x < NPART) {
+        double s = 0.0;
+#pragma unroll
+        for (int wi = 0; wi < TILE / 32; ++wi) s += red[wi][threadIdx.x];
+        partials[(size_t)blockIdx.x * NPART + threadIdx.x] = s;
+    }
+}
+
+// Forces back to caller order (FP64), accumulators reset to zero.
+template <typename R>
+__global__ void k_forces_out(int n, int ld, const int* __restrict__ perm,
+                             typename Acc<R>::T* __restrict__ facc, double* __restrict__ F,
+                             int* __restrict__ status)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int i = perm[k];
+    bool bad = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double f = Acc<R>::value(facc[(size_t)a * ld + k]);
+        facc[(size_t)a * ld + k] = 0;
+        bad |= !isfinite(f);
+        F[(size_t)a * n + i] = f;
+    }
+    if (bad) atomicOr(status, ST_NONFINITE);
+}
+
+// One block: sums the per-tile partials in a fixed order into out[0..NPART).
+__global__ void __launch_bounds__(256) k_reduce_partials(const double* __restrict__ partials,
+                                                         int ntiles, double* __restrict__ out)
+{
+    __shared__ double sh[256];
+    for (int c = 0; c < NPART; ++c) {
+        double s = 0.0;
+        for (int t = threadIdx.x; t < ntiles; t += blockDim.x) s += partials[(size_t)t * NPART + c];
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[c] = sh[0];
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Velocity Verlet (Sec. II.B), FP64
+// ----------------------------------------------------------------------------
+
+// thermo layout (device doubles): [0] dt of the current step, [1] time,
+// [2] step count, [3] KE, [4] vmax, [5] dt_max, [6] d_max, [7] last dt
+constexpr int TH_DT = 0, TH_TIME = 1, TH_STEP = 2, TH_KE = 3, TH_VMAX = 4, TH_DTMAX = 5,
+              TH_DMAX = 6, TH_DTLAST = 7, TH_N = 8;
+
+// v += dt/2 F/m ; x += dt v ; wrap periodic coordinates into [0, L)
+__global__ void k_kick_drift(Grid g, double acc, const double* __restrict__ thermo,
+                             double* __restrict__ x, double* __restrict__ v,
+                             const double* __restrict__ F)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    const double dt = thermo[TH_DT];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        size_t o = (size_t)a * g.n + i;
+        double vv = v[o] + 0.5 * dt * acc * F[o];
+        double xx = x[o] + dt * vv;
+        if (g.pbc[a]) xx -= g.L[a] * floor(xx * g.invL[a]);
+        v[o] = vv;
+        x[o] = xx;
+    }
+}
+
+// v += dt/2 F/m and per-block (sum v^2, max |v|)
+__global__ void __launch_bounds__(256) k_kick_thermo(int n, double acc,
+                                                     const double* __restrict__ thermo,
+                                                     double* __restrict__ v,
+                                                     const double* __restrict__ F,
+                                                     double* __restrict__ part, int half_kick)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double v2 = 0.0;
+    if (i < n) {
+        const double dt = half_kick ? thermo[TH_DT] : 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            size_t o = (size_t)a * n + i;
+            double vv = v[o] + 0.5 * dt * acc * F[o];
+            if (half_kick) v[o] = vv;
+            v2 += vv * vv;
+        }
+    }
+    double vm = v2;
+    __shared__ double sh[2][8];
+    for (int o = 16; o > 0; o >>= 1) {
+        v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+        vm = fmax(vm, __shfl_xor_sync(0xffffffffu, vm, o));
+    }
+    if ((threadIdx.x & 31) == 0) { sh[0][threadIdx.x >> 5] = v2; sh[1][threadIdx.x >> 5] = vm; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < 8; ++w) { a += sh[0][w]; b = fmax(b, sh[1][w]); }
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+}
+
+// One block: KE, max|v|, time bookkeeping and the next step's dt
+// (dt = min(dt_max, d_max / max|v|) when d_max > 0).
+__global__ void __launch_bounds__(256) k_thermo_step(const double* __restrict__ part, int nb,
+                                                     double mass, double ev_amu,
+                                                     double* __restrict__ thermo,
+                                                     int advance)
+{
+    __shared__ double sa[256], sb[256];
+    double a = 0.0, b = 0.0;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+        a += part[2 * t];
+        b = fmax(b, part[2 * t + 1]);
+    }
+    sa[threadIdx.x] = a;
+    sb[threadIdx.x] = b;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sa[threadIdx.x] += sa[threadIdx.x + o];
+            sb[threadIdx.x] = fmax(sb[threadIdx.x], sb[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double ke = 0.5 * mass * sa[0] / ev_amu;
+        const double vmax = sqrt(sb[0]);
+        if (advance) {
+            thermo[TH_TIME] += thermo[TH_DT];
+            thermo[TH_STEP] += 1.0;
+            thermo[TH_DTLAST] = thermo[TH_DT];
+        }
+        thermo[TH_KE] = ke;
+        thermo[TH_VMAX] = vmax;
+        double dt = thermo[TH_DTMAX];
+        const double dmax = thermo[TH_DMAX];
+        if (dmax > 0.0 && vmax > 0.0 && dmax / vmax < dt) dt = dmax / vmax;
+        thermo[TH_DT] = dt;
+    }
+}
+
+}  // namespace nepk

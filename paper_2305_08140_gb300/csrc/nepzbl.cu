@@ -1,0 +1,744 @@
+// nepzbl.cu -- C ABI of the NEP-ZBL library: context, scratch memory, one
+// force evaluation and graph-captured velocity-Verlet MD (see nepzbl.h).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/nepzbl.h"
+#include "nep_device.cuh"
+
+using namespace nepk;
+
+namespace {
+
+// e^2 / (4 pi eps0) in eV*A (CODATA), prefactor of Eq. 2
+constexpr double COULOMB_EV_A = 14.39964547;
+// 1 eV/amu in A^2/fs^2
+constexpr double EV_AMU = 1.602176634e-19 / 1.66053906660e-27 * 1e-10;
+
+thread_local std::string g_init_error;
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    int kernels = 0;
+    int steps = 0;
+};
+
+}  // namespace
+
+struct nep_ctx {
+    int precision = NEP_FP32;
+    int device = 0;
+    Model<float> mf;
+    Model<double> md;
+    double mass = 0.0;
+    double rcR = 0.0;
+    std::string err;
+
+    // capacities
+    int ld = 0;        // atoms
+    int M = 0;         // neighbour slots per atom
+    int ccap = 0;      // cells
+    // scratch (device)
+    int *cell_of = nullptr, *slot_of = nullptr, *perm = nullptr, *cell_sorted = nullptr;
+    void* pos4 = nullptr;
+    int2* cnt = nullptr;
+    int* nbr = nullptr;
+    void* facc = nullptr;
+    double* partials = nullptr;
+    double* vpart = nullptr;
+    int *count = nullptr, *start = nullptr, *scan_sums = nullptr;
+    double* backup = nullptr;        // x, v, F copies for MD rollback
+    double* thermo = nullptr;        // TH_N doubles
+    double* thermo_backup = nullptr;
+    double* result = nullptr;        // NPART doubles (E, W)
+    int* status = nullptr;           // [0] status bits, [1..2] max counts
+    unsigned long long* pairs = nullptr;
+    // pinned host mirrors
+    double* h_result = nullptr;      // NPART + TH_N
+    int* h_status = nullptr;         // 3
+    unsigned long long* h_pairs = nullptr;
+
+    cudaStream_t cap_stream = nullptr;
+    std::map<int, GraphEntry> graphs;
+    const void* graph_key[4] = {nullptr, nullptr, nullptr, nullptr};
+    int graph_n = -1;
+    Grid graph_grid;
+
+    // options and counters
+    int timing = 0;
+    int chunk = 10;
+    int64_t launches = 0;
+    int64_t timed_launches = 0;
+    double timed_ms = 0.0;
+    std::vector<cudaEvent_t> events;   // pairs (start, stop)
+    int last_max_total = 0, last_max_ang = 0;
+    long long last_pairs_r = 0, last_pairs_a = 0;
+    bool capturing = false;
+    int capture_kernels = 0;
+    int capture_timed = 0;
+};
+
+static int fail(nep_ctx* c, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    else g_init_error = buf;
+    return code;
+}
+
+#define CK(call)                                                                           \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(ctx, NEP_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+static void count_launch(nep_ctx* ctx)
+{
+    if (ctx->capturing) ctx->capture_kernels++;
+    else ctx->launches++;
+}
+
+template <typename T>
+static void free_dev(T*& p)
+{
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+static void drop_graphs(nep_ctx* ctx)
+{
+    for (auto& kv : ctx->graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    ctx->graphs.clear();
+}
+
+static void free_scratch(nep_ctx* ctx)
+{
+    drop_graphs(ctx);
+    free_dev(ctx->cell_of); free_dev(ctx->slot_of); free_dev(ctx->perm);
+    free_dev(ctx->cell_sorted); free_dev(ctx->pos4); free_dev(ctx->cnt); free_dev(ctx->nbr);
+    free_dev(ctx->facc); free_dev(ctx->partials); free_dev(ctx->vpart); free_dev(ctx->backup);
+    ctx->ld = 0;
+    ctx->M = 0;
+}
+
+// Atom-sized buffers for n atoms with M neighbour slots.
+static int ensure_atoms(nep_ctx* ctx, int n, int M)
+{
+    if (n <= ctx->ld && M <= ctx->M && ctx->nbr) return NEP_OK;
+    int ld = n > ctx->ld ? n + n / 16 + 128 : ctx->ld;
+    int MM = M > ctx->M ? M : ctx->M;
+    cudaDeviceSynchronize();
+    free_scratch(ctx);
+    size_t acc = ctx->precision == NEP_FP32 ? sizeof(long long) : sizeof(double);
+    size_t p4 = ctx->precision == NEP_FP32 ? sizeof(float4) : sizeof(double4);
+    int tiles = (ld + TILE - 1) / TILE;
+    int vb = (ld + 255) / 256;
+    CK(cudaMalloc(&ctx->cell_of, sizeof(int) * ld));
+    CK(cudaMalloc(&ctx->slot_of, sizeof(int) * ld));
+    CK(cudaMalloc(&ctx->perm, sizeof(int) * ld));
+    CK(cudaMalloc(&ctx->cell_sorted, sizeof(int) * ld));
+    CK(cudaMalloc(&ctx->pos4, p4 * ld));
+    CK(cudaMalloc(&ctx->cnt, sizeof(int2) * ld));
+    CK(cudaMalloc(&ctx->nbr, sizeof(int) * (size_t)ld * MM));
+    CK(cudaMalloc(&ctx->facc, acc * 3 * (size_t)ld));
+    CK(cudaMemset(ctx->facc, 0, acc * 3 * (size_t)ld));
+    CK(cudaMalloc(&ctx->partials, sizeof(double) * NPART * (size_t)tiles));
+    CK(cudaMalloc(&ctx->vpart, sizeof(double) * 2 * (size_t)vb));
+    CK(cudaMalloc(&ctx->backup, sizeof(double) * 9 * (size_t)ld));
+    ctx->ld = ld;
+    ctx->M = MM;
+    return NEP_OK;
+}
+
+static int ensure_cells(nep_ctx* ctx, int ncell)
+{
+    if (ncell <= ctx->ccap) return NEP_OK;
+    int cap = ncell + ncell / 8 + 64;
+    if ((cap + SCAN_B - 1) / SCAN_B > SCAN_B)
+        return fail(ctx, NEP_ERR_BOX, "cell grid too large (%d cells)", ncell);
+    cudaDeviceSynchronize();
+    drop_graphs(ctx);
+    free_dev(ctx->count); free_dev(ctx->start); free_dev(ctx->scan_sums);
+    CK(cudaMalloc(&ctx->count, sizeof(int) * (size_t)(cap + 1)));
+    CK(cudaMalloc(&ctx->start, sizeof(int) * (size_t)(cap + 1)));
+    CK(cudaMalloc(&ctx->scan_sums, sizeof(int) * (size_t)SCAN_B));
+    ctx->ccap = cap;
+    return NEP_OK;
+}
+
+// Cell grid for a diagonal box; periodic dims need >= 3 cells of >= rc_R.
+static int make_grid(nep_ctx* ctx, int64_t n, const double box[9], const int32_t pbc[3], Grid& g)
+{
+    memset(&g, 0, sizeof(Grid));
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            if (a != b && box[3 * a + b] != 0.0)
+                return fail(ctx, NEP_ERR_BOX, "only diagonal (orthorhombic) boxes are supported");
+    for (int a = 0; a < 3; ++a) {
+        double L = box[4 * a];
+        if (!(L > 0.0) || !isfinite(L)) return fail(ctx, NEP_ERR_BOX, "box length %d is %g", a, L);
+        int nc = (int)floor(L / ctx->rcR);
+        if (pbc[a]) {
+            if (nc < 3)
+                return fail(ctx, NEP_ERR_BOX,
+                            "periodic box length %g < 3 r_c^R = %g (small boxes are not supported "
+                            "by the cell-list path)", L, 3 * ctx->rcR);
+        } else if (nc < 1) {
+            nc = 1;
+        }
+        if (nc > 1024) nc = 1024;
+        g.nc[a] = nc;
+        g.pbc[a] = pbc[a] ? 1 : 0;
+        g.lc[a] = L / nc;
+        g.inv_lc[a] = nc / L;
+        g.L[a] = L;
+        g.invL[a] = 1.0 / L;
+    }
+    g.n = (int)n;
+    return NEP_OK;
+}
+
+static int check_device_ptr(nep_ctx* ctx, const void* p, const char* what)
+{
+    if (!p) return fail(ctx, NEP_ERR_INVALID_ARG, "%s is NULL", what);
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, NEP_ERR_INVALID_ARG, "%s is not a CUDA pointer", what);
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(ctx, NEP_ERR_INVALID_ARG, "%s must be device memory", what);
+    return NEP_OK;
+}
+
+// Launches one force evaluation on stream s (no synchronisation).
+// Kernels: bin count, 3-kernel scan, scatter, cell finalize, neighbours,
+// force kernel, forces out, reduction.
+template <typename R>
+static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int32_t* types,
+                       double* F, double* site_energy, cudaStream_t s, int timed_slot)
+{
+    Grid g = g0;
+    g.ld = ctx->ld;
+    g.M = ctx->M;
+    const int n = g.n;
+    const int ncell = g.nc[0] * g.nc[1] * g.nc[2];
+    const Model<R>* Pp;
+    if constexpr (sizeof(R) == 4) Pp = &ctx->mf;
+    else Pp = &ctx->md;
+    const Model<R>& P = *Pp;
+    CK(cudaMemsetAsync(ctx->count, 0, sizeof(int) * (size_t)(ncell + 1), s));
+    CK(cudaMemsetAsync(ctx->pairs, 0, sizeof(unsigned long long) * 2, s));
+    if (n == 0) return NEP_OK;
+    const int tb = 256;
+    const int nb = (n + tb - 1) / tb;
+    k_bin_count<<<nb, tb, 0, s>>>(g, x, ctx->cell_of, ctx->slot_of, ctx->count, ctx->status);
+    count_launch(ctx);
+    const int sb = (ncell + SCAN_B - 1) / SCAN_B;
+    k_scan_blocks<<<sb, SCAN_T, 0, s>>>(ctx->count, ncell, ctx->start, ctx->scan_sums);
+    count_launch(ctx);
+    k_scan_sums<<<1, SCAN_T, 0, s>>>(ctx->scan_sums, sb, ctx->start, ncell);
+    count_launch(ctx);
+    k_scan_add<<<(ncell + tb - 1) / tb, tb, 0, s>>>(ctx->start, ncell, ctx->scan_sums);
+    count_launch(ctx);
+    k_bin_scatter<<<nb, tb, 0, s>>>(n, ctx->cell_of, ctx->slot_of, ctx->start, ctx->perm);
+    count_launch(ctx);
+    k_cell_finalize<R><<<(ncell + 127) / 128, 128, 0, s>>>(
+        g, ncell, ctx->start, ctx->perm, x, types, (typename V4<R>::T*)ctx->pos4, ctx->cell_sorted);
+    count_launch(ctx);
+    k_neighbors<R><<<(n + 127) / 128, 128, 0, s>>>(
+        g, (R)(P.rcR2), (R)(P.rcA2), (const typename V4<R>::T*)ctx->pos4, ctx->cell_sorted,
+        ctx->start, ctx->nbr, ctx->cnt, ctx->status, ctx->status + 1, ctx->pairs);
+    count_launch(ctx);
+    const int tiles = (n + TILE - 1) / TILE;
+    if (timed_slot >= 0) {
+        if (ctx->capturing)
+            CK(cudaEventRecordWithFlags(ctx->events[2 * timed_slot], s, cudaEventRecordExternal));
+        else
+            CK(cudaEventRecord(ctx->events[2 * timed_slot], s));
+    }
+    k_nep<R><<<tiles, TILE, 0, s>>>(P, g, (const typename V4<R>::T*)ctx->pos4, ctx->nbr, ctx->cnt,
+                                   ctx->perm, x, (typename Acc<R>::T*)ctx->facc, ctx->partials,
+                                   site_energy, ctx->status);
+    count_launch(ctx);
+    if (timed_slot >= 0) {
+        if (ctx->capturing)
+            CK(cudaEventRecordWithFlags(ctx->events[2 * timed_slot + 1], s, cudaEventRecordExternal));
+        else
+            CK(cudaEventRecord(ctx->events[2 * timed_slot + 1], s));
+    }
+    k_forces_out<R><<<nb, tb, 0, s>>>(n, ctx->ld, ctx->perm, (typename Acc<R>::T*)ctx->facc, F,
+                                      ctx->status);
+    count_launch(ctx);
+    k_reduce_partials<<<1, 256, 0, s>>>(ctx->partials, tiles, ctx->result);
+    count_launch(ctx);
+    CK(cudaGetLastError());
+    return NEP_OK;
+}
+
+static int eval(nep_ctx* ctx, const Grid& g, const double* x, const int32_t* types, double* F,
+                double* site_energy, cudaStream_t s, int timed_slot)
+{
+    return ctx->precision == NEP_FP32
+               ? launch_eval<float>(ctx, g, x, types, F, site_energy, s, timed_slot)
+               : launch_eval<double>(ctx, g, x, types, F, site_energy, s, timed_slot);
+}
+
+static int ensure_events(nep_ctx* ctx, int pairs)
+{
+    while ((int)ctx->events.size() < 2 * pairs) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        ctx->events.push_back(e);
+    }
+    return NEP_OK;
+}
+
+static int collect_timing(nep_ctx* ctx, int count)
+{
+    for (int t = 0; t < count; ++t) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->events[2 * t], ctx->events[2 * t + 1]));
+        ctx->timed_ms += ms;
+        ctx->timed_launches++;
+    }
+    return NEP_OK;
+}
+
+// Reads status, counters and results to pinned host memory and waits.
+static int readback(nep_ctx* ctx, cudaStream_t s)
+{
+    CK(cudaMemcpyAsync(ctx->h_status, ctx->status, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->h_pairs, ctx->pairs, sizeof(unsigned long long) * 2,
+                       cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->h_result, ctx->result, sizeof(double) * NPART, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->h_result + NPART, ctx->thermo, sizeof(double) * TH_N,
+                       cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ctx->last_max_total = ctx->h_status[1];
+    ctx->last_max_ang = ctx->h_status[2];
+    ctx->last_pairs_r = (long long)ctx->h_pairs[0];
+    ctx->last_pairs_a = (long long)ctx->h_pairs[1];
+    return NEP_OK;
+}
+
+static int grown_capacity(int needed) { return needed + needed / 4 + 8; }
+
+template <typename R>
+static void build_model(Model<R>& P, const nep_params* p)
+{
+    const int Dd = D, Hh = H;
+    const double* w0 = p->params;
+    const double* b0 = w0 + Hh * Dd;
+    const double* w1 = b0 + Hh;
+    const double* b1 = w1 + Hh;
+    const double* cR = b1 + 1;
+    const double* cA = cR + NR * KR;
+    for (int mu = 0; mu < Hh; ++mu)
+        for (int nu = 0; nu < Dd; ++nu) P.w0[mu * Dd + nu] = (R)(w0[mu * Dd + nu] * p->q_scaler[nu]);
+    for (int mu = 0; mu < Hh; ++mu) {
+        P.b0[mu] = (R)b0[mu];
+        P.w1[mu] = (R)w1[mu];
+    }
+    P.b1 = (R)b1[0];
+    for (int n = 0; n < NR; ++n) {
+        double s = 0.0;
+        for (int k = 0; k < KR; ++k) {
+            P.hR[n * KR + k] = (R)(0.5 * cR[n * KR + k]);
+            s += 0.5 * cR[n * KR + k];
+        }
+        P.CR[n] = (R)s;
+    }
+    for (int n = 0; n < NA; ++n) {
+        double s = 0.0;
+        for (int k = 0; k < KA; ++k) {
+            P.hA[n * KA + k] = (R)(0.5 * cA[n * KA + k]);
+            s += 0.5 * cA[n * KA + k];
+        }
+        P.CA[n] = (R)s;
+    }
+    P.rcR2 = (R)(p->rc_radial * p->rc_radial);
+    P.rcA2 = (R)(p->rc_angular * p->rc_angular);
+    P.inv_rcR = (R)(1.0 / p->rc_radial);
+    P.inv_rcA = (R)(1.0 / p->rc_angular);
+    P.zbl_r2 = (R)p->zbl_r_outer;
+    const double Z = (double)p->z[0];
+    P.zbl_k = COULOMB_EV_A * Z * Z;
+    P.zbl_inv_a = (pow(Z, 0.23) + pow(Z, 0.23)) / 0.46848;
+    P.zbl_r1 = p->zbl_r_inner;
+    P.zbl_rr2 = p->zbl_r_outer;
+}
+
+// ============================================================================
+// C ABI
+// ============================================================================
+
+extern "C" {
+
+int nep_init(const nep_params* p, int precision, nep_ctx** out)
+{
+    nep_ctx* ctx = nullptr;
+    if (!p || !out) return fail(nullptr, NEP_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (precision != NEP_FP32 && precision != NEP_FP64)
+        return fail(nullptr, NEP_ERR_INVALID_ARG, "precision must be NEP_FP32 or NEP_FP64");
+    if (p->n_types != 1)
+        return fail(nullptr, NEP_ERR_UNSUPPORTED, "this build supports one species (n_types = 1)");
+    if (p->n_max_radial != NR - 1 || p->n_max_angular != NA - 1 ||
+        p->basis_size_radial != KR - 1 || p->basis_size_angular != KA - 1 || p->l_max != LM ||
+        p->use_4body != 1 || p->n_hidden != H)
+        return fail(nullptr, NEP_ERR_UNSUPPORTED,
+                    "this build is compiled for n_max 4/4, basis 8/8, l_max 4, 4-body, 30 neurons");
+    const int64_t np = (int64_t)H * D + 2 * H + 1 + NR * KR + NA * KA;
+    if (!p->params || p->n_params != np)
+        return fail(nullptr, NEP_ERR_INVALID_ARG, "params must hold %lld values", (long long)np);
+    if (!p->q_scaler) return fail(nullptr, NEP_ERR_INVALID_ARG, "q_scaler is NULL");
+    for (int64_t i = 0; i < np; ++i)
+        if (!isfinite(p->params[i])) return fail(nullptr, NEP_ERR_INVALID_ARG, "non-finite parameter");
+    for (int i = 0; i < D; ++i)
+        if (!isfinite(p->q_scaler[i])) return fail(nullptr, NEP_ERR_INVALID_ARG, "non-finite scaler");
+    if (!(p->rc_radial > 0) || !(p->rc_angular > 0) || p->rc_angular > p->rc_radial ||
+        !(p->zbl_r_outer > p->zbl_r_inner) || !(p->zbl_r_inner >= 0) ||
+        p->zbl_r_outer > p->rc_angular)
+        return fail(nullptr, NEP_ERR_INVALID_ARG,
+                    "need 0 <= zbl_r_inner < zbl_r_outer <= rc_angular <= rc_radial");
+    if (!(p->z[0] > 0) || !(p->mass[0] > 0))
+        return fail(nullptr, NEP_ERR_INVALID_ARG, "Z and mass must be positive");
+
+    ctx = new (std::nothrow) nep_ctx();
+    if (!ctx) return fail(nullptr, NEP_ERR_INVALID_ARG, "out of host memory");
+    ctx->precision = precision;
+    ctx->mass = p->mass[0];
+    ctx->rcR = p->rc_radial;
+    build_model<float>(ctx->mf, p);
+    build_model<double>(ctx->md, p);
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->thermo, sizeof(double) * TH_N);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->thermo_backup, sizeof(double) * TH_N);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->result, sizeof(double) * NPART);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->status, sizeof(int) * 3);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->pairs, sizeof(unsigned long long) * 2);
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_result, sizeof(double) * (NPART + TH_N));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_status, sizeof(int) * 3);
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_pairs, sizeof(unsigned long long) * 2);
+    if (e == cudaSuccess) e = cudaMemset(ctx->thermo, 0, sizeof(double) * TH_N);
+    if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(int) * 3);
+    if (e != cudaSuccess) {
+        int rc = fail(nullptr, NEP_ERR_CUDA, "CUDA setup failed: %s", cudaGetErrorString(e));
+        nep_free(ctx);
+        return rc;
+    }
+    ctx->M = 0;
+    *out = ctx;
+    return NEP_OK;
+}
+
+void nep_free(nep_ctx* ctx)
+{
+    if (!ctx) return;
+    cudaDeviceSynchronize();
+    free_scratch(ctx);
+    free_dev(ctx->count); free_dev(ctx->start); free_dev(ctx->scan_sums);
+    free_dev(ctx->thermo); free_dev(ctx->thermo_backup); free_dev(ctx->result);
+    free_dev(ctx->status); free_dev(ctx->pairs);
+    if (ctx->h_result) cudaFreeHost(ctx->h_result);
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    if (ctx->h_pairs) cudaFreeHost(ctx->h_pairs);
+    for (auto e : ctx->events) cudaEventDestroy(e);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    delete ctx;
+}
+
+const char* nep_last_error(const nep_ctx* ctx)
+{
+    return ctx ? ctx->err.c_str() : g_init_error.c_str();
+}
+
+int nep_set_option(nep_ctx* ctx, int option, int64_t value)
+{
+    if (!ctx) return NEP_ERR_INVALID_ARG;
+    switch (option) {
+    case NEP_OPT_TIMING:
+        ctx->timing = value ? 1 : 0;
+        drop_graphs(ctx);
+        return NEP_OK;
+    case NEP_OPT_GRAPH_CHUNK:
+        if (value < 1 || value > 100000) return fail(ctx, NEP_ERR_INVALID_ARG, "bad chunk");
+        ctx->chunk = (int)value;
+        return NEP_OK;
+    case NEP_OPT_NBR_CAPACITY:
+        if (value < 1 || value > 1000000) return fail(ctx, NEP_ERR_INVALID_ARG, "bad capacity");
+        if (ctx->ld > 0) {
+            if (value > ctx->M) return ensure_atoms(ctx, ctx->ld, (int)value);
+            return NEP_OK;
+        }
+        ctx->M = (int)value;
+        return NEP_OK;
+    default:
+        return fail(ctx, NEP_ERR_INVALID_ARG, "unknown option %d", option);
+    }
+}
+
+int nep_get_stats(const nep_ctx* ctx, nep_stats* out)
+{
+    if (!ctx || !out) return NEP_ERR_INVALID_ARG;
+    out->kernel_launches = ctx->launches;
+    out->timed_launches = ctx->timed_launches;
+    out->timed_ms = ctx->timed_ms;
+    out->pairs_radial = ctx->last_pairs_r;
+    out->pairs_angular = ctx->last_pairs_a;
+    out->max_nbr_radial = ctx->last_max_total;
+    out->max_nbr_angular = ctx->last_max_ang;
+    out->nbr_capacity = ctx->M;
+    out->graph_chunk = ctx->chunk;
+    return NEP_OK;
+}
+
+int nep_reset_stats(nep_ctx* ctx)
+{
+    if (!ctx) return NEP_ERR_INVALID_ARG;
+    ctx->launches = 0;
+    ctx->timed_launches = 0;
+    ctx->timed_ms = 0.0;
+    return NEP_OK;
+}
+
+// One evaluation with growth of the neighbour capacity on overflow.
+static int compute_with_retry(nep_ctx* ctx, const Grid& g, const double* x, const int32_t* types,
+                              double* F, double* site_energy, cudaStream_t s)
+{
+    const int ncell = g.nc[0] * g.nc[1] * g.nc[2];
+    int rc = ensure_cells(ctx, ncell);
+    if (rc) return rc;
+    int M = ctx->M > 0 ? ctx->M : 96;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        rc = ensure_atoms(ctx, g.n, M);
+        if (rc) return rc;
+        CK(cudaMemsetAsync(ctx->status, 0, sizeof(int) * 3, s));
+        int slot = -1;
+        if (ctx->timing) {
+            rc = ensure_events(ctx, 1);
+            if (rc) return rc;
+            slot = 0;
+        }
+        rc = eval(ctx, g, x, types, F, site_energy, s, slot);
+        if (rc) return rc;
+        rc = readback(ctx, s);
+        if (rc) return rc;
+        if (slot == 0 && g.n > 0) {
+            rc = collect_timing(ctx, 1);
+            if (rc) return rc;
+        }
+        if (ctx->h_status[0] & ST_OVERFLOW) {
+            M = grown_capacity(ctx->h_status[1]);
+            continue;
+        }
+        if (ctx->h_status[0] & ST_NONFINITE)
+            return fail(ctx, NEP_ERR_NONFINITE, "non-finite positions, energies or forces");
+        return NEP_OK;
+    }
+    return fail(ctx, NEP_ERR_NBR_OVERFLOW, "neighbour capacity could not be grown enough");
+}
+
+int nep_compute(nep_ctx* ctx, int64_t n_atoms, const double* xyz, const double box[9],
+                const int32_t* types, const int32_t pbc[3], double* energy, double* forces,
+                double* virial, double* site_energy, void* stream)
+{
+    if (!ctx) return NEP_ERR_INVALID_ARG;
+    if (n_atoms < 0 || n_atoms >= (1 << 26))
+        return fail(ctx, NEP_ERR_INVALID_ARG, "n_atoms must be in [0, 2^26)");
+    if (!box || !pbc || !energy) return fail(ctx, NEP_ERR_INVALID_ARG, "NULL host argument");
+    Grid g;
+    int rc = make_grid(ctx, n_atoms, box, pbc, g);
+    if (rc) return rc;
+    if (n_atoms == 0) {
+        *energy = 0.0;
+        if (virial) for (int t = 0; t < 9; ++t) virial[t] = 0.0;
+        return NEP_OK;
+    }
+    if ((rc = check_device_ptr(ctx, xyz, "xyz")) || (rc = check_device_ptr(ctx, types, "types")) ||
+        (rc = check_device_ptr(ctx, forces, "forces")))
+        return rc;
+    if (site_energy && (rc = check_device_ptr(ctx, site_energy, "site_energy"))) return rc;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = compute_with_retry(ctx, g, xyz, types, forces, site_energy, s);
+    if (rc) return rc;
+    *energy = ctx->h_result[0];
+    if (virial) for (int t = 0; t < 9; ++t) virial[t] = ctx->h_result[1 + t];
+    return NEP_OK;
+}
+
+// Captures `steps` MD steps into a graph (on the context's capture stream).
+static int capture_steps(nep_ctx* ctx, const Grid& g, nep_md_state* st, int steps, GraphEntry& ge)
+{
+    cudaStream_t cs = ctx->cap_stream;
+    const double acc = EV_AMU / ctx->mass;
+    const int n = g.n;
+    const int tb = 256, nb = (n + tb - 1) / tb;
+    if (ctx->timing) {
+        int rc = ensure_events(ctx, steps);
+        if (rc) return rc;
+    }
+    ctx->capturing = true;
+    ctx->capture_kernels = 0;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int rc = NEP_OK;
+    for (int t = 0; t < steps && !rc; ++t) {
+        k_kick_drift<<<nb, tb, 0, cs>>>(g, acc, ctx->thermo, st->xyz, st->vel, st->forces);
+        count_launch(ctx);
+        rc = eval(ctx, g, st->xyz, st->types, st->forces, nullptr, cs, ctx->timing ? t : -1);
+        if (rc) break;
+        k_kick_thermo<<<nb, tb, 0, cs>>>(n, acc, ctx->thermo, st->vel, st->forces, ctx->vpart, 1);
+        count_launch(ctx);
+        k_thermo_step<<<1, 256, 0, cs>>>(ctx->vpart, nb, ctx->mass, EV_AMU, ctx->thermo, 1);
+        count_launch(ctx);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    ctx->capturing = false;
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(ctx, NEP_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&ge.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess)
+        return fail(ctx, NEP_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    ge.kernels = ctx->capture_kernels;
+    ge.steps = steps;
+    return NEP_OK;
+}
+
+int md_step(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
+{
+    if (!ctx) return NEP_ERR_INVALID_ARG;
+    if (!st || n_steps < 0) return fail(ctx, NEP_ERR_INVALID_ARG, "bad state or step count");
+    const int64_t n = st->n_atoms;
+    if (n <= 0 || n >= (1 << 26)) return fail(ctx, NEP_ERR_INVALID_ARG, "n_atoms must be in [1, 2^26)");
+    if (!(st->dt_max > 0) || !isfinite(st->dt_max))
+        return fail(ctx, NEP_ERR_INVALID_ARG, "dt_max must be positive");
+    int rc;
+    if ((rc = check_device_ptr(ctx, st->xyz, "xyz")) || (rc = check_device_ptr(ctx, st->vel, "vel")) ||
+        (rc = check_device_ptr(ctx, st->forces, "forces")) ||
+        (rc = check_device_ptr(ctx, st->types, "types")))
+        return rc;
+    Grid g;
+    if ((rc = make_grid(ctx, n, st->box, st->pbc, g))) return rc;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!st->forces_valid) {
+        rc = compute_with_retry(ctx, g, st->xyz, st->types, st->forces, nullptr, s);
+        if (rc) return rc;
+        st->forces_valid = 1;
+        st->potential_energy = ctx->h_result[0];
+        for (int t = 0; t < 9; ++t) st->virial[t] = ctx->h_result[1 + t];
+    }
+    {
+        int rc2 = ensure_cells(ctx, g.nc[0] * g.nc[1] * g.nc[2]);
+        if (rc2) return rc2;
+        int need = ctx->M > 0 ? ctx->M : 96;
+        if (ctx->last_max_total > 0 && grown_capacity(ctx->last_max_total) > need)
+            need = grown_capacity(ctx->last_max_total);
+        if ((rc2 = ensure_atoms(ctx, (int)n, need))) return rc2;
+    }
+    // graphs are bound to the state's pointers and sizes
+    if (ctx->graph_key[0] != st->xyz || ctx->graph_key[1] != st->vel ||
+        ctx->graph_key[2] != st->forces || ctx->graph_key[3] != st->types || ctx->graph_n != n ||
+        memcmp(&ctx->graph_grid, &g, sizeof(Grid)) != 0) {
+        drop_graphs(ctx);
+        ctx->graph_key[0] = st->xyz; ctx->graph_key[1] = st->vel;
+        ctx->graph_key[2] = st->forces; ctx->graph_key[3] = st->types;
+        ctx->graph_n = (int)n;
+        ctx->graph_grid = g;
+    }
+    // thermo: dt_max, d_max, time, step; initial dt from the current velocities
+    double th[TH_N] = {0};
+    th[TH_TIME] = st->time;
+    th[TH_STEP] = (double)st->step;
+    th[TH_DTMAX] = st->dt_max;
+    th[TH_DMAX] = st->d_max;
+    th[TH_DTLAST] = st->dt_last;
+    CK(cudaMemcpyAsync(ctx->thermo, th, sizeof(th), cudaMemcpyHostToDevice, s));
+    {
+        const int tb = 256, nb = (int)((n + tb - 1) / tb);
+        k_kick_thermo<<<nb, tb, 0, s>>>((int)n, 0.0, ctx->thermo, st->vel, st->forces, ctx->vpart, 0);
+        count_launch(ctx);
+        k_thermo_step<<<1, 256, 0, s>>>(ctx->vpart, nb, ctx->mass, EV_AMU, ctx->thermo, 0);
+        count_launch(ctx);
+        CK(cudaGetLastError());
+    }
+    int done = 0;
+    int retries = 0;
+    while (done < n_steps) {
+        const int len = (n_steps - done) < ctx->chunk ? (n_steps - done) : ctx->chunk;
+        auto it = ctx->graphs.find(len);
+        if (it == ctx->graphs.end()) {
+            GraphEntry ge;
+            rc = capture_steps(ctx, g, st, len, ge);
+            if (rc) return rc;
+            it = ctx->graphs.emplace(len, ge).first;
+        }
+        // rollback copy of x, v, F and the thermo block
+        const size_t bytes = sizeof(double) * 3 * (size_t)n;
+        CK(cudaMemcpyAsync(ctx->backup, st->xyz, bytes, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(ctx->backup + 3 * n, st->vel, bytes, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(ctx->backup + 6 * n, st->forces, bytes, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(ctx->thermo_backup, ctx->thermo, sizeof(double) * TH_N,
+                           cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemsetAsync(ctx->status, 0, sizeof(int) * 3, s));
+        CK(cudaGraphLaunch(it->second.exec, s));
+        ctx->launches += it->second.kernels;
+        rc = readback(ctx, s);
+        if (rc) return rc;
+        if (ctx->h_status[0] & ST_OVERFLOW) {
+            if (++retries > 4) return fail(ctx, NEP_ERR_NBR_OVERFLOW, "neighbour overflow persists");
+            CK(cudaMemcpyAsync(st->xyz, ctx->backup, bytes, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(st->vel, ctx->backup + 3 * n, bytes, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(st->forces, ctx->backup + 6 * n, bytes, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(ctx->thermo, ctx->thermo_backup, sizeof(double) * TH_N,
+                               cudaMemcpyDeviceToDevice, s));
+            CK(cudaStreamSynchronize(s));
+            rc = ensure_atoms(ctx, (int)n, grown_capacity(ctx->h_status[1]));
+            if (rc) return rc;
+            continue;
+        }
+        if (ctx->timing) {
+            rc = collect_timing(ctx, len);
+            if (rc) return rc;
+        }
+        if (ctx->h_status[0] & ST_NONFINITE)
+            return fail(ctx, NEP_ERR_NONFINITE, "non-finite values during MD");
+        done += len;
+    }
+    const double* th2 = ctx->h_result + NPART;
+    st->time = th2[TH_TIME];
+    st->step = (int64_t)llround(th2[TH_STEP]);
+    st->dt_last = th2[TH_DTLAST];
+    st->kinetic_energy = th2[TH_KE];
+    if (n_steps > 0) {
+        st->potential_energy = ctx->h_result[0];
+        for (int t = 0; t < 9; ++t) st->virial[t] = ctx->h_result[1 + t];
+    }
+    return NEP_OK;
+}
+
+}  // extern "C"

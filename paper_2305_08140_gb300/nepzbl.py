@@ -1,0 +1,271 @@
+"""Python binding of libnepzbl.so (C ABI in include/nepzbl.h).
+
+Argument marshalling only: every step of the force evaluation and of the MD
+step runs in the library's CUDA kernels.  PyTorch provides device memory and
+the current stream.  There is no CPU fallback: if the library cannot be built
+or loaded, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+NEP_OK = 0
+NEP_ERR_INVALID_ARG = -1
+NEP_ERR_CUDA = -2
+NEP_ERR_NBR_OVERFLOW = -3
+NEP_ERR_BOX = -4
+NEP_ERR_NONFINITE = -5
+NEP_ERR_ATOM_LOST = -6
+NEP_ERR_UNSUPPORTED = -7
+NEP_FP32 = 0
+NEP_FP64 = 1
+NEP_OPT_TIMING = 1
+NEP_OPT_GRAPH_CHUNK = 2
+NEP_OPT_NBR_CAPACITY = 3
+
+EXPORTED = ("nep_init", "nep_free", "nep_last_error", "nep_compute", "md_step",
+            "nep_get_stats", "nep_set_option", "nep_reset_stats")
+
+
+class NepParams(C.Structure):
+    _fields_ = [("n_types", C.c_int32), ("z", C.c_int32 * 4), ("mass", C.c_double * 4),
+                ("rc_radial", C.c_double), ("rc_angular", C.c_double),
+                ("zbl_r_inner", C.c_double), ("zbl_r_outer", C.c_double),
+                ("n_max_radial", C.c_int32), ("n_max_angular", C.c_int32),
+                ("basis_size_radial", C.c_int32), ("basis_size_angular", C.c_int32),
+                ("l_max", C.c_int32), ("use_4body", C.c_int32), ("n_hidden", C.c_int32),
+                ("params", C.POINTER(C.c_double)), ("n_params", C.c_int64),
+                ("q_scaler", C.POINTER(C.c_double))]
+
+
+class NepMdState(C.Structure):
+    _fields_ = [("n_atoms", C.c_int64), ("xyz", C.c_void_p), ("vel", C.c_void_p),
+                ("forces", C.c_void_p), ("types", C.c_void_p), ("box", C.c_double * 9),
+                ("pbc", C.c_int32 * 3), ("forces_valid", C.c_int32), ("dt_max", C.c_double),
+                ("d_max", C.c_double), ("time", C.c_double), ("step", C.c_int64),
+                ("dt_last", C.c_double), ("potential_energy", C.c_double),
+                ("kinetic_energy", C.c_double), ("virial", C.c_double * 9)]
+
+
+class NepStats(C.Structure):
+    _fields_ = [("kernel_launches", C.c_int64), ("timed_launches", C.c_int64),
+                ("timed_ms", C.c_double), ("pairs_radial", C.c_int64),
+                ("pairs_angular", C.c_int64), ("max_nbr_radial", C.c_int32),
+                ("max_nbr_angular", C.c_int32), ("nbr_capacity", C.c_int32),
+                ("graph_chunk", C.c_int32)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build: bool = True):
+    """Loads libnepzbl.so, compiling it first when it is missing or stale."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libnepzbl.so not found at {path}; run python -m "
+                          "paper_2305_08140_gb300.build")
+    L = C.CDLL(path)
+    vp = C.c_void_p
+    L.nep_init.argtypes = [C.POINTER(NepParams), C.c_int, C.POINTER(vp)]
+    L.nep_init.restype = C.c_int
+    L.nep_free.argtypes = [vp]
+    L.nep_free.restype = None
+    L.nep_last_error.argtypes = [vp]
+    L.nep_last_error.restype = C.c_char_p
+    L.nep_compute.argtypes = [vp, C.c_int64, vp, C.POINTER(C.c_double), vp,
+                              C.POINTER(C.c_int32), C.POINTER(C.c_double), vp,
+                              C.POINTER(C.c_double), vp, vp]
+    L.nep_compute.restype = C.c_int
+    L.md_step.argtypes = [vp, C.POINTER(NepMdState), C.c_int, vp]
+    L.md_step.restype = C.c_int
+    L.nep_get_stats.argtypes = [vp, C.POINTER(NepStats)]
+    L.nep_get_stats.restype = C.c_int
+    L.nep_set_option.argtypes = [vp, C.c_int, C.c_int64]
+    L.nep_set_option.restype = C.c_int
+    L.nep_reset_stats.argtypes = [vp]
+    L.nep_reset_stats.restype = C.c_int
+    _lib = L
+    return L
+
+
+class NepError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"NEP error {code}: {msg}")
+        self.code = code
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _box9(box) -> np.ndarray:
+    b = np.asarray(box, dtype=np.float64)
+    if b.shape == (3,):
+        b = np.diag(b)
+    return np.ascontiguousarray(b.reshape(9))
+
+
+class NEP:
+    """A NEP-ZBL model on the current CUDA device.
+
+    ``model`` is an ``inputs.NepModel`` (hyperparameters, flat parameters,
+    scaler); ``precision`` is "fp32" (mixed) or "fp64"."""
+
+    def __init__(self, model, precision: str = "fp32", mass: float | None = None):
+        self.lib = load()
+        self.model = model
+        self._params = np.ascontiguousarray(model.params, dtype=np.float64)
+        self._scaler = np.ascontiguousarray(model.scaler, dtype=np.float64)
+        p = NepParams()
+        p.n_types = 1
+        p.z[0] = int(model.z)
+        from .inputs import MASS_W
+        p.mass[0] = float(MASS_W if mass is None else mass)
+        p.rc_radial = model.rc_radial
+        p.rc_angular = model.rc_angular
+        p.zbl_r_inner = model.zbl_r_inner
+        p.zbl_r_outer = model.zbl_r_outer
+        p.n_max_radial = model.n_max_radial
+        p.n_max_angular = model.n_max_angular
+        p.basis_size_radial = model.basis_size_radial
+        p.basis_size_angular = model.basis_size_angular
+        p.l_max = model.l_max
+        p.use_4body = model.use_4body
+        p.n_hidden = model.n_hidden
+        p.params = self._params.ctypes.data_as(C.POINTER(C.c_double))
+        p.n_params = len(self._params)
+        p.q_scaler = self._scaler.ctypes.data_as(C.POINTER(C.c_double))
+        self.precision = {"fp32": NEP_FP32, "fp64": NEP_FP64}[precision]
+        h = C.c_void_p()
+        rc = self.lib.nep_init(C.byref(p), self.precision, C.byref(h))
+        if rc != NEP_OK:
+            raise NepError(rc, self.lib.nep_last_error(None).decode())
+        self.ctx = h
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.nep_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != NEP_OK:
+            raise NepError(rc, self.lib.nep_last_error(self.ctx).decode())
+
+    def compute(self, xyz, box, pbc, types=None, forces=None, site_energy=False, stream=None):
+        """One evaluation.  ``xyz`` is a CUDA float64 tensor (3, n) (SoA).
+        Returns (E, F (3, n) CUDA tensor, W (3, 3) numpy, U (n) tensor or None)."""
+        import torch
+        assert xyz.is_cuda and xyz.dtype == torch.float64 and xyz.dim() == 2 and xyz.shape[0] == 3
+        xyz = xyz.contiguous()
+        n = xyz.shape[1]
+        if types is None:
+            types = torch.zeros(n, dtype=torch.int32, device=xyz.device)
+        if forces is None:
+            forces = torch.empty((3, n), dtype=torch.float64, device=xyz.device)
+        U = torch.empty(n, dtype=torch.float64, device=xyz.device) if site_energy else None
+        b = _box9(box)
+        pb = (C.c_int32 * 3)(*[int(v) for v in pbc])
+        E = C.c_double()
+        W = (C.c_double * 9)()
+        rc = self.lib.nep_compute(self.ctx, n, C.c_void_p(xyz.data_ptr()),
+                                  b.ctypes.data_as(C.POINTER(C.c_double)),
+                                  C.c_void_p(types.data_ptr()), pb, C.byref(E),
+                                  C.c_void_p(forces.data_ptr()), W,
+                                  C.c_void_p(U.data_ptr()) if U is not None else None,
+                                  _stream_ptr(stream))
+        self._check(rc)
+        return E.value, forces, np.array(W[:]).reshape(3, 3), U
+
+    def md(self, state: "MDState", n_steps: int, stream=None):
+        self._check(self.lib.md_step(self.ctx, C.byref(state.c), int(n_steps), _stream_ptr(stream)))
+        return state
+
+    def stats(self) -> dict:
+        s = NepStats()
+        self._check(self.lib.nep_get_stats(self.ctx, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in NepStats._fields_}
+
+    def set_option(self, option: int, value: int):
+        self._check(self.lib.nep_set_option(self.ctx, int(option), int(value)))
+
+    def reset_stats(self):
+        self._check(self.lib.nep_reset_stats(self.ctx))
+
+
+class MDState:
+    """Device-resident MD state (SoA float64 tensors of shape (3, n))."""
+
+    def __init__(self, xyz, vel, box, pbc, dt_max=1.0, d_max=0.0, types=None, forces=None):
+        import torch
+        self.xyz = xyz.contiguous()
+        self.vel = vel.contiguous()
+        n = self.xyz.shape[1]
+        self.types = (torch.zeros(n, dtype=torch.int32, device=xyz.device)
+                      if types is None else types)
+        self.forces = (torch.zeros((3, n), dtype=torch.float64, device=xyz.device)
+                       if forces is None else forces)
+        c = NepMdState()
+        c.n_atoms = n
+        c.xyz = self.xyz.data_ptr()
+        c.vel = self.vel.data_ptr()
+        c.forces = self.forces.data_ptr()
+        c.types = self.types.data_ptr()
+        for t, v in enumerate(_box9(box)):
+            c.box[t] = v
+        for t in range(3):
+            c.pbc[t] = int(pbc[t])
+        c.forces_valid = 0 if forces is None else 1
+        c.dt_max = float(dt_max)
+        c.d_max = float(d_max)
+        self.c = c
+
+    @property
+    def time(self):
+        return self.c.time
+
+    @property
+    def step(self):
+        return self.c.step
+
+    @property
+    def potential_energy(self):
+        return self.c.potential_energy
+
+    @property
+    def kinetic_energy(self):
+        return self.c.kinetic_energy
+
+    @property
+    def dt_last(self):
+        return self.c.dt_last
+
+    @property
+    def virial(self):
+        return np.array(self.c.virial[:]).reshape(3, 3)
+
+
+def to_device_soa(a, device="cuda"):
+    """(n, 3) numpy array -> (3, n) float64 CUDA tensor."""
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.float64).T)).to(device)

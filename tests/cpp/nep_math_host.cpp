@@ -1,0 +1,23 @@
+// Host build of the CUDA path's per-pair math (nep_math.cuh) for CPU tests.
+#include "../../paper_2305_08140_gb300/csrc/nep_math.cuh"
+
+extern "C" {
+
+void h_harmonics(double x, double y, double z, double* Y) { nepm::harmonics<double>(x, y, z, Y); }
+
+void h_harmonics_grad_dot(double x, double y, double z, const double* G, double* v)
+{
+    nepm::harmonics_grad_dot<double>(x, y, z, G, v[0], v[1], v[2]);
+}
+
+double h_fourbody(const double* A2, double* dq) { return nepm::fourbody<double>(A2, dq); }
+
+void h_cheb9(double r, double inv_rc, double* T, double* dT, double* out3)
+{
+    double fc, dfc, dxdr;
+    nepm::cheb<9, true, double>(r, inv_rc, T, dT, fc, dfc, dxdr);
+    out3[0] = fc; out3[1] = dfc; out3[2] = dxdr;
+}
+
+void h_harmonics_f(float x, float y, float z, float* Y) { nepm::harmonics<float>(x, y, z, Y); }
+}

@@ -1,0 +1,260 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on
+the same seeded inputs, element by element."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2305_08140_gb300 import inputs as I
+
+from gpu_common import (F32_E_PER_ATOM, F32_F, F64_F, assert_parity, gpu_eval, nep,
+                        oracle_eval)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_c1_2000_atoms(precision):
+    assert_parity(I.c1(), precision)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_ragged_periodic_box(precision):
+    # 6 x 6 x 7 cells: 504 atoms = 3 full tiles of 128 and a ragged one
+    s = I.small_box((6, 6, 7), sigma=0.1, seed=21)
+    assert_parity(s, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_open_z_slab(precision):
+    s = I.displaced(I.c5(ncell=8, vacuum=10.0), 0.05, 22)
+    assert_parity(s, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_close_pairs_zbl_clump(precision):
+    """A small version of the close-pair stress case: ZBL pairs down to 0.3 A,
+    ~7x the lattice density in the clump.  The FP32 bound gains a relative
+    term: forces of 1e4-1e5 eV/A carry FP32 rounding of ~1e-7 relative."""
+    s = I.c3(ncell=10, fraction=0.05, radius=6.0, seed=23)
+    assert_parity(s, precision, rel_force=(2e-6 if precision == "fp32" else 1e-12))
+
+
+def test_single_atom_and_dimer():
+    s = I.Structure(np.array([[3.0, 4.0, 5.0]]), np.array([20.0, 20.0, 20.0]),
+                    np.array([1, 1, 1], np.int32), np.zeros(1, np.int32))
+    E, F, W, U = gpu_eval(s, "fp64")
+    Eo, Fo, Wo, Uo = oracle_eval(s)
+    assert E == pytest.approx(Eo, abs=1e-12)
+    assert np.all(F == 0)
+    for r in (0.5, 1.5, 3.0, 5.0):
+        d = I.Structure(np.array([[5.0, 5.0, 5.0], [5.0 + r, 5.0, 5.0]]),
+                        np.array([20.0, 20.0, 20.0]), np.array([0, 0, 0], np.int32),
+                        np.zeros(2, np.int32))
+        for prec in ("fp32", "fp64"):
+            assert_parity(d, prec, rel_force=1e-6 if prec == "fp32" else 1e-12)
+
+
+def test_empty_system():
+    from paper_2305_08140_gb300 import nepzbl as N
+    import torch
+    x = torch.zeros((3, 0), dtype=torch.float64, device="cuda")
+    E, F, W, U = nep("fp32").compute(x, [20.0, 20.0, 20.0], [1, 1, 1])
+    assert E == 0.0 and np.all(W == 0)
+
+
+def test_fp32_deterministic_bitwise():
+    s = I.displaced(I.small_box((8, 8, 8)), 0.08, 31)
+    a = gpu_eval(s, "fp32")
+    b = gpu_eval(s, "fp32")
+    assert a[0] == b[0]
+    assert np.array_equal(a[1], b[1])
+    assert np.array_equal(a[2], b[2])
+    assert np.array_equal(a[3], b[3])
+
+
+def test_periodic_shift_and_permutation():
+    s = I.small_box((7, 7, 7), sigma=0.07, seed=32)
+    E, F, W, U = gpu_eval(s, "fp32")
+    t = s.copy()
+    t.pos = t.pos + np.array([13.1, -7.7, 101.3])       # different cells, wrapped
+    E2, F2, W2, U2 = gpu_eval(t, "fp32")
+    assert abs(E2 - E) / s.n < 1e-7
+    np.testing.assert_allclose(F2, F, atol=2e-5)
+    perm = np.random.default_rng(3).permutation(s.n)
+    t = s.copy()
+    t.pos = s.pos[perm]
+    E3, F3, W3, U3 = gpu_eval(t, "fp32")
+    assert abs(E3 - E) / s.n < 1e-7
+    np.testing.assert_allclose(F3, F[perm], atol=2e-5)
+
+
+def test_capacity_grows_on_overflow():
+    from paper_2305_08140_gb300 import nepzbl as N
+    m = N.NEP(I.nep_model(1), "fp32")
+    m.set_option(N.NEP_OPT_NBR_CAPACITY, 8)
+    s = I.displaced(I.small_box((6, 6, 6)), 0.05, 33)
+    E, F, W, U = m.compute(N.to_device_soa(s.pos), s.box, s.pbc, site_energy=True)
+    st = m.stats()
+    assert st["nbr_capacity"] >= st["max_nbr_radial"] >= 50
+    E0, F0, W0, U0 = gpu_eval(s, "fp32")
+    assert E == E0
+    np.testing.assert_array_equal(F.cpu().numpy().T, F0)
+    m.close()
+
+
+def test_error_codes():
+    from paper_2305_08140_gb300 import nepzbl as N
+    import torch
+    m = nep("fp32")
+    s = I.small_box((6, 6, 6))
+    x = N.to_device_soa(s.pos)
+    with pytest.raises(N.NepError) as e:
+        m.compute(x, np.array([[19.0, 1.0, 0], [0, 19.0, 0], [0, 0, 19.0]]), [1, 1, 1])
+    assert e.value.code == N.NEP_ERR_BOX
+    with pytest.raises(N.NepError) as e:
+        m.compute(x, [12.0, 19.0, 19.0], [1, 1, 1])          # < 3 r_c periodic
+    assert e.value.code == N.NEP_ERR_BOX
+    bad = x.clone()
+    bad[0, 5] = float("nan")
+    with pytest.raises(N.NepError) as e:
+        m.compute(bad, s.box, s.pbc)
+    assert e.value.code == N.NEP_ERR_NONFINITE
+    # host memory where device memory is required
+    import ctypes as C
+    host = np.zeros(3 * s.n)
+    Eo = C.c_double()
+    rc = m.lib.nep_compute(m.ctx, s.n, C.c_void_p(host.ctypes.data),
+                           np.diag(s.box).reshape(9).ctypes.data_as(C.POINTER(C.c_double)),
+                           C.c_void_p(torch.zeros(s.n, dtype=torch.int32, device="cuda").data_ptr()),
+                           (C.c_int32 * 3)(1, 1, 1), C.byref(Eo),
+                           C.c_void_p(torch.zeros(3 * s.n, dtype=torch.float64,
+                                                  device="cuda").data_ptr()),
+                           None, None, None)
+    assert rc == N.NEP_ERR_INVALID_ARG
+    model = I.nep_model(1)
+    model.n_hidden = 20
+    model.params = model.params[:model.n_params]
+    with pytest.raises(N.NepError) as e:
+        N.NEP(model, "fp32")
+    assert e.value.code == N.NEP_ERR_UNSUPPORTED
+
+
+def test_atom_outside_open_extent():
+    s = I.displaced(I.c5(ncell=6, vacuum=6.0), 0.05, 34)
+    s.pos[0, 2] = -25.0          # far below the grid (sputtered atom)
+    s.pos[1, 2] = s.box[2] + 40  # far above
+    s.pos[2] = s.pos[1] + np.array([1.2, 0.3, 0.4])   # a close pair up there
+    assert_parity(s, "fp32", rel_force=2e-6)
+    assert_parity(s, "fp64", rel_force=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads, sampled outputs
+# ---------------------------------------------------------------------------
+
+def _sampled(s, idx, precision="fp32", rel=0.0):
+    E, F, W, U = gpu_eval(s, precision)
+    Fo, Uo = O.forces_subset(I.nep_model(1), s.pos, s.box, s.pbc, idx)
+    dF = np.abs(F[idx] - Fo)
+    assert np.all(dF <= F32_F + rel * np.abs(Fo)), dF.max()
+    assert np.max(np.abs(U[idx] - Uo)) <= 2e-6 + rel * np.max(np.abs(Uo))
+    # properties at any size: E is the sum of the site energies, sum F = 0
+    assert abs(E - U.sum()) / s.n < 1e-9
+    if np.all(s.pbc):
+        assert np.max(np.abs(F.sum(axis=0))) / s.n < 1e-9
+    return E, F, W, U
+
+
+def test_c2_128000_atoms_full_oracle():
+    s = I.displaced(I.c2(), 0.05, 41)
+    assert_parity(s, "fp32")
+
+
+def test_c5_8192000_atoms_sampled():
+    s = I.c5()
+    rng = np.random.default_rng(42)
+    # random atoms plus atoms on both free surfaces
+    z = s.pos[:, 2]
+    surf = np.concatenate([np.argsort(z)[:40], np.argsort(z)[-40:]])
+    idx = np.unique(np.concatenate([rng.choice(s.n, 120, replace=False), surf[::4]]))
+    _sampled(s, idx)
+    t = I.displaced(s, 0.05, 43)
+    _sampled(t, idx)
+
+
+def test_c3_250000_atoms_sampled():
+    s = I.c3()
+    moved = s.meta["moved"]
+    rng = np.random.default_rng(44)
+    idx = np.unique(np.concatenate([rng.choice(moved, 60, replace=False),
+                                    rng.choice(s.n, 60, replace=False)]))
+    _sampled(s, idx, rel=2e-6)
+
+
+def test_md_graph_forces_equal_direct_evaluation_c5():
+    """The graph-captured MD step (the launch configuration the bench times)
+    evaluates forces bitwise equal to a direct evaluation: with a time step of
+    1e-30 fs positions do not move in FP64."""
+    import torch
+    from paper_2305_08140_gb300 import nepzbl as N
+    s = I.displaced(I.c5(), 0.05, 45)
+    m = nep("fp32")
+    x = N.to_device_soa(s.pos)
+    E, F, W, U = m.compute(x.clone(), s.box, s.pbc)
+    F = F.clone()
+    st = N.MDState(x.clone(), torch.zeros_like(x), s.box, s.pbc, dt_max=1e-30)
+    m.md(st, 2)
+    assert torch.equal(st.xyz, x)
+    assert torch.equal(st.forces, F)
+    assert st.potential_energy == E
+
+
+# ---------------------------------------------------------------------------
+# MD against the oracle's velocity Verlet
+# ---------------------------------------------------------------------------
+
+def _run_md(s, precision, nsteps, dt=1.0, d_max=0.0, chunk=None):
+    from paper_2305_08140_gb300 import nepzbl as N
+    m = nep(precision)
+    if chunk:
+        m.set_option(N.NEP_OPT_GRAPH_CHUNK, chunk)
+    st = N.MDState(N.to_device_soa(s.pos), N.to_device_soa(s.vel), s.box, s.pbc, dt_max=dt,
+                   d_max=d_max)
+    m.md(st, nsteps)
+    if chunk:
+        m.set_option(N.NEP_OPT_GRAPH_CHUNK, 10)
+    return st
+
+
+def _min_image(d, box, pbc):
+    return d - np.where(np.asarray(pbc) > 0, box * np.round(d / box), 0.0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_md_c1_100_steps(precision):
+    s = I.c1()
+    st = _run_md(s, precision, 100, chunk=7)     # 7 + 7 + ... + 2: several graph lengths
+    p, v, F, th = O.md(I.nep_model(1), s.pos, s.vel, s.box, s.pbc, s.mass, 1.0, 100)
+    xg = st.xyz.cpu().numpy().T
+    vg = st.vel.cpu().numpy().T
+    dp = np.abs(_min_image(xg - p, s.box, s.pbc))
+    if precision == "fp64":
+        assert dp.max() < 1e-9
+        assert np.abs(vg - v).max() < 1e-10
+        assert st.potential_energy == pytest.approx(th[-1, 2], abs=1e-8)
+        assert st.kinetic_energy == pytest.approx(th[-1, 3], abs=1e-8)
+    else:
+        assert dp.max() < 2e-5
+        assert abs(st.potential_energy - th[-1, 2]) / s.n < 2e-6
+        assert abs(st.kinetic_energy - th[-1, 3]) / s.n < 2e-6
+    assert st.step == 100 and st.time == pytest.approx(100.0)
+
+
+def test_md_variable_timestep_fp64():
+    s = I.c3(ncell=10, fraction=0.05, radius=6.0, seed=23)
+    st = _run_md(s, "fp64", 20, dt=1.0, d_max=0.01, chunk=6)
+    p, v, F, th = O.md(I.nep_model(1), s.pos, s.vel, s.box, s.pbc, s.mass, 1.0, 20, d_max=0.01)
+    assert st.time == pytest.approx(th[:, 1].sum(), rel=1e-9)
+    assert st.dt_last == pytest.approx(th[-1, 1], rel=1e-9)
+    xg = st.xyz.cpu().numpy().T
+    assert np.abs(_min_image(xg - p, s.box, s.pbc)).max() < 1e-8
