@@ -1,10 +1,11 @@
 """Writes the descriptor scaler table paper_2305_08140_gb300/data/q_scaler.json.
 
-For each parameter seed, s_nu = 1 / max_i |q_nu^i| over the 2,000-atom c1
-structure, with q computed by the FP64 oracle only.  The scaler plays the part
-of NEP's per-component descriptor normalisation: random weights U(-0.5, 0.5)
-applied to unscaled descriptors would leave some components negligible and
-others large.
+For each parameter seed, s_nu = 1 / max |q_nu^i| over every atom i of the
+scaler structures (c1 crystal, hot crystal, liquid-like packing, compressed
+crystal -- the kinds of structure in the paper's W training set, Sec. III.A),
+with q computed by the FP64 oracle only.  The scaler plays the part of NEP's
+per-component descriptor normalisation: random weights U(-0.5, 0.5) applied to
+unscaled descriptors would leave some components negligible and others large.
 
 Run:  python -m oracle.make_scaler
 """
@@ -20,14 +21,19 @@ SEEDS = (1, 101)
 
 
 def main():
-    s = I.c1()
-    table = {"definition": "s_nu = 1 / max_i |q_nu^i| over the c1 structure "
-                           "(2,000-atom bcc W, sigma 0.05 A, seed 0), q from the FP64 oracle",
+    structs = I.scaler_structures()
+    table = {"definition": "s_nu = 1 / max |q_nu^i| over all atoms of inputs.scaler_structures() "
+                           "(c1 crystal; 432-atom crystal sigma 0.3 A; 128-atom liquid-like "
+                           "packing; 432-atom crystal at 0.9 a, sigma 0.1 A); q from the FP64 "
+                           "oracle",
              "scalers": {}}
     for seed in SEEDS:
         m = I.nep_model(seed, with_scaler=False)
-        q = O.descriptors(m, s.pos, s.box, s.pbc)
-        table["scalers"][str(seed)] = [float(v) for v in 1.0 / np.max(np.abs(q), axis=0)]
+        qmax = np.zeros(m.dim)
+        for s in structs:
+            q = O.descriptors(m, s.pos, s.box, s.pbc, use_grid=False)
+            qmax = np.maximum(qmax, np.max(np.abs(q), axis=0))
+        table["scalers"][str(seed)] = [float(v) for v in 1.0 / qmax]
     out = os.path.join(os.path.dirname(I.__file__), "data", "q_scaler.json")
     with open(out, "w") as f:
         json.dump(table, f, indent=1)

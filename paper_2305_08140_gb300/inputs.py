@@ -256,9 +256,40 @@ def draw_params(model: NepModel, seed: int) -> np.ndarray:
     return np.random.default_rng(seed).uniform(-0.5, 0.5, model.n_params)
 
 
+def random_packing(ncell: int = 4, min_sep: float = 2.2, seed: int = 200) -> Structure:
+    """Liquid-like W: 2 ncell^3 atoms placed uniformly at random (rejection
+    below ``min_sep`` A, minimum image) in the periodic box of an ncell^3 bcc
+    crystal, i.e. at the crystal's density."""
+    rng = np.random.default_rng(seed)
+    L = ncell * A_W
+    n = 2 * ncell ** 3
+    pts = np.empty((n, 3))
+    t = 0
+    while t < n:
+        p = rng.uniform(0.0, L, 3)
+        d = pts[:t] - p
+        d -= L * np.round(d / L)
+        if t == 0 or np.min(np.einsum("ij,ij->i", d, d)) >= min_sep * min_sep:
+            pts[t] = p
+            t += 1
+    return Structure(pts, np.array([L, L, L]), np.array([1, 1, 1], np.int32),
+                     np.zeros(n, np.int32), name="liquid_like")
+
+
+def scaler_structures() -> list[Structure]:
+    """Structures over which the descriptor scaler is taken, one of each kind
+    the paper's W training set contains (Sec. III.A: bulk bcc, strongly
+    disordered and liquid structures, short interatomic distances): the c1
+    crystal, a hot crystal (sigma = 0.3 A), a liquid-like random packing and a
+    crystal compressed to 0.9 a."""
+    return [c1(), small_box((6, 6, 6), sigma=0.3, seed=201), random_packing(),
+            small_box((6, 6, 6), a=0.9 * A_W, sigma=0.1, seed=202)]
+
+
 def stored_scaler(seed: int) -> np.ndarray:
-    """Descriptor scaler for the parameter set ``seed`` (s_nu = 1 / max_i |q_nu^i|
-    over the c1 structure), as written by the oracle's scaler script."""
+    """Descriptor scaler for the parameter set ``seed``: s_nu = 1 / max |q_nu^i|
+    over all atoms i of ``scaler_structures()``, as written by the oracle's
+    scaler script."""
     with open(os.path.join(_DATA, "q_scaler.json")) as f:
         table = json.load(f)
     return np.array(table["scalers"][str(seed)], dtype=np.float64)
