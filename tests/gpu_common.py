@@ -52,7 +52,7 @@ def assert_parity(s, precision="fp32", seed=1, rel_force=0.0):
     else:
         tf, te, tu, tw = F64_F, F64_E_PER_ATOM, F64_U, F64_W_PER_ATOM
     dF = np.abs(F - Fo)
-    bound = tf + rel_force * np.abs(Fo)
+    bound = tf + rel_force * np.linalg.norm(Fo, axis=1, keepdims=True)
     worst = np.unravel_index(np.argmax(dF - bound), dF.shape)
     assert np.all(dF <= bound), (f"max |dF| {dF.max():.3e} at {worst}: gpu {F[worst]} "
                                  f"oracle {Fo[worst]}")
