@@ -210,7 +210,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2305_08140_gb300 import nepzbl as N
 
-    s = I.c5()
+    s = I.c5(ncell=args.ncell)
     n = s.n
     model = I.nep_model(1)
     nep = N.NEP(model, "fp32")
@@ -324,7 +324,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded bcc W lattice, random-init NEP-ZBL weights)",
-        "config": {"workload": WORKLOAD, "atoms": n, "precision": "fp32 descriptors/network/forces,"
+        "config": {"workload": WORKLOAD if args.ncell == 160 else
+                   f"PROFILING CASE {args.ncell}^3-cell slab, {n} atoms", "atoms": n, "precision": "fp32 descriptors/network/forces,"
                    " fp64 positions/integrator/energy/virial", "parallelism": "replicas" if ws > 1
                    else "single GPU", "l2": "inputs larger than L2 (state ~0.6 GB, lists ~3 GB)",
                    "graph_chunk": 25},
@@ -356,6 +357,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--ncell", type=int, default=160,
+                    help="slab size in bcc cells per side (160 = the 8,192,000-atom workload; "
+                         "smaller values only for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
