@@ -356,13 +356,22 @@ __device__ __forceinline__ void zbl_pair(double r, double k, double inv_a, doubl
     dU = dv * fc + v * dfc;
 }
 
+// The 27 stencil offsets (cell-edge multiples) of the neighbour codes, in
+// shared memory; filled by the first 27 threads of the block.
 template <typename R>
-__device__ __forceinline__ void stencil_offset(int code, const Grid& g, R& ox, R& oy, R& oz)
+__device__ __forceinline__ void fill_stencil(typename V4<R>::T* tab, const Grid& g)
 {
-    int a = code / 9, b = (code / 3) % 3, c = code % 3;
-    ox = (R)((a - 1) * g.lc[0]);
-    oy = (R)((b - 1) * g.lc[1]);
-    oz = (R)((c - 1) * g.lc[2]);
+    if (threadIdx.x < 27) {
+        int code = threadIdx.x;
+        int a = code / 9, b = (code / 3) % 3, c = code % 3;
+        typename V4<R>::T o;
+        o.x = (R)((a - 1) * g.lc[0]);
+        o.y = (R)((b - 1) * g.lc[1]);
+        o.z = (R)((c - 1) * g.lc[2]);
+        o.w = R(0);
+        tab[code] = o;
+    }
+    __syncthreads();
 }
 
 // ----------------------------------------------------------------------------
@@ -384,6 +393,9 @@ __global__ void __launch_bounds__(TILE) k_nep(const Model<R> P, const Grid g,
                                               int* __restrict__ status)
 {
     using A_ = Acc<R>;
+    using P4 = typename V4<R>::T;
+    __shared__ P4 s_off[27];
+    fill_stencil<R>(s_off, g);
     const int k = blockIdx.x * TILE + threadIdx.x;
     const int M = g.M;
     const size_t ld = (size_t)g.ld;
@@ -407,15 +419,26 @@ __global__ void __launch_bounds__(TILE) k_nep(const Model<R> P, const Grid g,
 #pragma unroll
             for (int lm = 0; lm < NLM; ++lm) A[n][lm] = R(0);
 
-        for (int s = 0; s < na + nro; ++s) {
-            const int slot = s < na ? s : M - nro + (s - na);
-            const int ent = nbr[slot * ld + k];
-            const int m = ent >> 5;
-            R ox, oy, oz;
-            stencil_offset(ent & 31, g, ox, oy, oz);
-            const typename V4<R>::T pj = pos4[m];
-            const R dx = pj.x - pi.x + ox, dy = pj.y - pi.y + oy, dz = pj.z - pi.z + oz;
-            const R r = nepm::nep_sqrt(dx * dx + dy * dy + dz * dz);
+        const int total = na + nro;
+        // two-stage prefetch: entry s + 2 and position s + 1 are loaded while
+        // pair s is computed
+        int ent_n = total > 0 ? nbr[(size_t)(na > 0 ? 0 : M - nro) * ld + k] : 0;
+        int ent_nn = total > 1 ? nbr[(size_t)(1 < na ? 1 : M - nro + (1 - na)) * ld + k] : 0;
+        P4 pj_n = total > 0 ? pos4[ent_n >> 5] : pi;
+        for (int s = 0; s < total; ++s) {
+            const int ent = ent_n;
+            const P4 pj = pj_n;
+            ent_n = ent_nn;
+            if (s + 1 < total) pj_n = pos4[ent_n >> 5];
+            if (s + 2 < total) {
+                const int s2 = s + 2;
+                ent_nn = nbr[(size_t)(s2 < na ? s2 : M - nro + (s2 - na)) * ld + k];
+            }
+            const P4 off = s_off[ent & 31];
+            const R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
+            const R r2 = dx * dx + dy * dy + dz * dz;
+            const R inv_r = nepm::nep_rsqrt(r2);
+            const R r = r2 * inv_r;
             R T[KR], dT[KR], fc, dfc, dxdr;
             nepm::cheb<KR, false>(r, P.inv_rcR, T, dT, fc, dfc, dxdr);
 #pragma unroll
@@ -427,7 +450,6 @@ __global__ void __launch_bounds__(TILE) k_nep(const Model<R> P, const Grid g,
             }
             if (s < na) {
                 nepm::cheb<KA, false>(r, P.inv_rcA, T, dT, fc, dfc, dxdr);
-                const R inv_r = R(1) / r;
                 R Y[NLM];
                 nepm::harmonics(dx * inv_r, dy * inv_r, dz * inv_r, Y);
 #pragma unroll
@@ -527,16 +549,24 @@ __global__ void __launch_bounds__(TILE) k_nep(const Model<R> P, const Grid g,
         bool bad = !isfinite(U);
         const int i_caller = perm[k];
 
-        for (int s = 0; s < na + nro; ++s) {
-            const int slot = s < na ? s : M - nro + (s - na);
-            const int ent = nbr[slot * ld + k];
+        ent_n = total > 0 ? nbr[(size_t)(na > 0 ? 0 : M - nro) * ld + k] : 0;
+        ent_nn = total > 1 ? nbr[(size_t)(1 < na ? 1 : M - nro + (1 - na)) * ld + k] : 0;
+        pj_n = total > 0 ? pos4[ent_n >> 5] : pi;
+        for (int s = 0; s < total; ++s) {
+            const int ent = ent_n;
+            const P4 pj = pj_n;
+            ent_n = ent_nn;
+            if (s + 1 < total) pj_n = pos4[ent_n >> 5];
+            if (s + 2 < total) {
+                const int s2 = s + 2;
+                ent_nn = nbr[(size_t)(s2 < na ? s2 : M - nro + (s2 - na)) * ld + k];
+            }
             const int m = ent >> 5;
-            R ox, oy, oz;
-            stencil_offset(ent & 31, g, ox, oy, oz);
-            const typename V4<R>::T pj = pos4[m];
-            const R dx = pj.x - pi.x + ox, dy = pj.y - pi.y + oy, dz = pj.z - pi.z + oz;
-            const R r = nepm::nep_sqrt(dx * dx + dy * dy + dz * dz);
-            const R inv_r = R(1) / r;
+            const P4 off = s_off[ent & 31];
+            const R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
+            const R r2 = dx * dx + dy * dy + dz * dz;
+            const R inv_r = nepm::nep_rsqrt(r2);
+            const R r = r2 * inv_r;
             const R ux = dx * inv_r, uy = dy * inv_r, uz = dz * inv_r;
             R T[KR], dT[KR], fc, dfc, dxdr;
             // radial: sum_n dU/dq_n g'_n(r)
@@ -674,6 +704,30 @@ __global__ void k_forces_out(int n, int ld, const int* __restrict__ perm,
         F[(size_t)a * n + i] = f;
     }
     if (bad) atomicOr(status, ST_NONFINITE);
+}
+
+// Stage 1 of the energy/virial sum: block b adds the tiles
+// [b * chunk, (b + 1) * chunk) in a fixed order; out[b * NPART + c].
+constexpr int RED1_MAX = 512;
+__global__ void __launch_bounds__(256) k_reduce_stage1(const double* __restrict__ partials,
+                                                       int ntiles, int chunk,
+                                                       double* __restrict__ out)
+{
+    __shared__ double sh[256];
+    const int t0 = blockIdx.x * chunk;
+    const int t1 = min(ntiles, t0 + chunk);
+    for (int c = 0; c < NPART; ++c) {
+        double s = 0.0;
+        for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) s += partials[(size_t)t * NPART + c];
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[(size_t)blockIdx.x * NPART + c] = sh[0];
+        __syncthreads();
+    }
 }
 
 // One block: sums the per-tile partials in a fixed order into out[0..NPART).

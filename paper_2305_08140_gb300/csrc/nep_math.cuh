@@ -55,6 +55,44 @@ NEP_HD void nep_sincospi(double x, double* s, double* c)
 #endif
 }
 
+NEP_HD float nep_rsqrt(float x)
+{
+#if defined(__CUDA_ARCH__)
+    return rsqrtf(x);
+#else
+    return 1.0f / sqrtf(x);
+#endif
+}
+NEP_HD double nep_rsqrt(double x) { return 1.0 / sqrt(x); }
+
+// sin(pi x) and cos(pi x) for x in [0, 1].  FP32: with theta = pi (x - 1/2)
+// in [-pi/2, pi/2], cos(pi x) = -sin(theta) and sin(pi x) = cos(theta), each
+// from its Taylor series (sin to theta^13, cos to theta^14; truncation below
+// 7e-10 on the interval), evaluated by Horner in theta^2.  FP64: sincospi.
+NEP_HD void cutoff_sincospi(float x, float* s, float* c)
+{
+    const float th = 3.14159265358979f * (x - 0.5f);
+    const float u = th * th;
+    float sn = 1.6059043836821613e-10f;            // 1/13!
+    sn = sn * u - 2.505210838544172e-08f;          // 1/11!
+    sn = sn * u + 2.7557319223985893e-06f;         // 1/9!
+    sn = sn * u - 1.984126984126984e-04f;          // 1/7!
+    sn = sn * u + 8.333333333333333e-03f;          // 1/5!
+    sn = sn * u - 1.6666666666666666e-01f;         // 1/3!
+    sn = (sn * u + 1.0f) * th;
+    float cs = -1.1470745597729725e-11f;           // 1/14!
+    cs = cs * u + 2.08767569878681e-09f;           // 1/12!
+    cs = cs * u - 2.755731922398589e-07f;          // 1/10!
+    cs = cs * u + 2.48015873015873e-05f;           // 1/8!
+    cs = cs * u - 1.388888888888889e-03f;          // 1/6!
+    cs = cs * u + 4.1666666666666664e-02f;         // 1/4!
+    cs = cs * u - 0.5f;                            // 1/2!
+    cs = cs * u + 1.0f;
+    *c = -sn;
+    *s = cs;
+}
+NEP_HD void cutoff_sincospi(double x, double* s, double* c) { nep_sincospi(x, s, c); }
+
 // Chebyshev values T_0..T_{K-1} at x = 2 (r/rc - 1)^2 - 1, the cutoff f_c and,
 // when DERIV, dT_k/dx, dx/dr and df_c/dr.  Requires r < rc.
 template <int K, bool DERIV, typename R>
@@ -63,7 +101,7 @@ NEP_HD void cheb(R r, R inv_rc, R* T, R* dT, R& fc, R& dfc, R& dxdr)
     R t = r * inv_rc - R(1);
     R x = R(2) * t * t - R(1);
     R s, c;
-    nep_sincospi(r * inv_rc, &s, &c);
+    cutoff_sincospi(r * inv_rc, &s, &c);
     fc = R(0.5) * (R(1) + c);
     T[0] = R(1);
     T[1] = x;

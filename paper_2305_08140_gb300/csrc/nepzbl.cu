@@ -54,6 +54,7 @@ struct nep_ctx {
     int* nbr = nullptr;
     void* facc = nullptr;
     double* partials = nullptr;
+    double* partials2 = nullptr;     // RED1_MAX x NPART
     double* vpart = nullptr;
     int *count = nullptr, *start = nullptr, *scan_sums = nullptr;
     double* backup = nullptr;        // x, v, F copies for MD rollback
@@ -131,7 +132,8 @@ static void free_scratch(nep_ctx* ctx)
     drop_graphs(ctx);
     free_dev(ctx->cell_of); free_dev(ctx->slot_of); free_dev(ctx->perm);
     free_dev(ctx->cell_sorted); free_dev(ctx->pos4); free_dev(ctx->cnt); free_dev(ctx->nbr);
-    free_dev(ctx->facc); free_dev(ctx->partials); free_dev(ctx->vpart); free_dev(ctx->backup);
+    free_dev(ctx->facc); free_dev(ctx->partials); free_dev(ctx->partials2);
+    free_dev(ctx->vpart); free_dev(ctx->backup);
     ctx->ld = 0;
     ctx->M = 0;
 }
@@ -158,6 +160,7 @@ static int ensure_atoms(nep_ctx* ctx, int n, int M)
     CK(cudaMalloc(&ctx->facc, acc * 3 * (size_t)ld));
     CK(cudaMemset(ctx->facc, 0, acc * 3 * (size_t)ld));
     CK(cudaMalloc(&ctx->partials, sizeof(double) * NPART * (size_t)tiles));
+    CK(cudaMalloc(&ctx->partials2, sizeof(double) * NPART * (size_t)RED1_MAX));
     CK(cudaMalloc(&ctx->vpart, sizeof(double) * 2 * (size_t)vb));
     CK(cudaMalloc(&ctx->backup, sizeof(double) * 9 * (size_t)ld));
     ctx->ld = ld;
@@ -286,8 +289,16 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     k_forces_out<R><<<nb, tb, 0, s>>>(n, ctx->ld, ctx->perm, (typename Acc<R>::T*)ctx->facc, F,
                                       ctx->status);
     count_launch(ctx);
-    k_reduce_partials<<<1, 256, 0, s>>>(ctx->partials, tiles, ctx->result);
-    count_launch(ctx);
+    {
+        // two-stage fixed-order sum of the per-tile energy/virial partials
+        const int chunk = (tiles + RED1_MAX - 1) / RED1_MAX > 64 ? (tiles + RED1_MAX - 1) / RED1_MAX
+                                                                 : 64;
+        const int nb1 = (tiles + chunk - 1) / chunk;
+        k_reduce_stage1<<<nb1, 256, 0, s>>>(ctx->partials, tiles, chunk, ctx->partials2);
+        count_launch(ctx);
+        k_reduce_partials<<<1, 256, 0, s>>>(ctx->partials2, nb1, ctx->result);
+        count_launch(ctx);
+    }
     CK(cudaGetLastError());
     return NEP_OK;
 }

@@ -21,3 +21,8 @@ void h_cheb9(double r, double inv_rc, double* T, double* dT, double* out3)
 
 void h_harmonics_f(float x, float y, float z, float* Y) { nepm::harmonics<float>(x, y, z, Y); }
 }
+
+extern "C" void h_cutoff_f(float x, float* sc)
+{
+    nepm::cutoff_sincospi(x, &sc[0], &sc[1]);
+}

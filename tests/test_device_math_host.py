@@ -102,3 +102,16 @@ def test_chebyshev_basis(lib):
         assert o[0] == pytest.approx(0.5 * (1 + math.cos(math.pi * r / rc)), abs=1e-15)
         assert o[1] == pytest.approx(-0.5 * math.pi / rc * math.sin(math.pi * r / rc), abs=1e-15)
         assert o[2] == pytest.approx(4 * (r / rc - 1) / rc, abs=1e-15)
+
+
+def test_fp32_cutoff_polynomial(lib):
+    """The FP32 sin/cos(pi x) used for the cutoff is within 3e-7 of the exact
+    values on [0, 1] (FP32 rounding of the Horner evaluation)."""
+    lib.h_cutoff_f.argtypes = [C.c_float, C.POINTER(C.c_float)]
+    out = np.zeros(2, np.float32)
+    worst = 0.0
+    for x in np.linspace(0.0, 1.0, 2001):
+        lib.h_cutoff_f(float(x), out.ctypes.data_as(C.POINTER(C.c_float)))
+        xf = float(np.float32(x))
+        worst = max(worst, abs(out[0] - math.sin(math.pi * xf)), abs(out[1] - math.cos(math.pi * xf)))
+    assert worst < 3e-7, worst
