@@ -178,6 +178,36 @@ int nep_set_option(nep_ctx* ctx, int option, int64_t value);
 /* Resets the counters of nep_stats (launches, timing). */
 int nep_reset_stats(nep_ctx* ctx);
 
+/* Force evaluation that allocates nothing (the paper has no counterpart; it is
+ * a deployment convenience).  It is meant for callers that may not allocate
+ * GPU memory at the point where they need forces: code embedded in a host
+ * program whose device memory is owned by that program's own pool, or code
+ * running while the host is capturing a stream into a graph, where a
+ * cudaMalloc would break the capture.  It takes the model parameters directly
+ * (no context: creating one allocates) and computes the same FP32 evaluation
+ * as nep_compute with a context created with NEP_FP32; arguments as in
+ * nep_compute.
+ *   Limits: at most 8192 atoms, 96 neighbours per atom within rc_radial
+ *   (beyond that NEP_ERR_NBR_OVERFLOW; there is no growth), a cell grid of at
+ *   most 8192 cells.  Larger systems are rejected with NEP_ERR_INVALID_ARG or
+ *   NEP_ERR_BOX before any GPU work.
+ *   Scratch: one fixed device array of about 3.8 MB that the library
+ *   declares at file scope; every GPU that loads the library holds it until
+ *   the process exits.  No cudaMalloc, cudaFree or other allocating call is
+ *   made.
+ *   Set-up: the first call on a device (with that device current) looks up
+ *   the array's device address once and caches it; make that first call
+ *   before any stream capture.
+ *   Concurrency: all calls share the one array; calls whose GPU work overlaps
+ *   (different streams, threads or processes' contexts on the same device
+ *   within this process) race and give wrong results.  Each call clears what
+ *   must start at zero and finishes with a stream synchronisation.
+ * Errors are reported through nep_last_error(NULL). */
+int nep_compute_static(const nep_params* p, int64_t n_atoms, const double* xyz,
+                       const double box[9], const int32_t* types, const int32_t pbc[3],
+                       double* energy, double* forces, double* virial, double* site_energy,
+                       void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -753,3 +754,196 @@ int md_step(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Force evaluation without any allocation: scratch in a fixed device array
+// ============================================================================
+//
+// For callers that cannot call cudaMalloc at the point where they need forces
+// (for example code running inside a host framework whose device memory is all
+// owned by its own pool, or a plugin that may not touch the allocator while a
+// stream is being captured by its host).  All scratch of one FP32 evaluation
+// lives in g_static_scratch below, a file-scope __device__ array that every GPU
+// loading this library holds until the process exits.
+
+namespace {
+
+constexpr int ST_MAX_ATOMS = 8192;   // largest system of the fixed-scratch path
+constexpr int ST_SLOTS = 96;         // neighbour slots per atom
+constexpr int ST_MAX_CELLS = 8192;   // largest cell grid
+constexpr int ST_TILES = (ST_MAX_ATOMS + TILE - 1) / TILE;
+
+constexpr size_t st_align(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t ST_OFF_CELL_OF = 0;
+constexpr size_t ST_OFF_SLOT_OF = ST_OFF_CELL_OF + st_align(sizeof(int) * ST_MAX_ATOMS);
+constexpr size_t ST_OFF_PERM = ST_OFF_SLOT_OF + st_align(sizeof(int) * ST_MAX_ATOMS);
+constexpr size_t ST_OFF_CELL_SORTED = ST_OFF_PERM + st_align(sizeof(int) * ST_MAX_ATOMS);
+constexpr size_t ST_OFF_POS4 = ST_OFF_CELL_SORTED + st_align(sizeof(int) * ST_MAX_ATOMS);
+constexpr size_t ST_OFF_CNT = ST_OFF_POS4 + st_align(sizeof(float4) * ST_MAX_ATOMS);
+constexpr size_t ST_OFF_NBR = ST_OFF_CNT + st_align(sizeof(int2) * ST_MAX_ATOMS);
+constexpr size_t ST_OFF_FACC = ST_OFF_NBR + st_align(sizeof(int) * (size_t)ST_MAX_ATOMS * ST_SLOTS);
+constexpr size_t ST_OFF_PART = ST_OFF_FACC + st_align(sizeof(long long) * 3 * ST_MAX_ATOMS);
+constexpr size_t ST_OFF_PART2 = ST_OFF_PART + st_align(sizeof(double) * NPART * ST_TILES);
+constexpr size_t ST_OFF_COUNT = ST_OFF_PART2 + st_align(sizeof(double) * NPART * RED1_MAX);
+constexpr size_t ST_OFF_START = ST_OFF_COUNT + st_align(sizeof(int) * (ST_MAX_CELLS + 1));
+constexpr size_t ST_OFF_SCAN = ST_OFF_START + st_align(sizeof(int) * (ST_MAX_CELLS + 1));
+constexpr size_t ST_OFF_RESULT = ST_OFF_SCAN + st_align(sizeof(int) * SCAN_B);
+constexpr size_t ST_OFF_STATUS = ST_OFF_RESULT + st_align(sizeof(double) * NPART);
+constexpr size_t ST_OFF_PAIRS = ST_OFF_STATUS + st_align(sizeof(int) * 3);
+constexpr size_t ST_BYTES = ST_OFF_PAIRS + st_align(sizeof(unsigned long long) * 2);
+
+constexpr int ST_MAX_DEVICES = 64;
+std::mutex g_static_mutex;
+unsigned char* g_static_ptr[ST_MAX_DEVICES] = {nullptr};
+
+}  // namespace
+
+// About 3.8 MB.  Host code must not use this name as an address: the device
+// address comes from cudaGetSymbolAddress (static_scratch_address below).
+static __device__ __align__(256) unsigned char g_static_scratch[ST_BYTES];
+
+// Device address of g_static_scratch on the current device; looked up once per
+// device (first call on that device) and cached.
+static int static_scratch_address(unsigned char** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return fail(nullptr, NEP_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= ST_MAX_DEVICES)
+        return fail(nullptr, NEP_ERR_CUDA, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(nullptr, NEP_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        g_static_ptr[dev] = (unsigned char*)p;
+    }
+    *out = g_static_ptr[dev];
+    return NEP_OK;
+}
+
+extern "C" int nep_compute_static(const nep_params* p, int64_t n_atoms, const double* xyz,
+                                  const double box[9], const int32_t* types,
+                                  const int32_t pbc[3], double* energy, double* forces,
+                                  double* virial, double* site_energy, void* stream)
+{
+    nep_ctx* ctx = nullptr;   // errors go to nep_last_error(NULL)
+    if (!p || !box || !pbc || !energy) return fail(nullptr, NEP_ERR_INVALID_ARG, "NULL argument");
+    if (n_atoms < 0 || n_atoms > ST_MAX_ATOMS)
+        return fail(nullptr, NEP_ERR_INVALID_ARG,
+                    "nep_compute_static handles at most %d atoms (got %lld)", ST_MAX_ATOMS,
+                    (long long)n_atoms);
+    if (p->n_types != 1 || p->n_max_radial != NR - 1 || p->n_max_angular != NA - 1 ||
+        p->basis_size_radial != KR - 1 || p->basis_size_angular != KA - 1 || p->l_max != LM ||
+        p->use_4body != 1 || p->n_hidden != H)
+        return fail(nullptr, NEP_ERR_UNSUPPORTED, "model sizes not supported by this build");
+    const int64_t np = (int64_t)H * D + 2 * H + 1 + NR * KR + NA * KA;
+    if (!p->params || p->n_params != np || !p->q_scaler)
+        return fail(nullptr, NEP_ERR_INVALID_ARG, "params must hold %lld values and a scaler",
+                    (long long)np);
+    if (!(p->rc_radial > 0) || !(p->rc_angular > 0) || p->rc_angular > p->rc_radial ||
+        !(p->zbl_r_outer > p->zbl_r_inner) || p->zbl_r_outer > p->rc_angular || !(p->z[0] > 0))
+        return fail(nullptr, NEP_ERR_INVALID_ARG, "bad cutoffs or nuclear charge");
+    // cell grid (diagonal box; periodic dims need >= 3 cells of >= rc_R)
+    Grid g;
+    memset(&g, 0, sizeof(g));
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            if (a != b && box[3 * a + b] != 0.0)
+                return fail(nullptr, NEP_ERR_BOX, "only diagonal boxes are supported");
+    for (int a = 0; a < 3; ++a) {
+        const double L = box[4 * a];
+        if (!(L > 0.0) || !isfinite(L)) return fail(nullptr, NEP_ERR_BOX, "box length %g", L);
+        int nc = (int)floor(L / p->rc_radial);
+        if (pbc[a] && nc < 3) return fail(nullptr, NEP_ERR_BOX, "periodic box shorter than 3 r_c");
+        if (nc < 1) nc = 1;
+        if (nc > 1024) nc = 1024;
+        g.nc[a] = nc;
+        g.pbc[a] = pbc[a] ? 1 : 0;
+        g.lc[a] = L / nc;
+        g.inv_lc[a] = nc / L;
+        g.L[a] = L;
+        g.invL[a] = 1.0 / L;
+    }
+    const int ncell = g.nc[0] * g.nc[1] * g.nc[2];
+    if (ncell > ST_MAX_CELLS)
+        return fail(nullptr, NEP_ERR_BOX, "cell grid of %d cells exceeds %d", ncell, ST_MAX_CELLS);
+    const int n = (int)n_atoms;
+    g.n = n;
+    g.ld = ST_MAX_ATOMS;
+    g.M = ST_SLOTS;
+    if (n == 0) {
+        *energy = 0.0;
+        if (virial) for (int t = 0; t < 9; ++t) virial[t] = 0.0;
+        return NEP_OK;
+    }
+    for (const void* q : {(const void*)xyz, (const void*)types, (const void*)forces}) {
+        cudaPointerAttributes at;
+        if (!q || cudaPointerGetAttributes(&at, q) != cudaSuccess ||
+            (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+            cudaGetLastError();
+            return fail(nullptr, NEP_ERR_INVALID_ARG, "inputs and outputs must be device memory");
+        }
+    }
+    unsigned char* base = nullptr;
+    int rc = static_scratch_address(&base);
+    if (rc) return rc;
+    int* cell_of = (int*)(base + ST_OFF_CELL_OF);
+    int* slot_of = (int*)(base + ST_OFF_SLOT_OF);
+    int* perm = (int*)(base + ST_OFF_PERM);
+    int* cell_sorted = (int*)(base + ST_OFF_CELL_SORTED);
+    float4* pos4 = (float4*)(base + ST_OFF_POS4);
+    int2* cnt = (int2*)(base + ST_OFF_CNT);
+    int* nbr = (int*)(base + ST_OFF_NBR);
+    long long* facc = (long long*)(base + ST_OFF_FACC);
+    double* partials = (double*)(base + ST_OFF_PART);
+    double* partials2 = (double*)(base + ST_OFF_PART2);
+    int* count = (int*)(base + ST_OFF_COUNT);
+    int* start = (int*)(base + ST_OFF_START);
+    int* scan_sums = (int*)(base + ST_OFF_SCAN);
+    double* result = (double*)(base + ST_OFF_RESULT);
+    int* status = (int*)(base + ST_OFF_STATUS);
+    unsigned long long* pairs = (unsigned long long*)(base + ST_OFF_PAIRS);
+
+    Model<float> P;
+    build_model<float>(P, p);
+    cudaStream_t s = (cudaStream_t)stream;
+    // the array keeps the previous call's contents: clear what must start at zero
+    CK(cudaMemsetAsync(facc, 0, sizeof(long long) * 3 * ST_MAX_ATOMS, s));
+    CK(cudaMemsetAsync(count, 0, sizeof(int) * (size_t)(ncell + 1), s));
+    CK(cudaMemsetAsync(status, 0, sizeof(int) * 3, s));
+    CK(cudaMemsetAsync(pairs, 0, sizeof(unsigned long long) * 2, s));
+    const int tb = 256, nb = (n + tb - 1) / tb;
+    k_bin_count<<<nb, tb, 0, s>>>(g, xyz, cell_of, slot_of, count, status);
+    const int sb = (ncell + SCAN_B - 1) / SCAN_B;
+    k_scan_blocks<<<sb, SCAN_T, 0, s>>>(count, ncell, start, scan_sums);
+    k_scan_sums<<<1, SCAN_T, 0, s>>>(scan_sums, sb, start, ncell);
+    k_scan_add<<<(ncell + tb - 1) / tb, tb, 0, s>>>(start, ncell, scan_sums);
+    k_bin_scatter<<<nb, tb, 0, s>>>(n, cell_of, slot_of, start, perm);
+    k_cell_finalize<float><<<(ncell + 127) / 128, 128, 0, s>>>(g, ncell, start, perm, xyz, types,
+                                                              pos4, cell_sorted);
+    k_neighbors<float><<<(n + 127) / 128, 128, 0, s>>>(g, P.rcR2, P.rcA2, pos4, cell_sorted, start,
+                                                      nbr, cnt, status, status + 1, pairs);
+    const int tiles = (n + TILE - 1) / TILE;
+    k_nep<float><<<tiles, TILE, 0, s>>>(P, g, pos4, nbr, cnt, perm, xyz, facc, partials,
+                                        site_energy, status);
+    k_forces_out<float><<<nb, tb, 0, s>>>(n, ST_MAX_ATOMS, perm, facc, forces, status);
+    k_reduce_stage1<<<1, 256, 0, s>>>(partials, tiles, tiles, partials2);
+    k_reduce_partials<<<1, 256, 0, s>>>(partials2, 1, result);
+    CK(cudaGetLastError());
+    int st[3];
+    double res[NPART];
+    CK(cudaMemcpyAsync(st, status, sizeof(st), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(res, result, sizeof(res), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (st[0] & ST_OVERFLOW)
+        return fail(nullptr, NEP_ERR_NBR_OVERFLOW,
+                    "an atom has %d neighbours within r_c; this path holds %d", st[1], ST_SLOTS);
+    if (st[0] & ST_NONFINITE)
+        return fail(nullptr, NEP_ERR_NONFINITE, "non-finite positions, energies or forces");
+    *energy = res[0];
+    if (virial) for (int t = 0; t < 9; ++t) virial[t] = res[1 + t];
+    return NEP_OK;
+}

@@ -29,7 +29,7 @@ NEP_OPT_GRAPH_CHUNK = 2
 NEP_OPT_NBR_CAPACITY = 3
 
 EXPORTED = ("nep_init", "nep_free", "nep_last_error", "nep_compute", "md_step",
-            "nep_get_stats", "nep_set_option", "nep_reset_stats")
+            "nep_get_stats", "nep_set_option", "nep_reset_stats", "nep_compute_static")
 
 
 class NepParams(C.Structure):
@@ -96,6 +96,10 @@ def load(build: bool = True):
     L.nep_set_option.restype = C.c_int
     L.nep_reset_stats.argtypes = [vp]
     L.nep_reset_stats.restype = C.c_int
+    L.nep_compute_static.argtypes = [C.POINTER(NepParams), C.c_int64, vp, C.POINTER(C.c_double),
+                                     vp, C.POINTER(C.c_int32), C.POINTER(C.c_double), vp,
+                                     C.POINTER(C.c_double), vp, vp]
+    L.nep_compute_static.restype = C.c_int
     _lib = L
     return L
 
