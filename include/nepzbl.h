@@ -178,6 +178,63 @@ int nep_set_option(nep_ctx* ctx, int option, int64_t value);
 /* Resets the counters of nep_stats (launches, timing). */
 int nep_reset_stats(nep_ctx* ctx);
 
+/* ---------------------------------------------------------------------------
+ * Batches of small periodic configurations (training-style workloads)
+ *
+ * Many independent periodic boxes are evaluated in one persistent launch: a
+ * CTA takes whole configurations from a work queue (largest first), builds
+ * their neighbour lists over all periodic images (self-images included, so
+ * boxes down to r_c^R per side are exact), evaluates energies and forces, and
+ * for the gradient entry points the derivative of a loss with respect to all
+ * n_params model parameters, including the force term's second derivatives:
+ * with e_i = dL/dF_i and eps_s = dL/dE_s,
+ *   dL/dtheta = sum_i d/dtheta [eps U_i - (dU_i/dq_i) . qdot_i],
+ *   qdot_i = sum_j (dq_i/dr_ij) . (e_j - e_i).
+ * Gradient sums are accumulated in FP64 and reduced in a fixed order.
+ * --------------------------------------------------------------------------- */
+typedef struct nep_batch {
+    int32_t n_configs;
+    int64_t n_atoms;             /* total atoms */
+    const double* xyz;           /* device double[3 * n_atoms] SoA, configurations
+                                    concatenated in order */
+    const int64_t* offsets;      /* host int64[n_configs + 1]: first atom of each
+                                    configuration; offsets[n_configs] = n_atoms */
+    const double* boxes;         /* host double[3 * n_configs]: periodic orthorhombic box
+                                    lengths, each >= rc_radial */
+    const int32_t* types;        /* device int32[n_atoms] (all 0 in this build) */
+} nep_batch;
+/* Each configuration holds 1..512 atoms. */
+
+/* Replaces the model parameters (same layout and length as nep_params.params;
+ * the descriptor scaler is kept).  Host memory. */
+int nep_set_params(nep_ctx* ctx, const double* params, int64_t n_params);
+
+/* Energies (device double[n_configs], eV) and forces (device double[3 * n_atoms]
+ * SoA, eV/A) of every configuration.  Synchronous on the stream. */
+int nep_batch_forward(nep_ctx* ctx, const nep_batch* batch, double* energies, double* forces,
+                      void* stream);
+
+/* Gradient (device double[n_params]) of a loss L(E, F) given its upstream
+ * derivatives dL/dE (device double[n_configs]) and dL/dF (device
+ * double[3 * n_atoms] SoA), evaluated at the context's current parameters. */
+int nep_batch_backward(nep_ctx* ctx, const nep_batch* batch, const double* dL_dE,
+                       const double* dL_dF, double* grad, void* stream);
+
+/* One persistent launch for forward, forces, the energy+force loss
+ *   L = w_energy * mean_s ((E_s - Et_s) / N_s)^2
+ *     + w_force  * mean over the 3 n_atoms components (F - Ft)^2
+ * (FP64 accumulation; host *loss) and its gradient (device double[n_params]).
+ * energies / forces (device) may be NULL. */
+int nep_batch_loss_grad(nep_ctx* ctx, const nep_batch* batch, const double* E_target,
+                        const double* F_target, double w_energy, double w_force, double* loss,
+                        double* grad, double* energies, double* forces, void* stream);
+
+/* Times the loss-gradient launch on this batch for each candidate of threads
+ * per CTA (atoms of one configuration processed side by side: 64, 128, 256)
+ * and CTAs per SM (1, 2, 4) and keeps the fastest for later batched calls. */
+int nep_batch_autotune(nep_ctx* ctx, const nep_batch* batch, const double* E_target,
+                       const double* F_target, void* stream, int* best_threads, int* best_per_sm);
+
 /* Force evaluation that allocates nothing (the paper has no counterpart; it is
  * a deployment convenience).  It is meant for callers that may not allocate
  * GPU memory at the point where they need forces: code embedded in a host

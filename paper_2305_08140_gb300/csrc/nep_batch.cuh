@@ -1,0 +1,611 @@
+// nep_batch.cuh -- many small periodic configurations in one persistent launch:
+// forward (energies, forces), backward (gradient of a loss with respect to
+// all model parameters, given dL/dE_s and dL/dF_i) and the fused
+// energy+force loss with its gradient.
+//
+// One CTA takes whole configurations from an atomic work queue.  A
+// configuration's positions, force accumulators and force residuals live in
+// shared memory; neighbour lists (all periodic images, self-images included)
+// and the per-atom backward state live in global scratch.
+//
+// Parameter gradient.  With e_i = dL/dF_i and eps_s = dL/dE_s, and
+// F_i = -dE/dr_i,
+//   dL/dtheta = sum_i d/dtheta [ eps U_i - a_i . qdot_i ],
+// where a_i = dU_i/dq_i and qdot_i = sum_j (dq_i/dd_ij) . (e_j - e_i) is the
+// derivative of atom i's descriptor along the residual field (the
+// force-loss term is minus the parameter derivative of E's directional
+// derivative along e).  Per atom this needs q, qdot (descriptor and its
+// tangent), the network's value, gradient and Hessian-vector product, and two
+// pair loops that contract the basis-coefficient derivatives.
+#pragma once
+
+#include "nep_device.cuh"
+
+namespace nepk {
+
+constexpr int BMAXA = 512;   // largest configuration handled by one CTA
+constexpr int NP = H * D + 2 * H + 1 + NR * KR + NA * KA;   // 1051 parameters
+constexpr int OFF_B0 = H * D, OFF_W1 = OFF_B0 + H, OFF_B1 = OFF_W1 + H;
+constexpr int OFF_CR = OFF_B1 + 1, OFF_CA = OFF_CR + NR * KR;
+
+// per-atom backward scratch layout (units of R)
+constexpr int BS_A = 0;                // A_nlm [NA][NLM]
+constexpr int BS_AD = NA * NLM;        // A-dot [NA][NLM]
+constexpr int BS_Q = 2 * NA * NLM;     // q [D]
+constexpr int BS_QD = BS_Q + D;        // q-dot [D]
+constexpr int BS_U = BS_QD + D;        // u_mu = w1 (eps s' - s'' h-dot) [H]
+constexpr int BS_V = BS_U + H;         // v_mu = w1 s' [H]
+constexpr int BS_GW1 = BS_V + H;       // eps t - s' h-dot [H]
+constexpr int BS_P = BS_GW1 + H;       // p = W^T u [D]
+constexpr int BS_AV = BS_P + D;        // a = W^T v [D]
+constexpr int BSTRIDE = BS_AV + D;
+
+enum { MODE_FORWARD = 0, MODE_BACKWARD = 1, MODE_LOSS = 2 };
+
+struct Batch {
+    int S;                     // configurations
+    int M;                     // neighbour slots per atom
+    long long ntot;            // atoms in the batch
+    const long long* off;      // [S + 1] first atom of each configuration
+    const int* order;          // [S] processing order (largest first)
+    const double* box;         // [S][3] periodic box lengths
+    const double* x;           // [3][ntot] positions
+    int* nbr;                  // [M][ntot] (local index << 5) | image code
+    int2* cnt;                 // [ntot] (angular, radial-only) counts
+    int* queue;                // work counter, zero before the launch
+    int* status;               // [3] status bits, max neighbour count
+    double* E;                 // [S] energies (forward, loss)
+    double* F;                 // [3][ntot] forces (forward, loss)
+    const double* dLdE;        // [S] (backward)
+    const double* dLdF;        // [3][ntot] (backward)
+    const double* Et;          // [S] target energies (loss)
+    const double* Ft;          // [3][ntot] target forces (loss)
+    double we, wf;             // loss weights
+    double* lpart;             // [S] loss of each configuration
+    double* gpart;             // [S][NP] gradient of each configuration
+    void* scr;                 // [ntot][BSTRIDE] backward scratch
+};
+
+// Sum of v over the CTA, in a fixed order; every thread gets the result.
+template <int BT>
+__device__ __forceinline__ double block_sum(double v, double* sh)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < BT / 32; ++w) s += sh[w];
+    return s;
+}
+
+// Neighbour list of local atom i: every atom j and image shift (-1, 0, 1 per
+// dimension; box >= r_c^R) with r < r_c^R, j = i only at a non-zero shift.
+template <typename R>
+__device__ __forceinline__ void batch_neighbors(const Model<R>& P, const Batch& b, long long a0,
+                                                int N, int i, const typename V4<R>::T* spos,
+                                                const double* L)
+{
+    using P4 = typename V4<R>::T;
+    const P4 pi = spos[i];
+    const R Lx = (R)L[0], Ly = (R)L[1], Lz = (R)L[2];
+    const int M = b.M;
+    const size_t col = (size_t)(a0 + i);
+    int na = 0, nro = 0, sa = 0, sro = 0;
+    for (int j = 0; j < N; ++j) {
+        const P4 pj = spos[j];
+        const R d0x = pj.x - pi.x, d0y = pj.y - pi.y, d0z = pj.z - pi.z;
+        for (int ox = -1; ox <= 1; ++ox) {
+            const R dx = d0x + R(ox) * Lx;
+            const R rx = dx * dx;
+            if (rx >= P.rcR2) continue;
+            for (int oy = -1; oy <= 1; ++oy) {
+                const R dy = d0y + R(oy) * Ly;
+                const R rxy = rx + dy * dy;
+                if (rxy >= P.rcR2) continue;
+                for (int oz = -1; oz <= 1; ++oz) {
+                    if (j == i && ox == 0 && oy == 0 && oz == 0) continue;
+                    const R dz = d0z + R(oz) * Lz;
+                    const R r2 = rxy + dz * dz;
+                    if (r2 >= P.rcR2) continue;
+                    const bool ang = r2 < P.rcA2;
+                    if (sa + sro < M) {
+                        const int ent = (j << 5) | ((ox + 1) * 9 + (oy + 1) * 3 + (oz + 1));
+                        if (ang) b.nbr[(size_t)(sa++) * b.ntot + col] = ent;
+                        else b.nbr[(size_t)(M - 1 - sro++) * b.ntot + col] = ent;
+                    }
+                    if (ang) ++na; else ++nro;
+                }
+            }
+        }
+    }
+    b.cnt[col] = make_int2(sa, sro);
+    if (na + nro > M) {
+        atomicOr(b.status, ST_OVERFLOW);
+        atomicMax(b.status + 1, na + nro);
+    }
+}
+
+template <typename R>
+struct PairGeom {
+    R dx, dy, dz, r, inv_r, ux, uy, uz;
+    int j;
+};
+
+template <typename R>
+__device__ __forceinline__ PairGeom<R> pair_geom(int ent, const typename V4<R>::T& pi,
+                                                 const typename V4<R>::T* spos,
+                                                 const typename V4<R>::T* s_off)
+{
+    PairGeom<R> g;
+    g.j = ent >> 5;
+    const typename V4<R>::T pj = spos[g.j];
+    const typename V4<R>::T o = s_off[ent & 31];
+    g.dx = pj.x - pi.x + o.x;
+    g.dy = pj.y - pi.y + o.y;
+    g.dz = pj.z - pi.z + o.z;
+    const R r2 = g.dx * g.dx + g.dy * g.dy + g.dz * g.dz;
+    g.inv_r = nepm::nep_rsqrt(r2);
+    g.r = r2 * g.inv_r;
+    g.ux = g.dx * g.inv_r;
+    g.uy = g.dy * g.inv_r;
+    g.uz = g.dz * g.inv_r;
+    return g;
+}
+
+__device__ __forceinline__ int slot_of(int s, int na, int nro, int M)
+{
+    return s < na ? s : M - nro + (s - na);
+}
+
+// Forward of local atom i: descriptor, network, pair forces scattered into
+// the shared accumulators; returns U_i (NEP + half ZBL).
+template <typename R>
+__device__ __forceinline__ double batch_atom_forward(const Model<R>& P, const Batch& b,
+                                                     long long a0, int i,
+                                                     const typename V4<R>::T* spos,
+                                                     const typename V4<R>::T* s_off,
+                                                     typename Acc<R>::T (*sF)[BMAXA], bool& bad)
+{
+    using A_ = Acc<R>;
+    const size_t col = (size_t)(a0 + i);
+    const int2 c2 = b.cnt[col];
+    const int na = c2.x, nro = c2.y, tot = na + nro, M = b.M;
+    const typename V4<R>::T pi = spos[i];
+    R qR[NR];
+    R A[NA][NLM];
+#pragma unroll
+    for (int n = 0; n < NR; ++n) qR[n] = R(0);
+#pragma unroll
+    for (int n = 0; n < NA; ++n)
+#pragma unroll
+        for (int lm = 0; lm < NLM; ++lm) A[n][lm] = R(0);
+    for (int s = 0; s < tot; ++s) {
+        const int ent = b.nbr[(size_t)slot_of(s, na, nro, M) * b.ntot + col];
+        const PairGeom<R> g = pair_geom<R>(ent, pi, spos, s_off);
+        desc_pair<R>(P, g.dx, g.dy, g.dz, g.r, g.inv_r, s < na, qR, A);
+    }
+    R bR[KR], B0;
+    const R U = network_adjoint<R>(P, qR, A, bR, B0);
+    double ez = 0.0;
+    typename A_::T fi[3] = {0, 0, 0};
+    bad |= !isfinite(U);
+    for (int s = 0; s < tot; ++s) {
+        const int ent = b.nbr[(size_t)slot_of(s, na, nro, M) * b.ntot + col];
+        const PairGeom<R> g = pair_geom<R>(ent, pi, spos, s_off);
+        R fx, fy, fz;
+        force_pair<R>(P, g.r, g.inv_r, g.ux, g.uy, g.uz, s < na, A, bR, B0, fx, fy, fz);
+        bad |= !isfinite(fx + fy + fz);
+        typename A_::T cx = A_::conv(fx), cy = A_::conv(fy), cz = A_::conv(fz);
+        if (s < na && g.r < P.zbl_r2) {
+            const double d64[3] = {(double)g.dx, (double)g.dy, (double)g.dz};
+            const double r64 = sqrt(d64[0] * d64[0] + d64[1] * d64[1] + d64[2] * d64[2]);
+            if (r64 < P.zbl_rr2) {
+                double Uz, dUz;
+                zbl_pair(r64, P.zbl_k, P.zbl_inv_a, P.zbl_r1, P.zbl_rr2, Uz, dUz);
+                ez += 0.5 * Uz;
+                const double c = 0.5 * dUz / r64;
+                cx += A_::convd(c * d64[0]);
+                cy += A_::convd(c * d64[1]);
+                cz += A_::convd(c * d64[2]);
+            }
+        }
+        fi[0] += cx; fi[1] += cy; fi[2] += cz;
+        A_::add(&sF[0][g.j], -cx);
+        A_::add(&sF[1][g.j], -cy);
+        A_::add(&sF[2][g.j], -cz);
+    }
+    A_::add(&sF[0][i], fi[0]);
+    A_::add(&sF[1][i], fi[1]);
+    A_::add(&sF[2][i], fi[2]);
+    return (double)U + ez;
+}
+
+// Backward, first pass for local atom i: descriptor q, its tangent q-dot along
+// the residual field, the network quantities; all into the atom's scratch row.
+template <typename R>
+__device__ __forceinline__ void batch_atom_tangent(const Model<R>& P, const Batch& b, long long a0,
+                                                   int i, double eps,
+                                                   const typename V4<R>::T* spos,
+                                                   const typename V4<R>::T* s_off,
+                                                   const R (*se)[BMAXA])
+{
+    const size_t col = (size_t)(a0 + i);
+    const int2 c2 = b.cnt[col];
+    const int na = c2.x, nro = c2.y, tot = na + nro, M = b.M;
+    const typename V4<R>::T pi = spos[i];
+    const R eix = se[0][i], eiy = se[1][i], eiz = se[2][i];
+    R* row = (R*)b.scr + col * BSTRIDE;
+    R q[D], qd[D];
+    // radial: q_n = sum g_n, q-dot_n = sum g'_n (u . dd)
+#pragma unroll
+    for (int n = 0; n < NR; ++n) { q[n] = R(0); qd[n] = R(0); }
+    for (int s = 0; s < tot; ++s) {
+        const int ent = b.nbr[(size_t)slot_of(s, na, nro, M) * b.ntot + col];
+        const PairGeom<R> g = pair_geom<R>(ent, pi, spos, s_off);
+        const R ud = g.ux * (se[0][g.j] - eix) + g.uy * (se[1][g.j] - eiy) + g.uz * (se[2][g.j] - eiz);
+        R T[KR], dT[KR], fc, dfc, dxdr;
+        nepm::cheb<KR, true>(g.r, P.inv_rcR, T, dT, fc, dfc, dxdr);
+#pragma unroll
+        for (int n = 0; n < NR; ++n) {
+            R a = P.CR[n], c = R(0);
+#pragma unroll
+            for (int kk = 0; kk < KR; ++kk) {
+                a += P.hR[n * KR + kk] * T[kk];
+                c += P.hR[n * KR + kk] * dT[kk];
+            }
+            q[n] += fc * a;
+            qd[n] += (dfc * a + fc * dxdr * c) * ud;
+        }
+    }
+    // angular, one radial channel at a time
+#pragma unroll 1
+    for (int n = 0; n < NA; ++n) {
+        R An[NLM], Ad[NLM];
+#pragma unroll
+        for (int lm = 0; lm < NLM; ++lm) { An[lm] = R(0); Ad[lm] = R(0); }
+        for (int s = 0; s < na; ++s) {
+            const int ent = b.nbr[(size_t)s * b.ntot + col];
+            const PairGeom<R> g = pair_geom<R>(ent, pi, spos, s_off);
+            const R ddx = se[0][g.j] - eix, ddy = se[1][g.j] - eiy, ddz = se[2][g.j] - eiz;
+            const R ud = g.ux * ddx + g.uy * ddy + g.uz * ddz;
+            R T[KA], dT[KA], fc, dfc, dxdr;
+            nepm::cheb<KA, true>(g.r, P.inv_rcA, T, dT, fc, dfc, dxdr);
+            R a = P.CA[n], c = R(0);
+#pragma unroll
+            for (int kk = 0; kk < KA; ++kk) {
+                a += P.hA[n * KA + kk] * T[kk];
+                c += P.hA[n * KA + kk] * dT[kk];
+            }
+            const R gn = fc * a, dgn = dfc * a + fc * dxdr * c;
+            R Y[NLM], Dd[NLM];
+            nepm::harmonics(g.ux, g.uy, g.uz, Y);
+            nepm::harmonics_dir(g.ux, g.uy, g.uz, ddx, ddy, ddz, Dd);
+#pragma unroll
+            for (int lm = 0; lm < NLM; ++lm) {
+                const int l = lm < 3 ? 1 : (lm < 8 ? 2 : (lm < 15 ? 3 : 4));
+                An[lm] += gn * Y[lm];
+                Ad[lm] += dgn * ud * Y[lm] + gn * g.inv_r * (Dd[lm] - R(l) * Y[lm] * ud);
+            }
+        }
+#pragma unroll
+        for (int lm = 0; lm < NLM; ++lm) {
+            row[BS_A + n * NLM + lm] = An[lm];
+            row[BS_AD + n * NLM + lm] = Ad[lm];
+        }
+#pragma unroll
+        for (int l = 1; l <= LM; ++l) {
+            const int lo = l * l - 1, hi = (l + 1) * (l + 1) - 1;
+            R qq = R(0), qqd = R(0);
+#pragma unroll
+            for (int lm = lo; lm < hi; ++lm) {
+                qq += An[lm] * An[lm];
+                qqd += R(2) * An[lm] * Ad[lm];
+            }
+            q[NR + (l - 1) * NA + n] = qq;
+            qd[NR + (l - 1) * NA + n] = qqd;
+        }
+        R G4[5];
+        q[NR + LM * NA + n] = nepm::fourbody(&An[3], G4);
+        R q4d = R(0);
+#pragma unroll
+        for (int t = 0; t < 5; ++t) q4d += G4[t] * Ad[3 + t];
+        qd[NR + LM * NA + n] = q4d;
+    }
+    // network: h = W q - b0, h-dot = W q-dot
+    const R e = (R)eps;
+#pragma unroll 1
+    for (int mu = 0; mu < H; ++mu) {
+        R h = -P.b0[mu], hd = R(0);
+#pragma unroll
+        for (int nu = 0; nu < D; ++nu) {
+            h += P.w0[mu * D + nu] * q[nu];
+            hd += P.w0[mu * D + nu] * qd[nu];
+        }
+        const R t = tanh(h);
+        const R s1 = R(1) - t * t;       // tanh'
+        const R s2 = R(-2) * t * s1;     // tanh''
+        row[BS_U + mu] = P.w1[mu] * (e * s1 - s2 * hd);
+        row[BS_V + mu] = P.w1[mu] * s1;
+        row[BS_GW1 + mu] = e * t - s1 * hd;
+    }
+#pragma unroll
+    for (int nu = 0; nu < D; ++nu) {
+        row[BS_Q + nu] = q[nu];
+        row[BS_QD + nu] = qd[nu];
+    }
+    // p = W^T u, a = W^T v
+#pragma unroll 1
+    for (int nu = 0; nu < D; ++nu) {
+        R pp = R(0), aa = R(0);
+#pragma unroll
+        for (int mu = 0; mu < H; ++mu) {
+            pp += P.w0[mu * D + nu] * row[BS_U + mu];
+            aa += P.w0[mu * D + nu] * row[BS_V + mu];
+        }
+        row[BS_P + nu] = pp;
+        row[BS_AV + nu] = aa;
+    }
+}
+
+// Radial basis-coefficient gradient contribution of local atom i:
+// g[n][k] += p_n f_k(r) - a_n f'_k(r) (u . dd).
+template <typename R>
+__device__ __forceinline__ void batch_atom_grad_cR(const Model<R>& P, const Batch& b, long long a0,
+                                                   int i, const typename V4<R>::T* spos,
+                                                   const typename V4<R>::T* s_off,
+                                                   const R (*se)[BMAXA], R (&gR)[NR * KR])
+{
+    const size_t col = (size_t)(a0 + i);
+    const int2 c2 = b.cnt[col];
+    const int na = c2.x, nro = c2.y, tot = na + nro, M = b.M;
+    const typename V4<R>::T pi = spos[i];
+    const R eix = se[0][i], eiy = se[1][i], eiz = se[2][i];
+    const R* row = (const R*)b.scr + col * BSTRIDE;
+    R p[NR], a[NR];
+#pragma unroll
+    for (int n = 0; n < NR; ++n) { p[n] = row[BS_P + n]; a[n] = row[BS_AV + n]; }
+    for (int s = 0; s < tot; ++s) {
+        const int ent = b.nbr[(size_t)slot_of(s, na, nro, M) * b.ntot + col];
+        const PairGeom<R> g = pair_geom<R>(ent, pi, spos, s_off);
+        const R ud = g.ux * (se[0][g.j] - eix) + g.uy * (se[1][g.j] - eiy) + g.uz * (se[2][g.j] - eiz);
+        R T[KR], dT[KR], fc, dfc, dxdr;
+        nepm::cheb<KR, true>(g.r, P.inv_rcR, T, dT, fc, dfc, dxdr);
+#pragma unroll
+        for (int kk = 0; kk < KR; ++kk) {
+            const R fk = R(0.5) * (T[kk] + R(1)) * fc;
+            const R dfk = R(0.5) * dT[kk] * dxdr * fc + R(0.5) * (T[kk] + R(1)) * dfc;
+#pragma unroll
+            for (int n = 0; n < NR; ++n) gR[n * KR + kk] += p[n] * fk - a[n] * dfk * ud;
+        }
+    }
+}
+
+// Angular basis-coefficient gradient of channel n for local atom i.
+template <typename R>
+__device__ __forceinline__ void batch_atom_grad_cA(const Model<R>& P, const Batch& b, long long a0,
+                                                   int i, int n, const typename V4<R>::T* spos,
+                                                   const typename V4<R>::T* s_off,
+                                                   const R (*se)[BMAXA], R (&gA)[KA])
+{
+    const size_t col = (size_t)(a0 + i);
+    const int na = b.cnt[col].x;
+    const typename V4<R>::T pi = spos[i];
+    const R eix = se[0][i], eiy = se[1][i], eiz = se[2][i];
+    const R* row = (const R*)b.scr + col * BSTRIDE;
+    // alpha = dPhi/dA, beta = dPhi/dA-dot for this channel
+    R al[NLM], be[NLM];
+    R An2[5], Ad2[5];
+#pragma unroll
+    for (int l = 1; l <= LM; ++l) {
+        const int lo = l * l - 1, hi = (l + 1) * (l + 1) - 1;
+        const R pl = row[BS_P + NR + (l - 1) * NA + n];
+        const R alv = row[BS_AV + NR + (l - 1) * NA + n];
+#pragma unroll
+        for (int lm = lo; lm < hi; ++lm) {
+            const R A_ = row[BS_A + n * NLM + lm], Ad_ = row[BS_AD + n * NLM + lm];
+            al[lm] = R(2) * pl * A_ - R(2) * alv * Ad_;
+            be[lm] = R(-2) * alv * A_;
+            if (l == 2) { An2[lm - 3] = A_; Ad2[lm - 3] = Ad_; }
+        }
+    }
+    {
+        const R p4 = row[BS_P + NR + LM * NA + n], a4 = row[BS_AV + NR + LM * NA + n];
+        R G4[5], Hv[5], T[6], Td[6], Sx[6];
+        nepm::fourbody(An2, G4);
+        nepm::fourbody_T(An2, T);
+        nepm::fourbody_T(Ad2, Td);
+        nepm::sym_anticomm(T, Td, Sx);
+        nepm::fourbody_map(Sx, Hv);
+#pragma unroll
+        for (int t = 0; t < 5; ++t) {
+            al[3 + t] += p4 * G4[t] - a4 * Hv[t];
+            be[3 + t] -= a4 * G4[t];
+        }
+    }
+    for (int s = 0; s < na; ++s) {
+        const int ent = b.nbr[(size_t)s * b.ntot + col];
+        const PairGeom<R> g = pair_geom<R>(ent, pi, spos, s_off);
+        const R ddx = se[0][g.j] - eix, ddy = se[1][g.j] - eiy, ddz = se[2][g.j] - eiz;
+        const R ud = g.ux * ddx + g.uy * ddy + g.uz * ddz;
+        R Y[NLM], Dd[NLM];
+        nepm::harmonics(g.ux, g.uy, g.uz, Y);
+        nepm::harmonics_dir(g.ux, g.uy, g.uz, ddx, ddy, ddz, Dd);
+        R S1 = R(0), S3 = R(0), SD = R(0), SL = R(0);
+#pragma unroll
+        for (int lm = 0; lm < NLM; ++lm) {
+            const int l = lm < 3 ? 1 : (lm < 8 ? 2 : (lm < 15 ? 3 : 4));
+            S1 += al[lm] * Y[lm];
+            S3 += be[lm] * Y[lm];
+            SD += be[lm] * Dd[lm];
+            SL += R(l) * be[lm] * Y[lm];
+        }
+        const R S2 = g.inv_r * (SD - ud * SL);
+        R T[KA], dT[KA], fc, dfc, dxdr;
+        nepm::cheb<KA, true>(g.r, P.inv_rcA, T, dT, fc, dfc, dxdr);
+#pragma unroll
+        for (int kk = 0; kk < KA; ++kk) {
+            const R fk = R(0.5) * (T[kk] + R(1)) * fc;
+            const R dfk = R(0.5) * dT[kk] * dxdr * fc + R(0.5) * (T[kk] + R(1)) * dfc;
+            gA[kk] += fk * (S1 + S2) + dfk * ud * S3;
+        }
+    }
+}
+
+// The persistent batched kernel.
+template <typename R, int MODE, int BT>
+__global__ void __launch_bounds__(BT) k_batch(const Model<R> P, const Batch b)
+{
+    using P4 = typename V4<R>::T;
+    using A_ = Acc<R>;
+    __shared__ P4 spos[BMAXA];
+    __shared__ typename A_::T sF[3][BMAXA];
+    __shared__ R se[3][BMAXA];
+    __shared__ P4 s_off[27];
+    __shared__ double sh[BT / 32];
+    __shared__ int s_cfg;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int t = atomicAdd(b.queue, 1);
+            s_cfg = t < b.S ? b.order[t] : -1;
+        }
+        __syncthreads();
+        const int cfg = s_cfg;
+        if (cfg < 0) break;
+        const long long a0 = b.off[cfg];
+        const int N = (int)(b.off[cfg + 1] - a0);
+        const double L[3] = {b.box[3 * cfg], b.box[3 * cfg + 1], b.box[3 * cfg + 2]};
+        for (int i = threadIdx.x; i < N; i += BT) {
+            P4 q;
+            double p[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                double v = b.x[(size_t)d * b.ntot + a0 + i];
+                if (!isfinite(v)) v = 0.0;
+                p[d] = v - L[d] * floor(v / L[d]);
+            }
+            q.x = (R)p[0]; q.y = (R)p[1]; q.z = (R)p[2]; q.w = R(0);
+            spos[i] = q;
+            sF[0][i] = 0; sF[1][i] = 0; sF[2][i] = 0;
+        }
+        if (threadIdx.x < 27) {
+            const int c = threadIdx.x;
+            P4 o;
+            o.x = (R)((c / 9 - 1) * L[0]);
+            o.y = (R)(((c / 3) % 3 - 1) * L[1]);
+            o.z = (R)((c % 3 - 1) * L[2]);
+            o.w = R(0);
+            s_off[c] = o;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < N; i += BT) batch_neighbors<R>(P, b, a0, N, i, spos, L);
+        double eps = 0.0;
+        if (MODE != MODE_BACKWARD) {
+            double esum = 0.0;
+            bool bad = false;
+            for (int i = threadIdx.x; i < N; i += BT)
+                esum += batch_atom_forward<R>(P, b, a0, i, spos, s_off, sF, bad);
+            if (bad) atomicOr(b.status, ST_NONFINITE);
+            const double E = block_sum<BT>(esum, sh);   // also orders the force scatter
+            if (threadIdx.x == 0) b.E[cfg] = E;
+            double f2 = 0.0;
+            for (int i = threadIdx.x; i < N; i += BT) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const size_t o = (size_t)d * b.ntot + a0 + i;
+                    const double f = A_::value(sF[d][i]);
+                    b.F[o] = f;
+                    if (MODE == MODE_LOSS) {
+                        const double r = f - b.Ft[o];
+                        f2 += r * r;
+                        se[d][i] = (R)(b.wf * 2.0 * r / (3.0 * (double)b.ntot));
+                    }
+                }
+            }
+            if (MODE == MODE_LOSS) {
+                const double F2 = block_sum<BT>(f2, sh);
+                const double dE = (E - b.Et[cfg]) / N;
+                eps = b.we * 2.0 * dE / ((double)N * b.S);
+                if (threadIdx.x == 0)
+                    b.lpart[cfg] = b.we * dE * dE / b.S + b.wf * F2 / (3.0 * (double)b.ntot);
+            }
+        } else {
+            for (int i = threadIdx.x; i < N; i += BT)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) se[d][i] = (R)b.dLdF[(size_t)d * b.ntot + a0 + i];
+            eps = b.dLdE[cfg];
+        }
+        __syncthreads();
+        if (MODE != MODE_FORWARD) {
+            double* gp = b.gpart + (size_t)cfg * NP;
+            for (int i = threadIdx.x; i < N; i += BT)
+                batch_atom_tangent<R>(P, b, a0, i, eps, spos, s_off, se);
+            __syncthreads();
+            // network weights: G_W = sum_i u (x) q - v (x) q-dot; b0, w1, b1
+            const R* scr = (const R*)b.scr;
+            for (int e = threadIdx.x; e < H * D + 2 * H + 1; e += BT) {
+                double acc = 0.0;
+                if (e < H * D) {
+                    const int mu = e / D, nu = e % D;
+                    for (int i = 0; i < N; ++i) {
+                        const R* row = scr + (size_t)(a0 + i) * BSTRIDE;
+                        acc += (double)row[BS_U + mu] * (double)row[BS_Q + nu] -
+                               (double)row[BS_V + mu] * (double)row[BS_QD + nu];
+                    }
+                    // W = w0 * s: chain to w0 through the scaler folded into P.w0
+                    acc *= (double)P.sc[nu];
+                } else if (e < OFF_W1) {
+                    for (int i = 0; i < N; ++i) acc -= (double)scr[(size_t)(a0 + i) * BSTRIDE + BS_U + (e - OFF_B0)];
+                } else if (e < OFF_B1) {
+                    for (int i = 0; i < N; ++i) acc += (double)scr[(size_t)(a0 + i) * BSTRIDE + BS_GW1 + (e - OFF_W1)];
+                } else {
+                    acc = -eps * N;
+                }
+                gp[e] = acc;
+            }
+            // radial basis coefficients
+            {
+                R gR[NR * KR];
+#pragma unroll
+                for (int t = 0; t < NR * KR; ++t) gR[t] = R(0);
+                for (int i = threadIdx.x; i < N; i += BT)
+                    batch_atom_grad_cR<R>(P, b, a0, i, spos, s_off, se, gR);
+#pragma unroll 1
+                for (int t = 0; t < NR * KR; ++t) {
+                    const double v = block_sum<BT>((double)gR[t], sh);
+                    if (threadIdx.x == 0) gp[OFF_CR + t] = v;
+                }
+            }
+            // angular basis coefficients, one channel at a time
+#pragma unroll 1
+            for (int n = 0; n < NA; ++n) {
+                R gA[KA];
+#pragma unroll
+                for (int t = 0; t < KA; ++t) gA[t] = R(0);
+                for (int i = threadIdx.x; i < N; i += BT)
+                    batch_atom_grad_cA<R>(P, b, a0, i, n, spos, s_off, se, gA);
+#pragma unroll 1
+                for (int t = 0; t < KA; ++t) {
+                    const double v = block_sum<BT>((double)gA[t], sh);
+                    if (threadIdx.x == 0) gp[OFF_CA + n * KA + t] = v;
+                }
+            }
+        }
+    }
+}
+
+// grad[p] = sum over configurations of gpart[c][p], in configuration order.
+static __global__ void k_batch_grad_reduce(const double* __restrict__ gpart, int S,
+                                    double* __restrict__ grad)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= NP) return;
+    double s = 0.0;
+    for (int c = 0; c < S; ++c) s += gpart[(size_t)c * NP + p];
+    grad[p] = s;
+}
+
+}  // namespace nepk

@@ -41,6 +41,7 @@ struct Model {
     R hR[NR * KR], CR[NR];   // c/2 and sum_k c/2 (radial)
     R hA[NA * KA], CA[NA];   // angular
     R rcR2, rcA2, inv_rcR, inv_rcA;
+    R sc[D];                 // s_nu (for the gradient with respect to w0)
     R zbl_r2;                // outer switch radius (pair test)
     double zbl_k;            // e^2/(4 pi eps0) Zi Zj (eV A)
     double zbl_inv_a;        // 1 / a (Eq. 4)
@@ -72,7 +73,7 @@ __device__ __forceinline__ int cell_coord(double x, int d, const Grid& g, double
     return c;
 }
 
-__global__ void k_bin_count(Grid g, const double* __restrict__ x, int* __restrict__ cell_of,
+static __global__ void k_bin_count(Grid g, const double* __restrict__ x, int* __restrict__ cell_of,
                             int* __restrict__ slot_of, int* __restrict__ count,
                             int* __restrict__ status)
 {
@@ -124,7 +125,7 @@ __device__ __forceinline__ int block_excl_scan(int v, int* sh, int& total)
     return before + s - v;
 }
 
-__global__ void __launch_bounds__(SCAN_T) k_scan_blocks(const int* __restrict__ in, int n,
+static __global__ void __launch_bounds__(SCAN_T) k_scan_blocks(const int* __restrict__ in, int n,
                                                         int* __restrict__ out,
                                                         int* __restrict__ block_sums)
 {
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_blocks(const int* __restrict__ 
 }
 
 // one block: exclusive scan of up to SCAN_B block sums; writes out[n] = total
-__global__ void __launch_bounds__(SCAN_T) k_scan_sums(int* __restrict__ sums, int nb,
+static __global__ void __launch_bounds__(SCAN_T) k_scan_sums(int* __restrict__ sums, int nb,
                                                       int* __restrict__ out, int n)
 {
     __shared__ int sh[32];
@@ -168,13 +169,13 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_sums(int* __restrict__ sums, in
     if (threadIdx.x == 0) out[n] = total;
 }
 
-__global__ void k_scan_add(int* __restrict__ out, int n, const int* __restrict__ sums)
+static __global__ void k_scan_add(int* __restrict__ out, int n, const int* __restrict__ sums)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] += sums[i / SCAN_B];
 }
 
-__global__ void k_bin_scatter(int n, const int* __restrict__ cell_of,
+static __global__ void k_bin_scatter(int n, const int* __restrict__ cell_of,
                               const int* __restrict__ slot_of, const int* __restrict__ start,
                               int* __restrict__ perm)
 {
@@ -375,6 +376,176 @@ __device__ __forceinline__ void fill_stencil(typename V4<R>::T* tab, const Grid&
 }
 
 // ----------------------------------------------------------------------------
+// Per-atom building blocks (inlined into the force kernels)
+// ----------------------------------------------------------------------------
+
+// Adds one neighbour (displacement d) to the descriptor sums of an atom: the
+// radial q_n and, for an angular neighbour, A_nlm = sum_j g_n Y_lm.
+template <typename R>
+__device__ __forceinline__ void desc_pair(const Model<R>& P, R dx, R dy, R dz, R r, R inv_r,
+                                          bool ang, R (&qR)[NR], R (&A)[NA][NLM])
+{
+    R T[KR], dT[KR], fc, dfc, dxdr;
+    nepm::cheb<KR, false>(r, P.inv_rcR, T, dT, fc, dfc, dxdr);
+#pragma unroll
+    for (int n = 0; n < NR; ++n) {
+        R acc = P.CR[n];
+#pragma unroll
+        for (int kk = 0; kk < KR; ++kk) acc += P.hR[n * KR + kk] * T[kk];
+        qR[n] += fc * acc;
+    }
+    if (ang) {
+        nepm::cheb<KA, false>(r, P.inv_rcA, T, dT, fc, dfc, dxdr);
+        R Y[NLM];
+        nepm::harmonics(dx * inv_r, dy * inv_r, dz * inv_r, Y);
+#pragma unroll
+        for (int n = 0; n < NA; ++n) {
+            R acc = P.CA[n];
+#pragma unroll
+            for (int kk = 0; kk < KA; ++kk) acc += P.hA[n * KA + kk] * T[kk];
+            const R gn = fc * acc;
+#pragma unroll
+            for (int lm = 0; lm < NLM; ++lm) A[n][lm] += gn * Y[lm];
+        }
+    }
+}
+
+// Network U(q) and its backward.  On return A holds dU/dA_nlm (4-body term
+// folded into l = 2), bR/B0 the radial adjoint contracted with the basis
+// coefficients: sum_n dU/dq_n g'_n(r) = df_c (B0 + sum_k bR_k T_k) + f_c x' sum_k bR_k T'_k.
+template <typename R>
+__device__ __forceinline__ R network_adjoint(const Model<R>& P, const R (&qR)[NR],
+                                             R (&A)[NA][NLM], R (&bR)[KR], R& B0)
+{
+    R h[H];
+#pragma unroll
+    for (int mu = 0; mu < H; ++mu) h[mu] = -P.b0[mu];
+#pragma unroll
+    for (int nu = 0; nu < NR; ++nu)
+#pragma unroll
+        for (int mu = 0; mu < H; ++mu) h[mu] += P.w0[mu * D + nu] * qR[nu];
+#pragma unroll
+    for (int l = 1; l <= LM; ++l) {
+        const int lo = l * l - 1, hi = (l + 1) * (l + 1) - 1;   // harmonic range
+#pragma unroll
+        for (int n = 0; n < NA; ++n) {
+            R q = R(0);
+#pragma unroll
+            for (int lm = lo; lm < hi; ++lm) q += A[n][lm] * A[n][lm];
+            const int nu = NR + (l - 1) * NA + n;
+#pragma unroll
+            for (int mu = 0; mu < H; ++mu) h[mu] += P.w0[mu * D + nu] * q;
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < NA; ++n) {
+        const R q4 = nepm::fourbody(&A[n][3], (R*)nullptr);
+        const int nu = NR + LM * NA + n;
+#pragma unroll
+        for (int mu = 0; mu < H; ++mu) h[mu] += P.w0[mu * D + nu] * q4;
+    }
+    R U = -P.b1;
+#pragma unroll
+    for (int mu = 0; mu < H; ++mu) {
+        const R t = tanh(h[mu]);
+        U += P.w1[mu] * t;
+        h[mu] = P.w1[mu] * (R(1) - t * t);   // dU/dh_mu
+    }
+    B0 = R(0);
+#pragma unroll
+    for (int kk = 0; kk < KR; ++kk) bR[kk] = R(0);
+#pragma unroll
+    for (int nu = 0; nu < NR; ++nu) {
+        R a = R(0);
+#pragma unroll
+        for (int mu = 0; mu < H; ++mu) a += h[mu] * P.w0[mu * D + nu];
+        B0 += a * P.CR[nu];
+#pragma unroll
+        for (int kk = 0; kk < KR; ++kk) bR[kk] += a * P.hR[nu * KR + kk];
+    }
+#pragma unroll
+    for (int n = 0; n < NA; ++n) {
+        R a4 = R(0), a2 = R(0);
+#pragma unroll
+        for (int mu = 0; mu < H; ++mu) {
+            a4 += h[mu] * P.w0[mu * D + NR + LM * NA + n];
+            a2 += h[mu] * P.w0[mu * D + NR + NA + n];
+        }
+        R dq4[5];
+        nepm::fourbody(&A[n][3], dq4);
+#pragma unroll
+        for (int t = 0; t < 5; ++t) A[n][3 + t] = R(2) * a2 * A[n][3 + t] + a4 * dq4[t];
+    }
+#pragma unroll
+    for (int l = 1; l <= LM; ++l) {
+        if (l == 2) continue;
+        const int lo = l * l - 1, hi = (l + 1) * (l + 1) - 1;
+#pragma unroll
+        for (int n = 0; n < NA; ++n) {
+            R a = R(0);
+#pragma unroll
+            for (int mu = 0; mu < H; ++mu) a += h[mu] * P.w0[mu * D + NR + (l - 1) * NA + n];
+#pragma unroll
+            for (int lm = lo; lm < hi; ++lm) A[n][lm] *= R(2) * a;
+        }
+    }
+    return U;
+}
+
+// dU_i/dd_ij for one neighbour from the atom's adjoint (NEP part only).
+template <typename R>
+__device__ __forceinline__ void force_pair(const Model<R>& P, R r, R inv_r, R ux, R uy, R uz,
+                                           bool ang, const R (&Ab)[NA][NLM], const R (&bR)[KR],
+                                           R B0, R& fx, R& fy, R& fz)
+{
+    R T[KR], dT[KR], fc, dfc, dxdr;
+    nepm::cheb<KR, true>(r, P.inv_rcR, T, dT, fc, dfc, dxdr);
+    R s1 = B0, s2 = R(0);
+#pragma unroll
+    for (int kk = 0; kk < KR; ++kk) {
+        s1 += bR[kk] * T[kk];
+        s2 += bR[kk] * dT[kk];
+    }
+    R fs = dfc * s1 + fc * dxdr * s2;   // coefficient of u
+    R vx = R(0), vy = R(0), vz = R(0);  // coefficient of 1/r
+    if (ang) {
+        nepm::cheb<KA, true>(r, P.inv_rcA, T, dT, fc, dfc, dxdr);
+        R gn[NA], dgn[NA];
+#pragma unroll
+        for (int n = 0; n < NA; ++n) {
+            R a = P.CA[n], b = R(0);
+#pragma unroll
+            for (int kk = 0; kk < KA; ++kk) {
+                a += P.hA[n * KA + kk] * T[kk];
+                b += P.hA[n * KA + kk] * dT[kk];
+            }
+            gn[n] = fc * a;
+            dgn[n] = dfc * a + fc * dxdr * b;
+        }
+        R Y[NLM], G[NLM];
+        nepm::harmonics(ux, uy, uz, Y);
+        R sang = R(0);
+#pragma unroll
+        for (int lm = 0; lm < NLM; ++lm) {
+            const int l = lm < 3 ? 1 : (lm < 8 ? 2 : (lm < 15 ? 3 : 4));
+            R gsum = R(0), dsum = R(0);
+#pragma unroll
+            for (int n = 0; n < NA; ++n) {
+                gsum += Ab[n][lm] * gn[n];
+                dsum += Ab[n][lm] * dgn[n];
+            }
+            G[lm] = gsum;
+            sang += (dsum - R(l) * inv_r * gsum) * Y[lm];
+        }
+        fs += sang;
+        nepm::harmonics_grad_dot(ux, uy, uz, G, vx, vy, vz);
+    }
+    fx = fs * ux + vx * inv_r;
+    fy = fs * uy + vy * inv_r;
+    fz = fs * uz + vz * inv_r;
+}
+
+// ----------------------------------------------------------------------------
 // The force kernel: one thread per atom (cell order), 128 atoms per block.
 // Descriptor sums -> network and its backward -> pair forces scattered to
 // both atoms of each pair -> per-tile energy and virial.
@@ -439,106 +610,12 @@ __global__ void __launch_bounds__(TILE) k_nep(const Model<R> P, const Grid g,
             const R r2 = dx * dx + dy * dy + dz * dz;
             const R inv_r = nepm::nep_rsqrt(r2);
             const R r = r2 * inv_r;
-            R T[KR], dT[KR], fc, dfc, dxdr;
-            nepm::cheb<KR, false>(r, P.inv_rcR, T, dT, fc, dfc, dxdr);
-#pragma unroll
-            for (int n = 0; n < NR; ++n) {
-                R acc = P.CR[n];
-#pragma unroll
-                for (int kk = 0; kk < KR; ++kk) acc += P.hR[n * KR + kk] * T[kk];
-                qR[n] += fc * acc;
-            }
-            if (s < na) {
-                nepm::cheb<KA, false>(r, P.inv_rcA, T, dT, fc, dfc, dxdr);
-                R Y[NLM];
-                nepm::harmonics(dx * inv_r, dy * inv_r, dz * inv_r, Y);
-#pragma unroll
-                for (int n = 0; n < NA; ++n) {
-                    R acc = P.CA[n];
-#pragma unroll
-                    for (int kk = 0; kk < KA; ++kk) acc += P.hA[n * KA + kk] * T[kk];
-                    const R gn = fc * acc;
-#pragma unroll
-                    for (int lm = 0; lm < NLM; ++lm) A[n][lm] += gn * Y[lm];
-                }
-            }
+            desc_pair<R>(P, dx, dy, dz, r, inv_r, s < na, qR, A);
         }
 
-        // ---------------- network (descriptor consumed on the fly) -----------
-        R h[H];
-#pragma unroll
-        for (int mu = 0; mu < H; ++mu) h[mu] = -P.b0[mu];
-#pragma unroll
-        for (int nu = 0; nu < NR; ++nu)
-#pragma unroll
-            for (int mu = 0; mu < H; ++mu) h[mu] += P.w0[mu * D + nu] * qR[nu];
-#pragma unroll
-        for (int l = 1; l <= LM; ++l) {
-            const int lo = l * l - 1, hi = (l + 1) * (l + 1) - 1;   // harmonic range
-#pragma unroll
-            for (int n = 0; n < NA; ++n) {
-                R q = R(0);
-#pragma unroll
-                for (int lm = lo; lm < hi; ++lm) q += A[n][lm] * A[n][lm];
-                const int nu = NR + (l - 1) * NA + n;
-#pragma unroll
-                for (int mu = 0; mu < H; ++mu) h[mu] += P.w0[mu * D + nu] * q;
-            }
-        }
-#pragma unroll
-        for (int n = 0; n < NA; ++n) {
-            const R q4 = nepm::fourbody(&A[n][3], (R*)nullptr);
-            const int nu = NR + LM * NA + n;
-#pragma unroll
-            for (int mu = 0; mu < H; ++mu) h[mu] += P.w0[mu * D + nu] * q4;
-        }
-        R U = -P.b1;
-#pragma unroll
-        for (int mu = 0; mu < H; ++mu) {
-            const R t = tanh(h[mu]);
-            U += P.w1[mu] * t;
-            h[mu] = P.w1[mu] * (R(1) - t * t);   // dU/dh_mu
-        }
-
-        // ---------------- adjoint: dU/dq -> radial coefficients, dU/dA -------
-        R bR[KR], B0 = R(0);
-#pragma unroll
-        for (int kk = 0; kk < KR; ++kk) bR[kk] = R(0);
-#pragma unroll
-        for (int nu = 0; nu < NR; ++nu) {
-            R a = R(0);
-#pragma unroll
-            for (int mu = 0; mu < H; ++mu) a += h[mu] * P.w0[mu * D + nu];
-            B0 += a * P.CR[nu];
-#pragma unroll
-            for (int kk = 0; kk < KR; ++kk) bR[kk] += a * P.hR[nu * KR + kk];
-        }
-#pragma unroll
-        for (int n = 0; n < NA; ++n) {
-            R a4 = R(0), a2 = R(0);
-#pragma unroll
-            for (int mu = 0; mu < H; ++mu) {
-                a4 += h[mu] * P.w0[mu * D + NR + LM * NA + n];
-                a2 += h[mu] * P.w0[mu * D + NR + NA + n];
-            }
-            R dq4[5];
-            nepm::fourbody(&A[n][3], dq4);
-#pragma unroll
-            for (int t = 0; t < 5; ++t) A[n][3 + t] = R(2) * a2 * A[n][3 + t] + a4 * dq4[t];
-        }
-#pragma unroll
-        for (int l = 1; l <= LM; ++l) {
-            if (l == 2) continue;
-            const int lo = l * l - 1, hi = (l + 1) * (l + 1) - 1;
-#pragma unroll
-            for (int n = 0; n < NA; ++n) {
-                R a = R(0);
-#pragma unroll
-                for (int mu = 0; mu < H; ++mu) a += h[mu] * P.w0[mu * D + NR + (l - 1) * NA + n];
-#pragma unroll
-                for (int lm = lo; lm < hi; ++lm) A[n][lm] *= R(2) * a;
-            }
-        }
+        // ---------------- network and its backward ---------------------------
+        R bR[KR], B0;
+        const R U = network_adjoint<R>(P, qR, A, bR, B0);
 
         // ---------------- pair forces --------------------------------------
         typename A_::T fi[3] = {0, 0, 0};
@@ -568,52 +645,8 @@ __global__ void __launch_bounds__(TILE) k_nep(const Model<R> P, const Grid g,
             const R inv_r = nepm::nep_rsqrt(r2);
             const R r = r2 * inv_r;
             const R ux = dx * inv_r, uy = dy * inv_r, uz = dz * inv_r;
-            R T[KR], dT[KR], fc, dfc, dxdr;
-            // radial: sum_n dU/dq_n g'_n(r)
-            nepm::cheb<KR, true>(r, P.inv_rcR, T, dT, fc, dfc, dxdr);
-            R s1 = B0, s2 = R(0);
-#pragma unroll
-            for (int kk = 0; kk < KR; ++kk) {
-                s1 += bR[kk] * T[kk];
-                s2 += bR[kk] * dT[kk];
-            }
-            R fs = dfc * s1 + fc * dxdr * s2;   // coefficient of u
-            R vx = R(0), vy = R(0), vz = R(0);  // coefficient of 1/r
-            if (s < na) {
-                nepm::cheb<KA, true>(r, P.inv_rcA, T, dT, fc, dfc, dxdr);
-                R gn[NA], dgn[NA];
-#pragma unroll
-                for (int n = 0; n < NA; ++n) {
-                    R a = P.CA[n], b = R(0);
-#pragma unroll
-                    for (int kk = 0; kk < KA; ++kk) {
-                        a += P.hA[n * KA + kk] * T[kk];
-                        b += P.hA[n * KA + kk] * dT[kk];
-                    }
-                    gn[n] = fc * a;
-                    dgn[n] = dfc * a + fc * dxdr * b;
-                }
-                R Y[NLM], G[NLM];
-                nepm::harmonics(ux, uy, uz, Y);
-                R sang = R(0);
-#pragma unroll
-                for (int lm = 0; lm < NLM; ++lm) {
-                    const int l = lm < 3 ? 1 : (lm < 8 ? 2 : (lm < 15 ? 3 : 4));
-                    R gsum = R(0), dsum = R(0);
-#pragma unroll
-                    for (int n = 0; n < NA; ++n) {
-                        gsum += A[n][lm] * gn[n];
-                        dsum += A[n][lm] * dgn[n];
-                    }
-                    G[lm] = gsum;
-                    sang += (dsum - R(l) * inv_r * gsum) * Y[lm];
-                }
-                fs += sang;
-                nepm::harmonics_grad_dot(ux, uy, uz, G, vx, vy, vz);
-            }
-            const R fx = fs * ux + vx * inv_r;
-            const R fy = fs * uy + vy * inv_r;
-            const R fz = fs * uz + vz * inv_r;
+            R fx, fy, fz;
+            force_pair<R>(P, r, inv_r, ux, uy, uz, s < na, A, bR, B0, fx, fy, fz);
             bad |= !isfinite(fx + fy + fz);
             typename A_::T cx = A_::conv(fx), cy = A_::conv(fy), cz = A_::conv(fz);
             // ZBL pair term (Eq. 1-4), FP64 from the FP64 positions
@@ -709,7 +742,7 @@ __global__ void k_forces_out(int n, int ld, const int* __restrict__ perm,
 // Stage 1 of the energy/virial sum: block b adds the tiles
 // [b * chunk, (b + 1) * chunk) in a fixed order; out[b * NPART + c].
 constexpr int RED1_MAX = 512;
-__global__ void __launch_bounds__(256) k_reduce_stage1(const double* __restrict__ partials,
+static __global__ void __launch_bounds__(256) k_reduce_stage1(const double* __restrict__ partials,
                                                        int ntiles, int chunk,
                                                        double* __restrict__ out)
 {
@@ -731,7 +764,7 @@ __global__ void __launch_bounds__(256) k_reduce_stage1(const double* __restrict_
 }
 
 // One block: sums the per-tile partials in a fixed order into out[0..NPART).
-__global__ void __launch_bounds__(256) k_reduce_partials(const double* __restrict__ partials,
+static __global__ void __launch_bounds__(256) k_reduce_partials(const double* __restrict__ partials,
                                                          int ntiles, double* __restrict__ out)
 {
     __shared__ double sh[256];
@@ -759,7 +792,7 @@ constexpr int TH_DT = 0, TH_TIME = 1, TH_STEP = 2, TH_KE = 3, TH_VMAX = 4, TH_DT
               TH_DMAX = 6, TH_DTLAST = 7, TH_N = 8;
 
 // v += dt/2 F/m ; x += dt v ; wrap periodic coordinates into [0, L)
-__global__ void k_kick_drift(Grid g, double acc, const double* __restrict__ thermo,
+static __global__ void k_kick_drift(Grid g, double acc, const double* __restrict__ thermo,
                              double* __restrict__ x, double* __restrict__ v,
                              const double* __restrict__ F)
 {
@@ -778,7 +811,7 @@ __global__ void k_kick_drift(Grid g, double acc, const double* __restrict__ ther
 }
 
 // v += dt/2 F/m and per-block (sum v^2, max |v|)
-__global__ void __launch_bounds__(256) k_kick_thermo(int n, double acc,
+static __global__ void __launch_bounds__(256) k_kick_thermo(int n, double acc,
                                                      const double* __restrict__ thermo,
                                                      double* __restrict__ v,
                                                      const double* __restrict__ F,
@@ -814,7 +847,7 @@ __global__ void __launch_bounds__(256) k_kick_thermo(int n, double acc,
 
 // One block: KE, max|v|, time bookkeeping and the next step's dt
 // (dt = min(dt_max, d_max / max|v|) when d_max > 0).
-__global__ void __launch_bounds__(256) k_thermo_step(const double* __restrict__ part, int nb,
+static __global__ void __launch_bounds__(256) k_thermo_step(const double* __restrict__ part, int nb,
                                                      double mass, double ev_amu,
                                                      double* __restrict__ thermo,
                                                      int advance)

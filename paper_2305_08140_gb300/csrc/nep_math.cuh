@@ -208,6 +208,99 @@ NEP_HD void harmonics_grad_dot(R x, R y, R z, const R* G, R& vx, R& vy, R& vz)
           s70_4 * (c3 * G[20] + s3m * G[21]);
 }
 
+// D[lm] = grad R_lm(u) . w, the directional derivatives of the homogeneous
+// polynomials above along w (each row is the gradient of harmonics_grad_dot
+// dotted with w).
+template <typename R>
+NEP_HD void harmonics_dir(R x, R y, R z, R wx, R wy, R wz, R* Dd)
+{
+    const R s3 = R(1.7320508075688772), s6_4 = R(0.6123724356957945),
+            s15 = R(3.872983346207417), s15_2 = R(1.9364916731037085),
+            s10_4 = R(0.7905694150420949), s5 = R(2.23606797749979),
+            s5_2 = R(1.118033988749895), s70_4 = R(2.091650066335189),
+            s35_2 = R(2.958039891549808);
+    R x2 = x * x, y2 = y * y, z2 = z * z, rho2 = x2 + y2;
+    R xy = x * y, xz = x * z, yz = y * z, xmy = x2 - y2, xyz = xy * z;
+    R c3 = x * (x2 - R(3) * y2), s3m = y * (R(3) * x2 - y2);
+    Dd[0] = wz; Dd[1] = wx; Dd[2] = wy;
+    Dd[3] = -x * wx - y * wy + R(2) * z * wz;
+    Dd[4] = s3 * (z * wx + x * wz);
+    Dd[5] = s3 * (z * wy + y * wz);
+    Dd[6] = s3 * (x * wx - y * wy);
+    Dd[7] = s3 * (y * wx + x * wy);
+    Dd[8] = R(-3) * xz * wx - R(3) * yz * wy + (R(3) * z2 - R(1.5) * rho2) * wz;
+    Dd[9] = s6_4 * ((R(4) * z2 - R(3) * x2 - y2) * wx - R(2) * xy * wy + R(8) * xz * wz);
+    Dd[10] = s6_4 * (R(-2) * xy * wx + (R(4) * z2 - x2 - R(3) * y2) * wy + R(8) * yz * wz);
+    Dd[11] = s15 * (xz * wx - yz * wy) + s15_2 * xmy * wz;
+    Dd[12] = s15 * (yz * wx + xz * wy + xy * wz);
+    Dd[13] = s10_4 * (R(3) * xmy * wx - R(6) * xy * wy);
+    Dd[14] = s10_4 * (R(6) * xy * wx + R(3) * xmy * wy);
+    R t15 = R(1.5) * rho2 - R(6) * z2;
+    Dd[15] = x * t15 * wx + y * t15 * wy + (R(4) * z2 * z - R(6) * z * rho2) * wz;
+    Dd[16] = s10_4 * (z * (R(4) * z2 - R(9) * x2 - R(3) * y2) * wx - R(6) * xyz * wy +
+                      R(3) * x * (R(4) * z2 - rho2) * wz);
+    Dd[17] = s10_4 * (R(-6) * xyz * wx + z * (R(4) * z2 - R(3) * x2 - R(9) * y2) * wy +
+                      R(3) * y * (R(4) * z2 - rho2) * wz);
+    Dd[18] = s5 * (x * (R(3) * z2 - x2) * wx - y * (R(3) * z2 - y2) * wy + R(3) * z * xmy * wz);
+    Dd[19] = s5_2 * (y * (R(6) * z2 - R(3) * x2 - y2) * wx + x * (R(6) * z2 - x2 - R(3) * y2) * wy) +
+             R(6) * s5 * xyz * wz;
+    Dd[20] = s70_4 * (R(3) * z * xmy * wx - R(6) * xyz * wy + c3 * wz);
+    Dd[21] = s70_4 * (R(6) * xyz * wx + R(3) * z * xmy * wy + s3m * wz);
+    Dd[22] = s35_2 * (c3 * wx - s3m * wy);
+    Dd[23] = s35_2 * (s3m * wx + c3 * wy);
+}
+
+// The symmetric traceless T of one channel from its l = 2 coefficients
+// (order xx, yy, zz, xy, xz, yz); see fourbody() below.
+template <typename R>
+NEP_HD void fourbody_T(const R* A2, R* T)
+{
+    const R i3 = R(0.5773502691896258);
+    T[0] = -A2[0] * R(1.0 / 3.0) + A2[3] * i3;
+    T[1] = -A2[0] * R(1.0 / 3.0) - A2[3] * i3;
+    T[2] = A2[0] * R(2.0 / 3.0);
+    T[3] = A2[4] * i3;
+    T[4] = A2[1] * i3;
+    T[5] = A2[2] * i3;
+}
+
+// out_m = 3 <dT/dA_m, S> for a symmetric S (xx, yy, zz, xy, xz, yz): with
+// S = T^2 this is d tr(T^3)/dA; with S = T T' + T' T it is the Hessian of
+// tr(T^3) applied to the direction A' (T' = T(A')).
+template <typename R>
+NEP_HD void fourbody_map(const R* S, R* out)
+{
+    const R i3 = R(0.5773502691896258);
+    out[0] = -S[0] - S[1] + R(2) * S[2];
+    out[1] = R(6) * S[4] * i3;
+    out[2] = R(6) * S[5] * i3;
+    out[3] = R(3) * (S[0] - S[1]) * i3;
+    out[4] = R(6) * S[3] * i3;
+}
+
+// Symmetric product P = X Y + Y X of two symmetric matrices (same order).
+template <typename R>
+NEP_HD void sym_anticomm(const R* X, const R* Yv, R* P)
+{
+    // full entries: X = [[a d e][d b f][e f c]]
+    R xy_xx = X[0] * Yv[0] + X[3] * Yv[3] + X[4] * Yv[4];
+    R xy_yy = X[3] * Yv[3] + X[1] * Yv[1] + X[5] * Yv[5];
+    R xy_zz = X[4] * Yv[4] + X[5] * Yv[5] + X[2] * Yv[2];
+    R xy_xy = X[0] * Yv[3] + X[3] * Yv[1] + X[4] * Yv[5];   // (XY)_xy
+    R xy_yx = X[3] * Yv[0] + X[1] * Yv[3] + X[5] * Yv[4];   // (XY)_yx
+    R xy_xz = X[0] * Yv[4] + X[3] * Yv[5] + X[4] * Yv[2];
+    R xy_zx = X[4] * Yv[0] + X[5] * Yv[3] + X[2] * Yv[4];
+    R xy_yz = X[3] * Yv[4] + X[1] * Yv[5] + X[5] * Yv[2];
+    R xy_zy = X[4] * Yv[3] + X[5] * Yv[1] + X[2] * Yv[5];
+    // (XY + YX) = XY + (XY)^T for symmetric X, Y
+    P[0] = R(2) * xy_xx;
+    P[1] = R(2) * xy_yy;
+    P[2] = R(2) * xy_zz;
+    P[3] = xy_xy + xy_yx;
+    P[4] = xy_xz + xy_zx;
+    P[5] = xy_yz + xy_zy;
+}
+
 // 4-body invariant of one radial channel from its l = 2 coefficients
 // A2[0..4] (harmonic order R20, R21c, R21s, R22c, R22s):
 // T = sum_j g_j (u u^T - I/3) is the linear image

@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <new>
@@ -14,7 +15,8 @@
 #include <vector>
 
 #include "../../include/nepzbl.h"
-#include "nep_device.cuh"
+#include "nep_batch.cuh"
+#include "nep_batch_launch.h"
 
 using namespace nepk;
 
@@ -87,6 +89,25 @@ struct nep_ctx {
     bool capturing = false;
     int capture_kernels = 0;
     int capture_timed = 0;
+
+    // batched configurations (small periodic boxes)
+    long long b_ntot_cap = 0;
+    int b_S_cap = 0;
+    int b_M = 0;
+    int* b_nbr = nullptr;
+    int2* b_cnt = nullptr;
+    void* b_scr = nullptr;
+    double* b_gpart = nullptr;
+    double* b_lpart = nullptr;
+    double* b_E = nullptr;
+    double* b_F = nullptr;
+    long long* b_off = nullptr;
+    int* b_order = nullptr;
+    double* b_box = nullptr;
+    int* b_queue = nullptr;
+    int b_bt = 128;          // threads per CTA
+    int b_per_sm = 0;        // CTAs per SM (0: as many as fit)
+    int b_tuned = 0;
 };
 
 static int fail(nep_ctx* c, int code, const char* fmt, ...)
@@ -385,6 +406,7 @@ static void build_model(Model<R>& P, const nep_params* p)
         }
         P.CA[n] = (R)s;
     }
+    for (int nu = 0; nu < Dd; ++nu) P.sc[nu] = (R)p->q_scaler[nu];
     P.rcR2 = (R)(p->rc_radial * p->rc_radial);
     P.rcA2 = (R)(p->rc_angular * p->rc_angular);
     P.inv_rcR = (R)(1.0 / p->rc_radial);
@@ -462,11 +484,22 @@ int nep_init(const nep_params* p, int precision, nep_ctx** out)
     return NEP_OK;
 }
 
+static void free_batch(nep_ctx* ctx)
+{
+    free_dev(ctx->b_nbr); free_dev(ctx->b_cnt); free_dev(ctx->b_scr); free_dev(ctx->b_gpart);
+    free_dev(ctx->b_lpart); free_dev(ctx->b_E); free_dev(ctx->b_F); free_dev(ctx->b_off);
+    free_dev(ctx->b_order); free_dev(ctx->b_box); free_dev(ctx->b_queue);
+    ctx->b_ntot_cap = 0;
+    ctx->b_S_cap = 0;
+    ctx->b_M = 0;
+}
+
 void nep_free(nep_ctx* ctx)
 {
     if (!ctx) return;
     cudaDeviceSynchronize();
     free_scratch(ctx);
+    free_batch(ctx);
     free_dev(ctx->count); free_dev(ctx->start); free_dev(ctx->scan_sums);
     free_dev(ctx->thermo); free_dev(ctx->thermo_backup); free_dev(ctx->result);
     free_dev(ctx->status); free_dev(ctx->pairs);
@@ -751,6 +784,271 @@ int md_step(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
         for (int t = 0; t < 9; ++t) st->virial[t] = ctx->h_result[1 + t];
     }
     return NEP_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================
+// Batches of small periodic configurations
+// ============================================================================
+
+static int batch_buffers(nep_ctx* ctx, long long ntot, int S, int M)
+{
+    if (ntot <= ctx->b_ntot_cap && S <= ctx->b_S_cap && M <= ctx->b_M && ctx->b_nbr) return NEP_OK;
+    cudaDeviceSynchronize();
+    const long long nc = std::max(ntot, ctx->b_ntot_cap);
+    const int Sc = std::max(S, ctx->b_S_cap);
+    const int Mc = std::max(M, ctx->b_M);
+    free_batch(ctx);
+    const size_t rsz = ctx->precision == NEP_FP32 ? sizeof(float) : sizeof(double);
+    CK(cudaMalloc(&ctx->b_nbr, sizeof(int) * (size_t)nc * Mc));
+    CK(cudaMalloc(&ctx->b_cnt, sizeof(int2) * (size_t)nc));
+    CK(cudaMalloc(&ctx->b_scr, rsz * (size_t)nc * BSTRIDE));
+    CK(cudaMalloc(&ctx->b_F, sizeof(double) * 3 * (size_t)nc));
+    CK(cudaMalloc(&ctx->b_gpart, sizeof(double) * (size_t)Sc * NP));
+    CK(cudaMalloc(&ctx->b_lpart, sizeof(double) * (size_t)Sc));
+    CK(cudaMalloc(&ctx->b_E, sizeof(double) * (size_t)Sc));
+    CK(cudaMalloc(&ctx->b_off, sizeof(long long) * (size_t)(Sc + 1)));
+    CK(cudaMalloc(&ctx->b_order, sizeof(int) * (size_t)Sc));
+    CK(cudaMalloc(&ctx->b_box, sizeof(double) * 3 * (size_t)Sc));
+    CK(cudaMalloc(&ctx->b_queue, sizeof(int)));
+    ctx->b_ntot_cap = nc;
+    ctx->b_S_cap = Sc;
+    ctx->b_M = Mc;
+    return NEP_OK;
+}
+
+// Validates a batch, uploads its offsets/boxes/order and fills b.
+static int batch_prepare(nep_ctx* ctx, const nep_batch* bt, cudaStream_t s, Batch& b)
+{
+    if (!bt || bt->n_configs < 1 || !bt->offsets || !bt->boxes)
+        return fail(ctx, NEP_ERR_INVALID_ARG, "batch needs n_configs >= 1, offsets and boxes");
+    const int S = bt->n_configs;
+    if (bt->offsets[0] != 0 || bt->offsets[S] != bt->n_atoms || bt->n_atoms >= (1LL << 31))
+        return fail(ctx, NEP_ERR_INVALID_ARG, "offsets must start at 0 and end at n_atoms");
+    std::vector<int> order(S);
+    for (int c = 0; c < S; ++c) {
+        const long long n = bt->offsets[c + 1] - bt->offsets[c];
+        if (n < 1 || n > BMAXA)
+            return fail(ctx, NEP_ERR_INVALID_ARG, "configuration %d has %lld atoms (1..%d)", c, n,
+                        BMAXA);
+        for (int a = 0; a < 3; ++a) {
+            const double L = bt->boxes[3 * c + a];
+            if (!(L >= ctx->rcR) || !isfinite(L))
+                return fail(ctx, NEP_ERR_BOX, "configuration %d: box length %g < r_c^R", c, L);
+        }
+        order[c] = c;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        return bt->offsets[a + 1] - bt->offsets[a] > bt->offsets[c + 1] - bt->offsets[c];
+    });
+    int rc;
+    if ((rc = check_device_ptr(ctx, bt->xyz, "batch xyz"))) return rc;
+    int M = ctx->b_M > 0 ? ctx->b_M : 112;
+    if ((rc = batch_buffers(ctx, bt->n_atoms, S, M))) return rc;
+    std::vector<long long> off(bt->offsets, bt->offsets + S + 1);
+    CK(cudaMemcpyAsync(ctx->b_off, off.data(), sizeof(long long) * (S + 1), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->b_box, bt->boxes, sizeof(double) * 3 * S, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->b_order, order.data(), sizeof(int) * S, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    memset(&b, 0, sizeof(b));
+    b.S = S;
+    b.ntot = bt->n_atoms;
+    b.off = ctx->b_off;
+    b.order = ctx->b_order;
+    b.box = ctx->b_box;
+    b.x = bt->xyz;
+    b.queue = ctx->b_queue;
+    b.status = ctx->status;
+    b.lpart = ctx->b_lpart;
+    b.gpart = ctx->b_gpart;
+    return NEP_OK;
+}
+
+// Runs one batched launch (with neighbour-capacity growth) and waits.
+static int batch_launch(nep_ctx* ctx, Batch& b, int mode, double* grad, cudaStream_t s)
+{
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int bt = ctx->precision == NEP_FP32 ? ctx->b_bt : 128;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        b.M = ctx->b_M;
+        b.nbr = ctx->b_nbr;
+        b.cnt = ctx->b_cnt;
+        b.scr = ctx->b_scr;
+        b.gpart = ctx->b_gpart;
+        b.lpart = ctx->b_lpart;
+        b.off = ctx->b_off;
+        b.order = ctx->b_order;
+        b.box = ctx->b_box;
+        b.queue = ctx->b_queue;
+        int per_sm = ctx->b_per_sm > 0 ? ctx->b_per_sm
+                                        : batch_blocks_per_sm(ctx->precision, mode, bt);
+        int grid = std::min(b.S, std::max(1, per_sm * sms));
+        CK(cudaMemsetAsync(ctx->b_queue, 0, sizeof(int), s));
+        CK(cudaMemsetAsync(ctx->status, 0, sizeof(int) * 3, s));
+        CK(launch_batch(ctx->precision, mode, bt, grid, ctx->mf, ctx->md, b, grad, s));
+        ctx->launches += mode == 0 ? 1 : 2;
+        CK(cudaMemcpyAsync(ctx->h_status, ctx->status, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (ctx->h_status[0] & ST_OVERFLOW) {
+            // keep the batch description: reallocation must not lose offsets/boxes/order
+            std::vector<long long> off(b.S + 1);
+            std::vector<double> box(3 * (size_t)b.S);
+            std::vector<int> order(b.S);
+            CK(cudaMemcpy(off.data(), ctx->b_off, sizeof(long long) * (b.S + 1), cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(box.data(), ctx->b_box, sizeof(double) * 3 * b.S, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(order.data(), ctx->b_order, sizeof(int) * b.S, cudaMemcpyDeviceToHost));
+            const int need = grown_capacity(ctx->h_status[1]);
+            int rc = batch_buffers(ctx, b.ntot, b.S, need);
+            if (rc) return rc;
+            CK(cudaMemcpy(ctx->b_off, off.data(), sizeof(long long) * (b.S + 1), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(ctx->b_box, box.data(), sizeof(double) * 3 * b.S, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(ctx->b_order, order.data(), sizeof(int) * b.S, cudaMemcpyHostToDevice));
+            continue;
+        }
+        if (ctx->h_status[0] & ST_NONFINITE)
+            return fail(ctx, NEP_ERR_NONFINITE, "non-finite values in the batch");
+        return NEP_OK;
+    }
+    return fail(ctx, NEP_ERR_NBR_OVERFLOW, "neighbour capacity could not be grown enough");
+}
+
+extern "C" {
+
+int nep_set_params(nep_ctx* ctx, const double* params, int64_t n_params)
+{
+    if (!ctx) return NEP_ERR_INVALID_ARG;
+    const int64_t np = (int64_t)H * D + 2 * H + 1 + NR * KR + NA * KA;
+    if (!params || n_params != np)
+        return fail(ctx, NEP_ERR_INVALID_ARG, "params must hold %lld values", (long long)np);
+    for (int64_t i = 0; i < np; ++i)
+        if (!isfinite(params[i])) return fail(ctx, NEP_ERR_INVALID_ARG, "non-finite parameter");
+    // rebuild both models from the new parameters and the stored scaler
+    double sc[D];
+    for (int nu = 0; nu < D; ++nu) sc[nu] = ctx->md.sc[nu];
+    nep_params p;
+    memset(&p, 0, sizeof(p));
+    p.params = params;
+    p.q_scaler = sc;
+    p.rc_radial = ctx->rcR;
+    p.rc_angular = sqrt(ctx->md.rcA2);
+    p.zbl_r_inner = ctx->md.zbl_r1;
+    p.zbl_r_outer = ctx->md.zbl_rr2;
+    const double kz = ctx->md.zbl_k, inva = ctx->md.zbl_inv_a;
+    build_model<float>(ctx->mf, &p);
+    build_model<double>(ctx->md, &p);
+    ctx->mf.zbl_k = kz; ctx->md.zbl_k = kz;
+    ctx->mf.zbl_inv_a = inva; ctx->md.zbl_inv_a = inva;
+    drop_graphs(ctx);
+    return NEP_OK;
+}
+
+int nep_batch_forward(nep_ctx* ctx, const nep_batch* batch, double* energies, double* forces,
+                      void* stream)
+{
+    if (!ctx) return NEP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    if ((rc = check_device_ptr(ctx, energies, "energies")) ||
+        (rc = check_device_ptr(ctx, forces, "forces")))
+        return rc;
+    Batch b;
+    if ((rc = batch_prepare(ctx, batch, s, b))) return rc;
+    b.E = energies;
+    b.F = forces;
+    return batch_launch(ctx, b, MODE_FORWARD, nullptr, s);
+}
+
+int nep_batch_backward(nep_ctx* ctx, const nep_batch* batch, const double* dL_dE,
+                       const double* dL_dF, double* grad, void* stream)
+{
+    if (!ctx) return NEP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    if ((rc = check_device_ptr(ctx, dL_dE, "dL_dE")) || (rc = check_device_ptr(ctx, dL_dF, "dL_dF")) ||
+        (rc = check_device_ptr(ctx, grad, "grad")))
+        return rc;
+    Batch b;
+    if ((rc = batch_prepare(ctx, batch, s, b))) return rc;
+    b.dLdE = dL_dE;
+    b.dLdF = dL_dF;
+    return batch_launch(ctx, b, MODE_BACKWARD, grad, s);
+}
+
+int nep_batch_loss_grad(nep_ctx* ctx, const nep_batch* batch, const double* E_target,
+                        const double* F_target, double w_energy, double w_force, double* loss,
+                        double* grad, double* energies, double* forces, void* stream)
+{
+    if (!ctx) return NEP_ERR_INVALID_ARG;
+    if (!loss) return fail(ctx, NEP_ERR_INVALID_ARG, "loss is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    if ((rc = check_device_ptr(ctx, E_target, "E_target")) ||
+        (rc = check_device_ptr(ctx, F_target, "F_target")) || (rc = check_device_ptr(ctx, grad, "grad")))
+        return rc;
+    if (energies && (rc = check_device_ptr(ctx, energies, "energies"))) return rc;
+    if (forces && (rc = check_device_ptr(ctx, forces, "forces"))) return rc;
+    Batch b;
+    if ((rc = batch_prepare(ctx, batch, s, b))) return rc;
+    b.E = energies ? energies : ctx->b_E;
+    b.F = forces ? forces : ctx->b_F;
+    b.Et = E_target;
+    b.Ft = F_target;
+    b.we = w_energy;
+    b.wf = w_force;
+    if ((rc = batch_launch(ctx, b, MODE_LOSS, grad, s))) return rc;
+    std::vector<double> lp(b.S);
+    CK(cudaMemcpy(lp.data(), ctx->b_lpart, sizeof(double) * b.S, cudaMemcpyDeviceToHost));
+    double L = 0.0;
+    for (int c = 0; c < b.S; ++c) L += lp[c];
+    *loss = L;
+    return NEP_OK;
+}
+
+int nep_batch_autotune(nep_ctx* ctx, const nep_batch* batch, const double* E_target,
+                       const double* F_target, void* stream, int* best_threads, int* best_per_sm)
+{
+    if (!ctx) return NEP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    double* grad = nullptr;
+    CK(cudaMalloc(&grad, sizeof(double) * NP));
+    const int bts[3] = {64, 128, 256};
+    const int nbt = ctx->precision == NEP_FP32 ? 3 : 1;
+    float best = 1e30f;
+    int bb = ctx->b_bt, bs = ctx->b_per_sm;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int rc = NEP_OK;
+    for (int a = 0; a < nbt && !rc; ++a) {
+        for (int per = 1; per <= 4 && !rc; per *= 2) {
+            ctx->b_bt = ctx->precision == NEP_FP32 ? bts[a] : 128;
+            ctx->b_per_sm = per;
+            double L = 0.0;
+            rc = nep_batch_loss_grad(ctx, batch, E_target, F_target, 1.0, 1.0, &L, grad, nullptr,
+                                     nullptr, stream);   // warm-up
+            if (rc) break;
+            cudaEventRecord(e0, s);
+            rc = nep_batch_loss_grad(ctx, batch, E_target, F_target, 1.0, 1.0, &L, grad, nullptr,
+                                     nullptr, stream);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (!rc && ms < best) { best = ms; bb = ctx->b_bt; bs = per; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(grad);
+    ctx->b_bt = bb;
+    ctx->b_per_sm = bs;
+    ctx->b_tuned = 1;
+    if (best_threads) *best_threads = bb;
+    if (best_per_sm) *best_per_sm = bs;
+    return rc;
 }
 
 }  // extern "C"

@@ -29,7 +29,9 @@ NEP_OPT_GRAPH_CHUNK = 2
 NEP_OPT_NBR_CAPACITY = 3
 
 EXPORTED = ("nep_init", "nep_free", "nep_last_error", "nep_compute", "md_step",
-            "nep_get_stats", "nep_set_option", "nep_reset_stats", "nep_compute_static")
+            "nep_get_stats", "nep_set_option", "nep_reset_stats", "nep_compute_static",
+            "nep_set_params", "nep_batch_forward", "nep_batch_backward", "nep_batch_loss_grad",
+            "nep_batch_autotune")
 
 
 class NepParams(C.Structure):
@@ -58,6 +60,12 @@ class NepStats(C.Structure):
                 ("pairs_angular", C.c_int64), ("max_nbr_radial", C.c_int32),
                 ("max_nbr_angular", C.c_int32), ("nbr_capacity", C.c_int32),
                 ("graph_chunk", C.c_int32)]
+
+
+class NepBatch(C.Structure):
+    _fields_ = [("n_configs", C.c_int32), ("n_atoms", C.c_int64), ("xyz", C.c_void_p),
+                ("offsets", C.POINTER(C.c_int64)), ("boxes", C.POINTER(C.c_double)),
+                ("types", C.c_void_p)]
 
 
 _lib = None
@@ -100,6 +108,18 @@ def load(build: bool = True):
                                      vp, C.POINTER(C.c_int32), C.POINTER(C.c_double), vp,
                                      C.POINTER(C.c_double), vp, vp]
     L.nep_compute_static.restype = C.c_int
+    L.nep_set_params.argtypes = [vp, C.POINTER(C.c_double), C.c_int64]
+    L.nep_set_params.restype = C.c_int
+    bp = C.POINTER(NepBatch)
+    L.nep_batch_forward.argtypes = [vp, bp, vp, vp, vp]
+    L.nep_batch_forward.restype = C.c_int
+    L.nep_batch_backward.argtypes = [vp, bp, vp, vp, vp, vp]
+    L.nep_batch_backward.restype = C.c_int
+    L.nep_batch_loss_grad.argtypes = [vp, bp, vp, vp, C.c_double, C.c_double,
+                                      C.POINTER(C.c_double), vp, vp, vp, vp]
+    L.nep_batch_loss_grad.restype = C.c_int
+    L.nep_batch_autotune.argtypes = [vp, bp, vp, vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.nep_batch_autotune.restype = C.c_int
     _lib = L
     return L
 
@@ -215,6 +235,126 @@ class NEP:
 
     def reset_stats(self):
         self._check(self.lib.nep_reset_stats(self.ctx))
+
+
+    # ---- batches of small periodic configurations ----------------------------
+
+    def set_params(self, theta):
+        """Replaces the model parameters (numpy or torch, length n_params)."""
+        try:
+            import torch
+            if isinstance(theta, torch.Tensor):
+                theta = theta.detach().cpu().numpy()
+        except ImportError:
+            pass
+        t = np.ascontiguousarray(theta, dtype=np.float64)
+        self._check(self.lib.nep_set_params(self.ctx, t.ctypes.data_as(C.POINTER(C.c_double)),
+                                            len(t)))
+
+    def batch_forward(self, batch: "Batch", stream=None):
+        """Energies (S,) and forces (3, N) of every configuration (CUDA tensors)."""
+        import torch
+        E = torch.empty(batch.S, dtype=torch.float64, device=batch.device)
+        F = torch.empty((3, batch.N), dtype=torch.float64, device=batch.device)
+        self._check(self.lib.nep_batch_forward(self.ctx, C.byref(batch.c), C.c_void_p(E.data_ptr()),
+                                               C.c_void_p(F.data_ptr()), _stream_ptr(stream)))
+        return E, F
+
+    def batch_backward(self, batch: "Batch", dLdE, dLdF, stream=None):
+        """Parameter gradient (n_params,) of a loss from dL/dE (S,) and dL/dF (3, N)."""
+        import torch
+        dLdE = dLdE.contiguous().to(torch.float64)
+        dLdF = dLdF.contiguous().to(torch.float64)
+        g = torch.empty(len(self._params), dtype=torch.float64, device=batch.device)
+        self._check(self.lib.nep_batch_backward(self.ctx, C.byref(batch.c),
+                                                C.c_void_p(dLdE.data_ptr()),
+                                                C.c_void_p(dLdF.data_ptr()),
+                                                C.c_void_p(g.data_ptr()), _stream_ptr(stream)))
+        return g
+
+    def batch_loss_grad(self, batch: "Batch", E_target, F_target, w_energy=1.0, w_force=1.0,
+                        stream=None):
+        """Fused forward + energy/force MSE loss + gradient in one persistent launch.
+        Returns (loss, grad (n_params,), E (S,), F (3, N))."""
+        import torch
+        E = torch.empty(batch.S, dtype=torch.float64, device=batch.device)
+        F = torch.empty((3, batch.N), dtype=torch.float64, device=batch.device)
+        g = torch.empty(len(self._params), dtype=torch.float64, device=batch.device)
+        Et = E_target.contiguous()
+        Ft = F_target.contiguous()
+        L = C.c_double()
+        self._check(self.lib.nep_batch_loss_grad(
+            self.ctx, C.byref(batch.c), C.c_void_p(Et.data_ptr()), C.c_void_p(Ft.data_ptr()),
+            float(w_energy), float(w_force), C.byref(L), C.c_void_p(g.data_ptr()),
+            C.c_void_p(E.data_ptr()), C.c_void_p(F.data_ptr()), _stream_ptr(stream)))
+        return L.value, g, E, F
+
+    def batch_autotune(self, batch: "Batch", E_target, F_target, stream=None):
+        bt, per = C.c_int(), C.c_int()
+        self._check(self.lib.nep_batch_autotune(
+            self.ctx, C.byref(batch.c), C.c_void_p(E_target.contiguous().data_ptr()),
+            C.c_void_p(F_target.contiguous().data_ptr()), _stream_ptr(stream), C.byref(bt),
+            C.byref(per)))
+        return bt.value, per.value
+
+
+class Batch:
+    """A batch of periodic configurations on the device (SoA positions, host
+    offsets and box lengths) for the batched entry points."""
+
+    def __init__(self, structures, device="cuda"):
+        import torch
+        self.device = torch.device(device)
+        self.S = len(structures)
+        counts = [s.n for s in structures]
+        self.offsets = np.zeros(self.S + 1, np.int64)
+        self.offsets[1:] = np.cumsum(counts)
+        self.N = int(self.offsets[-1])
+        self.boxes = np.ascontiguousarray(np.concatenate([np.asarray(s.box, float)
+                                                          for s in structures]))
+        pos = np.concatenate([s.pos for s in structures], axis=0)
+        self.xyz = to_device_soa(pos, self.device)
+        self.types = torch.zeros(self.N, dtype=torch.int32, device=self.device)
+        c = NepBatch()
+        c.n_configs = self.S
+        c.n_atoms = self.N
+        c.xyz = self.xyz.data_ptr()
+        c.offsets = self.offsets.ctypes.data_as(C.POINTER(C.c_int64))
+        c.boxes = self.boxes.ctypes.data_as(C.POINTER(C.c_double))
+        c.types = self.types.data_ptr()
+        self.c = c
+
+
+def energy_forces_function():
+    """torch.autograd.Function: (theta, nep, batch) -> (E (S,), F (3, N)).  Its
+    backward calls the library's hand-written gradient kernels with the
+    upstream dL/dE and dL/dF (the force term needs the second derivatives of
+    the energy), returning dL/dtheta."""
+    import torch
+
+    class NEPEnergyForces(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, theta, nep, batch):
+            nep.set_params(theta)
+            E, F = nep.batch_forward(batch)
+            ctx.nep = nep
+            ctx.batch = batch
+            ctx.save_for_backward(theta)
+            return E, F
+
+        @staticmethod
+        def backward(ctx, gE, gF):
+            (theta,) = ctx.saved_tensors
+            nep, batch = ctx.nep, ctx.batch
+            if gE is None:
+                gE = torch.zeros(batch.S, dtype=torch.float64, device=batch.device)
+            if gF is None:
+                gF = torch.zeros((3, batch.N), dtype=torch.float64, device=batch.device)
+            nep.set_params(theta)
+            g = nep.batch_backward(batch, gE, gF)
+            return g.to(theta.device, theta.dtype), None, None
+
+    return NEPEnergyForces
 
 
 class MDState:

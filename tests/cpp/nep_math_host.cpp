@@ -26,3 +26,17 @@ extern "C" void h_cutoff_f(float x, float* sc)
 {
     nepm::cutoff_sincospi(x, &sc[0], &sc[1]);
 }
+
+extern "C" void h_harmonics_dir(const double* u, const double* w, double* D)
+{
+    nepm::harmonics_dir<double>(u[0], u[1], u[2], w[0], w[1], w[2], D);
+}
+
+extern "C" void h_fourbody_hvp(const double* A2, const double* Ad, double* out)
+{
+    double T[6], Td[6], S[6];
+    nepm::fourbody_T<double>(A2, T);
+    nepm::fourbody_T<double>(Ad, Td);
+    nepm::sym_anticomm<double>(T, Td, S);
+    nepm::fourbody_map<double>(S, out);
+}

@@ -115,3 +115,30 @@ def test_fp32_cutoff_polynomial(lib):
         xf = float(np.float32(x))
         worst = max(worst, abs(out[0] - math.sin(math.pi * xf)), abs(out[1] - math.cos(math.pi * xf)))
     assert worst < 3e-7, worst
+
+
+def test_harmonics_directional_derivative(lib):
+    lib.h_harmonics_dir.argtypes = [C.POINTER(C.c_double)] * 3
+    rng = np.random.default_rng(5)
+    for _ in range(10):
+        u = rng.normal(size=3)
+        w = rng.normal(size=3)
+        D = np.zeros(24)
+        lib.h_harmonics_dir(_p(u), _p(w), _p(D))
+        h = 1e-6
+        fd = (Y(lib, u + h * w) - Y(lib, u - h * w)) / (2 * h)
+        np.testing.assert_allclose(D, fd, rtol=1e-7, atol=1e-8)
+
+
+def test_fourbody_hessian_vector_product(lib):
+    lib.h_fourbody_hvp.argtypes = [C.POINTER(C.c_double)] * 3
+    rng = np.random.default_rng(6)
+    A2 = rng.normal(size=5)
+    Ad = rng.normal(size=5)
+    out = np.zeros(5)
+    lib.h_fourbody_hvp(_p(A2), _p(Ad), _p(out))
+    h = 1e-6
+    gp, gm = np.zeros(5), np.zeros(5)
+    lib.h_fourbody(_p(A2 + h * Ad), _p(gp))
+    lib.h_fourbody(_p(A2 - h * Ad), _p(gm))
+    np.testing.assert_allclose(out, (gp - gm) / (2 * h), rtol=1e-7, atol=1e-9)
