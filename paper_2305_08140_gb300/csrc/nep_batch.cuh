@@ -174,10 +174,10 @@ __device__ __forceinline__ double batch_atom_forward(const Model<R>& P, const Ba
     const int2 c2 = b.cnt[col];
     const int na = c2.x, nro = c2.y, tot = na + nro, M = b.M;
     const typename V4<R>::T pi = spos[i];
-    R qR[NR];
+    R Sb[KR];
     R A[NA][NLM];
 #pragma unroll
-    for (int n = 0; n < NR; ++n) qR[n] = R(0);
+    for (int kk = 0; kk < KR; ++kk) Sb[kk] = R(0);
 #pragma unroll
     for (int n = 0; n < NA; ++n)
 #pragma unroll
@@ -185,8 +185,10 @@ __device__ __forceinline__ double batch_atom_forward(const Model<R>& P, const Ba
     for (int s = 0; s < tot; ++s) {
         const int ent = b.nbr[(size_t)slot_of(s, na, nro, M) * b.ntot + col];
         const PairGeom<R> g = pair_geom<R>(ent, pi, spos, s_off);
-        desc_pair<R>(P, g.dx, g.dy, g.dz, g.r, g.inv_r, s < na, qR, A);
+        desc_pair<R>(P, g.dx, g.dy, g.dz, g.r, g.inv_r, s < na, Sb, A);
     }
+    R qR[NR];
+    radial_q<R>(P, Sb, qR);
     R bR[KR], B0;
     const R U = network_adjoint<R>(P, qR, A, bR, B0);
     double ez = 0.0;

@@ -227,7 +227,7 @@ __global__ void k_cell_finalize(Grid g, int ncell, const int* __restrict__ start
 // ----------------------------------------------------------------------------
 
 template <typename R>
-__global__ void __launch_bounds__(128) k_neighbors(Grid g, R rcR2, R rcA2,
+__global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                                                    const typename V4<R>::T* __restrict__ pos4,
                                                    const int* __restrict__ cell_sorted,
                                                    const int* __restrict__ start,
@@ -236,42 +236,48 @@ __global__ void __launch_bounds__(128) k_neighbors(Grid g, R rcR2, R rcA2,
                                                    int* __restrict__ maxc,
                                                    unsigned long long* __restrict__ pairs)
 {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
     int na = 0, nro = 0, sa = 0, sro = 0;
     if (k < g.n) {
-        typename V4<R>::T p = pos4[k];
-        int c = cell_sorted[k];
-        int cz = c % g.nc[2], cy = (c / g.nc[2]) % g.nc[1], cx = c / (g.nc[2] * g.nc[1]);
+        const typename V4<R>::T p = pos4[k];
+        const int c = cell_sorted[k];
+        const int ncx = g.nc[0], ncy = g.nc[1], ncz = g.nc[2];
+        const int cz = c % ncz, cy = (c / ncz) % ncy, cx = c / (ncz * ncy);
+        // cell edges in R: the offsets ox * lc are exact multiples, the same
+        // values the force kernel adds for the stencil codes
+        const R lx = (R)g.lc[0], ly = (R)g.lc[1], lz = (R)g.lc[2];
         const int M = g.M;
+        int* col = nbr + k;
+        const size_t ld = (size_t)g.ld;
         for (int ox = -1; ox <= 1; ++ox) {
             int X = cx + ox;
-            if (g.pbc[0]) X = (X + g.nc[0]) % g.nc[0];
-            else if (X < 0 || X >= g.nc[0]) continue;
-            R offx = (R)(ox * g.lc[0]);
+            if (g.pbc[0]) { X += X < 0 ? ncx : 0; X -= X >= ncx ? ncx : 0; }
+            else if (X < 0 || X >= ncx) continue;
+            const R px = p.x - R(ox) * lx;
             for (int oy = -1; oy <= 1; ++oy) {
                 int Y = cy + oy;
-                if (g.pbc[1]) Y = (Y + g.nc[1]) % g.nc[1];
-                else if (Y < 0 || Y >= g.nc[1]) continue;
-                R offy = (R)(oy * g.lc[1]);
+                if (g.pbc[1]) { Y += Y < 0 ? ncy : 0; Y -= Y >= ncy ? ncy : 0; }
+                else if (Y < 0 || Y >= ncy) continue;
+                const R py = p.y - R(oy) * ly;
+                const int rowXY = (X * ncy + Y) * ncz;
                 for (int oz = -1; oz <= 1; ++oz) {
                     int Z = cz + oz;
-                    if (g.pbc[2]) Z = (Z + g.nc[2]) % g.nc[2];
-                    else if (Z < 0 || Z >= g.nc[2]) continue;
-                    R offz = (R)(oz * g.lc[2]);
-                    int code = (ox + 1) * 9 + (oy + 1) * 3 + (oz + 1);
-                    int c2 = (X * g.nc[1] + Y) * g.nc[2] + Z;
-                    int e = start[c2 + 1];
+                    if (g.pbc[2]) { Z += Z < 0 ? ncz : 0; Z -= Z >= ncz ? ncz : 0; }
+                    else if (Z < 0 || Z >= ncz) continue;
+                    const R pz = p.z - R(oz) * lz;
+                    const int code = (ox + 1) * 9 + (oy + 1) * 3 + (oz + 1);
+                    const int c2 = rowXY + Z;
+                    const int e = start[c2 + 1];
                     for (int m = start[c2]; m < e; ++m) {
-                        if (m == k) continue;
-                        typename V4<R>::T q = pos4[m];
-                        R dx = q.x - p.x + offx, dy = q.y - p.y + offy, dz = q.z - p.z + offz;
-                        R r2 = dx * dx + dy * dy + dz * dz;
-                        if (r2 < rcR2) {
-                            bool ang = r2 < rcA2;
+                        const typename V4<R>::T q = pos4[m];
+                        const R dx = q.x - px, dy = q.y - py, dz = q.z - pz;
+                        const R r2 = dx * dx + dy * dy + dz * dz;
+                        if (r2 < rcR2 && m != k) {
+                            const bool ang = r2 < rcA2;
                             if (sa + sro < M) {
-                                int ent = (m << 5) | code;
-                                if (ang) nbr[(size_t)(sa++) * g.ld + k] = ent;
-                                else nbr[(size_t)(M - 1 - sro++) * g.ld + k] = ent;
+                                const int ent = (m << 5) | code;
+                                if (ang) col[(size_t)(sa++) * ld] = ent;
+                                else col[(size_t)(M - 1 - sro++) * ld] = ent;
                             }
                             if (ang) ++na; else ++nro;
                         }
@@ -380,20 +386,16 @@ __device__ __forceinline__ void fill_stencil(typename V4<R>::T* tab, const Grid&
 // ----------------------------------------------------------------------------
 
 // Adds one neighbour (displacement d) to the descriptor sums of an atom: the
-// radial q_n and, for an angular neighbour, A_nlm = sum_j g_n Y_lm.
+// radial basis sums Sb_k = sum_j f_c T_k(x_j) (q_n follows per atom from
+// radial_q) and, for an angular neighbour, A_nlm = sum_j g_n Y_lm.
 template <typename R>
 __device__ __forceinline__ void desc_pair(const Model<R>& P, R dx, R dy, R dz, R r, R inv_r,
-                                          bool ang, R (&qR)[NR], R (&A)[NA][NLM])
+                                          bool ang, R (&Sb)[KR], R (&A)[NA][NLM])
 {
     R T[KR], dT[KR], fc, dfc, dxdr;
     nepm::cheb<KR, false>(r, P.inv_rcR, T, dT, fc, dfc, dxdr);
 #pragma unroll
-    for (int n = 0; n < NR; ++n) {
-        R acc = P.CR[n];
-#pragma unroll
-        for (int kk = 0; kk < KR; ++kk) acc += P.hR[n * KR + kk] * T[kk];
-        qR[n] += fc * acc;
-    }
+    for (int kk = 0; kk < KR; ++kk) Sb[kk] += fc * T[kk];
     if (ang) {
         nepm::cheb<KA, false>(r, P.inv_rcA, T, dT, fc, dfc, dxdr);
         R Y[NLM];
@@ -407,6 +409,19 @@ __device__ __forceinline__ void desc_pair(const Model<R>& P, R dx, R dy, R dz, R
 #pragma unroll
             for (int lm = 0; lm < NLM; ++lm) A[n][lm] += gn * Y[lm];
         }
+    }
+}
+
+// q_n = sum_j g_n(r_j) = C_n Sb_0 + sum_k h_nk Sb_k (T_0 = 1).
+template <typename R>
+__device__ __forceinline__ void radial_q(const Model<R>& P, const R (&Sb)[KR], R (&qR)[NR])
+{
+#pragma unroll
+    for (int n = 0; n < NR; ++n) {
+        R acc = P.CR[n] * Sb[0];
+#pragma unroll
+        for (int kk = 0; kk < KR; ++kk) acc += P.hR[n * KR + kk] * Sb[kk];
+        qR[n] = acc;
     }
 }
 
@@ -561,30 +576,50 @@ __global__ void __launch_bounds__(TILE) k_nep(const Model<R> P, const Grid g,
                                               typename Acc<R>::T* __restrict__ facc,
                                               double* __restrict__ partials,
                                               double* __restrict__ site_energy,
-                                              int* __restrict__ status)
+                                              int* __restrict__ status, int stage_slots)
 {
     using A_ = Acc<R>;
     using P4 = typename V4<R>::T;
     __shared__ P4 s_off[27];
-    fill_stencil<R>(s_off, g);
+    __shared__ int s_max;
+    extern __shared__ int s_ent[];   // [stage_slots][TILE] staged neighbour entries
+    if (threadIdx.x == 0) s_max = 0;
+    fill_stencil<R>(s_off, g);       // ends with __syncthreads
     const int k = blockIdx.x * TILE + threadIdx.x;
     const int M = g.M;
     const size_t ld = (size_t)g.ld;
+    // the block's lists go to shared memory when its longest list fits
+    const int2 cnt_k = k < g.n ? cnt[k] : make_int2(0, 0);
+    atomicMax(&s_max, cnt_k.x + cnt_k.y);
+    __syncthreads();
+    const bool staged = s_max <= stage_slots;
+    if (staged && k < g.n) {
+        for (int s = 0; s < cnt_k.x; ++s) s_ent[s * TILE + threadIdx.x] = nbr[(size_t)s * ld + k];
+        for (int u = 0; u < cnt_k.y; ++u)
+            s_ent[(cnt_k.x + u) * TILE + threadIdx.x] = nbr[(size_t)(M - 1 - u) * ld + k];
+    }
     double e_site = 0.0;
-    double wv[9];
+    R w[9];                 // virial of the NEP pair terms (R)
+    double wz[9];           // virial of the ZBL pair terms (FP64)
+    bool has_zbl = false;
 #pragma unroll
-    for (int t = 0; t < 9; ++t) wv[t] = 0.0;
+    for (int t = 0; t < 9; ++t) { w[t] = R(0); wz[t] = 0.0; }
 
     if (k < g.n) {
         const typename V4<R>::T pi = pos4[k];
-        const int2 c2 = cnt[k];
-        const int na = c2.x, nro = c2.y;
+        const int na = cnt_k.x, nro = cnt_k.y;
+        // entry s of the list: angular pairs first, then radial-only pairs
+        auto entry = [&](int s) -> int {
+            if (staged) return s_ent[s * TILE + threadIdx.x];
+            const int slot = s < na ? s : M - 1 - (s - na);
+            return nbr[(size_t)slot * ld + k];
+        };
 
         // ---------------- descriptor sums ----------------
-        R qR[NR];
+        R Sb[KR];
         R A[NA][NLM];
 #pragma unroll
-        for (int n = 0; n < NR; ++n) qR[n] = R(0);
+        for (int kk = 0; kk < KR; ++kk) Sb[kk] = R(0);
 #pragma unroll
         for (int n = 0; n < NA; ++n)
 #pragma unroll
@@ -593,25 +628,24 @@ __global__ void __launch_bounds__(TILE) k_nep(const Model<R> P, const Grid g,
         const int total = na + nro;
         // two-stage prefetch: entry s + 2 and position s + 1 are loaded while
         // pair s is computed
-        int ent_n = total > 0 ? nbr[(size_t)(na > 0 ? 0 : M - nro) * ld + k] : 0;
-        int ent_nn = total > 1 ? nbr[(size_t)(1 < na ? 1 : M - nro + (1 - na)) * ld + k] : 0;
+        int ent_n = total > 0 ? entry(0) : 0;
+        int ent_nn = total > 1 ? entry(1) : 0;
         P4 pj_n = total > 0 ? pos4[ent_n >> 5] : pi;
         for (int s = 0; s < total; ++s) {
             const int ent = ent_n;
             const P4 pj = pj_n;
             ent_n = ent_nn;
             if (s + 1 < total) pj_n = pos4[ent_n >> 5];
-            if (s + 2 < total) {
-                const int s2 = s + 2;
-                ent_nn = nbr[(size_t)(s2 < na ? s2 : M - nro + (s2 - na)) * ld + k];
-            }
+            if (s + 2 < total) ent_nn = entry(s + 2);
             const P4 off = s_off[ent & 31];
             const R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
             const R r2 = dx * dx + dy * dy + dz * dz;
             const R inv_r = nepm::nep_rsqrt(r2);
             const R r = r2 * inv_r;
-            desc_pair<R>(P, dx, dy, dz, r, inv_r, s < na, qR, A);
+            desc_pair<R>(P, dx, dy, dz, r, inv_r, s < na, Sb, A);
         }
+        R qR[NR];
+        radial_q<R>(P, Sb, qR);
 
         // ---------------- network and its backward ---------------------------
         R bR[KR], B0;
@@ -619,25 +653,19 @@ __global__ void __launch_bounds__(TILE) k_nep(const Model<R> P, const Grid g,
 
         // ---------------- pair forces --------------------------------------
         typename A_::T fi[3] = {0, 0, 0};
-        R w[9];
-#pragma unroll
-        for (int t = 0; t < 9; ++t) w[t] = R(0);
         double ez = 0.0;
         bool bad = !isfinite(U);
         const int i_caller = perm[k];
 
-        ent_n = total > 0 ? nbr[(size_t)(na > 0 ? 0 : M - nro) * ld + k] : 0;
-        ent_nn = total > 1 ? nbr[(size_t)(1 < na ? 1 : M - nro + (1 - na)) * ld + k] : 0;
+        ent_n = total > 0 ? entry(0) : 0;
+        ent_nn = total > 1 ? entry(1) : 0;
         pj_n = total > 0 ? pos4[ent_n >> 5] : pi;
         for (int s = 0; s < total; ++s) {
             const int ent = ent_n;
             const P4 pj = pj_n;
             ent_n = ent_nn;
             if (s + 1 < total) pj_n = pos4[ent_n >> 5];
-            if (s + 2 < total) {
-                const int s2 = s + 2;
-                ent_nn = nbr[(size_t)(s2 < na ? s2 : M - nro + (s2 - na)) * ld + k];
-            }
+            if (s + 2 < total) ent_nn = entry(s + 2);
             const int m = ent >> 5;
             const P4 off = s_off[ent & 31];
             const R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
@@ -673,10 +701,11 @@ __global__ void __launch_bounds__(TILE) k_nep(const Model<R> P, const Grid g,
                     cy += A_::convd(f3[1]);
                     cz += A_::convd(f3[2]);
                     bad |= !isfinite(c);
+                    has_zbl = true;
 #pragma unroll
                     for (int a = 0; a < 3; ++a)
 #pragma unroll
-                        for (int b = 0; b < 3; ++b) wv[3 * a + b] -= f3[a] * d64[b];
+                        for (int b = 0; b < 3; ++b) wz[3 * a + b] -= f3[a] * d64[b];
                 }
             }
             fi[0] += cx; fi[1] += cy; fi[2] += cz;
@@ -691,25 +720,31 @@ __global__ void __launch_bounds__(TILE) k_nep(const Model<R> P, const Grid g,
         A_::add(&facc[ld + k], fi[1]);
         A_::add(&facc[2 * ld + k], fi[2]);
         e_site = (double)U + ez;
-#pragma unroll
-        for (int t = 0; t < 9; ++t) wv[t] += (double)w[t];
         if (site_energy) site_energy[i_caller] = e_site;
         if (bad) atomicOr(status, ST_NONFINITE);
     }
 
     // ---------------- per-tile energy and virial (fixed order) ----------------
+    // energy: FP64 over the warp; NEP virial: R over the warp (32 atoms), then
+    // FP64; ZBL virial: FP64, only in warps that have a ZBL pair
     __shared__ double red[TILE / 32][NPART];
-    double v[NPART];
-    v[0] = e_site;
 #pragma unroll
-    for (int t = 0; t < 9; ++t) v[1 + t] = wv[t];
+    for (int o = 16; o > 0; o >>= 1) e_site += __shfl_xor_sync(0xffffffffu, e_site, o);
 #pragma unroll
-    for (int t = 0; t < NPART; ++t)
+    for (int t = 0; t < 9; ++t)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[t] += __shfl_xor_sync(0xffffffffu, v[t], o);
-    if ((threadIdx.x & 31) == 0)
+        for (int o = 16; o > 0; o >>= 1) w[t] += __shfl_xor_sync(0xffffffffu, w[t], o);
+    if (__any_sync(0xffffffffu, has_zbl)) {
 #pragma unroll
-        for (int t = 0; t < NPART; ++t) red[threadIdx.x >> 5][t] = v[t];
+        for (int t = 0; t < 9; ++t)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) wz[t] += __shfl_xor_sync(0xffffffffu, wz[t], o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5][0] = e_site;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) red[threadIdx.x >> 5][1 + t] = (double)w[t] + wz[t];
+    }
     __syncthreads();
     if (threadIdx.x < NPART) {
         double s = 0.0;

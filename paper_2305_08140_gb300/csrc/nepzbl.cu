@@ -26,6 +26,8 @@ namespace {
 constexpr double COULOMB_EV_A = 14.39964547;
 // 1 eV/amu in A^2/fs^2
 constexpr double EV_AMU = 1.602176634e-19 / 1.66053906660e-27 * 1e-10;
+// longest neighbour list (slots) the force kernel stages in shared memory
+constexpr int STAGE_MAX_SLOTS = 112;
 
 thread_local std::string g_init_error;
 
@@ -89,6 +91,7 @@ struct nep_ctx {
     bool capturing = false;
     int capture_kernels = 0;
     int capture_timed = 0;
+    int nep_smem_set[2] = {0, 0};
 
     // batched configurations (small periodic boxes)
     long long b_ntot_cap = 0;
@@ -298,9 +301,18 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
         else
             CK(cudaEventRecord(ctx->events[2 * timed_slot], s));
     }
-    k_nep<R><<<tiles, TILE, 0, s>>>(P, g, (const typename V4<R>::T*)ctx->pos4, ctx->nbr, ctx->cnt,
-                                   ctx->perm, x, (typename Acc<R>::T*)ctx->facc, ctx->partials,
-                                   site_energy, ctx->status);
+    // neighbour entries of a block are staged in shared memory when they fit
+    const int stage_slots = ctx->M < STAGE_MAX_SLOTS ? ctx->M : STAGE_MAX_SLOTS;
+    const size_t stage_bytes = sizeof(int) * (size_t)stage_slots * TILE;
+    if (!ctx->nep_smem_set[sizeof(R) == 4 ? 0 : 1]) {
+        CK(cudaFuncSetAttribute(k_nep<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(int) * STAGE_MAX_SLOTS * TILE)));
+        ctx->nep_smem_set[sizeof(R) == 4 ? 0 : 1] = 1;
+    }
+    k_nep<R><<<tiles, TILE, stage_bytes, s>>>(P, g, (const typename V4<R>::T*)ctx->pos4, ctx->nbr,
+                                             ctx->cnt, ctx->perm, x,
+                                             (typename Acc<R>::T*)ctx->facc, ctx->partials,
+                                             site_energy, ctx->status, stage_slots);
     count_launch(ctx);
     if (timed_slot >= 0) {
         if (ctx->capturing)
@@ -1226,7 +1238,7 @@ extern "C" int nep_compute_static(const nep_params* p, int64_t n_atoms, const do
                                                       nbr, cnt, status, status + 1, pairs);
     const int tiles = (n + TILE - 1) / TILE;
     k_nep<float><<<tiles, TILE, 0, s>>>(P, g, pos4, nbr, cnt, perm, xyz, facc, partials,
-                                        site_energy, status);
+                                        site_energy, status, 0);
     k_forces_out<float><<<nb, tb, 0, s>>>(n, ST_MAX_ATOMS, perm, facc, forces, status);
     k_reduce_stage1<<<1, 256, 0, s>>>(partials, tiles, tiles, partials2);
     k_reduce_partials<<<1, 256, 0, s>>>(partials2, 1, result);
