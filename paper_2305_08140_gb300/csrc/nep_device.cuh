@@ -754,6 +754,357 @@ __global__ void __launch_bounds__(TILE) k_nep(const Model<R> P, const Grid g,
     }
 }
 
+// ----------------------------------------------------------------------------
+// The force evaluation split by register footprint.  Only the ~14 angular
+// pairs of an atom need its 120 angular accumulators; the ~58 radial terms
+// need 9.  So:
+//   k_radial_q     all pairs  -> q_n (radial descriptor)            small state
+//   k_nep_ang      angular pairs -> A_nlm, network, adjoint, angular and ZBL
+//                  pair forces, energy                              large state
+//   k_radial_force all pairs  -> radial pair forces from b_k        small state
+// All three scatter into the same fixed-point sums (order independent).
+// ----------------------------------------------------------------------------
+
+__device__ __forceinline__ int list_slot(int s, int na, int M)
+{
+    return s < na ? s : M - 1 - (s - na);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_radial_q(const Model<R> P, const Grid g,
+                                                  const typename V4<R>::T* __restrict__ pos4,
+                                                  const int* __restrict__ nbr,
+                                                  const int2* __restrict__ cnt,
+                                                  R* __restrict__ qr)
+{
+    using P4 = typename V4<R>::T;
+    __shared__ P4 s_off[27];
+    fill_stencil<R>(s_off, g);
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.n) return;
+    const size_t ld = (size_t)g.ld;
+    const int2 c2 = cnt[k];
+    const int na = c2.x, total = c2.x + c2.y, M = g.M;
+    const P4 pi = pos4[k];
+    R Sb[KR];
+#pragma unroll
+    for (int kk = 0; kk < KR; ++kk) Sb[kk] = R(0);
+    int ent_n = total > 0 ? nbr[(size_t)list_slot(0, na, M) * ld + k] : 0;
+    for (int s = 0; s < total; ++s) {
+        const int ent = ent_n;
+        if (s + 1 < total) ent_n = nbr[(size_t)list_slot(s + 1, na, M) * ld + k];
+        const P4 pj = pos4[ent >> 5];
+        const P4 off = s_off[ent & 31];
+        const R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
+        const R r2 = dx * dx + dy * dy + dz * dz;
+        const R r = r2 * nepm::nep_rsqrt(r2);
+        R T[KR], dT[KR], fc, dfc, dxdr;
+        nepm::cheb<KR, false>(r, P.inv_rcR, T, dT, fc, dfc, dxdr);
+#pragma unroll
+        for (int kk = 0; kk < KR; ++kk) Sb[kk] += fc * T[kk];
+    }
+    R q[NR];
+    radial_q<R>(P, Sb, q);
+#pragma unroll
+    for (int n = 0; n < NR; ++n) qr[(size_t)n * ld + k] = q[n];
+}
+
+// Angular part of dU_i/dd_ij for one angular neighbour (no radial term).
+template <typename R>
+__device__ __forceinline__ void force_pair_ang(const Model<R>& P, R r, R inv_r, R ux, R uy, R uz,
+                                               const R (&Ab)[NA][NLM], R& fx, R& fy, R& fz)
+{
+    R T[KA], dT[KA], fc, dfc, dxdr;
+    nepm::cheb<KA, true>(r, P.inv_rcA, T, dT, fc, dfc, dxdr);
+    R gn[NA], dgn[NA];
+#pragma unroll
+    for (int n = 0; n < NA; ++n) {
+        R a = P.CA[n], b = R(0);
+#pragma unroll
+        for (int kk = 0; kk < KA; ++kk) {
+            a += P.hA[n * KA + kk] * T[kk];
+            b += P.hA[n * KA + kk] * dT[kk];
+        }
+        gn[n] = fc * a;
+        dgn[n] = dfc * a + fc * dxdr * b;
+    }
+    R Y[NLM], G[NLM];
+    nepm::harmonics(ux, uy, uz, Y);
+    R sang = R(0);
+#pragma unroll
+    for (int lm = 0; lm < NLM; ++lm) {
+        const int l = lm < 3 ? 1 : (lm < 8 ? 2 : (lm < 15 ? 3 : 4));
+        R gsum = R(0), dsum = R(0);
+#pragma unroll
+        for (int n = 0; n < NA; ++n) {
+            gsum += Ab[n][lm] * gn[n];
+            dsum += Ab[n][lm] * dgn[n];
+        }
+        G[lm] = gsum;
+        sang += (dsum - R(l) * inv_r * gsum) * Y[lm];
+    }
+    R vx, vy, vz;
+    nepm::harmonics_grad_dot(ux, uy, uz, G, vx, vy, vz);
+    fx = sang * ux + vx * inv_r;
+    fy = sang * uy + vy * inv_r;
+    fz = sang * uz + vz * inv_r;
+}
+
+// Per-tile energy and virial partials (fixed order); see k_nep.
+template <typename R>
+__device__ __forceinline__ void tile_partials(double e_site, R (&w)[9], double (&wz)[9],
+                                              bool has_zbl, double* __restrict__ out)
+{
+    __shared__ double red[TILE / 32][NPART];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e_site += __shfl_xor_sync(0xffffffffu, e_site, o);
+#pragma unroll
+    for (int t = 0; t < 9; ++t)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w[t] += __shfl_xor_sync(0xffffffffu, w[t], o);
+    if (__any_sync(0xffffffffu, has_zbl)) {
+#pragma unroll
+        for (int t = 0; t < 9; ++t)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) wz[t] += __shfl_xor_sync(0xffffffffu, wz[t], o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5][0] = e_site;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) red[threadIdx.x >> 5][1 + t] = (double)w[t] + wz[t];
+    }
+    __syncthreads();
+    if (threadIdx.x < NPART) {
+        double sum = 0.0;
+#pragma unroll
+        for (int wi = 0; wi < TILE / 32; ++wi) sum += red[wi][threadIdx.x];
+        out[threadIdx.x] = sum;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g,
+                                                  const typename V4<R>::T* __restrict__ pos4,
+                                                  const int* __restrict__ nbr,
+                                                  const int2* __restrict__ cnt,
+                                                  const int* __restrict__ perm,
+                                                  const double* __restrict__ x64,
+                                                  const R* __restrict__ qr,
+                                                  R* __restrict__ br,
+                                                  typename Acc<R>::T* __restrict__ facc,
+                                                  double* __restrict__ partials,
+                                                  double* __restrict__ site_energy,
+                                                  int* __restrict__ status, int stage_slots)
+{
+    using A_ = Acc<R>;
+    using P4 = typename V4<R>::T;
+    __shared__ P4 s_off[27];
+    __shared__ int s_max;
+    extern __shared__ int s_ent[];   // [stage_slots][TILE] angular entries
+    if (threadIdx.x == 0) s_max = 0;
+    fill_stencil<R>(s_off, g);
+    const int k = blockIdx.x * TILE + threadIdx.x;
+    const size_t ld = (size_t)g.ld;
+    const int na = k < g.n ? cnt[k].x : 0;
+    atomicMax(&s_max, na);
+    __syncthreads();
+    const bool staged = s_max <= stage_slots;
+    if (staged)
+        for (int s = 0; s < na; ++s) s_ent[s * TILE + threadIdx.x] = nbr[(size_t)s * ld + k];
+    double e_site = 0.0;
+    R w[9];
+    double wz[9];
+    bool has_zbl = false;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) { w[t] = R(0); wz[t] = 0.0; }
+
+    if (k < g.n) {
+        const P4 pi = pos4[k];
+        auto entry = [&](int s) -> int {
+            return staged ? s_ent[s * TILE + threadIdx.x] : nbr[(size_t)s * ld + k];
+        };
+        R A[NA][NLM];
+#pragma unroll
+        for (int n = 0; n < NA; ++n)
+#pragma unroll
+            for (int lm = 0; lm < NLM; ++lm) A[n][lm] = R(0);
+        int ent_n = na > 0 ? entry(0) : 0;
+        P4 pj_n = na > 0 ? pos4[ent_n >> 5] : pi;
+        for (int s = 0; s < na; ++s) {
+            const int ent = ent_n;
+            const P4 pj = pj_n;
+            if (s + 1 < na) {
+                ent_n = entry(s + 1);
+                pj_n = pos4[ent_n >> 5];
+            }
+            const P4 off = s_off[ent & 31];
+            const R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
+            const R r2 = dx * dx + dy * dy + dz * dz;
+            const R inv_r = nepm::nep_rsqrt(r2);
+            const R r = r2 * inv_r;
+            R T[KA], dT[KA], fc, dfc, dxdr;
+            nepm::cheb<KA, false>(r, P.inv_rcA, T, dT, fc, dfc, dxdr);
+            R Y[NLM];
+            nepm::harmonics(dx * inv_r, dy * inv_r, dz * inv_r, Y);
+#pragma unroll
+            for (int n = 0; n < NA; ++n) {
+                R acc = P.CA[n];
+#pragma unroll
+                for (int kk = 0; kk < KA; ++kk) acc += P.hA[n * KA + kk] * T[kk];
+                const R gn = fc * acc;
+#pragma unroll
+                for (int lm = 0; lm < NLM; ++lm) A[n][lm] += gn * Y[lm];
+            }
+        }
+        R qR[NR];
+#pragma unroll
+        for (int n = 0; n < NR; ++n) qR[n] = qr[(size_t)n * ld + k];
+        R bR[KR], B0;
+        const R U = network_adjoint<R>(P, qR, A, bR, B0);
+#pragma unroll
+        for (int kk = 0; kk < KR; ++kk) br[(size_t)kk * ld + k] = bR[kk];
+        br[(size_t)KR * ld + k] = B0;
+
+        typename A_::T fi[3] = {0, 0, 0};
+        double ez = 0.0;
+        bool bad = !isfinite(U);
+        const int i_caller = perm[k];
+        ent_n = na > 0 ? entry(0) : 0;
+        pj_n = na > 0 ? pos4[ent_n >> 5] : pi;
+        for (int s = 0; s < na; ++s) {
+            const int ent = ent_n;
+            const P4 pj = pj_n;
+            if (s + 1 < na) {
+                ent_n = entry(s + 1);
+                pj_n = pos4[ent_n >> 5];
+            }
+            const int m = ent >> 5;
+            const P4 off = s_off[ent & 31];
+            const R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
+            const R r2 = dx * dx + dy * dy + dz * dz;
+            const R inv_r = nepm::nep_rsqrt(r2);
+            const R r = r2 * inv_r;
+            R fx, fy, fz;
+            force_pair_ang<R>(P, r, inv_r, dx * inv_r, dy * inv_r, dz * inv_r, A, fx, fy, fz);
+            bad |= !isfinite(fx + fy + fz);
+            typename A_::T cx = A_::conv(fx), cy = A_::conv(fy), cz = A_::conv(fz);
+            if (r < P.zbl_r2) {
+                double d64[3];
+                if (sizeof(R) == 4) {
+                    const int j_caller = perm[m];
+                    for (int a = 0; a < 3; ++a) {
+                        double t = x64[a * g.n + j_caller] - x64[a * g.n + i_caller];
+                        if (g.pbc[a]) t -= g.L[a] * rint(t * g.invL[a]);
+                        d64[a] = t;
+                    }
+                } else {
+                    d64[0] = (double)dx; d64[1] = (double)dy; d64[2] = (double)dz;
+                }
+                const double r64 = sqrt(d64[0] * d64[0] + d64[1] * d64[1] + d64[2] * d64[2]);
+                if (r64 < P.zbl_rr2) {
+                    double Uz, dUz;
+                    zbl_pair(r64, P.zbl_k, P.zbl_inv_a, P.zbl_r1, P.zbl_rr2, Uz, dUz);
+                    ez += 0.5 * Uz;
+                    const double c = 0.5 * dUz / r64;
+                    const double f3[3] = {c * d64[0], c * d64[1], c * d64[2]};
+                    cx += A_::convd(f3[0]);
+                    cy += A_::convd(f3[1]);
+                    cz += A_::convd(f3[2]);
+                    bad |= !isfinite(c);
+                    has_zbl = true;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+#pragma unroll
+                        for (int b = 0; b < 3; ++b) wz[3 * a + b] -= f3[a] * d64[b];
+                }
+            }
+            fi[0] += cx; fi[1] += cy; fi[2] += cz;
+            A_::add(&facc[m], -cx);
+            A_::add(&facc[ld + m], -cy);
+            A_::add(&facc[2 * ld + m], -cz);
+            w[0] -= fx * dx; w[1] -= fx * dy; w[2] -= fx * dz;
+            w[3] -= fy * dx; w[4] -= fy * dy; w[5] -= fy * dz;
+            w[6] -= fz * dx; w[7] -= fz * dy; w[8] -= fz * dz;
+        }
+        A_::add(&facc[k], fi[0]);
+        A_::add(&facc[ld + k], fi[1]);
+        A_::add(&facc[2 * ld + k], fi[2]);
+        e_site = (double)U + ez;
+        if (site_energy) site_energy[i_caller] = e_site;
+        if (bad) atomicOr(status, ST_NONFINITE);
+    }
+    tile_partials<R>(e_site, w, wz, has_zbl, partials + (size_t)blockIdx.x * NPART);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(TILE) k_radial_force(const Model<R> P, const Grid g,
+                                                       const typename V4<R>::T* __restrict__ pos4,
+                                                       const int* __restrict__ nbr,
+                                                       const int2* __restrict__ cnt,
+                                                       const R* __restrict__ br,
+                                                       typename Acc<R>::T* __restrict__ facc,
+                                                       double* __restrict__ partials,
+                                                       int* __restrict__ status)
+{
+    using A_ = Acc<R>;
+    using P4 = typename V4<R>::T;
+    __shared__ P4 s_off[27];
+    fill_stencil<R>(s_off, g);
+    const int k = blockIdx.x * TILE + threadIdx.x;
+    const size_t ld = (size_t)g.ld;
+    R w[9];
+    double wz[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) { w[t] = R(0); wz[t] = 0.0; }
+    if (k < g.n) {
+        const int2 c2 = cnt[k];
+        const int na = c2.x, total = c2.x + c2.y, M = g.M;
+        const P4 pi = pos4[k];
+        R bR[KR];
+#pragma unroll
+        for (int kk = 0; kk < KR; ++kk) bR[kk] = br[(size_t)kk * ld + k];
+        const R B0 = br[(size_t)KR * ld + k];
+        typename A_::T fi[3] = {0, 0, 0};
+        bool bad = false;
+        int ent_n = total > 0 ? nbr[(size_t)list_slot(0, na, M) * ld + k] : 0;
+        for (int s = 0; s < total; ++s) {
+            const int ent = ent_n;
+            if (s + 1 < total) ent_n = nbr[(size_t)list_slot(s + 1, na, M) * ld + k];
+            const int m = ent >> 5;
+            const P4 pj = pos4[m];
+            const P4 off = s_off[ent & 31];
+            const R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
+            const R r2 = dx * dx + dy * dy + dz * dz;
+            const R inv_r = nepm::nep_rsqrt(r2);
+            const R r = r2 * inv_r;
+            R T[KR], dT[KR], fc, dfc, dxdr;
+            nepm::cheb<KR, true>(r, P.inv_rcR, T, dT, fc, dfc, dxdr);
+            R s1 = B0, s2 = R(0);
+#pragma unroll
+            for (int kk = 0; kk < KR; ++kk) {
+                s1 += bR[kk] * T[kk];
+                s2 += bR[kk] * dT[kk];
+            }
+            const R fs = (dfc * s1 + fc * dxdr * s2) * inv_r;   // coefficient of d
+            const R fx = fs * dx, fy = fs * dy, fz = fs * dz;
+            bad |= !isfinite(fs);
+            const typename A_::T cx = A_::conv(fx), cy = A_::conv(fy), cz = A_::conv(fz);
+            fi[0] += cx; fi[1] += cy; fi[2] += cz;
+            A_::add(&facc[m], -cx);
+            A_::add(&facc[ld + m], -cy);
+            A_::add(&facc[2 * ld + m], -cz);
+            w[0] -= fx * dx; w[1] -= fx * dy; w[2] -= fx * dz;
+            w[3] -= fy * dx; w[4] -= fy * dy; w[5] -= fy * dz;
+            w[6] -= fz * dx; w[7] -= fz * dy; w[8] -= fz * dz;
+        }
+        A_::add(&facc[k], fi[0]);
+        A_::add(&facc[ld + k], fi[1]);
+        A_::add(&facc[2 * ld + k], fi[2]);
+        if (bad) atomicOr(status, ST_NONFINITE);
+    }
+    tile_partials<R>(0.0, w, wz, false, partials + (size_t)blockIdx.x * NPART);
+}
+
 // Forces back to caller order (FP64), accumulators reset to zero.
 template <typename R>
 __global__ void k_forces_out(int n, int ld, const int* __restrict__ perm,

@@ -58,8 +58,10 @@ struct nep_ctx {
     int2* cnt = nullptr;
     int* nbr = nullptr;
     void* facc = nullptr;
-    double* partials = nullptr;
+    double* partials = nullptr;      // 2 x tiles x NPART
     double* partials2 = nullptr;     // RED1_MAX x NPART
+    void* qr = nullptr;              // radial descriptor [NR][ld] (R)
+    void* br = nullptr;              // radial adjoint b_k, B0 [KR + 1][ld] (R)
     double* vpart = nullptr;
     int *count = nullptr, *start = nullptr, *scan_sums = nullptr;
     double* backup = nullptr;        // x, v, F copies for MD rollback
@@ -158,6 +160,7 @@ static void free_scratch(nep_ctx* ctx)
     free_dev(ctx->cell_of); free_dev(ctx->slot_of); free_dev(ctx->perm);
     free_dev(ctx->cell_sorted); free_dev(ctx->pos4); free_dev(ctx->cnt); free_dev(ctx->nbr);
     free_dev(ctx->facc); free_dev(ctx->partials); free_dev(ctx->partials2);
+    free_dev(ctx->qr); free_dev(ctx->br);
     free_dev(ctx->vpart); free_dev(ctx->backup);
     ctx->ld = 0;
     ctx->M = 0;
@@ -184,7 +187,10 @@ static int ensure_atoms(nep_ctx* ctx, int n, int M)
     CK(cudaMalloc(&ctx->nbr, sizeof(int) * (size_t)ld * MM));
     CK(cudaMalloc(&ctx->facc, acc * 3 * (size_t)ld));
     CK(cudaMemset(ctx->facc, 0, acc * 3 * (size_t)ld));
-    CK(cudaMalloc(&ctx->partials, sizeof(double) * NPART * (size_t)tiles));
+    CK(cudaMalloc(&ctx->partials, sizeof(double) * NPART * 2 * (size_t)tiles));
+    const size_t rsz = ctx->precision == NEP_FP32 ? sizeof(float) : sizeof(double);
+    CK(cudaMalloc(&ctx->qr, rsz * NR * (size_t)ld));
+    CK(cudaMalloc(&ctx->br, rsz * (KR + 1) * (size_t)ld));
     CK(cudaMalloc(&ctx->partials2, sizeof(double) * NPART * (size_t)RED1_MAX));
     CK(cudaMalloc(&ctx->vpart, sizeof(double) * 2 * (size_t)vb));
     CK(cudaMalloc(&ctx->backup, sizeof(double) * 9 * (size_t)ld));
@@ -295,24 +301,34 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
         ctx->start, ctx->nbr, ctx->cnt, ctx->status, ctx->status + 1, ctx->pairs);
     count_launch(ctx);
     const int tiles = (n + TILE - 1) / TILE;
+    // the three force kernels are timed together when timing is on
     if (timed_slot >= 0) {
         if (ctx->capturing)
             CK(cudaEventRecordWithFlags(ctx->events[2 * timed_slot], s, cudaEventRecordExternal));
         else
             CK(cudaEventRecord(ctx->events[2 * timed_slot], s));
     }
-    // neighbour entries of a block are staged in shared memory when they fit
+    // radial descriptor (all pairs, small state)
+    const typename V4<R>::T* p4 = (const typename V4<R>::T*)ctx->pos4;
+    typename Acc<R>::T* fa = (typename Acc<R>::T*)ctx->facc;
+    k_radial_q<R><<<(n + 127) / 128, 128, 0, s>>>(P, g, p4, ctx->nbr, ctx->cnt, (R*)ctx->qr);
+    count_launch(ctx);
+    // angular part, network, ZBL (the block's angular entries staged in shared
+    // memory when they fit)
     const int stage_slots = ctx->M < STAGE_MAX_SLOTS ? ctx->M : STAGE_MAX_SLOTS;
     const size_t stage_bytes = sizeof(int) * (size_t)stage_slots * TILE;
     if (!ctx->nep_smem_set[sizeof(R) == 4 ? 0 : 1]) {
-        CK(cudaFuncSetAttribute(k_nep<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        CK(cudaFuncSetAttribute(k_nep_ang<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(sizeof(int) * STAGE_MAX_SLOTS * TILE)));
         ctx->nep_smem_set[sizeof(R) == 4 ? 0 : 1] = 1;
     }
-    k_nep<R><<<tiles, TILE, stage_bytes, s>>>(P, g, (const typename V4<R>::T*)ctx->pos4, ctx->nbr,
-                                             ctx->cnt, ctx->perm, x,
-                                             (typename Acc<R>::T*)ctx->facc, ctx->partials,
-                                             site_energy, ctx->status, stage_slots);
+    k_nep_ang<R><<<tiles, TILE, stage_bytes, s>>>(P, g, p4, ctx->nbr, ctx->cnt, ctx->perm, x,
+                                                 (const R*)ctx->qr, (R*)ctx->br, fa, ctx->partials,
+                                                 site_energy, ctx->status, stage_slots);
+    count_launch(ctx);
+    // radial pair forces (all pairs, small state)
+    k_radial_force<R><<<tiles, TILE, 0, s>>>(P, g, p4, ctx->nbr, ctx->cnt, (const R*)ctx->br, fa,
+                                            ctx->partials + (size_t)tiles * NPART, ctx->status);
     count_launch(ctx);
     if (timed_slot >= 0) {
         if (ctx->capturing)
@@ -325,10 +341,10 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     count_launch(ctx);
     {
         // two-stage fixed-order sum of the per-tile energy/virial partials
-        const int chunk = (tiles + RED1_MAX - 1) / RED1_MAX > 64 ? (tiles + RED1_MAX - 1) / RED1_MAX
-                                                                 : 64;
-        const int nb1 = (tiles + chunk - 1) / chunk;
-        k_reduce_stage1<<<nb1, 256, 0, s>>>(ctx->partials, tiles, chunk, ctx->partials2);
+        const int nt = 2 * tiles;   // angular/energy tiles, then radial tiles
+        const int chunk = (nt + RED1_MAX - 1) / RED1_MAX > 64 ? (nt + RED1_MAX - 1) / RED1_MAX : 64;
+        const int nb1 = (nt + chunk - 1) / chunk;
+        k_reduce_stage1<<<nb1, 256, 0, s>>>(ctx->partials, nt, chunk, ctx->partials2);
         count_launch(ctx);
         k_reduce_partials<<<1, 256, 0, s>>>(ctx->partials2, nb1, ctx->result);
         count_launch(ctx);
