@@ -31,7 +31,7 @@ constexpr int NPART = 10;              // energy + 9 virial components per tile
 constexpr int ST_OVERFLOW = 1, ST_NONFINITE = 2, ST_FORCE_RANGE = 4;
 
 template <typename R> struct V4 { using T = float4; };
-template <> struct V4<double> { using T = double4_32a; };
+template <> struct V4<double> { using T = double4; };
 
 // Model constants passed by value as a kernel argument (constant bank).
 template <typename R>
@@ -305,8 +305,7 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
     }
 }
 
-// Warp-per-cell neighbour build (row-major lists: entry s of atom k at
-// nbr[k * M + s]).  The warp copies the atoms of its cell's 27
+// Warp-per-cell neighbour build.  The warp copies the atoms of its cell's 27
 // stencil cells into shared memory, shifted by their periodic offsets so that
 // d = candidate - atom, then takes the cell's atoms one at a time: the lanes
 // test 32 candidates at once and compact the hits with ballots (angular pairs
@@ -337,6 +336,7 @@ __global__ void __launch_bounds__(NBR_WARPS * 32) k_neighbors_warp(
         const int cz = c % ncz, cy = (c / ncz) % ncy, cx = c / (ncz * ncy);
         const int a0 = start[c], a1 = start[c + 1];
         const int M = g.M;
+        const size_t ld = (size_t)g.ld;
         const R lx = (R)g.lc[0], ly = (R)g.lc[1], lz = (R)g.lc[2];
         // lanes 0..26 look up the stencil cells (range, staged offset)
         int nb = 0;
@@ -404,11 +404,11 @@ __global__ void __launch_bounds__(NBR_WARPS * 32) k_neighbors_warp(
                     // in bounds always; entries of an overflowing list are never used
                     if (hitA) {
                         const int slot = na + __popc(bA & lt);
-                        if (slot < M) nbr[(size_t)k * M + slot] = ent;
+                        if (slot < M) nbr[(size_t)slot * ld + k] = ent;
                     }
                     if (hitR) {
                         const int u = nro + __popc(bR & lt);
-                        if (u < M) nbr[(size_t)k * M + (M - 1 - u)] = ent;
+                        if (u < M) nbr[(size_t)(M - 1 - u) * ld + k] = ent;
                     }
                     na += __popc(bA);
                     nro += __popc(bR);
@@ -440,8 +440,8 @@ __global__ void __launch_bounds__(NBR_WARPS * 32) k_neighbors_warp(
                             const bool ang = r2 < rcA2;
                             if (sa + sro < M) {
                                 const int ent = (m << 5) | code;
-                                if (ang) nbr[(size_t)k * M + (sa++)] = ent;
-                                else nbr[(size_t)k * M + (M - 1 - sro++)] = ent;
+                                if (ang) nbr[(size_t)(sa++) * ld + k] = ent;
+                                else nbr[(size_t)(M - 1 - sro++) * ld + k] = ent;
                             }
                             if (ang) ++na; else ++nro;
                         }
@@ -920,8 +920,7 @@ __global__ void __launch_bounds__(TILE) k_nep(const Model<R> P, const Grid g,
 }
 
 // ----------------------------------------------------------------------------
-// The force evaluation split by register footprint (row-major neighbour
-// lists from k_neighbors_warp).  Only the ~14 angular
+// The force evaluation split by register footprint.  Only the ~14 angular
 // pairs of an atom need its 120 angular accumulators; the ~58 radial terms
 // need 9.  So:
 //   k_radial_q     all pairs  -> q_n (radial descriptor)            small state
@@ -955,11 +954,10 @@ __global__ void __launch_bounds__(128) k_radial_q(const Model<R> P, const Grid g
     R Sb[KR];
 #pragma unroll
     for (int kk = 0; kk < KR; ++kk) Sb[kk] = R(0);
-    const int* row = nbr + (size_t)k * M;
-    int ent_n = total > 0 ? row[list_slot(0, na, M)] : 0;
+    int ent_n = total > 0 ? nbr[(size_t)list_slot(0, na, M) * ld + k] : 0;
     for (int s = 0; s < total; ++s) {
         const int ent = ent_n;
-        if (s + 1 < total) ent_n = row[list_slot(s + 1, na, M)];
+        if (s + 1 < total) ent_n = nbr[(size_t)list_slot(s + 1, na, M) * ld + k];
         const P4 pj = pos4[ent >> 5];
         const P4 off = s_off[ent & 31];
         const R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
@@ -1076,9 +1074,8 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
     atomicMax(&s_max, na);
     __syncthreads();
     const bool staged = s_max <= stage_slots;
-    const int* row = nbr + (size_t)k * g.M;
     if (staged)
-        for (int s = 0; s < na; ++s) s_ent[s * TILE + threadIdx.x] = row[s];
+        for (int s = 0; s < na; ++s) s_ent[s * TILE + threadIdx.x] = nbr[(size_t)s * ld + k];
     double e_site = 0.0;
     R w[9];
     double wz[9];
@@ -1089,7 +1086,7 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
     if (k < g.n) {
         const P4 pi = pos4[k];
         auto entry = [&](int s) -> int {
-            return staged ? s_ent[s * TILE + threadIdx.x] : row[s];
+            return staged ? s_ent[s * TILE + threadIdx.x] : nbr[(size_t)s * ld + k];
         };
         R A[NA][NLM];
 #pragma unroll
@@ -1234,11 +1231,10 @@ __global__ void __launch_bounds__(TILE) k_radial_force(const Model<R> P, const G
         const R B0 = br[(size_t)KR * ld + k];
         typename A_::T fi[3] = {0, 0, 0};
         bool bad = false;
-        const int* row = nbr + (size_t)k * M;
-        int ent_n = total > 0 ? row[list_slot(0, na, M)] : 0;
+        int ent_n = total > 0 ? nbr[(size_t)list_slot(0, na, M) * ld + k] : 0;
         for (int s = 0; s < total; ++s) {
             const int ent = ent_n;
-            if (s + 1 < total) ent_n = row[list_slot(s + 1, na, M)];
+            if (s + 1 < total) ent_n = nbr[(size_t)list_slot(s + 1, na, M) * ld + k];
             const int m = ent >> 5;
             const P4 pj = pos4[m];
             const P4 off = s_off[ent & 31];
