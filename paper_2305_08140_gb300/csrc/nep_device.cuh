@@ -305,171 +305,6 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
     }
 }
 
-// Warp-per-cell neighbour build.  The warp copies the atoms of its cell's 27
-// stencil cells into shared memory, shifted by their periodic offsets so that
-// d = candidate - atom, then takes the cell's atoms one at a time: the lanes
-// test 32 candidates at once and compact the hits with ballots (angular pairs
-// from the front of the atom's list, radial-only pairs from the back, in
-// stencil order).  A cell whose stencil holds more candidates than fit falls
-// back to one lane per atom reading the candidates from global memory.
-template <typename R> struct NbrCap { static constexpr int v = 512; };
-template <> struct NbrCap<double> { static constexpr int v = 256; };
-constexpr int NBR_WARPS = 4;
-
-template <typename R>
-__global__ void __launch_bounds__(NBR_WARPS * 32) k_neighbors_warp(
-    Grid g, int ncell, R rcR2, R rcA2, const typename V4<R>::T* __restrict__ pos4,
-    const int* __restrict__ start, int* __restrict__ nbr, int2* __restrict__ cnt,
-    int* __restrict__ status, int* __restrict__ maxc, unsigned long long* __restrict__ pairs)
-{
-    using P4 = typename V4<R>::T;
-    constexpr int CAP = NbrCap<R>::v;
-    __shared__ P4 cand[NBR_WARPS][CAP];
-    __shared__ int s_b0[NBR_WARPS][27], s_nb[NBR_WARPS][27], s_off[NBR_WARPS][27];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c = blockIdx.x * NBR_WARPS + warp;
-    // per-lane statistics (each atom counted on exactly one lane)
-    int wmax_tot = 0, wmax_na = 0;
-    unsigned long long wpairs_r = 0, wpairs_a = 0;
-    if (c < ncell) {
-        const int ncx = g.nc[0], ncy = g.nc[1], ncz = g.nc[2];
-        const int cz = c % ncz, cy = (c / ncz) % ncy, cx = c / (ncz * ncy);
-        const int a0 = start[c], a1 = start[c + 1];
-        const int M = g.M;
-        const size_t ld = (size_t)g.ld;
-        const R lx = (R)g.lc[0], ly = (R)g.lc[1], lz = (R)g.lc[2];
-        // lanes 0..26 look up the stencil cells (range, staged offset)
-        int nb = 0;
-        if (lane < 27) {
-            const int ox = lane / 9 - 1, oy = (lane / 3) % 3 - 1, oz = lane % 3 - 1;
-            int X = cx + ox, Y = cy + oy, Z = cz + oz;
-            bool ok = a1 > a0;
-            if (g.pbc[0]) { X += X < 0 ? ncx : 0; X -= X >= ncx ? ncx : 0; } else ok &= X >= 0 && X < ncx;
-            if (g.pbc[1]) { Y += Y < 0 ? ncy : 0; Y -= Y >= ncy ? ncy : 0; } else ok &= Y >= 0 && Y < ncy;
-            if (g.pbc[2]) { Z += Z < 0 ? ncz : 0; Z -= Z >= ncz ? ncz : 0; } else ok &= Z >= 0 && Z < ncz;
-            int b0 = 0;
-            if (ok) {
-                const int c2 = (X * ncy + Y) * ncz + Z;
-                b0 = start[c2];
-                nb = start[c2 + 1] - b0;
-            }
-            s_b0[warp][lane] = b0;
-            s_nb[warp][lane] = nb;
-        }
-        int incl = nb;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        const int T = __shfl_sync(0xffffffffu, incl, 31);
-        if (lane < 27) s_off[warp][lane] = incl - nb;
-        __syncwarp();
-        if (a1 > a0 && T <= CAP) {
-            // stage the candidates, shifted by their stencil offsets
-            for (int code = 0; code < 27; ++code) {
-                const int cb0 = s_b0[warp][code], cn = s_nb[warp][code], co = s_off[warp][code];
-                const R sx = R(code / 9 - 1) * lx, sy = R((code / 3) % 3 - 1) * ly,
-                        sz = R(code % 3 - 1) * lz;
-                for (int j = lane; j < cn; j += 32) {
-                    P4 q = pos4[cb0 + j];
-                    q.x += sx; q.y += sy; q.z += sz;
-                    if constexpr (sizeof(R) == 4) q.w = __int_as_float(((cb0 + j) << 5) | code);
-                    else q.w = (double)(((cb0 + j) << 5) | code);
-                    cand[warp][co + j] = q;
-                }
-            }
-            __syncwarp();
-            const unsigned lt = (1u << lane) - 1u;
-            for (int k = a0; k < a1; ++k) {
-                const P4 p = pos4[k];
-                int na = 0, nro = 0;
-                for (int q0 = 0; q0 < T; q0 += 32) {
-                    const int q = q0 + lane;
-                    bool hitA = false, hitR = false;
-                    int ent = 0;
-                    if (q < T) {
-                        const P4 cq = cand[warp][q];
-                        if constexpr (sizeof(R) == 4) ent = __float_as_int(cq.w);
-                        else ent = (int)cq.w;
-                        const R dx = cq.x - p.x, dy = cq.y - p.y, dz = cq.z - p.z;
-                        const R r2 = dx * dx + dy * dy + dz * dz;
-                        if (r2 < rcR2 && (ent >> 5) != k) {
-                            hitA = r2 < rcA2;
-                            hitR = !hitA;
-                        }
-                    }
-                    const unsigned bA = __ballot_sync(0xffffffffu, hitA);
-                    const unsigned bR = __ballot_sync(0xffffffffu, hitR);
-                    // in bounds always; entries of an overflowing list are never used
-                    if (hitA) {
-                        const int slot = na + __popc(bA & lt);
-                        if (slot < M) nbr[(size_t)slot * ld + k] = ent;
-                    }
-                    if (hitR) {
-                        const int u = nro + __popc(bR & lt);
-                        if (u < M) nbr[(size_t)(M - 1 - u) * ld + k] = ent;
-                    }
-                    na += __popc(bA);
-                    nro += __popc(bR);
-                }
-                if (lane == 0) {
-                    cnt[k] = na + nro <= M ? make_int2(na, nro) : make_int2(0, 0);
-                    if (na + nro > M) atomicOr(status, ST_OVERFLOW);
-                    wmax_tot = max(wmax_tot, na + nro);
-                    wmax_na = max(wmax_na, na);
-                    wpairs_r += (unsigned long long)(na + nro);
-                    wpairs_a += (unsigned long long)na;
-                }
-            }
-        } else if (a1 > a0) {
-            // dense stencil: one lane per atom of the cell, candidates from global memory
-            for (int k = a0 + lane; k < a1; k += 32) {
-                const P4 p = pos4[k];
-                int na = 0, nro = 0, sa = 0, sro = 0;
-                for (int code = 0; code < 27; ++code) {
-                    const int cb0 = s_b0[warp][code], cn = s_nb[warp][code];
-                    const R sx = R(code / 9 - 1) * lx, sy = R((code / 3) % 3 - 1) * ly,
-                            sz = R(code % 3 - 1) * lz;
-                    for (int j = 0; j < cn; ++j) {
-                        const int m = cb0 + j;
-                        const P4 q = pos4[m];
-                        const R dx = (q.x + sx) - p.x, dy = (q.y + sy) - p.y, dz = (q.z + sz) - p.z;
-                        const R r2 = dx * dx + dy * dy + dz * dz;
-                        if (r2 < rcR2 && m != k) {
-                            const bool ang = r2 < rcA2;
-                            if (sa + sro < M) {
-                                const int ent = (m << 5) | code;
-                                if (ang) nbr[(size_t)(sa++) * ld + k] = ent;
-                                else nbr[(size_t)(M - 1 - sro++) * ld + k] = ent;
-                            }
-                            if (ang) ++na; else ++nro;
-                        }
-                    }
-                }
-                cnt[k] = make_int2(sa, sro);
-                if (na + nro > M) atomicOr(status, ST_OVERFLOW);
-                wmax_tot = max(wmax_tot, na + nro);
-                wmax_na = max(wmax_na, na);
-                wpairs_r += (unsigned long long)(na + nro);
-                wpairs_a += (unsigned long long)na;
-            }
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        wmax_tot = max(wmax_tot, __shfl_xor_sync(0xffffffffu, wmax_tot, o));
-        wmax_na = max(wmax_na, __shfl_xor_sync(0xffffffffu, wmax_na, o));
-        wpairs_r += __shfl_xor_sync(0xffffffffu, wpairs_r, o);
-        wpairs_a += __shfl_xor_sync(0xffffffffu, wpairs_a, o);
-    }
-    if (lane == 0) {
-        if (wmax_tot > 0) atomicMax(&maxc[0], wmax_tot);
-        if (wmax_na > 0) atomicMax(&maxc[1], wmax_na);
-        if (wpairs_r) atomicAdd(&pairs[0], wpairs_r);
-        if (wpairs_a) atomicAdd(&pairs[1], wpairs_a);
-    }
-}
-
 // ----------------------------------------------------------------------------
 // Force accumulation policy
 // ----------------------------------------------------------------------------

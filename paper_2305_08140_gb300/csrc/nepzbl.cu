@@ -296,9 +296,9 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     k_cell_finalize<R><<<(ncell + 127) / 128, 128, 0, s>>>(
         g, ncell, ctx->start, ctx->perm, x, types, (typename V4<R>::T*)ctx->pos4, ctx->cell_sorted);
     count_launch(ctx);
-    k_neighbors_warp<R><<<(ncell + NBR_WARPS - 1) / NBR_WARPS, NBR_WARPS * 32, 0, s>>>(
-        g, ncell, (R)(P.rcR2), (R)(P.rcA2), (const typename V4<R>::T*)ctx->pos4, ctx->start,
-        ctx->nbr, ctx->cnt, ctx->status, ctx->status + 1, ctx->pairs);
+    k_neighbors<R><<<(n + 127) / 128, 128, 0, s>>>(
+        g, (R)(P.rcR2), (R)(P.rcA2), (const typename V4<R>::T*)ctx->pos4, ctx->cell_sorted,
+        ctx->start, ctx->nbr, ctx->cnt, ctx->status, ctx->status + 1, ctx->pairs);
     count_launch(ctx);
     const int tiles = (n + TILE - 1) / TILE;
     // the three force kernels are timed together when timing is on
