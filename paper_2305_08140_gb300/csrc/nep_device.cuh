@@ -31,7 +31,7 @@ constexpr int NPART = 10;              // energy + 9 virial components per tile
 constexpr int ST_OVERFLOW = 1, ST_NONFINITE = 2, ST_FORCE_RANGE = 4;
 
 template <typename R> struct V4 { using T = float4; };
-template <> struct V4<double> { using T = double4; };
+template <> struct V4<double> { using T = double4_32a; };
 
 // Model constants passed by value as a kernel argument (constant bank).
 template <typename R>

@@ -175,7 +175,7 @@ static int ensure_atoms(nep_ctx* ctx, int n, int M)
     cudaDeviceSynchronize();
     free_scratch(ctx);
     size_t acc = ctx->precision == NEP_FP32 ? sizeof(long long) : sizeof(double);
-    size_t p4 = ctx->precision == NEP_FP32 ? sizeof(float4) : sizeof(double4);
+    size_t p4 = ctx->precision == NEP_FP32 ? sizeof(float4) : sizeof(double4_32a);
     int tiles = (ld + TILE - 1) / TILE;
     int vb = (ld + 255) / 256;
     CK(cudaMalloc(&ctx->cell_of, sizeof(int) * ld));
