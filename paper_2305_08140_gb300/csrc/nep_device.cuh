@@ -890,7 +890,7 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
                                                   const int* __restrict__ perm,
                                                   const double* __restrict__ x64,
                                                   const R* __restrict__ qr,
-                                                  R* __restrict__ br,
+                                                  typename V4<R>::T* __restrict__ br,
                                                   typename Acc<R>::T* __restrict__ facc,
                                                   double* __restrict__ partials,
                                                   double* __restrict__ site_energy,
@@ -961,9 +961,15 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
         for (int n = 0; n < NR; ++n) qR[n] = qr[(size_t)n * ld + k];
         R bR[KR], B0;
         const R U = network_adjoint<R>(P, qR, A, bR, B0);
-#pragma unroll
-        for (int kk = 0; kk < KR; ++kk) br[(size_t)kk * ld + k] = bR[kk];
-        br[(size_t)KR * ld + k] = B0;
+        {
+            P4 b0v, b1v, b2v;
+            b0v.x = bR[0]; b0v.y = bR[1]; b0v.z = bR[2]; b0v.w = bR[3];
+            b1v.x = bR[4]; b1v.y = bR[5]; b1v.z = bR[6]; b1v.w = bR[7];
+            b2v.x = bR[8]; b2v.y = B0; b2v.z = R(0); b2v.w = R(0);
+            br[3 * (size_t)k] = b0v;
+            br[3 * (size_t)k + 1] = b1v;
+            br[3 * (size_t)k + 2] = b2v;
+        }
 
         typename A_::T fi[3] = {0, 0, 0};
         double ez = 0.0;
@@ -1036,12 +1042,18 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
     tile_partials<R>(e_site, w, wz, has_zbl, partials + (size_t)blockIdx.x * NPART);
 }
 
+// Radial pair forces by gathering: with the radial adjoint of both atoms,
+//   f_ij - f_ji = [f_c' (B0_i + B0_j + sum_k (b_i + b_j)_k T_k)
+//                  + f_c x' sum_k (b_i + b_j)_k T'_k] u_ij,
+// so each atom sums its own radial force from its neighbours' packed adjoint
+// (bp[k] = (b_0..b_8, B0), 12 values per atom) without atomics; the virial is
+// -1/2 sum_i sum_j (f_ij - f_ji) (x) d_ij.
 template <typename R>
 __global__ void __launch_bounds__(TILE) k_radial_force(const Model<R> P, const Grid g,
                                                        const typename V4<R>::T* __restrict__ pos4,
                                                        const int* __restrict__ nbr,
                                                        const int2* __restrict__ cnt,
-                                                       const R* __restrict__ br,
+                                                       const typename V4<R>::T* __restrict__ bp,
                                                        typename Acc<R>::T* __restrict__ facc,
                                                        double* __restrict__ partials,
                                                        int* __restrict__ status)
@@ -1060,18 +1072,15 @@ __global__ void __launch_bounds__(TILE) k_radial_force(const Model<R> P, const G
         const int2 c2 = cnt[k];
         const int na = c2.x, total = c2.x + c2.y, M = g.M;
         const P4 pi = pos4[k];
-        R bR[KR];
-#pragma unroll
-        for (int kk = 0; kk < KR; ++kk) bR[kk] = br[(size_t)kk * ld + k];
-        const R B0 = br[(size_t)KR * ld + k];
-        typename A_::T fi[3] = {0, 0, 0};
-        bool bad = false;
+        const P4 bi0 = bp[3 * (size_t)k], bi1 = bp[3 * (size_t)k + 1], bi2 = bp[3 * (size_t)k + 2];
+        R fx = R(0), fy = R(0), fz = R(0);
         int ent_n = total > 0 ? nbr[(size_t)list_slot(0, na, M) * ld + k] : 0;
         for (int s = 0; s < total; ++s) {
             const int ent = ent_n;
             if (s + 1 < total) ent_n = nbr[(size_t)list_slot(s + 1, na, M) * ld + k];
             const int m = ent >> 5;
             const P4 pj = pos4[m];
+            const P4 bj0 = bp[3 * (size_t)m], bj1 = bp[3 * (size_t)m + 1], bj2 = bp[3 * (size_t)m + 2];
             const P4 off = s_off[ent & 31];
             const R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
             const R r2 = dx * dx + dy * dy + dz * dz;
@@ -1079,28 +1088,28 @@ __global__ void __launch_bounds__(TILE) k_radial_force(const Model<R> P, const G
             const R r = r2 * inv_r;
             R T[KR], dT[KR], fc, dfc, dxdr;
             nepm::cheb<KR, true>(r, P.inv_rcR, T, dT, fc, dfc, dxdr);
-            R s1 = B0, s2 = R(0);
+            const R b[KR] = {bi0.x + bj0.x, bi0.y + bj0.y, bi0.z + bj0.z, bi0.w + bj0.w,
+                             bi1.x + bj1.x, bi1.y + bj1.y, bi1.z + bj1.z, bi1.w + bj1.w,
+                             bi2.x + bj2.x};
+            R s1 = bi2.y + bj2.y, s2 = R(0);
 #pragma unroll
             for (int kk = 0; kk < KR; ++kk) {
-                s1 += bR[kk] * T[kk];
-                s2 += bR[kk] * dT[kk];
+                s1 += b[kk] * T[kk];
+                s2 += b[kk] * dT[kk];
             }
-            const R fs = (dfc * s1 + fc * dxdr * s2) * inv_r;   // coefficient of d
-            const R fx = fs * dx, fy = fs * dy, fz = fs * dz;
-            bad |= !isfinite(fs);
-            const typename A_::T cx = A_::conv(fx), cy = A_::conv(fy), cz = A_::conv(fz);
-            fi[0] += cx; fi[1] += cy; fi[2] += cz;
-            A_::add(&facc[m], -cx);
-            A_::add(&facc[ld + m], -cy);
-            A_::add(&facc[2 * ld + m], -cz);
-            w[0] -= fx * dx; w[1] -= fx * dy; w[2] -= fx * dz;
-            w[3] -= fy * dx; w[4] -= fy * dy; w[5] -= fy * dz;
-            w[6] -= fz * dx; w[7] -= fz * dy; w[8] -= fz * dz;
+            const R fs = (dfc * s1 + fc * dxdr * s2) * inv_r;   // (f_ij - f_ji) = fs d
+            const R gx = fs * dx, gy = fs * dy, gz = fs * dz;
+            fx += gx; fy += gy; fz += gz;
+            w[0] -= gx * dx; w[1] -= gx * dy; w[2] -= gx * dz;
+            w[3] -= gy * dx; w[4] -= gy * dy; w[5] -= gy * dz;
+            w[6] -= gz * dx; w[7] -= gz * dy; w[8] -= gz * dz;
         }
-        A_::add(&facc[k], fi[0]);
-        A_::add(&facc[ld + k], fi[1]);
-        A_::add(&facc[2 * ld + k], fi[2]);
-        if (bad) atomicOr(status, ST_NONFINITE);
+        if (!isfinite(fx + fy + fz)) atomicOr(status, ST_NONFINITE);
+        A_::add(&facc[k], A_::conv(fx));
+        A_::add(&facc[ld + k], A_::conv(fy));
+        A_::add(&facc[2 * ld + k], A_::conv(fz));
+#pragma unroll
+        for (int t = 0; t < 9; ++t) w[t] *= R(0.5);
     }
     tile_partials<R>(0.0, w, wz, false, partials + (size_t)blockIdx.x * NPART);
 }

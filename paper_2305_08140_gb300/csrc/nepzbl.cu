@@ -61,7 +61,7 @@ struct nep_ctx {
     double* partials = nullptr;      // 2 x tiles x NPART
     double* partials2 = nullptr;     // RED1_MAX x NPART
     void* qr = nullptr;              // radial descriptor [NR][ld] (R)
-    void* br = nullptr;              // radial adjoint b_k, B0 [KR + 1][ld] (R)
+    void* br = nullptr;              // radial adjoint (b_0..b_8, B0, 0, 0) per atom: 3 x V4
     double* vpart = nullptr;
     int *count = nullptr, *start = nullptr, *scan_sums = nullptr;
     double* backup = nullptr;        // x, v, F copies for MD rollback
@@ -190,7 +190,7 @@ static int ensure_atoms(nep_ctx* ctx, int n, int M)
     CK(cudaMalloc(&ctx->partials, sizeof(double) * NPART * 2 * (size_t)tiles));
     const size_t rsz = ctx->precision == NEP_FP32 ? sizeof(float) : sizeof(double);
     CK(cudaMalloc(&ctx->qr, rsz * NR * (size_t)ld));
-    CK(cudaMalloc(&ctx->br, rsz * (KR + 1) * (size_t)ld));
+    CK(cudaMalloc(&ctx->br, rsz * 12 * (size_t)ld));
     CK(cudaMalloc(&ctx->partials2, sizeof(double) * NPART * (size_t)RED1_MAX));
     CK(cudaMalloc(&ctx->vpart, sizeof(double) * 2 * (size_t)vb));
     CK(cudaMalloc(&ctx->backup, sizeof(double) * 9 * (size_t)ld));
@@ -323,11 +323,12 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
         ctx->nep_smem_set[sizeof(R) == 4 ? 0 : 1] = 1;
     }
     k_nep_ang<R><<<tiles, TILE, stage_bytes, s>>>(P, g, p4, ctx->nbr, ctx->cnt, ctx->perm, x,
-                                                 (const R*)ctx->qr, (R*)ctx->br, fa, ctx->partials,
-                                                 site_energy, ctx->status, stage_slots);
+                                                 (const R*)ctx->qr, (typename V4<R>::T*)ctx->br, fa,
+                                                 ctx->partials, site_energy, ctx->status, stage_slots);
     count_launch(ctx);
     // radial pair forces (all pairs, small state)
-    k_radial_force<R><<<tiles, TILE, 0, s>>>(P, g, p4, ctx->nbr, ctx->cnt, (const R*)ctx->br, fa,
+    k_radial_force<R><<<tiles, TILE, 0, s>>>(P, g, p4, ctx->nbr, ctx->cnt,
+                                            (const typename V4<R>::T*)ctx->br, fa,
                                             ctx->partials + (size_t)tiles * NPART, ctx->status);
     count_launch(ctx);
     if (timed_slot >= 0) {
