@@ -166,6 +166,79 @@ def cpu_baseline_sample(seconds_hint: float = 20.0) -> dict:
                        f"force evaluations in {dt:.1f} s; value counts atom-evaluations/s")}
 
 
+def _time_md(N, nep, s, steps, warm, dev, d_max=0.0, chunk=25):
+    """Atom-steps/s of `steps` graph-replayed MD steps (CUDA events)."""
+    import torch
+    st = N.MDState(N.to_device_soa(s.pos, dev), N.to_device_soa(s.vel, dev), s.box, s.pbc,
+                   dt_max=1.0, d_max=d_max)
+    nep.set_option(N.NEP_OPT_GRAPH_CHUNK, min(chunk, steps))
+    nep.md(st, warm)
+    nep.md(st, min(chunk, steps))
+    if steps % chunk and steps > chunk:
+        nep.md(st, steps % chunk)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    nep.md(st, steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"value": s.n * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+            "steps": steps, "atoms": s.n, "sim_time_fs": st.time}
+
+
+def other_configs(dev):
+    """Throughput of the other benchmark workloads (same library, same kernels)."""
+    import torch
+    from paper_2305_08140_gb300 import nepzbl as N
+    model = I.nep_model(1)
+    out = {}
+    # 2,000-atom bcc W: plain FP64 as configured, and the FP32 path; 100 NVE steps
+    s = I.c1()
+    for prec in ("fp64", "fp32"):
+        nep = N.NEP(model, prec)
+        out[f"c1_2000_{prec}"] = _time_md(N, nep, s, 100, 3, dev)
+        nep.close()
+    # 128,000-atom bcc W at 1000 K: FP32 path (1,000 steps) vs plain FP64 path (100 steps)
+    s = I.c2()
+    nep = N.NEP(model, "fp32")
+    out["c2_128000_fp32"] = _time_md(N, nep, s, 1000, 3, dev)
+    nep.close()
+    nep = N.NEP(model, "fp64")
+    out["c2_128000_fp64"] = _time_md(N, nep, s, 100, 3, dev)
+    nep.close()
+    # 250,000 atoms with a dense clump, variable time step (0.01 A per step), 500 steps
+    s = I.c3()
+    nep = N.NEP(model, "fp32")
+    out["c3_250000_fp32_variable_dt"] = _time_md(N, nep, s, 500, 3, dev, d_max=0.01)
+    nep.close()
+    # 512 small periodic boxes: one persistent launch of forward + energy/force loss +
+    # parameter gradient (targets from the seed-101 model evaluated by the same library)
+    structs = I.c4()
+    b = N.Batch(structs, dev)
+    tgt = N.NEP(I.nep_model(101), "fp32")
+    Et, Ft = tgt.batch_forward(b)
+    tgt.close()
+    nep = N.NEP(model, "fp32")
+    bt, per = nep.batch_autotune(b, Et, Ft)
+    for _ in range(3):
+        nep.batch_loss_grad(b, Et, Ft)
+    torch.cuda.synchronize()
+    reps = 20
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        L, g, E, F = nep.batch_loss_grad(b, Et, Ft)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / reps
+    out["c4_512_configs_loss_grad_fp32"] = {
+        "value": b.N / dt, "unit": "atom-gradients/s", "ms_per_step": dt * 1e3,
+        "configs": b.S, "atoms": b.N, "loss": L, "autotune": {"threads": bt, "ctas_per_sm": per},
+        "note": "host-timed synchronous API call (forward + loss + gradient)"}
+    nep.close()
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -313,6 +386,11 @@ def run_ours(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.skip_cpu:
         cpu = cpu_baseline_sample()
+    others = None
+    if rank == 0 and not args.skip_extras:
+        del st
+        torch.cuda.empty_cache()
+        others = other_configs(dev)
 
     if dist:
         dist.barrier()
@@ -342,6 +420,7 @@ def run_ours(args):
                      "kernel_share": stats["timed_ms"] / ms if ms > 0 else None,
                      "pairs_radial": pr, "pairs_angular": pa},
         "fp64_path": fp64,
+        "other_configs": others,
         "e2e": e2e,
         "cpu_baseline": cpu,
     }
@@ -357,6 +436,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-extras", action="store_true",
+                    help="skip the measurements of the other workloads")
     ap.add_argument("--ncell", type=int, default=160,
                     help="slab size in bcc cells per side (160 = the 8,192,000-atom workload; "
                          "smaller values only for profiling)")
