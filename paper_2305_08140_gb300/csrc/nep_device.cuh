@@ -789,11 +789,16 @@ __global__ void __launch_bounds__(128) k_radial_q(const Model<R> P, const Grid g
     R Sb[KR];
 #pragma unroll
     for (int kk = 0; kk < KR; ++kk) Sb[kk] = R(0);
+    // two-stage prefetch: entry s + 2 and position s + 1 in flight during pair s
     int ent_n = total > 0 ? nbr[(size_t)list_slot(0, na, M) * ld + k] : 0;
+    int ent_nn = total > 1 ? nbr[(size_t)list_slot(1, na, M) * ld + k] : 0;
+    P4 pj_n = total > 0 ? pos4[ent_n >> 5] : pi;
     for (int s = 0; s < total; ++s) {
         const int ent = ent_n;
-        if (s + 1 < total) ent_n = nbr[(size_t)list_slot(s + 1, na, M) * ld + k];
-        const P4 pj = pos4[ent >> 5];
+        const P4 pj = pj_n;
+        ent_n = ent_nn;
+        if (s + 1 < total) pj_n = pos4[ent_n >> 5];
+        if (s + 2 < total) ent_nn = nbr[(size_t)list_slot(s + 2, na, M) * ld + k];
         const P4 off = s_off[ent & 31];
         const R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
         const R r2 = dx * dx + dy * dy + dz * dz;
@@ -1074,13 +1079,25 @@ __global__ void __launch_bounds__(TILE) k_radial_force(const Model<R> P, const G
         const P4 pi = pos4[k];
         const P4 bi0 = bp[3 * (size_t)k], bi1 = bp[3 * (size_t)k + 1], bi2 = bp[3 * (size_t)k + 2];
         R fx = R(0), fy = R(0), fz = R(0);
+        // two-stage prefetch: entry s + 2, position and adjoint s + 1 in flight
         int ent_n = total > 0 ? nbr[(size_t)list_slot(0, na, M) * ld + k] : 0;
+        int ent_nn = total > 1 ? nbr[(size_t)list_slot(1, na, M) * ld + k] : 0;
+        P4 pj_n = pi, bj0_n = bi0, bj1_n = bi1, bj2_n = bi2;
+        if (total > 0) {
+            const size_t m0 = (size_t)(ent_n >> 5);
+            pj_n = pos4[m0];
+            bj0_n = bp[3 * m0]; bj1_n = bp[3 * m0 + 1]; bj2_n = bp[3 * m0 + 2];
+        }
         for (int s = 0; s < total; ++s) {
             const int ent = ent_n;
-            if (s + 1 < total) ent_n = nbr[(size_t)list_slot(s + 1, na, M) * ld + k];
-            const int m = ent >> 5;
-            const P4 pj = pos4[m];
-            const P4 bj0 = bp[3 * (size_t)m], bj1 = bp[3 * (size_t)m + 1], bj2 = bp[3 * (size_t)m + 2];
+            const P4 pj = pj_n, bj0 = bj0_n, bj1 = bj1_n, bj2 = bj2_n;
+            ent_n = ent_nn;
+            if (s + 1 < total) {
+                const size_t m1 = (size_t)(ent_n >> 5);
+                pj_n = pos4[m1];
+                bj0_n = bp[3 * m1]; bj1_n = bp[3 * m1 + 1]; bj2_n = bp[3 * m1 + 2];
+            }
+            if (s + 2 < total) ent_nn = nbr[(size_t)list_slot(s + 2, na, M) * ld + k];
             const P4 off = s_off[ent & 31];
             const R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
             const R r2 = dx * dx + dy * dy + dz * dz;
