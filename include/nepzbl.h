@@ -162,17 +162,24 @@ typedef struct nep_stats {
     int32_t max_nbr_angular;
     int32_t nbr_capacity;       /* current neighbour slots per atom */
     int32_t graph_chunk;        /* MD steps per captured graph */
+    int64_t list_builds_skin;   /* MD neighbour-list builds with a Verlet skin so far */
 } nep_stats;
 
 int nep_get_stats(const nep_ctx* ctx, nep_stats* out);
 
-/* Options: NEP_OPT_TIMING (0/1) times every force-kernel launch with CUDA
- * events (also inside MD graphs); NEP_OPT_GRAPH_CHUNK sets the MD steps per
- * captured graph (>= 1); NEP_OPT_NBR_CAPACITY sets the neighbour slots per
- * atom (grows automatically when exceeded). */
-#define NEP_OPT_TIMING        1
-#define NEP_OPT_GRAPH_CHUNK   2
-#define NEP_OPT_NBR_CAPACITY  3
+/* Options: NEP_OPT_TIMING (0/1) times every force evaluation (the three force
+ * kernels) with CUDA events, also inside MD graphs; NEP_OPT_GRAPH_CHUNK sets
+ * the MD steps per captured graph (>= 1); NEP_OPT_NBR_CAPACITY sets the
+ * neighbour slots per atom (grows automatically when exceeded);
+ * NEP_OPT_SKIN_MILLIANGSTROM sets a Verlet skin for md_step in units of
+ * 0.001 A (0, the default, rebuilds the neighbour lists every step; > 0 builds
+ * them with r_c + skin and rebuilds only after some atom moved more than
+ * skin / 2 since the last build, which leaves every pair within r_c in the
+ * lists). */
+#define NEP_OPT_TIMING               1
+#define NEP_OPT_GRAPH_CHUNK          2
+#define NEP_OPT_NBR_CAPACITY         3
+#define NEP_OPT_SKIN_MILLIANGSTROM   4
 int nep_set_option(nep_ctx* ctx, int option, int64_t value);
 
 /* Resets the counters of nep_stats (launches, timing). */

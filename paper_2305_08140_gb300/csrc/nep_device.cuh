@@ -75,8 +75,10 @@ __device__ __forceinline__ int cell_coord(double x, int d, const Grid& g, double
 
 static __global__ void k_bin_count(Grid g, const double* __restrict__ x, int* __restrict__ cell_of,
                             int* __restrict__ slot_of, int* __restrict__ count,
-                            int* __restrict__ status)
+                            int* __restrict__ status,
+                            const int* __restrict__ gate = nullptr)
 {
+    if (gate && *gate == 0) return;   // lists still valid (Verlet skin)
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n) return;
     double p[3] = {x[i], x[g.n + i], x[2 * g.n + i]};
@@ -127,8 +129,10 @@ __device__ __forceinline__ int block_excl_scan(int v, int* sh, int& total)
 
 static __global__ void __launch_bounds__(SCAN_T) k_scan_blocks(const int* __restrict__ in, int n,
                                                         int* __restrict__ out,
-                                                        int* __restrict__ block_sums)
+                                                        int* __restrict__ block_sums,
+                            const int* __restrict__ gate = nullptr)
 {
+    if (gate && *gate == 0) return;   // lists still valid (Verlet skin)
     __shared__ int sh[32];
     int base = blockIdx.x * SCAN_B + threadIdx.x * SCAN_ITEMS;
     int v[SCAN_ITEMS], sum = 0;
@@ -149,8 +153,10 @@ static __global__ void __launch_bounds__(SCAN_T) k_scan_blocks(const int* __rest
 
 // one block: exclusive scan of up to SCAN_B block sums; writes out[n] = total
 static __global__ void __launch_bounds__(SCAN_T) k_scan_sums(int* __restrict__ sums, int nb,
-                                                      int* __restrict__ out, int n)
+                                                      int* __restrict__ out, int n,
+                            const int* __restrict__ gate = nullptr)
 {
+    if (gate && *gate == 0) return;   // lists still valid (Verlet skin)
     __shared__ int sh[32];
     int base = threadIdx.x * SCAN_ITEMS;
     int v[SCAN_ITEMS], sum = 0;
@@ -169,16 +175,20 @@ static __global__ void __launch_bounds__(SCAN_T) k_scan_sums(int* __restrict__ s
     if (threadIdx.x == 0) out[n] = total;
 }
 
-static __global__ void k_scan_add(int* __restrict__ out, int n, const int* __restrict__ sums)
+static __global__ void k_scan_add(int* __restrict__ out, int n, const int* __restrict__ sums,
+                            const int* __restrict__ gate = nullptr)
 {
+    if (gate && *gate == 0) return;   // lists still valid (Verlet skin)
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] += sums[i / SCAN_B];
 }
 
 static __global__ void k_bin_scatter(int n, const int* __restrict__ cell_of,
                               const int* __restrict__ slot_of, const int* __restrict__ start,
-                              int* __restrict__ perm)
+                              int* __restrict__ perm,
+                            const int* __restrict__ gate = nullptr)
 {
+    if (gate && *gate == 0) return;   // lists still valid (Verlet skin)
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     perm[start[cell_of[i]] + slot_of[i]] = i;
@@ -192,8 +202,10 @@ __global__ void k_cell_finalize(Grid g, int ncell, const int* __restrict__ start
                                 int* __restrict__ perm, const double* __restrict__ x,
                                 const int32_t* __restrict__ types,
                                 typename V4<R>::T* __restrict__ pos4,
-                                int* __restrict__ cell_sorted)
+                                int* __restrict__ cell_sorted,
+                            const int* __restrict__ gate = nullptr)
 {
+    if (gate && *gate == 0) return;   // lists still valid (Verlet skin)
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
     int b = start[c], e = start[c + 1];
@@ -234,8 +246,10 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                                                    int* __restrict__ nbr, int2* __restrict__ cnt,
                                                    int* __restrict__ status,
                                                    int* __restrict__ maxc,
-                                                   unsigned long long* __restrict__ pairs)
+                                                   unsigned long long* __restrict__ pairs,
+                            const int* __restrict__ gate = nullptr)
 {
+    if (gate && *gate == 0) return;   // lists still valid (Verlet skin)
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     int na = 0, nro = 0, sa = 0, sro = 0;
     if (k < g.n) {
@@ -303,6 +317,71 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
         if (pr) atomicAdd(&pairs[0], pr);
         if (pa) atomicAdd(&pairs[1], pa);
     }
+}
+
+// ----------------------------------------------------------------------------
+// Verlet skin: lists built with r_c + skin are reused until an atom has moved
+// more than skin/2 since the last build (then no pair can have crossed r_c
+// unseen).  The rebuild kernels above return at once when *gate == 0.
+// ----------------------------------------------------------------------------
+
+// gate |= any atom moved more than skin/2 (minimum image in periodic dims)
+static __global__ void k_skin_check(Grid g, const double* __restrict__ x,
+                                    const double* __restrict__ xref, double thr2,
+                                    int* __restrict__ gate)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool moved = false;
+    if (i < g.n) {
+        double d2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double d = x[(size_t)a * g.n + i] - xref[(size_t)a * g.n + i];
+            if (g.pbc[a]) d -= g.L[a] * rint(d * g.invL[a]);
+            d2 += d * d;
+        }
+        moved = !(d2 <= thr2);   // NaN also forces a rebuild
+    }
+    if (__any_sync(0xffffffffu, moved) && (threadIdx.x & 31) == 0) atomicOr(gate, 1);
+}
+
+// count[0..n) = 0 and the reference positions <- x, when rebuilding
+static __global__ void k_skin_rebuild_prep(int* __restrict__ count, int ncell,
+                                           const double* __restrict__ x,
+                                           double* __restrict__ xref, int n3,
+                                           const int* __restrict__ gate,
+                                           unsigned long long* __restrict__ nrebuild)
+{
+    if (*gate == 0) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) atomicAdd(nrebuild, 1ull);
+    if (i <= ncell) count[i] = 0;
+    if (i < n3) xref[i] = x[i];
+}
+
+// cell-relative positions from the current FP64 positions, cells fixed since
+// the last build (minimum image with respect to the cell in periodic dims)
+template <typename R>
+__global__ void k_refresh_pos4(Grid g, const int* __restrict__ perm,
+                               const int* __restrict__ cell_sorted,
+                               const double* __restrict__ x,
+                               typename V4<R>::T* __restrict__ pos4)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.n) return;
+    const int i = perm[k];
+    const int c = cell_sorted[k];
+    const int cc[3] = {c / (g.nc[2] * g.nc[1]), (c / g.nc[2]) % g.nc[1], c % g.nc[2]};
+    R rel[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double d = x[(size_t)a * g.n + i] - cc[a] * g.lc[a];
+        if (g.pbc[a]) d -= g.L[a] * rint(d * g.invL[a]);
+        rel[a] = (R)d;
+    }
+    typename V4<R>::T q = pos4[k];
+    q.x = rel[0]; q.y = rel[1]; q.z = rel[2];
+    pos4[k] = q;
 }
 
 // ----------------------------------------------------------------------------
@@ -802,6 +881,7 @@ __global__ void __launch_bounds__(128) k_radial_q(const Model<R> P, const Grid g
         const P4 off = s_off[ent & 31];
         const R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
         const R r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 >= P.rcR2) continue;   // beyond r_c (lists built with a skin)
         const R r = r2 * nepm::nep_rsqrt(r2);
         R T[KR], dT[KR], fc, dfc, dxdr;
         nepm::cheb<KR, false>(r, P.inv_rcR, T, dT, fc, dfc, dxdr);
@@ -945,6 +1025,7 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
             const P4 off = s_off[ent & 31];
             const R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
             const R r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 >= P.rcA2) continue;   // beyond r_c^A (lists built with a skin)
             const R inv_r = nepm::nep_rsqrt(r2);
             const R r = r2 * inv_r;
             R T[KA], dT[KA], fc, dfc, dxdr;
@@ -993,6 +1074,7 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
             const P4 off = s_off[ent & 31];
             const R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
             const R r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 >= P.rcA2) continue;
             const R inv_r = nepm::nep_rsqrt(r2);
             const R r = r2 * inv_r;
             R fx, fy, fz;
@@ -1101,6 +1183,7 @@ __global__ void __launch_bounds__(TILE) k_radial_force(const Model<R> P, const G
             const P4 off = s_off[ent & 31];
             const R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
             const R r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 >= P.rcR2) continue;   // beyond r_c (lists built with a skin)
             const R inv_r = nepm::nep_rsqrt(r2);
             const R r = r2 * inv_r;
             R T[KR], dT[KR], fc, dfc, dxdr;
@@ -1262,8 +1345,9 @@ static __global__ void __launch_bounds__(256) k_kick_thermo(int n, double acc,
 static __global__ void __launch_bounds__(256) k_thermo_step(const double* __restrict__ part, int nb,
                                                      double mass, double ev_amu,
                                                      double* __restrict__ thermo,
-                                                     int advance)
+                                                     int advance, int* __restrict__ gate = nullptr)
 {
+    if (gate && threadIdx.x == 0) *gate = 0;   // lists are current after this step
     __shared__ double sa[256], sb[256];
     double a = 0.0, b = 0.0;
     for (int t = threadIdx.x; t < nb; t += blockDim.x) {

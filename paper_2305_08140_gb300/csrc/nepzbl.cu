@@ -94,6 +94,12 @@ struct nep_ctx {
     int capture_kernels = 0;
     int capture_timed = 0;
     int nep_smem_set[2] = {0, 0};
+    // Verlet skin for MD (0: rebuild every step)
+    double skin = 0.0;
+    double* xref = nullptr;          // positions at the last list build (3 x ld)
+    int* gate = nullptr;             // device: 1 = rebuild the lists this step
+    unsigned long long* nrebuild = nullptr;
+    long long rebuilds = 0;
 
     // batched configurations (small periodic boxes)
     long long b_ntot_cap = 0;
@@ -160,7 +166,7 @@ static void free_scratch(nep_ctx* ctx)
     free_dev(ctx->cell_of); free_dev(ctx->slot_of); free_dev(ctx->perm);
     free_dev(ctx->cell_sorted); free_dev(ctx->pos4); free_dev(ctx->cnt); free_dev(ctx->nbr);
     free_dev(ctx->facc); free_dev(ctx->partials); free_dev(ctx->partials2);
-    free_dev(ctx->qr); free_dev(ctx->br);
+    free_dev(ctx->qr); free_dev(ctx->br); free_dev(ctx->xref);
     free_dev(ctx->vpart); free_dev(ctx->backup);
     ctx->ld = 0;
     ctx->M = 0;
@@ -194,6 +200,7 @@ static int ensure_atoms(nep_ctx* ctx, int n, int M)
     CK(cudaMalloc(&ctx->partials2, sizeof(double) * NPART * (size_t)RED1_MAX));
     CK(cudaMalloc(&ctx->vpart, sizeof(double) * 2 * (size_t)vb));
     CK(cudaMalloc(&ctx->backup, sizeof(double) * 9 * (size_t)ld));
+    CK(cudaMalloc(&ctx->xref, sizeof(double) * 3 * (size_t)ld));
     ctx->ld = ld;
     ctx->M = MM;
     return NEP_OK;
@@ -216,8 +223,10 @@ static int ensure_cells(nep_ctx* ctx, int ncell)
 }
 
 // Cell grid for a diagonal box; periodic dims need >= 3 cells of >= rc_R.
-static int make_grid(nep_ctx* ctx, int64_t n, const double box[9], const int32_t pbc[3], Grid& g)
+static int make_grid(nep_ctx* ctx, int64_t n, const double box[9], const int32_t pbc[3], Grid& g,
+                     double rcell = 0.0)
 {
+    const double rc_cell = rcell > 0.0 ? rcell : ctx->rcR;
     memset(&g, 0, sizeof(Grid));
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b)
@@ -226,12 +235,12 @@ static int make_grid(nep_ctx* ctx, int64_t n, const double box[9], const int32_t
     for (int a = 0; a < 3; ++a) {
         double L = box[4 * a];
         if (!(L > 0.0) || !isfinite(L)) return fail(ctx, NEP_ERR_BOX, "box length %d is %g", a, L);
-        int nc = (int)floor(L / ctx->rcR);
+        int nc = (int)floor(L / rc_cell);
         if (pbc[a]) {
             if (nc < 3)
                 return fail(ctx, NEP_ERR_BOX,
-                            "periodic box length %g < 3 r_c^R = %g (small boxes are not supported "
-                            "by the cell-list path)", L, 3 * ctx->rcR);
+                            "periodic box length %g < 3 x %g A (cell-list path; small boxes go "
+                            "through the batched entry points)", L, rc_cell);
         } else if (nc < 1) {
             nc = 1;
         }
@@ -266,7 +275,8 @@ static int check_device_ptr(nep_ctx* ctx, const void* p, const char* what)
 // force kernel, forces out, reduction.
 template <typename R>
 static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int32_t* types,
-                       double* F, double* site_energy, cudaStream_t s, int timed_slot)
+                       double* F, double* site_energy, cudaStream_t s, int timed_slot,
+                       int* gate)
 {
     Grid g = g0;
     g.ld = ctx->ld;
@@ -277,29 +287,49 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     if constexpr (sizeof(R) == 4) Pp = &ctx->mf;
     else Pp = &ctx->md;
     const Model<R>& P = *Pp;
-    CK(cudaMemsetAsync(ctx->count, 0, sizeof(int) * (size_t)(ncell + 1), s));
-    CK(cudaMemsetAsync(ctx->pairs, 0, sizeof(unsigned long long) * 2, s));
     if (n == 0) return NEP_OK;
     const int tb = 256;
     const int nb = (n + tb - 1) / tb;
-    k_bin_count<<<nb, tb, 0, s>>>(g, x, ctx->cell_of, ctx->slot_of, ctx->count, ctx->status);
+    // list cutoffs: r_c, or r_c + skin when the lists are reused between steps
+    const double sk = gate ? ctx->skin : 0.0;
+    const double rl = ctx->rcR + sk, ra = sqrt(ctx->md.rcA2) + sk;
+    if (gate) {
+        // rebuild only when an atom moved more than skin/2 since the last build
+        k_skin_check<<<nb, tb, 0, s>>>(g, x, ctx->xref, 0.25 * sk * sk, gate);
+        count_launch(ctx);
+        const int np = std::max(ncell + 1, 3 * n);
+        k_skin_rebuild_prep<<<(np + tb - 1) / tb, tb, 0, s>>>(ctx->count, ncell, x, ctx->xref,
+                                                             3 * n, gate, ctx->nrebuild);
+        count_launch(ctx);
+    } else {
+        CK(cudaMemsetAsync(ctx->count, 0, sizeof(int) * (size_t)(ncell + 1), s));
+        CK(cudaMemsetAsync(ctx->pairs, 0, sizeof(unsigned long long) * 2, s));
+    }
+    k_bin_count<<<nb, tb, 0, s>>>(g, x, ctx->cell_of, ctx->slot_of, ctx->count, ctx->status, gate);
     count_launch(ctx);
     const int sb = (ncell + SCAN_B - 1) / SCAN_B;
-    k_scan_blocks<<<sb, SCAN_T, 0, s>>>(ctx->count, ncell, ctx->start, ctx->scan_sums);
+    k_scan_blocks<<<sb, SCAN_T, 0, s>>>(ctx->count, ncell, ctx->start, ctx->scan_sums, gate);
     count_launch(ctx);
-    k_scan_sums<<<1, SCAN_T, 0, s>>>(ctx->scan_sums, sb, ctx->start, ncell);
+    k_scan_sums<<<1, SCAN_T, 0, s>>>(ctx->scan_sums, sb, ctx->start, ncell, gate);
     count_launch(ctx);
-    k_scan_add<<<(ncell + tb - 1) / tb, tb, 0, s>>>(ctx->start, ncell, ctx->scan_sums);
+    k_scan_add<<<(ncell + tb - 1) / tb, tb, 0, s>>>(ctx->start, ncell, ctx->scan_sums, gate);
     count_launch(ctx);
-    k_bin_scatter<<<nb, tb, 0, s>>>(n, ctx->cell_of, ctx->slot_of, ctx->start, ctx->perm);
+    k_bin_scatter<<<nb, tb, 0, s>>>(n, ctx->cell_of, ctx->slot_of, ctx->start, ctx->perm, gate);
     count_launch(ctx);
     k_cell_finalize<R><<<(ncell + 127) / 128, 128, 0, s>>>(
-        g, ncell, ctx->start, ctx->perm, x, types, (typename V4<R>::T*)ctx->pos4, ctx->cell_sorted);
+        g, ncell, ctx->start, ctx->perm, x, types, (typename V4<R>::T*)ctx->pos4, ctx->cell_sorted,
+        gate);
     count_launch(ctx);
     k_neighbors<R><<<(n + 127) / 128, 128, 0, s>>>(
-        g, (R)(P.rcR2), (R)(P.rcA2), (const typename V4<R>::T*)ctx->pos4, ctx->cell_sorted,
-        ctx->start, ctx->nbr, ctx->cnt, ctx->status, ctx->status + 1, ctx->pairs);
+        g, (R)(rl * rl), (R)(ra * ra), (const typename V4<R>::T*)ctx->pos4, ctx->cell_sorted,
+        ctx->start, ctx->nbr, ctx->cnt, ctx->status, ctx->status + 1, ctx->pairs, gate);
     count_launch(ctx);
+    if (gate) {
+        // cell-relative positions of this step (cells as of the last build)
+        k_refresh_pos4<R><<<nb, tb, 0, s>>>(g, ctx->perm, ctx->cell_sorted, x,
+                                           (typename V4<R>::T*)ctx->pos4);
+        count_launch(ctx);
+    }
     const int tiles = (n + TILE - 1) / TILE;
     // the three force kernels are timed together when timing is on
     if (timed_slot >= 0) {
@@ -355,11 +385,11 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
 }
 
 static int eval(nep_ctx* ctx, const Grid& g, const double* x, const int32_t* types, double* F,
-                double* site_energy, cudaStream_t s, int timed_slot)
+                double* site_energy, cudaStream_t s, int timed_slot, int* gate = nullptr)
 {
     return ctx->precision == NEP_FP32
-               ? launch_eval<float>(ctx, g, x, types, F, site_energy, s, timed_slot)
-               : launch_eval<double>(ctx, g, x, types, F, site_energy, s, timed_slot);
+               ? launch_eval<float>(ctx, g, x, types, F, site_energy, s, timed_slot, gate)
+               : launch_eval<double>(ctx, g, x, types, F, site_energy, s, timed_slot, gate);
 }
 
 static int ensure_events(nep_ctx* ctx, int pairs)
@@ -498,6 +528,9 @@ int nep_init(const nep_params* p, int precision, nep_ctx** out)
     if (e == cudaSuccess) e = cudaMalloc(&ctx->result, sizeof(double) * NPART);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->status, sizeof(int) * 3);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->pairs, sizeof(unsigned long long) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->gate, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->nrebuild, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(ctx->nrebuild, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_result, sizeof(double) * (NPART + TH_N));
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_status, sizeof(int) * 3);
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_pairs, sizeof(unsigned long long) * 2);
@@ -531,7 +564,7 @@ void nep_free(nep_ctx* ctx)
     free_batch(ctx);
     free_dev(ctx->count); free_dev(ctx->start); free_dev(ctx->scan_sums);
     free_dev(ctx->thermo); free_dev(ctx->thermo_backup); free_dev(ctx->result);
-    free_dev(ctx->status); free_dev(ctx->pairs);
+    free_dev(ctx->status); free_dev(ctx->pairs); free_dev(ctx->gate); free_dev(ctx->nrebuild);
     if (ctx->h_result) cudaFreeHost(ctx->h_result);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->h_pairs) cudaFreeHost(ctx->h_pairs);
@@ -556,6 +589,11 @@ int nep_set_option(nep_ctx* ctx, int option, int64_t value)
     case NEP_OPT_GRAPH_CHUNK:
         if (value < 1 || value > 100000) return fail(ctx, NEP_ERR_INVALID_ARG, "bad chunk");
         ctx->chunk = (int)value;
+        return NEP_OK;
+    case NEP_OPT_SKIN_MILLIANGSTROM:
+        if (value < 0 || value > 3000) return fail(ctx, NEP_ERR_INVALID_ARG, "skin must be 0..3 A");
+        ctx->skin = value * 1e-3;
+        drop_graphs(ctx);
         return NEP_OK;
     case NEP_OPT_NBR_CAPACITY:
         if (value < 1 || value > 1000000) return fail(ctx, NEP_ERR_INVALID_ARG, "bad capacity");
@@ -582,6 +620,10 @@ int nep_get_stats(const nep_ctx* ctx, nep_stats* out)
     out->max_nbr_angular = ctx->last_max_ang;
     out->nbr_capacity = ctx->M;
     out->graph_chunk = ctx->chunk;
+    unsigned long long nb = 0;
+    if (ctx->nrebuild && cudaMemcpy(&nb, ctx->nrebuild, sizeof(nb), cudaMemcpyDeviceToHost) != cudaSuccess)
+        nb = 0;
+    out->list_builds_skin = (int64_t)nb;
     return NEP_OK;
 }
 
@@ -678,11 +720,12 @@ static int capture_steps(nep_ctx* ctx, const Grid& g, nep_md_state* st, int step
     for (int t = 0; t < steps && !rc; ++t) {
         k_kick_drift<<<nb, tb, 0, cs>>>(g, acc, ctx->thermo, st->xyz, st->vel, st->forces);
         count_launch(ctx);
-        rc = eval(ctx, g, st->xyz, st->types, st->forces, nullptr, cs, ctx->timing ? t : -1);
+        int* gate = ctx->skin > 0.0 ? ctx->gate : nullptr;
+        rc = eval(ctx, g, st->xyz, st->types, st->forces, nullptr, cs, ctx->timing ? t : -1, gate);
         if (rc) break;
         k_kick_thermo<<<nb, tb, 0, cs>>>(n, acc, ctx->thermo, st->vel, st->forces, ctx->vpart, 1);
         count_launch(ctx);
-        k_thermo_step<<<1, 256, 0, cs>>>(ctx->vpart, nb, ctx->mass, EV_AMU, ctx->thermo, 1);
+        k_thermo_step<<<1, 256, 0, cs>>>(ctx->vpart, nb, ctx->mass, EV_AMU, ctx->thermo, 1, gate);
         count_launch(ctx);
     }
     cudaGraph_t graph = nullptr;
@@ -715,12 +758,14 @@ int md_step(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
         (rc = check_device_ptr(ctx, st->forces, "forces")) ||
         (rc = check_device_ptr(ctx, st->types, "types")))
         return rc;
-    Grid g;
-    if ((rc = make_grid(ctx, n, st->box, st->pbc, g))) return rc;
+    Grid g0, g;
+    if ((rc = make_grid(ctx, n, st->box, st->pbc, g0))) return rc;
+    // with a Verlet skin the MD lists (and cells) use r_c + skin
+    if ((rc = make_grid(ctx, n, st->box, st->pbc, g, ctx->rcR + ctx->skin))) return rc;
     CK(cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
     if (!st->forces_valid) {
-        rc = compute_with_retry(ctx, g, st->xyz, st->types, st->forces, nullptr, s);
+        rc = compute_with_retry(ctx, g0, st->xyz, st->types, st->forces, nullptr, s);
         if (rc) return rc;
         st->forces_valid = 1;
         st->potential_energy = ctx->h_result[0];
@@ -730,8 +775,12 @@ int md_step(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
         int rc2 = ensure_cells(ctx, g.nc[0] * g.nc[1] * g.nc[2]);
         if (rc2) return rc2;
         int need = ctx->M > 0 ? ctx->M : 96;
-        if (ctx->last_max_total > 0 && grown_capacity(ctx->last_max_total) > need)
-            need = grown_capacity(ctx->last_max_total);
+        if (ctx->last_max_total > 0) {
+            // lists with a skin hold ((r_c + skin) / r_c)^3 as many pairs
+            const double sc = pow((ctx->rcR + ctx->skin) / ctx->rcR, 3.0);
+            const int est = grown_capacity((int)ceil(ctx->last_max_total * sc));
+            if (est > need) need = est;
+        }
         if ((rc2 = ensure_atoms(ctx, (int)n, need))) return rc2;
     }
     // graphs are bound to the state's pointers and sizes
@@ -762,6 +811,7 @@ int md_step(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
     }
     int done = 0;
     int retries = 0;
+    bool force_rebuild = true;   // the caller may have moved atoms since the last call
     while (done < n_steps) {
         const int len = (n_steps - done) < ctx->chunk ? (n_steps - done) : ctx->chunk;
         auto it = ctx->graphs.find(len);
@@ -779,6 +829,11 @@ int md_step(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
         CK(cudaMemcpyAsync(ctx->thermo_backup, ctx->thermo, sizeof(double) * TH_N,
                            cudaMemcpyDeviceToDevice, s));
         CK(cudaMemsetAsync(ctx->status, 0, sizeof(int) * 3, s));
+        if (ctx->skin > 0.0 && force_rebuild) {
+            const int one = 1;
+            CK(cudaMemcpyAsync(ctx->gate, &one, sizeof(int), cudaMemcpyHostToDevice, s));
+            force_rebuild = false;
+        }
         CK(cudaGraphLaunch(it->second.exec, s));
         ctx->launches += it->second.kernels;
         rc = readback(ctx, s);
@@ -793,6 +848,7 @@ int md_step(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
             CK(cudaStreamSynchronize(s));
             rc = ensure_atoms(ctx, (int)n, grown_capacity(ctx->h_status[1]));
             if (rc) return rc;
+            force_rebuild = true;
             continue;
         }
         if (ctx->timing) {

@@ -27,6 +27,7 @@ NEP_FP64 = 1
 NEP_OPT_TIMING = 1
 NEP_OPT_GRAPH_CHUNK = 2
 NEP_OPT_NBR_CAPACITY = 3
+NEP_OPT_SKIN_MILLIANGSTROM = 4
 
 EXPORTED = ("nep_init", "nep_free", "nep_last_error", "nep_compute", "md_step",
             "nep_get_stats", "nep_set_option", "nep_reset_stats", "nep_compute_static",
@@ -59,7 +60,7 @@ class NepStats(C.Structure):
                 ("timed_ms", C.c_double), ("pairs_radial", C.c_int64),
                 ("pairs_angular", C.c_int64), ("max_nbr_radial", C.c_int32),
                 ("max_nbr_angular", C.c_int32), ("nbr_capacity", C.c_int32),
-                ("graph_chunk", C.c_int32)]
+                ("graph_chunk", C.c_int32), ("list_builds_skin", C.c_int64)]
 
 
 class NepBatch(C.Structure):

@@ -265,3 +265,45 @@ def test_md_variable_timestep_fp64():
     assert st.dt_last == pytest.approx(th[-1, 1], rel=1e-9)
     xg = st.xyz.cpu().numpy().T
     assert np.abs(_min_image(xg - p, s.box, s.pbc)).max() < 1e-8
+
+
+# ---------------------------------------------------------------------------
+# Verlet skin: lists built with r_c + skin and reused; same trajectories
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_md_with_verlet_skin_matches_oracle(precision):
+    from paper_2305_08140_gb300 import nepzbl as N
+    s = I.c1()
+    m = N.NEP(I.nep_model(1), precision)
+    m.set_option(N.NEP_OPT_SKIN_MILLIANGSTROM, 1000)
+    m.set_option(N.NEP_OPT_GRAPH_CHUNK, 9)
+    st = N.MDState(N.to_device_soa(s.pos), N.to_device_soa(s.vel), s.box, s.pbc, dt_max=1.0)
+    m.md(st, 100)
+    builds = m.stats()["list_builds_skin"]
+    assert 1 <= builds < 50, builds       # the lists were reused
+    p, v, F, th = O.md(I.nep_model(1), s.pos, s.vel, s.box, s.pbc, s.mass, 1.0, 100)
+    dp = np.abs(_min_image(st.xyz.cpu().numpy().T - p, s.box, s.pbc))
+    if precision == "fp64":
+        assert dp.max() < 1e-9
+        assert st.potential_energy == pytest.approx(th[-1, 2], abs=1e-8)
+    else:
+        assert dp.max() < 2e-5
+        assert abs(st.potential_energy - th[-1, 2]) / s.n < 2e-6
+    m.close()
+
+
+def test_md_skin_variable_timestep_clump_fp64():
+    from paper_2305_08140_gb300 import nepzbl as N
+    s = I.c3(ncell=10, fraction=0.05, radius=6.0, seed=23)
+    m = N.NEP(I.nep_model(1), "fp64")
+    m.set_option(N.NEP_OPT_SKIN_MILLIANGSTROM, 300)
+    m.set_option(N.NEP_OPT_GRAPH_CHUNK, 7)
+    st = N.MDState(N.to_device_soa(s.pos), N.to_device_soa(s.vel), s.box, s.pbc, dt_max=1.0,
+                   d_max=0.01)
+    m.md(st, 30)
+    p, v, F, th = O.md(I.nep_model(1), s.pos, s.vel, s.box, s.pbc, s.mass, 1.0, 30, d_max=0.01)
+    assert st.time == pytest.approx(th[:, 1].sum(), rel=1e-9)
+    assert np.abs(_min_image(st.xyz.cpu().numpy().T - p, s.box, s.pbc)).max() < 1e-8
+    assert m.stats()["list_builds_skin"] < 30
+    m.close()
