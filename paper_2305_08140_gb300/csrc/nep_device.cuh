@@ -849,12 +849,18 @@ __device__ __forceinline__ int list_slot(int s, int na, int M)
     return s < na ? s : M - 1 - (s - na);
 }
 
+// With a Verlet skin (act_nbr != nullptr) the kernel also writes this step's
+// lists of the pairs within r_c (angular ones from the front, radial-only ones
+// from the back, same layout as nbr), so the angular and radial-force kernels
+// never branch over pairs beyond the cutoffs.
 template <typename R>
 __global__ void __launch_bounds__(128) k_radial_q(const Model<R> P, const Grid g,
                                                   const typename V4<R>::T* __restrict__ pos4,
                                                   const int* __restrict__ nbr,
                                                   const int2* __restrict__ cnt,
-                                                  R* __restrict__ qr)
+                                                  R* __restrict__ qr,
+                                                  int* __restrict__ act_nbr = nullptr,
+                                                  int2* __restrict__ act_cnt = nullptr)
 {
     using P4 = typename V4<R>::T;
     __shared__ P4 s_off[27];
@@ -868,6 +874,7 @@ __global__ void __launch_bounds__(128) k_radial_q(const Model<R> P, const Grid g
     R Sb[KR];
 #pragma unroll
     for (int kk = 0; kk < KR; ++kk) Sb[kk] = R(0);
+    int a_na = 0, a_nro = 0;
     // two-stage prefetch: entry s + 2 and position s + 1 in flight during pair s
     int ent_n = total > 0 ? nbr[(size_t)list_slot(0, na, M) * ld + k] : 0;
     int ent_nn = total > 1 ? nbr[(size_t)list_slot(1, na, M) * ld + k] : 0;
@@ -882,12 +889,17 @@ __global__ void __launch_bounds__(128) k_radial_q(const Model<R> P, const Grid g
         const R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
         const R r2 = dx * dx + dy * dy + dz * dz;
         if (r2 >= P.rcR2) continue;   // beyond r_c (lists built with a skin)
+        if (act_nbr) {
+            if (r2 < P.rcA2) act_nbr[(size_t)(a_na++) * ld + k] = ent;
+            else act_nbr[(size_t)(M - 1 - a_nro++) * ld + k] = ent;
+        }
         const R r = r2 * nepm::nep_rsqrt(r2);
         R T[KR], dT[KR], fc, dfc, dxdr;
         nepm::cheb<KR, false>(r, P.inv_rcR, T, dT, fc, dfc, dxdr);
 #pragma unroll
         for (int kk = 0; kk < KR; ++kk) Sb[kk] += fc * T[kk];
     }
+    if (act_cnt) act_cnt[k] = make_int2(a_na, a_nro);
     R q[NR];
     radial_q<R>(P, Sb, q);
 #pragma unroll

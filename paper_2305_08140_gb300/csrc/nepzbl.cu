@@ -97,6 +97,8 @@ struct nep_ctx {
     // Verlet skin for MD (0: rebuild every step)
     double skin = 0.0;
     double* xref = nullptr;          // positions at the last list build (3 x ld)
+    int* nbr_act = nullptr;          // this step's pairs within r_c (skin runs) [M][ld]
+    int2* cnt_act = nullptr;
     int* gate = nullptr;             // device: 1 = rebuild the lists this step
     unsigned long long* nrebuild = nullptr;
     long long rebuilds = 0;
@@ -166,7 +168,8 @@ static void free_scratch(nep_ctx* ctx)
     free_dev(ctx->cell_of); free_dev(ctx->slot_of); free_dev(ctx->perm);
     free_dev(ctx->cell_sorted); free_dev(ctx->pos4); free_dev(ctx->cnt); free_dev(ctx->nbr);
     free_dev(ctx->facc); free_dev(ctx->partials); free_dev(ctx->partials2);
-    free_dev(ctx->qr); free_dev(ctx->br); free_dev(ctx->xref);
+    free_dev(ctx->qr); free_dev(ctx->br); free_dev(ctx->xref); free_dev(ctx->nbr_act);
+    free_dev(ctx->cnt_act);
     free_dev(ctx->vpart); free_dev(ctx->backup);
     ctx->ld = 0;
     ctx->M = 0;
@@ -201,6 +204,10 @@ static int ensure_atoms(nep_ctx* ctx, int n, int M)
     CK(cudaMalloc(&ctx->vpart, sizeof(double) * 2 * (size_t)vb));
     CK(cudaMalloc(&ctx->backup, sizeof(double) * 9 * (size_t)ld));
     CK(cudaMalloc(&ctx->xref, sizeof(double) * 3 * (size_t)ld));
+    if (ctx->skin > 0.0) {
+        CK(cudaMalloc(&ctx->nbr_act, sizeof(int) * (size_t)ld * MM));
+        CK(cudaMalloc(&ctx->cnt_act, sizeof(int2) * (size_t)ld));
+    }
     ctx->ld = ld;
     ctx->M = MM;
     return NEP_OK;
@@ -341,7 +348,12 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     // radial descriptor (all pairs, small state)
     const typename V4<R>::T* p4 = (const typename V4<R>::T*)ctx->pos4;
     typename Acc<R>::T* fa = (typename Acc<R>::T*)ctx->facc;
-    k_radial_q<R><<<(n + 127) / 128, 128, 0, s>>>(P, g, p4, ctx->nbr, ctx->cnt, (R*)ctx->qr);
+    // with a skin: this step's lists within r_c go to nbr_act / cnt_act
+    int* lnbr = gate ? ctx->nbr_act : ctx->nbr;
+    int2* lcnt = gate ? ctx->cnt_act : ctx->cnt;
+    k_radial_q<R><<<(n + 127) / 128, 128, 0, s>>>(P, g, p4, ctx->nbr, ctx->cnt, (R*)ctx->qr,
+                                                 gate ? ctx->nbr_act : nullptr,
+                                                 gate ? ctx->cnt_act : nullptr);
     count_launch(ctx);
     // angular part, network, ZBL (the block's angular entries staged in shared
     // memory when they fit)
@@ -352,12 +364,12 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
                                 (int)(sizeof(int) * STAGE_MAX_SLOTS * TILE)));
         ctx->nep_smem_set[sizeof(R) == 4 ? 0 : 1] = 1;
     }
-    k_nep_ang<R><<<tiles, TILE, stage_bytes, s>>>(P, g, p4, ctx->nbr, ctx->cnt, ctx->perm, x,
+    k_nep_ang<R><<<tiles, TILE, stage_bytes, s>>>(P, g, p4, lnbr, lcnt, ctx->perm, x,
                                                  (const R*)ctx->qr, (typename V4<R>::T*)ctx->br, fa,
                                                  ctx->partials, site_energy, ctx->status, stage_slots);
     count_launch(ctx);
     // radial pair forces (all pairs, small state)
-    k_radial_force<R><<<tiles, TILE, 0, s>>>(P, g, p4, ctx->nbr, ctx->cnt,
+    k_radial_force<R><<<tiles, TILE, 0, s>>>(P, g, p4, lnbr, lcnt,
                                             (const typename V4<R>::T*)ctx->br, fa,
                                             ctx->partials + (size_t)tiles * NPART, ctx->status);
     count_launch(ctx);
@@ -594,6 +606,12 @@ int nep_set_option(nep_ctx* ctx, int option, int64_t value)
         if (value < 0 || value > 3000) return fail(ctx, NEP_ERR_INVALID_ARG, "skin must be 0..3 A");
         ctx->skin = value * 1e-3;
         drop_graphs(ctx);
+        if (ctx->skin > 0.0 && ctx->ld > 0 && !ctx->nbr_act) {
+            cudaDeviceSynchronize();
+            const int ld = ctx->ld, M = ctx->M;
+            free_scratch(ctx);
+            return ensure_atoms(ctx, ld, M);
+        }
         return NEP_OK;
     case NEP_OPT_NBR_CAPACITY:
         if (value < 1 || value > 1000000) return fail(ctx, NEP_ERR_INVALID_ARG, "bad capacity");
