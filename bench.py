@@ -194,14 +194,15 @@ def other_configs(dev):
     from paper_2305_08140_gb300 import nepzbl as N
     model = I.nep_model(1)
     out = {}
-    # the slab with a 1 A Verlet skin: lists rebuilt only after an atom moved 0.5 A
+    # the slab with a 0.5 A Verlet skin: lists rebuilt only after an atom moved 0.25 A
     s = I.c5()
     nep = N.NEP(model, "fp32")
-    nep.set_option(N.NEP_OPT_SKIN_MILLIANGSTROM, 1000)
+    nep.set_option(N.NEP_OPT_SKIN_MILLIANGSTROM, 500)
     r = _time_md(N, nep, s, 100, 3, dev)
     r["list_builds"] = nep.stats()["list_builds_skin"]
-    r["note"] = "Verlet skin 1 A (lists with r_c + 1 A, rebuilt after a 0.5 A displacement)"
-    out["c5_8192000_fp32_skin_1A"] = r
+    r["note"] = ("Verlet skin 0.5 A (lists with r_c + 0.5 A, rebuilt after a 0.25 A "
+                 "displacement; pairs within r_c compacted every step)")
+    out["c5_8192000_fp32_skin_0.5A"] = r
     nep.close()
     del s
     # 2,000-atom bcc W: plain FP64 as configured, and the FP32 path; 100 NVE steps
