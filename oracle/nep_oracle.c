@@ -25,6 +25,10 @@
  *                 (j = k included), l = 1..lmax, stored l-major
  *   q^4b_n      = tr(T_n^3), T_n = sum_j g^A_n(r_ij) (u_ij u_ij^T - I/3)
  *   U^NEP       = sum_mu w1_mu tanh(sum_nu w0_{mu nu} s_nu q_nu - b0_mu) - b1
+ * With several species (T types) every pair term uses the coefficients of
+ * its ordered species pair: g_n of the pair (i, j) is sum_k c^{t_i t_j}_nk
+ * f_k(r_ij), t_i the species of the centre, t_j of the neighbour; the network
+ * is shared by all species; Z_i, Z_j in Eq. 2 and 4 are the pair's charges.
  * Forces are F = -dE/dr, virial W_ab = -sum_i sum_j (dU_i/dr_ij)_a (r_ij)_b,
  * with r_ij = r_j - r_i, all from analytic FP64 derivatives of the formulas
  * above (the Legendre double sum and the 3x3 tensor form, not spherical
@@ -45,6 +49,7 @@
 #define ORC_OK 0
 #define ORC_ERR_ARG (-1)
 #define ORC_ERR_MEM (-2)
+#define ORC_MAX_TYPES 8
 
 /* e^2 / (4 pi eps0) in eV*A (CODATA), the prefactor of Eq. 2 */
 #define ORC_COULOMB 14.39964547
@@ -59,30 +64,49 @@ typedef struct {
     int use4b;           /* 4-body term on/off */
     int H;               /* hidden neurons */
     int D;               /* descriptor length */
-    double Z;            /* nuclear charge of the single species */
+    int T;               /* number of species */
+    double Z[ORC_MAX_TYPES];  /* nuclear charge per species */
     double zr1, zr2;     /* Tersoff switch radii of the ZBL term */
-    const double *w0, *b0, *w1, *b1, *cR, *cA;  /* views into params */
+    const double *w0, *b0, *w1, *b1;  /* views into params */
+    const double *cR, *cA;   /* [T][T][n][K]: block (t_i, t_j) */
     const double *s;     /* descriptor scaler, length D */
 } orc_model;
 
-/* ihp = {nR, nA, KR, KA, lmax, use4b, H}; dhp = {rcR, rcA, Z, zr1, zr2} */
+/* Radial / angular coefficients c^{ti tj} of an ordered species pair. */
+static const double *coef_R(const orc_model *m, int ti, int tj)
+{
+    return m->cR + (size_t)(ti * m->T + tj) * m->nR * m->KR;
+}
+static const double *coef_A(const orc_model *m, int ti, int tj)
+{
+    return m->cA + (size_t)(ti * m->T + tj) * m->nA * m->KA;
+}
+
+/* ihp = {nR, nA, KR, KA, lmax, use4b, H, T};
+ * dhp = {rcR, rcA, zr1, zr2, Z_0, ..., Z_{T-1}};
+ * params = w0[H][D], b0[H], w1[H], b1, cR[T][T][nR][KR], cA[T][T][nA][KA] */
 static int model_init(orc_model *m, const int *ihp, const double *dhp,
                       const double *params, const double *scaler)
 {
     m->nR = ihp[0]; m->nA = ihp[1]; m->KR = ihp[2]; m->KA = ihp[3];
-    m->lmax = ihp[4]; m->use4b = ihp[5]; m->H = ihp[6];
-    m->rcR = dhp[0]; m->rcA = dhp[1]; m->Z = dhp[2]; m->zr1 = dhp[3]; m->zr2 = dhp[4];
+    m->lmax = ihp[4]; m->use4b = ihp[5]; m->H = ihp[6]; m->T = ihp[7];
+    m->rcR = dhp[0]; m->rcA = dhp[1]; m->zr1 = dhp[2]; m->zr2 = dhp[3];
     if (m->nR < 1 || m->nA < 1 || m->nA > 16 || m->nR > 64 || m->KR < 1 ||
         m->KA < 1 || m->KR > 64 || m->KA > 64 || m->lmax < 0 || m->lmax > 63 ||
-        m->H < 1 || !(m->rcR > 0) || !(m->rcA > 0) || !(m->zr2 > m->zr1))
+        m->H < 1 || !(m->rcR > 0) || !(m->rcA > 0) || !(m->zr2 > m->zr1) ||
+        m->T < 1 || m->T > ORC_MAX_TYPES)
         return ORC_ERR_ARG;
+    for (int t = 0; t < m->T; ++t) {
+        m->Z[t] = dhp[4 + t];
+        if (!(m->Z[t] > 0)) return ORC_ERR_ARG;
+    }
     m->D = m->nR + m->nA * m->lmax + (m->use4b ? m->nA : 0);
     const double *p = params;
     m->w0 = p; p += (size_t)m->H * m->D;
     m->b0 = p; p += m->H;
     m->w1 = p; p += m->H;
     m->b1 = p; p += 1;
-    m->cR = p; p += (size_t)m->nR * m->KR;
+    m->cR = p; p += (size_t)m->T * m->T * m->nR * m->KR;
     m->cA = p;
     m->s = scaler;
     return ORC_OK;
@@ -91,9 +115,9 @@ static int model_init(orc_model *m, const int *ihp, const double *dhp,
 int orc_n_params(const int *ihp)
 {
     int nR = ihp[0], nA = ihp[1], KR = ihp[2], KA = ihp[3], lmax = ihp[4];
-    int use4b = ihp[5], H = ihp[6];
+    int use4b = ihp[5], H = ihp[6], T = ihp[7];
     int D = nR + nA * lmax + (use4b ? nA : 0);
-    return H * D + 2 * H + 1 + nR * KR + nA * KA;
+    return H * D + 2 * H + 1 + T * T * (nR * KR + nA * KA);
 }
 
 int orc_num_threads(void)
@@ -216,12 +240,14 @@ void orc_zbl(double r, double Zi, double Zj, double r1, double r2,
  * NEP site energy of one atom
  * ------------------------------------------------------------------------- */
 
-/* Descriptor q (length D) of one atom from the displacement vectors of its
- * radial neighbours dR[3*nr] (r < rcR) and angular neighbours dA[3*na]
- * (r < rcA).  If the gradient buffers are given, also returns
- * dU^NEP/dd for each neighbour (gR[3*nr], gA[3*na]) and U^NEP itself. */
-static double site_nep(const orc_model *m, int nr, const double *dR, int na,
-                       const double *dA, double *q_out, double *gR, double *gA)
+/* Descriptor q (length D) of one atom of species ti from the displacement
+ * vectors of its radial neighbours dR[3*nr] (r < rcR, species tR[nr]) and
+ * angular neighbours dA[3*na] (r < rcA, species tA[na]).  If the gradient
+ * buffers are given, also returns dU^NEP/dd for each neighbour (gR[3*nr],
+ * gA[3*na]) and U^NEP itself. */
+static double site_nep(const orc_model *m, int ti, int nr, const double *dR, const int *tR,
+                       int na, const double *dA, const int *tA, double *q_out, double *gR,
+                       double *gA)
 {
     const int nR = m->nR, nA = m->nA, L = m->lmax, D = m->D, H = m->H;
     double *q = (double *)calloc((size_t)D, sizeof(double));
@@ -235,7 +261,7 @@ static double site_nep(const orc_model *m, int nr, const double *dR, int na,
     for (int s = 0; s < nr; ++s) {
         const double *d = dR + 3 * s;
         double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        radial_functions(m->cR, nR, m->KR, r, m->rcR, g, dg);
+        radial_functions(coef_R(m, ti, tR[s]), nR, m->KR, r, m->rcR, g, dg);
         for (int n = 0; n < nR; ++n) q[n] += g[n];
     }
     /* angular neighbours: distance, unit vector, g^A_n and dg^A_n/dr */
@@ -244,7 +270,7 @@ static double site_nep(const orc_model *m, int nr, const double *dR, int na,
         double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         rA[s] = r;
         for (int a = 0; a < 3; ++a) uA[3 * s + a] = d[a] / r;
-        radial_functions(m->cA, nA, m->KA, r, m->rcA, g, dg);
+        radial_functions(coef_A(m, ti, tA[s]), nA, m->KA, r, m->rcA, g, dg);
         for (int n = 0; n < nA; ++n) { gnA[n * na + s] = g[n]; dgnA[n * na + s] = dg[n]; }
     }
     /* q_nl: Legendre double sum over all ordered pairs (j, k), j = k included */
@@ -296,7 +322,7 @@ static double site_nep(const orc_model *m, int nr, const double *dR, int na,
         for (int s = 0; s < nr; ++s) {
             const double *d = dR + 3 * s;
             double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-            radial_functions(m->cR, nR, m->KR, r, m->rcR, g, dg);
+            radial_functions(coef_R(m, ti, tR[s]), nR, m->KR, r, m->rcR, g, dg);
             double sc = 0.0;
             for (int n = 0; n < nR; ++n) sc += dUdq[n] * dg[n];
             for (int a = 0; a < 3; ++a) gR[3 * s + a] = sc * d[a] / r;
@@ -358,12 +384,15 @@ static double site_nep(const orc_model *m, int nr, const double *dR, int na,
 /* Exported single-environment evaluation (for tests): U^NEP, q and gradients
  * of one atom given its neighbour displacements. */
 int orc_site(const int *ihp, const double *dhp, const double *params,
-             const double *scaler, int nr, const double *dR, int na,
-             const double *dA, double *U, double *q, double *gR, double *gA)
+             const double *scaler, int ti, int nr, const double *dR, const int *tR, int na,
+             const double *dA, const int *tA, double *U, double *q, double *gR, double *gA)
 {
     orc_model m;
     if (model_init(&m, ihp, dhp, params, scaler)) return ORC_ERR_ARG;
-    *U = site_nep(&m, nr, dR, na, dA, q, gR, gA);
+    if (ti < 0 || ti >= m.T) return ORC_ERR_ARG;
+    for (int s = 0; s < nr; ++s) if (tR[s] < 0 || tR[s] >= m.T) return ORC_ERR_ARG;
+    for (int s = 0; s < na; ++s) if (tA[s] < 0 || tA[s] >= m.T) return ORC_ERR_ARG;
+    *U = site_nep(&m, ti, nr, dR, tR, na, dA, tA, q, gR, gA);
     return ORC_OK;
 }
 
@@ -398,23 +427,28 @@ double orc_fourbody_triple(int na, const double *g, const double *u)
 typedef struct {
     int n, cap;
     int *j;        /* neighbour atom */
+    int *t;        /* its species */
     double *d;     /* displacement r_j (+ image) - r_i, 3 per entry */
     double *g;     /* dU_i/dd for this entry, 3 per entry */
 } orc_list;
 
-static int list_push(orc_list *L, int j, const double *d)
+static int list_push(orc_list *L, int j, int t, const double *d)
 {
     if (L->n == L->cap) {
         int cap = L->cap ? 2 * L->cap : 32;
         int *nj = (int *)realloc(L->j, sizeof(int) * (size_t)cap);
         if (!nj) return ORC_ERR_MEM;
         L->j = nj;
+        int *nt = (int *)realloc(L->t, sizeof(int) * (size_t)cap);
+        if (!nt) return ORC_ERR_MEM;
+        L->t = nt;
         double *nd = (double *)realloc(L->d, sizeof(double) * 3 * (size_t)cap);
         if (!nd) return ORC_ERR_MEM;
         L->d = nd;
         L->cap = cap;
     }
     L->j[L->n] = j;
+    L->t[L->n] = t;
     for (int a = 0; a < 3; ++a) L->d[3 * L->n + a] = d[a];
     L->n++;
     return ORC_OK;
@@ -422,7 +456,7 @@ static int list_push(orc_list *L, int j, const double *d)
 
 static void list_free(orc_list *L)
 {
-    free(L->j); free(L->d); free(L->g);
+    free(L->j); free(L->t); free(L->d); free(L->g);
     memset(L, 0, sizeof(*L));
 }
 
@@ -431,7 +465,19 @@ typedef struct {
     const double *pos;   /* (N,3) */
     double box[3];
     int pbc[3];
+    const int *types;    /* (N) species, or NULL for all 0 */
 } orc_sys;
+
+static int sys_type(const orc_sys *S, int i) { return S->types ? S->types[i] : 0; }
+
+/* Every species index in [0, T). */
+static int types_valid(const orc_sys *S, int T)
+{
+    if (!S->types) return 1;
+    for (int i = 0; i < S->N; ++i)
+        if (S->types[i] < 0 || S->types[i] >= T) return 0;
+    return 1;
+}
 
 typedef struct {
     int use;             /* 0: brute force */
@@ -463,7 +509,7 @@ static int query_brute(const orc_sys *S, int i, double rc, orc_list *out)
                                    base[2] + n2 * S->box[2]};
                     double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
                     if (j == i && n0 == 0 && n1 == 0 && n2 == 0) continue;
-                    if (r2 < rc2 && list_push(out, j, d)) return ORC_ERR_MEM;
+                    if (r2 < rc2 && list_push(out, j, sys_type(S, j), d)) return ORC_ERR_MEM;
                 }
     }
     return ORC_OK;
@@ -552,7 +598,8 @@ static int query_grid(const orc_sys *S, const orc_grid *G, int i, double rc, orc
                         d[a] = S->pos[3 * j + a] - xi[a];
                         if (S->pbc[a]) d[a] -= S->box[a] * floor(d[a] / S->box[a] + 0.5);
                     }
-                    if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < rc2 && list_push(out, j, d))
+                    if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < rc2 &&
+                        list_push(out, j, sys_type(S, j), d))
                         return ORC_ERR_MEM;
                 }
             }
@@ -577,7 +624,7 @@ static int cmp_double(const void *a, const void *b)
 int orc_neighbor_counts(int N, const double *pos, const double *box, const int *pbc,
                         double rc, int mode, int *counts, int maxn, double *dist)
 {
-    orc_sys S = {N, pos, {box[0], box[1], box[2]}, {pbc[0], pbc[1], pbc[2]}};
+    orc_sys S = {N, pos, {box[0], box[1], box[2]}, {pbc[0], pbc[1], pbc[2]}, NULL};
     orc_grid G;
     memset(&G, 0, sizeof(G));
     if (mode == 1 && grid_build(&S, rc, &G)) return ORC_ERR_MEM;
@@ -626,12 +673,14 @@ static int atom_eval(const orc_model *m, const orc_sys *S, const orc_grid *G, in
     at->A.g = (double *)malloc(sizeof(double) * 3 * (size_t)(at->A.n + 1));
     at->Z.g = (double *)malloc(sizeof(double) * 3 * (size_t)(at->Z.n + 1));
     if (!at->R.g || !at->A.g || !at->Z.g) return ORC_ERR_MEM;
-    at->U = site_nep(m, at->R.n, at->R.d, at->A.n, at->A.d, q, at->R.g, at->A.g);
+    const int ti = sys_type(S, i);
+    at->U = site_nep(m, ti, at->R.n, at->R.d, at->R.t, at->A.n, at->A.d, at->A.t, q, at->R.g,
+                     at->A.g);
     for (int s = 0; s < at->Z.n; ++s) {
         const double *d = at->Z.d + 3 * s;
         double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         double U, dU;
-        orc_zbl(r, m->Z, m->Z, m->zr1, m->zr2, &U, &dU);
+        orc_zbl(r, m->Z[ti], m->Z[at->Z.t[s]], m->zr1, m->zr2, &U, &dU);
         at->U += 0.5 * U;                                     /* Eq. 1 */
         for (int a = 0; a < 3; ++a) at->Z.g[3 * s + a] = 0.5 * dU * d[a] / r;
     }
@@ -698,23 +747,25 @@ static int efv(const orc_model *m, const orc_sys *S, int use_grid, double *E, do
  * neighbours.  Any output pointer may be NULL. */
 int orc_energy_forces_virial(const int *ihp, const double *dhp, const double *params,
                              const double *scaler, int N, const double *pos,
-                             const double *box, const int *pbc, int use_grid,
-                             double *E, double *F, double *W, double *U)
+                             const int *types, const double *box, const int *pbc,
+                             int use_grid, double *E, double *F, double *W, double *U)
 {
     orc_model m;
     if (model_init(&m, ihp, dhp, params, scaler) || N < 0) return ORC_ERR_ARG;
-    orc_sys S = {N, pos, {box[0], box[1], box[2]}, {pbc[0], pbc[1], pbc[2]}};
+    orc_sys S = {N, pos, {box[0], box[1], box[2]}, {pbc[0], pbc[1], pbc[2]}, types};
+    if (!types_valid(&S, m.T)) return ORC_ERR_ARG;
     return efv(&m, &S, use_grid, E, F, W, U, NULL);
 }
 
 /* Unscaled descriptors q (N, D) of every atom. */
 int orc_descriptors(const int *ihp, const double *dhp, const double *params,
-                    const double *scaler, int N, const double *pos, const double *box,
-                    const int *pbc, int use_grid, double *q)
+                    const double *scaler, int N, const double *pos, const int *types,
+                    const double *box, const int *pbc, int use_grid, double *q)
 {
     orc_model m;
     if (model_init(&m, ihp, dhp, params, scaler) || N < 0) return ORC_ERR_ARG;
-    orc_sys S = {N, pos, {box[0], box[1], box[2]}, {pbc[0], pbc[1], pbc[2]}};
+    orc_sys S = {N, pos, {box[0], box[1], box[2]}, {pbc[0], pbc[1], pbc[2]}, types};
+    if (!types_valid(&S, m.T)) return ORC_ERR_ARG;
     return efv(&m, &S, use_grid, NULL, NULL, NULL, NULL, q);
 }
 
@@ -723,12 +774,14 @@ int orc_descriptors(const int *ihp, const double *dhp, const double *params,
  *   F_a = sum_{s in lists(a), j_s != a} g_{a,s} - sum_{k != a} sum_{t: j_t = a} g_{k,t}
  * where k runs over the distinct atoms in the radial neighbourhood of a. */
 int orc_forces_subset(const int *ihp, const double *dhp, const double *params,
-                      const double *scaler, int N, const double *pos, const double *box,
-                      const int *pbc, int nidx, const int64_t *idx, double *F, double *U)
+                      const double *scaler, int N, const double *pos, const int *types,
+                      const double *box, const int *pbc, int nidx, const int64_t *idx,
+                      double *F, double *U)
 {
     orc_model m;
     if (model_init(&m, ihp, dhp, params, scaler) || N < 0) return ORC_ERR_ARG;
-    orc_sys S = {N, pos, {box[0], box[1], box[2]}, {pbc[0], pbc[1], pbc[2]}};
+    orc_sys S = {N, pos, {box[0], box[1], box[2]}, {pbc[0], pbc[1], pbc[2]}, types};
+    if (!types_valid(&S, m.T)) return ORC_ERR_ARG;
     orc_grid G;
     memset(&G, 0, sizeof(G));
     if (grid_build(&S, m.rcR, &G)) return ORC_ERR_MEM;
@@ -789,20 +842,22 @@ int orc_forces_subset(const int *ihp, const double *dhp, const double *params,
  * coordinates are wrapped into [0, L).  thermo (nsteps x 4, may be NULL)
  * receives t, dt, potential and kinetic energy after each step.  F (N,3) holds
  * the forces at the initial positions on entry when forces_valid != 0, and
- * the final forces on return. */
+ * the final forces on return.  mass[t] is the mass (amu) of species t. */
 int orc_md(const int *ihp, const double *dhp, const double *params, const double *scaler,
-           int N, double *pos, double *vel, double *F, int forces_valid, const double *box,
-           const int *pbc, double mass, double dt_max, double d_max, int nsteps,
-           int use_grid, double *thermo)
+           int N, double *pos, double *vel, double *F, int forces_valid, const int *types,
+           const double *box, const int *pbc, const double *mass, double dt_max,
+           double d_max, int nsteps, int use_grid, double *thermo)
 {
     orc_model m;
-    if (model_init(&m, ihp, dhp, params, scaler) || N < 0 || !(mass > 0)) return ORC_ERR_ARG;
-    orc_sys S = {N, pos, {box[0], box[1], box[2]}, {pbc[0], pbc[1], pbc[2]}};
+    if (model_init(&m, ihp, dhp, params, scaler) || N < 0) return ORC_ERR_ARG;
+    for (int t = 0; t < m.T; ++t)
+        if (!(mass[t] > 0)) return ORC_ERR_ARG;
+    orc_sys S = {N, pos, {box[0], box[1], box[2]}, {pbc[0], pbc[1], pbc[2]}, types};
+    if (!types_valid(&S, m.T)) return ORC_ERR_ARG;
     double E, W[9];
     int err = ORC_OK;
     if (!forces_valid) err = efv(&m, &S, use_grid, &E, F, W, NULL, NULL);
     double t = 0.0;
-    const double acc = ORC_EV_AMU / mass;
     for (int step = 0; step < nsteps && !err; ++step) {
         double dt = dt_max;
         if (d_max > 0) {
@@ -815,6 +870,7 @@ int orc_md(const int *ihp, const double *dhp, const double *params, const double
             if (vmax > 0 && d_max / vmax < dt) dt = d_max / vmax;
         }
         for (int i = 0; i < 3 * N; ++i) {
+            const double acc = ORC_EV_AMU / mass[sys_type(&S, i / 3)];
             vel[i] += 0.5 * dt * F[i] * acc;
             pos[i] += dt * vel[i];
         }
@@ -824,10 +880,10 @@ int orc_md(const int *ihp, const double *dhp, const double *params, const double
         err = efv(&m, &S, use_grid, &E, F, W, NULL, NULL);
         double ke = 0.0;
         for (int i = 0; i < 3 * N; ++i) {
-            vel[i] += 0.5 * dt * F[i] * acc;
-            ke += vel[i] * vel[i];
+            const double mi = mass[sys_type(&S, i / 3)];
+            vel[i] += 0.5 * dt * F[i] * (ORC_EV_AMU / mi);
+            ke += 0.5 * mi * vel[i] * vel[i] / ORC_EV_AMU;
         }
-        ke *= 0.5 * mass / ORC_EV_AMU;
         t += dt;
         if (thermo) {
             thermo[4 * step + 0] = t;

@@ -38,14 +38,15 @@ def lib():
         L = C.CDLL(LIB)
         dp = C.POINTER(C.c_double)
         ip = C.POINTER(C.c_int)
-        L.orc_energy_forces_virial.argtypes = [ip, dp, dp, dp, C.c_int, dp, dp, ip, C.c_int,
-                                               dp, dp, dp, dp]
-        L.orc_descriptors.argtypes = [ip, dp, dp, dp, C.c_int, dp, dp, ip, C.c_int, dp]
-        L.orc_forces_subset.argtypes = [ip, dp, dp, dp, C.c_int, dp, dp, ip, C.c_int,
+        L.orc_energy_forces_virial.argtypes = [ip, dp, dp, dp, C.c_int, dp, ip, dp, ip,
+                                               C.c_int, dp, dp, dp, dp]
+        L.orc_descriptors.argtypes = [ip, dp, dp, dp, C.c_int, dp, ip, dp, ip, C.c_int, dp]
+        L.orc_forces_subset.argtypes = [ip, dp, dp, dp, C.c_int, dp, ip, dp, ip, C.c_int,
                                         C.POINTER(C.c_int64), dp, dp]
-        L.orc_md.argtypes = [ip, dp, dp, dp, C.c_int, dp, dp, dp, C.c_int, dp, ip,
-                             C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, dp]
-        L.orc_site.argtypes = [ip, dp, dp, dp, C.c_int, dp, C.c_int, dp, dp, dp, dp, dp]
+        L.orc_md.argtypes = [ip, dp, dp, dp, C.c_int, dp, dp, dp, C.c_int, ip, dp, ip,
+                             dp, C.c_double, C.c_double, C.c_int, C.c_int, dp]
+        L.orc_site.argtypes = [ip, dp, dp, dp, C.c_int, C.c_int, dp, ip, C.c_int, dp, ip,
+                               dp, dp, dp, dp]
         L.orc_neighbor_counts.argtypes = [C.c_int, dp, dp, ip, C.c_double, C.c_int, ip,
                                           C.c_int, dp]
         L.orc_cutoff.argtypes = [C.c_double, C.c_double, dp, dp]
@@ -80,10 +81,29 @@ def _f64(a):
 def _hp(model):
     ihp = np.array([model.n_max_radial + 1, model.n_max_angular + 1,
                     model.basis_size_radial + 1, model.basis_size_angular + 1,
-                    model.l_max, model.use_4body, model.n_hidden], dtype=np.int32)
-    dhp = np.array([model.rc_radial, model.rc_angular, float(model.z),
-                    model.zbl_r_inner, model.zbl_r_outer], dtype=np.float64)
+                    model.l_max, model.use_4body, model.n_hidden, model.n_types],
+                   dtype=np.int32)
+    dhp = np.array([model.rc_radial, model.rc_angular, model.zbl_r_inner, model.zbl_r_outer,
+                    *[float(z) for z in model.zs]], dtype=np.float64)
     return ihp, dhp
+
+
+def _types(types, n):
+    if types is None:
+        return np.zeros(max(n, 1), np.int32)
+    t = np.ascontiguousarray(types, dtype=np.int32)
+    if t.shape != (n,):
+        raise ValueError("types must have one entry per atom")
+    return t if n > 0 else np.zeros(1, np.int32)
+
+
+def _masses(model, mass):
+    m = np.atleast_1d(np.asarray(mass, dtype=np.float64))
+    if m.size == 1:
+        m = np.full(model.n_types, float(m[0]))
+    if m.size != model.n_types:
+        raise ValueError("one mass per species")
+    return np.ascontiguousarray(m)
 
 
 def _check(rc, what):
@@ -91,85 +111,95 @@ def _check(rc, what):
         raise RuntimeError(f"oracle {what} failed with code {rc}")
 
 
-def energy_forces_virial(model, pos, box, pbc, use_grid=True, params=None):
-    """E, F (N,3), W (3,3), U_site (N) of one system."""
+def energy_forces_virial(model, pos, box, pbc, use_grid=True, params=None, types=None):
+    """E, F (N,3), W (3,3), U_site (N) of one system (``types``: species per
+    atom, default all 0)."""
     ihp, dhp = _hp(model)
     p = _f64(model.params if params is None else params)
     s = _f64(model.scaler)
     pos = _f64(pos)
     n = pos.shape[0]
+    t = _types(types, n)
     box = _f64(box)
     pbc = np.ascontiguousarray(pbc, dtype=np.int32)
     E = np.zeros(1)
     F = np.zeros((n, 3))
     W = np.zeros(9)
     U = np.zeros(n)
-    _check(lib().orc_energy_forces_virial(_i(ihp), _d(dhp), _d(p), _d(s), n, _d(pos), _d(box),
-                                          _i(pbc), int(use_grid), _d(E), _d(F), _d(W), _d(U)),
+    _check(lib().orc_energy_forces_virial(_i(ihp), _d(dhp), _d(p), _d(s), n, _d(pos), _i(t),
+                                          _d(box), _i(pbc), int(use_grid), _d(E), _d(F), _d(W),
+                                          _d(U)),
            "energy_forces_virial")
     return float(E[0]), F, W.reshape(3, 3), U
 
 
-def descriptors(model, pos, box, pbc, use_grid=True):
+def descriptors(model, pos, box, pbc, use_grid=True, types=None):
     """Unscaled descriptors (N, D)."""
     ihp, dhp = _hp(model)
     p = _f64(model.params)
     s = _f64(model.scaler if model.scaler is not None else np.ones(model.dim))
     pos = _f64(pos)
     n = pos.shape[0]
+    t = _types(types, n)
     q = np.zeros((n, model.dim))
-    _check(lib().orc_descriptors(_i(ihp), _d(dhp), _d(p), _d(s), n, _d(pos), _d(_f64(box)),
-                                 _i(np.ascontiguousarray(pbc, dtype=np.int32)), int(use_grid),
-                                 _d(q)), "descriptors")
+    _check(lib().orc_descriptors(_i(ihp), _d(dhp), _d(p), _d(s), n, _d(pos), _i(t),
+                                 _d(_f64(box)), _i(np.ascontiguousarray(pbc, dtype=np.int32)),
+                                 int(use_grid), _d(q)), "descriptors")
     return q
 
 
-def forces_subset(model, pos, box, pbc, idx):
+def forces_subset(model, pos, box, pbc, idx, types=None):
     """Forces (len(idx), 3) and site energies (len(idx)) of the listed atoms."""
     ihp, dhp = _hp(model)
     p = _f64(model.params)
     s = _f64(model.scaler)
     pos = _f64(pos)
+    t = _types(types, pos.shape[0])
     idx = np.ascontiguousarray(idx, dtype=np.int64)
     F = np.zeros((len(idx), 3))
     U = np.zeros(len(idx))
-    _check(lib().orc_forces_subset(_i(ihp), _d(dhp), _d(p), _d(s), pos.shape[0], _d(pos),
+    _check(lib().orc_forces_subset(_i(ihp), _d(dhp), _d(p), _d(s), pos.shape[0], _d(pos), _i(t),
                                    _d(_f64(box)), _i(np.ascontiguousarray(pbc, dtype=np.int32)),
                                    len(idx), idx.ctypes.data_as(C.POINTER(C.c_int64)),
                                    _d(F), _d(U)), "forces_subset")
     return F, U
 
 
-def site(model, dR, dA):
-    """U^NEP, q (unscaled), dU/dd for radial and angular neighbour lists of one atom."""
+def site(model, dR, dA, ti=0, tR=None, tA=None):
+    """U^NEP, q (unscaled), dU/dd for radial and angular neighbour lists of one
+    atom of species ``ti`` (neighbour species ``tR``, ``tA``, default 0)."""
     ihp, dhp = _hp(model)
     p = _f64(model.params)
     s = _f64(model.scaler)
     dR = _f64(np.reshape(dR, (-1, 3)))
     dA = _f64(np.reshape(dA, (-1, 3)))
+    tR = _types(tR, dR.shape[0])
+    tA = _types(tA, dA.shape[0])
     U = np.zeros(1)
     q = np.zeros(model.dim)
     gR = np.zeros_like(dR)
     gA = np.zeros_like(dA)
-    _check(lib().orc_site(_i(ihp), _d(dhp), _d(p), _d(s), dR.shape[0], _d(dR), dA.shape[0],
-                          _d(dA), _d(U), _d(q), _d(gR), _d(gA)), "site")
+    _check(lib().orc_site(_i(ihp), _d(dhp), _d(p), _d(s), int(ti), dR.shape[0], _d(dR), _i(tR),
+                          dA.shape[0], _d(dA), _i(tA), _d(U), _d(q), _d(gR), _d(gA)), "site")
     return float(U[0]), q, gR, gA
 
 
 def md(model, pos, vel, box, pbc, mass, dt_max, nsteps, d_max=0.0, forces=None,
-       use_grid=True):
-    """Velocity-Verlet NVE; returns (pos, vel, forces, thermo[nsteps, 4])."""
+       use_grid=True, types=None):
+    """Velocity-Verlet NVE; returns (pos, vel, forces, thermo[nsteps, 4]).
+    ``mass``: one value, or one per species."""
     ihp, dhp = _hp(model)
     p = _f64(model.params)
     s = _f64(model.scaler)
     pos = _f64(pos).copy()
     vel = _f64(vel).copy()
     n = pos.shape[0]
+    t = _types(types, n)
     F = np.zeros((n, 3)) if forces is None else _f64(forces).copy()
     thermo = np.zeros((nsteps, 4))
     _check(lib().orc_md(_i(ihp), _d(dhp), _d(p), _d(s), n, _d(pos), _d(vel), _d(F),
-                        0 if forces is None else 1, _d(_f64(box)),
-                        _i(np.ascontiguousarray(pbc, dtype=np.int32)), float(mass),
+                        0 if forces is None else 1, _i(t), _d(_f64(box)),
+                        _i(np.ascontiguousarray(pbc, dtype=np.int32)), _d(_masses(model, mass)),
                         float(dt_max), float(d_max), int(nsteps), int(use_grid), _d(thermo)),
            "md")
     return pos, vel, F, thermo

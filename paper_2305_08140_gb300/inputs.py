@@ -20,6 +20,11 @@ of the five benchmark configurations:
   constant scaled by U(0.95, 1.05), displacements sigma = 0.1 A (seed 4).
 * ``c5``: 8,192,000-atom bcc W slab, 160x160x160 cells, periodic in x, y,
   open in z with 30 A of vacuum on each side, 300 K (seed 5).
+
+Several species (the multi-species form of the model): ``alloy`` puts a
+random solid solution of the listed species on a bcc lattice, ``b2`` the
+ordered CsCl arrangement of two species, ``hea`` the equiatomic W-Mo-Ta-Nb
+solid solution.  Species data (Z, mass) are the elements' standard values.
 """
 from __future__ import annotations
 
@@ -36,6 +41,9 @@ Z_W = 74               # nuclear charge of W (Eq. 2)
 KB_EV = 8.617333262e-5  # Boltzmann constant, eV/K
 # 1 eV/amu expressed in A^2/fs^2 (CODATA e and u)
 EV_PER_AMU_A2_FS2 = 1.602176634e-19 / 1.66053906660e-27 * 1e-10
+
+# Z and standard atomic mass (amu) of the species the multi-species workloads use
+SPECIES = {"W": (74, 183.84), "Mo": (42, 95.95), "Ta": (73, 180.94788), "Nb": (41, 92.90637)}
 
 _DATA = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
 
@@ -83,15 +91,24 @@ def bcc(nx: int, ny: int, nz: int, a: float = A_W) -> np.ndarray:
 
 
 def maxwell_boltzmann(rng: np.random.Generator, n: int, temperature: float,
-                      mass: float = MASS_W) -> np.ndarray:
+                      mass=MASS_W) -> np.ndarray:
     """Velocities (A/fs) from a Maxwell-Boltzmann draw; the centre-of-mass
     velocity is removed and the set is rescaled to exactly ``temperature``
-    with 3N - 3 degrees of freedom."""
-    sigma = np.sqrt(KB_EV * temperature / mass * EV_PER_AMU_A2_FS2)
-    v = rng.normal(0.0, sigma, size=(n, 3))
-    v -= v.mean(axis=0, keepdims=True)
+    with 3N - 3 degrees of freedom.  ``mass``: one value (the same draw as
+    before per-atom masses existed) or one per atom."""
+    if np.ndim(mass) == 0:
+        sigma = np.sqrt(KB_EV * temperature / mass * EV_PER_AMU_A2_FS2)
+        v = rng.normal(0.0, sigma, size=(n, 3))
+        v -= v.mean(axis=0, keepdims=True)
+        m = np.full(n, float(mass))
+    else:
+        m = np.asarray(mass, dtype=np.float64)
+        sigma = np.sqrt(KB_EV * temperature / m * EV_PER_AMU_A2_FS2)
+        v = rng.normal(0.0, 1.0, size=(n, 3)) * sigma[:, None]
+        if n > 0:
+            v -= (m[:, None] * v).sum(axis=0, keepdims=True) / m.sum()
     if n > 1 and temperature > 0:
-        ke = 0.5 * mass * np.sum(v * v) / EV_PER_AMU_A2_FS2
+        ke = 0.5 * np.sum(m[:, None] * v * v) / EV_PER_AMU_A2_FS2
         t_now = 2.0 * ke / ((3 * n - 3) * KB_EV)
         v *= np.sqrt(temperature / t_now)
     return v
@@ -203,6 +220,44 @@ def displaced(s: Structure, sigma: float, seed: int) -> Structure:
     return t
 
 
+def alloy(s: Structure, fractions, seed: int) -> Structure:
+    """Copy of ``s`` with species drawn per atom: exactly round(f_t N) atoms of
+    species t (the last species takes the remainder), placed by a seeded
+    permutation."""
+    t = s.copy()
+    n = t.n
+    counts = [int(round(f * n)) for f in fractions[:-1]]
+    counts.append(n - sum(counts))
+    labels = np.concatenate([np.full(c, k, np.int32) for k, c in enumerate(counts)])
+    t.types = labels[np.random.default_rng(seed).permutation(n)].astype(np.int32)
+    return t
+
+
+def b2(ncell: int, a: float = A_W) -> Structure:
+    """Ordered CsCl (B2) crystal: species 0 on the cube corners, species 1 on
+    the body centres of a periodic ncell^3 bcc lattice."""
+    s = _cubic(ncell, a)
+    s.types = np.tile(np.array([0, 1], np.int32), s.n // 2)
+    return s
+
+
+def hea(ncell: int = 40, a: float = 3.23, temperature: float = 300.0,
+        seed: int = 6) -> Structure:
+    """Equiatomic random bcc W-Mo-Ta-Nb (species 0..3), periodic ncell^3
+    cells; the seed-6 generator draws the species permutation, then sigma =
+    0.05 A displacements, then velocities at ``temperature`` with each atom's
+    own mass."""
+    s = _cubic(ncell, a)
+    rng = np.random.default_rng(seed)
+    labels = np.tile(np.arange(4, dtype=np.int32), s.n // 4 + 1)[:s.n]
+    s.types = labels[rng.permutation(s.n)].astype(np.int32)
+    s.pos += rng.normal(0.0, 0.05, size=s.pos.shape)
+    masses = np.array([SPECIES[e][1] for e in ("W", "Mo", "Ta", "Nb")])
+    s.vel = maxwell_boltzmann(rng, s.n, temperature, masses[s.types])
+    s.name = f"hea_WMoTaNb_{s.n}"
+    return s
+
+
 def small_box(ncell: tuple[int, int, int], a: float = A_W, sigma: float = 0.0,
               seed: int = 0, pbc=(1, 1, 1)) -> Structure:
     """A bcc box of ``ncell`` cells with optional displacements."""
@@ -218,9 +273,10 @@ def small_box(ncell: tuple[int, int, int], a: float = A_W, sigma: float = 0.0,
 
 @dataclass
 class NepModel:
-    """NEP-ZBL model for one species. ``params`` is the flat parameter vector
-    in the order w0[H x D] (row-major), b0[H], w1[H], b1, cR[nR x KR],
-    cA[nA x KA]; ``scaler`` multiplies the descriptor (length D)."""
+    """NEP-ZBL model. ``params`` is the flat parameter vector in the order
+    w0[H x D] (row-major), b0[H], w1[H], b1, cR[T][T][nR x KR],
+    cA[T][T][nA x KA] (block (a, b): centre species a, neighbour species b;
+    T = number of species); ``scaler`` multiplies the descriptor (length D)."""
     rc_radial: float = 6.0
     rc_angular: float = 4.0
     n_max_radial: int = 4
@@ -230,12 +286,24 @@ class NepModel:
     l_max: int = 4
     use_4body: int = 1
     n_hidden: int = 30
-    z: int = Z_W
+    species: tuple = ("W",)
     zbl_r_inner: float = 1.0
     zbl_r_outer: float = 2.0
     params: np.ndarray | None = None
     scaler: np.ndarray | None = None
     seed: int = 1
+
+    @property
+    def n_types(self) -> int:
+        return len(self.species)
+
+    @property
+    def zs(self) -> list[int]:
+        return [SPECIES[e][0] for e in self.species]
+
+    @property
+    def masses(self) -> list[float]:
+        return [SPECIES[e][1] for e in self.species]
 
     @property
     def dim(self) -> int:
@@ -248,7 +316,7 @@ class NepModel:
         D, H = self.dim, self.n_hidden
         nR, nA = self.n_max_radial + 1, self.n_max_angular + 1
         KR, KA = self.basis_size_radial + 1, self.basis_size_angular + 1
-        return H * D + H + H + 1 + nR * KR + nA * KA
+        return H * D + H + H + 1 + self.n_types ** 2 * (nR * KR + nA * KA)
 
 
 def draw_params(model: NepModel, seed: int) -> np.ndarray:
@@ -276,29 +344,39 @@ def random_packing(ncell: int = 4, min_sep: float = 2.2, seed: int = 200) -> Str
                      np.zeros(n, np.int32), name="liquid_like")
 
 
-def scaler_structures() -> list[Structure]:
+def scaler_structures(n_types: int = 1) -> list[Structure]:
     """Structures over which the descriptor scaler is taken, one of each kind
     the paper's W training set contains (Sec. III.A: bulk bcc, strongly
     disordered and liquid structures, short interatomic distances): the c1
     crystal, a hot crystal (sigma = 0.3 A), a liquid-like random packing and a
-    crystal compressed to 0.9 a."""
-    return [c1(), small_box((6, 6, 6), sigma=0.3, seed=201), random_packing(),
-            small_box((6, 6, 6), a=0.9 * A_W, sigma=0.1, seed=202)]
+    crystal compressed to 0.9 a.  For several species each structure becomes an
+    equiatomic random solid solution (seeds 210, 211, ...)."""
+    out = [c1(), small_box((6, 6, 6), sigma=0.3, seed=201), random_packing(),
+           small_box((6, 6, 6), a=0.9 * A_W, sigma=0.1, seed=202)]
+    if n_types > 1:
+        out = [alloy(s, [1.0 / n_types] * n_types, 210 + k) for k, s in enumerate(out)]
+    return out
 
 
-def stored_scaler(seed: int) -> np.ndarray:
+def scaler_key(seed: int, species=("W",)) -> str:
+    """Key of a model's scaler in the stored table."""
+    return str(seed) if tuple(species) == ("W",) else f"{seed}:{'-'.join(species)}"
+
+
+def stored_scaler(seed: int, species=("W",)) -> np.ndarray:
     """Descriptor scaler for the parameter set ``seed``: s_nu = 1 / max |q_nu^i|
     over all atoms i of ``scaler_structures()``, as written by the oracle's
     scaler script."""
     with open(os.path.join(_DATA, "q_scaler.json")) as f:
         table = json.load(f)
-    return np.array(table["scalers"][str(seed)], dtype=np.float64)
+    return np.array(table["scalers"][scaler_key(seed, species)], dtype=np.float64)
 
 
-def nep_model(seed: int = 1, with_scaler: bool = True) -> NepModel:
-    """The random-init W model: r_c 6/4 A, n_max 4/4, basis 8, l_max 4 with the
-    4-body term, 30 hidden neurons, ZBL switch 1.0/2.0 A."""
-    m = NepModel(seed=seed)
+def nep_model(seed: int = 1, with_scaler: bool = True, species=("W",)) -> NepModel:
+    """The random-init model: r_c 6/4 A, n_max 4/4, basis 8, l_max 4 with the
+    4-body term, 30 hidden neurons, ZBL switch 1.0/2.0 A; W alone unless
+    ``species`` lists several."""
+    m = NepModel(seed=seed, species=tuple(species))
     m.params = draw_params(m, seed)
-    m.scaler = stored_scaler(seed) if with_scaler else np.ones(m.dim)
+    m.scaler = stored_scaler(seed, species) if with_scaler else np.ones(m.dim)
     return m

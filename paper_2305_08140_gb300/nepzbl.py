@@ -151,16 +151,20 @@ class NEP:
     ``model`` is an ``inputs.NepModel`` (hyperparameters, flat parameters,
     scaler); ``precision`` is "fp32" (mixed) or "fp64"."""
 
-    def __init__(self, model, precision: str = "fp32", mass: float | None = None):
+    def __init__(self, model, precision: str = "fp32", mass=None):
         self.lib = load()
         self.model = model
         self._params = np.ascontiguousarray(model.params, dtype=np.float64)
         self._scaler = np.ascontiguousarray(model.scaler, dtype=np.float64)
         p = NepParams()
-        p.n_types = 1
-        p.z[0] = int(model.z)
-        from .inputs import MASS_W
-        p.mass[0] = float(MASS_W if mass is None else mass)
+        T = model.n_types
+        if not 1 <= T <= 4:
+            raise ValueError("1 to 4 species")
+        masses = model.masses if mass is None else np.broadcast_to(np.asarray(mass, float), (T,))
+        p.n_types = T
+        for t in range(T):
+            p.z[t] = int(model.zs[t])
+            p.mass[t] = float(masses[t])
         p.rc_radial = model.rc_radial
         p.rc_angular = model.rc_angular
         p.zbl_r_inner = model.zbl_r_inner

@@ -27,7 +27,7 @@ def _params_struct(model):
             np.ascontiguousarray(model.scaler, dtype=np.float64))
     p = N.NepParams()
     p.n_types = 1
-    p.z[0] = int(model.z)
+    p.z[0] = int(model.zs[0])
     p.mass[0] = I.MASS_W
     p.rc_radial, p.rc_angular = model.rc_radial, model.rc_angular
     p.zbl_r_inner, p.zbl_r_outer = model.zbl_r_inner, model.zbl_r_outer
