@@ -65,12 +65,17 @@ extern "C" {
 typedef struct nep_ctx nep_ctx;   /* opaque; created by nep_init */
 
 /* Model definition, copied by nep_init (the caller may free it afterwards).
- * This build supports n_types = 1, n_max_radial = n_max_angular = 4,
+ * This build supports n_types = 1..4, n_max_radial = n_max_angular = 4,
  * basis_size_radial = basis_size_angular = 8, l_max = 4, use_4body = 1,
- * n_hidden = 30 (descriptor length D = 30, 1051 parameters), with
- * zbl_r_outer <= rc_angular <= rc_radial. */
+ * n_hidden = 30 (descriptor length D = 30; 961 + 90 T^2 parameters for T
+ * species, 1051 for one), with zbl_r_outer <= rc_angular <= rc_radial.
+ * Several species (the multi-species form of the NEP descriptor, Sec. II.A
+ * and the NEP papers it cites): every pair term of the pair (i, j) uses the
+ * coefficient block of the ordered species pair (t_i, t_j); the network is
+ * shared; the ZBL term of the pair uses Z_{t_i}, Z_{t_j} in Eq. 2 and 4
+ * (with the W-W screening function of Eq. 3 for every pair). */
 typedef struct nep_params {
-    int32_t n_types;                 /* number of species (1) */
+    int32_t n_types;                 /* number of species T (1..4) */
     int32_t z[4];                    /* nuclear charge Z per species (Eq. 2, 4) */
     double  mass[4];                 /* mass per species (amu), used by md_step */
     double  rc_radial;               /* r_c^R (A) */
@@ -85,7 +90,8 @@ typedef struct nep_params {
     int32_t use_4body;               /* 1: append q4_n = tr(T_n^3) */
     int32_t n_hidden;                /* hidden tanh neurons */
     const double* params;            /* host, flat: w0[H][D] row-major, b0[H], w1[H], b1,
-                                        cR[nR][KR], cA[nA][KA] */
+                                        cR[T][T][nR][KR], cA[T][T][nA][KA] (block
+                                        [t_i][t_j]: centre species, neighbour species) */
     int64_t n_params;                /* length of params */
     const double* q_scaler;          /* host, length D: s_nu */
 } nep_params;
@@ -108,7 +114,8 @@ const char* nep_last_error(const nep_ctx* ctx);
  *                A periodic dimension needs box[d][d] >= 3 * rc_radial.  For an
  *                open dimension, box[d][d] is the extent [0, L) over which the
  *                cell grid is laid (atoms outside it are still handled).
- *   types        device int32[n_atoms] species index (all 0 in this build)
+ *   types        device int32[n_atoms] species index in [0, n_types); an index
+ *                outside is reported as NEP_ERR_INVALID_ARG
  *   pbc          host int32[3], 1 periodic, 0 open
  *   energy       host double[1]: E (eV)
  *   forces       device double[3 * n_atoms], SoA (eV/A), overwritten
@@ -128,7 +135,8 @@ typedef struct nep_md_state {
                                periodic coordinates are wrapped into [0, L) */
     double* vel;            /* device double[3n] SoA velocities (A/fs) */
     double* forces;         /* device double[3n] SoA forces at xyz (eV/A) */
-    const int32_t* types;   /* device int32[n] */
+    const int32_t* types;   /* device int32[n] species in [0, n_types); each atom moves
+                               with the mass of its species (nep_params.mass) */
     double box[9];          /* host copy of the cell (see nep_compute) */
     int32_t pbc[3];
     int32_t forces_valid;   /* in/out: 0 = md_step first computes forces at xyz */
@@ -208,9 +216,10 @@ typedef struct nep_batch {
                                     configuration; offsets[n_configs] = n_atoms */
     const double* boxes;         /* host double[3 * n_configs]: periodic orthorhombic box
                                     lengths, each >= rc_radial */
-    const int32_t* types;        /* device int32[n_atoms] (all 0 in this build) */
+    const int32_t* types;        /* device int32[n_atoms] (all 0: one species) */
 } nep_batch;
-/* Each configuration holds 1..512 atoms. */
+/* Each configuration holds 1..512 atoms.  The batched entry points support
+ * one species (n_types = 1); other models get NEP_ERR_UNSUPPORTED. */
 
 /* Replaces the model parameters (same layout and length as nep_params.params;
  * the descriptor scaler is kept).  Host memory. */
@@ -251,7 +260,9 @@ int nep_batch_autotune(nep_ctx* ctx, const nep_batch* batch, const double* E_tar
  * (no context: creating one allocates) and computes the same FP32 evaluation
  * as nep_compute with a context created with NEP_FP32; arguments as in
  * nep_compute.
- *   Limits: at most 8192 atoms, 96 neighbours per atom within rc_radial
+ *   Limits: one species (n_types = 1, else NEP_ERR_UNSUPPORTED; a nonzero
+ *   species index gives NEP_ERR_INVALID_ARG), at most 8192 atoms, 96
+ *   neighbours per atom within rc_radial
  *   (beyond that NEP_ERR_NBR_OVERFLOW; there is no growth), a cell grid of at
  *   most 8192 cells.  Larger systems are rejected with NEP_ERR_INVALID_ARG or
  *   NEP_ERR_BOX before any GPU work.

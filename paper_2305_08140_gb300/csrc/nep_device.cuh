@@ -13,6 +13,11 @@
 //                  slots [M - nro, M) hold rc_A <= r < rc_R
 //   facc[a * ld + k] force accumulators in cell order: int64 fixed point
 //                  (2^-32 eV/A) for float, double for double
+//   coef[p * CSTR]  (several species) coefficients of the ordered species
+//                  pair p = t_i * T + t_j: radial h (c/2) [0, 45), C [45, 50),
+//                  angular h [52, 97), C [97, 102)
+//   br[(k * T + t) * 3]  radial adjoint of atom k contracted with the
+//                  coefficients of neighbour species t (b_0..b_8, B0, 0, 0)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -26,9 +31,12 @@ constexpr int NR = 5, NA = 5, KR = 9, KA = 9, LM = 4, NLM = 24, H = 30;
 constexpr int D = NR + NA * LM + NA;   // 30
 constexpr int TILE = 128;              // atoms per block of the force kernel
 constexpr int NPART = 10;              // energy + 9 virial components per tile
+constexpr int NT_MAX = 4;              // species
+constexpr int CSTR = 104;              // coefficients per ordered species pair
+constexpr int C_RAD = 0, C_ANG = 52;   // radial / angular block offsets
 
 // status bits
-constexpr int ST_OVERFLOW = 1, ST_NONFINITE = 2, ST_FORCE_RANGE = 4;
+constexpr int ST_OVERFLOW = 1, ST_NONFINITE = 2, ST_FORCE_RANGE = 4, ST_BADTYPE = 8;
 
 template <typename R> struct V4 { using T = float4; };
 template <> struct V4<double> { using T = double4_32a; };
@@ -46,6 +54,9 @@ struct Model {
     double zbl_k;            // e^2/(4 pi eps0) Zi Zj (eV A)
     double zbl_inv_a;        // 1 / a (Eq. 4)
     double zbl_r1, zbl_rr2;  // switch radii
+    int ntypes;              // species
+    double zbl_kp[NT_MAX * NT_MAX];      // zbl_k of the ordered pair t_i * T + t_j
+    double zbl_inv_ap[NT_MAX * NT_MAX];  // zbl_inv_a of the pair
 };
 
 // Cell grid and sizes.
@@ -57,6 +68,7 @@ struct Grid {
     int n;                     // atoms
     int ld;                    // leading dimension of nbr / facc (atom capacity)
     int M;                     // neighbour slots per atom
+    int ntypes;                // species (types must lie in [0, ntypes))
 };
 
 // ----------------------------------------------------------------------------
@@ -202,8 +214,8 @@ __global__ void k_cell_finalize(Grid g, int ncell, const int* __restrict__ start
                                 int* __restrict__ perm, const double* __restrict__ x,
                                 const int32_t* __restrict__ types,
                                 typename V4<R>::T* __restrict__ pos4,
-                                int* __restrict__ cell_sorted,
-                            const int* __restrict__ gate = nullptr)
+                                int* __restrict__ cell_sorted, int* __restrict__ status,
+                                const int* __restrict__ gate = nullptr)
 {
     if (gate && *gate == 0) return;   // lists still valid (Verlet skin)
     int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -216,6 +228,7 @@ __global__ void k_cell_finalize(Grid g, int ncell, const int* __restrict__ start
     }
     int cz = c % g.nc[2], cy = (c / g.nc[2]) % g.nc[1], cx = c / (g.nc[2] * g.nc[1]);
     int cc[3] = {cx, cy, cz};
+    bool badtype = false;
     for (int s = b; s < e; ++s) {
         int i = perm[s];
         R rel[3];
@@ -228,10 +241,13 @@ __global__ void k_cell_finalize(Grid g, int ncell, const int* __restrict__ start
         }
         typename V4<R>::T q;
         q.x = rel[0]; q.y = rel[1]; q.z = rel[2];
-        q.w = (R)types[i];
+        int t = types[i];
+        if (t < 0 || t >= g.ntypes) { badtype = true; t = 0; }
+        q.w = (R)t;
         pos4[s] = q;
         cell_sorted[s] = c;
     }
+    if (badtype) atomicOr(status, ST_BADTYPE);
 }
 
 // ----------------------------------------------------------------------------
@@ -505,11 +521,10 @@ __device__ __forceinline__ void radial_q(const Model<R>& P, const R (&Sb)[KR], R
 }
 
 // Network U(q) and its backward.  On return A holds dU/dA_nlm (4-body term
-// folded into l = 2), bR/B0 the radial adjoint contracted with the basis
-// coefficients: sum_n dU/dq_n g'_n(r) = df_c (B0 + sum_k bR_k T_k) + f_c x' sum_k bR_k T'_k.
+// folded into l = 2) and aR the radial adjoint dU/dq_n.
 template <typename R>
-__device__ __forceinline__ R network_adjoint(const Model<R>& P, const R (&qR)[NR],
-                                             R (&A)[NA][NLM], R (&bR)[KR], R& B0)
+__device__ __forceinline__ R network_adjoint_core(const Model<R>& P, const R (&qR)[NR],
+                                                  R (&A)[NA][NLM], R (&aR)[NR])
 {
     R h[H];
 #pragma unroll
@@ -545,17 +560,12 @@ __device__ __forceinline__ R network_adjoint(const Model<R>& P, const R (&qR)[NR
         U += P.w1[mu] * t;
         h[mu] = P.w1[mu] * (R(1) - t * t);   // dU/dh_mu
     }
-    B0 = R(0);
-#pragma unroll
-    for (int kk = 0; kk < KR; ++kk) bR[kk] = R(0);
 #pragma unroll
     for (int nu = 0; nu < NR; ++nu) {
         R a = R(0);
 #pragma unroll
         for (int mu = 0; mu < H; ++mu) a += h[mu] * P.w0[mu * D + nu];
-        B0 += a * P.CR[nu];
-#pragma unroll
-        for (int kk = 0; kk < KR; ++kk) bR[kk] += a * P.hR[nu * KR + kk];
+        aR[nu] = a;
     }
 #pragma unroll
     for (int n = 0; n < NA; ++n) {
@@ -582,6 +592,26 @@ __device__ __forceinline__ R network_adjoint(const Model<R>& P, const R (&qR)[NR
 #pragma unroll
             for (int lm = lo; lm < hi; ++lm) A[n][lm] *= R(2) * a;
         }
+    }
+    return U;
+}
+
+// One species: the radial adjoint contracted with the basis coefficients,
+// sum_n dU/dq_n g'_n(r) = df_c (B0 + sum_k bR_k T_k) + f_c x' sum_k bR_k T'_k.
+template <typename R>
+__device__ __forceinline__ R network_adjoint(const Model<R>& P, const R (&qR)[NR],
+                                             R (&A)[NA][NLM], R (&bR)[KR], R& B0)
+{
+    R aR[NR];
+    const R U = network_adjoint_core<R>(P, qR, A, aR);
+    B0 = R(0);
+#pragma unroll
+    for (int kk = 0; kk < KR; ++kk) bR[kk] = R(0);
+#pragma unroll
+    for (int nu = 0; nu < NR; ++nu) {
+        B0 += aR[nu] * P.CR[nu];
+#pragma unroll
+        for (int kk = 0; kk < KR; ++kk) bR[kk] += aR[nu] * P.hR[nu * KR + kk];
     }
     return U;
 }
@@ -853,16 +883,21 @@ __device__ __forceinline__ int list_slot(int s, int na, int M)
 // lists of the pairs within r_c (angular ones from the front, radial-only ones
 // from the back, same layout as nbr), so the angular and radial-force kernels
 // never branch over pairs beyond the cutoffs.
-template <typename R>
+// MS (several species): basis sums per neighbour species, Sb[t][k] =
+// sum_{j of species t} f_c T_k, contracted per atom with the coefficients of
+// the pairs (t_i, t) from coef.
+template <typename R, bool MS>
 __global__ void __launch_bounds__(128) k_radial_q(const Model<R> P, const Grid g,
                                                   const typename V4<R>::T* __restrict__ pos4,
                                                   const int* __restrict__ nbr,
                                                   const int2* __restrict__ cnt,
                                                   R* __restrict__ qr,
-                                                  int* __restrict__ act_nbr = nullptr,
-                                                  int2* __restrict__ act_cnt = nullptr)
+                                                  int* __restrict__ act_nbr,
+                                                  int2* __restrict__ act_cnt,
+                                                  const R* __restrict__ coef)
 {
     using P4 = typename V4<R>::T;
+    constexpr int NTS = MS ? NT_MAX : 1;
     __shared__ P4 s_off[27];
     fill_stencil<R>(s_off, g);
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -871,9 +906,12 @@ __global__ void __launch_bounds__(128) k_radial_q(const Model<R> P, const Grid g
     const int2 c2 = cnt[k];
     const int na = c2.x, total = c2.x + c2.y, M = g.M;
     const P4 pi = pos4[k];
-    R Sb[KR];
+    const int T = MS ? P.ntypes : 1;
+    R Sb[NTS][KR];
 #pragma unroll
-    for (int kk = 0; kk < KR; ++kk) Sb[kk] = R(0);
+    for (int t = 0; t < NTS; ++t)
+#pragma unroll
+        for (int kk = 0; kk < KR; ++kk) Sb[t][kk] = R(0);
     int a_na = 0, a_nro = 0;
     // two-stage prefetch: entry s + 2 and position s + 1 in flight during pair s
     int ent_n = total > 0 ? nbr[(size_t)list_slot(0, na, M) * ld + k] : 0;
@@ -894,33 +932,68 @@ __global__ void __launch_bounds__(128) k_radial_q(const Model<R> P, const Grid g
             else act_nbr[(size_t)(M - 1 - a_nro++) * ld + k] = ent;
         }
         const R r = r2 * nepm::nep_rsqrt(r2);
-        R T[KR], dT[KR], fc, dfc, dxdr;
-        nepm::cheb<KR, false>(r, P.inv_rcR, T, dT, fc, dfc, dxdr);
+        R Tk[KR], dT[KR], fc, dfc, dxdr;
+        nepm::cheb<KR, false>(r, P.inv_rcR, Tk, dT, fc, dfc, dxdr);
+        if constexpr (MS) {
+            const int tj = (int)pj.w;
 #pragma unroll
-        for (int kk = 0; kk < KR; ++kk) Sb[kk] += fc * T[kk];
+            for (int t = 0; t < NTS; ++t) {
+                if (t < T) {
+                    const R wt = tj == t ? fc : R(0);
+#pragma unroll
+                    for (int kk = 0; kk < KR; ++kk) Sb[t][kk] += wt * Tk[kk];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int kk = 0; kk < KR; ++kk) Sb[0][kk] += fc * Tk[kk];
+        }
     }
     if (act_cnt) act_cnt[k] = make_int2(a_na, a_nro);
     R q[NR];
-    radial_q<R>(P, Sb, q);
+    if constexpr (MS) {
+        const int ti = (int)pi.w;
+#pragma unroll
+        for (int n = 0; n < NR; ++n) q[n] = R(0);
+#pragma unroll
+        for (int t = 0; t < NTS; ++t) {
+            if (t < T) {
+                const R* c = coef + (size_t)(ti * T + t) * CSTR + C_RAD;
+#pragma unroll
+                for (int n = 0; n < NR; ++n) {
+                    R acc = c[NR * KR + n] * Sb[t][0];
+#pragma unroll
+                    for (int kk = 0; kk < KR; ++kk) acc += c[n * KR + kk] * Sb[t][kk];
+                    q[n] += acc;
+                }
+            }
+        }
+    } else {
+        radial_q<R>(P, Sb[0], q);
+    }
 #pragma unroll
     for (int n = 0; n < NR; ++n) qr[(size_t)n * ld + k] = q[n];
 }
 
 // Angular part of dU_i/dd_ij for one angular neighbour (no radial term).
+// cs: the pair's angular coefficients (h [0, 45), C [45, 50)) with several
+// species, nullptr for the model's own (one species).
 template <typename R>
 __device__ __forceinline__ void force_pair_ang(const Model<R>& P, R r, R inv_r, R ux, R uy, R uz,
-                                               const R (&Ab)[NA][NLM], R& fx, R& fy, R& fz)
+                                               const R (&Ab)[NA][NLM], R& fx, R& fy, R& fz,
+                                               const R* cs = nullptr)
 {
     R T[KA], dT[KA], fc, dfc, dxdr;
     nepm::cheb<KA, true>(r, P.inv_rcA, T, dT, fc, dfc, dxdr);
     R gn[NA], dgn[NA];
 #pragma unroll
     for (int n = 0; n < NA; ++n) {
-        R a = P.CA[n], b = R(0);
+        R a = cs ? cs[NA * KA + n] : P.CA[n], b = R(0);
 #pragma unroll
         for (int kk = 0; kk < KA; ++kk) {
-            a += P.hA[n * KA + kk] * T[kk];
-            b += P.hA[n * KA + kk] * dT[kk];
+            const R h = cs ? cs[n * KA + kk] : P.hA[n * KA + kk];
+            a += h * T[kk];
+            b += h * dT[kk];
         }
         gn[n] = fc * a;
         dgn[n] = dfc * a + fc * dxdr * b;
@@ -979,7 +1052,11 @@ __device__ __forceinline__ void tile_partials(double e_site, R (&w)[9], double (
     }
 }
 
-template <typename R>
+// MS (several species): the coefficient table of all ordered species pairs
+// is copied to shared memory ahead of the staged entries; each angular pair
+// reads its own block, and the radial adjoint is written once per neighbour
+// species (br[(k * T + t) * 3]).
+template <typename R, bool MS>
 __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g,
                                                   const typename V4<R>::T* __restrict__ pos4,
                                                   const int* __restrict__ nbr,
@@ -991,13 +1068,22 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
                                                   typename Acc<R>::T* __restrict__ facc,
                                                   double* __restrict__ partials,
                                                   double* __restrict__ site_energy,
-                                                  int* __restrict__ status, int stage_slots)
+                                                  int* __restrict__ status, int stage_slots,
+                                                  const R* __restrict__ coef)
 {
     using A_ = Acc<R>;
     using P4 = typename V4<R>::T;
     __shared__ P4 s_off[27];
     __shared__ int s_max;
-    extern __shared__ int s_ent[];   // [stage_slots][TILE] angular entries
+    // dynamic: [T * T * CSTR] coefficients (MS only), then [stage_slots][TILE]
+    // angular entries
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    const int T = MS ? P.ntypes : 1;
+    R* s_coef = reinterpret_cast<R*>(s_dyn);
+    int* s_ent = reinterpret_cast<int*>(s_dyn + (MS ? sizeof(R) * T * T * CSTR : 0));
+    if constexpr (MS) {
+        for (int t = threadIdx.x; t < T * T * CSTR; t += TILE) s_coef[t] = coef[t];
+    }
     if (threadIdx.x == 0) s_max = 0;
     fill_stencil<R>(s_off, g);
     const int k = blockIdx.x * TILE + threadIdx.x;
@@ -1017,6 +1103,7 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
 
     if (k < g.n) {
         const P4 pi = pos4[k];
+        const int ti = MS ? (int)pi.w : 0;
         auto entry = [&](int s) -> int {
             return staged ? s_ent[s * TILE + threadIdx.x] : nbr[(size_t)s * ld + k];
         };
@@ -1040,15 +1127,16 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
             if (r2 >= P.rcA2) continue;   // beyond r_c^A (lists built with a skin)
             const R inv_r = nepm::nep_rsqrt(r2);
             const R r = r2 * inv_r;
-            R T[KA], dT[KA], fc, dfc, dxdr;
-            nepm::cheb<KA, false>(r, P.inv_rcA, T, dT, fc, dfc, dxdr);
+            R Tk[KA], dT[KA], fc, dfc, dxdr;
+            nepm::cheb<KA, false>(r, P.inv_rcA, Tk, dT, fc, dfc, dxdr);
             R Y[NLM];
             nepm::harmonics(dx * inv_r, dy * inv_r, dz * inv_r, Y);
+            const R* cs = MS ? s_coef + ((size_t)ti * T + (int)pj.w) * CSTR + C_ANG : nullptr;
 #pragma unroll
             for (int n = 0; n < NA; ++n) {
-                R acc = P.CA[n];
+                R acc = MS ? cs[NA * KA + n] : P.CA[n];
 #pragma unroll
-                for (int kk = 0; kk < KA; ++kk) acc += P.hA[n * KA + kk] * T[kk];
+                for (int kk = 0; kk < KA; ++kk) acc += (MS ? cs[n * KA + kk] : P.hA[n * KA + kk]) * Tk[kk];
                 const R gn = fc * acc;
 #pragma unroll
                 for (int lm = 0; lm < NLM; ++lm) A[n][lm] += gn * Y[lm];
@@ -1057,16 +1145,36 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
         R qR[NR];
 #pragma unroll
         for (int n = 0; n < NR; ++n) qR[n] = qr[(size_t)n * ld + k];
-        R bR[KR], B0;
-        const R U = network_adjoint<R>(P, qR, A, bR, B0);
-        {
+        R U;
+        auto store_b = [&](const R (&bR)[KR], R B0, size_t slot) {
             P4 b0v, b1v, b2v;
             b0v.x = bR[0]; b0v.y = bR[1]; b0v.z = bR[2]; b0v.w = bR[3];
             b1v.x = bR[4]; b1v.y = bR[5]; b1v.z = bR[6]; b1v.w = bR[7];
             b2v.x = bR[8]; b2v.y = B0; b2v.z = R(0); b2v.w = R(0);
-            br[3 * (size_t)k] = b0v;
-            br[3 * (size_t)k + 1] = b1v;
-            br[3 * (size_t)k + 2] = b2v;
+            br[3 * slot] = b0v;
+            br[3 * slot + 1] = b1v;
+            br[3 * slot + 2] = b2v;
+        };
+        if constexpr (MS) {
+            R aR[NR];
+            U = network_adjoint_core<R>(P, qR, A, aR);
+            for (int t = 0; t < T; ++t) {
+                const R* c = s_coef + ((size_t)ti * T + t) * CSTR + C_RAD;
+                R bR[KR], B0 = R(0);
+#pragma unroll
+                for (int kk = 0; kk < KR; ++kk) bR[kk] = R(0);
+#pragma unroll
+                for (int nu = 0; nu < NR; ++nu) {
+                    B0 += aR[nu] * c[NR * KR + nu];
+#pragma unroll
+                    for (int kk = 0; kk < KR; ++kk) bR[kk] += aR[nu] * c[nu * KR + kk];
+                }
+                store_b(bR, B0, (size_t)k * T + t);
+            }
+        } else {
+            R bR[KR], B0;
+            U = network_adjoint<R>(P, qR, A, bR, B0);
+            store_b(bR, B0, (size_t)k);
         }
 
         typename A_::T fi[3] = {0, 0, 0};
@@ -1090,7 +1198,9 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
             const R inv_r = nepm::nep_rsqrt(r2);
             const R r = r2 * inv_r;
             R fx, fy, fz;
-            force_pair_ang<R>(P, r, inv_r, dx * inv_r, dy * inv_r, dz * inv_r, A, fx, fy, fz);
+            force_pair_ang<R>(P, r, inv_r, dx * inv_r, dy * inv_r, dz * inv_r, A, fx, fy, fz,
+                              MS ? s_coef + ((size_t)ti * T + (int)pj.w) * CSTR + C_ANG
+                                 : nullptr);
             bad |= !isfinite(fx + fy + fz);
             typename A_::T cx = A_::conv(fx), cy = A_::conv(fy), cz = A_::conv(fz);
             if (r < P.zbl_r2) {
@@ -1108,7 +1218,9 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
                 const double r64 = sqrt(d64[0] * d64[0] + d64[1] * d64[1] + d64[2] * d64[2]);
                 if (r64 < P.zbl_rr2) {
                     double Uz, dUz;
-                    zbl_pair(r64, P.zbl_k, P.zbl_inv_a, P.zbl_r1, P.zbl_rr2, Uz, dUz);
+                    const int pz = MS ? ti * T + (int)pj.w : 0;
+                    zbl_pair(r64, MS ? P.zbl_kp[pz] : P.zbl_k, MS ? P.zbl_inv_ap[pz] : P.zbl_inv_a,
+                             P.zbl_r1, P.zbl_rr2, Uz, dUz);
                     ez += 0.5 * Uz;
                     const double c = 0.5 * dUz / r64;
                     const double f3[3] = {c * d64[0], c * d64[1], c * d64[2]};
@@ -1147,7 +1259,9 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
 // so each atom sums its own radial force from its neighbours' packed adjoint
 // (bp[k] = (b_0..b_8, B0), 12 values per atom) without atomics; the virial is
 // -1/2 sum_i sum_j (f_ij - f_ji) (x) d_ij.
-template <typename R>
+// MS (several species): the pair (i, j) adds atom i's adjoint for neighbour
+// species t_j and atom j's for species t_i (bp[(k * T + t) * 3]).
+template <typename R, bool MS>
 __global__ void __launch_bounds__(TILE) k_radial_force(const Model<R> P, const Grid g,
                                                        const typename V4<R>::T* __restrict__ pos4,
                                                        const int* __restrict__ nbr,
@@ -1171,15 +1285,17 @@ __global__ void __launch_bounds__(TILE) k_radial_force(const Model<R> P, const G
         const int2 c2 = cnt[k];
         const int na = c2.x, total = c2.x + c2.y, M = g.M;
         const P4 pi = pos4[k];
-        const P4 bi0 = bp[3 * (size_t)k], bi1 = bp[3 * (size_t)k + 1], bi2 = bp[3 * (size_t)k + 2];
+        const int T = MS ? P.ntypes : 1;
+        const int ti = MS ? (int)pi.w : 0;
+        P4 bi0 = bp[3 * (size_t)k], bi1 = bp[3 * (size_t)k + 1], bi2 = bp[3 * (size_t)k + 2];
         R fx = R(0), fy = R(0), fz = R(0);
         // two-stage prefetch: entry s + 2, position and adjoint s + 1 in flight
         int ent_n = total > 0 ? nbr[(size_t)list_slot(0, na, M) * ld + k] : 0;
         int ent_nn = total > 1 ? nbr[(size_t)list_slot(1, na, M) * ld + k] : 0;
         P4 pj_n = pi, bj0_n = bi0, bj1_n = bi1, bj2_n = bi2;
         if (total > 0) {
-            const size_t m0 = (size_t)(ent_n >> 5);
-            pj_n = pos4[m0];
+            const size_t m0 = (size_t)(ent_n >> 5) * T + ti;
+            pj_n = pos4[ent_n >> 5];
             bj0_n = bp[3 * m0]; bj1_n = bp[3 * m0 + 1]; bj2_n = bp[3 * m0 + 2];
         }
         for (int s = 0; s < total; ++s) {
@@ -1187,9 +1303,14 @@ __global__ void __launch_bounds__(TILE) k_radial_force(const Model<R> P, const G
             const P4 pj = pj_n, bj0 = bj0_n, bj1 = bj1_n, bj2 = bj2_n;
             ent_n = ent_nn;
             if (s + 1 < total) {
-                const size_t m1 = (size_t)(ent_n >> 5);
-                pj_n = pos4[m1];
+                const size_t m1 = (size_t)(ent_n >> 5) * T + ti;
+                pj_n = pos4[ent_n >> 5];
                 bj0_n = bp[3 * m1]; bj1_n = bp[3 * m1 + 1]; bj2_n = bp[3 * m1 + 2];
+            }
+            if constexpr (MS) {
+                // this atom's adjoint for the neighbour's species (L1-resident)
+                const size_t mi = (size_t)k * T + (int)pj.w;
+                bi0 = bp[3 * mi]; bi1 = bp[3 * mi + 1]; bi2 = bp[3 * mi + 2];
             }
             if (s + 2 < total) ent_nn = nbr[(size_t)list_slot(s + 2, na, M) * ld + k];
             const P4 off = s_off[ent & 31];
@@ -1298,14 +1419,30 @@ static __global__ void __launch_bounds__(256) k_reduce_partials(const double* __
 constexpr int TH_DT = 0, TH_TIME = 1, TH_STEP = 2, TH_KE = 3, TH_VMAX = 4, TH_DTMAX = 5,
               TH_DMAX = 6, TH_DTLAST = 7, TH_N = 8;
 
+// Masses of the species: m[t] (amu) and acc[t] = (1 eV/amu in A^2/fs^2) / m[t].
+struct MassTab {
+    int ntypes;
+    double m[NT_MAX];
+    double acc[NT_MAX];
+};
+
+__device__ __forceinline__ int species_of(const MassTab& mt, const int32_t* types, int i)
+{
+    if (mt.ntypes == 1) return 0;
+    const int t = types[i];
+    return t < 0 ? 0 : (t >= mt.ntypes ? mt.ntypes - 1 : t);   // flagged by k_cell_finalize
+}
+
 // v += dt/2 F/m ; x += dt v ; wrap periodic coordinates into [0, L)
-static __global__ void k_kick_drift(Grid g, double acc, const double* __restrict__ thermo,
+static __global__ void k_kick_drift(Grid g, MassTab mt, const int32_t* __restrict__ types,
+                             const double* __restrict__ thermo,
                              double* __restrict__ x, double* __restrict__ v,
                              const double* __restrict__ F)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n) return;
     const double dt = thermo[TH_DT];
+    const double acc = mt.acc[species_of(mt, types, i)];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         size_t o = (size_t)a * g.n + i;
@@ -1317,26 +1454,29 @@ static __global__ void k_kick_drift(Grid g, double acc, const double* __restrict
     }
 }
 
-// v += dt/2 F/m and per-block (sum v^2, max |v|)
-static __global__ void __launch_bounds__(256) k_kick_thermo(int n, double acc,
+// v += dt/2 F/m and per-block (sum m v^2, max |v|^2)
+static __global__ void __launch_bounds__(256) k_kick_thermo(int n, MassTab mt,
+                                                     const int32_t* __restrict__ types,
                                                      const double* __restrict__ thermo,
                                                      double* __restrict__ v,
                                                      const double* __restrict__ F,
                                                      double* __restrict__ part, int half_kick)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double v2 = 0.0;
+    double v2 = 0.0, vm = 0.0;
     if (i < n) {
+        const int t = species_of(mt, types, i);
+        const double acc = mt.acc[t];
         const double dt = half_kick ? thermo[TH_DT] : 0.0;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             size_t o = (size_t)a * n + i;
             double vv = v[o] + 0.5 * dt * acc * F[o];
             if (half_kick) v[o] = vv;
-            v2 += vv * vv;
+            vm += vv * vv;
         }
+        v2 = mt.m[t] * vm;
     }
-    double vm = v2;
     __shared__ double sh[2][8];
     for (int o = 16; o > 0; o >>= 1) {
         v2 += __shfl_xor_sync(0xffffffffu, v2, o);
@@ -1355,7 +1495,7 @@ static __global__ void __launch_bounds__(256) k_kick_thermo(int n, double acc,
 // One block: KE, max|v|, time bookkeeping and the next step's dt
 // (dt = min(dt_max, d_max / max|v|) when d_max > 0).
 static __global__ void __launch_bounds__(256) k_thermo_step(const double* __restrict__ part, int nb,
-                                                     double mass, double ev_amu,
+                                                     double ev_amu,
                                                      double* __restrict__ thermo,
                                                      int advance, int* __restrict__ gate = nullptr)
 {
@@ -1377,7 +1517,7 @@ static __global__ void __launch_bounds__(256) k_thermo_step(const double* __rest
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const double ke = 0.5 * mass * sa[0] / ev_amu;
+        const double ke = 0.5 * sa[0] / ev_amu;
         const double vmax = sqrt(sb[0]);
         if (advance) {
             thermo[TH_TIME] += thermo[TH_DT];

@@ -44,7 +44,12 @@ struct nep_ctx {
     int device = 0;
     Model<float> mf;
     Model<double> md;
-    double mass = 0.0;
+    nep_params hp;                   // hyperparameters, Z and masses (pointers cleared)
+    std::vector<double> scaler;
+    int ntypes = 1;
+    MassTab mt;
+    float* coef_f = nullptr;         // several species: [T * T][CSTR] pair coefficients
+    double* coef_d = nullptr;
     double rcR = 0.0;
     std::string err;
 
@@ -93,7 +98,7 @@ struct nep_ctx {
     bool capturing = false;
     int capture_kernels = 0;
     int capture_timed = 0;
-    int nep_smem_set[2] = {0, 0};
+    int nep_smem_set[4] = {0, 0, 0, 0};
     // Verlet skin for MD (0: rebuild every step)
     double skin = 0.0;
     double* xref = nullptr;          // positions at the last list build (3 x ld)
@@ -199,7 +204,7 @@ static int ensure_atoms(nep_ctx* ctx, int n, int M)
     CK(cudaMalloc(&ctx->partials, sizeof(double) * NPART * 2 * (size_t)tiles));
     const size_t rsz = ctx->precision == NEP_FP32 ? sizeof(float) : sizeof(double);
     CK(cudaMalloc(&ctx->qr, rsz * NR * (size_t)ld));
-    CK(cudaMalloc(&ctx->br, rsz * 12 * (size_t)ld));
+    CK(cudaMalloc(&ctx->br, rsz * 12 * (size_t)ctx->ntypes * ld));
     CK(cudaMalloc(&ctx->partials2, sizeof(double) * NPART * (size_t)RED1_MAX));
     CK(cudaMalloc(&ctx->vpart, sizeof(double) * 2 * (size_t)vb));
     CK(cudaMalloc(&ctx->backup, sizeof(double) * 9 * (size_t)ld));
@@ -260,6 +265,7 @@ static int make_grid(nep_ctx* ctx, int64_t n, const double box[9], const int32_t
         g.invL[a] = 1.0 / L;
     }
     g.n = (int)n;
+    g.ntypes = ctx->ntypes;
     return NEP_OK;
 }
 
@@ -325,7 +331,7 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     count_launch(ctx);
     k_cell_finalize<R><<<(ncell + 127) / 128, 128, 0, s>>>(
         g, ncell, ctx->start, ctx->perm, x, types, (typename V4<R>::T*)ctx->pos4, ctx->cell_sorted,
-        gate);
+        ctx->status, gate);
     count_launch(ctx);
     k_neighbors<R><<<(n + 127) / 128, 128, 0, s>>>(
         g, (R)(rl * rl), (R)(ra * ra), (const typename V4<R>::T*)ctx->pos4, ctx->cell_sorted,
@@ -351,27 +357,35 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     // with a skin: this step's lists within r_c go to nbr_act / cnt_act
     int* lnbr = gate ? ctx->nbr_act : ctx->nbr;
     int2* lcnt = gate ? ctx->cnt_act : ctx->cnt;
-    k_radial_q<R><<<(n + 127) / 128, 128, 0, s>>>(P, g, p4, ctx->nbr, ctx->cnt, (R*)ctx->qr,
-                                                 gate ? ctx->nbr_act : nullptr,
-                                                 gate ? ctx->cnt_act : nullptr);
+    const R* coef;
+    if constexpr (sizeof(R) == 4) coef = ctx->coef_f;
+    else coef = ctx->coef_d;
+    const bool ms = ctx->ntypes > 1;
+    (ms ? k_radial_q<R, true> : k_radial_q<R, false>)<<<(n + 127) / 128, 128, 0, s>>>(
+        P, g, p4, ctx->nbr, ctx->cnt, (R*)ctx->qr, gate ? ctx->nbr_act : nullptr,
+        gate ? ctx->cnt_act : nullptr, coef);
     count_launch(ctx);
     // angular part, network, ZBL (the block's angular entries staged in shared
-    // memory when they fit)
+    // memory when they fit; with several species the pair coefficients first)
     const int stage_slots = ctx->M < STAGE_MAX_SLOTS ? ctx->M : STAGE_MAX_SLOTS;
-    const size_t stage_bytes = sizeof(int) * (size_t)stage_slots * TILE;
-    if (!ctx->nep_smem_set[sizeof(R) == 4 ? 0 : 1]) {
-        CK(cudaFuncSetAttribute(k_nep_ang<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(sizeof(int) * STAGE_MAX_SLOTS * TILE)));
-        ctx->nep_smem_set[sizeof(R) == 4 ? 0 : 1] = 1;
+    const size_t coef_bytes = ms ? sizeof(R) * (size_t)ctx->ntypes * ctx->ntypes * CSTR : 0;
+    const size_t stage_bytes = coef_bytes + sizeof(int) * (size_t)stage_slots * TILE;
+    auto kang = ms ? k_nep_ang<R, true> : k_nep_ang<R, false>;
+    const int ks = (sizeof(R) == 4 ? 0 : 2) + (ms ? 1 : 0);
+    if (!ctx->nep_smem_set[ks]) {
+        CK(cudaFuncSetAttribute(kang, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(R) * NT_MAX * NT_MAX * CSTR +
+                                      sizeof(int) * STAGE_MAX_SLOTS * TILE)));
+        ctx->nep_smem_set[ks] = 1;
     }
-    k_nep_ang<R><<<tiles, TILE, stage_bytes, s>>>(P, g, p4, lnbr, lcnt, ctx->perm, x,
-                                                 (const R*)ctx->qr, (typename V4<R>::T*)ctx->br, fa,
-                                                 ctx->partials, site_energy, ctx->status, stage_slots);
+    kang<<<tiles, TILE, stage_bytes, s>>>(P, g, p4, lnbr, lcnt, ctx->perm, x, (const R*)ctx->qr,
+                                          (typename V4<R>::T*)ctx->br, fa, ctx->partials,
+                                          site_energy, ctx->status, stage_slots, coef);
     count_launch(ctx);
     // radial pair forces (all pairs, small state)
-    k_radial_force<R><<<tiles, TILE, 0, s>>>(P, g, p4, lnbr, lcnt,
-                                            (const typename V4<R>::T*)ctx->br, fa,
-                                            ctx->partials + (size_t)tiles * NPART, ctx->status);
+    (ms ? k_radial_force<R, true> : k_radial_force<R, false>)<<<tiles, TILE, 0, s>>>(
+        P, g, p4, lnbr, lcnt, (const typename V4<R>::T*)ctx->br, fa,
+        ctx->partials + (size_t)tiles * NPART, ctx->status);
     count_launch(ctx);
     if (timed_slot >= 0) {
         if (ctx->capturing)
@@ -488,6 +502,92 @@ static void build_model(Model<R>& P, const nep_params* p)
     P.zbl_inv_a = (pow(Z, 0.23) + pow(Z, 0.23)) / 0.46848;
     P.zbl_r1 = p->zbl_r_inner;
     P.zbl_rr2 = p->zbl_r_outer;
+    // ZBL prefactor and screening length of every ordered species pair (Eq. 2, 4)
+    const int T = p->n_types < 1 ? 1 : p->n_types;
+    P.ntypes = T;
+    for (int a = 0; a < NT_MAX * NT_MAX; ++a) { P.zbl_kp[a] = 0.0; P.zbl_inv_ap[a] = 0.0; }
+    for (int a = 0; a < T; ++a)
+        for (int b = 0; b < T; ++b) {
+            const double Za = (double)p->z[a], Zb = (double)p->z[b];
+            P.zbl_kp[a * T + b] = COULOMB_EV_A * Za * Zb;
+            P.zbl_inv_ap[a * T + b] = (pow(Za, 0.23) + pow(Zb, 0.23)) / 0.46848;
+        }
+}
+
+// Number of model parameters for T species.
+static int64_t n_params_for(int T)
+{
+    return (int64_t)H * D + 2 * H + 1 + (int64_t)T * T * (NR * KR + NA * KA);
+}
+
+// Pair coefficient table [T * T][CSTR] (h = c/2 and C = sum_k c/2 of every
+// ordered species pair, radial then angular) in precision R.
+template <typename R>
+static void pair_table(const nep_params* p, std::vector<R>& tab)
+{
+    const int T = p->n_types;
+    const double* cR = p->params + (int64_t)H * D + 2 * H + 1;
+    const double* cA = cR + (int64_t)T * T * NR * KR;
+    tab.assign((size_t)T * T * CSTR, R(0));
+    for (int pr = 0; pr < T * T; ++pr) {
+        R* o = tab.data() + (size_t)pr * CSTR;
+        for (int n = 0; n < NR; ++n) {
+            double sum = 0.0;
+            for (int k = 0; k < KR; ++k) {
+                const double h = 0.5 * cR[((size_t)pr * NR + n) * KR + k];
+                o[C_RAD + n * KR + k] = (R)h;
+                sum += h;
+            }
+            o[C_RAD + NR * KR + n] = (R)sum;
+        }
+        for (int n = 0; n < NA; ++n) {
+            double sum = 0.0;
+            for (int k = 0; k < KA; ++k) {
+                const double h = 0.5 * cA[((size_t)pr * NA + n) * KA + k];
+                o[C_ANG + n * KA + k] = (R)h;
+                sum += h;
+            }
+            o[C_ANG + NA * KA + n] = (R)sum;
+        }
+    }
+}
+
+// Builds both precisions' models and, for several species, the device pair
+// tables, from the stored hyperparameters and `params`.
+static int setup_model(nep_ctx* ctx, const double* params)
+{
+    nep_params p = ctx->hp;
+    p.params = params;
+    p.q_scaler = ctx->scaler.data();
+    const int T = p.n_types;
+    if (T == 1) {
+        build_model<float>(ctx->mf, &p);
+        build_model<double>(ctx->md, &p);
+    } else {
+        // the one-species fields hold block (0, 0); the kernels for several
+        // species read the pair tables instead
+        std::vector<double> one((size_t)n_params_for(1));
+        const int64_t head = (int64_t)H * D + 2 * H + 1;
+        std::copy(params, params + head, one.begin());
+        std::copy(params + head, params + head + NR * KR, one.begin() + head);
+        std::copy(params + head + (int64_t)T * T * NR * KR,
+                  params + head + (int64_t)T * T * NR * KR + NA * KA,
+                  one.begin() + head + NR * KR);
+        nep_params p1 = p;
+        p1.params = one.data();
+        p1.n_params = (int64_t)one.size();
+        build_model<float>(ctx->mf, &p1);
+        build_model<double>(ctx->md, &p1);
+        std::vector<float> tf;
+        std::vector<double> td;
+        pair_table<float>(&p, tf);
+        pair_table<double>(&p, td);
+        if (!ctx->coef_f) CK(cudaMalloc(&ctx->coef_f, sizeof(float) * tf.size()));
+        if (!ctx->coef_d) CK(cudaMalloc(&ctx->coef_d, sizeof(double) * td.size()));
+        CK(cudaMemcpy(ctx->coef_f, tf.data(), sizeof(float) * tf.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->coef_d, td.data(), sizeof(double) * td.size(), cudaMemcpyHostToDevice));
+    }
+    return NEP_OK;
 }
 
 // ============================================================================
@@ -503,14 +603,14 @@ int nep_init(const nep_params* p, int precision, nep_ctx** out)
     *out = nullptr;
     if (precision != NEP_FP32 && precision != NEP_FP64)
         return fail(nullptr, NEP_ERR_INVALID_ARG, "precision must be NEP_FP32 or NEP_FP64");
-    if (p->n_types != 1)
-        return fail(nullptr, NEP_ERR_UNSUPPORTED, "this build supports one species (n_types = 1)");
+    if (p->n_types < 1 || p->n_types > NT_MAX)
+        return fail(nullptr, NEP_ERR_UNSUPPORTED, "n_types must be 1..%d", NT_MAX);
     if (p->n_max_radial != NR - 1 || p->n_max_angular != NA - 1 ||
         p->basis_size_radial != KR - 1 || p->basis_size_angular != KA - 1 || p->l_max != LM ||
         p->use_4body != 1 || p->n_hidden != H)
         return fail(nullptr, NEP_ERR_UNSUPPORTED,
                     "this build is compiled for n_max 4/4, basis 8/8, l_max 4, 4-body, 30 neurons");
-    const int64_t np = (int64_t)H * D + 2 * H + 1 + NR * KR + NA * KA;
+    const int64_t np = n_params_for(p->n_types);
     if (!p->params || p->n_params != np)
         return fail(nullptr, NEP_ERR_INVALID_ARG, "params must hold %lld values", (long long)np);
     if (!p->q_scaler) return fail(nullptr, NEP_ERR_INVALID_ARG, "q_scaler is NULL");
@@ -523,16 +623,25 @@ int nep_init(const nep_params* p, int precision, nep_ctx** out)
         p->zbl_r_outer > p->rc_angular)
         return fail(nullptr, NEP_ERR_INVALID_ARG,
                     "need 0 <= zbl_r_inner < zbl_r_outer <= rc_angular <= rc_radial");
-    if (!(p->z[0] > 0) || !(p->mass[0] > 0))
-        return fail(nullptr, NEP_ERR_INVALID_ARG, "Z and mass must be positive");
+    for (int t = 0; t < p->n_types; ++t)
+        if (!(p->z[t] > 0) || !(p->mass[t] > 0) || !isfinite(p->mass[t]))
+            return fail(nullptr, NEP_ERR_INVALID_ARG, "Z and mass of species %d must be positive", t);
 
     ctx = new (std::nothrow) nep_ctx();
     if (!ctx) return fail(nullptr, NEP_ERR_INVALID_ARG, "out of host memory");
     ctx->precision = precision;
-    ctx->mass = p->mass[0];
     ctx->rcR = p->rc_radial;
-    build_model<float>(ctx->mf, p);
-    build_model<double>(ctx->md, p);
+    ctx->hp = *p;
+    ctx->hp.params = nullptr;
+    ctx->hp.q_scaler = nullptr;
+    ctx->scaler.assign(p->q_scaler, p->q_scaler + D);
+    ctx->ntypes = p->n_types;
+    ctx->mt.ntypes = p->n_types;
+    for (int t = 0; t < NT_MAX; ++t) {
+        const double m = t < p->n_types ? p->mass[t] : 1.0;
+        ctx->mt.m[t] = m;
+        ctx->mt.acc[t] = EV_AMU / m;
+    }
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->thermo, sizeof(double) * TH_N);
@@ -550,6 +659,11 @@ int nep_init(const nep_params* p, int precision, nep_ctx** out)
     if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(int) * 3);
     if (e != cudaSuccess) {
         int rc = fail(nullptr, NEP_ERR_CUDA, "CUDA setup failed: %s", cudaGetErrorString(e));
+        nep_free(ctx);
+        return rc;
+    }
+    if (setup_model(ctx, p->params) != NEP_OK) {
+        int rc = fail(nullptr, NEP_ERR_CUDA, "%s", ctx->err.c_str());
         nep_free(ctx);
         return rc;
     }
@@ -577,6 +691,7 @@ void nep_free(nep_ctx* ctx)
     free_dev(ctx->count); free_dev(ctx->start); free_dev(ctx->scan_sums);
     free_dev(ctx->thermo); free_dev(ctx->thermo_backup); free_dev(ctx->result);
     free_dev(ctx->status); free_dev(ctx->pairs); free_dev(ctx->gate); free_dev(ctx->nrebuild);
+    free_dev(ctx->coef_f); free_dev(ctx->coef_d);
     if (ctx->h_result) cudaFreeHost(ctx->h_result);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->h_pairs) cudaFreeHost(ctx->h_pairs);
@@ -680,6 +795,9 @@ static int compute_with_retry(nep_ctx* ctx, const Grid& g, const double* x, cons
             rc = collect_timing(ctx, 1);
             if (rc) return rc;
         }
+        if (ctx->h_status[0] & ST_BADTYPE)
+            return fail(ctx, NEP_ERR_INVALID_ARG, "species index out of range [0, %d)",
+                        ctx->ntypes);
         if (ctx->h_status[0] & ST_OVERFLOW) {
             M = grown_capacity(ctx->h_status[1]);
             continue;
@@ -724,7 +842,6 @@ int nep_compute(nep_ctx* ctx, int64_t n_atoms, const double* xyz, const double b
 static int capture_steps(nep_ctx* ctx, const Grid& g, nep_md_state* st, int steps, GraphEntry& ge)
 {
     cudaStream_t cs = ctx->cap_stream;
-    const double acc = EV_AMU / ctx->mass;
     const int n = g.n;
     const int tb = 256, nb = (n + tb - 1) / tb;
     if (ctx->timing) {
@@ -736,14 +853,16 @@ static int capture_steps(nep_ctx* ctx, const Grid& g, nep_md_state* st, int step
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     int rc = NEP_OK;
     for (int t = 0; t < steps && !rc; ++t) {
-        k_kick_drift<<<nb, tb, 0, cs>>>(g, acc, ctx->thermo, st->xyz, st->vel, st->forces);
+        k_kick_drift<<<nb, tb, 0, cs>>>(g, ctx->mt, st->types, ctx->thermo, st->xyz, st->vel,
+                                        st->forces);
         count_launch(ctx);
         int* gate = ctx->skin > 0.0 ? ctx->gate : nullptr;
         rc = eval(ctx, g, st->xyz, st->types, st->forces, nullptr, cs, ctx->timing ? t : -1, gate);
         if (rc) break;
-        k_kick_thermo<<<nb, tb, 0, cs>>>(n, acc, ctx->thermo, st->vel, st->forces, ctx->vpart, 1);
+        k_kick_thermo<<<nb, tb, 0, cs>>>(n, ctx->mt, st->types, ctx->thermo, st->vel, st->forces,
+                                         ctx->vpart, 1);
         count_launch(ctx);
-        k_thermo_step<<<1, 256, 0, cs>>>(ctx->vpart, nb, ctx->mass, EV_AMU, ctx->thermo, 1, gate);
+        k_thermo_step<<<1, 256, 0, cs>>>(ctx->vpart, nb, EV_AMU, ctx->thermo, 1, gate);
         count_launch(ctx);
     }
     cudaGraph_t graph = nullptr;
@@ -821,9 +940,10 @@ int md_step(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
     CK(cudaMemcpyAsync(ctx->thermo, th, sizeof(th), cudaMemcpyHostToDevice, s));
     {
         const int tb = 256, nb = (int)((n + tb - 1) / tb);
-        k_kick_thermo<<<nb, tb, 0, s>>>((int)n, 0.0, ctx->thermo, st->vel, st->forces, ctx->vpart, 0);
+        k_kick_thermo<<<nb, tb, 0, s>>>((int)n, ctx->mt, st->types, ctx->thermo, st->vel,
+                                        st->forces, ctx->vpart, 0);
         count_launch(ctx);
-        k_thermo_step<<<1, 256, 0, s>>>(ctx->vpart, nb, ctx->mass, EV_AMU, ctx->thermo, 0);
+        k_thermo_step<<<1, 256, 0, s>>>(ctx->vpart, nb, EV_AMU, ctx->thermo, 0);
         count_launch(ctx);
         CK(cudaGetLastError());
     }
@@ -856,6 +976,9 @@ int md_step(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
         ctx->launches += it->second.kernels;
         rc = readback(ctx, s);
         if (rc) return rc;
+        if (ctx->h_status[0] & ST_BADTYPE)
+            return fail(ctx, NEP_ERR_INVALID_ARG, "species index out of range [0, %d)",
+                        ctx->ntypes);
         if (ctx->h_status[0] & ST_OVERFLOW) {
             if (++retries > 4) return fail(ctx, NEP_ERR_NBR_OVERFLOW, "neighbour overflow persists");
             CK(cudaMemcpyAsync(st->xyz, ctx->backup, bytes, cudaMemcpyDeviceToDevice, s));
@@ -924,6 +1047,8 @@ static int batch_buffers(nep_ctx* ctx, long long ntot, int S, int M)
 // Validates a batch, uploads its offsets/boxes/order and fills b.
 static int batch_prepare(nep_ctx* ctx, const nep_batch* bt, cudaStream_t s, Batch& b)
 {
+    if (ctx->ntypes != 1)
+        return fail(ctx, NEP_ERR_UNSUPPORTED, "the batched entry points support one species");
     if (!bt || bt->n_configs < 1 || !bt->offsets || !bt->boxes)
         return fail(ctx, NEP_ERR_INVALID_ARG, "batch needs n_configs >= 1, offsets and boxes");
     const int S = bt->n_configs;
@@ -1023,27 +1148,16 @@ extern "C" {
 int nep_set_params(nep_ctx* ctx, const double* params, int64_t n_params)
 {
     if (!ctx) return NEP_ERR_INVALID_ARG;
-    const int64_t np = (int64_t)H * D + 2 * H + 1 + NR * KR + NA * KA;
+    const int64_t np = n_params_for(ctx->ntypes);
     if (!params || n_params != np)
         return fail(ctx, NEP_ERR_INVALID_ARG, "params must hold %lld values", (long long)np);
     for (int64_t i = 0; i < np; ++i)
         if (!isfinite(params[i])) return fail(ctx, NEP_ERR_INVALID_ARG, "non-finite parameter");
-    // rebuild both models from the new parameters and the stored scaler
-    double sc[D];
-    for (int nu = 0; nu < D; ++nu) sc[nu] = ctx->md.sc[nu];
-    nep_params p;
-    memset(&p, 0, sizeof(p));
-    p.params = params;
-    p.q_scaler = sc;
-    p.rc_radial = ctx->rcR;
-    p.rc_angular = sqrt(ctx->md.rcA2);
-    p.zbl_r_inner = ctx->md.zbl_r1;
-    p.zbl_r_outer = ctx->md.zbl_rr2;
-    const double kz = ctx->md.zbl_k, inva = ctx->md.zbl_inv_a;
-    build_model<float>(ctx->mf, &p);
-    build_model<double>(ctx->md, &p);
-    ctx->mf.zbl_k = kz; ctx->md.zbl_k = kz;
-    ctx->mf.zbl_inv_a = inva; ctx->md.zbl_inv_a = inva;
+    // rebuild both models (and pair tables) from the new parameters and the
+    // stored hyperparameters and scaler; graphs hold the old model by value
+    CK(cudaDeviceSynchronize());
+    int rc = setup_model(ctx, params);
+    if (rc) return rc;
     drop_graphs(ctx);
     return NEP_OK;
 }
@@ -1275,6 +1389,7 @@ extern "C" int nep_compute_static(const nep_params* p, int64_t n_atoms, const do
     g.n = n;
     g.ld = ST_MAX_ATOMS;
     g.M = ST_SLOTS;
+    g.ntypes = 1;
     if (n == 0) {
         *energy = 0.0;
         if (virial) for (int t = 0; t < 9; ++t) virial[t] = 0.0;
@@ -1324,7 +1439,7 @@ extern "C" int nep_compute_static(const nep_params* p, int64_t n_atoms, const do
     k_scan_add<<<(ncell + tb - 1) / tb, tb, 0, s>>>(start, ncell, scan_sums);
     k_bin_scatter<<<nb, tb, 0, s>>>(n, cell_of, slot_of, start, perm);
     k_cell_finalize<float><<<(ncell + 127) / 128, 128, 0, s>>>(g, ncell, start, perm, xyz, types,
-                                                              pos4, cell_sorted);
+                                                              pos4, cell_sorted, status);
     k_neighbors<float><<<(n + 127) / 128, 128, 0, s>>>(g, P.rcR2, P.rcA2, pos4, cell_sorted, start,
                                                       nbr, cnt, status, status + 1, pairs);
     const int tiles = (n + TILE - 1) / TILE;
@@ -1342,6 +1457,8 @@ extern "C" int nep_compute_static(const nep_params* p, int64_t n_atoms, const do
     if (st[0] & ST_OVERFLOW)
         return fail(nullptr, NEP_ERR_NBR_OVERFLOW,
                     "an atom has %d neighbours within r_c; this path holds %d", st[1], ST_SLOTS);
+    if (st[0] & ST_BADTYPE)
+        return fail(nullptr, NEP_ERR_INVALID_ARG, "species index out of range (one species)");
     if (st[0] & ST_NONFINITE)
         return fail(nullptr, NEP_ERR_NONFINITE, "non-finite positions, energies or forces");
     *energy = res[0];
