@@ -169,8 +169,9 @@ def cpu_baseline_sample(seconds_hint: float = 20.0) -> dict:
 def _time_md(N, nep, s, steps, warm, dev, d_max=0.0, chunk=25):
     """Atom-steps/s of `steps` graph-replayed MD steps (CUDA events)."""
     import torch
+    types = torch.tensor(s.types, dtype=torch.int32, device=dev)
     st = N.MDState(N.to_device_soa(s.pos, dev), N.to_device_soa(s.vel, dev), s.box, s.pbc,
-                   dt_max=1.0, d_max=d_max)
+                   dt_max=1.0, d_max=d_max, types=types)
     nep.set_option(N.NEP_OPT_GRAPH_CHUNK, min(chunk, steps))
     nep.md(st, warm)
     nep.md(st, min(chunk, steps))
@@ -203,6 +204,20 @@ def other_configs(dev):
     r["note"] = ("Verlet skin 0.5 A (lists with r_c + 0.5 A, rebuilt after a 0.25 A "
                  "displacement; pairs within r_c compacted every step)")
     out["c5_8192000_fp32_skin_0.5A"] = r
+    nep.close()
+    # the same slab as a random 50/50 W-Mo solid solution with a two-species model
+    # (pair coefficient tables, mixed-Z ZBL, two masses)
+    s = I.alloy(s, [0.5, 0.5], seed=305)
+    nep = N.NEP(I.nep_model(301, species=("W", "Mo")), "fp32")
+    r = _time_md(N, nep, s, 100, 3, dev)
+    r["note"] = "two species (W, Mo), random labels, same geometry and velocities as the slab"
+    out["c5_8192000_WMo_fp32"] = r
+    nep.close()
+    del s
+    # equiatomic W-Mo-Ta-Nb, 128,000 atoms, four species, 1,000 steps
+    s = I.hea()
+    nep = N.NEP(I.nep_model(401, species=("W", "Mo", "Ta", "Nb")), "fp32")
+    out["hea_WMoTaNb_128000_fp32"] = _time_md(N, nep, s, 1000, 3, dev)
     nep.close()
     del s
     # 2,000-atom bcc W: plain FP64 as configured, and the FP32 path; 100 NVE steps
