@@ -261,6 +261,36 @@ def other_configs(dev):
         "value": b.N / dt, "unit": "atom-gradients/s", "ms_per_step": dt * 1e3,
         "configs": b.S, "atoms": b.N, "loss": L, "autotune": {"threads": bt, "ctas_per_sm": per},
         "note": "host-timed synchronous API call (forward + loss + gradient)"}
+    # one SNES generation of the paper's training (population 50, Sec. III.A) over the
+    # same 512 configurations: candidates, the NEP loss of all 50 in one launch, update
+    n_pop = 50
+    d = len(model.params)
+    mu = torch.tensor(model.params, dtype=torch.float64, device=dev)
+    sigma = torch.full((d,), 0.01, dtype=torch.float64, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    samples = torch.randn((n_pop, d), generator=g, dtype=torch.float64, device=dev)
+    Wt = torch.zeros((b.S, 6), dtype=torch.float64, device=dev)
+    tgt_W = N.NEP(I.nep_model(101), "fp32")
+    _, _, W9 = tgt_W.batch_forward(b, virials=True)
+    tgt_W.close()
+    Wt[:] = W9.reshape(b.S, 9)[:, [0, 4, 8, 5, 6, 1]]
+    for _ in range(2):
+        N.snes_generation(nep, b, mu, sigma, samples, Et, Ft, Wt)
+    torch.cuda.synchronize()
+    reps = 5
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        losses = N.snes_generation(nep, b, mu, sigma, samples, Et, Ft, Wt)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / reps
+    out["c4_512_configs_snes_generation_pop50_fp32"] = {
+        "value": n_pop * b.N / dt, "unit": "atom-evaluations/s", "ms_per_step": dt * 1e3,
+        "population": n_pop, "configs": b.S, "atoms": b.N,
+        "best_loss": float(losses[:, 0].min()),
+        "note": ("host-timed synchronous API call: candidates mu + sigma s_k, lists, 50 x 512 "
+                 "forward passes with energy/force/virial RMSE and L1/L2 terms, ranking and "
+                 "update; samples drawn once on the device and reused")}
     nep.close()
     return out
 

@@ -202,10 +202,14 @@ int nep_reset_stats(nep_ctx* ctx);
  * boxes down to r_c^R per side are exact), evaluates energies and forces, and
  * for the gradient entry points the derivative of a loss with respect to all
  * n_params model parameters, including the force term's second derivatives:
- * with e_i = dL/dF_i and eps_s = dL/dE_s,
+ * with e_i = dL/dF_i, eps_s = dL/dE_s and G_s = dL/dW_s (3x3),
  *   dL/dtheta = sum_i d/dtheta [eps U_i - (dU_i/dq_i) . qdot_i],
- *   qdot_i = sum_j (dq_i/dr_ij) . (e_j - e_i).
- * Gradient sums are accumulated in FP64 and reduced in a fixed order.
+ *   qdot_i = sum_j (dq_i/dd_ij) . v_ij,  v_ij = (e_j - e_i) + G_s d_ij
+ * (the virial W = -sum_ij (dU_i/dd_ij) (x) d_ij enters like a homogeneous
+ * deformation of the pair vectors).  Gradient sums are accumulated in FP64
+ * and reduced in a fixed order.
+ * Virials are 3x3 row-major per configuration (eV); virial targets and the
+ * virial loss use the six components xx, yy, zz, yz, zx, xy.
  * --------------------------------------------------------------------------- */
 typedef struct nep_batch {
     int32_t n_configs;
@@ -221,35 +225,98 @@ typedef struct nep_batch {
 /* Each configuration holds 1..512 atoms.  The batched entry points support
  * one species (n_types = 1); other models get NEP_ERR_UNSUPPORTED. */
 
+/* Training targets of a batch (Sec. III.A: every structure has a target
+ * energy and forces, some a target virial). */
+typedef struct nep_targets {
+    const double* energy;        /* device double[n_configs] (eV) */
+    const double* forces;        /* device double[3 * n_atoms] SoA (eV/A) */
+    const double* virial;        /* device double[6 * n_configs]: xx, yy, zz, yz, zx, xy
+                                    per configuration (eV), or NULL (no virial term) */
+    const uint8_t* has_virial;   /* host uint8[n_configs]: 1 where the configuration has a
+                                    virial target; NULL = every configuration */
+} nep_targets;
+
+/* Loss weights: lambda_e, lambda_f, lambda_v of the data terms and lambda_1,
+ * lambda_2 of the regularisers (Sec. III.A uses 1, 1, 0.1, 0.05, 0.05). */
+typedef struct nep_loss_weights {
+    double energy, force, virial;
+    double l1, l2;
+} nep_loss_weights;
+
 /* Replaces the model parameters (same layout and length as nep_params.params;
  * the descriptor scaler is kept).  Host memory. */
 int nep_set_params(nep_ctx* ctx, const double* params, int64_t n_params);
 
-/* Energies (device double[n_configs], eV) and forces (device double[3 * n_atoms]
- * SoA, eV/A) of every configuration.  Synchronous on the stream. */
+/* Energies (device double[n_configs], eV), forces (device double[3 * n_atoms]
+ * SoA, eV/A) and, if virials != NULL, virials (device double[9 * n_configs],
+ * eV) of every configuration.  Synchronous on the stream. */
 int nep_batch_forward(nep_ctx* ctx, const nep_batch* batch, double* energies, double* forces,
-                      void* stream);
+                      double* virials, void* stream);
 
-/* Gradient (device double[n_params]) of a loss L(E, F) given its upstream
- * derivatives dL/dE (device double[n_configs]) and dL/dF (device
- * double[3 * n_atoms] SoA), evaluated at the context's current parameters. */
+/* Gradient (device double[n_params]) of a loss L(E, F, W) given its upstream
+ * derivatives dL/dE (device double[n_configs]), dL/dF (device
+ * double[3 * n_atoms] SoA) and dL/dW (device double[9 * n_configs], or NULL
+ * for none), evaluated at the context's current parameters. */
 int nep_batch_backward(nep_ctx* ctx, const nep_batch* batch, const double* dL_dE,
-                       const double* dL_dF, double* grad, void* stream);
+                       const double* dL_dF, const double* dL_dW, double* grad, void* stream);
 
-/* One persistent launch for forward, forces, the energy+force loss
- *   L = w_energy * mean_s ((E_s - Et_s) / N_s)^2
- *     + w_force  * mean over the 3 n_atoms components (F - Ft)^2
- * (FP64 accumulation; host *loss) and its gradient (device double[n_params]).
- * energies / forces (device) may be NULL. */
-int nep_batch_loss_grad(nep_ctx* ctx, const nep_batch* batch, const double* E_target,
-                        const double* F_target, double w_energy, double w_force, double* loss,
-                        double* grad, double* energies, double* forces, void* stream);
+/* One persistent launch for forward, forces, virials, the mean-square loss
+ *   L = w.energy * mean_s ((E_s - Et_s) / N_s)^2
+ *     + w.force  * mean over the 3 n_atoms components (F - Ft)^2
+ *     + w.virial * mean over configurations with a virial target and the six
+ *                  components ((W_s - Wt_s) / N_s)^2
+ * (FP64 accumulation; w.l1 and w.l2 are not used here) and its gradient
+ * (device double[n_params]).  loss: host double[4] = total, energy, force and
+ * virial terms.  energies, forces, virials (device) may be NULL. */
+int nep_batch_loss_grad(nep_ctx* ctx, const nep_batch* batch, const nep_targets* targets,
+                        const nep_loss_weights* w, double* loss, double* grad,
+                        double* energies, double* forces, double* virials, void* stream);
 
 /* Times the loss-gradient launch on this batch for each candidate of threads
  * per CTA (atoms of one configuration processed side by side: 64, 128, 256)
  * and CTAs per SM (1, 2, 4) and keeps the fastest for later batched calls. */
-int nep_batch_autotune(nep_ctx* ctx, const nep_batch* batch, const double* E_target,
-                       const double* F_target, void* stream, int* best_threads, int* best_per_sm);
+int nep_batch_autotune(nep_ctx* ctx, const nep_batch* batch, const nep_targets* targets,
+                       const nep_loss_weights* w, void* stream, int* best_threads,
+                       int* best_per_sm);
+
+/* ---------------------------------------------------------------------------
+ * Population training (the separable natural evolution strategy, SNES, that
+ * Sec. III.A trains the model with; Schaul et al. 2011)
+ *
+ * The NEP training loss of a parameter vector theta over a batch (Sec. III.A,
+ * the terms of Fig. 1(a)):
+ *   L = w.energy RMSE_E + w.force RMSE_F + w.virial RMSE_V + L1 + L2,
+ *   RMSE_E = sqrt(mean_s ((E_s - Et_s) / N_s)^2),
+ *   RMSE_F = sqrt(mean over the 3 n_atoms components (F - Ft)^2),
+ *   RMSE_V = sqrt(mean over configurations with a virial target and the six
+ *            components ((W_s - Wt_s) / N_s)^2)   (0 without targets),
+ *   L1 = w.l1 (1/P) sum_p |theta_p|,  L2 = w.l2 sqrt((1/P) sum_p theta_p^2).
+ * The whole population is evaluated in one launch (after one launch that
+ * builds the neighbour lists): each work item is one (configuration,
+ * individual) pair whose model sits in shared memory.
+ * --------------------------------------------------------------------------- */
+
+/* Loss terms of n_pop (1..1024) parameter vectors thetas (device
+ * double[n_pop * n_params], host layout of nep_params.params) at the
+ * context's hyperparameters and scaler: losses (device double[6 * n_pop]) =
+ * total, L1, L2, RMSE_E, RMSE_F, RMSE_V per individual.  Synchronous. */
+int nep_population_loss(nep_ctx* ctx, const nep_batch* batch, const nep_targets* targets,
+                        const nep_loss_weights* w, int n_pop, const double* thetas,
+                        double* losses, void* stream);
+
+/* One SNES generation.  mu, sigma: device double[n_params], updated in place;
+ * samples: device double[n_pop * n_params] standard-normal draws supplied by
+ * the caller.  Candidates theta_k = mu + sigma * s_k are evaluated with
+ * nep_population_loss (losses as there, device double[6 * n_pop]), ranked by
+ * total loss (ties by index) and given the utilities
+ *   u_r = max(0, ln(n_pop/2 + 1) - ln r) / sum_j max(0, ln(n_pop/2 + 1) - ln j) - 1/n_pop;
+ * then mu += eta_mu sigma sum_k u_k s_k and
+ * sigma *= exp(eta_sigma / 2 sum_k u_k (s_k^2 - 1)).  The usual rates are
+ * eta_mu = 1, eta_sigma = (3 + ln n_params) / (5 sqrt(n_params)).  Synchronous. */
+int nep_snes_generation(nep_ctx* ctx, const nep_batch* batch, const nep_targets* targets,
+                        const nep_loss_weights* w, int n_pop, double* mu, double* sigma,
+                        const double* samples, double eta_mu, double eta_sigma, double* losses,
+                        void* stream);
 
 /* Force evaluation that allocates nothing (the paper has no counterpart; it is
  * a deployment convenience).  It is meant for callers that may not allocate

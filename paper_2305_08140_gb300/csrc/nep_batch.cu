@@ -11,11 +11,12 @@ static cudaError_t run(int mode, int grid, const Model<R>& P, const Batch& b, do
     switch (mode) {
     case MODE_FORWARD: k_batch<R, MODE_FORWARD, BT><<<grid, BT, 0, s>>>(P, b); break;
     case MODE_BACKWARD: k_batch<R, MODE_BACKWARD, BT><<<grid, BT, 0, s>>>(P, b); break;
+    case MODE_LISTS: k_batch<R, MODE_LISTS, BT><<<grid, BT, 0, s>>>(P, b); break;
     default: k_batch<R, MODE_LOSS, BT><<<grid, BT, 0, s>>>(P, b); break;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (mode != MODE_FORWARD) {
+    if (mode == MODE_BACKWARD || mode == MODE_LOSS) {
         k_batch_grad_reduce<<<(NP + 255) / 256, 256, 0, s>>>(b.gpart, b.S, grad);
         e = cudaGetLastError();
     }
@@ -29,6 +30,61 @@ cudaError_t launch_batch(int precision, int mode, int bt, int grid, const Model<
     if (bt == 64) return run<float, 64>(mode, grid, mf, b, grad, s);
     if (bt == 256) return run<float, 256>(mode, grid, mf, b, grad, s);
     return run<float, 128>(mode, grid, mf, b, grad, s);
+}
+
+cudaError_t launch_population(int precision, int n_pop, const Model<float>& mf,
+                              const Model<double>& md, const double* scaler,
+                              const double* thetas, void* models, const Batch& b, double* pout,
+                              int grid, cudaStream_t s)
+{
+    if (precision == 1) {
+        k_build_models<double><<<n_pop, 256, 0, s>>>(md, scaler, thetas, (Model<double>*)models);
+        k_batch_pop<double, 128><<<grid, 128, 0, s>>>((const Model<double>*)models, n_pop, b, pout);
+    } else {
+        k_build_models<float><<<n_pop, 256, 0, s>>>(mf, scaler, thetas, (Model<float>*)models);
+        k_batch_pop<float, 128><<<grid, 128, 0, s>>>((const Model<float>*)models, n_pop, b, pout);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_population_loss(int n_pop, const double* pout, const double* thetas, int S,
+                                   long long ntot, double nv, double we, double wf, double wv,
+                                   double l1, double l2, double* losses, cudaStream_t s)
+{
+    k_pop_loss<256><<<n_pop, 256, 0, s>>>(pout, thetas, S, ntot, nv, we, wf, wv, l1, l2, losses);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_snes_sample(const double* mu, const double* sigma, const double* samples,
+                               int n_pop, double* thetas, cudaStream_t s)
+{
+    const long long n = (long long)n_pop * NP;
+    k_snes_sample<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(mu, sigma, samples, n_pop, thetas);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_snes_update(double* mu, double* sigma, const double* samples,
+                               const double* losses, double* util, int n_pop, double eta_mu,
+                               double eta_sigma, cudaStream_t s)
+{
+    k_snes_utilities<<<1, 1024, 0, s>>>(losses, n_pop, util);
+    k_snes_update<<<(NP + 255) / 256, 256, 0, s>>>(mu, sigma, samples, util, n_pop, eta_mu,
+                                                  eta_sigma);
+    return cudaGetLastError();
+}
+
+int population_blocks_per_sm(int precision)
+{
+    int n = 0;
+    cudaError_t e = precision == 1
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_pop<double, 128>, 128, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_pop<float, 128>, 128, 0);
+    return e == cudaSuccess && n > 0 ? n : 1;
+}
+
+size_t model_bytes(int precision)
+{
+    return precision == 1 ? sizeof(Model<double>) : sizeof(Model<float>);
 }
 
 template <typename K>

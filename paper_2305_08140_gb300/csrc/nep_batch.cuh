@@ -17,6 +17,11 @@
 // derivative along e).  Per atom this needs q, qdot (descriptor and its
 // tangent), the network's value, gradient and Hessian-vector product, and two
 // pair loops that contract the basis-coefficient derivatives.
+// Virial term.  With W = -sum_ij (dU_i/dd_ij) (x) d_ij and G_s = dL/dW_s,
+//   sum_ab G_ab dW_ab/dtheta = -d/dtheta sum_ij (dU_i/dd_ij) . (G d_ij),
+// the same form as the force term, so the pair direction becomes
+//   v_ij = (e_j - e_i) + G_s d_ij
+// and everything downstream is unchanged.
 #pragma once
 
 #include "nep_device.cuh"
@@ -40,7 +45,7 @@ constexpr int BS_P = BS_GW1 + H;       // p = W^T u [D]
 constexpr int BS_AV = BS_P + D;        // a = W^T v [D]
 constexpr int BSTRIDE = BS_AV + D;
 
-enum { MODE_FORWARD = 0, MODE_BACKWARD = 1, MODE_LOSS = 2 };
+enum { MODE_FORWARD = 0, MODE_BACKWARD = 1, MODE_LOSS = 2, MODE_LISTS = 3 };
 
 struct Batch {
     int S;                     // configurations
@@ -61,7 +66,12 @@ struct Batch {
     const double* Et;          // [S] target energies (loss)
     const double* Ft;          // [3][ntot] target forces (loss)
     double we, wf;             // loss weights
-    double* lpart;             // [S] loss of each configuration
+    double* W;                 // [S][9] virials (forward, loss), or nullptr
+    const double* Wt;          // [S][6] target virials xx yy zz yz zx xy (loss), or nullptr
+    const unsigned char* hv;   // [S] 1 = configuration has a virial target (loss)
+    double wv, nv;             // virial weight, number of configurations with a target
+    const double* dLdW;        // [S][9] (backward), or nullptr
+    double* lpart;             // [S][3] energy, force and virial loss of each configuration
     double* gpart;             // [S][NP] gradient of each configuration
     void* scr;                 // [ntot][BSTRIDE] backward scratch
 };
@@ -160,6 +170,16 @@ __device__ __forceinline__ int slot_of(int s, int na, int nro, int M)
     return s < na ? s : M - nro + (s - na);
 }
 
+// Pair direction of the backward: v_ij = (e_j - e_i) + G d_ij.
+template <typename R>
+__device__ __forceinline__ void pair_dir(const PairGeom<R>& g, const R (*se)[BMAXA], R eix, R eiy,
+                                         R eiz, const R* G, R& vx, R& vy, R& vz)
+{
+    vx = se[0][g.j] - eix + G[0] * g.dx + G[1] * g.dy + G[2] * g.dz;
+    vy = se[1][g.j] - eiy + G[3] * g.dx + G[4] * g.dy + G[5] * g.dz;
+    vz = se[2][g.j] - eiz + G[6] * g.dx + G[7] * g.dy + G[8] * g.dz;
+}
+
 // Forward of local atom i: descriptor, network, pair forces scattered into
 // the shared accumulators; returns U_i (NEP + half ZBL).
 template <typename R>
@@ -167,7 +187,8 @@ __device__ __forceinline__ double batch_atom_forward(const Model<R>& P, const Ba
                                                      long long a0, int i,
                                                      const typename V4<R>::T* spos,
                                                      const typename V4<R>::T* s_off,
-                                                     typename Acc<R>::T (*sF)[BMAXA], bool& bad)
+                                                     typename Acc<R>::T (*sF)[BMAXA], bool& bad,
+                                                     double (&w)[9])
 {
     using A_ = Acc<R>;
     const size_t col = (size_t)(a0 + i);
@@ -201,8 +222,9 @@ __device__ __forceinline__ double batch_atom_forward(const Model<R>& P, const Ba
         force_pair<R>(P, g.r, g.inv_r, g.ux, g.uy, g.uz, s < na, A, bR, B0, fx, fy, fz);
         bad |= !isfinite(fx + fy + fz);
         typename A_::T cx = A_::conv(fx), cy = A_::conv(fy), cz = A_::conv(fz);
+        const double d64[3] = {(double)g.dx, (double)g.dy, (double)g.dz};
+        double f64[3] = {(double)fx, (double)fy, (double)fz};
         if (s < na && g.r < P.zbl_r2) {
-            const double d64[3] = {(double)g.dx, (double)g.dy, (double)g.dz};
             const double r64 = sqrt(d64[0] * d64[0] + d64[1] * d64[1] + d64[2] * d64[2]);
             if (r64 < P.zbl_rr2) {
                 double Uz, dUz;
@@ -212,8 +234,15 @@ __device__ __forceinline__ double batch_atom_forward(const Model<R>& P, const Ba
                 cx += A_::convd(c * d64[0]);
                 cy += A_::convd(c * d64[1]);
                 cz += A_::convd(c * d64[2]);
+                f64[0] += c * d64[0];
+                f64[1] += c * d64[1];
+                f64[2] += c * d64[2];
             }
         }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) w[3 * a + c] -= f64[a] * d64[c];
         fi[0] += cx; fi[1] += cy; fi[2] += cz;
         A_::add(&sF[0][g.j], -cx);
         A_::add(&sF[1][g.j], -cy);
@@ -232,7 +261,7 @@ __device__ __forceinline__ void batch_atom_tangent(const Model<R>& P, const Batc
                                                    int i, double eps,
                                                    const typename V4<R>::T* spos,
                                                    const typename V4<R>::T* s_off,
-                                                   const R (*se)[BMAXA])
+                                                   const R (*se)[BMAXA], const R* G)
 {
     const size_t col = (size_t)(a0 + i);
     const int2 c2 = b.cnt[col];
@@ -247,7 +276,9 @@ __device__ __forceinline__ void batch_atom_tangent(const Model<R>& P, const Batc
     for (int s = 0; s < tot; ++s) {
         const int ent = b.nbr[(size_t)slot_of(s, na, nro, M) * b.ntot + col];
         const PairGeom<R> g = pair_geom<R>(ent, pi, spos, s_off);
-        const R ud = g.ux * (se[0][g.j] - eix) + g.uy * (se[1][g.j] - eiy) + g.uz * (se[2][g.j] - eiz);
+        R vx, vy, vz;
+        pair_dir<R>(g, se, eix, eiy, eiz, G, vx, vy, vz);
+        const R ud = g.ux * vx + g.uy * vy + g.uz * vz;
         R T[KR], dT[KR], fc, dfc, dxdr;
         nepm::cheb<KR, true>(g.r, P.inv_rcR, T, dT, fc, dfc, dxdr);
 #pragma unroll
@@ -271,7 +302,8 @@ __device__ __forceinline__ void batch_atom_tangent(const Model<R>& P, const Batc
         for (int s = 0; s < na; ++s) {
             const int ent = b.nbr[(size_t)s * b.ntot + col];
             const PairGeom<R> g = pair_geom<R>(ent, pi, spos, s_off);
-            const R ddx = se[0][g.j] - eix, ddy = se[1][g.j] - eiy, ddz = se[2][g.j] - eiz;
+            R ddx, ddy, ddz;
+            pair_dir<R>(g, se, eix, eiy, eiz, G, ddx, ddy, ddz);
             const R ud = g.ux * ddx + g.uy * ddy + g.uz * ddz;
             R T[KA], dT[KA], fc, dfc, dxdr;
             nepm::cheb<KA, true>(g.r, P.inv_rcA, T, dT, fc, dfc, dxdr);
@@ -358,7 +390,8 @@ template <typename R>
 __device__ __forceinline__ void batch_atom_grad_cR(const Model<R>& P, const Batch& b, long long a0,
                                                    int i, const typename V4<R>::T* spos,
                                                    const typename V4<R>::T* s_off,
-                                                   const R (*se)[BMAXA], R (&gR)[NR * KR])
+                                                   const R (*se)[BMAXA], const R* G,
+                                                   R (&gR)[NR * KR])
 {
     const size_t col = (size_t)(a0 + i);
     const int2 c2 = b.cnt[col];
@@ -372,7 +405,9 @@ __device__ __forceinline__ void batch_atom_grad_cR(const Model<R>& P, const Batc
     for (int s = 0; s < tot; ++s) {
         const int ent = b.nbr[(size_t)slot_of(s, na, nro, M) * b.ntot + col];
         const PairGeom<R> g = pair_geom<R>(ent, pi, spos, s_off);
-        const R ud = g.ux * (se[0][g.j] - eix) + g.uy * (se[1][g.j] - eiy) + g.uz * (se[2][g.j] - eiz);
+        R vx, vy, vz;
+        pair_dir<R>(g, se, eix, eiy, eiz, G, vx, vy, vz);
+        const R ud = g.ux * vx + g.uy * vy + g.uz * vz;
         R T[KR], dT[KR], fc, dfc, dxdr;
         nepm::cheb<KR, true>(g.r, P.inv_rcR, T, dT, fc, dfc, dxdr);
 #pragma unroll
@@ -390,7 +425,8 @@ template <typename R>
 __device__ __forceinline__ void batch_atom_grad_cA(const Model<R>& P, const Batch& b, long long a0,
                                                    int i, int n, const typename V4<R>::T* spos,
                                                    const typename V4<R>::T* s_off,
-                                                   const R (*se)[BMAXA], R (&gA)[KA])
+                                                   const R (*se)[BMAXA], const R* G,
+                                                   R (&gA)[KA])
 {
     const size_t col = (size_t)(a0 + i);
     const int na = b.cnt[col].x;
@@ -430,7 +466,8 @@ __device__ __forceinline__ void batch_atom_grad_cA(const Model<R>& P, const Batc
     for (int s = 0; s < na; ++s) {
         const int ent = b.nbr[(size_t)s * b.ntot + col];
         const PairGeom<R> g = pair_geom<R>(ent, pi, spos, s_off);
-        const R ddx = se[0][g.j] - eix, ddy = se[1][g.j] - eiy, ddz = se[2][g.j] - eiz;
+        R ddx, ddy, ddz;
+        pair_dir<R>(g, se, eix, eiy, eiz, G, ddx, ddy, ddz);
         const R ud = g.ux * ddx + g.uy * ddy + g.uz * ddz;
         R Y[NLM], Dd[NLM];
         nepm::harmonics(g.ux, g.uy, g.uz, Y);
@@ -467,6 +504,7 @@ __global__ void __launch_bounds__(BT) k_batch(const Model<R> P, const Batch b)
     __shared__ R se[3][BMAXA];
     __shared__ P4 s_off[27];
     __shared__ double sh[BT / 32];
+    __shared__ R sG[9];
     __shared__ int s_cfg;
     for (;;) {
         __syncthreads();
@@ -504,15 +542,36 @@ __global__ void __launch_bounds__(BT) k_batch(const Model<R> P, const Batch b)
         }
         __syncthreads();
         for (int i = threadIdx.x; i < N; i += BT) batch_neighbors<R>(P, b, a0, N, i, spos, L);
+        if (MODE == MODE_LISTS) continue;   // lists only (population evaluation)
         double eps = 0.0;
+        if (threadIdx.x < 9) sG[threadIdx.x] = R(0);
         if (MODE != MODE_BACKWARD) {
             double esum = 0.0;
+            double w[9];
+#pragma unroll
+            for (int t = 0; t < 9; ++t) w[t] = 0.0;
             bool bad = false;
             for (int i = threadIdx.x; i < N; i += BT)
-                esum += batch_atom_forward<R>(P, b, a0, i, spos, s_off, sF, bad);
+                esum += batch_atom_forward<R>(P, b, a0, i, spos, s_off, sF, bad, w);
             if (bad) atomicOr(b.status, ST_NONFINITE);
             const double E = block_sum<BT>(esum, sh);   // also orders the force scatter
             if (threadIdx.x == 0) b.E[cfg] = E;
+            double Wc[9];
+#pragma unroll 1
+            for (int t = 0; t < 9; ++t) Wc[t] = block_sum<BT>(w[t], sh);
+            if (b.W && threadIdx.x == 0)
+                for (int t = 0; t < 9; ++t) b.W[(size_t)cfg * 9 + t] = Wc[t];
+            double lv = 0.0;
+            if (MODE == MODE_LOSS && b.Wt && b.hv[cfg]) {
+                // six components xx yy zz yz zx xy of (W - W_target) / N
+                const int ia[6] = {0, 4, 8, 5, 6, 1};
+                const double inv = 1.0 / ((double)N * N);
+                for (int c = 0; c < 6; ++c) {
+                    const double dw = Wc[ia[c]] - b.Wt[(size_t)cfg * 6 + c];
+                    lv += b.wv * dw * dw * inv / (6.0 * b.nv);
+                    if (threadIdx.x == 0) sG[ia[c]] = (R)(b.wv * 2.0 * dw * inv / (6.0 * b.nv));
+                }
+            }
             double f2 = 0.0;
             for (int i = threadIdx.x; i < N; i += BT) {
 #pragma unroll
@@ -531,20 +590,24 @@ __global__ void __launch_bounds__(BT) k_batch(const Model<R> P, const Batch b)
                 const double F2 = block_sum<BT>(f2, sh);
                 const double dE = (E - b.Et[cfg]) / N;
                 eps = b.we * 2.0 * dE / ((double)N * b.S);
-                if (threadIdx.x == 0)
-                    b.lpart[cfg] = b.we * dE * dE / b.S + b.wf * F2 / (3.0 * (double)b.ntot);
+                if (threadIdx.x == 0) {
+                    b.lpart[(size_t)cfg * 3] = b.we * dE * dE / b.S;
+                    b.lpart[(size_t)cfg * 3 + 1] = b.wf * F2 / (3.0 * (double)b.ntot);
+                    b.lpart[(size_t)cfg * 3 + 2] = lv;
+                }
             }
         } else {
             for (int i = threadIdx.x; i < N; i += BT)
 #pragma unroll
                 for (int d = 0; d < 3; ++d) se[d][i] = (R)b.dLdF[(size_t)d * b.ntot + a0 + i];
             eps = b.dLdE[cfg];
+            if (b.dLdW && threadIdx.x < 9) sG[threadIdx.x] = (R)b.dLdW[(size_t)cfg * 9 + threadIdx.x];
         }
         __syncthreads();
         if (MODE != MODE_FORWARD) {
             double* gp = b.gpart + (size_t)cfg * NP;
             for (int i = threadIdx.x; i < N; i += BT)
-                batch_atom_tangent<R>(P, b, a0, i, eps, spos, s_off, se);
+                batch_atom_tangent<R>(P, b, a0, i, eps, spos, s_off, se, sG);
             __syncthreads();
             // network weights: G_W = sum_i u (x) q - v (x) q-dot; b0, w1, b1
             const R* scr = (const R*)b.scr;
@@ -574,7 +637,7 @@ __global__ void __launch_bounds__(BT) k_batch(const Model<R> P, const Batch b)
 #pragma unroll
                 for (int t = 0; t < NR * KR; ++t) gR[t] = R(0);
                 for (int i = threadIdx.x; i < N; i += BT)
-                    batch_atom_grad_cR<R>(P, b, a0, i, spos, s_off, se, gR);
+                    batch_atom_grad_cR<R>(P, b, a0, i, spos, s_off, se, sG, gR);
 #pragma unroll 1
                 for (int t = 0; t < NR * KR; ++t) {
                     const double v = block_sum<BT>((double)gR[t], sh);
@@ -588,7 +651,7 @@ __global__ void __launch_bounds__(BT) k_batch(const Model<R> P, const Batch b)
 #pragma unroll
                 for (int t = 0; t < KA; ++t) gA[t] = R(0);
                 for (int i = threadIdx.x; i < N; i += BT)
-                    batch_atom_grad_cA<R>(P, b, a0, i, n, spos, s_off, se, gA);
+                    batch_atom_grad_cA<R>(P, b, a0, i, n, spos, s_off, se, sG, gA);
 #pragma unroll 1
                 for (int t = 0; t < KA; ++t) {
                     const double v = block_sum<BT>((double)gA[t], sh);
@@ -597,6 +660,231 @@ __global__ void __launch_bounds__(BT) k_batch(const Model<R> P, const Batch b)
             }
         }
     }
+}
+
+// ----------------------------------------------------------------------------
+// Population evaluation (SNES, Sec. III.A): the NEP loss of n_pop parameter
+// vectors over the whole batch in one launch.
+// ----------------------------------------------------------------------------
+
+// Model k of the population from theta_k (host layout) and the base model
+// (hyperparameters, scaler, ZBL): w0 scaled by s_nu, h = c/2, C = sum_k c/2.
+template <typename R>
+__global__ void k_build_models(const Model<R> base, const double* __restrict__ scaler,
+                               const double* __restrict__ thetas, Model<R>* __restrict__ out)
+{
+    const int k = blockIdx.x;
+    const double* th = thetas + (size_t)k * NP;
+    Model<R>& m = out[k];
+    // everything that is not a parameter comes from the base model
+    const unsigned* src = reinterpret_cast<const unsigned*>(&base);
+    unsigned* dst = reinterpret_cast<unsigned*>(&m);
+    for (int t = threadIdx.x; t < (int)(sizeof(Model<R>) / 4); t += blockDim.x) dst[t] = src[t];
+    __syncthreads();
+    for (int e = threadIdx.x; e < H * D; e += blockDim.x) m.w0[e] = (R)(th[e] * scaler[e % D]);
+    for (int e = threadIdx.x; e < H; e += blockDim.x) {
+        m.b0[e] = (R)th[OFF_B0 + e];
+        m.w1[e] = (R)th[OFF_W1 + e];
+    }
+    if (threadIdx.x == 0) m.b1 = (R)th[OFF_B1];
+    for (int e = threadIdx.x; e < NR * KR; e += blockDim.x) m.hR[e] = (R)(0.5 * th[OFF_CR + e]);
+    for (int e = threadIdx.x; e < NA * KA; e += blockDim.x) m.hA[e] = (R)(0.5 * th[OFF_CA + e]);
+    if (threadIdx.x < NR) {
+        double c = 0.0;
+        for (int kk = 0; kk < KR; ++kk) c += 0.5 * th[OFF_CR + threadIdx.x * KR + kk];
+        m.CR[threadIdx.x] = (R)c;
+    } else if (threadIdx.x >= 32 && threadIdx.x < 32 + NA) {
+        const int n = threadIdx.x - 32;
+        double c = 0.0;
+        for (int kk = 0; kk < KA; ++kk) c += 0.5 * th[OFF_CA + n * KA + kk];
+        m.CA[n] = (R)c;
+    }
+}
+
+// Work item t = (configuration order[t / n_pop], individual t % n_pop): the
+// individual's model is copied to shared memory, the configuration's forward
+// pass uses the lists built by the MODE_LISTS launch, and the item writes
+// pout[(k * S + cfg) * 3] = (dE / N, sum |dF|^2, sum over the six virial
+// components of (dW / N)^2 or 0 without a virial target).
+template <typename R, int BT>
+__global__ void __launch_bounds__(BT) k_batch_pop(const Model<R>* __restrict__ models, int n_pop,
+                                                  const Batch b, double* __restrict__ pout)
+{
+    using P4 = typename V4<R>::T;
+    using A_ = Acc<R>;
+    __shared__ Model<R> sP;
+    __shared__ P4 spos[BMAXA];
+    __shared__ typename A_::T sF[3][BMAXA];
+    __shared__ P4 s_off[27];
+    __shared__ double sh[BT / 32];
+    __shared__ int s_item;
+    const long long n_items = (long long)n_pop * b.S;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(b.queue, 1);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= n_items) break;
+        const int cfg = b.order[item / n_pop];
+        const int k = (int)(item % n_pop);
+        {
+            const unsigned* src = reinterpret_cast<const unsigned*>(models + k);
+            unsigned* dst = reinterpret_cast<unsigned*>(&sP);
+            for (int t = threadIdx.x; t < (int)(sizeof(Model<R>) / 4); t += BT) dst[t] = src[t];
+        }
+        const long long a0 = b.off[cfg];
+        const int N = (int)(b.off[cfg + 1] - a0);
+        const double L[3] = {b.box[3 * cfg], b.box[3 * cfg + 1], b.box[3 * cfg + 2]};
+        for (int i = threadIdx.x; i < N; i += BT) {
+            P4 q;
+            double p[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                double v = b.x[(size_t)d * b.ntot + a0 + i];
+                if (!isfinite(v)) v = 0.0;
+                p[d] = v - L[d] * floor(v / L[d]);
+            }
+            q.x = (R)p[0]; q.y = (R)p[1]; q.z = (R)p[2]; q.w = R(0);
+            spos[i] = q;
+            sF[0][i] = 0; sF[1][i] = 0; sF[2][i] = 0;
+        }
+        if (threadIdx.x < 27) {
+            const int c = threadIdx.x;
+            P4 o;
+            o.x = (R)((c / 9 - 1) * L[0]);
+            o.y = (R)(((c / 3) % 3 - 1) * L[1]);
+            o.z = (R)((c % 3 - 1) * L[2]);
+            o.w = R(0);
+            s_off[c] = o;
+        }
+        __syncthreads();
+        double esum = 0.0;
+        double w[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) w[t] = 0.0;
+        bool bad = false;
+        for (int i = threadIdx.x; i < N; i += BT)
+            esum += batch_atom_forward<R>(sP, b, a0, i, spos, s_off, sF, bad, w);
+        if (bad) atomicOr(b.status, ST_NONFINITE);
+        const double E = block_sum<BT>(esum, sh);   // also orders the force scatter
+        double f2 = 0.0;
+        for (int i = threadIdx.x; i < N; i += BT) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const size_t o = (size_t)d * b.ntot + a0 + i;
+                const double r = A_::value(sF[d][i]) - b.Ft[o];
+                f2 += r * r;
+            }
+        }
+        const double F2 = block_sum<BT>(f2, sh);
+        double v2 = 0.0;
+        if (b.Wt && b.hv[cfg]) {
+            const int ia[6] = {0, 4, 8, 5, 6, 1};
+            double Wc[9];
+#pragma unroll 1
+            for (int t = 0; t < 9; ++t) Wc[t] = block_sum<BT>(w[t], sh);
+            for (int c = 0; c < 6; ++c) {
+                const double dw = (Wc[ia[c]] - b.Wt[(size_t)cfg * 6 + c]) / N;
+                v2 += dw * dw;
+            }
+        }
+        if (threadIdx.x == 0) {
+            double* o = pout + ((size_t)k * b.S + cfg) * 3;
+            o[0] = (E - b.Et[cfg]) / N;
+            o[1] = F2;
+            o[2] = v2;
+        }
+    }
+}
+
+// losses[k * 6 + (0..5)] = total, L1, L2, RMSE_E, RMSE_F, RMSE_V of
+// individual k (one CTA per individual, fixed summation order).
+template <int BT>
+__global__ void __launch_bounds__(BT) k_pop_loss(const double* __restrict__ pout,
+                                                 const double* __restrict__ thetas, int S,
+                                                 long long ntot, double nv, double we, double wf,
+                                                 double wv, double l1, double l2,
+                                                 double* __restrict__ losses)
+{
+    __shared__ double sh[BT / 32];
+    const int k = blockIdx.x;
+    double e2 = 0.0, f2 = 0.0, v2 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int c = threadIdx.x; c < S; c += BT) {
+        const double* o = pout + ((size_t)k * S + c) * 3;
+        e2 += o[0] * o[0];
+        f2 += o[1];
+        v2 += o[2];
+    }
+    for (int p = threadIdx.x; p < NP; p += BT) {
+        const double t = thetas[(size_t)k * NP + p];
+        a1 += fabs(t);
+        a2 += t * t;
+    }
+    e2 = block_sum<BT>(e2, sh);
+    f2 = block_sum<BT>(f2, sh);
+    v2 = block_sum<BT>(v2, sh);
+    a1 = block_sum<BT>(a1, sh);
+    a2 = block_sum<BT>(a2, sh);
+    if (threadIdx.x == 0) {
+        const double re = sqrt(e2 / S), rf = sqrt(f2 / (3.0 * (double)ntot));
+        const double rv = nv > 0 ? sqrt(v2 / (6.0 * nv)) : 0.0;
+        const double r1 = l1 * a1 / NP, r2 = l2 * sqrt(a2 / NP);
+        double* o = losses + (size_t)k * 6;
+        o[0] = we * re + wf * rf + wv * rv + r1 + r2;
+        o[1] = r1;
+        o[2] = r2;
+        o[3] = re;
+        o[4] = rf;
+        o[5] = rv;
+    }
+}
+
+// SNES candidates theta_k = mu + sigma * s_k.
+static __global__ void k_snes_sample(const double* __restrict__ mu, const double* __restrict__ sigma,
+                                     const double* __restrict__ samples, int n_pop,
+                                     double* __restrict__ thetas)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n_pop * NP) return;
+    const int p = (int)(t % NP);
+    thetas[t] = mu[p] + sigma[p] * samples[t];
+}
+
+// SNES utilities by rank (best first, ties by index):
+// u_r = max(0, ln(n/2 + 1) - ln r) / sum_j max(0, ln(n/2 + 1) - ln j) - 1/n.
+static __global__ void k_snes_utilities(const double* __restrict__ losses, int n_pop,
+                                        double* __restrict__ util)
+{
+    const int k = threadIdx.x;
+    double norm = 0.0;
+    for (int r = 1; r <= n_pop; ++r) norm += fmax(0.0, log(n_pop / 2.0 + 1.0) - log((double)r));
+    if (k >= n_pop) return;
+    const double lk = losses[(size_t)k * 6];
+    int rank = 0;
+    for (int j = 0; j < n_pop; ++j) {
+        const double lj = losses[(size_t)j * 6];
+        rank += (lj < lk || (lj == lk && j < k)) ? 1 : 0;
+    }
+    util[k] = fmax(0.0, log(n_pop / 2.0 + 1.0) - log((double)(rank + 1))) / norm - 1.0 / n_pop;
+}
+
+// mu += eta_mu sigma sum_k u_k s_k ;  sigma *= exp(eta_sigma / 2 sum_k u_k (s_k^2 - 1)).
+static __global__ void k_snes_update(double* __restrict__ mu, double* __restrict__ sigma,
+                                     const double* __restrict__ samples,
+                                     const double* __restrict__ util, int n_pop, double eta_mu,
+                                     double eta_sigma)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= NP) return;
+    double gm = 0.0, gs = 0.0;
+    for (int k = 0; k < n_pop; ++k) {
+        const double sk = samples[(size_t)k * NP + p];
+        gm += util[k] * sk;
+        gs += util[k] * (sk * sk - 1.0);
+    }
+    const double sg = sigma[p];
+    mu[p] += eta_mu * sg * gm;
+    sigma[p] = sg * exp(0.5 * eta_sigma * gs);
 }
 
 // grad[p] = sum over configurations of gpart[c][p], in configuration order.

@@ -119,10 +119,20 @@ struct nep_ctx {
     double* b_lpart = nullptr;
     double* b_E = nullptr;
     double* b_F = nullptr;
+    double* b_W = nullptr;           // [S][9] virials
+    unsigned char* b_hv = nullptr;   // [S] has-virial mask of the last loss call
+    int b_hv_cap = 0;
     long long* b_off = nullptr;
     int* b_order = nullptr;
     double* b_box = nullptr;
     int* b_queue = nullptr;
+    // population evaluation (SNES)
+    double* p_thetas = nullptr;      // [n_pop][NP]
+    void* p_models = nullptr;        // n_pop models
+    double* p_out = nullptr;         // [n_pop][S][3]
+    double* p_util = nullptr;        // [1024]
+    double* d_scaler = nullptr;      // [D] FP64 descriptor scaler
+    size_t p_thetas_cap = 0, p_models_cap = 0, p_out_cap = 0;
     int b_bt = 128;          // threads per CTA
     int b_per_sm = 0;        // CTAs per SM (0: as many as fit)
     int b_tuned = 0;
@@ -676,7 +686,7 @@ static void free_batch(nep_ctx* ctx)
 {
     free_dev(ctx->b_nbr); free_dev(ctx->b_cnt); free_dev(ctx->b_scr); free_dev(ctx->b_gpart);
     free_dev(ctx->b_lpart); free_dev(ctx->b_E); free_dev(ctx->b_F); free_dev(ctx->b_off);
-    free_dev(ctx->b_order); free_dev(ctx->b_box); free_dev(ctx->b_queue);
+    free_dev(ctx->b_order); free_dev(ctx->b_box); free_dev(ctx->b_queue); free_dev(ctx->b_W);
     ctx->b_ntot_cap = 0;
     ctx->b_S_cap = 0;
     ctx->b_M = 0;
@@ -691,7 +701,9 @@ void nep_free(nep_ctx* ctx)
     free_dev(ctx->count); free_dev(ctx->start); free_dev(ctx->scan_sums);
     free_dev(ctx->thermo); free_dev(ctx->thermo_backup); free_dev(ctx->result);
     free_dev(ctx->status); free_dev(ctx->pairs); free_dev(ctx->gate); free_dev(ctx->nrebuild);
-    free_dev(ctx->coef_f); free_dev(ctx->coef_d);
+    free_dev(ctx->coef_f); free_dev(ctx->coef_d); free_dev(ctx->b_hv);
+    free_dev(ctx->p_thetas); free_dev(ctx->p_models); free_dev(ctx->p_out); free_dev(ctx->p_util);
+    free_dev(ctx->d_scaler);
     if (ctx->h_result) cudaFreeHost(ctx->h_result);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->h_pairs) cudaFreeHost(ctx->h_pairs);
@@ -1018,6 +1030,19 @@ int md_step(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
 // Batches of small periodic configurations
 // ============================================================================
 
+// Grows a device buffer to at least `bytes`.
+static int grow(nep_ctx* ctx, void** p, size_t& cap, size_t bytes, cudaStream_t s)
+{
+    if (bytes <= cap && *p) return NEP_OK;
+    CK(cudaStreamSynchronize(s));
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    cap = 0;
+    CK(cudaMalloc(p, bytes));
+    cap = bytes;
+    return NEP_OK;
+}
+
 static int batch_buffers(nep_ctx* ctx, long long ntot, int S, int M)
 {
     if (ntot <= ctx->b_ntot_cap && S <= ctx->b_S_cap && M <= ctx->b_M && ctx->b_nbr) return NEP_OK;
@@ -1032,8 +1057,9 @@ static int batch_buffers(nep_ctx* ctx, long long ntot, int S, int M)
     CK(cudaMalloc(&ctx->b_scr, rsz * (size_t)nc * BSTRIDE));
     CK(cudaMalloc(&ctx->b_F, sizeof(double) * 3 * (size_t)nc));
     CK(cudaMalloc(&ctx->b_gpart, sizeof(double) * (size_t)Sc * NP));
-    CK(cudaMalloc(&ctx->b_lpart, sizeof(double) * (size_t)Sc));
+    CK(cudaMalloc(&ctx->b_lpart, sizeof(double) * 3 * (size_t)Sc));
     CK(cudaMalloc(&ctx->b_E, sizeof(double) * (size_t)Sc));
+    CK(cudaMalloc(&ctx->b_W, sizeof(double) * 9 * (size_t)Sc));
     CK(cudaMalloc(&ctx->b_off, sizeof(long long) * (size_t)(Sc + 1)));
     CK(cudaMalloc(&ctx->b_order, sizeof(int) * (size_t)Sc));
     CK(cudaMalloc(&ctx->b_box, sizeof(double) * 3 * (size_t)Sc));
@@ -1094,7 +1120,10 @@ static int batch_prepare(nep_ctx* ctx, const nep_batch* bt, cudaStream_t s, Batc
 }
 
 // Runs one batched launch (with neighbour-capacity growth) and waits.
-static int batch_launch(nep_ctx* ctx, Batch& b, int mode, double* grad, cudaStream_t s)
+// uE, uF, uW: the caller's outputs, or nullptr for the context's scratch
+// (re-pointed after a reallocation).
+static int batch_launch(nep_ctx* ctx, Batch& b, int mode, double* grad, cudaStream_t s,
+                        double* uE = nullptr, double* uF = nullptr, double* uW = nullptr)
 {
     int dev = 0, sms = 0;
     CK(cudaGetDevice(&dev));
@@ -1111,13 +1140,16 @@ static int batch_launch(nep_ctx* ctx, Batch& b, int mode, double* grad, cudaStre
         b.order = ctx->b_order;
         b.box = ctx->b_box;
         b.queue = ctx->b_queue;
+        b.E = uE ? uE : ctx->b_E;
+        b.F = uF ? uF : ctx->b_F;
+        b.W = uW ? uW : ctx->b_W;
         int per_sm = ctx->b_per_sm > 0 ? ctx->b_per_sm
                                         : batch_blocks_per_sm(ctx->precision, mode, bt);
         int grid = std::min(b.S, std::max(1, per_sm * sms));
         CK(cudaMemsetAsync(ctx->b_queue, 0, sizeof(int), s));
         CK(cudaMemsetAsync(ctx->status, 0, sizeof(int) * 3, s));
         CK(launch_batch(ctx->precision, mode, bt, grid, ctx->mf, ctx->md, b, grad, s));
-        ctx->launches += mode == 0 ? 1 : 2;
+        ctx->launches += (mode == MODE_BACKWARD || mode == MODE_LOSS) ? 2 : 1;
         CK(cudaMemcpyAsync(ctx->h_status, ctx->status, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (ctx->h_status[0] & ST_OVERFLOW) {
@@ -1163,7 +1195,7 @@ int nep_set_params(nep_ctx* ctx, const double* params, int64_t n_params)
 }
 
 int nep_batch_forward(nep_ctx* ctx, const nep_batch* batch, double* energies, double* forces,
-                      void* stream)
+                      double* virials, void* stream)
 {
     if (!ctx) return NEP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1171,15 +1203,14 @@ int nep_batch_forward(nep_ctx* ctx, const nep_batch* batch, double* energies, do
     if ((rc = check_device_ptr(ctx, energies, "energies")) ||
         (rc = check_device_ptr(ctx, forces, "forces")))
         return rc;
+    if (virials && (rc = check_device_ptr(ctx, virials, "virials"))) return rc;
     Batch b;
     if ((rc = batch_prepare(ctx, batch, s, b))) return rc;
-    b.E = energies;
-    b.F = forces;
-    return batch_launch(ctx, b, MODE_FORWARD, nullptr, s);
+    return batch_launch(ctx, b, MODE_FORWARD, nullptr, s, energies, forces, virials);
 }
 
 int nep_batch_backward(nep_ctx* ctx, const nep_batch* batch, const double* dL_dE,
-                       const double* dL_dF, double* grad, void* stream)
+                       const double* dL_dF, const double* dL_dW, double* grad, void* stream)
 {
     if (!ctx) return NEP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1187,45 +1218,82 @@ int nep_batch_backward(nep_ctx* ctx, const nep_batch* batch, const double* dL_dE
     if ((rc = check_device_ptr(ctx, dL_dE, "dL_dE")) || (rc = check_device_ptr(ctx, dL_dF, "dL_dF")) ||
         (rc = check_device_ptr(ctx, grad, "grad")))
         return rc;
+    if (dL_dW && (rc = check_device_ptr(ctx, dL_dW, "dL_dW"))) return rc;
     Batch b;
     if ((rc = batch_prepare(ctx, batch, s, b))) return rc;
     b.dLdE = dL_dE;
     b.dLdF = dL_dF;
+    b.dLdW = dL_dW;
     return batch_launch(ctx, b, MODE_BACKWARD, grad, s);
 }
 
-int nep_batch_loss_grad(nep_ctx* ctx, const nep_batch* batch, const double* E_target,
-                        const double* F_target, double w_energy, double w_force, double* loss,
-                        double* grad, double* energies, double* forces, void* stream)
+// Uploads the has-virial mask (all ones when NULL) and returns how many
+// configurations have a virial target.
+static int upload_virial_mask(nep_ctx* ctx, const nep_targets* t, int S, cudaStream_t s, int* nv)
 {
-    if (!ctx) return NEP_ERR_INVALID_ARG;
-    if (!loss) return fail(ctx, NEP_ERR_INVALID_ARG, "loss is NULL");
-    cudaStream_t s = (cudaStream_t)stream;
-    int rc;
-    if ((rc = check_device_ptr(ctx, E_target, "E_target")) ||
-        (rc = check_device_ptr(ctx, F_target, "F_target")) || (rc = check_device_ptr(ctx, grad, "grad")))
-        return rc;
-    if (energies && (rc = check_device_ptr(ctx, energies, "energies"))) return rc;
-    if (forces && (rc = check_device_ptr(ctx, forces, "forces"))) return rc;
-    Batch b;
-    if ((rc = batch_prepare(ctx, batch, s, b))) return rc;
-    b.E = energies ? energies : ctx->b_E;
-    b.F = forces ? forces : ctx->b_F;
-    b.Et = E_target;
-    b.Ft = F_target;
-    b.we = w_energy;
-    b.wf = w_force;
-    if ((rc = batch_launch(ctx, b, MODE_LOSS, grad, s))) return rc;
-    std::vector<double> lp(b.S);
-    CK(cudaMemcpy(lp.data(), ctx->b_lpart, sizeof(double) * b.S, cudaMemcpyDeviceToHost));
-    double L = 0.0;
-    for (int c = 0; c < b.S; ++c) L += lp[c];
-    *loss = L;
+    *nv = 0;
+    if (!t->virial) return NEP_OK;
+    int rc = check_device_ptr(ctx, t->virial, "virial targets");
+    if (rc) return rc;
+    if (S > ctx->b_hv_cap) {
+        CK(cudaStreamSynchronize(s));
+        free_dev(ctx->b_hv);
+        CK(cudaMalloc(&ctx->b_hv, (size_t)S));
+        ctx->b_hv_cap = S;
+    }
+    std::vector<unsigned char> hv(S);
+    for (int c = 0; c < S; ++c) {
+        hv[c] = t->has_virial ? (t->has_virial[c] ? 1 : 0) : 1;
+        *nv += hv[c];
+    }
+    CK(cudaMemcpyAsync(ctx->b_hv, hv.data(), (size_t)S, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
     return NEP_OK;
 }
 
-int nep_batch_autotune(nep_ctx* ctx, const nep_batch* batch, const double* E_target,
-                       const double* F_target, void* stream, int* best_threads, int* best_per_sm)
+int nep_batch_loss_grad(nep_ctx* ctx, const nep_batch* batch, const nep_targets* t,
+                        const nep_loss_weights* w, double* loss, double* grad, double* energies,
+                        double* forces, double* virials, void* stream)
+{
+    if (!ctx) return NEP_ERR_INVALID_ARG;
+    if (!loss || !t || !w) return fail(ctx, NEP_ERR_INVALID_ARG, "loss, targets or weights is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    if ((rc = check_device_ptr(ctx, t->energy, "energy targets")) ||
+        (rc = check_device_ptr(ctx, t->forces, "force targets")) ||
+        (rc = check_device_ptr(ctx, grad, "grad")))
+        return rc;
+    if (energies && (rc = check_device_ptr(ctx, energies, "energies"))) return rc;
+    if (forces && (rc = check_device_ptr(ctx, forces, "forces"))) return rc;
+    if (virials && (rc = check_device_ptr(ctx, virials, "virials"))) return rc;
+    Batch b;
+    if ((rc = batch_prepare(ctx, batch, s, b))) return rc;
+    int nv = 0;
+    if ((rc = upload_virial_mask(ctx, t, b.S, s, &nv))) return rc;
+    b.Et = t->energy;
+    b.Ft = t->forces;
+    b.Wt = nv > 0 ? t->virial : nullptr;
+    b.hv = ctx->b_hv;
+    b.nv = nv;
+    b.we = w->energy;
+    b.wf = w->force;
+    b.wv = w->virial;
+    if ((rc = batch_launch(ctx, b, MODE_LOSS, grad, s, energies, forces, virials))) return rc;
+    std::vector<double> lp(3 * (size_t)b.S);
+    CK(cudaMemcpy(lp.data(), ctx->b_lpart, sizeof(double) * 3 * b.S, cudaMemcpyDeviceToHost));
+    double terms[3] = {0.0, 0.0, 0.0};
+    for (int c = 0; c < b.S; ++c)
+        for (int k = 0; k < 3; ++k) terms[k] += lp[3 * (size_t)c + k];
+    loss[0] = terms[0] + terms[1] + terms[2];
+    loss[1] = terms[0];
+    loss[2] = terms[1];
+    loss[3] = terms[2];
+    return NEP_OK;
+}
+
+int nep_batch_autotune(nep_ctx* ctx, const nep_batch* batch, const nep_targets* t,
+                       const nep_loss_weights* w, void* stream, int* best_threads,
+                       int* best_per_sm)
 {
     if (!ctx) return NEP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1243,13 +1311,12 @@ int nep_batch_autotune(nep_ctx* ctx, const nep_batch* batch, const double* E_tar
         for (int per = 1; per <= 4 && !rc; per *= 2) {
             ctx->b_bt = ctx->precision == NEP_FP32 ? bts[a] : 128;
             ctx->b_per_sm = per;
-            double L = 0.0;
-            rc = nep_batch_loss_grad(ctx, batch, E_target, F_target, 1.0, 1.0, &L, grad, nullptr,
-                                     nullptr, stream);   // warm-up
+            double L[4];
+            rc = nep_batch_loss_grad(ctx, batch, t, w, L, grad, nullptr, nullptr, nullptr,
+                                     stream);   // warm-up
             if (rc) break;
             cudaEventRecord(e0, s);
-            rc = nep_batch_loss_grad(ctx, batch, E_target, F_target, 1.0, 1.0, &L, grad, nullptr,
-                                     nullptr, stream);
+            rc = nep_batch_loss_grad(ctx, batch, t, w, L, grad, nullptr, nullptr, nullptr, stream);
             cudaEventRecord(e1, s);
             cudaEventSynchronize(e1);
             float ms = 0.f;
@@ -1266,6 +1333,106 @@ int nep_batch_autotune(nep_ctx* ctx, const nep_batch* batch, const double* E_tar
     if (best_threads) *best_threads = bb;
     if (best_per_sm) *best_per_sm = bs;
     return rc;
+}
+
+
+// Loss terms of n_pop parameter vectors (device thetas [n_pop][NP]) over the
+// batch: one list-building launch, the models, one population launch, one
+// loss launch; losses (device) [n_pop][6].
+static int population_eval(nep_ctx* ctx, const nep_batch* batch, const nep_targets* t,
+                           const nep_loss_weights* w, int n_pop, const double* thetas,
+                           double* losses, cudaStream_t s)
+{
+    int rc;
+    if ((rc = check_device_ptr(ctx, t->energy, "energy targets")) ||
+        (rc = check_device_ptr(ctx, t->forces, "force targets")))
+        return rc;
+    Batch b;
+    if ((rc = batch_prepare(ctx, batch, s, b))) return rc;
+    int nv = 0;
+    if ((rc = upload_virial_mask(ctx, t, b.S, s, &nv))) return rc;
+    // neighbour lists of every configuration (capacity grows on overflow)
+    if ((rc = batch_launch(ctx, b, MODE_LISTS, nullptr, s))) return rc;
+    b.Et = t->energy;
+    b.Ft = t->forces;
+    b.Wt = nv > 0 ? t->virial : nullptr;
+    b.hv = ctx->b_hv;
+    b.nv = nv;
+    if (!ctx->d_scaler) {
+        CK(cudaMalloc(&ctx->d_scaler, sizeof(double) * D));
+        CK(cudaMemcpy(ctx->d_scaler, ctx->scaler.data(), sizeof(double) * D, cudaMemcpyHostToDevice));
+    }
+    if ((rc = grow(ctx, &ctx->p_models, ctx->p_models_cap, model_bytes(ctx->precision) * n_pop, s)) ||
+        (rc = grow(ctx, (void**)&ctx->p_out, ctx->p_out_cap,
+                   sizeof(double) * 3 * (size_t)n_pop * b.S, s)))
+        return rc;
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const long long items = (long long)n_pop * b.S;
+    const int grid = (int)std::min<long long>(items, (long long)population_blocks_per_sm(ctx->precision) * sms);
+    CK(cudaMemsetAsync(ctx->b_queue, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(ctx->status, 0, sizeof(int) * 3, s));
+    CK(launch_population(ctx->precision, n_pop, ctx->mf, ctx->md, ctx->d_scaler, thetas,
+                         ctx->p_models, b, ctx->p_out, grid, s));
+    CK(launch_population_loss(n_pop, ctx->p_out, thetas, b.S, b.ntot, (double)nv, w->energy,
+                              w->force, w->virial, w->l1, w->l2, losses, s));
+    ctx->launches += 3;
+    CK(cudaMemcpyAsync(ctx->h_status, ctx->status, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (ctx->h_status[0] & ST_NONFINITE)
+        return fail(ctx, NEP_ERR_NONFINITE, "non-finite values in the population");
+    return NEP_OK;
+}
+
+static int population_args(nep_ctx* ctx, const nep_targets* t, const nep_loss_weights* w,
+                           int n_pop)
+{
+    if (!t || !w) return fail(ctx, NEP_ERR_INVALID_ARG, "targets or weights is NULL");
+    if (n_pop < 1 || n_pop > 1024) return fail(ctx, NEP_ERR_INVALID_ARG, "n_pop must be 1..1024");
+    if ((long long)n_pop * NP > (1LL << 31))
+        return fail(ctx, NEP_ERR_INVALID_ARG, "population too large");
+    return NEP_OK;
+}
+
+int nep_population_loss(nep_ctx* ctx, const nep_batch* batch, const nep_targets* t,
+                        const nep_loss_weights* w, int n_pop, const double* thetas,
+                        double* losses, void* stream)
+{
+    if (!ctx) return NEP_ERR_INVALID_ARG;
+    int rc;
+    if ((rc = population_args(ctx, t, w, n_pop))) return rc;
+    if ((rc = check_device_ptr(ctx, thetas, "thetas")) || (rc = check_device_ptr(ctx, losses, "losses")))
+        return rc;
+    return population_eval(ctx, batch, t, w, n_pop, thetas, losses, (cudaStream_t)stream);
+}
+
+int nep_snes_generation(nep_ctx* ctx, const nep_batch* batch, const nep_targets* t,
+                        const nep_loss_weights* w, int n_pop, double* mu, double* sigma,
+                        const double* samples, double eta_mu, double eta_sigma, double* losses,
+                        void* stream)
+{
+    if (!ctx) return NEP_ERR_INVALID_ARG;
+    int rc;
+    if ((rc = population_args(ctx, t, w, n_pop))) return rc;
+    if ((rc = check_device_ptr(ctx, mu, "mu")) || (rc = check_device_ptr(ctx, sigma, "sigma")) ||
+        (rc = check_device_ptr(ctx, samples, "samples")) ||
+        (rc = check_device_ptr(ctx, losses, "losses")))
+        return rc;
+    if (!isfinite(eta_mu) || !isfinite(eta_sigma))
+        return fail(ctx, NEP_ERR_INVALID_ARG, "learning rates must be finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = grow(ctx, (void**)&ctx->p_thetas, ctx->p_thetas_cap, sizeof(double) * NP * (size_t)n_pop,
+                   s)))
+        return rc;
+    if (!ctx->p_util) CK(cudaMalloc(&ctx->p_util, sizeof(double) * 1024));
+    CK(launch_snes_sample(mu, sigma, samples, n_pop, ctx->p_thetas, s));
+    ctx->launches += 1;
+    if ((rc = population_eval(ctx, batch, t, w, n_pop, ctx->p_thetas, losses, s))) return rc;
+    CK(launch_snes_update(mu, sigma, samples, losses, ctx->p_util, n_pop, eta_mu, eta_sigma, s));
+    ctx->launches += 2;
+    CK(cudaStreamSynchronize(s));
+    return NEP_OK;
 }
 
 }  // extern "C"

@@ -32,7 +32,7 @@ NEP_OPT_SKIN_MILLIANGSTROM = 4
 EXPORTED = ("nep_init", "nep_free", "nep_last_error", "nep_compute", "md_step",
             "nep_get_stats", "nep_set_option", "nep_reset_stats", "nep_compute_static",
             "nep_set_params", "nep_batch_forward", "nep_batch_backward", "nep_batch_loss_grad",
-            "nep_batch_autotune")
+            "nep_batch_autotune", "nep_population_loss", "nep_snes_generation")
 
 
 class NepParams(C.Structure):
@@ -61,6 +61,16 @@ class NepStats(C.Structure):
                 ("pairs_angular", C.c_int64), ("max_nbr_radial", C.c_int32),
                 ("max_nbr_angular", C.c_int32), ("nbr_capacity", C.c_int32),
                 ("graph_chunk", C.c_int32), ("list_builds_skin", C.c_int64)]
+
+
+class NepTargets(C.Structure):
+    _fields_ = [("energy", C.c_void_p), ("forces", C.c_void_p), ("virial", C.c_void_p),
+                ("has_virial", C.POINTER(C.c_uint8))]
+
+
+class NepLossWeights(C.Structure):
+    _fields_ = [("energy", C.c_double), ("force", C.c_double), ("virial", C.c_double),
+                ("l1", C.c_double), ("l2", C.c_double)]
 
 
 class NepBatch(C.Structure):
@@ -112,14 +122,20 @@ def load(build: bool = True):
     L.nep_set_params.argtypes = [vp, C.POINTER(C.c_double), C.c_int64]
     L.nep_set_params.restype = C.c_int
     bp = C.POINTER(NepBatch)
-    L.nep_batch_forward.argtypes = [vp, bp, vp, vp, vp]
+    tp = C.POINTER(NepTargets)
+    wp = C.POINTER(NepLossWeights)
+    L.nep_batch_forward.argtypes = [vp, bp, vp, vp, vp, vp]
     L.nep_batch_forward.restype = C.c_int
-    L.nep_batch_backward.argtypes = [vp, bp, vp, vp, vp, vp]
+    L.nep_batch_backward.argtypes = [vp, bp, vp, vp, vp, vp, vp]
     L.nep_batch_backward.restype = C.c_int
-    L.nep_batch_loss_grad.argtypes = [vp, bp, vp, vp, C.c_double, C.c_double,
-                                      C.POINTER(C.c_double), vp, vp, vp, vp]
+    L.nep_batch_loss_grad.argtypes = [vp, bp, tp, wp, C.POINTER(C.c_double), vp, vp, vp, vp, vp]
     L.nep_batch_loss_grad.restype = C.c_int
-    L.nep_batch_autotune.argtypes = [vp, bp, vp, vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.nep_batch_autotune.argtypes = [vp, bp, tp, wp, vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.nep_population_loss.argtypes = [vp, bp, tp, wp, C.c_int, vp, vp, vp]
+    L.nep_population_loss.restype = C.c_int
+    L.nep_snes_generation.argtypes = [vp, bp, tp, wp, C.c_int, vp, vp, vp, C.c_double, C.c_double,
+                                      vp, vp]
+    L.nep_snes_generation.restype = C.c_int
     L.nep_batch_autotune.restype = C.c_int
     _lib = L
     return L
@@ -256,51 +272,138 @@ class NEP:
         self._check(self.lib.nep_set_params(self.ctx, t.ctypes.data_as(C.POINTER(C.c_double)),
                                             len(t)))
 
-    def batch_forward(self, batch: "Batch", stream=None):
-        """Energies (S,) and forces (3, N) of every configuration (CUDA tensors)."""
+    def batch_forward(self, batch: "Batch", virials=False, stream=None):
+        """Energies (S,) and forces (3, N) of every configuration (CUDA tensors),
+        and virials (S, 3, 3) if ``virials``."""
         import torch
         E = torch.empty(batch.S, dtype=torch.float64, device=batch.device)
         F = torch.empty((3, batch.N), dtype=torch.float64, device=batch.device)
+        W = torch.empty((batch.S, 3, 3), dtype=torch.float64, device=batch.device) if virials \
+            else None
         self._check(self.lib.nep_batch_forward(self.ctx, C.byref(batch.c), C.c_void_p(E.data_ptr()),
-                                               C.c_void_p(F.data_ptr()), _stream_ptr(stream)))
-        return E, F
+                                               C.c_void_p(F.data_ptr()),
+                                               C.c_void_p(W.data_ptr()) if virials else None,
+                                               _stream_ptr(stream)))
+        return (E, F, W) if virials else (E, F)
 
-    def batch_backward(self, batch: "Batch", dLdE, dLdF, stream=None):
-        """Parameter gradient (n_params,) of a loss from dL/dE (S,) and dL/dF (3, N)."""
+    def batch_backward(self, batch: "Batch", dLdE, dLdF, dLdW=None, stream=None):
+        """Parameter gradient (n_params,) of a loss from dL/dE (S,), dL/dF (3, N)
+        and optionally dL/dW (S, 3, 3)."""
         import torch
         dLdE = dLdE.contiguous().to(torch.float64)
         dLdF = dLdF.contiguous().to(torch.float64)
+        if dLdW is not None:
+            dLdW = dLdW.contiguous().to(torch.float64)
         g = torch.empty(len(self._params), dtype=torch.float64, device=batch.device)
         self._check(self.lib.nep_batch_backward(self.ctx, C.byref(batch.c),
                                                 C.c_void_p(dLdE.data_ptr()),
                                                 C.c_void_p(dLdF.data_ptr()),
+                                                C.c_void_p(dLdW.data_ptr()) if dLdW is not None
+                                                else None,
                                                 C.c_void_p(g.data_ptr()), _stream_ptr(stream)))
         return g
 
+    @staticmethod
+    def _targets(E_target, F_target, W_target=None, has_virial=None):
+        t = NepTargets()
+        keep = [E_target.contiguous(), F_target.contiguous()]
+        t.energy = keep[0].data_ptr()
+        t.forces = keep[1].data_ptr()
+        if W_target is not None:
+            keep.append(W_target.contiguous())
+            t.virial = keep[-1].data_ptr()
+            if has_virial is not None:
+                hv = np.ascontiguousarray(has_virial, dtype=np.uint8)
+                keep.append(hv)
+                t.has_virial = hv.ctypes.data_as(C.POINTER(C.c_uint8))
+        return t, keep
+
     def batch_loss_grad(self, batch: "Batch", E_target, F_target, w_energy=1.0, w_force=1.0,
-                        stream=None):
-        """Fused forward + energy/force MSE loss + gradient in one persistent launch.
-        Returns (loss, grad (n_params,), E (S,), F (3, N))."""
+                        W_target=None, has_virial=None, w_virial=0.0, stream=None):
+        """Fused forward + mean-square loss (energy, force and, with ``W_target``
+        (S, 6: xx yy zz yz zx xy), virial terms) + gradient in one persistent
+        launch.  Returns (loss, grad (n_params,), E (S,), F (3, N)); the loss
+        terms and the virials (S, 3, 3) are kept in ``last_loss_terms`` and
+        ``last_virials``."""
         import torch
         E = torch.empty(batch.S, dtype=torch.float64, device=batch.device)
         F = torch.empty((3, batch.N), dtype=torch.float64, device=batch.device)
+        W = torch.empty((batch.S, 3, 3), dtype=torch.float64, device=batch.device)
         g = torch.empty(len(self._params), dtype=torch.float64, device=batch.device)
-        Et = E_target.contiguous()
-        Ft = F_target.contiguous()
-        L = C.c_double()
+        t, keep = self._targets(E_target, F_target, W_target, has_virial)
+        w = NepLossWeights(float(w_energy), float(w_force), float(w_virial), 0.0, 0.0)
+        L = (C.c_double * 4)()
         self._check(self.lib.nep_batch_loss_grad(
-            self.ctx, C.byref(batch.c), C.c_void_p(Et.data_ptr()), C.c_void_p(Ft.data_ptr()),
-            float(w_energy), float(w_force), C.byref(L), C.c_void_p(g.data_ptr()),
-            C.c_void_p(E.data_ptr()), C.c_void_p(F.data_ptr()), _stream_ptr(stream)))
-        return L.value, g, E, F
+            self.ctx, C.byref(batch.c), C.byref(t), C.byref(w), L, C.c_void_p(g.data_ptr()),
+            C.c_void_p(E.data_ptr()), C.c_void_p(F.data_ptr()), C.c_void_p(W.data_ptr()),
+            _stream_ptr(stream)))
+        self.last_loss_terms = {"energy": L[1], "force": L[2], "virial": L[3]}
+        self.last_virials = W
+        return L[0], g, E, F
 
-    def batch_autotune(self, batch: "Batch", E_target, F_target, stream=None):
+    def batch_autotune(self, batch: "Batch", E_target, F_target, W_target=None, has_virial=None,
+                       w_virial=0.0, stream=None):
         bt, per = C.c_int(), C.c_int()
-        self._check(self.lib.nep_batch_autotune(
-            self.ctx, C.byref(batch.c), C.c_void_p(E_target.contiguous().data_ptr()),
-            C.c_void_p(F_target.contiguous().data_ptr()), _stream_ptr(stream), C.byref(bt),
-            C.byref(per)))
+        t, keep = self._targets(E_target, F_target, W_target, has_virial)
+        w = NepLossWeights(1.0, 1.0, float(w_virial), 0.0, 0.0)
+        self._check(self.lib.nep_batch_autotune(self.ctx, C.byref(batch.c), C.byref(t),
+                                                C.byref(w), _stream_ptr(stream), C.byref(bt),
+                                                C.byref(per)))
         return bt.value, per.value
+
+
+# loss weights of the paper's training (Sec. III.A)
+PAPER_WEIGHTS = {"energy": 1.0, "force": 1.0, "virial": 0.1, "l1": 0.05, "l2": 0.05}
+LOSS_TERMS = ("total", "l1", "l2", "energy", "force", "virial")
+
+
+def _weights(w):
+    w = dict(PAPER_WEIGHTS, **(w or {}))
+    return NepLossWeights(w["energy"], w["force"], w["virial"], w["l1"], w["l2"])
+
+
+def population_loss(nep: "NEP", batch: "Batch", thetas, E_target, F_target, W_target=None,
+                    has_virial=None, weights=None, stream=None):
+    """NEP loss terms (n_pop, 6: total, L1, L2, RMSE_E, RMSE_F, RMSE_V) of the
+    parameter vectors thetas (n_pop, n_params) (CUDA float64)."""
+    import torch
+    thetas = thetas.contiguous().to(torch.float64)
+    n_pop = thetas.shape[0]
+    losses = torch.empty((n_pop, 6), dtype=torch.float64, device=batch.device)
+    t, keep = NEP._targets(E_target, F_target, W_target, has_virial)
+    w = _weights(weights)
+    nep._check(nep.lib.nep_population_loss(nep.ctx, C.byref(batch.c), C.byref(t), C.byref(w),
+                                           int(n_pop), C.c_void_p(thetas.data_ptr()),
+                                           C.c_void_p(losses.data_ptr()), _stream_ptr(stream)))
+    return losses
+
+
+def snes_generation(nep: "NEP", batch: "Batch", mu, sigma, samples, E_target, F_target,
+                    W_target=None, has_virial=None, weights=None, eta_mu=None, eta_sigma=None,
+                    stream=None):
+    """One SNES generation: mu, sigma (n_params,) CUDA float64 tensors are
+    updated in place from the standard-normal samples (n_pop, n_params).
+    Returns the candidates' loss terms (n_pop, 6)."""
+    import math
+    import torch
+    d = mu.numel()
+    if eta_mu is None:
+        eta_mu = 1.0
+    if eta_sigma is None:
+        eta_sigma = (3.0 + math.log(d)) / (5.0 * math.sqrt(d))
+    assert mu.is_contiguous() and sigma.is_contiguous() and mu.dtype == torch.float64
+    samples = samples.contiguous().to(torch.float64)
+    n_pop = samples.shape[0]
+    losses = torch.empty((n_pop, 6), dtype=torch.float64, device=batch.device)
+    t, keep = NEP._targets(E_target, F_target, W_target, has_virial)
+    w = _weights(weights)
+    nep._check(nep.lib.nep_snes_generation(nep.ctx, C.byref(batch.c), C.byref(t), C.byref(w),
+                                           int(n_pop), C.c_void_p(mu.data_ptr()),
+                                           C.c_void_p(sigma.data_ptr()),
+                                           C.c_void_p(samples.data_ptr()), float(eta_mu),
+                                           float(eta_sigma), C.c_void_p(losses.data_ptr()),
+                                           _stream_ptr(stream)))
+    return losses
 
 
 class Batch:
@@ -330,25 +433,26 @@ class Batch:
         self.c = c
 
 
-def energy_forces_function():
-    """torch.autograd.Function: (theta, nep, batch) -> (E (S,), F (3, N)).  Its
-    backward calls the library's hand-written gradient kernels with the
-    upstream dL/dE and dL/dF (the force term needs the second derivatives of
-    the energy), returning dL/dtheta."""
+def energy_forces_function(virials: bool = False):
+    """torch.autograd.Function: (theta, nep, batch) -> (E (S,), F (3, N)), or
+    (E, F, W (S, 3, 3)) with ``virials``.  Its backward calls the library's
+    hand-written gradient kernels with the upstream dL/dE, dL/dF (and dL/dW)
+    (the force and virial terms need second derivatives of the energy),
+    returning dL/dtheta."""
     import torch
 
     class NEPEnergyForces(torch.autograd.Function):
         @staticmethod
         def forward(ctx, theta, nep, batch):
             nep.set_params(theta)
-            E, F = nep.batch_forward(batch)
+            out = nep.batch_forward(batch, virials=virials)
             ctx.nep = nep
             ctx.batch = batch
             ctx.save_for_backward(theta)
-            return E, F
+            return out
 
         @staticmethod
-        def backward(ctx, gE, gF):
+        def backward(ctx, gE, gF, gW=None):
             (theta,) = ctx.saved_tensors
             nep, batch = ctx.nep, ctx.batch
             if gE is None:
@@ -356,7 +460,7 @@ def energy_forces_function():
             if gF is None:
                 gF = torch.zeros((3, batch.N), dtype=torch.float64, device=batch.device)
             nep.set_params(theta)
-            g = nep.batch_backward(batch, gE, gF)
+            g = nep.batch_backward(batch, gE, gF, gW)
             return g.to(theta.device, theta.dtype), None, None
 
     return NEPEnergyForces

@@ -206,3 +206,139 @@ def test_autotune_and_overflow_growth():
     np.testing.assert_allclose(g1.cpu().numpy(), g0.cpu().numpy(), rtol=1e-5,
                                atol=1e-7 * float(g0.abs().max()))
     nep.close()
+
+
+# ---------------------------------------------------------------------------
+# Virials: per-configuration virial, virial loss term and its gradient
+# ---------------------------------------------------------------------------
+
+def _oracle_W(model, structs):
+    from oracle import training as T
+    return T.evaluate(model, structs)[2]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_batch_virials_match_oracle(precision):
+    structs = I.c4(24, seed=21)
+    nep, b = _gpu(structs, precision)
+    E, F, W = nep.batch_forward(b, virials=True)
+    Wo = _oracle_W(I.nep_model(1), structs)
+    W = W.cpu().numpy()
+    tw = 2e-5 if precision == "fp32" else 1e-10
+    for c, s in enumerate(structs):
+        assert np.max(np.abs(W[c] - Wo[c])) / s.n <= tw, (c, W[c], Wo[c])
+    nep.close()
+
+
+def _virial_targets(structs, seed=22):
+    """Seed-101 model virials (six components) as targets, with a mask."""
+    from oracle import training as T
+    W6 = T.virial6(_oracle_W(I.nep_model(TARGET_SEED), structs))
+    hv = np.random.default_rng(seed).integers(0, 2, len(structs)).astype(np.uint8)
+    hv[0] = 1
+    return W6, hv
+
+
+def _oracle_mse(model, theta, structs, Et, Ft, W6t, hv, we, wf, wv):
+    from oracle import training as T
+    E, F, W = T.evaluate(model, structs, theta)
+    N = [s.n for s in structs]
+    return T.mse_loss(E, F, T.virial6(W), Et, Ft, W6t, N, hv, we, wf, wv)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_loss_with_virial_term_gradient_all_parameters_fd(precision):
+    """Energy + force + virial mean-square loss on a small batch with some
+    configurations lacking a virial target: loss terms against the oracle,
+    all 1051 gradient components against central differences of the oracle's
+    loss."""
+    import torch
+    structs = _small_configs(4, seed=23)
+    Et, Ft = _targets(structs)
+    W6t, hv = _virial_targets(structs)
+    model = I.nep_model(1)
+    nep, b = _gpu(structs, precision)
+    Etd, Ftd = _targets_dev(Et, Ft)
+    Wtd = torch.tensor(W6t, dtype=torch.float64, device="cuda")
+    we, wf, wv = 1.0, 1.0, 0.1
+    L, g, E, F = nep.batch_loss_grad(b, Etd, Ftd, we, wf, W_target=Wtd, has_virial=hv, w_virial=wv)
+    Lo, le, lf, lv = _oracle_mse(model, None, structs, Et, Ft, W6t, hv, we, wf, wv)
+    rel = 1e-10 if precision == "fp64" else 2e-5
+    assert L == pytest.approx(Lo, rel=rel)
+    assert nep.last_loss_terms["virial"] == pytest.approx(lv, rel=rel)
+    assert lv > 0.01 * Lo            # the virial term matters in this test
+    theta = model.params.copy()
+    fd = np.zeros(len(theta))
+    for k in range(len(theta)):
+        h = 1e-6 * max(1.0, abs(theta[k]))
+        tp = theta.copy(); tp[k] += h
+        tm = theta.copy(); tm[k] -= h
+        fd[k] = (_oracle_mse(model, tp, structs, Et, Ft, W6t, hv, we, wf, wv)[0]
+                 - _oracle_mse(model, tm, structs, Et, Ft, W6t, hv, we, wf, wv)[0]) / (2 * h)
+    g = g.cpu().numpy()
+    if precision == "fp64":
+        np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-9 * np.max(np.abs(fd)))
+    else:
+        assert np.linalg.norm(g - fd) / np.linalg.norm(fd) <= 1e-5
+    nep.close()
+
+
+def test_backward_with_virial_upstream():
+    """nep_batch_backward with random dL/dE, dL/dF and dL/dW equals the FD
+    derivative of sum_s c_s E_s + sum_i d_i . F_i + sum_s G_s : W_s."""
+    import torch
+    from oracle import training as T
+    structs = _small_configs(3, seed=24)
+    nep, b = _gpu(structs, "fp64")
+    rng = np.random.default_rng(25)
+    c = rng.normal(size=len(structs))
+    d = [rng.normal(size=(s.n, 3)) for s in structs]
+    G = rng.normal(size=(len(structs), 3, 3))
+    g = nep.batch_backward(b, torch.tensor(c, device="cuda"),
+                           torch.tensor(np.concatenate(d).T.copy(), device="cuda"),
+                           torch.tensor(G, device="cuda")).cpu().numpy()
+    model = I.nep_model(1)
+
+    def functional(theta):
+        E, F, W = T.evaluate(model, structs, theta)
+        return float(c @ E + sum(np.sum(di * fi) for di, fi in zip(d, F)) + np.sum(G * W))
+
+    # five-point differences with h = 1e-4: the virial sums thousands of pair
+    # terms of ~10 eV, so a 1e-6 step would leave ~1e-6 of rounding noise
+    th = model.params
+    for k in np.concatenate([np.arange(0, 900, 89), np.arange(900, 1051, 11)]):
+        h = 1e-4 * max(1.0, abs(th[k]))
+        f = []
+        for m in (-2, -1, 1, 2):
+            t = th.copy(); t[k] += m * h
+            f.append(functional(t))
+        fdk = (f[0] - 8 * f[1] + 8 * f[2] - f[3]) / (12 * h)
+        assert g[k] == pytest.approx(fdk, rel=1e-7, abs=1e-9 * max(1.0, np.max(np.abs(g))))
+    nep.close()
+
+
+def test_autograd_function_with_virials():
+    import torch
+    from paper_2305_08140_gb300 import nepzbl as N
+    structs = _small_configs(4, seed=26)
+    Et, Ft = _targets(structs)
+    W6t, hv = _virial_targets(structs, seed=27)
+    nep, b = _gpu(structs, "fp64")
+    Etd, Ftd = _targets_dev(Et, Ft)
+    Wtd = torch.tensor(W6t, dtype=torch.float64, device="cuda")
+    L_fused, g_fused, _, _ = nep.batch_loss_grad(b, Etd, Ftd, W_target=Wtd, has_virial=hv,
+                                                 w_virial=0.1)
+    fn = N.energy_forces_function(virials=True)
+    theta = torch.tensor(I.nep_model(1).params, dtype=torch.float64, requires_grad=True)
+    E, F, W = fn.apply(theta, nep, b)
+    Ns = torch.tensor([s.n for s in structs], dtype=torch.float64, device="cuda")
+    idx = [(0, 0), (1, 1), (2, 2), (1, 2), (2, 0), (0, 1)]
+    W6 = torch.stack([W[:, a, c] for a, c in idx], dim=1)
+    m = torch.tensor(hv, dtype=torch.bool, device="cuda")
+    lv = 0.1 * torch.mean(((W6 - Wtd)[m] / Ns[m, None]) ** 2)
+    loss = torch.mean(((E - Etd) / Ns) ** 2) + torch.mean((F - Ftd) ** 2) + lv
+    loss.backward()
+    assert loss.item() == pytest.approx(L_fused, rel=1e-12)
+    np.testing.assert_allclose(theta.grad.numpy(), g_fused.cpu().numpy(), rtol=1e-8,
+                               atol=1e-12 * float(g_fused.abs().max()))
+    nep.close()
