@@ -894,3 +894,178 @@ int orc_md(const int *ihp, const double *dhp, const double *params, const double
     }
     return err;
 }
+
+/* ---------------------------------------------------------------------------
+ * Cascade protocol pieces (Sec. II.B): a Nose-Hoover chain thermostat on a
+ * group of atoms (Martyna, Klein and Tuckerman 1992) and a Berendsen
+ * barostat for the NPT equilibration at a target pressure.
+ *
+ * One step of length dt (Trotter splitting, as in Martyna, Tuckerman, Tobias
+ * and Klein 1996, one Suzuki-Yoshida weight):
+ *   NHC(dt/2) ; v += dt/2 F/m ; x += dt v ; F(x) ; v += dt/2 F/m ; NHC(dt/2) ;
+ *   then, with a barostat, x_a *= mu_a and L_a *= mu_a for every periodic a,
+ *   mu_a = [1 - beta (dt / tau_p) (p0 - P_aa)]^(1/3),
+ *   P_aa = (sum_i m_i v_ia^2 + W_aa) / V   (W: the virial of the new positions).
+ * NHC(d) for the group g (N_f = 3 N_g, Q_1 = N_f kT tau^2, Q_j = kT tau^2,
+ * G_1 = (2 K_g - N_f kT) / Q_1, G_j = (Q_{j-1} v_{j-1}^2 - kT) / Q_j):
+ *   v_M += d/2 G_M;
+ *   for j = M-1..1: v_j *= e^{-d/4 v_{j+1}}; v_j += d/2 G_j; v_j *= e^{-d/4 v_{j+1}}
+ *   s = e^{-d v_1}: group velocities *= s, K_g *= s^2;  xi_j += d v_j
+ *   for j = 1..M-1: v_j *= e^{-d/4 v_{j+1}}; v_j += d/2 G_j; v_j *= e^{-d/4 v_{j+1}}
+ *   v_M += d/2 G_M
+ * (each G evaluated with the current values).  The thermostat energy
+ * sum_j Q_j v_j^2 / 2 + N_f kT xi_1 + kT sum_{j>1} xi_j makes
+ * PE + KE + E_NHC a constant of the motion.
+ * ------------------------------------------------------------------------- */
+
+#define ORC_KB 8.617333262e-5   /* eV/K */
+#define ORC_MAXCHAIN 8
+
+typedef struct {
+    int M;
+    double kT, Nf, Q[ORC_MAXCHAIN], v[ORC_MAXCHAIN], xi[ORC_MAXCHAIN];
+} orc_nhc;
+
+static double nhc_G(const orc_nhc *c, int j, double Kg)
+{
+    if (j == 0) return (2.0 * Kg - c->Nf * c->kT) / c->Q[0];
+    return (c->Q[j - 1] * c->v[j - 1] * c->v[j - 1] - c->kT) / c->Q[j];
+}
+
+static void nhc_sub(orc_nhc *c, int j, double d, double Kg)
+{
+    if (j + 1 < c->M) c->v[j] *= exp(-0.25 * d * c->v[j + 1]);
+    c->v[j] += 0.5 * d * nhc_G(c, j, Kg);
+    if (j + 1 < c->M) c->v[j] *= exp(-0.25 * d * c->v[j + 1]);
+}
+
+/* One NHC(d) sweep; returns the velocity scale of the group. */
+static double nhc_half(orc_nhc *c, double d, double Kg)
+{
+    const int M = c->M;
+    for (int j = M - 1; j >= 0; --j) nhc_sub(c, j, d, Kg);
+    const double s = exp(-d * c->v[0]);
+    Kg *= s * s;
+    for (int j = 0; j < M; ++j) c->xi[j] += d * c->v[j];
+    for (int j = 0; j < M; ++j) nhc_sub(c, j, d, Kg);
+    return s;
+}
+
+static double nhc_energy(const orc_nhc *c)
+{
+    double e = 0.0;
+    for (int j = 0; j < c->M; ++j) e += 0.5 * c->Q[j] * c->v[j] * c->v[j];
+    e += c->Nf * c->kT * c->xi[0];
+    for (int j = 1; j < c->M; ++j) e += c->kT * c->xi[j];
+    return e;
+}
+
+static double group_ke(int N, const double *vel, const int *types, const double *mass,
+                       const unsigned char *group)
+{
+    double k = 0.0;
+    for (int i = 0; i < N; ++i) {
+        if (group && !group[i]) continue;
+        const double mi = mass[types ? types[i] : 0];
+        for (int a = 0; a < 3; ++a) k += 0.5 * mi * vel[3 * i + a] * vel[3 * i + a] / ORC_EV_AMU;
+    }
+    return k;
+}
+
+/* Velocity Verlet with the optional thermostat and barostat above.
+ * ext = {T (K), tau (fs), chain length, p0 (eV/A^3), tau_p (fs), beta (A^3/eV)};
+ * the thermostat is on when thermostat != 0 (group: N flags, NULL = all
+ * atoms), the barostat when tau_p > 0.  box (3) is updated in place.
+ * thermo (nsteps x 8): t, dt, PE, KE, E_NHC, Lx, Ly, Lz after each step. */
+int orc_md_ext(const int *ihp, const double *dhp, const double *params, const double *scaler,
+               int N, double *pos, double *vel, double *F, int forces_valid, const int *types,
+               double *box, const int *pbc, const double *mass, double dt_max, double d_max,
+               int nsteps, int use_grid, int thermostat, const unsigned char *group,
+               const double *ext, double *thermo)
+{
+    orc_model m;
+    if (model_init(&m, ihp, dhp, params, scaler) || N < 0) return ORC_ERR_ARG;
+    for (int t = 0; t < m.T; ++t)
+        if (!(mass[t] > 0)) return ORC_ERR_ARG;
+    orc_sys S = {N, pos, {box[0], box[1], box[2]}, {pbc[0], pbc[1], pbc[2]}, types};
+    if (!types_valid(&S, m.T)) return ORC_ERR_ARG;
+    orc_nhc c;
+    memset(&c, 0, sizeof(c));
+    if (thermostat) {
+        c.M = (int)ext[2];
+        if (c.M < 1 || c.M > ORC_MAXCHAIN || !(ext[0] > 0) || !(ext[1] > 0)) return ORC_ERR_ARG;
+        int ng = 0;
+        for (int i = 0; i < N; ++i) ng += group ? (group[i] != 0) : 1;
+        c.kT = ORC_KB * ext[0];
+        c.Nf = 3.0 * ng;
+        c.Q[0] = (c.Nf > 0 ? c.Nf : 1.0) * c.kT * ext[1] * ext[1];
+        for (int j = 1; j < c.M; ++j) c.Q[j] = c.kT * ext[1] * ext[1];
+    }
+    const int baro = ext && ext[4] > 0;
+    double E, W[9];
+    int err = ORC_OK;
+    if (!forces_valid) err = efv(&m, &S, use_grid, &E, F, W, NULL, NULL);
+    double t = 0.0;
+    for (int step = 0; step < nsteps && !err; ++step) {
+        double dt = dt_max;
+        if (d_max > 0) {
+            double vmax = 0.0;
+            for (int i = 0; i < N; ++i) {
+                double v = sqrt(vel[3 * i] * vel[3 * i] + vel[3 * i + 1] * vel[3 * i + 1] +
+                                vel[3 * i + 2] * vel[3 * i + 2]);
+                if (v > vmax) vmax = v;
+            }
+            if (vmax > 0 && d_max / vmax < dt) dt = d_max / vmax;
+        }
+        if (thermostat) {
+            const double sc = nhc_half(&c, 0.5 * dt, group_ke(N, vel, types, mass, group));
+            for (int i = 0; i < N; ++i)
+                if (!group || group[i])
+                    for (int a = 0; a < 3; ++a) vel[3 * i + a] *= sc;
+        }
+        for (int i = 0; i < 3 * N; ++i) {
+            const double acc = ORC_EV_AMU / mass[sys_type(&S, i / 3)];
+            vel[i] += 0.5 * dt * F[i] * acc;
+            pos[i] += dt * vel[i];
+        }
+        for (int i = 0; i < N; ++i)
+            for (int a = 0; a < 3; ++a)
+                if (pbc[a]) pos[3 * i + a] -= S.box[a] * floor(pos[3 * i + a] / S.box[a]);
+        err = efv(&m, &S, use_grid, &E, F, W, NULL, NULL);
+        for (int i = 0; i < 3 * N; ++i)
+            vel[i] += 0.5 * dt * F[i] * (ORC_EV_AMU / mass[sys_type(&S, i / 3)]);
+        if (thermostat) {
+            const double sc = nhc_half(&c, 0.5 * dt, group_ke(N, vel, types, mass, group));
+            for (int i = 0; i < N; ++i)
+                if (!group || group[i])
+                    for (int a = 0; a < 3; ++a) vel[3 * i + a] *= sc;
+        }
+        double ke = 0.0, kab[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < N; ++i) {
+            const double mi = mass[sys_type(&S, i)];
+            for (int a = 0; a < 3; ++a) {
+                ke += 0.5 * mi * vel[3 * i + a] * vel[3 * i + a] / ORC_EV_AMU;
+                kab[a] += mi * vel[3 * i + a] * vel[3 * i + a] / ORC_EV_AMU;
+            }
+        }
+        t += dt;
+        if (baro && !err) {
+            const double V = S.box[0] * S.box[1] * S.box[2];
+            for (int a = 0; a < 3; ++a) {
+                if (!pbc[a]) continue;
+                const double P = (kab[a] + W[4 * a]) / V;
+                const double mu = cbrt(1.0 - ext[5] * (dt / ext[4]) * (ext[3] - P));
+                for (int i = 0; i < N; ++i) pos[3 * i + a] *= mu;
+                S.box[a] *= mu;
+                box[a] = S.box[a];
+            }
+        }
+        if (thermo) {
+            double *o = thermo + 8 * (size_t)step;
+            o[0] = t; o[1] = dt; o[2] = E; o[3] = ke;
+            o[4] = thermostat ? nhc_energy(&c) : 0.0;
+            o[5] = S.box[0]; o[6] = S.box[1]; o[7] = S.box[2];
+        }
+    }
+    return err;
+}

@@ -45,6 +45,9 @@ def lib():
                                         C.POINTER(C.c_int64), dp, dp]
         L.orc_md.argtypes = [ip, dp, dp, dp, C.c_int, dp, dp, dp, C.c_int, ip, dp, ip,
                              dp, C.c_double, C.c_double, C.c_int, C.c_int, dp]
+        L.orc_md_ext.argtypes = [ip, dp, dp, dp, C.c_int, dp, dp, dp, C.c_int, ip, dp, ip,
+                                 dp, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int,
+                                 C.POINTER(C.c_uint8), dp, dp]
         L.orc_site.argtypes = [ip, dp, dp, dp, C.c_int, C.c_int, dp, ip, C.c_int, dp, ip,
                                dp, dp, dp, dp]
         L.orc_neighbor_counts.argtypes = [C.c_int, dp, dp, ip, C.c_double, C.c_int, ip,
@@ -104,6 +107,10 @@ def _masses(model, mass):
     if m.size != model.n_types:
         raise ValueError("one mass per species")
     return np.ascontiguousarray(m)
+
+
+# 1 eV/amu in A^2/fs^2 (CODATA e and u)
+EV_PER_AMU = 1.602176634e-19 / 1.66053906660e-27 * 1e-10
 
 
 def _check(rc, what):
@@ -253,3 +260,60 @@ def fourbody_triple(g, u):
     g = _f64(g)
     u = _f64(np.reshape(u, (-1, 3)))
     return float(lib().orc_fourbody_triple(len(g), _d(g), _d(u)))
+
+
+# 1 eV/A^3 in GPa (CODATA e)
+EV_A3_GPA = 160.21766208
+
+
+def md_ext(model, pos, vel, box, pbc, mass, dt_max, nsteps, d_max=0.0, forces=None,
+           use_grid=True, types=None, thermostat=None, barostat=None):
+    """Velocity Verlet with a Nose-Hoover chain thermostat on a group and a
+    Berendsen barostat (``orc_md_ext``).  thermostat = dict(T (K), tau (fs),
+    chain, group (N bools) or None); barostat = dict(p0 (GPa), tau (fs), beta
+    (1/GPa)).  Returns (pos, vel, forces, thermo[nsteps, 8], box)."""
+    ihp, dhp = _hp(model)
+    p = _f64(model.params)
+    s = _f64(model.scaler)
+    pos = _f64(pos).copy()
+    vel = _f64(vel).copy()
+    box = _f64(box).copy()
+    n = pos.shape[0]
+    t = _types(types, n)
+    F = np.zeros((n, 3)) if forces is None else _f64(forces).copy()
+    thermo = np.zeros((nsteps, 8))
+    ext = np.zeros(6)
+    group = None
+    if thermostat is not None:
+        ext[0], ext[1], ext[2] = thermostat["T"], thermostat["tau"], thermostat.get("chain", 4)
+        if thermostat.get("group") is not None:
+            group = np.ascontiguousarray(thermostat["group"], dtype=np.uint8)
+    if barostat is not None:
+        ext[3] = barostat["p0"] / EV_A3_GPA
+        ext[4] = barostat["tau"]
+        ext[5] = barostat["beta"] * EV_A3_GPA
+    _check(lib().orc_md_ext(_i(ihp), _d(dhp), _d(p), _d(s), n, _d(pos), _d(vel), _d(F),
+                            0 if forces is None else 1, _i(t), _d(box),
+                            _i(np.ascontiguousarray(pbc, dtype=np.int32)), _d(_masses(model, mass)),
+                            float(dt_max), float(d_max), int(nsteps), int(use_grid),
+                            1 if thermostat is not None else 0,
+                            group.ctypes.data_as(C.POINTER(C.c_uint8)) if group is not None
+                            else None, _d(ext), _d(thermo)), "md_ext")
+    return pos, vel, F, thermo, box
+
+
+def pka_atom(pos, box, pbc, point):
+    """Index of the atom nearest to ``point`` (minimum image in periodic
+    dimensions; ties to the lowest index)."""
+    d = np.asarray(pos, dtype=np.float64) - np.asarray(point, dtype=np.float64)
+    box = np.asarray(box, dtype=np.float64)
+    per = np.asarray(pbc) > 0
+    d[:, per] -= box[per] * np.round(d[:, per] / box[per])
+    return int(np.argmin(np.einsum("ij,ij->i", d, d)))
+
+
+def pka_velocity(energy_ev, mass_amu, direction):
+    """Velocity (A/fs) of kinetic energy ``energy_ev`` along ``direction``."""
+    u = np.asarray(direction, dtype=np.float64)
+    u = u / np.linalg.norm(u)
+    return np.sqrt(2.0 * energy_ev / mass_amu * EV_PER_AMU) * u
