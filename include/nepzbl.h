@@ -150,14 +150,60 @@ typedef struct nep_md_state {
     double potential_energy;/* E after the last step (eV) */
     double kinetic_energy;  /* KE after the last step (eV) */
     double virial[9];       /* W after the last step (eV) */
+    double thermostat_energy;  /* energy of the Nose-Hoover chain after the last step
+                                  (eV; 0 without a thermostat): PE + KE + this is
+                                  conserved */
 } nep_md_state;
 
-/* Advances the state by n_steps velocity-Verlet NVE steps (Sec. II.B):
- *   v += dt/2 F/m; x += dt v; F = F(x); v += dt/2 F/m.
+/* Advances the state by n_steps velocity-Verlet steps (Sec. II.B):
+ *   v += dt/2 F/m; x += dt v; F = F(x); v += dt/2 F/m,
+ * NVE unless a thermostat and/or barostat is set (below).
  * Steps are replayed from captured CUDA graphs in chunks; if a chunk
  * overflows the neighbour capacity the chunk is rolled back from a device
- * copy, the capacity grows and the chunk runs again. */
+ * copy, the capacity grows and the chunk runs again.  With a barostat the box
+ * changes every step and the steps are launched directly (box read back after
+ * each step; state->box is updated). */
 int md_step(nep_ctx* ctx, nep_md_state* state, int n_steps, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Cascade protocol (Sec. II.B): the atoms within 3 a0 of the box boundaries
+ * are held at 300 K by a Nose-Hoover chain thermostat, the system is first
+ * equilibrated at 300 K and 0 GPa, and the PKA starts with its energy along
+ * <135>.
+ * --------------------------------------------------------------------------- */
+
+/* Nose-Hoover chain (Martyna, Klein and Tuckerman 1992) on a group of atoms,
+ * integrated by the Trotter splitting NHC(dt/2) Verlet NHC(dt/2) (Martyna,
+ * Tuckerman, Tobias and Klein 1996): N_f = 3 x group size, Q_1 = N_f k T tau^2,
+ * Q_j = k T tau^2.  The chain is set to rest by this call and persists across
+ * md_step calls. */
+typedef struct nep_thermostat {
+    double temperature;      /* K */
+    double tau;              /* fs */
+    int32_t chain_length;    /* 1..8 */
+    const uint8_t* group;    /* device uint8[n_atoms] of the MD state, 1 = thermostatted;
+                                NULL = every atom.  Read by later md_step calls. */
+} nep_thermostat;
+int nep_set_thermostat(nep_ctx* ctx, const nep_thermostat* t);   /* t == NULL: off */
+
+/* Berendsen barostat: after each step, for every periodic dimension a,
+ *   P_aa = (sum_i m_i v_ia^2 + W_aa) / V,
+ *   mu_a = [1 - compressibility (dt / tau) (pressure - P_aa)]^(1/3),
+ * and x_a, L_a are multiplied by mu_a (velocities unchanged); open
+ * dimensions keep their extent.  A Verlet skin is not used while it is on. */
+typedef struct nep_barostat {
+    double pressure;         /* target (GPa) */
+    double tau;              /* fs */
+    double compressibility;  /* 1/GPa */
+} nep_barostat;
+int nep_set_barostat(nep_ctx* ctx, const nep_barostat* b);   /* b == NULL: off */
+
+/* PKA launch: the atom nearest to point (A; minimum image in periodic
+ * dimensions, lowest index on ties) gets the velocity of kinetic energy
+ * `energy` (eV) along `direction` (any nonzero length; the paper uses
+ * <135>), replacing its velocity.  *atom receives its index.  Synchronous. */
+int nep_pka(nep_ctx* ctx, nep_md_state* state, const double point[3], double energy,
+            const double direction[3], int64_t* atom, void* stream);
 
 /* Counters of a context (for benchmarks and tests). */
 typedef struct nep_stats {

@@ -1415,9 +1415,14 @@ static __global__ void __launch_bounds__(256) k_reduce_partials(const double* __
 // ----------------------------------------------------------------------------
 
 // thermo layout (device doubles): [0] dt of the current step, [1] time,
-// [2] step count, [3] KE, [4] vmax, [5] dt_max, [6] d_max, [7] last dt
+// [2] step count, [3] KE, [4] vmax, [5] dt_max, [6] d_max, [7] last dt,
+// [8..10] sum_i m_i v_ia^2 (eV) for a = x, y, z, [11] thermostat scale of the
+// last chain sweep, [12] thermostat energy, [13..15] barostat scale mu_a
 constexpr int TH_DT = 0, TH_TIME = 1, TH_STEP = 2, TH_KE = 3, TH_VMAX = 4, TH_DTMAX = 5,
-              TH_DMAX = 6, TH_DTLAST = 7, TH_N = 8;
+              TH_DMAX = 6, TH_DTLAST = 7, TH_KXX = 8, TH_NHC_S = 11, TH_ENHC = 12,
+              TH_MU = 13, TH_N = 16;
+// per-block partials of k_kick_thermo: sum m v^2, max |v|^2, sum m v_x^2, v_y^2, v_z^2
+constexpr int KT_PART = 5;
 
 // Masses of the species: m[t] (amu) and acc[t] = (1 eV/amu in A^2/fs^2) / m[t].
 struct MassTab {
@@ -1463,7 +1468,7 @@ static __global__ void __launch_bounds__(256) k_kick_thermo(int n, MassTab mt,
                                                      double* __restrict__ part, int half_kick)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double v2 = 0.0, vm = 0.0;
+    double v2 = 0.0, vm = 0.0, va[3] = {0.0, 0.0, 0.0};
     if (i < n) {
         const int t = species_of(mt, types, i);
         const double acc = mt.acc[t];
@@ -1474,21 +1479,31 @@ static __global__ void __launch_bounds__(256) k_kick_thermo(int n, MassTab mt,
             double vv = v[o] + 0.5 * dt * acc * F[o];
             if (half_kick) v[o] = vv;
             vm += vv * vv;
+            va[a] = mt.m[t] * vv * vv;
         }
         v2 = mt.m[t] * vm;
     }
-    __shared__ double sh[2][8];
+    __shared__ double sh[KT_PART][8];
     for (int o = 16; o > 0; o >>= 1) {
         v2 += __shfl_xor_sync(0xffffffffu, v2, o);
         vm = fmax(vm, __shfl_xor_sync(0xffffffffu, vm, o));
+#pragma unroll
+        for (int a = 0; a < 3; ++a) va[a] += __shfl_xor_sync(0xffffffffu, va[a], o);
     }
-    if ((threadIdx.x & 31) == 0) { sh[0][threadIdx.x >> 5] = v2; sh[1][threadIdx.x >> 5] = vm; }
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][threadIdx.x >> 5] = v2;
+        sh[1][threadIdx.x >> 5] = vm;
+        for (int a = 0; a < 3; ++a) sh[2 + a][threadIdx.x >> 5] = va[a];
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int w = 0; w < 8; ++w) { a += sh[0][w]; b = fmax(b, sh[1][w]); }
-        part[2 * blockIdx.x] = a;
-        part[2 * blockIdx.x + 1] = b;
+        double r[KT_PART] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int w = 0; w < 8; ++w) {
+            r[0] += sh[0][w];
+            r[1] = fmax(r[1], sh[1][w]);
+            for (int a = 0; a < 3; ++a) r[2 + a] += sh[2 + a][w];
+        }
+        for (int c = 0; c < KT_PART; ++c) part[KT_PART * blockIdx.x + c] = r[c];
     }
 }
 
@@ -1500,23 +1515,27 @@ static __global__ void __launch_bounds__(256) k_thermo_step(const double* __rest
                                                      int advance, int* __restrict__ gate = nullptr)
 {
     if (gate && threadIdx.x == 0) *gate = 0;   // lists are current after this step
-    __shared__ double sa[256], sb[256];
-    double a = 0.0, b = 0.0;
+    __shared__ double sa[256], sb[256], sk[3][256];
+    double a = 0.0, b = 0.0, k3[3] = {0.0, 0.0, 0.0};
     for (int t = threadIdx.x; t < nb; t += blockDim.x) {
-        a += part[2 * t];
-        b = fmax(b, part[2 * t + 1]);
+        a += part[KT_PART * t];
+        b = fmax(b, part[KT_PART * t + 1]);
+        for (int c = 0; c < 3; ++c) k3[c] += part[KT_PART * t + 2 + c];
     }
     sa[threadIdx.x] = a;
     sb[threadIdx.x] = b;
+    for (int c = 0; c < 3; ++c) sk[c][threadIdx.x] = k3[c];
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) {
             sa[threadIdx.x] += sa[threadIdx.x + o];
             sb[threadIdx.x] = fmax(sb[threadIdx.x], sb[threadIdx.x + o]);
+            for (int c = 0; c < 3; ++c) sk[c][threadIdx.x] += sk[c][threadIdx.x + o];
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
+        for (int c = 0; c < 3; ++c) thermo[TH_KXX + c] = sk[c][0] / ev_amu;
         const double ke = 0.5 * sa[0] / ev_amu;
         const double vmax = sqrt(sb[0]);
         if (advance) {
@@ -1531,6 +1550,228 @@ static __global__ void __launch_bounds__(256) k_thermo_step(const double* __rest
         if (dmax > 0.0 && vmax > 0.0 && dmax / vmax < dt) dt = dmax / vmax;
         thermo[TH_DT] = dt;
     }
+}
+
+// ----------------------------------------------------------------------------
+// Cascade protocol pieces (Sec. II.B): Nose-Hoover chain thermostat on a
+// group of atoms, Berendsen barostat, PKA launch
+// ----------------------------------------------------------------------------
+
+constexpr int NHC_MAX = 8;
+// nhc state (device doubles): [0, 8) v_j, [8, 16) xi_j, [16] N_f (3 x group size)
+constexpr int NHC_V = 0, NHC_XI = 8, NHC_NF = 16, NHC_N = 17;
+
+struct NhcParams {
+    int M;          // chain length
+    double kT;      // eV
+    double tau2;    // tau^2 (fs^2): Q_1 = N_f kT tau^2, Q_j = kT tau^2
+};
+
+// 3 x the number of group atoms (group == nullptr: every atom).
+static __global__ void k_group_count(int n, const uint8_t* __restrict__ group,
+                                     double* __restrict__ nhc)
+{
+    __shared__ int sc[256];
+    int c = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) c += group ? (group[i] != 0) : 1;
+    sc[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sc[threadIdx.x] += sc[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) nhc[NHC_NF] = 3.0 * sc[0];
+}
+
+// Per-block sums of 1/2 m v^2 (eV) over the group.
+static __global__ void __launch_bounds__(256) k_group_ke(int n, MassTab mt,
+                                                        const int32_t* __restrict__ types,
+                                                        const uint8_t* __restrict__ group,
+                                                        const double* __restrict__ v,
+                                                        double ev_amu, double* __restrict__ part)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double k = 0.0;
+    if (i < n && (!group || group[i])) {
+        const double m = mt.m[species_of(mt, types, i)];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double vv = v[(size_t)a * n + i];
+            k += 0.5 * m * vv * vv / ev_amu;
+        }
+    }
+    __shared__ double sh[8];
+    for (int o = 16; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = k;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += sh[w];
+        part[blockIdx.x] = s;
+    }
+}
+
+// One chain sweep NHC(d), d = dt/2 (Martyna-Tuckerman-Tobias-Klein splitting):
+// reduces the group's kinetic energy, advances the chain, stores the group's
+// velocity scale in thermo[TH_NHC_S] and the thermostat energy in
+// thermo[TH_ENHC].  One block.
+static __global__ void __launch_bounds__(256) k_nhc_chain(const double* __restrict__ part, int nb,
+                                                         NhcParams np, double* __restrict__ nhc,
+                                                         double* __restrict__ thermo)
+{
+    __shared__ double sh[256];
+    double a = 0.0;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) a += part[t];
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    double Kg = sh[0];
+    const int M = np.M;
+    const double d = 0.5 * thermo[TH_DT];
+    const double Nf = nhc[NHC_NF];
+    double Q[NHC_MAX], v[NHC_MAX];
+    for (int j = 0; j < M; ++j) {
+        Q[j] = (j == 0 ? (Nf > 0.0 ? Nf : 1.0) : 1.0) * np.kT * np.tau2;
+        v[j] = nhc[NHC_V + j];
+    }
+    auto G = [&](int j) {
+        return j == 0 ? (2.0 * Kg - Nf * np.kT) / Q[0]
+                      : (Q[j - 1] * v[j - 1] * v[j - 1] - np.kT) / Q[j];
+    };
+    auto sub = [&](int j) {
+        if (j + 1 < M) v[j] *= exp(-0.25 * d * v[j + 1]);
+        v[j] += 0.5 * d * G(j);
+        if (j + 1 < M) v[j] *= exp(-0.25 * d * v[j + 1]);
+    };
+    for (int j = M - 1; j >= 0; --j) sub(j);
+    const double s = exp(-d * v[0]);
+    Kg *= s * s;
+    for (int j = 0; j < M; ++j) nhc[NHC_XI + j] += d * v[j];
+    for (int j = 0; j < M; ++j) sub(j);
+    double e = 0.0;
+    for (int j = 0; j < M; ++j) {
+        nhc[NHC_V + j] = v[j];
+        e += 0.5 * Q[j] * v[j] * v[j];
+    }
+    e += Nf * np.kT * nhc[NHC_XI];
+    for (int j = 1; j < M; ++j) e += np.kT * nhc[NHC_XI + j];
+    thermo[TH_NHC_S] = s;
+    thermo[TH_ENHC] = e;
+}
+
+// Group velocities *= thermo[TH_NHC_S].
+static __global__ void k_group_scale(int n, const uint8_t* __restrict__ group,
+                                     const double* __restrict__ thermo, double* __restrict__ v)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || (group && !group[i])) return;
+    const double s = thermo[TH_NHC_S];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) v[(size_t)a * n + i] *= s;
+}
+
+// Berendsen barostat (one thread): with P_aa = (sum m v_a^2 + W_aa) / V,
+// mu_a = [1 - beta (dt / tau_p) (p0 - P_aa)]^(1/3) for periodic a, 1 otherwise;
+// box[a] *= mu_a.  result = (E, W[9]) of the current positions.
+static __global__ void k_barostat(const double* __restrict__ result, double* __restrict__ thermo,
+                                  double* __restrict__ box, int3 pbc, double p0, double tau_p,
+                                  double beta)
+{
+    if (threadIdx.x != 0) return;
+    const double V = box[0] * box[1] * box[2];
+    const int per[3] = {pbc.x, pbc.y, pbc.z};
+    const double dt = thermo[TH_DT];
+    for (int a = 0; a < 3; ++a) {
+        double mu = 1.0;
+        if (per[a]) {
+            const double P = (thermo[TH_KXX + a] + result[1 + 4 * a]) / V;
+            mu = cbrt(1.0 - beta * (dt / tau_p) * (p0 - P));
+        }
+        thermo[TH_MU + a] = mu;
+    }
+    for (int a = 0; a < 3; ++a) box[a] *= thermo[TH_MU + a];
+}
+
+// x_a *= mu_a.
+static __global__ void k_scale_positions(int n, const double* __restrict__ thermo,
+                                         double* __restrict__ x)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[(size_t)a * n + i] *= thermo[TH_MU + a];
+}
+
+// PKA: per-block nearest atom to p (minimum image in periodic dimensions),
+// ties to the lowest index; out[2 * b] = d^2, out[2 * b + 1] = index.
+static __global__ void __launch_bounds__(256) k_nearest(int n, const double* __restrict__ x,
+                                                       double3 p, double3 L, int3 pbc,
+                                                       double* __restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double best = 1e300;
+    int bi = n;
+    if (i < n) {
+        const double c[3] = {p.x, p.y, p.z}, Lb[3] = {L.x, L.y, L.z};
+        const int per[3] = {pbc.x, pbc.y, pbc.z};
+        double r2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            double d = x[(size_t)a * n + i] - c[a];
+            if (per[a]) d -= Lb[a] * rint(d / Lb[a]);
+            r2 += d * d;
+        }
+        best = r2;
+        bi = i;
+    }
+    __shared__ double sd[256];
+    __shared__ int si[256];
+    sd[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            const double d2 = sd[threadIdx.x + o];
+            const int i2 = si[threadIdx.x + o];
+            if (d2 < sd[threadIdx.x] || (d2 == sd[threadIdx.x] && i2 < si[threadIdx.x])) {
+                sd[threadIdx.x] = d2;
+                si[threadIdx.x] = i2;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[2 * blockIdx.x] = sd[0];
+        out[2 * blockIdx.x + 1] = (double)si[0];
+    }
+}
+
+// Picks the nearest atom from the block results (fixed order) and gives it
+// the velocity of kinetic energy e (eV) along the unit vector u:
+// |v| = sqrt(2 e / m); result index in *atom.
+static __global__ void k_pka_set(const double* __restrict__ part, int nb, int n, MassTab mt,
+                                 const int32_t* __restrict__ types, double e, double3 u,
+                                 double ev_amu, double* __restrict__ v,
+                                 long long* __restrict__ atom)
+{
+    if (threadIdx.x != 0) return;
+    double best = 1e300;
+    int bi = n;
+    for (int b = 0; b < nb; ++b) {
+        const double d2 = part[2 * b];
+        const int i2 = (int)part[2 * b + 1];
+        if (d2 < best || (d2 == best && i2 < bi)) { best = d2; bi = i2; }
+    }
+    *atom = bi;
+    if (bi >= n) return;
+    const double m = mt.m[species_of(mt, types, bi)];
+    const double sp = sqrt(2.0 * e / m * ev_amu);
+    v[bi] = sp * u.x;
+    v[(size_t)n + bi] = sp * u.y;
+    v[2 * (size_t)n + bi] = sp * u.z;
 }
 
 }  // namespace nepk

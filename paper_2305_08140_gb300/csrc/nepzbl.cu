@@ -26,6 +26,9 @@ namespace {
 constexpr double COULOMB_EV_A = 14.39964547;
 // 1 eV/amu in A^2/fs^2
 constexpr double EV_AMU = 1.602176634e-19 / 1.66053906660e-27 * 1e-10;
+// Boltzmann constant (eV/K) and 1 eV/A^3 in GPa (CODATA)
+constexpr double KB_EV = 8.617333262e-5;
+constexpr double EV_A3_GPA = 160.21766208;
 // longest neighbour list (slots) the force kernel stages in shared memory
 constexpr int STAGE_MAX_SLOTS = 112;
 
@@ -99,6 +102,19 @@ struct nep_ctx {
     int capture_kernels = 0;
     int capture_timed = 0;
     int nep_smem_set[4] = {0, 0, 0, 0};
+    // Nose-Hoover chain thermostat on a group, Berendsen barostat (MD)
+    int nhc_on = 0;
+    NhcParams nhc_p;
+    const uint8_t* nhc_group = nullptr;   // caller's device flags (nullptr: all atoms)
+    double* nhc = nullptr;                // device state [NHC_N]
+    double* nhc_backup = nullptr;
+    int nhc_counted = -1;                 // atom count the group size was taken for
+    int baro_on = 0;
+    double baro_p0 = 0.0, baro_tau = 0.0, baro_beta = 0.0;   // eV/A^3, fs, A^3/eV
+    double* d_box = nullptr;              // device box lengths [3]
+    double* pka_part = nullptr;           // [2 * blocks] nearest-atom search
+    long long* pka_atom = nullptr;
+    size_t pka_cap = 0;
     // Verlet skin for MD (0: rebuild every step)
     double skin = 0.0;
     double* xref = nullptr;          // positions at the last list build (3 x ld)
@@ -216,7 +232,7 @@ static int ensure_atoms(nep_ctx* ctx, int n, int M)
     CK(cudaMalloc(&ctx->qr, rsz * NR * (size_t)ld));
     CK(cudaMalloc(&ctx->br, rsz * 12 * (size_t)ctx->ntypes * ld));
     CK(cudaMalloc(&ctx->partials2, sizeof(double) * NPART * (size_t)RED1_MAX));
-    CK(cudaMalloc(&ctx->vpart, sizeof(double) * 2 * (size_t)vb));
+    CK(cudaMalloc(&ctx->vpart, sizeof(double) * KT_PART * (size_t)vb));
     CK(cudaMalloc(&ctx->backup, sizeof(double) * 9 * (size_t)ld));
     CK(cudaMalloc(&ctx->xref, sizeof(double) * 3 * (size_t)ld));
     if (ctx->skin > 0.0) {
@@ -704,6 +720,8 @@ void nep_free(nep_ctx* ctx)
     free_dev(ctx->coef_f); free_dev(ctx->coef_d); free_dev(ctx->b_hv);
     free_dev(ctx->p_thetas); free_dev(ctx->p_models); free_dev(ctx->p_out); free_dev(ctx->p_util);
     free_dev(ctx->d_scaler);
+    free_dev(ctx->nhc); free_dev(ctx->nhc_backup); free_dev(ctx->d_box); free_dev(ctx->pka_part);
+    free_dev(ctx->pka_atom);
     if (ctx->h_result) cudaFreeHost(ctx->h_result);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->h_pairs) cudaFreeHost(ctx->h_pairs);
@@ -850,6 +868,47 @@ int nep_compute(nep_ctx* ctx, int64_t n_atoms, const double* xyz, const double b
     return NEP_OK;
 }
 
+// One chain sweep NHC(dt/2) of the thermostatted group (3 kernels).
+static void enqueue_nhc(nep_ctx* ctx, int n, const int32_t* types, double* vel, cudaStream_t s)
+{
+    const int tb = 256, nb = (n + tb - 1) / tb;
+    k_group_ke<<<nb, tb, 0, s>>>(n, ctx->mt, types, ctx->nhc_group, vel, EV_AMU, ctx->vpart);
+    count_launch(ctx);
+    k_nhc_chain<<<1, 256, 0, s>>>(ctx->vpart, nb, ctx->nhc_p, ctx->nhc, ctx->thermo);
+    count_launch(ctx);
+    k_group_scale<<<nb, tb, 0, s>>>(n, ctx->nhc_group, ctx->thermo, vel);
+    count_launch(ctx);
+}
+
+// One velocity-Verlet step on stream s:
+//   [NHC(dt/2)] v += dt/2 F/m, x += dt v; F(x); v += dt/2 F/m [NHC(dt/2)];
+//   kinetic energy, max |v| and the next dt.
+static int enqueue_step(nep_ctx* ctx, const Grid& g, nep_md_state* st, cudaStream_t s, int slot)
+{
+    const int n = g.n;
+    const int tb = 256, nb = (n + tb - 1) / tb;
+    if (ctx->nhc_on) enqueue_nhc(ctx, n, st->types, st->vel, s);
+    k_kick_drift<<<nb, tb, 0, s>>>(g, ctx->mt, st->types, ctx->thermo, st->xyz, st->vel,
+                                   st->forces);
+    count_launch(ctx);
+    int* gate = ctx->skin > 0.0 && !ctx->baro_on ? ctx->gate : nullptr;
+    int rc = eval(ctx, g, st->xyz, st->types, st->forces, nullptr, s, slot, gate);
+    if (rc) return rc;
+    k_kick_thermo<<<nb, tb, 0, s>>>(n, ctx->mt, st->types, ctx->thermo, st->vel, st->forces,
+                                    ctx->vpart, 1);
+    count_launch(ctx);
+    if (ctx->nhc_on) {
+        enqueue_nhc(ctx, n, st->types, st->vel, s);
+        // kinetic energy and speeds after the thermostat's scaling
+        k_kick_thermo<<<nb, tb, 0, s>>>(n, ctx->mt, st->types, ctx->thermo, st->vel, st->forces,
+                                        ctx->vpart, 0);
+        count_launch(ctx);
+    }
+    k_thermo_step<<<1, 256, 0, s>>>(ctx->vpart, nb, EV_AMU, ctx->thermo, 1, gate);
+    count_launch(ctx);
+    return NEP_OK;
+}
+
 // Captures `steps` MD steps into a graph (on the context's capture stream).
 static int capture_steps(nep_ctx* ctx, const Grid& g, nep_md_state* st, int steps, GraphEntry& ge)
 {
@@ -864,19 +923,9 @@ static int capture_steps(nep_ctx* ctx, const Grid& g, nep_md_state* st, int step
     ctx->capture_kernels = 0;
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     int rc = NEP_OK;
-    for (int t = 0; t < steps && !rc; ++t) {
-        k_kick_drift<<<nb, tb, 0, cs>>>(g, ctx->mt, st->types, ctx->thermo, st->xyz, st->vel,
-                                        st->forces);
-        count_launch(ctx);
-        int* gate = ctx->skin > 0.0 ? ctx->gate : nullptr;
-        rc = eval(ctx, g, st->xyz, st->types, st->forces, nullptr, cs, ctx->timing ? t : -1, gate);
-        if (rc) break;
-        k_kick_thermo<<<nb, tb, 0, cs>>>(n, ctx->mt, st->types, ctx->thermo, st->vel, st->forces,
-                                         ctx->vpart, 1);
-        count_launch(ctx);
-        k_thermo_step<<<1, 256, 0, cs>>>(ctx->vpart, nb, EV_AMU, ctx->thermo, 1, gate);
-        count_launch(ctx);
-    }
+    (void)n;
+    (void)nb;
+    for (int t = 0; t < steps && !rc; ++t) rc = enqueue_step(ctx, g, st, cs, ctx->timing ? t : -1);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &graph);
     ctx->capturing = false;
@@ -893,6 +942,80 @@ static int capture_steps(nep_ctx* ctx, const Grid& g, nep_md_state* st, int step
     ge.steps = steps;
     return NEP_OK;
 }
+
+}  // extern "C"
+
+// MD steps with the Berendsen barostat: the box changes every step, so the
+// steps are launched directly (no graph): one step, the barostat scale
+// mu_a (device), x_a *= mu_a, then the new box is read back to lay the next
+// step's cell grid.  A neighbour overflow restores the step's start, grows
+// the capacity and repeats the step.
+static int md_steps_barostat(nep_ctx* ctx, nep_md_state* st, int n_steps, cudaStream_t s)
+{
+    const int64_t n = st->n_atoms;
+    const size_t bytes = sizeof(double) * 3 * (size_t)n;
+    double h_box[3] = {st->box[0], st->box[4], st->box[8]};
+    CK(cudaMemcpyAsync(ctx->d_box, h_box, sizeof(h_box), cudaMemcpyHostToDevice, s));
+    const int3 pbc = make_int3(st->pbc[0] ? 1 : 0, st->pbc[1] ? 1 : 0, st->pbc[2] ? 1 : 0);
+    int retries = 0;
+    for (int step = 0; step < n_steps;) {
+        Grid g;
+        int rc = make_grid(ctx, n, st->box, st->pbc, g);
+        if (rc) return rc;
+        if ((rc = ensure_cells(ctx, g.nc[0] * g.nc[1] * g.nc[2]))) return rc;
+        if ((rc = ensure_atoms(ctx, (int)n, ctx->M > 0 ? ctx->M : 96))) return rc;
+        CK(cudaMemcpyAsync(ctx->backup, st->xyz, bytes, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(ctx->backup + 3 * n, st->vel, bytes, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(ctx->backup + 6 * n, st->forces, bytes, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(ctx->thermo_backup, ctx->thermo, sizeof(double) * TH_N,
+                           cudaMemcpyDeviceToDevice, s));
+        if (ctx->nhc_on)
+            CK(cudaMemcpyAsync(ctx->nhc_backup, ctx->nhc, sizeof(double) * NHC_N,
+                               cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemsetAsync(ctx->status, 0, sizeof(int) * 3, s));
+        g.ld = ctx->ld;
+        g.M = ctx->M;
+        if ((rc = enqueue_step(ctx, g, st, s, -1))) return rc;
+        k_barostat<<<1, 32, 0, s>>>(ctx->result, ctx->thermo, ctx->d_box, pbc, ctx->baro_p0,
+                                    ctx->baro_tau, ctx->baro_beta);
+        count_launch(ctx);
+        const int tb = 256;
+        k_scale_positions<<<(int)((n + tb - 1) / tb), tb, 0, s>>>((int)n, ctx->thermo, st->xyz);
+        count_launch(ctx);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(h_box, ctx->d_box, sizeof(h_box), cudaMemcpyDeviceToHost, s));
+        rc = readback(ctx, s);
+        if (rc) return rc;
+        if (ctx->h_status[0] & ST_BADTYPE)
+            return fail(ctx, NEP_ERR_INVALID_ARG, "species index out of range [0, %d)",
+                        ctx->ntypes);
+        if (ctx->h_status[0] & ST_OVERFLOW) {
+            if (++retries > 4) return fail(ctx, NEP_ERR_NBR_OVERFLOW, "neighbour overflow persists");
+            CK(cudaMemcpyAsync(st->xyz, ctx->backup, bytes, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(st->vel, ctx->backup + 3 * n, bytes, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(st->forces, ctx->backup + 6 * n, bytes, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(ctx->thermo, ctx->thermo_backup, sizeof(double) * TH_N,
+                               cudaMemcpyDeviceToDevice, s));
+            if (ctx->nhc_on)
+                CK(cudaMemcpyAsync(ctx->nhc, ctx->nhc_backup, sizeof(double) * NHC_N,
+                                   cudaMemcpyDeviceToDevice, s));
+            h_box[0] = st->box[0]; h_box[1] = st->box[4]; h_box[2] = st->box[8];
+            CK(cudaMemcpyAsync(ctx->d_box, h_box, sizeof(h_box), cudaMemcpyHostToDevice, s));
+            CK(cudaStreamSynchronize(s));
+            if ((rc = ensure_atoms(ctx, (int)n, grown_capacity(ctx->h_status[1])))) return rc;
+            continue;
+        }
+        if (ctx->h_status[0] & ST_NONFINITE)
+            return fail(ctx, NEP_ERR_NONFINITE, "non-finite values during MD");
+        st->box[0] = h_box[0];
+        st->box[4] = h_box[1];
+        st->box[8] = h_box[2];
+        ++step;
+    }
+    return NEP_OK;
+}
+
+extern "C" {
 
 int md_step(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
 {
@@ -957,9 +1080,19 @@ int md_step(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
         count_launch(ctx);
         k_thermo_step<<<1, 256, 0, s>>>(ctx->vpart, nb, EV_AMU, ctx->thermo, 0);
         count_launch(ctx);
+        if (ctx->nhc_on && ctx->nhc_counted != (int)n) {
+            k_group_count<<<1, 256, 0, s>>>((int)n, ctx->nhc_group, ctx->nhc);
+            count_launch(ctx);
+            ctx->nhc_counted = (int)n;
+        }
         CK(cudaGetLastError());
     }
-    int done = 0;
+    if (ctx->baro_on) {
+        rc = md_steps_barostat(ctx, st, n_steps, s);
+        if (rc) return rc;
+        n_steps = n_steps > 0 ? n_steps : 0;
+    }
+    int done = ctx->baro_on ? n_steps : 0;
     int retries = 0;
     bool force_rebuild = true;   // the caller may have moved atoms since the last call
     while (done < n_steps) {
@@ -978,6 +1111,9 @@ int md_step(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
         CK(cudaMemcpyAsync(ctx->backup + 6 * n, st->forces, bytes, cudaMemcpyDeviceToDevice, s));
         CK(cudaMemcpyAsync(ctx->thermo_backup, ctx->thermo, sizeof(double) * TH_N,
                            cudaMemcpyDeviceToDevice, s));
+        if (ctx->nhc_on)
+            CK(cudaMemcpyAsync(ctx->nhc_backup, ctx->nhc, sizeof(double) * NHC_N,
+                               cudaMemcpyDeviceToDevice, s));
         CK(cudaMemsetAsync(ctx->status, 0, sizeof(int) * 3, s));
         if (ctx->skin > 0.0 && force_rebuild) {
             const int one = 1;
@@ -998,6 +1134,9 @@ int md_step(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
             CK(cudaMemcpyAsync(st->forces, ctx->backup + 6 * n, bytes, cudaMemcpyDeviceToDevice, s));
             CK(cudaMemcpyAsync(ctx->thermo, ctx->thermo_backup, sizeof(double) * TH_N,
                                cudaMemcpyDeviceToDevice, s));
+            if (ctx->nhc_on)
+                CK(cudaMemcpyAsync(ctx->nhc, ctx->nhc_backup, sizeof(double) * NHC_N,
+                                   cudaMemcpyDeviceToDevice, s));
             CK(cudaStreamSynchronize(s));
             rc = ensure_atoms(ctx, (int)n, grown_capacity(ctx->h_status[1]));
             if (rc) return rc;
@@ -1017,6 +1156,7 @@ int md_step(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
     st->step = (int64_t)llround(th2[TH_STEP]);
     st->dt_last = th2[TH_DTLAST];
     st->kinetic_energy = th2[TH_KE];
+    st->thermostat_energy = ctx->nhc_on ? th2[TH_ENHC] : 0.0;
     if (n_steps > 0) {
         st->potential_energy = ctx->h_result[0];
         for (int t = 0; t < 9; ++t) st->virial[t] = ctx->h_result[1 + t];
@@ -1632,3 +1772,103 @@ extern "C" int nep_compute_static(const nep_params* p, int64_t n_atoms, const do
     if (virial) for (int t = 0; t < 9; ++t) virial[t] = res[1 + t];
     return NEP_OK;
 }
+
+// ============================================================================
+// Cascade protocol pieces: thermostat, barostat, PKA launch
+// ============================================================================
+
+extern "C" {
+
+int nep_set_thermostat(nep_ctx* ctx, const nep_thermostat* t)
+{
+    if (!ctx) return NEP_ERR_INVALID_ARG;
+    drop_graphs(ctx);
+    if (!t) {
+        ctx->nhc_on = 0;
+        return NEP_OK;
+    }
+    if (!(t->temperature > 0) || !(t->tau > 0) || !isfinite(t->temperature) || !isfinite(t->tau) ||
+        t->chain_length < 1 || t->chain_length > NHC_MAX)
+        return fail(ctx, NEP_ERR_INVALID_ARG, "thermostat needs T > 0, tau > 0, chain 1..%d",
+                    NHC_MAX);
+    int rc;
+    if (t->group && (rc = check_device_ptr(ctx, t->group, "thermostat group"))) return rc;
+    if (!ctx->nhc) {
+        CK(cudaMalloc(&ctx->nhc, sizeof(double) * NHC_N));
+        CK(cudaMalloc(&ctx->nhc_backup, sizeof(double) * NHC_N));
+    }
+    CK(cudaMemset(ctx->nhc, 0, sizeof(double) * NHC_N));   // chain at rest
+    ctx->nhc_p.M = t->chain_length;
+    ctx->nhc_p.kT = KB_EV * t->temperature;
+    ctx->nhc_p.tau2 = t->tau * t->tau;
+    ctx->nhc_group = t->group;
+    ctx->nhc_counted = -1;
+    ctx->nhc_on = 1;
+    return NEP_OK;
+}
+
+int nep_set_barostat(nep_ctx* ctx, const nep_barostat* b)
+{
+    if (!ctx) return NEP_ERR_INVALID_ARG;
+    drop_graphs(ctx);
+    if (!b) {
+        ctx->baro_on = 0;
+        return NEP_OK;
+    }
+    if (!isfinite(b->pressure) || !(b->tau > 0) || !isfinite(b->tau) ||
+        !(b->compressibility >= 0) || !isfinite(b->compressibility))
+        return fail(ctx, NEP_ERR_INVALID_ARG, "barostat needs a finite pressure, tau > 0, "
+                                              "compressibility >= 0");
+    if (!ctx->d_box) CK(cudaMalloc(&ctx->d_box, sizeof(double) * 3));
+    ctx->baro_p0 = b->pressure / EV_A3_GPA;
+    ctx->baro_tau = b->tau;
+    ctx->baro_beta = b->compressibility * EV_A3_GPA;
+    ctx->baro_on = 1;
+    return NEP_OK;
+}
+
+int nep_pka(nep_ctx* ctx, nep_md_state* st, const double point[3], double energy,
+            const double direction[3], int64_t* atom, void* stream)
+{
+    if (!ctx) return NEP_ERR_INVALID_ARG;
+    if (!st || !point || !direction || !atom) return fail(ctx, NEP_ERR_INVALID_ARG, "NULL argument");
+    const int64_t n = st->n_atoms;
+    if (n <= 0 || n >= (1 << 26)) return fail(ctx, NEP_ERR_INVALID_ARG, "n_atoms must be in [1, 2^26)");
+    const double un = sqrt(direction[0] * direction[0] + direction[1] * direction[1] +
+                           direction[2] * direction[2]);
+    if (!(energy >= 0) || !isfinite(energy) || !(un > 0) || !isfinite(un))
+        return fail(ctx, NEP_ERR_INVALID_ARG, "PKA needs energy >= 0 and a nonzero direction");
+    int rc;
+    if ((rc = check_device_ptr(ctx, st->xyz, "xyz")) || (rc = check_device_ptr(ctx, st->vel, "vel")) ||
+        (rc = check_device_ptr(ctx, st->types, "types")))
+        return rc;
+    for (int a = 0; a < 3; ++a)
+        if (!(st->box[4 * a] > 0) || !isfinite(point[a]))
+            return fail(ctx, NEP_ERR_INVALID_ARG, "bad box or point");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int tb = 256, nb = (int)((n + tb - 1) / tb);
+    const size_t need = sizeof(double) * 2 * (size_t)nb;
+    if (need > ctx->pka_cap) {
+        CK(cudaStreamSynchronize(s));
+        free_dev(ctx->pka_part);
+        CK(cudaMalloc(&ctx->pka_part, need));
+        ctx->pka_cap = need;
+    }
+    if (!ctx->pka_atom) CK(cudaMalloc(&ctx->pka_atom, sizeof(long long)));
+    k_nearest<<<nb, tb, 0, s>>>((int)n, st->xyz, make_double3(point[0], point[1], point[2]),
+                                make_double3(st->box[0], st->box[4], st->box[8]),
+                                make_int3(st->pbc[0] ? 1 : 0, st->pbc[1] ? 1 : 0, st->pbc[2] ? 1 : 0),
+                                ctx->pka_part);
+    k_pka_set<<<1, 32, 0, s>>>(ctx->pka_part, nb, (int)n, ctx->mt, st->types, energy,
+                               make_double3(direction[0] / un, direction[1] / un, direction[2] / un),
+                               EV_AMU, st->vel, ctx->pka_atom);
+    ctx->launches += 2;
+    CK(cudaGetLastError());
+    long long a = 0;
+    CK(cudaMemcpyAsync(&a, ctx->pka_atom, sizeof(a), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *atom = a;
+    return NEP_OK;
+}
+
+}  // extern "C"

@@ -32,7 +32,8 @@ NEP_OPT_SKIN_MILLIANGSTROM = 4
 EXPORTED = ("nep_init", "nep_free", "nep_last_error", "nep_compute", "md_step",
             "nep_get_stats", "nep_set_option", "nep_reset_stats", "nep_compute_static",
             "nep_set_params", "nep_batch_forward", "nep_batch_backward", "nep_batch_loss_grad",
-            "nep_batch_autotune", "nep_population_loss", "nep_snes_generation")
+            "nep_batch_autotune", "nep_population_loss", "nep_snes_generation",
+            "nep_set_thermostat", "nep_set_barostat", "nep_pka")
 
 
 class NepParams(C.Structure):
@@ -52,7 +53,17 @@ class NepMdState(C.Structure):
                 ("pbc", C.c_int32 * 3), ("forces_valid", C.c_int32), ("dt_max", C.c_double),
                 ("d_max", C.c_double), ("time", C.c_double), ("step", C.c_int64),
                 ("dt_last", C.c_double), ("potential_energy", C.c_double),
-                ("kinetic_energy", C.c_double), ("virial", C.c_double * 9)]
+                ("kinetic_energy", C.c_double), ("virial", C.c_double * 9),
+                ("thermostat_energy", C.c_double)]
+
+
+class NepThermostat(C.Structure):
+    _fields_ = [("temperature", C.c_double), ("tau", C.c_double), ("chain_length", C.c_int32),
+                ("group", C.c_void_p)]
+
+
+class NepBarostat(C.Structure):
+    _fields_ = [("pressure", C.c_double), ("tau", C.c_double), ("compressibility", C.c_double)]
 
 
 class NepStats(C.Structure):
@@ -131,6 +142,13 @@ def load(build: bool = True):
     L.nep_batch_loss_grad.argtypes = [vp, bp, tp, wp, C.POINTER(C.c_double), vp, vp, vp, vp, vp]
     L.nep_batch_loss_grad.restype = C.c_int
     L.nep_batch_autotune.argtypes = [vp, bp, tp, wp, vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.nep_set_thermostat.argtypes = [vp, C.POINTER(NepThermostat)]
+    L.nep_set_thermostat.restype = C.c_int
+    L.nep_set_barostat.argtypes = [vp, C.POINTER(NepBarostat)]
+    L.nep_set_barostat.restype = C.c_int
+    L.nep_pka.argtypes = [vp, C.POINTER(NepMdState), C.POINTER(C.c_double), C.c_double,
+                          C.POINTER(C.c_double), C.POINTER(C.c_int64), vp]
+    L.nep_pka.restype = C.c_int
     L.nep_population_loss.argtypes = [vp, bp, tp, wp, C.c_int, vp, vp, vp]
     L.nep_population_loss.restype = C.c_int
     L.nep_snes_generation.argtypes = [vp, bp, tp, wp, C.c_int, vp, vp, vp, C.c_double, C.c_double,
@@ -245,6 +263,36 @@ class NEP:
     def md(self, state: "MDState", n_steps: int, stream=None):
         self._check(self.lib.md_step(self.ctx, C.byref(state.c), int(n_steps), _stream_ptr(stream)))
         return state
+
+    def set_thermostat(self, temperature=None, tau=100.0, chain=4, group=None):
+        """Nose-Hoover chain on the atoms flagged in ``group`` (CUDA uint8
+        tensor, kept alive here; None = every atom); temperature None: off."""
+        if temperature is None:
+            self._check(self.lib.nep_set_thermostat(self.ctx, None))
+            self._group = None
+            return
+        t = NepThermostat(float(temperature), float(tau), int(chain),
+                          group.data_ptr() if group is not None else None)
+        self._group = group
+        self._check(self.lib.nep_set_thermostat(self.ctx, C.byref(t)))
+
+    def set_barostat(self, pressure=None, tau=1000.0, compressibility=0.003):
+        """Berendsen barostat (GPa, fs, 1/GPa); pressure None: off."""
+        if pressure is None:
+            self._check(self.lib.nep_set_barostat(self.ctx, None))
+            return
+        b = NepBarostat(float(pressure), float(tau), float(compressibility))
+        self._check(self.lib.nep_set_barostat(self.ctx, C.byref(b)))
+
+    def pka(self, state: "MDState", point, energy, direction=(1.0, 3.0, 5.0), stream=None):
+        """Gives the atom nearest to ``point`` kinetic energy ``energy`` (eV)
+        along ``direction``; returns its index."""
+        p = (C.c_double * 3)(*[float(v) for v in point])
+        d = (C.c_double * 3)(*[float(v) for v in direction])
+        a = C.c_int64()
+        self._check(self.lib.nep_pka(self.ctx, C.byref(state.c), p, float(energy), d, C.byref(a),
+                                     _stream_ptr(stream)))
+        return a.value
 
     def stats(self) -> dict:
         s = NepStats()
@@ -512,6 +560,14 @@ class MDState:
     @property
     def dt_last(self):
         return self.c.dt_last
+
+    @property
+    def thermostat_energy(self):
+        return self.c.thermostat_energy
+
+    @property
+    def box(self):
+        return np.array([self.c.box[0], self.c.box[4], self.c.box[8]])
 
     @property
     def virial(self):
