@@ -205,9 +205,40 @@ def other_configs(dev):
                  "displacement; pairs within r_c compacted every step)")
     out["c5_8192000_fp32_skin_0.5A"] = r
     nep.close()
+    # the start of a foil cascade on the slab: Nose-Hoover chain (300 K) on the 3 a0
+    # shell at the x and y faces, a 100 keV PKA 10 A below the top surface along
+    # (1, 3, -5), variable time step (0.01 A per step, dt <= 1 fs)
+    s = I.c5()
+    nep = N.NEP(model, "fp32")
+    grp = torch.tensor(I.border_group(s), dtype=torch.uint8, device=dev)
+    nep.set_thermostat(300.0, tau=100.0, chain=4, group=grp)
+    types = torch.tensor(s.types, dtype=torch.int32, device=dev)
+    st = N.MDState(N.to_device_soa(s.pos, dev), N.to_device_soa(s.vel, dev), s.box, s.pbc,
+                   dt_max=1.0, d_max=0.01, types=types)
+    top = float(s.pos[:, 2].max())
+    atom = nep.pka(st, (0.5 * s.box[0], 0.5 * s.box[1], top - 10.0), 1.0e5, (1.0, 3.0, -5.0))
+    nep.set_option(N.NEP_OPT_GRAPH_CHUNK, 25)
+    nep.md(st, 3)
+    nep.md(st, 25)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    nep.md(st, 100)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out["c5_8192000_cascade_start_fp32"] = {
+        "value": s.n * 100 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / 100, "steps": 100,
+        "atoms": s.n, "sim_time_fs": st.time, "pka_atom": atom,
+        "thermostatted_atoms": int(grp.sum().item()),
+        "note": ("Nose-Hoover chain on the 3 a0 shell of the periodic faces, 100 keV PKA "
+                 "along (1, 3, -5), variable dt (0.01 A per step)")}
+    nep.close()
+    del s, st
     # the same slab as a random 50/50 W-Mo solid solution with a two-species model
     # (pair coefficient tables, mixed-Z ZBL, two masses)
-    s = I.alloy(s, [0.5, 0.5], seed=305)
+    s = I.alloy(I.c5(), [0.5, 0.5], seed=305)
     nep = N.NEP(I.nep_model(301, species=("W", "Mo")), "fp32")
     r = _time_md(N, nep, s, 100, 3, dev)
     r["note"] = "two species (W, Mo), random labels, same geometry and velocities as the slab"

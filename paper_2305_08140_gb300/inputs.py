@@ -258,6 +258,18 @@ def hea(ncell: int = 40, a: float = 3.23, temperature: float = 300.0,
     return s
 
 
+def border_group(s: Structure, width: float = 3 * A_W) -> np.ndarray:
+    """uint8 flags of the atoms within ``width`` of a periodic face of the box
+    (the thermostatted shell of the cascade runs, Sec. II.B: 3 a0; the free
+    surfaces of a foil are not part of it)."""
+    d = np.full(s.n, np.inf)
+    for a in range(3):
+        if s.pbc[a]:
+            x = np.mod(s.pos[:, a], s.box[a])
+            d = np.minimum(d, np.minimum(x, s.box[a] - x))
+    return (d < width).astype(np.uint8)
+
+
 def small_box(ncell: tuple[int, int, int], a: float = A_W, sigma: float = 0.0,
               seed: int = 0, pbc=(1, 1, 1)) -> Structure:
     """A bcc box of ``ncell`` cells with optional displacements."""
