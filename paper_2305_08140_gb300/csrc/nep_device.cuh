@@ -1172,9 +1172,18 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
                 store_b(bR, B0, (size_t)k * T + t);
             }
         } else {
+            // one species: the record the radial-force kernel gathers per
+            // neighbour, (x, y, z, b_8), (b_0 + B0, b_1, b_2, b_3), (b_4..b_7)
+            // (T_0 = 1 and T_0' = 0, so B0 folds into b_0)
             R bR[KR], B0;
             U = network_adjoint<R>(P, qR, A, bR, B0);
-            store_b(bR, B0, (size_t)k);
+            P4 r0, r1, r2;
+            r0.x = pi.x; r0.y = pi.y; r0.z = pi.z; r0.w = bR[8];
+            r1.x = bR[0] + B0; r1.y = bR[1]; r1.z = bR[2]; r1.w = bR[3];
+            r2.x = bR[4]; r2.y = bR[5]; r2.z = bR[6]; r2.w = bR[7];
+            br[3 * (size_t)k] = r0;
+            br[3 * (size_t)k + 1] = r1;
+            br[3 * (size_t)k + 2] = r2;
         }
 
         typename A_::T fi[3] = {0, 0, 0};
@@ -1257,8 +1266,10 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
 //   f_ij - f_ji = [f_c' (B0_i + B0_j + sum_k (b_i + b_j)_k T_k)
 //                  + f_c x' sum_k (b_i + b_j)_k T'_k] u_ij,
 // so each atom sums its own radial force from its neighbours' packed adjoint
-// (bp[k] = (b_0..b_8, B0), 12 values per atom) without atomics; the virial is
-// -1/2 sum_i sum_j (f_ij - f_ji) (x) d_ij.
+// without atomics; the virial is -1/2 sum_i sum_j (f_ij - f_ji) (x) d_ij.
+// One species: bp[3k..3k+2] = (x, y, z, b_8), (b_0 + B0, b_1..b_3), (b_4..b_7)
+// (position and adjoint in one gathered record); several species: pos4 and
+// bp[(k T + t) * 3] = (b_0..b_3), (b_4..b_7), (b_8, B0, 0, 0).
 // MS (several species): the pair (i, j) adds atom i's adjoint for neighbour
 // species t_j and atom j's for species t_i (bp[(k * T + t) * 3]).
 template <typename R, bool MS>
@@ -1281,7 +1292,61 @@ __global__ void __launch_bounds__(TILE) k_radial_force(const Model<R> P, const G
     double wz[9];
 #pragma unroll
     for (int t = 0; t < 9; ++t) { w[t] = R(0); wz[t] = 0.0; }
-    if (k < g.n) {
+    if (!MS && k < g.n) {
+        // one species: three 16-byte loads per neighbour (position and adjoint
+        // in one record written by the angular kernel)
+        const int2 c2 = cnt[k];
+        const int na = c2.x, total = c2.x + c2.y, M = g.M;
+        const P4 ri0 = bp[3 * (size_t)k], ri1 = bp[3 * (size_t)k + 1], ri2 = bp[3 * (size_t)k + 2];
+        R fx = R(0), fy = R(0), fz = R(0);
+        int ent_n = total > 0 ? nbr[(size_t)list_slot(0, na, M) * ld + k] : 0;
+        int ent_nn = total > 1 ? nbr[(size_t)list_slot(1, na, M) * ld + k] : 0;
+        P4 rj0_n = ri0, rj1_n = ri1, rj2_n = ri2;
+        if (total > 0) {
+            const size_t m0 = (size_t)(ent_n >> 5);
+            rj0_n = bp[3 * m0]; rj1_n = bp[3 * m0 + 1]; rj2_n = bp[3 * m0 + 2];
+        }
+        for (int s = 0; s < total; ++s) {
+            const int ent = ent_n;
+            const P4 rj0 = rj0_n, rj1 = rj1_n, rj2 = rj2_n;
+            ent_n = ent_nn;
+            if (s + 1 < total) {
+                const size_t m1 = (size_t)(ent_n >> 5);
+                rj0_n = bp[3 * m1]; rj1_n = bp[3 * m1 + 1]; rj2_n = bp[3 * m1 + 2];
+            }
+            if (s + 2 < total) ent_nn = nbr[(size_t)list_slot(s + 2, na, M) * ld + k];
+            const P4 off = s_off[ent & 31];
+            const R dx = rj0.x - ri0.x + off.x, dy = rj0.y - ri0.y + off.y, dz = rj0.z - ri0.z + off.z;
+            const R r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 >= P.rcR2) continue;   // beyond r_c (lists built with a skin)
+            const R inv_r = nepm::nep_rsqrt(r2);
+            const R r = r2 * inv_r;
+            R T[KR], dT[KR], fc, dfc, dxdr;
+            nepm::cheb<KR, true>(r, P.inv_rcR, T, dT, fc, dfc, dxdr);
+            const R b[KR] = {ri1.x + rj1.x, ri1.y + rj1.y, ri1.z + rj1.z, ri1.w + rj1.w,
+                             ri2.x + rj2.x, ri2.y + rj2.y, ri2.z + rj2.z, ri2.w + rj2.w,
+                             ri0.w + rj0.w};
+            R s1 = b[0], s2 = R(0);
+#pragma unroll
+            for (int kk = 1; kk < KR; ++kk) {
+                s1 += b[kk] * T[kk];
+                s2 += b[kk] * dT[kk];
+            }
+            const R fs = (dfc * s1 + fc * dxdr * s2) * inv_r;   // (f_ij - f_ji) = fs d
+            const R gx = fs * dx, gy = fs * dy, gz = fs * dz;
+            fx += gx; fy += gy; fz += gz;
+            w[0] -= gx * dx; w[1] -= gx * dy; w[2] -= gx * dz;
+            w[3] -= gy * dx; w[4] -= gy * dy; w[5] -= gy * dz;
+            w[6] -= gz * dx; w[7] -= gz * dy; w[8] -= gz * dz;
+        }
+        if (!isfinite(fx + fy + fz)) atomicOr(status, ST_NONFINITE);
+        A_::add(&facc[k], A_::conv(fx));
+        A_::add(&facc[ld + k], A_::conv(fy));
+        A_::add(&facc[2 * ld + k], A_::conv(fz));
+#pragma unroll
+        for (int t = 0; t < 9; ++t) w[t] *= R(0.5);
+    }
+    if (MS && k < g.n) {
         const int2 c2 = cnt[k];
         const int na = c2.x, total = c2.x + c2.y, M = g.M;
         const P4 pi = pos4[k];
