@@ -217,6 +217,9 @@ typedef struct nep_stats {
     int32_t nbr_capacity;       /* current neighbour slots per atom */
     int32_t graph_chunk;        /* MD steps per captured graph */
     int64_t list_builds_skin;   /* MD neighbour-list builds with a Verlet skin so far */
+    int32_t radial_q_in_neighbor_kernel;  /* 1: the last evaluation summed the radial
+                                             descriptor in the neighbour-list kernel (one
+                                             species, lists rebuilt every step) */
 } nep_stats;
 
 int nep_get_stats(const nep_ctx* ctx, nep_stats* out);

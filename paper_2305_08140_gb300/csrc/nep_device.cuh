@@ -254,7 +254,20 @@ __global__ void k_cell_finalize(Grid g, int ncell, const int* __restrict__ start
 // Neighbour lists: 27-cell stencil, minimum image through the stencil offset
 // ----------------------------------------------------------------------------
 
+// Radial basis coefficients for the neighbour kernel that also sums the
+// radial descriptor (one species).
 template <typename R>
+struct RadCoef {
+    R inv_rcR;
+    R hR[NR * KR], CR[NR];
+};
+
+// WQ: also the radial descriptor q_n of every atom (one species, lists
+// rebuilt every step), from the pairs the force kernels will see: the
+// displacement is recomputed for each hit in the force kernels' form
+// (pj - pi) + offset, and pairs with r >= r_c in that form are left out
+// as they skip them.
+template <typename R, bool WQ>
 __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                                                    const typename V4<R>::T* __restrict__ pos4,
                                                    const int* __restrict__ cell_sorted,
@@ -263,11 +276,15 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                                                    int* __restrict__ status,
                                                    int* __restrict__ maxc,
                                                    unsigned long long* __restrict__ pairs,
-                            const int* __restrict__ gate = nullptr)
+                                                   const int* __restrict__ gate,
+                                                   const RadCoef<R> rq, R* __restrict__ qr)
 {
     if (gate && *gate == 0) return;   // lists still valid (Verlet skin)
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     int na = 0, nro = 0, sa = 0, sro = 0;
+    R Sb[WQ ? KR : 1];
+#pragma unroll
+    for (int kk = 0; kk < (WQ ? KR : 1); ++kk) Sb[kk] = R(0);
     if (k < g.n) {
         const typename V4<R>::T p = pos4[k];
         const int c = cell_sorted[k];
@@ -310,6 +327,18 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                                 else col[(size_t)(M - 1 - sro++) * ld] = ent;
                             }
                             if (ang) ++na; else ++nro;
+                            if constexpr (WQ) {
+                                const R fx = q.x - p.x + R(ox) * lx, fy = q.y - p.y + R(oy) * ly,
+                                        fz = q.z - p.z + R(oz) * lz;
+                                const R f2 = fx * fx + fy * fy + fz * fz;
+                                if (f2 < rcR2) {
+                                    const R rr = f2 * nepm::nep_rsqrt(f2);
+                                    R T[KR], dT[KR], fc, dfc, dxdr;
+                                    nepm::cheb<KR, false>(rr, rq.inv_rcR, T, dT, fc, dfc, dxdr);
+#pragma unroll
+                                    for (int kk = 0; kk < KR; ++kk) Sb[kk] += fc * T[kk];
+                                }
+                            }
                         }
                     }
                 }
@@ -317,6 +346,16 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
         }
         cnt[k] = make_int2(sa, sro);
         if (na + nro > M) atomicOr(status, ST_OVERFLOW);
+        if constexpr (WQ) {
+            // q_n = C_n Sb_0 + sum_k h_nk Sb_k
+#pragma unroll
+            for (int n = 0; n < NR; ++n) {
+                R acc = rq.CR[n] * Sb[0];
+#pragma unroll
+                for (int kk = 0; kk < KR; ++kk) acc += rq.hR[n * KR + kk] * Sb[kk];
+                qr[(size_t)n * ld + k] = acc;
+            }
+        }
     }
     // statistics: block maxima and pair sums
     int tot = na + nro;

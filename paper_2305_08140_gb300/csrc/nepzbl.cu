@@ -102,6 +102,7 @@ struct nep_ctx {
     int capture_kernels = 0;
     int capture_timed = 0;
     int nep_smem_set[4] = {0, 0, 0, 0};
+    int radial_q_fused = 0;          // last evaluation summed q in the neighbour kernel
     // Nose-Hoover chain thermostat on a group, Berendsen barostat (MD)
     int nhc_on = 0;
     NhcParams nhc_p;
@@ -359,10 +360,20 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
         g, ncell, ctx->start, ctx->perm, x, types, (typename V4<R>::T*)ctx->pos4, ctx->cell_sorted,
         ctx->status, gate);
     count_launch(ctx);
-    k_neighbors<R><<<(n + 127) / 128, 128, 0, s>>>(
+    // one species, lists rebuilt every step: the neighbour kernel also sums
+    // the radial descriptor (no separate radial-descriptor pass)
+    const bool ms = ctx->ntypes > 1;
+    const bool fuse_q = !ms && !gate;
+    RadCoef<R> rq;
+    rq.inv_rcR = P.inv_rcR;
+    for (int t = 0; t < NR * KR; ++t) rq.hR[t] = P.hR[t];
+    for (int t = 0; t < NR; ++t) rq.CR[t] = P.CR[t];
+    (fuse_q ? k_neighbors<R, true> : k_neighbors<R, false>)<<<(n + 127) / 128, 128, 0, s>>>(
         g, (R)(rl * rl), (R)(ra * ra), (const typename V4<R>::T*)ctx->pos4, ctx->cell_sorted,
-        ctx->start, ctx->nbr, ctx->cnt, ctx->status, ctx->status + 1, ctx->pairs, gate);
+        ctx->start, ctx->nbr, ctx->cnt, ctx->status, ctx->status + 1, ctx->pairs, gate, rq,
+        (R*)ctx->qr);
     count_launch(ctx);
+    ctx->radial_q_fused = fuse_q ? 1 : 0;
     if (gate) {
         // cell-relative positions of this step (cells as of the last build)
         k_refresh_pos4<R><<<nb, tb, 0, s>>>(g, ctx->perm, ctx->cell_sorted, x,
@@ -386,11 +397,12 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     const R* coef;
     if constexpr (sizeof(R) == 4) coef = ctx->coef_f;
     else coef = ctx->coef_d;
-    const bool ms = ctx->ntypes > 1;
-    (ms ? k_radial_q<R, true> : k_radial_q<R, false>)<<<(n + 127) / 128, 128, 0, s>>>(
-        P, g, p4, ctx->nbr, ctx->cnt, (R*)ctx->qr, gate ? ctx->nbr_act : nullptr,
-        gate ? ctx->cnt_act : nullptr, coef);
-    count_launch(ctx);
+    if (!fuse_q) {
+        (ms ? k_radial_q<R, true> : k_radial_q<R, false>)<<<(n + 127) / 128, 128, 0, s>>>(
+            P, g, p4, ctx->nbr, ctx->cnt, (R*)ctx->qr, gate ? ctx->nbr_act : nullptr,
+            gate ? ctx->cnt_act : nullptr, coef);
+        count_launch(ctx);
+    }
     // angular part, network, ZBL (the block's angular entries staged in shared
     // memory when they fit; with several species the pair coefficients first)
     const int stage_slots = ctx->M < STAGE_MAX_SLOTS ? ctx->M : STAGE_MAX_SLOTS;
@@ -787,6 +799,7 @@ int nep_get_stats(const nep_ctx* ctx, nep_stats* out)
     if (ctx->nrebuild && cudaMemcpy(&nb, ctx->nrebuild, sizeof(nb), cudaMemcpyDeviceToHost) != cudaSuccess)
         nb = 0;
     out->list_builds_skin = (int64_t)nb;
+    out->radial_q_in_neighbor_kernel = ctx->radial_q_fused;
     return NEP_OK;
 }
 
@@ -1747,8 +1760,10 @@ extern "C" int nep_compute_static(const nep_params* p, int64_t n_atoms, const do
     k_bin_scatter<<<nb, tb, 0, s>>>(n, cell_of, slot_of, start, perm);
     k_cell_finalize<float><<<(ncell + 127) / 128, 128, 0, s>>>(g, ncell, start, perm, xyz, types,
                                                               pos4, cell_sorted, status);
-    k_neighbors<float><<<(n + 127) / 128, 128, 0, s>>>(g, P.rcR2, P.rcA2, pos4, cell_sorted, start,
-                                                      nbr, cnt, status, status + 1, pairs);
+    k_neighbors<float, false><<<(n + 127) / 128, 128, 0, s>>>(g, P.rcR2, P.rcA2, pos4, cell_sorted,
+                                                             start, nbr, cnt, status, status + 1,
+                                                             pairs, nullptr, RadCoef<float>{},
+                                                             nullptr);
     const int tiles = (n + TILE - 1) / TILE;
     k_nep<float><<<tiles, TILE, 0, s>>>(P, g, pos4, nbr, cnt, perm, xyz, facc, partials,
                                         site_energy, status, 0);
