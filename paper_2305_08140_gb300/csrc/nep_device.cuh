@@ -215,7 +215,8 @@ __global__ void k_cell_finalize(Grid g, int ncell, const int* __restrict__ start
                                 const int32_t* __restrict__ types,
                                 typename V4<R>::T* __restrict__ pos4,
                                 int* __restrict__ cell_sorted, int* __restrict__ status,
-                                const int* __restrict__ gate = nullptr)
+                                const int* __restrict__ gate = nullptr,
+                                int* __restrict__ invperm = nullptr)
 {
     if (gate && *gate == 0) return;   // lists still valid (Verlet skin)
     int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -246,6 +247,7 @@ __global__ void k_cell_finalize(Grid g, int ncell, const int* __restrict__ start
         q.w = (R)t;
         pos4[s] = q;
         cell_sorted[s] = c;
+        if (invperm) invperm[i] = s;
     }
     if (badtype) atomicOr(status, ST_BADTYPE);
 }
@@ -1451,6 +1453,28 @@ __global__ void __launch_bounds__(TILE) k_radial_force(const Model<R> P, const G
     tile_partials<R>(0.0, w, wz, false, partials + (size_t)blockIdx.x * NPART);
 }
 
+// Forces back to caller order (FP64), one thread per caller index: the
+// writes are coalesced and the reads gathered through invperm (caller index
+// -> cell-ordered slot).  The accumulators are cleared before the next
+// evaluation by a memset.
+template <typename R>
+__global__ void k_forces_gather(int n, int ld, const int* __restrict__ invperm,
+                                const typename Acc<R>::T* __restrict__ facc,
+                                double* __restrict__ F, int* __restrict__ status)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int k = invperm[i];
+    bool bad = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double f = Acc<R>::value(facc[(size_t)a * ld + k]);
+        bad |= !isfinite(f);
+        F[(size_t)a * n + i] = f;
+    }
+    if (bad) atomicOr(status, ST_NONFINITE);
+}
+
 // Forces back to caller order (FP64), accumulators reset to zero.
 template <typename R>
 __global__ void k_forces_out(int n, int ld, const int* __restrict__ perm,
@@ -1563,13 +1587,15 @@ static __global__ void k_kick_drift(Grid g, MassTab mt, const int32_t* __restric
     }
 }
 
-// v += dt/2 F/m and per-block (sum m v^2, max |v|^2)
+// v += dt/2 F/m and per-block (sum m v^2, max |v|^2, and with `tensor` the
+// per-dimension sums m v_a^2 the barostat needs; zeros otherwise)
 static __global__ void __launch_bounds__(256) k_kick_thermo(int n, MassTab mt,
                                                      const int32_t* __restrict__ types,
                                                      const double* __restrict__ thermo,
                                                      double* __restrict__ v,
                                                      const double* __restrict__ F,
-                                                     double* __restrict__ part, int half_kick)
+                                                     double* __restrict__ part, int half_kick,
+                                                     int tensor)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     double v2 = 0.0, vm = 0.0, va[3] = {0.0, 0.0, 0.0};
@@ -1591,13 +1617,16 @@ static __global__ void __launch_bounds__(256) k_kick_thermo(int n, MassTab mt,
     for (int o = 16; o > 0; o >>= 1) {
         v2 += __shfl_xor_sync(0xffffffffu, v2, o);
         vm = fmax(vm, __shfl_xor_sync(0xffffffffu, vm, o));
+    }
+    if (tensor) {
+        for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) va[a] += __shfl_xor_sync(0xffffffffu, va[a], o);
+            for (int a = 0; a < 3; ++a) va[a] += __shfl_xor_sync(0xffffffffu, va[a], o);
     }
     if ((threadIdx.x & 31) == 0) {
         sh[0][threadIdx.x >> 5] = v2;
         sh[1][threadIdx.x >> 5] = vm;
-        for (int a = 0; a < 3; ++a) sh[2 + a][threadIdx.x >> 5] = va[a];
+        for (int a = 0; a < 3; ++a) sh[2 + a][threadIdx.x >> 5] = tensor ? va[a] : 0.0;
     }
     __syncthreads();
     if (threadIdx.x == 0) {

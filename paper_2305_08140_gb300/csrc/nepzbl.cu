@@ -62,6 +62,7 @@ struct nep_ctx {
     int ccap = 0;      // cells
     // scratch (device)
     int *cell_of = nullptr, *slot_of = nullptr, *perm = nullptr, *cell_sorted = nullptr;
+    int* invperm = nullptr;          // caller index -> cell-ordered slot
     void* pos4 = nullptr;
     int2* cnt = nullptr;
     int* nbr = nullptr;
@@ -198,7 +199,7 @@ static void free_scratch(nep_ctx* ctx)
 {
     drop_graphs(ctx);
     free_dev(ctx->cell_of); free_dev(ctx->slot_of); free_dev(ctx->perm);
-    free_dev(ctx->cell_sorted); free_dev(ctx->pos4); free_dev(ctx->cnt); free_dev(ctx->nbr);
+    free_dev(ctx->cell_sorted); free_dev(ctx->invperm); free_dev(ctx->pos4); free_dev(ctx->cnt); free_dev(ctx->nbr);
     free_dev(ctx->facc); free_dev(ctx->partials); free_dev(ctx->partials2);
     free_dev(ctx->qr); free_dev(ctx->br); free_dev(ctx->xref); free_dev(ctx->nbr_act);
     free_dev(ctx->cnt_act);
@@ -223,6 +224,7 @@ static int ensure_atoms(nep_ctx* ctx, int n, int M)
     CK(cudaMalloc(&ctx->slot_of, sizeof(int) * ld));
     CK(cudaMalloc(&ctx->perm, sizeof(int) * ld));
     CK(cudaMalloc(&ctx->cell_sorted, sizeof(int) * ld));
+    CK(cudaMalloc(&ctx->invperm, sizeof(int) * ld));
     CK(cudaMalloc(&ctx->pos4, p4 * ld));
     CK(cudaMalloc(&ctx->cnt, sizeof(int2) * ld));
     CK(cudaMalloc(&ctx->nbr, sizeof(int) * (size_t)ld * MM));
@@ -358,7 +360,7 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     count_launch(ctx);
     k_cell_finalize<R><<<(ncell + 127) / 128, 128, 0, s>>>(
         g, ncell, ctx->start, ctx->perm, x, types, (typename V4<R>::T*)ctx->pos4, ctx->cell_sorted,
-        ctx->status, gate);
+        ctx->status, gate, ctx->invperm);
     count_launch(ctx);
     // one species, lists rebuilt every step: the neighbour kernel also sums
     // the radial descriptor (no separate radial-descriptor pass)
@@ -381,7 +383,9 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
         count_launch(ctx);
     }
     const int tiles = (n + TILE - 1) / TILE;
-    // the three force kernels are timed together when timing is on
+    // force accumulators start at zero (the forces are gathered out of them)
+    CK(cudaMemsetAsync(ctx->facc, 0, sizeof(typename Acc<R>::T) * 3 * (size_t)ctx->ld, s));
+    // the force kernels are timed together when timing is on
     if (timed_slot >= 0) {
         if (ctx->capturing)
             CK(cudaEventRecordWithFlags(ctx->events[2 * timed_slot], s, cudaEventRecordExternal));
@@ -431,8 +435,8 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
         else
             CK(cudaEventRecord(ctx->events[2 * timed_slot + 1], s));
     }
-    k_forces_out<R><<<nb, tb, 0, s>>>(n, ctx->ld, ctx->perm, (typename Acc<R>::T*)ctx->facc, F,
-                                      ctx->status);
+    k_forces_gather<R><<<nb, tb, 0, s>>>(n, ctx->ld, ctx->invperm,
+                                         (const typename Acc<R>::T*)ctx->facc, F, ctx->status);
     count_launch(ctx);
     {
         // two-stage fixed-order sum of the per-tile energy/virial partials
@@ -908,13 +912,13 @@ static int enqueue_step(nep_ctx* ctx, const Grid& g, nep_md_state* st, cudaStrea
     int rc = eval(ctx, g, st->xyz, st->types, st->forces, nullptr, s, slot, gate);
     if (rc) return rc;
     k_kick_thermo<<<nb, tb, 0, s>>>(n, ctx->mt, st->types, ctx->thermo, st->vel, st->forces,
-                                    ctx->vpart, 1);
+                                    ctx->vpart, 1, ctx->baro_on);
     count_launch(ctx);
     if (ctx->nhc_on) {
         enqueue_nhc(ctx, n, st->types, st->vel, s);
         // kinetic energy and speeds after the thermostat's scaling
         k_kick_thermo<<<nb, tb, 0, s>>>(n, ctx->mt, st->types, ctx->thermo, st->vel, st->forces,
-                                        ctx->vpart, 0);
+                                        ctx->vpart, 0, ctx->baro_on);
         count_launch(ctx);
     }
     k_thermo_step<<<1, 256, 0, s>>>(ctx->vpart, nb, EV_AMU, ctx->thermo, 1, gate);
@@ -1089,7 +1093,7 @@ int md_step(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
     {
         const int tb = 256, nb = (int)((n + tb - 1) / tb);
         k_kick_thermo<<<nb, tb, 0, s>>>((int)n, ctx->mt, st->types, ctx->thermo, st->vel,
-                                        st->forces, ctx->vpart, 0);
+                                        st->forces, ctx->vpart, 0, ctx->baro_on);
         count_launch(ctx);
         k_thermo_step<<<1, 256, 0, s>>>(ctx->vpart, nb, EV_AMU, ctx->thermo, 0);
         count_launch(ctx);
