@@ -362,10 +362,12 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
         g, ncell, ctx->start, ctx->perm, x, types, (typename V4<R>::T*)ctx->pos4, ctx->cell_sorted,
         ctx->status, gate, ctx->invperm);
     count_launch(ctx);
-    // one species, lists rebuilt every step: the neighbour kernel also sums
-    // the radial descriptor (no separate radial-descriptor pass)
+    // one species, lists rebuilt every step, FP32: the neighbour kernel also
+    // sums the radial descriptor (no separate radial-descriptor pass); the
+    // FP64 path keeps the separate pass (FP64 arithmetic in the divergent hit
+    // branch of the search costs more than the pass)
     const bool ms = ctx->ntypes > 1;
-    const bool fuse_q = !ms && !gate;
+    const bool fuse_q = !ms && !gate && sizeof(R) == 4;
     RadCoef<R> rq;
     rq.inv_rcR = P.inv_rcR;
     for (int t = 0; t < NR * KR; ++t) rq.hR[t] = P.hR[t];
