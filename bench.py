@@ -57,6 +57,11 @@ FP32_LANES = 128
 #   per angular pair, force pass: Chebyshev with derivatives 40,
 #     g_n and g'_n 190, harmonics 60, G_lm and G'_lm 480, S 96,
 #     gradient polynomial contraction ~200, assembly 12                     -> 1078
+# DRAM bytes (read + write) of the two timed force kernels (k_nep_ang +
+# k_radial_force) per atom, from one ncu capture of the same build on the
+# 1,024,000-atom slab (profiles/force_kernels_ncu_full_slab_1024000.md):
+# 514.2 MB per launch pair; scaled by the atom count.
+TRAFFIC_PER_ATOM = 514.2e6 / 1.024e6
 FLOP_ATOM = 4630
 FLOP_PAIR_R = 128 + 122
 FLOP_PAIR_A = 424 + 1078
@@ -504,7 +509,10 @@ def run_ours(args):
                                 "forces; radial descriptor summed in k_neighbors)" if q_fused
                                 else "k_radial_q + k_nep_ang + k_radial_force"),
                      "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tflops, "traffic": None,
+                     "frac": achieved / peak_tflops,
+                     "traffic": TRAFFIC_PER_ATOM * n if q_fused else None,
+                     "traffic_note": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the "
+                                      "timed kernels, 1,024,000-atom capture scaled by atoms"),
                      "peak_kind": f"FP32 issue rate {SMS} SMs x {FP32_LANES} lanes x 2 x "
                                   f"{sm_mhz:.0f} MHz (sm_max_mhz, {peak_kind})",
                      "kernel_ms": k_ms, "flop_per_launch": flop,
