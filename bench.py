@@ -146,29 +146,64 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_baseline_sample(seconds_hint: float = 20.0) -> dict:
-    """The FP64 oracle, as it stands, on a bounded sample of the workload:
-    one velocity-Verlet step of a laterally cut piece of the slab (the full
-    160-cell depth and both free surfaces, 12 x 12 cells across, 46,080 atoms),
-    on every host thread it uses."""
-    from oracle import oracle as O
-    nl = 12
+def _slab_cut(nl):
+    """The full-depth slab cut to nl x nl cells across (open z, periodic x, y)."""
     pos = I.bcc(nl, nl, 160)
     pos[:, 2] += 30.0
     L = nl * I.A_W
     box = np.array([L, L, 160 * I.A_W + 60.0])
     pbc = np.array([1, 1, 0], np.int32)
     vel = I.maxwell_boltzmann(np.random.default_rng(5), len(pos), 300.0)
+    return pos, vel, box, pbc
+
+
+_SINGLE_THREAD = """
+import sys, time, json
+sys.path.insert(0, {root!r})
+from oracle import oracle as O
+from paper_2305_08140_gb300 import inputs as I
+s = I.c1()
+m = I.nep_model(1)
+p, v, F, _ = O.md(m, s.pos, s.vel, s.box, s.pbc, s.mass, 1.0, 1)
+t0 = time.perf_counter()
+O.md(m, p, v, s.box, s.pbc, s.mass, 1.0, {steps}, forces=F)
+dt = time.perf_counter() - t0
+print(json.dumps({{"value": s.n * {steps} / dt, "threads": O.num_threads(), "seconds": dt}}))
+"""
+
+
+def cpu_baseline_sample() -> dict:
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    four velocity-Verlet steps of a laterally cut piece of the slab (the full
+    160-cell depth and both free surfaces, 32 x 32 cells across, 327,680
+    atoms) on every host thread it uses, and, in a child process limited to
+    one thread, 20 steps of the 2,000-atom crystal."""
+    import subprocess
+    from oracle import oracle as O
+    nl, steps = 32, 4
+    pos, vel, box, pbc = _slab_cut(nl)
     model = I.nep_model(1)
-    # forces at the start are part of the step's work only once
+    p, v, F, _ = O.md(model, pos, vel, box, pbc, I.MASS_W, 1.0, 0)    # initial forces
     t0 = time.perf_counter()
-    O.md(model, pos, vel, box, pbc, I.MASS_W, 1.0, 1)
+    O.md(model, p, v, box, pbc, I.MASS_W, 1.0, steps, forces=F)
     dt = time.perf_counter() - t0
     n = len(pos)
-    return {"value": n * 2 / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": (f"FP64 oracle velocity-Verlet step of a {nl}x{nl}x160-cell cut of the "
-                       f"slab ({n} atoms, open z, periodic x,y): initial forces + 1 step = 2 "
-                       f"force evaluations in {dt:.1f} s; value counts atom-evaluations/s")}
+    single = None
+    try:
+        env = dict(os.environ, OMP_NUM_THREADS="1")
+        root = os.path.dirname(os.path.abspath(__file__))
+        out = subprocess.run([sys.executable, "-c", _SINGLE_THREAD.format(root=root, steps=20)],
+                             env=env, capture_output=True, text=True, timeout=300)
+        single = json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as e:   # the single-thread figure is context only
+        single = {"error": str(e)[:200]}
+    return {"value": n * steps / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": (f"FP64 oracle, {steps} velocity-Verlet steps of a {nl}x{nl}x160-cell cut "
+                       f"of the slab ({n} atoms, open z, periodic x,y) in {dt:.1f} s"),
+            "single_thread": {"value": single.get("value"), "unit": UNIT,
+                              "sample": "FP64 oracle, 20 steps of the 2,000-atom crystal "
+                                        "(10^3 cells), OMP_NUM_THREADS=1",
+                              **{k: v for k, v in single.items() if k != "value"}}}
 
 
 def _time_md(N, nep, s, steps, warm, dev, d_max=0.0, chunk=25):
@@ -337,12 +372,7 @@ def run_reference(args):
         return 0
     from oracle import oracle as O
     nl = 12
-    pos = I.bcc(nl, nl, 160)
-    pos[:, 2] += 30.0
-    L = nl * I.A_W
-    box = np.array([L, L, 160 * I.A_W + 60.0])
-    pbc = np.array([1, 1, 0], np.int32)
-    vel = I.maxwell_boltzmann(np.random.default_rng(5), len(pos), 300.0)
+    pos, vel, box, pbc = _slab_cut(nl)
     model = I.nep_model(1)
     p, v, F, _ = O.md(model, pos, vel, box, pbc, I.MASS_W, 1.0, max(args.warmup, 0))
     t0 = time.perf_counter()
