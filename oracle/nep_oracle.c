@@ -37,6 +37,11 @@
  * Neighbours: either brute force over all atoms and all periodic images
  * (self-images included), or a plain cell grid with the minimum image (only
  * when every periodic box length holds at least three cells of size >= rc).
+ *
+ * Cells: box = 9 doubles, the rows of H are the cell vectors a, b, c, and a
+ * position is x = s H with fractional s (periodic dimensions wrap s into
+ * [0, 1)).  A diagonal H is the orthorhombic box of lengths H_aa; any other
+ * (triclinic) H uses brute-force neighbours with images x_j - x_i + n H.
  */
 #include <math.h>
 #include <stdint.h>
@@ -463,12 +468,71 @@ static void list_free(orc_list *L)
 typedef struct {
     int N;
     const double *pos;   /* (N,3) */
-    double box[3];
+    double box[3];       /* diagonal of H */
     int pbc[3];
     const int *types;    /* (N) species, or NULL for all 0 */
+    int tric;            /* H has off-diagonal entries */
+    double h[9], hinv[9];   /* H (rows a, b, c) and its inverse */
 } orc_sys;
 
 static int sys_type(const orc_sys *S, int i) { return S->types ? S->types[i] : 0; }
+
+/* Fills the cell of S from the row-major 3x3 H; 0 if det H <= 0. */
+static int sys_cell(orc_sys *S, const double *h)
+{
+    memcpy(S->h, h, sizeof(S->h));
+    S->tric = 0;
+    for (int a = 0; a < 3; ++a) {
+        S->box[a] = h[4 * a];
+        for (int b = 0; b < 3; ++b)
+            if (a != b && h[3 * a + b] != 0.0) S->tric = 1;
+    }
+    const double c00 = h[4] * h[8] - h[5] * h[7], c01 = h[5] * h[6] - h[3] * h[8],
+                 c02 = h[3] * h[7] - h[4] * h[6];
+    const double det = h[0] * c00 + h[1] * c01 + h[2] * c02;
+    if (!(det > 0)) return 0;
+    /* inverse = adjugate / det */
+    S->hinv[0] = c00 / det;
+    S->hinv[1] = (h[2] * h[7] - h[1] * h[8]) / det;
+    S->hinv[2] = (h[1] * h[5] - h[2] * h[4]) / det;
+    S->hinv[3] = c01 / det;
+    S->hinv[4] = (h[0] * h[8] - h[2] * h[6]) / det;
+    S->hinv[5] = (h[2] * h[3] - h[0] * h[5]) / det;
+    S->hinv[6] = c02 / det;
+    S->hinv[7] = (h[1] * h[6] - h[0] * h[7]) / det;
+    S->hinv[8] = (h[0] * h[4] - h[1] * h[3]) / det;
+    return 1;
+}
+
+/* Fractional coordinates s = x H^-1 (row vectors). */
+static void to_frac(const orc_sys *S, const double *x, double *f)
+{
+    for (int a = 0; a < 3; ++a)
+        f[a] = x[0] * S->hinv[a] + x[1] * S->hinv[3 + a] + x[2] * S->hinv[6 + a];
+}
+
+/* Perpendicular width of the cell along lattice direction a: V / |b x c|. */
+static double cell_width(const orc_sys *S, int a)
+{
+    const double *u = S->h + 3 * ((a + 1) % 3), *v = S->h + 3 * ((a + 2) % 3);
+    const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2],
+                 cz = u[0] * v[1] - u[1] * v[0];
+    const double *w = S->h + 3 * a;
+    return fabs(w[0] * cx + w[1] * cy + w[2] * cz) / sqrt(cx * cx + cy * cy + cz * cz);
+}
+
+/* Periodic wrap of one position (triclinic): x -= sum_a floor(s_a) H_a. */
+static void wrap_tric(const orc_sys *S, double *x)
+{
+    double f[3];
+    to_frac(S, x, f);
+    for (int a = 0; a < 3; ++a) {
+        if (!S->pbc[a]) continue;
+        const double k = floor(f[a]);
+        if (k != 0.0)
+            for (int b = 0; b < 3; ++b) x[b] -= k * S->h[3 * a + b];
+    }
+}
 
 /* Every species index in [0, T). */
 static int types_valid(const orc_sys *S, int T)
@@ -488,8 +552,40 @@ typedef struct {
 
 /* Brute force: every atom j and every periodic image with |d| < rc, the atom
  * itself excluded only at zero shift. */
+static int query_brute_tric(const orc_sys *S, int i, double rc, orc_list *out)
+{
+    int nmax[3];
+    for (int a = 0; a < 3; ++a)
+        nmax[a] = S->pbc[a] ? (int)ceil(rc / cell_width(S, a)) + 1 : 0;
+    const double *xi = S->pos + 3 * i;
+    double rc2 = rc * rc;
+    for (int j = 0; j < S->N; ++j) {
+        const double *xj = S->pos + 3 * j;
+        double base[3], f[3];
+        for (int a = 0; a < 3; ++a) base[a] = xj[a] - xi[a];
+        to_frac(S, base, f);
+        for (int a = 0; a < 3; ++a) {
+            if (!S->pbc[a]) continue;
+            const double k = floor(f[a] + 0.5);
+            for (int b = 0; b < 3; ++b) base[b] -= k * S->h[3 * a + b];
+        }
+        for (int n0 = -nmax[0]; n0 <= nmax[0]; ++n0)
+            for (int n1 = -nmax[1]; n1 <= nmax[1]; ++n1)
+                for (int n2 = -nmax[2]; n2 <= nmax[2]; ++n2) {
+                    double d[3];
+                    for (int b = 0; b < 3; ++b)
+                        d[b] = base[b] + n0 * S->h[b] + n1 * S->h[3 + b] + n2 * S->h[6 + b];
+                    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    if (j == i && n0 == 0 && n1 == 0 && n2 == 0) continue;
+                    if (r2 < rc2 && list_push(out, j, sys_type(S, j), d)) return ORC_ERR_MEM;
+                }
+    }
+    return ORC_OK;
+}
+
 static int query_brute(const orc_sys *S, int i, double rc, orc_list *out)
 {
+    if (S->tric) return query_brute_tric(S, i, rc, out);
     int nmax[3];
     for (int a = 0; a < 3; ++a)
         nmax[a] = S->pbc[a] ? (int)ceil(rc / S->box[a]) + 1 : 0;
@@ -520,6 +616,7 @@ static int query_brute(const orc_sys *S, int i, double rc, orc_list *out)
 static int grid_build(const orc_sys *S, double rc, orc_grid *G)
 {
     memset(G, 0, sizeof(*G));
+    if (S->tric) return ORC_OK;                   /* brute force */
     for (int a = 0; a < 3; ++a) {
         if (S->pbc[a]) {
             int nc = (int)floor(S->box[a] / rc);
@@ -624,7 +721,8 @@ static int cmp_double(const void *a, const void *b)
 int orc_neighbor_counts(int N, const double *pos, const double *box, const int *pbc,
                         double rc, int mode, int *counts, int maxn, double *dist)
 {
-    orc_sys S = {N, pos, {box[0], box[1], box[2]}, {pbc[0], pbc[1], pbc[2]}, NULL};
+    orc_sys S = {N, pos, {0, 0, 0}, {pbc[0], pbc[1], pbc[2]}, NULL, 0, {0}, {0}};
+    if (!sys_cell(&S, box)) return ORC_ERR_ARG;
     orc_grid G;
     memset(&G, 0, sizeof(G));
     if (mode == 1 && grid_build(&S, rc, &G)) return ORC_ERR_MEM;
@@ -752,7 +850,8 @@ int orc_energy_forces_virial(const int *ihp, const double *dhp, const double *pa
 {
     orc_model m;
     if (model_init(&m, ihp, dhp, params, scaler) || N < 0) return ORC_ERR_ARG;
-    orc_sys S = {N, pos, {box[0], box[1], box[2]}, {pbc[0], pbc[1], pbc[2]}, types};
+    orc_sys S = {N, pos, {0, 0, 0}, {pbc[0], pbc[1], pbc[2]}, types, 0, {0}, {0}};
+    if (!sys_cell(&S, box)) return ORC_ERR_ARG;
     if (!types_valid(&S, m.T)) return ORC_ERR_ARG;
     return efv(&m, &S, use_grid, E, F, W, U, NULL);
 }
@@ -764,7 +863,8 @@ int orc_descriptors(const int *ihp, const double *dhp, const double *params,
 {
     orc_model m;
     if (model_init(&m, ihp, dhp, params, scaler) || N < 0) return ORC_ERR_ARG;
-    orc_sys S = {N, pos, {box[0], box[1], box[2]}, {pbc[0], pbc[1], pbc[2]}, types};
+    orc_sys S = {N, pos, {0, 0, 0}, {pbc[0], pbc[1], pbc[2]}, types, 0, {0}, {0}};
+    if (!sys_cell(&S, box)) return ORC_ERR_ARG;
     if (!types_valid(&S, m.T)) return ORC_ERR_ARG;
     return efv(&m, &S, use_grid, NULL, NULL, NULL, NULL, q);
 }
@@ -780,7 +880,8 @@ int orc_forces_subset(const int *ihp, const double *dhp, const double *params,
 {
     orc_model m;
     if (model_init(&m, ihp, dhp, params, scaler) || N < 0) return ORC_ERR_ARG;
-    orc_sys S = {N, pos, {box[0], box[1], box[2]}, {pbc[0], pbc[1], pbc[2]}, types};
+    orc_sys S = {N, pos, {0, 0, 0}, {pbc[0], pbc[1], pbc[2]}, types, 0, {0}, {0}};
+    if (!sys_cell(&S, box)) return ORC_ERR_ARG;
     if (!types_valid(&S, m.T)) return ORC_ERR_ARG;
     orc_grid G;
     memset(&G, 0, sizeof(G));
@@ -852,7 +953,8 @@ int orc_md(const int *ihp, const double *dhp, const double *params, const double
     if (model_init(&m, ihp, dhp, params, scaler) || N < 0) return ORC_ERR_ARG;
     for (int t = 0; t < m.T; ++t)
         if (!(mass[t] > 0)) return ORC_ERR_ARG;
-    orc_sys S = {N, pos, {box[0], box[1], box[2]}, {pbc[0], pbc[1], pbc[2]}, types};
+    orc_sys S = {N, pos, {0, 0, 0}, {pbc[0], pbc[1], pbc[2]}, types, 0, {0}, {0}};
+    if (!sys_cell(&S, box)) return ORC_ERR_ARG;
     if (!types_valid(&S, m.T)) return ORC_ERR_ARG;
     double E, W[9];
     int err = ORC_OK;
@@ -874,9 +976,11 @@ int orc_md(const int *ihp, const double *dhp, const double *params, const double
             vel[i] += 0.5 * dt * F[i] * acc;
             pos[i] += dt * vel[i];
         }
-        for (int i = 0; i < N; ++i)
+        for (int i = 0; i < N; ++i) {
+            if (S.tric) { wrap_tric(&S, pos + 3 * i); continue; }
             for (int a = 0; a < 3; ++a)
-                if (pbc[a]) pos[3 * i + a] -= box[a] * floor(pos[3 * i + a] / box[a]);
+                if (pbc[a]) pos[3 * i + a] -= S.box[a] * floor(pos[3 * i + a] / S.box[a]);
+        }
         err = efv(&m, &S, use_grid, &E, F, W, NULL, NULL);
         double ke = 0.0;
         for (int i = 0; i < 3 * N; ++i) {
@@ -975,7 +1079,8 @@ static double group_ke(int N, const double *vel, const int *types, const double 
 /* Velocity Verlet with the optional thermostat and barostat above.
  * ext = {T (K), tau (fs), chain length, p0 (eV/A^3), tau_p (fs), beta (A^3/eV)};
  * the thermostat is on when thermostat != 0 (group: N flags, NULL = all
- * atoms), the barostat when tau_p > 0.  box (3) is updated in place.
+ * atoms), the barostat when tau_p > 0 (orthorhombic cells only).  box (H,
+ * 9 doubles) is updated in place.
  * thermo (nsteps x 8): t, dt, PE, KE, E_NHC, Lx, Ly, Lz after each step. */
 int orc_md_ext(const int *ihp, const double *dhp, const double *params, const double *scaler,
                int N, double *pos, double *vel, double *F, int forces_valid, const int *types,
@@ -987,7 +1092,8 @@ int orc_md_ext(const int *ihp, const double *dhp, const double *params, const do
     if (model_init(&m, ihp, dhp, params, scaler) || N < 0) return ORC_ERR_ARG;
     for (int t = 0; t < m.T; ++t)
         if (!(mass[t] > 0)) return ORC_ERR_ARG;
-    orc_sys S = {N, pos, {box[0], box[1], box[2]}, {pbc[0], pbc[1], pbc[2]}, types};
+    orc_sys S = {N, pos, {0, 0, 0}, {pbc[0], pbc[1], pbc[2]}, types, 0, {0}, {0}};
+    if (!sys_cell(&S, box)) return ORC_ERR_ARG;
     if (!types_valid(&S, m.T)) return ORC_ERR_ARG;
     orc_nhc c;
     memset(&c, 0, sizeof(c));
@@ -1002,6 +1108,7 @@ int orc_md_ext(const int *ihp, const double *dhp, const double *params, const do
         for (int j = 1; j < c.M; ++j) c.Q[j] = c.kT * ext[1] * ext[1];
     }
     const int baro = ext && ext[4] > 0;
+    if (baro && S.tric) return ORC_ERR_ARG;          /* the barostat scales an orthorhombic box */
     double E, W[9];
     int err = ORC_OK;
     if (!forces_valid) err = efv(&m, &S, use_grid, &E, F, W, NULL, NULL);
@@ -1028,9 +1135,11 @@ int orc_md_ext(const int *ihp, const double *dhp, const double *params, const do
             vel[i] += 0.5 * dt * F[i] * acc;
             pos[i] += dt * vel[i];
         }
-        for (int i = 0; i < N; ++i)
+        for (int i = 0; i < N; ++i) {
+            if (S.tric) { wrap_tric(&S, pos + 3 * i); continue; }
             for (int a = 0; a < 3; ++a)
                 if (pbc[a]) pos[3 * i + a] -= S.box[a] * floor(pos[3 * i + a] / S.box[a]);
+        }
         err = efv(&m, &S, use_grid, &E, F, W, NULL, NULL);
         for (int i = 0; i < 3 * N; ++i)
             vel[i] += 0.5 * dt * F[i] * (ORC_EV_AMU / mass[sys_type(&S, i / 3)]);
@@ -1057,7 +1166,9 @@ int orc_md_ext(const int *ihp, const double *dhp, const double *params, const do
                 const double mu = cbrt(1.0 - ext[5] * (dt / ext[4]) * (ext[3] - P));
                 for (int i = 0; i < N; ++i) pos[3 * i + a] *= mu;
                 S.box[a] *= mu;
-                box[a] = S.box[a];
+                S.h[4 * a] = S.box[a];
+                S.hinv[4 * a] = 1.0 / S.box[a];
+                box[4 * a] = S.box[a];
             }
         }
         if (thermo) {

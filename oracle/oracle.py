@@ -113,6 +113,14 @@ def _masses(model, mass):
 EV_PER_AMU = 1.602176634e-19 / 1.66053906660e-27 * 1e-10
 
 
+def _box9(box):
+    """Row-major 3x3 cell H from box lengths (3,) or a (3, 3) matrix."""
+    b = np.asarray(box, dtype=np.float64)
+    if b.shape == (3,):
+        b = np.diag(b)
+    return np.ascontiguousarray(b.reshape(9))
+
+
 def _check(rc, what):
     if rc != 0:
         raise RuntimeError(f"oracle {what} failed with code {rc}")
@@ -127,7 +135,7 @@ def energy_forces_virial(model, pos, box, pbc, use_grid=True, params=None, types
     pos = _f64(pos)
     n = pos.shape[0]
     t = _types(types, n)
-    box = _f64(box)
+    box = _box9(box)
     pbc = np.ascontiguousarray(pbc, dtype=np.int32)
     E = np.zeros(1)
     F = np.zeros((n, 3))
@@ -150,7 +158,7 @@ def descriptors(model, pos, box, pbc, use_grid=True, types=None):
     t = _types(types, n)
     q = np.zeros((n, model.dim))
     _check(lib().orc_descriptors(_i(ihp), _d(dhp), _d(p), _d(s), n, _d(pos), _i(t),
-                                 _d(_f64(box)), _i(np.ascontiguousarray(pbc, dtype=np.int32)),
+                                 _d(_box9(box)), _i(np.ascontiguousarray(pbc, dtype=np.int32)),
                                  int(use_grid), _d(q)), "descriptors")
     return q
 
@@ -166,7 +174,7 @@ def forces_subset(model, pos, box, pbc, idx, types=None):
     F = np.zeros((len(idx), 3))
     U = np.zeros(len(idx))
     _check(lib().orc_forces_subset(_i(ihp), _d(dhp), _d(p), _d(s), pos.shape[0], _d(pos), _i(t),
-                                   _d(_f64(box)), _i(np.ascontiguousarray(pbc, dtype=np.int32)),
+                                   _d(_box9(box)), _i(np.ascontiguousarray(pbc, dtype=np.int32)),
                                    len(idx), idx.ctypes.data_as(C.POINTER(C.c_int64)),
                                    _d(F), _d(U)), "forces_subset")
     return F, U
@@ -205,7 +213,7 @@ def md(model, pos, vel, box, pbc, mass, dt_max, nsteps, d_max=0.0, forces=None,
     F = np.zeros((n, 3)) if forces is None else _f64(forces).copy()
     thermo = np.zeros((nsteps, 4))
     _check(lib().orc_md(_i(ihp), _d(dhp), _d(p), _d(s), n, _d(pos), _d(vel), _d(F),
-                        0 if forces is None else 1, _i(t), _d(_f64(box)),
+                        0 if forces is None else 1, _i(t), _d(_box9(box)),
                         _i(np.ascontiguousarray(pbc, dtype=np.int32)), _d(_masses(model, mass)),
                         float(dt_max), float(d_max), int(nsteps), int(use_grid), _d(thermo)),
            "md")
@@ -219,7 +227,7 @@ def neighbor_counts(pos, box, pbc, rc, mode=0, maxn=0):
     n = pos.shape[0]
     counts = np.zeros(n, np.int32)
     dist = np.zeros((n, max(maxn, 1)))
-    _check(lib().orc_neighbor_counts(n, _d(pos), _d(_f64(box)),
+    _check(lib().orc_neighbor_counts(n, _d(pos), _d(_box9(box)),
                                      _i(np.ascontiguousarray(pbc, dtype=np.int32)), float(rc),
                                      int(mode), _i(counts), int(maxn),
                                      _d(dist) if maxn > 0 else None), "neighbor_counts")
@@ -277,7 +285,8 @@ def md_ext(model, pos, vel, box, pbc, mass, dt_max, nsteps, d_max=0.0, forces=No
     s = _f64(model.scaler)
     pos = _f64(pos).copy()
     vel = _f64(vel).copy()
-    box = _f64(box).copy()
+    diag = np.asarray(box).shape == (3,)
+    box = _box9(box).copy()
     n = pos.shape[0]
     t = _types(types, n)
     F = np.zeros((n, 3)) if forces is None else _f64(forces).copy()
@@ -299,7 +308,19 @@ def md_ext(model, pos, vel, box, pbc, mass, dt_max, nsteps, d_max=0.0, forces=No
                             1 if thermostat is not None else 0,
                             group.ctypes.data_as(C.POINTER(C.c_uint8)) if group is not None
                             else None, _d(ext), _d(thermo)), "md_ext")
-    return pos, vel, F, thermo, box
+    box = box.reshape(3, 3)
+    return pos, vel, F, thermo, (np.diag(box).copy() if diag else box)
+
+
+def min_image(d, box, pbc):
+    """Displacements (M, 3) reduced to the nearest image along each periodic
+    lattice direction (fractional rounding)."""
+    H = _box9(box).reshape(3, 3)
+    d = np.array(d, dtype=np.float64, copy=True)
+    f = d @ np.linalg.inv(H)
+    per = np.asarray(pbc) > 0
+    f[:, per] -= np.round(f[:, per])
+    return f @ H
 
 
 def pka_atom(pos, box, pbc, point):
@@ -308,7 +329,10 @@ def pka_atom(pos, box, pbc, point):
     d = np.asarray(pos, dtype=np.float64) - np.asarray(point, dtype=np.float64)
     box = np.asarray(box, dtype=np.float64)
     per = np.asarray(pbc) > 0
-    d[:, per] -= box[per] * np.round(d[:, per] / box[per])
+    if box.shape == (3,):
+        d[:, per] -= box[per] * np.round(d[:, per] / box[per])
+    else:
+        d = min_image(d, box, pbc)
     return int(np.argmin(np.einsum("ij,ij->i", d, d)))
 
 
