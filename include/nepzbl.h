@@ -52,7 +52,7 @@ extern "C" {
 #define NEP_ERR_INVALID_ARG   (-1)  /* bad pointer, size, or parameter */
 #define NEP_ERR_CUDA          (-2)  /* a CUDA runtime call failed */
 #define NEP_ERR_NBR_OVERFLOW  (-3)  /* neighbour capacity exceeded and could not grow */
-#define NEP_ERR_BOX           (-4)  /* box not diagonal, not positive, or too small */
+#define NEP_ERR_BOX           (-4)  /* cell with det <= 0, non-finite, or too small */
 #define NEP_ERR_NONFINITE     (-5)  /* NaN/Inf in positions, energies or forces */
 #define NEP_ERR_ATOM_LOST     (-6)  /* reserved: atom outside any representable cell */
 #define NEP_ERR_UNSUPPORTED   (-7)  /* model sizes this build was not compiled for */
@@ -110,10 +110,13 @@ const char* nep_last_error(const nep_ctx* ctx);
 /* One force evaluation (Eq. 1-4 and the descriptor above).
  *   n_atoms      number of atoms (0 allowed; < 2^26)
  *   xyz          device double[3 * n_atoms], SoA: x[0..n), y[0..n), z[0..n) (A)
- *   box          host double[9], row-major 3x3 cell; must be diagonal.
- *                A periodic dimension needs box[d][d] >= 3 * rc_radial.  For an
- *                open dimension, box[d][d] is the extent [0, L) over which the
- *                cell grid is laid (atoms outside it are still handled).
+ *   box          host double[9], row-major 3x3 cell H whose rows are the cell
+ *                vectors a, b, c (x = s H for fractional s); det H > 0.  A
+ *                diagonal H is an orthorhombic box of lengths H[d][d]; any other
+ *                H is a triclinic cell.  A periodic direction needs a
+ *                perpendicular cell width >= 3 * rc_radial.  For an open
+ *                direction the cell spans fractional [0, 1) over which the cell
+ *                grid is laid (atoms outside it are still handled).
  *   types        device int32[n_atoms] species index in [0, n_types); an index
  *                outside is reported as NEP_ERR_INVALID_ARG
  *   pbc          host int32[3], 1 periodic, 0 open

@@ -69,7 +69,61 @@ struct Grid {
     int ld;                    // leading dimension of nbr / facc (atom capacity)
     int M;                     // neighbour slots per atom
     int ntypes;                // species (types must lie in [0, ntypes))
+    // triclinic cell: rows of h are the cell vectors, x = s h for fractional s;
+    // cells are the parallelepipeds h_a / nc_a (tric = 0: the orthorhombic
+    // fields above are used and h, hinv are diagonal)
+    int tric;
+    double h[9], hinv[9];
 };
+
+// Fractional coordinates s = x h^-1 (row vectors).
+__device__ __forceinline__ void to_frac(const Grid& g, const double (&x)[3], double (&f)[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) f[a] = x[0] * g.hinv[a] + x[1] * g.hinv[3 + a] + x[2] * g.hinv[6 + a];
+}
+
+// Nearest-image displacement (triclinic): d -= sum_a rint(s_a) h_a over periodic a.
+__device__ __forceinline__ void min_image_tric(const Grid& g, double (&d)[3])
+{
+    double f[3];
+    to_frac(g, d, f);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (!g.pbc[a]) continue;
+        const double k = rint(f[a]);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) d[b] -= k * g.h[3 * a + b];
+    }
+}
+
+// Cell of a position (triclinic) and its Cartesian offset from the cell's
+// origin: periodic fractional coordinates wrapped into [0, 1), cell indices
+// clamped to the grid (open dimensions).
+__device__ __forceinline__ void cell_tric(const Grid& g, const double (&x)[3], int (&c)[3],
+                                          double (&rel)[3])
+{
+    double f[3];
+    to_frac(g, x, f);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (g.pbc[a]) f[a] -= floor(f[a]);
+        int k = (int)floor(f[a] * g.nc[a]);
+        k = k < 0 ? 0 : (k >= g.nc[a] ? g.nc[a] - 1 : k);
+        c[a] = k;
+        f[a] -= (double)k / g.nc[a];
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b) rel[b] = f[0] * g.h[b] + f[1] * g.h[3 + b] + f[2] * g.h[6 + b];
+}
+
+// Cartesian offset of the stencil cell (oa, ob, oc) from the home cell
+// (triclinic), in double; the same expression wherever it is needed.
+__device__ __forceinline__ double stencil_off_tric(const Grid& g, int oa, int ob, int oc, int b)
+{
+    return (double)oa * g.h[b] / g.nc[0] + (double)ob * g.h[3 + b] / g.nc[1] +
+           (double)oc * g.h[6 + b] / g.nc[2];
+}
 
 // ----------------------------------------------------------------------------
 // Binning: cell of each atom, slot within the cell (atomic), counting sort
@@ -96,10 +150,16 @@ static __global__ void k_bin_count(Grid g, const double* __restrict__ x, int* __
     double p[3] = {x[i], x[g.n + i], x[2 * g.n + i]};
     int c[3];
     bool bad = false;
-    for (int d = 0; d < 3; ++d) {
+    for (int d = 0; d < 3; ++d)
         if (!isfinite(p[d])) { bad = true; p[d] = 0.0; }
-        double w;
-        c[d] = cell_coord(p[d], d, g, w);
+    if (g.tric) {
+        double rel[3];
+        cell_tric(g, p, c, rel);
+    } else {
+        for (int d = 0; d < 3; ++d) {
+            double w;
+            c[d] = cell_coord(p[d], d, g, w);
+        }
     }
     if (bad) atomicOr(status, ST_NONFINITE);
     int cell = (c[0] * g.nc[1] + c[1]) * g.nc[2] + c[2];
@@ -233,12 +293,23 @@ __global__ void k_cell_finalize(Grid g, int ncell, const int* __restrict__ start
     for (int s = b; s < e; ++s) {
         int i = perm[s];
         R rel[3];
-        for (int d = 0; d < 3; ++d) {
-            double p = x[d * g.n + i];
-            if (!isfinite(p)) p = 0.0;
-            double w;
-            cell_coord(p, d, g, w);
-            rel[d] = (R)(w - cc[d] * g.lc[d]);
+        if (g.tric) {
+            double p[3], r3[3];
+            int c3[3];
+            for (int d = 0; d < 3; ++d) {
+                p[d] = x[d * g.n + i];
+                if (!isfinite(p[d])) p[d] = 0.0;
+            }
+            cell_tric(g, p, c3, r3);
+            for (int d = 0; d < 3; ++d) rel[d] = (R)r3[d];
+        } else {
+            for (int d = 0; d < 3; ++d) {
+                double p = x[d * g.n + i];
+                if (!isfinite(p)) p = 0.0;
+                double w;
+                cell_coord(p, d, g, w);
+                rel[d] = (R)(w - cc[d] * g.lc[d]);
+            }
         }
         typename V4<R>::T q;
         q.x = rel[0]; q.y = rel[1]; q.z = rel[2];
@@ -269,7 +340,9 @@ struct RadCoef {
 // displacement is recomputed for each hit in the force kernels' form
 // (pj - pi) + offset, and pairs with r >= r_c in that form are left out
 // as they skip them.
-template <typename R, bool WQ>
+// TRIC: triclinic cells (stencil offsets are vectors; the orthorhombic
+// instantiation keeps per-axis offsets).
+template <typename R, bool WQ, bool TRIC = false>
 __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                                                    const typename V4<R>::T* __restrict__ pos4,
                                                    const int* __restrict__ cell_sorted,
@@ -302,18 +375,25 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
             int X = cx + ox;
             if (g.pbc[0]) { X += X < 0 ? ncx : 0; X -= X >= ncx ? ncx : 0; }
             else if (X < 0 || X >= ncx) continue;
-            const R px = p.x - R(ox) * lx;
+            const R px0 = p.x - R(ox) * lx;
             for (int oy = -1; oy <= 1; ++oy) {
                 int Y = cy + oy;
                 if (g.pbc[1]) { Y += Y < 0 ? ncy : 0; Y -= Y >= ncy ? ncy : 0; }
                 else if (Y < 0 || Y >= ncy) continue;
-                const R py = p.y - R(oy) * ly;
+                const R py0 = p.y - R(oy) * ly;
                 const int rowXY = (X * ncy + Y) * ncz;
                 for (int oz = -1; oz <= 1; ++oz) {
                     int Z = cz + oz;
                     if (g.pbc[2]) { Z += Z < 0 ? ncz : 0; Z -= Z >= ncz ? ncz : 0; }
                     else if (Z < 0 || Z >= ncz) continue;
-                    const R pz = p.z - R(oz) * lz;
+                    // offset of this stencil cell: the values the force
+                    // kernels add for the code (fill_stencil)
+                    R px = px0, py = py0, pz = p.z - R(oz) * lz;
+                    if constexpr (TRIC) {
+                        px = p.x - (R)stencil_off_tric(g, ox, oy, oz, 0);
+                        py = p.y - (R)stencil_off_tric(g, ox, oy, oz, 1);
+                        pz = p.z - (R)stencil_off_tric(g, ox, oy, oz, 2);
+                    }
                     const int code = (ox + 1) * 9 + (oy + 1) * 3 + (oz + 1);
                     const int c2 = rowXY + Z;
                     const int e = start[c2 + 1];
@@ -330,8 +410,14 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                             }
                             if (ang) ++na; else ++nro;
                             if constexpr (WQ) {
-                                const R fx = q.x - p.x + R(ox) * lx, fy = q.y - p.y + R(oy) * ly,
-                                        fz = q.z - p.z + R(oz) * lz;
+                                R ofx = R(ox) * lx, ofy = R(oy) * ly, ofz = R(oz) * lz;
+                                if constexpr (TRIC) {
+                                    ofx = (R)stencil_off_tric(g, ox, oy, oz, 0);
+                                    ofy = (R)stencil_off_tric(g, ox, oy, oz, 1);
+                                    ofz = (R)stencil_off_tric(g, ox, oy, oz, 2);
+                                }
+                                const R fx = q.x - p.x + ofx, fy = q.y - p.y + ofy,
+                                        fz = q.z - p.z + ofz;
                                 const R f2 = fx * fx + fy * fy + fz * fz;
                                 if (f2 < rcR2) {
                                     const R rr = f2 * nepm::nep_rsqrt(f2);
@@ -391,11 +477,19 @@ static __global__ void k_skin_check(Grid g, const double* __restrict__ x,
     bool moved = false;
     if (i < g.n) {
         double d2 = 0.0;
+        if (g.tric) {
+            double d[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            double d = x[(size_t)a * g.n + i] - xref[(size_t)a * g.n + i];
-            if (g.pbc[a]) d -= g.L[a] * rint(d * g.invL[a]);
-            d2 += d * d;
+            for (int a = 0; a < 3; ++a) d[a] = x[(size_t)a * g.n + i] - xref[(size_t)a * g.n + i];
+            min_image_tric(g, d);
+            d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        } else {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                double d = x[(size_t)a * g.n + i] - xref[(size_t)a * g.n + i];
+                if (g.pbc[a]) d -= g.L[a] * rint(d * g.invL[a]);
+                d2 += d * d;
+            }
         }
         moved = !(d2 <= thr2);   // NaN also forces a rebuild
     }
@@ -430,11 +524,23 @@ __global__ void k_refresh_pos4(Grid g, const int* __restrict__ perm,
     const int c = cell_sorted[k];
     const int cc[3] = {c / (g.nc[2] * g.nc[1]), (c / g.nc[2]) % g.nc[1], c % g.nc[2]};
     R rel[3];
+    if (g.tric) {
+        double d[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        double d = x[(size_t)a * g.n + i] - cc[a] * g.lc[a];
-        if (g.pbc[a]) d -= g.L[a] * rint(d * g.invL[a]);
-        rel[a] = (R)d;
+        for (int b = 0; b < 3; ++b)
+            d[b] = x[(size_t)b * g.n + i] - ((double)cc[0] * g.h[b] / g.nc[0] +
+                                             (double)cc[1] * g.h[3 + b] / g.nc[1] +
+                                             (double)cc[2] * g.h[6 + b] / g.nc[2]);
+        min_image_tric(g, d);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) rel[b] = (R)d[b];
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double d = x[(size_t)a * g.n + i] - cc[a] * g.lc[a];
+            if (g.pbc[a]) d -= g.L[a] * rint(d * g.invL[a]);
+            rel[a] = (R)d;
+        }
     }
     typename V4<R>::T q = pos4[k];
     q.x = rel[0]; q.y = rel[1]; q.z = rel[2];
@@ -508,9 +614,15 @@ __device__ __forceinline__ void fill_stencil(typename V4<R>::T* tab, const Grid&
         int code = threadIdx.x;
         int a = code / 9, b = (code / 3) % 3, c = code % 3;
         typename V4<R>::T o;
-        o.x = (R)((a - 1) * g.lc[0]);
-        o.y = (R)((b - 1) * g.lc[1]);
-        o.z = (R)((c - 1) * g.lc[2]);
+        if (g.tric) {
+            o.x = (R)stencil_off_tric(g, a - 1, b - 1, c - 1, 0);
+            o.y = (R)stencil_off_tric(g, a - 1, b - 1, c - 1, 1);
+            o.z = (R)stencil_off_tric(g, a - 1, b - 1, c - 1, 2);
+        } else {
+            o.x = (R)((a - 1) * g.lc[0]);
+            o.y = (R)((b - 1) * g.lc[1]);
+            o.z = (R)((c - 1) * g.lc[2]);
+        }
         o.w = R(0);
         tab[code] = o;
     }
@@ -834,9 +946,10 @@ __global__ void __launch_bounds__(TILE) k_nep(const Model<R> P, const Grid g,
                     const int j_caller = perm[m];
                     for (int a = 0; a < 3; ++a) {
                         double t = x64[a * g.n + j_caller] - x64[a * g.n + i_caller];
-                        if (g.pbc[a]) t -= g.L[a] * rint(t * g.invL[a]);
+                        if (!g.tric && g.pbc[a]) t -= g.L[a] * rint(t * g.invL[a]);
                         d64[a] = t;
                     }
+                    if (g.tric) min_image_tric(g, d64);
                 } else {
                     d64[0] = (double)dx; d64[1] = (double)dy; d64[2] = (double)dz;
                 }
@@ -1259,9 +1372,10 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
                     const int j_caller = perm[m];
                     for (int a = 0; a < 3; ++a) {
                         double t = x64[a * g.n + j_caller] - x64[a * g.n + i_caller];
-                        if (g.pbc[a]) t -= g.L[a] * rint(t * g.invL[a]);
+                        if (!g.tric && g.pbc[a]) t -= g.L[a] * rint(t * g.invL[a]);
                         d64[a] = t;
                     }
+                    if (g.tric) min_image_tric(g, d64);
                 } else {
                     d64[0] = (double)dx; d64[1] = (double)dy; d64[2] = (double)dz;
                 }
@@ -1576,15 +1690,31 @@ static __global__ void k_kick_drift(Grid g, MassTab mt, const int32_t* __restric
     if (i >= g.n) return;
     const double dt = thermo[TH_DT];
     const double acc = mt.acc[species_of(mt, types, i)];
+    double xn[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         size_t o = (size_t)a * g.n + i;
         double vv = v[o] + 0.5 * dt * acc * F[o];
         double xx = x[o] + dt * vv;
-        if (g.pbc[a]) xx -= g.L[a] * floor(xx * g.invL[a]);
+        if (!g.tric && g.pbc[a]) xx -= g.L[a] * floor(xx * g.invL[a]);
         v[o] = vv;
-        x[o] = xx;
+        xn[a] = xx;
     }
+    if (g.tric) {
+        // x -= sum_a floor(s_a) h_a over periodic a
+        double f[3];
+        to_frac(g, xn, f);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (!g.pbc[a]) continue;
+            const double k = floor(f[a]);
+            if (k != 0.0)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) xn[b] -= k * g.h[3 * a + b];
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[(size_t)a * g.n + i] = xn[a];
 }
 
 // v += dt/2 F/m and per-block (sum m v^2, max |v|^2, and with `tensor` the
@@ -1842,22 +1972,23 @@ static __global__ void k_scale_positions(int n, const double* __restrict__ therm
 // PKA: per-block nearest atom to p (minimum image in periodic dimensions),
 // ties to the lowest index; out[2 * b] = d^2, out[2 * b + 1] = index.
 static __global__ void __launch_bounds__(256) k_nearest(int n, const double* __restrict__ x,
-                                                       double3 p, double3 L, int3 pbc,
+                                                       double3 p, const Grid g,
                                                        double* __restrict__ out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double best = 1e300;
     int bi = n;
     if (i < n) {
-        const double c[3] = {p.x, p.y, p.z}, Lb[3] = {L.x, L.y, L.z};
-        const int per[3] = {pbc.x, pbc.y, pbc.z};
-        double r2 = 0.0;
-        for (int a = 0; a < 3; ++a) {
-            double d = x[(size_t)a * n + i] - c[a];
-            if (per[a]) d -= Lb[a] * rint(d / Lb[a]);
-            r2 += d * d;
+        const double c[3] = {p.x, p.y, p.z};
+        double d[3];
+        for (int a = 0; a < 3; ++a) d[a] = x[(size_t)a * n + i] - c[a];
+        if (g.tric) {
+            min_image_tric(g, d);
+        } else {
+            for (int a = 0; a < 3; ++a)
+                if (g.pbc[a]) d[a] -= g.L[a] * rint(d[a] / g.L[a]);
         }
-        best = r2;
+        best = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
         bi = i;
     }
     __shared__ double sd[256];

@@ -269,23 +269,46 @@ static int make_grid(nep_ctx* ctx, int64_t n, const double box[9], const int32_t
 {
     const double rc_cell = rcell > 0.0 ? rcell : ctx->rcR;
     memset(&g, 0, sizeof(Grid));
+    for (int t = 0; t < 9; ++t)
+        if (!isfinite(box[t])) return fail(ctx, NEP_ERR_BOX, "non-finite cell entry");
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b)
-            if (a != b && box[3 * a + b] != 0.0)
-                return fail(ctx, NEP_ERR_BOX, "only diagonal (orthorhombic) boxes are supported");
+            if (a != b && box[3 * a + b] != 0.0) g.tric = 1;
+    // H (rows = cell vectors), its inverse, and the perpendicular widths V / |h_b x h_c|
+    const double* h = box;
+    const double c00 = h[4] * h[8] - h[5] * h[7], c01 = h[5] * h[6] - h[3] * h[8],
+                 c02 = h[3] * h[7] - h[4] * h[6];
+    const double det = h[0] * c00 + h[1] * c01 + h[2] * c02;
+    if (!(det > 0.0)) return fail(ctx, NEP_ERR_BOX, "cell volume det(H) = %g must be positive", det);
+    for (int t = 0; t < 9; ++t) g.h[t] = h[t];
+    g.hinv[0] = c00 / det;
+    g.hinv[1] = (h[2] * h[7] - h[1] * h[8]) / det;
+    g.hinv[2] = (h[1] * h[5] - h[2] * h[4]) / det;
+    g.hinv[3] = c01 / det;
+    g.hinv[4] = (h[0] * h[8] - h[2] * h[6]) / det;
+    g.hinv[5] = (h[2] * h[3] - h[0] * h[5]) / det;
+    g.hinv[6] = c02 / det;
+    g.hinv[7] = (h[1] * h[6] - h[0] * h[7]) / det;
+    g.hinv[8] = (h[0] * h[4] - h[1] * h[3]) / det;
     for (int a = 0; a < 3; ++a) {
-        double L = box[4 * a];
-        if (!(L > 0.0) || !isfinite(L)) return fail(ctx, NEP_ERR_BOX, "box length %d is %g", a, L);
-        int nc = (int)floor(L / rc_cell);
+        const double* u = h + 3 * ((a + 1) % 3);
+        const double* v = h + 3 * ((a + 2) % 3);
+        const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2],
+                     cz = u[0] * v[1] - u[1] * v[0];
+        // width along lattice direction a (the box length for a diagonal H)
+        const double W = g.tric ? det / sqrt(cx * cx + cy * cy + cz * cz) : box[4 * a];
+        if (!(W > 0.0)) return fail(ctx, NEP_ERR_BOX, "cell width %d is %g", a, W);
+        int nc = (int)floor(W / rc_cell);
         if (pbc[a]) {
             if (nc < 3)
                 return fail(ctx, NEP_ERR_BOX,
-                            "periodic box length %g < 3 x %g A (cell-list path; small boxes go "
-                            "through the batched entry points)", L, rc_cell);
+                            "periodic cell width %g < 3 x %g A (cell-list path; small boxes go "
+                            "through the batched entry points)", W, rc_cell);
         } else if (nc < 1) {
             nc = 1;
         }
         if (nc > 1024) nc = 1024;
+        const double L = box[4 * a];
         g.nc[a] = nc;
         g.pbc[a] = pbc[a] ? 1 : 0;
         g.lc[a] = L / nc;
@@ -372,7 +395,9 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     rq.inv_rcR = P.inv_rcR;
     for (int t = 0; t < NR * KR; ++t) rq.hR[t] = P.hR[t];
     for (int t = 0; t < NR; ++t) rq.CR[t] = P.CR[t];
-    (fuse_q ? k_neighbors<R, true> : k_neighbors<R, false>)<<<(n + 127) / 128, 128, 0, s>>>(
+    auto kn = g.tric ? (fuse_q ? k_neighbors<R, true, true> : k_neighbors<R, false, true>)
+                     : (fuse_q ? k_neighbors<R, true, false> : k_neighbors<R, false, false>);
+    kn<<<(n + 127) / 128, 128, 0, s>>>(
         g, (R)(rl * rl), (R)(ra * ra), (const typename V4<R>::T*)ctx->pos4, ctx->cell_sorted,
         ctx->start, ctx->nbr, ctx->cnt, ctx->status, ctx->status + 1, ctx->pairs, gate, rq,
         (R*)ctx->qr);
@@ -973,6 +998,10 @@ static int md_steps_barostat(nep_ctx* ctx, nep_md_state* st, int n_steps, cudaSt
 {
     const int64_t n = st->n_atoms;
     const size_t bytes = sizeof(double) * 3 * (size_t)n;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            if (a != b && st->box[3 * a + b] != 0.0)
+                return fail(ctx, NEP_ERR_UNSUPPORTED, "the barostat scales orthorhombic boxes only");
     double h_box[3] = {st->box[0], st->box[4], st->box[8]};
     CK(cudaMemcpyAsync(ctx->d_box, h_box, sizeof(h_box), cudaMemcpyHostToDevice, s));
     const int3 pbc = make_int3(st->pbc[0] ? 1 : 0, st->pbc[1] ? 1 : 0, st->pbc[2] ? 1 : 0);
@@ -1864,8 +1893,7 @@ int nep_pka(nep_ctx* ctx, nep_md_state* st, const double point[3], double energy
         (rc = check_device_ptr(ctx, st->types, "types")))
         return rc;
     for (int a = 0; a < 3; ++a)
-        if (!(st->box[4 * a] > 0) || !isfinite(point[a]))
-            return fail(ctx, NEP_ERR_INVALID_ARG, "bad box or point");
+        if (!isfinite(point[a])) return fail(ctx, NEP_ERR_INVALID_ARG, "bad point");
     cudaStream_t s = (cudaStream_t)stream;
     const int tb = 256, nb = (int)((n + tb - 1) / tb);
     const size_t need = sizeof(double) * 2 * (size_t)nb;
@@ -1876,9 +1904,9 @@ int nep_pka(nep_ctx* ctx, nep_md_state* st, const double point[3], double energy
         ctx->pka_cap = need;
     }
     if (!ctx->pka_atom) CK(cudaMalloc(&ctx->pka_atom, sizeof(long long)));
-    k_nearest<<<nb, tb, 0, s>>>((int)n, st->xyz, make_double3(point[0], point[1], point[2]),
-                                make_double3(st->box[0], st->box[4], st->box[8]),
-                                make_int3(st->pbc[0] ? 1 : 0, st->pbc[1] ? 1 : 0, st->pbc[2] ? 1 : 0),
+    Grid gp;
+    if ((rc = make_grid(ctx, n, st->box, st->pbc, gp))) return rc;
+    k_nearest<<<nb, tb, 0, s>>>((int)n, st->xyz, make_double3(point[0], point[1], point[2]), gp,
                                 ctx->pka_part);
     k_pka_set<<<1, 32, 0, s>>>(ctx->pka_part, nb, (int)n, ctx->mt, st->types, energy,
                                make_double3(direction[0] / un, direction[1] / un, direction[2] / un),

@@ -53,8 +53,9 @@ class Structure:
     """Atoms in an orthorhombic box.
 
     pos:   (N, 3) float64 positions in A
-    box:   (3,) float64 box lengths in A; for an open dimension it is the extent
-           of the region in which the atoms start (vacuum included)
+    box:   (3,) float64 box lengths in A (orthorhombic), or (3, 3) float64 cell
+           whose rows are the cell vectors (triclinic); for an open dimension it
+           is the extent of the region in which the atoms start
     pbc:   (3,) int32, 1 = periodic, 0 = open
     types: (N,) int32 species index (0 for W)
     vel:   (N, 3) float64 velocities in A/fs, or None
@@ -256,6 +257,20 @@ def hea(ncell: int = 40, a: float = 3.23, temperature: float = 300.0,
     s.vel = maxwell_boltzmann(rng, s.n, temperature, masses[s.types])
     s.name = f"hea_WMoTaNb_{s.n}"
     return s
+
+
+def triclinic(ncell: int = 7, shear: float = 3.0, sigma: float = 0.05, seed: int = 81,
+              pbc=(1, 1, 1)) -> Structure:
+    """bcc W in a skewed periodic cell: H = a ncell I plus off-diagonal entries
+    drawn from U(-shear, shear) (seed), the crystal's fractional sites mapped
+    into it, then sigma displacements (same generator)."""
+    rng = np.random.default_rng(seed)
+    L = ncell * A_W
+    H = np.diag([L] * 3) + rng.uniform(-shear, shear, (3, 3)) * (1 - np.eye(3))
+    frac = bcc(ncell, ncell, ncell) / L
+    pos = frac @ H + rng.normal(0.0, sigma, size=frac.shape)
+    return Structure(pos, H, np.array(pbc, np.int32), np.zeros(len(pos), np.int32),
+                     name=f"triclinic_bcc_W_{len(pos)}")
 
 
 def border_group(s: Structure, width: float = 3 * A_W) -> np.ndarray:

@@ -108,8 +108,8 @@ def test_error_codes():
     m = nep("fp32")
     s = I.small_box((6, 6, 6))
     x = N.to_device_soa(s.pos)
-    with pytest.raises(N.NepError) as e:
-        m.compute(x, np.array([[19.0, 1.0, 0], [0, 19.0, 0], [0, 0, 19.0]]), [1, 1, 1])
+    with pytest.raises(N.NepError) as e:      # left-handed cell (det H < 0)
+        m.compute(x, np.array([[0, 19.0, 0], [19.0, 1.0, 0], [0, 0, 19.0]]), [1, 1, 1])
     assert e.value.code == N.NEP_ERR_BOX
     with pytest.raises(N.NepError) as e:
         m.compute(x, [12.0, 19.0, 19.0], [1, 1, 1])          # < 3 r_c periodic

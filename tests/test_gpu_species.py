@@ -105,12 +105,14 @@ def test_one_species_model_equals_identical_blocks():
     m2.scaler = w.scaler
     s = _wmo_box(seed=321, close=False)
     x = N.to_device_soa(s.pos)
-    for prec, tol in (("fp32", 2e-6), ("fp64", 1e-10)):
+    # FP32: the two paths sum the radial basis in different orders (per
+    # neighbour species, or inside the neighbour search)
+    for prec, tol, tol_e in (("fp32", 2e-6, 2e-8), ("fp64", 1e-10, 1e-12)):
         a = N.NEP(w, prec)
         b = N.NEP(m2, prec)
         E1, F1, W1, _ = a.compute(x, s.box, s.pbc)
         E2, F2, W2, _ = b.compute(x, s.box, s.pbc, types=_types_dev(s))
-        assert abs(E1 - E2) / s.n < 1e-9
+        assert abs(E1 - E2) / s.n < tol_e
         assert float((F1 - F2).abs().max()) < tol
         a.close()
         b.close()
