@@ -272,10 +272,12 @@ typedef struct nep_batch {
                                     configuration; offsets[n_configs] = n_atoms */
     const double* boxes;         /* host double[3 * n_configs]: periodic orthorhombic box
                                     lengths, each >= rc_radial */
-    const int32_t* types;        /* device int32[n_atoms] (all 0: one species) */
+    const int32_t* types;        /* device int32[n_atoms] species in [0, n_types) (read
+                                    only for models of several species) */
 } nep_batch;
-/* Each configuration holds 1..512 atoms.  The batched entry points support
- * one species (n_types = 1); other models get NEP_ERR_UNSUPPORTED. */
+/* Each configuration holds 1..512 atoms.  With several species the gradient
+ * has n_params = 961 + 90 T^2 entries in the layout of nep_params.params
+ * (coefficient block (t_i, t_j) of every ordered species pair). */
 
 /* Training targets of a batch (Sec. III.A: every structure has a target
  * energy and forces, some a target virial). */

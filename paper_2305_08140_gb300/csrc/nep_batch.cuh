@@ -72,8 +72,14 @@ struct Batch {
     double wv, nv;             // virial weight, number of configurations with a target
     const double* dLdW;        // [S][9] (backward), or nullptr
     double* lpart;             // [S][3] energy, force and virial loss of each configuration
-    double* gpart;             // [S][NP] gradient of each configuration
+    double* gpart;             // [S][np] gradient of each configuration
     void* scr;                 // [ntot][BSTRIDE] backward scratch
+    // several species: T types, the pair coefficient table [T * T][CSTR] (R),
+    // species of every atom, and the parameter count 961 + 90 T^2
+    int T;
+    const void* coef;
+    const int* types;
+    int np;
 };
 
 // Sum of v over the CTA, in a fixed order; every thread gets the result.
@@ -182,7 +188,23 @@ __device__ __forceinline__ void pair_dir(const PairGeom<R>& g, const R (*se)[BMA
 
 // Forward of local atom i: descriptor, network, pair forces scattered into
 // the shared accumulators; returns U_i (NEP + half ZBL).
+// Pair coefficient block (t_i, t_j) with several species, nullptr otherwise.
+template <typename R, bool MS>
+__device__ __forceinline__ const R* pair_coef(const Batch& b, int ti, int tj)
+{
+    if constexpr (MS) return (const R*)b.coef + (size_t)(ti * b.T + tj) * CSTR;
+    else return nullptr;
+}
+
 template <typename R>
+__device__ __forceinline__ int species_at(const typename V4<R>::T& p)
+{
+    return (int)p.w;
+}
+
+// MS: coefficients of every pair from its species block (pair_coef); the
+// radial descriptor and radial force per pair instead of through basis sums.
+template <typename R, bool MS = false>
 __device__ __forceinline__ double batch_atom_forward(const Model<R>& P, const Batch& b,
                                                      long long a0, int i,
                                                      const typename V4<R>::T* spos,
@@ -195,10 +217,14 @@ __device__ __forceinline__ double batch_atom_forward(const Model<R>& P, const Ba
     const int2 c2 = b.cnt[col];
     const int na = c2.x, nro = c2.y, tot = na + nro, M = b.M;
     const typename V4<R>::T pi = spos[i];
+    const int ti = MS ? species_at<R>(pi) : 0;
     R Sb[KR];
     R A[NA][NLM];
+    R qR[NR];
 #pragma unroll
     for (int kk = 0; kk < KR; ++kk) Sb[kk] = R(0);
+#pragma unroll
+    for (int n = 0; n < NR; ++n) qR[n] = R(0);
 #pragma unroll
     for (int n = 0; n < NA; ++n)
 #pragma unroll
@@ -206,12 +232,43 @@ __device__ __forceinline__ double batch_atom_forward(const Model<R>& P, const Ba
     for (int s = 0; s < tot; ++s) {
         const int ent = b.nbr[(size_t)slot_of(s, na, nro, M) * b.ntot + col];
         const PairGeom<R> g = pair_geom<R>(ent, pi, spos, s_off);
-        desc_pair<R>(P, g.dx, g.dy, g.dz, g.r, g.inv_r, s < na, Sb, A);
+        if constexpr (MS) {
+            const R* cs = pair_coef<R, MS>(b, ti, species_at<R>(spos[g.j]));
+            R T[KR], dT[KR], fc, dfc, dxdr;
+            nepm::cheb<KR, false>(g.r, P.inv_rcR, T, dT, fc, dfc, dxdr);
+#pragma unroll
+            for (int n = 0; n < NR; ++n) {
+                R a = cs[C_RAD + NR * KR + n];
+#pragma unroll
+                for (int kk = 0; kk < KR; ++kk) a += cs[C_RAD + n * KR + kk] * T[kk];
+                qR[n] += fc * a;
+            }
+            if (s < na) {
+                nepm::cheb<KA, false>(g.r, P.inv_rcA, T, dT, fc, dfc, dxdr);
+                R Y[NLM];
+                nepm::harmonics(g.ux, g.uy, g.uz, Y);
+#pragma unroll
+                for (int n = 0; n < NA; ++n) {
+                    R a = cs[C_ANG + NA * KA + n];
+#pragma unroll
+                    for (int kk = 0; kk < KA; ++kk) a += cs[C_ANG + n * KA + kk] * T[kk];
+                    const R gn = fc * a;
+#pragma unroll
+                    for (int lm = 0; lm < NLM; ++lm) A[n][lm] += gn * Y[lm];
+                }
+            }
+        } else {
+            desc_pair<R>(P, g.dx, g.dy, g.dz, g.r, g.inv_r, s < na, Sb, A);
+        }
     }
-    R qR[NR];
-    radial_q<R>(P, Sb, qR);
-    R bR[KR], B0;
-    const R U = network_adjoint<R>(P, qR, A, bR, B0);
+    R bR[KR], B0, aR[NR];
+    R U;
+    if constexpr (MS) {
+        U = network_adjoint_core<R>(P, qR, A, aR);
+    } else {
+        radial_q<R>(P, Sb, qR);
+        U = network_adjoint<R>(P, qR, A, bR, B0);
+    }
     double ez = 0.0;
     typename A_::T fi[3] = {0, 0, 0};
     bad |= !isfinite(U);
@@ -219,7 +276,33 @@ __device__ __forceinline__ double batch_atom_forward(const Model<R>& P, const Ba
         const int ent = b.nbr[(size_t)slot_of(s, na, nro, M) * b.ntot + col];
         const PairGeom<R> g = pair_geom<R>(ent, pi, spos, s_off);
         R fx, fy, fz;
-        force_pair<R>(P, g.r, g.inv_r, g.ux, g.uy, g.uz, s < na, A, bR, B0, fx, fy, fz);
+        int tj = 0;
+        if constexpr (MS) {
+            tj = species_at<R>(spos[g.j]);
+            const R* cs = pair_coef<R, MS>(b, ti, tj);
+            // radial: sum_n dU/dq_n g_n'(r) along u
+            R T[KR], dT[KR], fc, dfc, dxdr;
+            nepm::cheb<KR, true>(g.r, P.inv_rcR, T, dT, fc, dfc, dxdr);
+            R fs = R(0);
+#pragma unroll
+            for (int n = 0; n < NR; ++n) {
+                R a = cs[C_RAD + NR * KR + n], c = R(0);
+#pragma unroll
+                for (int kk = 0; kk < KR; ++kk) {
+                    a += cs[C_RAD + n * KR + kk] * T[kk];
+                    c += cs[C_RAD + n * KR + kk] * dT[kk];
+                }
+                fs += aR[n] * (dfc * a + fc * dxdr * c);
+            }
+            fx = fs * g.ux; fy = fs * g.uy; fz = fs * g.uz;
+            if (s < na) {
+                R ax, ay, az;
+                force_pair_ang<R>(P, g.r, g.inv_r, g.ux, g.uy, g.uz, A, ax, ay, az, cs + C_ANG);
+                fx += ax; fy += ay; fz += az;
+            }
+        } else {
+            force_pair<R>(P, g.r, g.inv_r, g.ux, g.uy, g.uz, s < na, A, bR, B0, fx, fy, fz);
+        }
         bad |= !isfinite(fx + fy + fz);
         typename A_::T cx = A_::conv(fx), cy = A_::conv(fy), cz = A_::conv(fz);
         const double d64[3] = {(double)g.dx, (double)g.dy, (double)g.dz};
@@ -228,7 +311,9 @@ __device__ __forceinline__ double batch_atom_forward(const Model<R>& P, const Ba
             const double r64 = sqrt(d64[0] * d64[0] + d64[1] * d64[1] + d64[2] * d64[2]);
             if (r64 < P.zbl_rr2) {
                 double Uz, dUz;
-                zbl_pair(r64, P.zbl_k, P.zbl_inv_a, P.zbl_r1, P.zbl_rr2, Uz, dUz);
+                const int pz = MS ? ti * b.T + tj : 0;
+                zbl_pair(r64, MS ? P.zbl_kp[pz] : P.zbl_k, MS ? P.zbl_inv_ap[pz] : P.zbl_inv_a,
+                         P.zbl_r1, P.zbl_rr2, Uz, dUz);
                 ez += 0.5 * Uz;
                 const double c = 0.5 * dUz / r64;
                 cx += A_::convd(c * d64[0]);
@@ -256,7 +341,7 @@ __device__ __forceinline__ double batch_atom_forward(const Model<R>& P, const Ba
 
 // Backward, first pass for local atom i: descriptor q, its tangent q-dot along
 // the residual field, the network quantities; all into the atom's scratch row.
-template <typename R>
+template <typename R, bool MS = false>
 __device__ __forceinline__ void batch_atom_tangent(const Model<R>& P, const Batch& b, long long a0,
                                                    int i, double eps,
                                                    const typename V4<R>::T* spos,
@@ -267,6 +352,7 @@ __device__ __forceinline__ void batch_atom_tangent(const Model<R>& P, const Batc
     const int2 c2 = b.cnt[col];
     const int na = c2.x, nro = c2.y, tot = na + nro, M = b.M;
     const typename V4<R>::T pi = spos[i];
+    const int ti = MS ? species_at<R>(pi) : 0;
     const R eix = se[0][i], eiy = se[1][i], eiz = se[2][i];
     R* row = (R*)b.scr + col * BSTRIDE;
     R q[D], qd[D];
@@ -281,13 +367,15 @@ __device__ __forceinline__ void batch_atom_tangent(const Model<R>& P, const Batc
         const R ud = g.ux * vx + g.uy * vy + g.uz * vz;
         R T[KR], dT[KR], fc, dfc, dxdr;
         nepm::cheb<KR, true>(g.r, P.inv_rcR, T, dT, fc, dfc, dxdr);
+        const R* cs = pair_coef<R, MS>(b, ti, MS ? species_at<R>(spos[g.j]) : 0);
 #pragma unroll
         for (int n = 0; n < NR; ++n) {
-            R a = P.CR[n], c = R(0);
+            R a = MS ? cs[C_RAD + NR * KR + n] : P.CR[n], c = R(0);
 #pragma unroll
             for (int kk = 0; kk < KR; ++kk) {
-                a += P.hR[n * KR + kk] * T[kk];
-                c += P.hR[n * KR + kk] * dT[kk];
+                const R h = MS ? cs[C_RAD + n * KR + kk] : P.hR[n * KR + kk];
+                a += h * T[kk];
+                c += h * dT[kk];
             }
             q[n] += fc * a;
             qd[n] += (dfc * a + fc * dxdr * c) * ud;
@@ -307,11 +395,13 @@ __device__ __forceinline__ void batch_atom_tangent(const Model<R>& P, const Batc
             const R ud = g.ux * ddx + g.uy * ddy + g.uz * ddz;
             R T[KA], dT[KA], fc, dfc, dxdr;
             nepm::cheb<KA, true>(g.r, P.inv_rcA, T, dT, fc, dfc, dxdr);
-            R a = P.CA[n], c = R(0);
+            const R* cs = pair_coef<R, MS>(b, ti, MS ? species_at<R>(spos[g.j]) : 0);
+            R a = MS ? cs[C_ANG + NA * KA + n] : P.CA[n], c = R(0);
 #pragma unroll
             for (int kk = 0; kk < KA; ++kk) {
-                a += P.hA[n * KA + kk] * T[kk];
-                c += P.hA[n * KA + kk] * dT[kk];
+                const R h = MS ? cs[C_ANG + n * KA + kk] : P.hA[n * KA + kk];
+                a += h * T[kk];
+                c += h * dT[kk];
             }
             const R gn = fc * a, dgn = dfc * a + fc * dxdr * c;
             R Y[NLM], Dd[NLM];
@@ -386,17 +476,21 @@ __device__ __forceinline__ void batch_atom_tangent(const Model<R>& P, const Batc
 
 // Radial basis-coefficient gradient contribution of local atom i:
 // g[n][k] += p_n f_k(r) - a_n f'_k(r) (u . dd).
-template <typename R>
+// With several species: only atoms of species ti_sel and their neighbours of
+// species tj_sel contribute (the gradient block (ti_sel, tj_sel)).
+template <typename R, bool MS = false>
 __device__ __forceinline__ void batch_atom_grad_cR(const Model<R>& P, const Batch& b, long long a0,
                                                    int i, const typename V4<R>::T* spos,
                                                    const typename V4<R>::T* s_off,
                                                    const R (*se)[BMAXA], const R* G,
-                                                   R (&gR)[NR * KR])
+                                                   R (&gR)[NR * KR], int ti_sel = 0,
+                                                   int tj_sel = 0)
 {
     const size_t col = (size_t)(a0 + i);
     const int2 c2 = b.cnt[col];
     const int na = c2.x, nro = c2.y, tot = na + nro, M = b.M;
     const typename V4<R>::T pi = spos[i];
+    if (MS && species_at<R>(pi) != ti_sel) return;
     const R eix = se[0][i], eiy = se[1][i], eiz = se[2][i];
     const R* row = (const R*)b.scr + col * BSTRIDE;
     R p[NR], a[NR];
@@ -404,6 +498,7 @@ __device__ __forceinline__ void batch_atom_grad_cR(const Model<R>& P, const Batc
     for (int n = 0; n < NR; ++n) { p[n] = row[BS_P + n]; a[n] = row[BS_AV + n]; }
     for (int s = 0; s < tot; ++s) {
         const int ent = b.nbr[(size_t)slot_of(s, na, nro, M) * b.ntot + col];
+        if (MS && species_at<R>(spos[ent >> 5]) != tj_sel) continue;
         const PairGeom<R> g = pair_geom<R>(ent, pi, spos, s_off);
         R vx, vy, vz;
         pair_dir<R>(g, se, eix, eiy, eiz, G, vx, vy, vz);
@@ -421,16 +516,17 @@ __device__ __forceinline__ void batch_atom_grad_cR(const Model<R>& P, const Batc
 }
 
 // Angular basis-coefficient gradient of channel n for local atom i.
-template <typename R>
+template <typename R, bool MS = false>
 __device__ __forceinline__ void batch_atom_grad_cA(const Model<R>& P, const Batch& b, long long a0,
                                                    int i, int n, const typename V4<R>::T* spos,
                                                    const typename V4<R>::T* s_off,
                                                    const R (*se)[BMAXA], const R* G,
-                                                   R (&gA)[KA])
+                                                   R (&gA)[KA], int ti_sel = 0, int tj_sel = 0)
 {
     const size_t col = (size_t)(a0 + i);
     const int na = b.cnt[col].x;
     const typename V4<R>::T pi = spos[i];
+    if (MS && species_at<R>(pi) != ti_sel) return;
     const R eix = se[0][i], eiy = se[1][i], eiz = se[2][i];
     const R* row = (const R*)b.scr + col * BSTRIDE;
     // alpha = dPhi/dA, beta = dPhi/dA-dot for this channel
@@ -465,6 +561,7 @@ __device__ __forceinline__ void batch_atom_grad_cA(const Model<R>& P, const Batc
     }
     for (int s = 0; s < na; ++s) {
         const int ent = b.nbr[(size_t)s * b.ntot + col];
+        if (MS && species_at<R>(spos[ent >> 5]) != tj_sel) continue;
         const PairGeom<R> g = pair_geom<R>(ent, pi, spos, s_off);
         R ddx, ddy, ddz;
         pair_dir<R>(g, se, eix, eiy, eiz, G, ddx, ddy, ddz);
@@ -494,7 +591,7 @@ __device__ __forceinline__ void batch_atom_grad_cA(const Model<R>& P, const Batc
 }
 
 // The persistent batched kernel.
-template <typename R, int MODE, int BT>
+template <typename R, int MODE, int BT, bool MS = false>
 __global__ void __launch_bounds__(BT) k_batch(const Model<R> P, const Batch b)
 {
     using P4 = typename V4<R>::T;
@@ -528,6 +625,14 @@ __global__ void __launch_bounds__(BT) k_batch(const Model<R> P, const Batch b)
                 p[d] = v - L[d] * floor(v / L[d]);
             }
             q.x = (R)p[0]; q.y = (R)p[1]; q.z = (R)p[2]; q.w = R(0);
+            if (MS) {
+                int t = b.types[a0 + i];
+                if (t < 0 || t >= b.T) {
+                    atomicOr(b.status, ST_BADTYPE);
+                    t = 0;
+                }
+                q.w = (R)t;
+            }
             spos[i] = q;
             sF[0][i] = 0; sF[1][i] = 0; sF[2][i] = 0;
         }
@@ -552,7 +657,7 @@ __global__ void __launch_bounds__(BT) k_batch(const Model<R> P, const Batch b)
             for (int t = 0; t < 9; ++t) w[t] = 0.0;
             bool bad = false;
             for (int i = threadIdx.x; i < N; i += BT)
-                esum += batch_atom_forward<R>(P, b, a0, i, spos, s_off, sF, bad, w);
+                esum += batch_atom_forward<R, MS>(P, b, a0, i, spos, s_off, sF, bad, w);
             if (bad) atomicOr(b.status, ST_NONFINITE);
             const double E = block_sum<BT>(esum, sh);   // also orders the force scatter
             if (threadIdx.x == 0) b.E[cfg] = E;
@@ -605,9 +710,9 @@ __global__ void __launch_bounds__(BT) k_batch(const Model<R> P, const Batch b)
         }
         __syncthreads();
         if (MODE != MODE_FORWARD) {
-            double* gp = b.gpart + (size_t)cfg * NP;
+            double* gp = b.gpart + (size_t)cfg * b.np;
             for (int i = threadIdx.x; i < N; i += BT)
-                batch_atom_tangent<R>(P, b, a0, i, eps, spos, s_off, se, sG);
+                batch_atom_tangent<R, MS>(P, b, a0, i, eps, spos, s_off, se, sG);
             __syncthreads();
             // network weights: G_W = sum_i u (x) q - v (x) q-dot; b0, w1, b1
             const R* scr = (const R*)b.scr;
@@ -631,31 +736,40 @@ __global__ void __launch_bounds__(BT) k_batch(const Model<R> P, const Batch b)
                 }
                 gp[e] = acc;
             }
-            // radial basis coefficients
-            {
+            // radial basis coefficients (several species: one pass per
+            // block (centre species, neighbour species))
+            const int TT = MS ? b.T : 1;
+            const int off_ca = OFF_CR + TT * TT * NR * KR;
+#pragma unroll 1
+            for (int blk = 0; blk < TT * TT; ++blk) {
                 R gR[NR * KR];
 #pragma unroll
                 for (int t = 0; t < NR * KR; ++t) gR[t] = R(0);
                 for (int i = threadIdx.x; i < N; i += BT)
-                    batch_atom_grad_cR<R>(P, b, a0, i, spos, s_off, se, sG, gR);
+                    batch_atom_grad_cR<R, MS>(P, b, a0, i, spos, s_off, se, sG, gR, blk / TT,
+                                              blk % TT);
 #pragma unroll 1
                 for (int t = 0; t < NR * KR; ++t) {
                     const double v = block_sum<BT>((double)gR[t], sh);
-                    if (threadIdx.x == 0) gp[OFF_CR + t] = v;
+                    if (threadIdx.x == 0) gp[OFF_CR + blk * NR * KR + t] = v;
                 }
             }
-            // angular basis coefficients, one channel at a time
+            // angular basis coefficients, one channel (and block) at a time
 #pragma unroll 1
-            for (int n = 0; n < NA; ++n) {
-                R gA[KA];
+            for (int blk = 0; blk < TT * TT; ++blk) {
+#pragma unroll 1
+                for (int n = 0; n < NA; ++n) {
+                    R gA[KA];
 #pragma unroll
-                for (int t = 0; t < KA; ++t) gA[t] = R(0);
-                for (int i = threadIdx.x; i < N; i += BT)
-                    batch_atom_grad_cA<R>(P, b, a0, i, n, spos, s_off, se, sG, gA);
+                    for (int t = 0; t < KA; ++t) gA[t] = R(0);
+                    for (int i = threadIdx.x; i < N; i += BT)
+                        batch_atom_grad_cA<R, MS>(P, b, a0, i, n, spos, s_off, se, sG, gA,
+                                                  blk / TT, blk % TT);
 #pragma unroll 1
-                for (int t = 0; t < KA; ++t) {
-                    const double v = block_sum<BT>((double)gA[t], sh);
-                    if (threadIdx.x == 0) gp[OFF_CA + n * KA + t] = v;
+                    for (int t = 0; t < KA; ++t) {
+                        const double v = block_sum<BT>((double)gA[t], sh);
+                        if (threadIdx.x == 0) gp[off_ca + blk * NA * KA + n * KA + t] = v;
+                    }
                 }
             }
         }
@@ -669,13 +783,37 @@ __global__ void __launch_bounds__(BT) k_batch(const Model<R> P, const Batch b)
 
 // Model k of the population from theta_k (host layout) and the base model
 // (hyperparameters, scaler, ZBL): w0 scaled by s_nu, h = c/2, C = sum_k c/2.
+// Several species (T > 1): the network into the model and every pair block
+// into tables[k][T * T][CSTR] (the model's own coefficient fields unused).
 template <typename R>
 __global__ void k_build_models(const Model<R> base, const double* __restrict__ scaler,
-                               const double* __restrict__ thetas, Model<R>* __restrict__ out)
+                               const double* __restrict__ thetas, Model<R>* __restrict__ out,
+                               int np, int T, R* __restrict__ tables)
 {
     const int k = blockIdx.x;
-    const double* th = thetas + (size_t)k * NP;
+    const double* th = thetas + (size_t)k * np;
     Model<R>& m = out[k];
+    if (T > 1) {
+        const double* cR = th + OFF_CR;
+        const double* cA = cR + (size_t)T * T * NR * KR;
+        R* tab = tables + (size_t)k * T * T * CSTR;
+        for (int e = threadIdx.x; e < T * T * CSTR; e += blockDim.x) {
+            const int pr = e / CSTR, o = e % CSTR;
+            double v = 0.0;
+            if (o < NR * KR) {
+                v = 0.5 * cR[(size_t)pr * NR * KR + o];
+            } else if (o < NR * KR + NR) {
+                const int n = o - NR * KR;
+                for (int kk = 0; kk < KR; ++kk) v += 0.5 * cR[(size_t)pr * NR * KR + n * KR + kk];
+            } else if (o >= C_ANG && o < C_ANG + NA * KA) {
+                v = 0.5 * cA[(size_t)pr * NA * KA + (o - C_ANG)];
+            } else if (o >= C_ANG + NA * KA && o < C_ANG + NA * KA + NA) {
+                const int n = o - C_ANG - NA * KA;
+                for (int kk = 0; kk < KA; ++kk) v += 0.5 * cA[(size_t)pr * NA * KA + n * KA + kk];
+            }
+            tab[e] = (R)v;
+        }
+    }
     // everything that is not a parameter comes from the base model
     const unsigned* src = reinterpret_cast<const unsigned*>(&base);
     unsigned* dst = reinterpret_cast<unsigned*>(&m);
@@ -687,6 +825,7 @@ __global__ void k_build_models(const Model<R> base, const double* __restrict__ s
         m.w1[e] = (R)th[OFF_W1 + e];
     }
     if (threadIdx.x == 0) m.b1 = (R)th[OFF_B1];
+    if (T > 1) return;
     for (int e = threadIdx.x; e < NR * KR; e += blockDim.x) m.hR[e] = (R)(0.5 * th[OFF_CR + e]);
     for (int e = threadIdx.x; e < NA * KA; e += blockDim.x) m.hA[e] = (R)(0.5 * th[OFF_CA + e]);
     if (threadIdx.x < NR) {
@@ -706,9 +845,10 @@ __global__ void k_build_models(const Model<R> base, const double* __restrict__ s
 // pass uses the lists built by the MODE_LISTS launch, and the item writes
 // pout[(k * S + cfg) * 3] = (dE / N, sum |dF|^2, sum over the six virial
 // components of (dW / N)^2 or 0 without a virial target).
-template <typename R, int BT>
+template <typename R, int BT, bool MS = false>
 __global__ void __launch_bounds__(BT) k_batch_pop(const Model<R>* __restrict__ models, int n_pop,
-                                                  const Batch b, double* __restrict__ pout)
+                                                  const Batch b, double* __restrict__ pout,
+                                                  const R* __restrict__ tables)
 {
     using P4 = typename V4<R>::T;
     using A_ = Acc<R>;
@@ -745,6 +885,14 @@ __global__ void __launch_bounds__(BT) k_batch_pop(const Model<R>* __restrict__ m
                 p[d] = v - L[d] * floor(v / L[d]);
             }
             q.x = (R)p[0]; q.y = (R)p[1]; q.z = (R)p[2]; q.w = R(0);
+            if (MS) {
+                int t = b.types[a0 + i];
+                if (t < 0 || t >= b.T) {
+                    atomicOr(b.status, ST_BADTYPE);
+                    t = 0;
+                }
+                q.w = (R)t;
+            }
             spos[i] = q;
             sF[0][i] = 0; sF[1][i] = 0; sF[2][i] = 0;
         }
@@ -763,8 +911,11 @@ __global__ void __launch_bounds__(BT) k_batch_pop(const Model<R>* __restrict__ m
 #pragma unroll
         for (int t = 0; t < 9; ++t) w[t] = 0.0;
         bool bad = false;
+        // the individual's pair table (several species)
+        Batch bk = b;
+        if (MS) bk.coef = tables + (size_t)k * b.T * b.T * CSTR;
         for (int i = threadIdx.x; i < N; i += BT)
-            esum += batch_atom_forward<R>(sP, b, a0, i, spos, s_off, sF, bad, w);
+            esum += batch_atom_forward<R, MS>(sP, bk, a0, i, spos, s_off, sF, bad, w);
         if (bad) atomicOr(b.status, ST_NONFINITE);
         const double E = block_sum<BT>(esum, sh);   // also orders the force scatter
         double f2 = 0.0;
@@ -804,7 +955,7 @@ __global__ void __launch_bounds__(BT) k_pop_loss(const double* __restrict__ pout
                                                  const double* __restrict__ thetas, int S,
                                                  long long ntot, double nv, double we, double wf,
                                                  double wv, double l1, double l2,
-                                                 double* __restrict__ losses)
+                                                 double* __restrict__ losses, int np)
 {
     __shared__ double sh[BT / 32];
     const int k = blockIdx.x;
@@ -815,8 +966,8 @@ __global__ void __launch_bounds__(BT) k_pop_loss(const double* __restrict__ pout
         f2 += o[1];
         v2 += o[2];
     }
-    for (int p = threadIdx.x; p < NP; p += BT) {
-        const double t = thetas[(size_t)k * NP + p];
+    for (int p = threadIdx.x; p < np; p += BT) {
+        const double t = thetas[(size_t)k * np + p];
         a1 += fabs(t);
         a2 += t * t;
     }
@@ -828,7 +979,7 @@ __global__ void __launch_bounds__(BT) k_pop_loss(const double* __restrict__ pout
     if (threadIdx.x == 0) {
         const double re = sqrt(e2 / S), rf = sqrt(f2 / (3.0 * (double)ntot));
         const double rv = nv > 0 ? sqrt(v2 / (6.0 * nv)) : 0.0;
-        const double r1 = l1 * a1 / NP, r2 = l2 * sqrt(a2 / NP);
+        const double r1 = l1 * a1 / np, r2 = l2 * sqrt(a2 / np);
         double* o = losses + (size_t)k * 6;
         o[0] = we * re + wf * rf + wv * rv + r1 + r2;
         o[1] = r1;
@@ -841,12 +992,12 @@ __global__ void __launch_bounds__(BT) k_pop_loss(const double* __restrict__ pout
 
 // SNES candidates theta_k = mu + sigma * s_k.
 static __global__ void k_snes_sample(const double* __restrict__ mu, const double* __restrict__ sigma,
-                                     const double* __restrict__ samples, int n_pop,
+                                     const double* __restrict__ samples, int n_pop, int np,
                                      double* __restrict__ thetas)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)n_pop * NP) return;
-    const int p = (int)(t % NP);
+    if (t >= (long long)n_pop * np) return;
+    const int p = (int)(t % np);
     thetas[t] = mu[p] + sigma[p] * samples[t];
 }
 
@@ -871,14 +1022,14 @@ static __global__ void k_snes_utilities(const double* __restrict__ losses, int n
 // mu += eta_mu sigma sum_k u_k s_k ;  sigma *= exp(eta_sigma / 2 sum_k u_k (s_k^2 - 1)).
 static __global__ void k_snes_update(double* __restrict__ mu, double* __restrict__ sigma,
                                      const double* __restrict__ samples,
-                                     const double* __restrict__ util, int n_pop, double eta_mu,
-                                     double eta_sigma)
+                                     const double* __restrict__ util, int n_pop, int np,
+                                     double eta_mu, double eta_sigma)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= NP) return;
+    if (p >= np) return;
     double gm = 0.0, gs = 0.0;
     for (int k = 0; k < n_pop; ++k) {
-        const double sk = samples[(size_t)k * NP + p];
+        const double sk = samples[(size_t)k * np + p];
         gm += util[k] * sk;
         gs += util[k] * (sk * sk - 1.0);
     }
@@ -888,13 +1039,13 @@ static __global__ void k_snes_update(double* __restrict__ mu, double* __restrict
 }
 
 // grad[p] = sum over configurations of gpart[c][p], in configuration order.
-static __global__ void k_batch_grad_reduce(const double* __restrict__ gpart, int S,
+static __global__ void k_batch_grad_reduce(const double* __restrict__ gpart, int S, int np,
                                     double* __restrict__ grad)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= NP) return;
+    if (p >= np) return;
     double s = 0.0;
-    for (int c = 0; c < S; ++c) s += gpart[(size_t)c * NP + p];
+    for (int c = 0; c < S; ++c) s += gpart[(size_t)c * np + p];
     grad[p] = s;
 }
 

@@ -145,7 +145,9 @@ struct nep_ctx {
     double* b_box = nullptr;
     int* b_queue = nullptr;
     // population evaluation (SNES)
-    double* p_thetas = nullptr;      // [n_pop][NP]
+    double* p_thetas = nullptr;      // [n_pop][n_params]
+    void* p_tables = nullptr;        // several species: n_pop pair tables
+    size_t p_tables_cap = 0;
     void* p_models = nullptr;        // n_pop models
     double* p_out = nullptr;         // [n_pop][S][3]
     double* p_util = nullptr;        // [1024]
@@ -762,6 +764,7 @@ void nep_free(nep_ctx* ctx)
     free_dev(ctx->status); free_dev(ctx->pairs); free_dev(ctx->gate); free_dev(ctx->nrebuild);
     free_dev(ctx->coef_f); free_dev(ctx->coef_d); free_dev(ctx->b_hv);
     free_dev(ctx->p_thetas); free_dev(ctx->p_models); free_dev(ctx->p_out); free_dev(ctx->p_util);
+    free_dev(ctx->p_tables);
     free_dev(ctx->d_scaler);
     free_dev(ctx->nhc); free_dev(ctx->nhc_backup); free_dev(ctx->d_box); free_dev(ctx->pka_part);
     free_dev(ctx->pka_atom);
@@ -1244,7 +1247,7 @@ static int batch_buffers(nep_ctx* ctx, long long ntot, int S, int M)
     CK(cudaMalloc(&ctx->b_cnt, sizeof(int2) * (size_t)nc));
     CK(cudaMalloc(&ctx->b_scr, rsz * (size_t)nc * BSTRIDE));
     CK(cudaMalloc(&ctx->b_F, sizeof(double) * 3 * (size_t)nc));
-    CK(cudaMalloc(&ctx->b_gpart, sizeof(double) * (size_t)Sc * NP));
+    CK(cudaMalloc(&ctx->b_gpart, sizeof(double) * (size_t)Sc * n_params_for(ctx->ntypes)));
     CK(cudaMalloc(&ctx->b_lpart, sizeof(double) * 3 * (size_t)Sc));
     CK(cudaMalloc(&ctx->b_E, sizeof(double) * (size_t)Sc));
     CK(cudaMalloc(&ctx->b_W, sizeof(double) * 9 * (size_t)Sc));
@@ -1261,8 +1264,6 @@ static int batch_buffers(nep_ctx* ctx, long long ntot, int S, int M)
 // Validates a batch, uploads its offsets/boxes/order and fills b.
 static int batch_prepare(nep_ctx* ctx, const nep_batch* bt, cudaStream_t s, Batch& b)
 {
-    if (ctx->ntypes != 1)
-        return fail(ctx, NEP_ERR_UNSUPPORTED, "the batched entry points support one species");
     if (!bt || bt->n_configs < 1 || !bt->offsets || !bt->boxes)
         return fail(ctx, NEP_ERR_INVALID_ARG, "batch needs n_configs >= 1, offsets and boxes");
     const int S = bt->n_configs;
@@ -1286,6 +1287,7 @@ static int batch_prepare(nep_ctx* ctx, const nep_batch* bt, cudaStream_t s, Batc
     });
     int rc;
     if ((rc = check_device_ptr(ctx, bt->xyz, "batch xyz"))) return rc;
+    if (ctx->ntypes > 1 && (rc = check_device_ptr(ctx, bt->types, "batch types"))) return rc;
     int M = ctx->b_M > 0 ? ctx->b_M : 112;
     if ((rc = batch_buffers(ctx, bt->n_atoms, S, M))) return rc;
     std::vector<long long> off(bt->offsets, bt->offsets + S + 1);
@@ -1304,6 +1306,11 @@ static int batch_prepare(nep_ctx* ctx, const nep_batch* bt, cudaStream_t s, Batc
     b.status = ctx->status;
     b.lpart = ctx->b_lpart;
     b.gpart = ctx->b_gpart;
+    b.T = ctx->ntypes;
+    b.np = (int)n_params_for(ctx->ntypes);
+    b.types = bt->types;
+    if (ctx->precision == NEP_FP32) b.coef = ctx->coef_f;
+    else b.coef = ctx->coef_d;
     return NEP_OK;
 }
 
@@ -1356,6 +1363,9 @@ static int batch_launch(nep_ctx* ctx, Batch& b, int mode, double* grad, cudaStre
             CK(cudaMemcpy(ctx->b_order, order.data(), sizeof(int) * b.S, cudaMemcpyHostToDevice));
             continue;
         }
+        if (ctx->h_status[0] & ST_BADTYPE)
+            return fail(ctx, NEP_ERR_INVALID_ARG, "species index out of range [0, %d)",
+                        ctx->ntypes);
         if (ctx->h_status[0] & ST_NONFINITE)
             return fail(ctx, NEP_ERR_NONFINITE, "non-finite values in the batch");
         return NEP_OK;
@@ -1486,7 +1496,7 @@ int nep_batch_autotune(nep_ctx* ctx, const nep_batch* batch, const nep_targets* 
     if (!ctx) return NEP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     double* grad = nullptr;
-    CK(cudaMalloc(&grad, sizeof(double) * NP));
+    CK(cudaMalloc(&grad, sizeof(double) * n_params_for(ctx->ntypes)));
     const int bts[3] = {64, 128, 256};
     const int nbt = ctx->precision == NEP_FP32 ? 3 : 1;
     float best = 1e30f;
@@ -1561,13 +1571,21 @@ static int population_eval(nep_ctx* ctx, const nep_batch* batch, const nep_targe
     const int grid = (int)std::min<long long>(items, (long long)population_blocks_per_sm(ctx->precision) * sms);
     CK(cudaMemsetAsync(ctx->b_queue, 0, sizeof(int), s));
     CK(cudaMemsetAsync(ctx->status, 0, sizeof(int) * 3, s));
+    if (b.T > 1) {
+        const size_t rsz = ctx->precision == NEP_FP32 ? sizeof(float) : sizeof(double);
+        if ((rc = grow(ctx, &ctx->p_tables, ctx->p_tables_cap,
+                       rsz * (size_t)b.T * b.T * CSTR * n_pop, s)))
+            return rc;
+    }
     CK(launch_population(ctx->precision, n_pop, ctx->mf, ctx->md, ctx->d_scaler, thetas,
-                         ctx->p_models, b, ctx->p_out, grid, s));
+                         ctx->p_models, ctx->p_tables, b, ctx->p_out, grid, s));
     CK(launch_population_loss(n_pop, ctx->p_out, thetas, b.S, b.ntot, (double)nv, w->energy,
-                              w->force, w->virial, w->l1, w->l2, losses, s));
+                              w->force, w->virial, w->l1, w->l2, losses, b.np, s));
     ctx->launches += 3;
     CK(cudaMemcpyAsync(ctx->h_status, ctx->status, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (ctx->h_status[0] & ST_BADTYPE)
+        return fail(ctx, NEP_ERR_INVALID_ARG, "species index out of range [0, %d)", ctx->ntypes);
     if (ctx->h_status[0] & ST_NONFINITE)
         return fail(ctx, NEP_ERR_NONFINITE, "non-finite values in the population");
     return NEP_OK;
@@ -1578,7 +1596,7 @@ static int population_args(nep_ctx* ctx, const nep_targets* t, const nep_loss_we
 {
     if (!t || !w) return fail(ctx, NEP_ERR_INVALID_ARG, "targets or weights is NULL");
     if (n_pop < 1 || n_pop > 1024) return fail(ctx, NEP_ERR_INVALID_ARG, "n_pop must be 1..1024");
-    if ((long long)n_pop * NP > (1LL << 31))
+    if ((long long)n_pop * n_params_for(ctx->ntypes) > (1LL << 31))
         return fail(ctx, NEP_ERR_INVALID_ARG, "population too large");
     return NEP_OK;
 }
@@ -1610,14 +1628,16 @@ int nep_snes_generation(nep_ctx* ctx, const nep_batch* batch, const nep_targets*
     if (!isfinite(eta_mu) || !isfinite(eta_sigma))
         return fail(ctx, NEP_ERR_INVALID_ARG, "learning rates must be finite");
     cudaStream_t s = (cudaStream_t)stream;
-    if ((rc = grow(ctx, (void**)&ctx->p_thetas, ctx->p_thetas_cap, sizeof(double) * NP * (size_t)n_pop,
-                   s)))
+    const int np = (int)n_params_for(ctx->ntypes);
+    if ((rc = grow(ctx, (void**)&ctx->p_thetas, ctx->p_thetas_cap,
+                   sizeof(double) * np * (size_t)n_pop, s)))
         return rc;
     if (!ctx->p_util) CK(cudaMalloc(&ctx->p_util, sizeof(double) * 1024));
-    CK(launch_snes_sample(mu, sigma, samples, n_pop, ctx->p_thetas, s));
+    CK(launch_snes_sample(mu, sigma, samples, n_pop, np, ctx->p_thetas, s));
     ctx->launches += 1;
     if ((rc = population_eval(ctx, batch, t, w, n_pop, ctx->p_thetas, losses, s))) return rc;
-    CK(launch_snes_update(mu, sigma, samples, losses, ctx->p_util, n_pop, eta_mu, eta_sigma, s));
+    CK(launch_snes_update(mu, sigma, samples, losses, ctx->p_util, n_pop, np, eta_mu, eta_sigma,
+                          s));
     ctx->launches += 2;
     CK(cudaStreamSynchronize(s));
     return NEP_OK;

@@ -471,7 +471,9 @@ class Batch:
                                                           for s in structures]))
         pos = np.concatenate([s.pos for s in structures], axis=0)
         self.xyz = to_device_soa(pos, self.device)
-        self.types = torch.zeros(self.N, dtype=torch.int32, device=self.device)
+        self.types = torch.tensor(np.concatenate([np.asarray(s.types, np.int32)
+                                                  for s in structures]),
+                                  dtype=torch.int32, device=self.device)
         c = NepBatch()
         c.n_configs = self.S
         c.n_atoms = self.N

@@ -207,10 +207,117 @@ def test_set_params_two_species():
     m.close()
 
 
-def test_batched_entry_points_reject_several_species():
+def test_batch_species_index_out_of_range():
+    import torch
     from paper_2305_08140_gb300 import nepzbl as N
     m = _nep(WMO, "fp32")
     b = N.Batch(I.c4(2))
+    b.types[3] = 2
     with pytest.raises(N.NepError) as e:
         m.batch_forward(b)
-    assert e.value.code == N.NEP_ERR_UNSUPPORTED
+    assert e.value.code == N.NEP_ERR_INVALID_ARG
+
+
+# ---------------------------------------------------------------------------
+# Batched (training) path with several species
+# ---------------------------------------------------------------------------
+
+def _one_species(structs):
+    return [I.Structure(t.pos, t.box, t.pbc, np.zeros_like(t.types)) for t in structs]
+
+
+def _alloy_configs(k, seed):
+    out = []
+    for c, s in enumerate([s for s in I.c4(64, seed=seed) if s.n <= 128][:k]):
+        out.append(I.alloy(s, [0.5, 0.5], seed=seed + 100 + c))
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_batch_forward_two_species(precision):
+    from oracle import training as T
+    from paper_2305_08140_gb300 import nepzbl as N
+    structs = _alloy_configs(8, 401)
+    model = _model(WMO)
+    nep = N.NEP(model, precision)
+    b = N.Batch(structs)
+    E, F, W = nep.batch_forward(b, virials=True)
+    Eo, Fo, Wo = T.evaluate(model, structs)
+    E, F, W = E.cpu().numpy(), F.cpu().numpy().T, W.cpu().numpy()
+    tf, te, tw = (1e-4, 1e-6, 2e-5) if precision == "fp32" else (1e-9, 1e-11, 1e-10)
+    for c, s in enumerate(structs):
+        a, z = b.offsets[c], b.offsets[c + 1]
+        assert abs(E[c] - Eo[c]) / s.n <= te
+        assert np.max(np.abs(F[a:z] - Fo[c])) <= tf
+        assert np.max(np.abs(W[c] - Wo[c])) / s.n <= tw
+    nep.close()
+
+
+def test_batch_loss_gradient_two_species_all_parameters_fd():
+    """All 961 + 90 x 4 = 1,321 parameters of the W-Mo model (FP64 path):
+    energy + force + virial mean-square loss against central differences of
+    the oracle's loss."""
+    import torch
+    from oracle import training as T
+    from paper_2305_08140_gb300 import nepzbl as N
+    structs = _alloy_configs(3, 402)
+    model = _model(WMO)
+    # targets: the W-only seed-101 model on the same positions (any fixed numbers)
+    Et, Ft, Wt = T.evaluate(I.nep_model(101), _one_species(structs))
+    W6t = T.virial6(Wt)
+    hv = np.array([1, 0, 1], np.uint8)
+    nep = N.NEP(model, "fp64")
+    b = N.Batch(structs)
+    dev = dict(dtype=torch.float64, device="cuda")
+    L, g, E, F = nep.batch_loss_grad(b, torch.tensor(Et, **dev),
+                                     torch.tensor(np.concatenate(Ft).T.copy(), **dev),
+                                     W_target=torch.tensor(W6t, **dev), has_virial=hv,
+                                     w_virial=0.1)
+    Nn = [s.n for s in structs]
+
+    def loss(theta):
+        E_, F_, W_ = T.evaluate(model, structs, theta)
+        return T.mse_loss(E_, F_, T.virial6(W_), Et, Ft, W6t, Nn, hv, 1.0, 1.0, 0.1)[0]
+
+    assert L == pytest.approx(loss(model.params), rel=1e-10)
+    g = g.cpu().numpy()
+    assert g.shape == (model.n_params,)
+    th = model.params
+    fd = np.zeros(len(th))
+    for k in range(len(th)):
+        h = 1e-6 * max(1.0, abs(th[k]))
+        tp = th.copy(); tp[k] += h
+        tm = th.copy(); tm[k] -= h
+        fd[k] = (loss(tp) - loss(tm)) / (2 * h)
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-9 * np.max(np.abs(fd)))
+    nep.close()
+
+
+def test_population_loss_four_species():
+    import torch
+    from oracle import training as T
+    from paper_2305_08140_gb300 import nepzbl as N
+    structs = [I.alloy(s, [0.25] * 4, seed=410 + c) for c, s in
+               enumerate([s for s in I.c4(64, seed=403) if s.n <= 128][:4])]
+    model = _model(HEA)
+    Et, Ft, Wt = T.evaluate(I.nep_model(101), _one_species(structs))
+    W6t = T.virial6(Wt)
+    hv = np.ones(len(structs), np.uint8)
+    weights = {"energy": 1.0, "force": 1.0, "virial": 0.1, "l1": 0.05, "l2": 0.05}
+    rng = np.random.default_rng(404)
+    thetas = model.params[None, :] + 0.05 * rng.normal(size=(3, model.n_params))
+    dev = dict(dtype=torch.float64, device="cuda")
+    for prec, rel in (("fp64", 1e-10), ("fp32", 2e-5)):
+        nep = N.NEP(model, prec)
+        b = N.Batch(structs)
+        L = N.population_loss(nep, b, torch.tensor(thetas, **dev), torch.tensor(Et, **dev),
+                              torch.tensor(np.concatenate(Ft).T.copy(), **dev),
+                              torch.tensor(W6t, **dev), hv, weights).cpu().numpy()
+        Nn = [s.n for s in structs]
+        for k in range(len(thetas)):
+            E_, F_, W_ = T.evaluate(model, structs, thetas[k])
+            d = T.nep_loss(thetas[k], T.rmse_terms(E_, F_, T.virial6(W_), Et, Ft, W6t, Nn, hv),
+                           weights)
+            ref = [d[t] for t in ("total", "l1", "l2", "energy", "force", "virial")]
+            np.testing.assert_allclose(L[k], ref, rtol=rel, atol=1e-12)
+        nep.close()
