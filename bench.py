@@ -395,6 +395,20 @@ def run_reference(args):
     return 0
 
 
+def replica_throughput(ms_local, n_local, steps, dist=None, device="cpu"):
+    """Whole-job throughput of replicas: the slowest rank's time (max over
+    ranks) and the atoms of all ranks x steps / that time.  Returns (ms, value)."""
+    import torch
+    ms, units = float(ms_local), float(n_local)
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([units], dtype=torch.float64, device=device)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        ms, units = float(t.item()), float(u.item())
+    return ms, units * steps / (ms * 1e-3)
+
+
 def run_ours(args):
     import torch
     ws, rank, local = _dist()
@@ -441,11 +455,7 @@ def run_ours(args):
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     stats = nep.stats()
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * n * args.steps / (ms * 1e-3)
+    ms, value = replica_throughput(ms, n, args.steps, dist, dev)
 
     # roofline of the dominant kernel (the force kernel), timed inside the region
     peaks, peak_kind = _measured_peaks()
