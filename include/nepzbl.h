@@ -374,10 +374,11 @@ int nep_snes_generation(nep_ctx* ctx, const nep_batch* batch, const nep_targets*
 
 /* Force evaluation that allocates nothing (the paper has no counterpart; it is
  * a deployment convenience).  It is meant for callers that may not allocate
- * GPU memory at the point where they need forces: code embedded in a host
- * program whose device memory is owned by that program's own pool, or code
- * running while the host is capturing a stream into a graph, where a
- * cudaMalloc would break the capture.  It takes the model parameters directly
+ * GPU memory at the point where they need forces: a plugin inside a host MD
+ * or training program that owns all device memory through its own pool or a
+ * fixed budget, and forbids its components to call cudaMalloc behind its
+ * back (an allocation there can fail or fragment the host's pool mid-run).
+ * It takes the model parameters directly
  * (no context: creating one allocates) and computes the same FP32 evaluation
  * as nep_compute with a context created with NEP_FP32; arguments as in
  * nep_compute.

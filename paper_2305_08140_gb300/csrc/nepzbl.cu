@@ -1650,9 +1650,9 @@ int nep_snes_generation(nep_ctx* ctx, const nep_batch* batch, const nep_targets*
 // ============================================================================
 //
 // For callers that cannot call cudaMalloc at the point where they need forces
-// (for example code running inside a host framework whose device memory is all
-// owned by its own pool, or a plugin that may not touch the allocator while a
-// stream is being captured by its host).  All scratch of one FP32 evaluation
+// (for example a plugin inside a host program whose device memory is all owned
+// by the host's own pool or fixed budget, so that components may not allocate
+// behind its back).  All scratch of one FP32 evaluation
 // lives in g_static_scratch below, a file-scope __device__ array that every GPU
 // loading this library holds until the process exits.
 

@@ -1,6 +1,6 @@
 """nep_compute_static: the force evaluation for callers that cannot allocate
-GPU memory when they need forces (memory owned by a host program's pool, or a
-host that is capturing a stream into a graph).  Its scratch is a fixed device
+GPU memory when they need forces (a plugin in a host program that owns all
+device memory through its own pool or budget).  Its scratch is a fixed device
 array inside the library.  Called through the C ABI and compared with
 nep_compute, on two calls in a row (the array keeps the previous call's
 contents, so the second call checks that what must start at zero is
