@@ -327,6 +327,30 @@ __global__ void k_cell_finalize(Grid g, int ncell, const int* __restrict__ start
 // Neighbour lists: 27-cell stencil, minimum image through the stencil offset
 // ----------------------------------------------------------------------------
 
+// The 27 stencil offsets (cell-edge multiples) of the neighbour codes, in
+// shared memory; filled by the first 27 threads of the block.
+template <typename R>
+__device__ __forceinline__ void fill_stencil(typename V4<R>::T* tab, const Grid& g)
+{
+    if (threadIdx.x < 27) {
+        int code = threadIdx.x;
+        int a = code / 9, b = (code / 3) % 3, c = code % 3;
+        typename V4<R>::T o;
+        if (g.tric) {
+            o.x = (R)stencil_off_tric(g, a - 1, b - 1, c - 1, 0);
+            o.y = (R)stencil_off_tric(g, a - 1, b - 1, c - 1, 1);
+            o.z = (R)stencil_off_tric(g, a - 1, b - 1, c - 1, 2);
+        } else {
+            o.x = (R)((a - 1) * g.lc[0]);
+            o.y = (R)((b - 1) * g.lc[1]);
+            o.z = (R)((c - 1) * g.lc[2]);
+        }
+        o.w = R(0);
+        tab[code] = o;
+    }
+    __syncthreads();
+}
+
 // Radial basis coefficients for the neighbour kernel that also sums the
 // radial descriptor (one species).
 template <typename R>
@@ -336,10 +360,12 @@ struct RadCoef {
 };
 
 // WQ: also the radial descriptor q_n of every atom (one species, lists
-// rebuilt every step), from the pairs the force kernels will see: the
-// displacement is recomputed for each hit in the force kernels' form
-// (pj - pi) + offset, and pairs with r >= r_c in that form are left out
-// as they skip them.
+// rebuilt every step), from the pairs the force kernels will see: after the
+// search each thread walks its own freshly written list with the
+// displacement in the force kernels' form (pj - pi) + offset, so pairs with
+// r >= r_c in that form are left out as they skip them.  The search itself
+// only tests and stores (few lanes of a warp hit at any one candidate, so
+// descriptor work inside the hit branch would run with most lanes idle).
 // TRIC: triclinic cells (stencil offsets are vectors; the orthorhombic
 // instantiation keeps per-axis offsets).
 template <typename R, bool WQ, bool TRIC = false>
@@ -354,14 +380,15 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                                                    const int* __restrict__ gate,
                                                    const RadCoef<R> rq, R* __restrict__ qr)
 {
+    using P4 = typename V4<R>::T;
     if (gate && *gate == 0) return;   // lists still valid (Verlet skin)
+    __shared__ P4 s_off[WQ ? 27 : 1];
+    if constexpr (WQ) fill_stencil<R>(s_off, g);
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    int na = 0, nro = 0, sa = 0, sro = 0;
-    R Sb[WQ ? KR : 1];
-#pragma unroll
-    for (int kk = 0; kk < (WQ ? KR : 1); ++kk) Sb[kk] = R(0);
+    // tot: all hits (overflow test); sa / sro: stored angular / radial-only
+    int tot = 0, sa = 0, sro = 0;
     if (k < g.n) {
-        const typename V4<R>::T p = pos4[k];
+        const P4 p = pos4[k];
         const int c = cell_sorted[k];
         const int ncx = g.nc[0], ncy = g.nc[1], ncz = g.nc[2];
         const int cz = c % ncz, cy = (c / ncz) % ncy, cx = c / (ncz * ncy);
@@ -398,44 +425,52 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                     const int c2 = rowXY + Z;
                     const int e = start[c2 + 1];
                     for (int m = start[c2]; m < e; ++m) {
-                        const typename V4<R>::T q = pos4[m];
+                        const P4 q = pos4[m];
                         const R dx = q.x - px, dy = q.y - py, dz = q.z - pz;
                         const R r2 = dx * dx + dy * dy + dz * dz;
-                        if (r2 < rcR2 && m != k) {
-                            const bool ang = r2 < rcA2;
-                            if (sa + sro < M) {
-                                const int ent = (m << 5) | code;
-                                if (ang) col[(size_t)(sa++) * ld] = ent;
-                                else col[(size_t)(M - 1 - sro++) * ld] = ent;
-                            }
-                            if (ang) ++na; else ++nro;
-                            if constexpr (WQ) {
-                                R ofx = R(ox) * lx, ofy = R(oy) * ly, ofz = R(oz) * lz;
-                                if constexpr (TRIC) {
-                                    ofx = (R)stencil_off_tric(g, ox, oy, oz, 0);
-                                    ofy = (R)stencil_off_tric(g, ox, oy, oz, 1);
-                                    ofz = (R)stencil_off_tric(g, ox, oy, oz, 2);
-                                }
-                                const R fx = q.x - p.x + ofx, fy = q.y - p.y + ofy,
-                                        fz = q.z - p.z + ofz;
-                                const R f2 = fx * fx + fy * fy + fz * fz;
-                                if (f2 < rcR2) {
-                                    const R rr = f2 * nepm::nep_rsqrt(f2);
-                                    R T[KR], dT[KR], fc, dfc, dxdr;
-                                    nepm::cheb<KR, false>(rr, rq.inv_rcR, T, dT, fc, dfc, dxdr);
-#pragma unroll
-                                    for (int kk = 0; kk < KR; ++kk) Sb[kk] += fc * T[kk];
-                                }
-                            }
-                        }
+                        const bool hit = r2 < rcR2 && m != k;
+                        const bool ang = r2 < rcA2;
+                        const bool room = sa + sro < M;
+                        if (hit && room)
+                            col[(size_t)(ang ? sa : M - 1 - sro) * ld] = (m << 5) | code;
+                        tot += hit;
+                        sa += hit && room && ang;
+                        sro += hit && room && !ang;
                     }
                 }
             }
         }
         cnt[k] = make_int2(sa, sro);
-        if (na + nro > M) atomicOr(status, ST_OVERFLOW);
+        if (tot > M) atomicOr(status, ST_OVERFLOW);
         if constexpr (WQ) {
-            // q_n = C_n Sb_0 + sum_k h_nk Sb_k
+            // Sb_k = sum_j f_c T_k over the stored pairs within r_c in the
+            // force kernels' form; q_n = C_n Sb_0 + sum_k h_nk Sb_k.  Entry
+            // s + 2 and position s + 1 are in flight during pair s.
+            R Sb[KR];
+#pragma unroll
+            for (int kk = 0; kk < KR; ++kk) Sb[kk] = R(0);
+            const int ns = sa + sro;
+            auto slot = [&](int t) { return t < sa ? t : M - 1 - (t - sa); };
+            int ent_n = ns > 0 ? col[(size_t)slot(0) * ld] : 0;
+            int ent_nn = ns > 1 ? col[(size_t)slot(1) * ld] : 0;
+            P4 pj_n = ns > 0 ? pos4[ent_n >> 5] : p;
+            for (int t = 0; t < ns; ++t) {
+                const int ent = ent_n;
+                const P4 pj = pj_n;
+                ent_n = ent_nn;
+                if (t + 1 < ns) pj_n = pos4[ent_n >> 5];
+                if (t + 2 < ns) ent_nn = col[(size_t)slot(t + 2) * ld];
+                const P4 off = s_off[ent & 31];
+                const R fx = pj.x - p.x + off.x, fy = pj.y - p.y + off.y, fz = pj.z - p.z + off.z;
+                const R f2 = fx * fx + fy * fy + fz * fz;
+                if (f2 < rcR2) {
+                    const R rr = f2 * nepm::nep_rsqrt(f2);
+                    R T[KR], dT[KR], fc, dfc, dxdr;
+                    nepm::cheb<KR, false>(rr, rq.inv_rcR, T, dT, fc, dfc, dxdr);
+#pragma unroll
+                    for (int kk = 0; kk < KR; ++kk) Sb[kk] += fc * T[kk];
+                }
+            }
 #pragma unroll
             for (int n = 0; n < NR; ++n) {
                 R acc = rq.CR[n] * Sb[0];
@@ -446,8 +481,8 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
         }
     }
     // statistics: block maxima and pair sums
-    int tot = na + nro;
-    unsigned long long pr = (unsigned long long)tot, pa = (unsigned long long)na;
+    int na = sa;
+    unsigned long long pr = (unsigned long long)tot, pa = (unsigned long long)sa;
     for (int o = 16; o > 0; o >>= 1) {
         tot = max(tot, __shfl_xor_sync(0xffffffffu, tot, o));
         na = max(na, __shfl_xor_sync(0xffffffffu, na, o));
@@ -603,30 +638,6 @@ __device__ __forceinline__ void zbl_pair(double r, double k, double inv_a, doubl
     double dv = -v * inv_r + k * inv_r * dphi * inv_a;
     U = v * fc;
     dU = dv * fc + v * dfc;
-}
-
-// The 27 stencil offsets (cell-edge multiples) of the neighbour codes, in
-// shared memory; filled by the first 27 threads of the block.
-template <typename R>
-__device__ __forceinline__ void fill_stencil(typename V4<R>::T* tab, const Grid& g)
-{
-    if (threadIdx.x < 27) {
-        int code = threadIdx.x;
-        int a = code / 9, b = (code / 3) % 3, c = code % 3;
-        typename V4<R>::T o;
-        if (g.tric) {
-            o.x = (R)stencil_off_tric(g, a - 1, b - 1, c - 1, 0);
-            o.y = (R)stencil_off_tric(g, a - 1, b - 1, c - 1, 1);
-            o.z = (R)stencil_off_tric(g, a - 1, b - 1, c - 1, 2);
-        } else {
-            o.x = (R)((a - 1) * g.lc[0]);
-            o.y = (R)((b - 1) * g.lc[1]);
-            o.z = (R)((c - 1) * g.lc[2]);
-        }
-        o.w = R(0);
-        tab[code] = o;
-    }
-    __syncthreads();
 }
 
 // ----------------------------------------------------------------------------
