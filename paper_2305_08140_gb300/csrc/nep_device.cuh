@@ -760,6 +760,112 @@ __device__ __forceinline__ R network_adjoint_core(const Model<R>& P, const R (&q
     return U;
 }
 
+// Rows of the network for the rolled loop below: row mu holds
+// (w0[mu][0..29] s, b0_mu, w1_mu), 32 values, in shared memory.
+constexpr int WROW = 32;
+static_assert(D + 2 == WROW, "network row layout");
+
+template <typename R>
+__device__ __forceinline__ void fill_network_rows(R* sw, const Model<R>& P)
+{
+    for (int t = threadIdx.x; t < H * WROW; t += blockDim.x) {
+        const int mu = t / WROW, c = t % WROW;
+        sw[t] = c < D ? P.w0[mu * D + c] : (c == D ? P.b0[mu] : P.w1[mu]);
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void load_row(const R* __restrict__ src, R (&w)[WROW]);
+template <>
+__device__ __forceinline__ void load_row<float>(const float* __restrict__ src, float (&w)[WROW])
+{
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+    for (int c = 0; c < WROW / 4; ++c) {
+        const float4 v = s4[c];
+        w[4 * c] = v.x; w[4 * c + 1] = v.y; w[4 * c + 2] = v.z; w[4 * c + 3] = v.w;
+    }
+}
+template <>
+__device__ __forceinline__ void load_row<double>(const double* __restrict__ src, double (&w)[WROW])
+{
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+#pragma unroll
+    for (int c = 0; c < WROW / 2; ++c) {
+        const double2 v = s2[c];
+        w[2 * c] = v.x; w[2 * c + 1] = v.y;
+    }
+}
+
+// network_adjoint_core with the hidden layer as one rolled loop over the
+// neurons: for each mu the row is read from shared memory (sw, see
+// fill_network_rows), h_mu = sum_nu w_mu,nu q_nu - b0_mu, and its term
+// w1_mu (1 - tanh^2) w_mu,nu is added to dU/dq_nu at once, so forward and
+// backward share one pass over the weights and the code stays small.  Same
+// sums in the same order as network_adjoint_core.
+template <typename R>
+__device__ __forceinline__ R network_adjoint_core_rolled(const Model<R>& P,
+                                                         const R* __restrict__ sw,
+                                                         const R (&qR)[NR], R (&A)[NA][NLM],
+                                                         R (&aR)[NR])
+{
+    R q[D];
+#pragma unroll
+    for (int nu = 0; nu < NR; ++nu) q[nu] = qR[nu];
+#pragma unroll
+    for (int l = 1; l <= LM; ++l) {
+        const int lo = l * l - 1, hi = (l + 1) * (l + 1) - 1;
+#pragma unroll
+        for (int n = 0; n < NA; ++n) {
+            R v = R(0);
+#pragma unroll
+            for (int lm = lo; lm < hi; ++lm) v += A[n][lm] * A[n][lm];
+            q[NR + (l - 1) * NA + n] = v;
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < NA; ++n) q[NR + LM * NA + n] = nepm::fourbody(&A[n][3], (R*)nullptr);
+    R a[D];
+#pragma unroll
+    for (int nu = 0; nu < D; ++nu) a[nu] = R(0);
+    R U = -P.b1;
+#pragma unroll 1
+    for (int mu = 0; mu < H; ++mu) {
+        R w[WROW];
+        load_row<R>(sw + mu * WROW, w);
+        R h = -w[D];
+#pragma unroll
+        for (int nu = 0; nu < D; ++nu) h += w[nu] * q[nu];
+        const R t = tanh(h);
+        U += w[D + 1] * t;
+        const R gm = w[D + 1] * (R(1) - t * t);   // dU/dh_mu
+#pragma unroll
+        for (int nu = 0; nu < D; ++nu) a[nu] += gm * w[nu];
+    }
+#pragma unroll
+    for (int nu = 0; nu < NR; ++nu) aR[nu] = a[nu];
+#pragma unroll
+    for (int n = 0; n < NA; ++n) {
+        const R a4 = a[NR + LM * NA + n], a2 = a[NR + NA + n];
+        R dq4[5];
+        nepm::fourbody(&A[n][3], dq4);
+#pragma unroll
+        for (int t = 0; t < 5; ++t) A[n][3 + t] = R(2) * a2 * A[n][3 + t] + a4 * dq4[t];
+    }
+#pragma unroll
+    for (int l = 1; l <= LM; ++l) {
+        if (l == 2) continue;
+        const int lo = l * l - 1, hi = (l + 1) * (l + 1) - 1;
+#pragma unroll
+        for (int n = 0; n < NA; ++n) {
+            const R al = a[NR + (l - 1) * NA + n];
+#pragma unroll
+            for (int lm = lo; lm < hi; ++lm) A[n][lm] *= R(2) * al;
+        }
+    }
+    return U;
+}
+
 // One species: the radial adjoint contracted with the basis coefficients,
 // sum_n dU/dq_n g'_n(r) = df_c (B0 + sum_k bR_k T_k) + f_c x' sum_k bR_k T'_k.
 template <typename R>
@@ -1249,7 +1355,9 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
     if constexpr (MS) {
         for (int t = threadIdx.x; t < T * T * CSTR; t += TILE) s_coef[t] = coef[t];
     }
+    __shared__ __align__(16) R s_w[H * WROW];
     if (threadIdx.x == 0) s_max = 0;
+    fill_network_rows<R>(s_w, P);
     fill_stencil<R>(s_off, g);
     const int k = blockIdx.x * TILE + threadIdx.x;
     const size_t ld = (size_t)g.ld;
@@ -1322,7 +1430,7 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
         };
         if constexpr (MS) {
             R aR[NR];
-            U = network_adjoint_core<R>(P, qR, A, aR);
+            U = network_adjoint_core_rolled<R>(P, s_w, qR, A, aR);
             for (int t = 0; t < T; ++t) {
                 const R* c = s_coef + ((size_t)ti * T + t) * CSTR + C_RAD;
                 R bR[KR], B0 = R(0);
@@ -1340,8 +1448,19 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
             // one species: the record the radial-force kernel gathers per
             // neighbour, (x, y, z, b_8), (b_0 + B0, b_1, b_2, b_3), (b_4..b_7)
             // (T_0 = 1 and T_0' = 0, so B0 folds into b_0)
-            R bR[KR], B0;
-            U = network_adjoint<R>(P, qR, A, bR, B0);
+            R bR[KR], B0 = R(0);
+            {
+                R aR[NR];
+                U = network_adjoint_core_rolled<R>(P, s_w, qR, A, aR);
+#pragma unroll
+                for (int kk = 0; kk < KR; ++kk) bR[kk] = R(0);
+#pragma unroll
+                for (int nu = 0; nu < NR; ++nu) {
+                    B0 += aR[nu] * P.CR[nu];
+#pragma unroll
+                    for (int kk = 0; kk < KR; ++kk) bR[kk] += aR[nu] * P.hR[nu * KR + kk];
+                }
+            }
             P4 r0, r1, r2;
             r0.x = pi.x; r0.y = pi.y; r0.z = pi.z; r0.w = bR[8];
             r1.x = bR[0] + B0; r1.y = bR[1]; r1.z = bR[2]; r1.w = bR[3];
