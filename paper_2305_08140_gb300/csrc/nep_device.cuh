@@ -139,32 +139,67 @@ __device__ __forceinline__ int cell_coord(double x, int d, const Grid& g, double
     return c;
 }
 
-static __global__ void k_bin_count(Grid g, const double* __restrict__ x, int* __restrict__ cell_of,
+// Range tests on the bit pattern of a double (integer instructions only: the
+// FP64 pipe of this GPU is narrow).  For x >= +0 the IEEE order of doubles is
+// the integer order of their bit patterns.
+__device__ __forceinline__ bool finite_bits(double x)
+{
+    return (__double_as_longlong(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+}
+// x in [0, L) for L > 0 (false for -0.0 and NaN)
+__device__ __forceinline__ bool in_box_bits(double x, double L)
+{
+    const long long b = __double_as_longlong(x);
+    return b >= 0 && b < __double_as_longlong(L);
+}
+// x - L floor(x / L), out of line: the caller's rare branch must not be
+// turned into predicated FP64 instructions that issue on every thread
+static __device__ __noinline__ double wrap_slow(double x, double L, double invL)
+{
+    return x - L * floor(x * invL);
+}
+
+// Cell of each atom and its slot in the cell (atomic count).  With rel
+// (orthorhombic or triclinic) the atom's position relative to its cell's
+// origin is written too, by caller index, so that k_cell_finalize need not
+// recompute it.
+template <typename R>
+__global__ void k_bin_count(Grid g, const double* __restrict__ x, int* __restrict__ cell_of,
                             int* __restrict__ slot_of, int* __restrict__ count,
-                            int* __restrict__ status,
-                            const int* __restrict__ gate = nullptr)
+                            int* __restrict__ status, const int* __restrict__ gate = nullptr,
+                            typename V4<R>::T* __restrict__ rel = nullptr)
 {
     if (gate && *gate == 0) return;   // lists still valid (Verlet skin)
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n) return;
     double p[3] = {x[i], x[g.n + i], x[2 * g.n + i]};
     int c[3];
+    double r3[3];
     bool bad = false;
     for (int d = 0; d < 3; ++d)
-        if (!isfinite(p[d])) { bad = true; p[d] = 0.0; }
+        if (!finite_bits(p[d])) { bad = true; p[d] = 0.0; }
     if (g.tric) {
-        double rel[3];
-        cell_tric(g, p, c, rel);
+        cell_tric(g, p, c, r3);
     } else {
         for (int d = 0; d < 3; ++d) {
-            double w;
-            c[d] = cell_coord(p[d], d, g, w);
+            double w = p[d];
+            if (g.pbc[d] && !in_box_bits(w, g.L[d])) w = wrap_slow(w, g.L[d], g.invL[d]);
+            int cd = (int)floor(w * g.inv_lc[d]);
+            cd = cd < 0 ? 0 : cd;
+            cd = cd >= g.nc[d] ? g.nc[d] - 1 : cd;
+            c[d] = cd;
+            r3[d] = w - cd * g.lc[d];
         }
     }
     if (bad) atomicOr(status, ST_NONFINITE);
     int cell = (c[0] * g.nc[1] + c[1]) * g.nc[2] + c[2];
     cell_of[i] = cell;
     slot_of[i] = atomicAdd(&count[cell], 1);
+    if (rel) {
+        typename V4<R>::T q;
+        q.x = (R)r3[0]; q.y = (R)r3[1]; q.z = (R)r3[2]; q.w = R(0);
+        rel[i] = q;
+    }
 }
 
 // exclusive scan of count[0..nc) into start[0..nc], 1024 items per block
@@ -276,7 +311,8 @@ __global__ void k_cell_finalize(Grid g, int ncell, const int* __restrict__ start
                                 typename V4<R>::T* __restrict__ pos4,
                                 int* __restrict__ cell_sorted, int* __restrict__ status,
                                 const int* __restrict__ gate = nullptr,
-                                int* __restrict__ invperm = nullptr)
+                                int* __restrict__ invperm = nullptr,
+                                const typename V4<R>::T* __restrict__ relp = nullptr)
 {
     if (gate && *gate == 0) return;   // lists still valid (Verlet skin)
     int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -293,7 +329,11 @@ __global__ void k_cell_finalize(Grid g, int ncell, const int* __restrict__ start
     for (int s = b; s < e; ++s) {
         int i = perm[s];
         R rel[3];
-        if (g.tric) {
+        if (relp) {
+            // written by k_bin_count from the same position
+            const typename V4<R>::T q = relp[i];
+            rel[0] = q.x; rel[1] = q.y; rel[2] = q.z;
+        } else if (g.tric) {
             double p[3], r3[3];
             int c3[3];
             for (int d = 0; d < 3; ++d) {
@@ -1709,14 +1749,27 @@ __global__ void k_forces_gather(int n, int ld, const int* __restrict__ invperm,
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int k = invperm[i];
-    bool bad = false;
+    if constexpr (sizeof(R) == 4) {
+        // fixed point (2^-32 eV/A) -> double: convert the integer, then take
+        // 32 from the exponent (exact: a nonzero int64 is at least 1 in
+        // magnitude); integer sums are always finite
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const double f = Acc<R>::value(facc[(size_t)a * ld + k]);
-        bad |= !isfinite(f);
-        F[(size_t)a * n + i] = f;
+        for (int a = 0; a < 3; ++a) {
+            const long long q = facc[(size_t)a * ld + k];
+            long long b = __double_as_longlong(__ll2double_rn(q));
+            if (q != 0) b -= 32LL << 52;
+            F[(size_t)a * n + i] = __longlong_as_double(b);
+        }
+    } else {
+        bool bad = false;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double f = Acc<R>::value(facc[(size_t)a * ld + k]);
+            bad |= !isfinite(f);
+            F[(size_t)a * n + i] = f;
+        }
+        if (bad) atomicOr(status, ST_NONFINITE);
     }
-    if (bad) atomicOr(status, ST_NONFINITE);
 }
 
 // Forces back to caller order (FP64), accumulators reset to zero.
@@ -1790,9 +1843,10 @@ static __global__ void __launch_bounds__(256) k_reduce_partials(const double* __
 // [2] step count, [3] KE, [4] vmax, [5] dt_max, [6] d_max, [7] last dt,
 // [8..10] sum_i m_i v_ia^2 (eV) for a = x, y, z, [11] thermostat scale of the
 // last chain sweep, [12] thermostat energy, [13..15] barostat scale mu_a
+// [16..19] half kick dt/2 acc_t of each species for the current dt
 constexpr int TH_DT = 0, TH_TIME = 1, TH_STEP = 2, TH_KE = 3, TH_VMAX = 4, TH_DTMAX = 5,
               TH_DMAX = 6, TH_DTLAST = 7, TH_KXX = 8, TH_NHC_S = 11, TH_ENHC = 12,
-              TH_MU = 13, TH_N = 16;
+              TH_MU = 13, TH_HKICK = 16, TH_N = 20;
 // per-block partials of k_kick_thermo: sum m v^2, max |v|^2, sum m v_x^2, v_y^2, v_z^2
 constexpr int KT_PART = 5;
 
@@ -1810,7 +1864,9 @@ __device__ __forceinline__ int species_of(const MassTab& mt, const int32_t* type
     return t < 0 ? 0 : (t >= mt.ntypes ? mt.ntypes - 1 : t);   // flagged by k_cell_finalize
 }
 
-// v += dt/2 F/m ; x += dt v ; wrap periodic coordinates into [0, L)
+// v += dt/2 F/m ; x += dt v ; wrap periodic coordinates into [0, L).  The
+// half kick dt/2 acc_t comes from thermo (k_thermo_step); the wrap is skipped
+// by an integer range test when the coordinate is already inside the box.
 static __global__ void k_kick_drift(Grid g, MassTab mt, const int32_t* __restrict__ types,
                              const double* __restrict__ thermo,
                              double* __restrict__ x, double* __restrict__ v,
@@ -1819,14 +1875,14 @@ static __global__ void k_kick_drift(Grid g, MassTab mt, const int32_t* __restric
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n) return;
     const double dt = thermo[TH_DT];
-    const double acc = mt.acc[species_of(mt, types, i)];
+    const double hk = thermo[TH_HKICK + species_of(mt, types, i)];
     double xn[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         size_t o = (size_t)a * g.n + i;
-        double vv = v[o] + 0.5 * dt * acc * F[o];
+        double vv = v[o] + hk * F[o];
         double xx = x[o] + dt * vv;
-        if (!g.tric && g.pbc[a]) xx -= g.L[a] * floor(xx * g.invL[a]);
+        if (!g.tric && g.pbc[a] && !in_box_bits(xx, g.L[a])) xx = wrap_slow(xx, g.L[a], g.invL[a]);
         v[o] = vv;
         xn[a] = xx;
     }
@@ -1848,44 +1904,63 @@ static __global__ void k_kick_drift(Grid g, MassTab mt, const int32_t* __restric
 }
 
 // v += dt/2 F/m and per-block (sum m v^2, max |v|^2, and with `tensor` the
-// per-dimension sums m v_a^2 the barostat needs; zeros otherwise)
-static __global__ void __launch_bounds__(256) k_kick_thermo(int n, MassTab mt,
+// per-dimension sums m v_a^2 the barostat needs; zeros otherwise).  The half
+// kick comes from thermo; max |v|^2 is reduced on the bit patterns of the
+// (non-negative) doubles.  LOWSUM (FP32 path): sum m v^2 over a warp in FP32
+// (the per-warp sums and everything after them in FP64).  HALF: apply the
+// half kick; TENSOR: the per-dimension sums (compile-time, so that no FP64
+// work of an unused branch issues).
+template <bool LOWSUM, bool HALF, bool TENSOR>
+__global__ void __launch_bounds__(256) k_kick_thermo(int n, MassTab mt,
                                                      const int32_t* __restrict__ types,
                                                      const double* __restrict__ thermo,
                                                      double* __restrict__ v,
                                                      const double* __restrict__ F,
-                                                     double* __restrict__ part, int half_kick,
-                                                     int tensor)
+                                                     double* __restrict__ part)
 {
+    constexpr bool half_kick = HALF, tensor = TENSOR;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double v2 = 0.0, vm = 0.0, va[3] = {0.0, 0.0, 0.0};
+    double v2 = 0.0, va[3] = {0.0, 0.0, 0.0};
+    long long vmb = 0;   // bit pattern of max |v|^2
     if (i < n) {
         const int t = species_of(mt, types, i);
-        const double acc = mt.acc[t];
-        const double dt = half_kick ? thermo[TH_DT] : 0.0;
+        double vm = 0.0, vv[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             size_t o = (size_t)a * n + i;
-            double vv = v[o] + 0.5 * dt * acc * F[o];
-            if (half_kick) v[o] = vv;
-            vm += vv * vv;
-            va[a] = mt.m[t] * vv * vv;
+            vv[a] = v[o];
+            if constexpr (half_kick) {
+                vv[a] += thermo[TH_HKICK + t] * F[o];
+                v[o] = vv[a];
+            }
+            vm += vv[a] * vv[a];
         }
         v2 = mt.m[t] * vm;
+        vmb = __double_as_longlong(vm);
+        if constexpr (tensor)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) va[a] = mt.m[t] * vv[a] * vv[a];
     }
     __shared__ double sh[KT_PART][8];
-    for (int o = 16; o > 0; o >>= 1) {
-        v2 += __shfl_xor_sync(0xffffffffu, v2, o);
-        vm = fmax(vm, __shfl_xor_sync(0xffffffffu, vm, o));
+    if constexpr (LOWSUM) {
+        float v2f = (float)v2;
+        for (int o = 16; o > 0; o >>= 1) v2f += __shfl_xor_sync(0xffffffffu, v2f, o);
+        v2 = (double)v2f;
+    } else {
+        for (int o = 16; o > 0; o >>= 1) v2 += __shfl_xor_sync(0xffffffffu, v2, o);
     }
-    if (tensor) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long u = __shfl_xor_sync(0xffffffffu, vmb, o);
+        vmb = u > vmb ? u : vmb;
+    }
+    if constexpr (tensor) {
         for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
             for (int a = 0; a < 3; ++a) va[a] += __shfl_xor_sync(0xffffffffu, va[a], o);
     }
     if ((threadIdx.x & 31) == 0) {
         sh[0][threadIdx.x >> 5] = v2;
-        sh[1][threadIdx.x >> 5] = vm;
+        sh[1][threadIdx.x >> 5] = __longlong_as_double(vmb);
         for (int a = 0; a < 3; ++a) sh[2 + a][threadIdx.x >> 5] = tensor ? va[a] : 0.0;
     }
     __syncthreads();
@@ -1905,7 +1980,8 @@ static __global__ void __launch_bounds__(256) k_kick_thermo(int n, MassTab mt,
 static __global__ void __launch_bounds__(256) k_thermo_step(const double* __restrict__ part, int nb,
                                                      double ev_amu,
                                                      double* __restrict__ thermo,
-                                                     int advance, int* __restrict__ gate = nullptr)
+                                                     int advance, MassTab mt,
+                                                     int* __restrict__ gate = nullptr)
 {
     if (gate && threadIdx.x == 0) *gate = 0;   // lists are current after this step
     __shared__ double sa[256], sb[256], sk[3][256];
@@ -1942,6 +2018,7 @@ static __global__ void __launch_bounds__(256) k_thermo_step(const double* __rest
         const double dmax = thermo[TH_DMAX];
         if (dmax > 0.0 && vmax > 0.0 && dmax / vmax < dt) dt = dmax / vmax;
         thermo[TH_DT] = dt;
+        for (int t = 0; t < NT_MAX; ++t) thermo[TH_HKICK + t] = 0.5 * dt * mt.acc[t];
     }
 }
 

@@ -64,6 +64,7 @@ struct nep_ctx {
     int *cell_of = nullptr, *slot_of = nullptr, *perm = nullptr, *cell_sorted = nullptr;
     int* invperm = nullptr;          // caller index -> cell-ordered slot
     void* pos4 = nullptr;
+    void* rel4 = nullptr;            // cell-relative position by caller index (binning)
     int2* cnt = nullptr;
     int* nbr = nullptr;
     void* facc = nullptr;
@@ -201,7 +202,7 @@ static void free_scratch(nep_ctx* ctx)
 {
     drop_graphs(ctx);
     free_dev(ctx->cell_of); free_dev(ctx->slot_of); free_dev(ctx->perm);
-    free_dev(ctx->cell_sorted); free_dev(ctx->invperm); free_dev(ctx->pos4); free_dev(ctx->cnt); free_dev(ctx->nbr);
+    free_dev(ctx->cell_sorted); free_dev(ctx->invperm); free_dev(ctx->pos4); free_dev(ctx->rel4); free_dev(ctx->cnt); free_dev(ctx->nbr);
     free_dev(ctx->facc); free_dev(ctx->partials); free_dev(ctx->partials2);
     free_dev(ctx->qr); free_dev(ctx->br); free_dev(ctx->xref); free_dev(ctx->nbr_act);
     free_dev(ctx->cnt_act);
@@ -228,6 +229,7 @@ static int ensure_atoms(nep_ctx* ctx, int n, int M)
     CK(cudaMalloc(&ctx->cell_sorted, sizeof(int) * ld));
     CK(cudaMalloc(&ctx->invperm, sizeof(int) * ld));
     CK(cudaMalloc(&ctx->pos4, p4 * ld));
+    CK(cudaMalloc(&ctx->rel4, p4 * ld));
     CK(cudaMalloc(&ctx->cnt, sizeof(int2) * ld));
     CK(cudaMalloc(&ctx->nbr, sizeof(int) * (size_t)ld * MM));
     CK(cudaMalloc(&ctx->facc, acc * 3 * (size_t)ld));
@@ -372,7 +374,8 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
         CK(cudaMemsetAsync(ctx->count, 0, sizeof(int) * (size_t)(ncell + 1), s));
         CK(cudaMemsetAsync(ctx->pairs, 0, sizeof(unsigned long long) * 2, s));
     }
-    k_bin_count<<<nb, tb, 0, s>>>(g, x, ctx->cell_of, ctx->slot_of, ctx->count, ctx->status, gate);
+    k_bin_count<R><<<nb, tb, 0, s>>>(g, x, ctx->cell_of, ctx->slot_of, ctx->count, ctx->status, gate,
+                                     (typename V4<R>::T*)ctx->rel4);
     count_launch(ctx);
     const int sb = (ncell + SCAN_B - 1) / SCAN_B;
     k_scan_blocks<<<sb, SCAN_T, 0, s>>>(ctx->count, ncell, ctx->start, ctx->scan_sums, gate);
@@ -385,7 +388,7 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     count_launch(ctx);
     k_cell_finalize<R><<<(ncell + 127) / 128, 128, 0, s>>>(
         g, ncell, ctx->start, ctx->perm, x, types, (typename V4<R>::T*)ctx->pos4, ctx->cell_sorted,
-        ctx->status, gate, ctx->invperm);
+        ctx->status, gate, ctx->invperm, (const typename V4<R>::T*)ctx->rel4);
     count_launch(ctx);
     // one species, lists rebuilt every step, FP32: the neighbour kernel also
     // sums the radial descriptor (no separate radial-descriptor pass); the
@@ -927,6 +930,19 @@ static void enqueue_nhc(nep_ctx* ctx, int n, const int32_t* types, double* vel, 
     count_launch(ctx);
 }
 
+// Kick + kinetic statistics (warp sums of m v^2 in FP32 on the FP32 path;
+// the half kick and the per-dimension sums chosen at compile time).
+static auto kick_thermo_kernel(const nep_ctx* ctx, int half_kick, int tensor)
+    -> decltype(&k_kick_thermo<true, true, true>)
+{
+    const bool lo = ctx->precision == NEP_FP32;
+    if (half_kick)
+        return tensor ? (lo ? k_kick_thermo<true, true, true> : k_kick_thermo<false, true, true>)
+                      : (lo ? k_kick_thermo<true, true, false> : k_kick_thermo<false, true, false>);
+    return tensor ? (lo ? k_kick_thermo<true, false, true> : k_kick_thermo<false, false, true>)
+                  : (lo ? k_kick_thermo<true, false, false> : k_kick_thermo<false, false, false>);
+}
+
 // One velocity-Verlet step on stream s:
 //   [NHC(dt/2)] v += dt/2 F/m, x += dt v; F(x); v += dt/2 F/m [NHC(dt/2)];
 //   kinetic energy, max |v| and the next dt.
@@ -941,17 +957,18 @@ static int enqueue_step(nep_ctx* ctx, const Grid& g, nep_md_state* st, cudaStrea
     int* gate = ctx->skin > 0.0 && !ctx->baro_on ? ctx->gate : nullptr;
     int rc = eval(ctx, g, st->xyz, st->types, st->forces, nullptr, s, slot, gate);
     if (rc) return rc;
-    k_kick_thermo<<<nb, tb, 0, s>>>(n, ctx->mt, st->types, ctx->thermo, st->vel, st->forces,
-                                    ctx->vpart, 1, ctx->baro_on);
+    kick_thermo_kernel(ctx, 1, ctx->baro_on)<<<nb, tb, 0, s>>>(n, ctx->mt, st->types, ctx->thermo,
+                                                               st->vel, st->forces, ctx->vpart);
     count_launch(ctx);
     if (ctx->nhc_on) {
         enqueue_nhc(ctx, n, st->types, st->vel, s);
         // kinetic energy and speeds after the thermostat's scaling
-        k_kick_thermo<<<nb, tb, 0, s>>>(n, ctx->mt, st->types, ctx->thermo, st->vel, st->forces,
-                                        ctx->vpart, 0, ctx->baro_on);
+        kick_thermo_kernel(ctx, 0, ctx->baro_on)<<<nb, tb, 0, s>>>(n, ctx->mt, st->types,
+                                                                   ctx->thermo, st->vel,
+                                                                   st->forces, ctx->vpart);
         count_launch(ctx);
     }
-    k_thermo_step<<<1, 256, 0, s>>>(ctx->vpart, nb, EV_AMU, ctx->thermo, 1, gate);
+    k_thermo_step<<<1, 256, 0, s>>>(ctx->vpart, nb, EV_AMU, ctx->thermo, 1, ctx->mt, gate);
     count_launch(ctx);
     return NEP_OK;
 }
@@ -1126,10 +1143,10 @@ int md_step(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
     CK(cudaMemcpyAsync(ctx->thermo, th, sizeof(th), cudaMemcpyHostToDevice, s));
     {
         const int tb = 256, nb = (int)((n + tb - 1) / tb);
-        k_kick_thermo<<<nb, tb, 0, s>>>((int)n, ctx->mt, st->types, ctx->thermo, st->vel,
-                                        st->forces, ctx->vpart, 0, ctx->baro_on);
+        kick_thermo_kernel(ctx, 0, ctx->baro_on)<<<nb, tb, 0, s>>>(
+            (int)n, ctx->mt, st->types, ctx->thermo, st->vel, st->forces, ctx->vpart);
         count_launch(ctx);
-        k_thermo_step<<<1, 256, 0, s>>>(ctx->vpart, nb, EV_AMU, ctx->thermo, 0);
+        k_thermo_step<<<1, 256, 0, s>>>(ctx->vpart, nb, EV_AMU, ctx->thermo, 0, ctx->mt);
         count_launch(ctx);
         if (ctx->nhc_on && ctx->nhc_counted != (int)n) {
             k_group_count<<<1, 256, 0, s>>>((int)n, ctx->nhc_group, ctx->nhc);
@@ -1807,7 +1824,7 @@ extern "C" int nep_compute_static(const nep_params* p, int64_t n_atoms, const do
     CK(cudaMemsetAsync(status, 0, sizeof(int) * 3, s));
     CK(cudaMemsetAsync(pairs, 0, sizeof(unsigned long long) * 2, s));
     const int tb = 256, nb = (n + tb - 1) / tb;
-    k_bin_count<<<nb, tb, 0, s>>>(g, xyz, cell_of, slot_of, count, status);
+    k_bin_count<float><<<nb, tb, 0, s>>>(g, xyz, cell_of, slot_of, count, status);
     const int sb = (ncell + SCAN_B - 1) / SCAN_B;
     k_scan_blocks<<<sb, SCAN_T, 0, s>>>(count, ncell, start, scan_sums);
     k_scan_sums<<<1, SCAN_T, 0, s>>>(scan_sums, sb, start, ncell);
