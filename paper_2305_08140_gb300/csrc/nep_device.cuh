@@ -184,7 +184,7 @@ __global__ void k_bin_count(Grid g, const double* __restrict__ x, int* __restric
         for (int d = 0; d < 3; ++d) {
             double w = p[d];
             if (g.pbc[d] && !in_box_bits(w, g.L[d])) w = wrap_slow(w, g.L[d], g.invL[d]);
-            int cd = (int)floor(w * g.inv_lc[d]);
+            int cd = __double2int_rd(w * g.inv_lc[d]);
             cd = cd < 0 ? 0 : cd;
             cd = cd >= g.nc[d] ? g.nc[d] - 1 : cd;
             c[d] = cd;
@@ -361,6 +361,56 @@ __global__ void k_cell_finalize(Grid g, int ncell, const int* __restrict__ start
         if (invperm) invperm[i] = s;
     }
     if (badtype) atomicOr(status, ST_BADTYPE);
+}
+
+// k_cell_finalize with the cell-relative positions from k_bin_count (rel):
+// one warp per cell.  A cell of at most 32 atoms is ordered by ranking (each
+// lane counts the smaller caller indices of the cell by shuffles) and its
+// atoms are then written by all lanes at once; a larger cell is ordered by
+// lane 0 (insertion sort) and written in chunks of 32.
+template <typename R>
+__global__ void __launch_bounds__(256) k_cell_finalize_w(
+    Grid g, int ncell, const int* __restrict__ start, int* __restrict__ perm,
+    const int32_t* __restrict__ types, typename V4<R>::T* __restrict__ pos4,
+    int* __restrict__ cell_sorted, int* __restrict__ status, const int* __restrict__ gate,
+    int* __restrict__ invperm, const typename V4<R>::T* __restrict__ rel)
+{
+    if (gate && *gate == 0) return;   // lists still valid (Verlet skin)
+    const int c = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (c >= ncell) return;   // whole warps leave together
+    const int b = start[c], e = start[c + 1], cnt = e - b;
+    bool badtype = false;
+    auto place = [&](int s, int i) {
+        const typename V4<R>::T q = rel[i];
+        typename V4<R>::T o;
+        o.x = q.x; o.y = q.y; o.z = q.z;
+        int t = types[i];
+        if (t < 0 || t >= g.ntypes) { badtype = true; t = 0; }
+        o.w = (R)t;
+        pos4[s] = o;
+        cell_sorted[s] = c;
+        if (invperm) invperm[i] = s;
+    };
+    if (cnt <= 32) {
+        const int v = lane < cnt ? perm[b + lane] : 0x7fffffff;
+        int rank = 0;
+        for (int j = 0; j < cnt; ++j) rank += __shfl_sync(0xffffffffu, v, j) < v;
+        if (lane < cnt) {
+            perm[b + rank] = v;
+            place(b + rank, v);
+        }
+    } else {
+        if (lane == 0)
+            for (int s = b + 1; s < e; ++s) {
+                int v = perm[s], t = s;
+                while (t > b && perm[t - 1] > v) { perm[t] = perm[t - 1]; --t; }
+                perm[t] = v;
+            }
+        __syncwarp();
+        for (int s = b + lane; s < e; s += 32) place(s, perm[s]);
+    }
+    if (__any_sync(0xffffffffu, badtype) && lane == 0) atomicOr(status, ST_BADTYPE);
 }
 
 // ----------------------------------------------------------------------------
@@ -1966,11 +2016,15 @@ __global__ void __launch_bounds__(256) k_kick_thermo(int n, MassTab mt,
     __syncthreads();
     if (threadIdx.x == 0) {
         double r[KT_PART] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        long long mb = 0;
         for (int w = 0; w < 8; ++w) {
             r[0] += sh[0][w];
-            r[1] = fmax(r[1], sh[1][w]);
-            for (int a = 0; a < 3; ++a) r[2 + a] += sh[2 + a][w];
+            const long long u = __double_as_longlong(sh[1][w]);
+            mb = u > mb ? u : mb;
+            if constexpr (tensor)
+                for (int a = 0; a < 3; ++a) r[2 + a] += sh[2 + a][w];
         }
+        r[1] = __longlong_as_double(mb);
         for (int c = 0; c < KT_PART; ++c) part[KT_PART * blockIdx.x + c] = r[c];
     }
 }

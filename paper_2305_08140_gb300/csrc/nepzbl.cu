@@ -386,8 +386,9 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     count_launch(ctx);
     k_bin_scatter<<<nb, tb, 0, s>>>(n, ctx->cell_of, ctx->slot_of, ctx->start, ctx->perm, gate);
     count_launch(ctx);
-    k_cell_finalize<R><<<(ncell + 127) / 128, 128, 0, s>>>(
-        g, ncell, ctx->start, ctx->perm, x, types, (typename V4<R>::T*)ctx->pos4, ctx->cell_sorted,
+    // one warp per cell (the positions relative to the cells from k_bin_count)
+    k_cell_finalize_w<R><<<(int)(((size_t)ncell * 32 + 255) / 256), 256, 0, s>>>(
+        g, ncell, ctx->start, ctx->perm, types, (typename V4<R>::T*)ctx->pos4, ctx->cell_sorted,
         ctx->status, gate, ctx->invperm, (const typename V4<R>::T*)ctx->rel4);
     count_launch(ctx);
     // one species, lists rebuilt every step, FP32: the neighbour kernel also
