@@ -458,8 +458,14 @@ struct RadCoef {
 // descriptor work inside the hit branch would run with most lanes idle).
 // TRIC: triclinic cells (stencil offsets are vectors; the orthorhombic
 // instantiation keeps per-axis offsets).
-template <typename R, bool WQ, bool TRIC = false>
-__global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
+// CH: the candidates of a stencil cell are tested in unrolled chunks of
+// NB_CHUNK that only set hit bits (angular, radial); the set bits are stored
+// afterwards in the same order (the lists are identical).  The chunk reads up
+// to NB_CHUNK - 1 positions past the cell, so pos4 must hold NB_CHUNK - 1
+// readable entries past the last atom; the bits of those are masked off.
+constexpr int NB_CHUNK = 16;
+template <typename R, bool WQ, bool TRIC = false, bool CH = false>
+__global__ void __launch_bounds__(128, CH ? 6 : 8) k_neighbors(Grid g, R rcR2, R rcA2,
                                                    const typename V4<R>::T* __restrict__ pos4,
                                                    const int* __restrict__ cell_sorted,
                                                    const int* __restrict__ start,
@@ -514,18 +520,52 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                     const int code = (ox + 1) * 9 + (oy + 1) * 3 + (oz + 1);
                     const int c2 = rowXY + Z;
                     const int e = start[c2 + 1];
-                    for (int m = start[c2]; m < e; ++m) {
-                        const P4 q = pos4[m];
-                        const R dx = q.x - px, dy = q.y - py, dz = q.z - pz;
-                        const R r2 = dx * dx + dy * dy + dz * dz;
-                        const bool hit = r2 < rcR2 && m != k;
-                        const bool ang = r2 < rcA2;
-                        const bool room = sa + sro < M;
-                        if (hit && room)
-                            col[(size_t)(ang ? sa : M - 1 - sro) * ld] = (m << 5) | code;
-                        tot += hit;
-                        sa += hit && room && ang;
-                        sro += hit && room && !ang;
+                    if constexpr (CH) {
+                        for (int m0 = start[c2]; m0 < e; m0 += NB_CHUNK) {
+                            const P4* q0 = pos4 + m0;
+                            unsigned hr = 0u, ha = 0u;   // r < rc_R, r < rc_A
+#pragma unroll
+                            for (int j = 0; j < NB_CHUNK; ++j) {
+                                const P4 q = q0[j];
+                                const R dx = q.x - px, dy = q.y - py, dz = q.z - pz;
+                                const R r2 = dx * dx + dy * dy + dz * dz;
+                                if (r2 < rcR2) hr |= 1u << j;
+                                if (r2 < rcA2) ha |= 1u << j;
+                            }
+                            // this cell's atoms only, never the atom itself
+                            const int nv = e - m0;
+                            unsigned keep = nv >= NB_CHUNK ? 0xffffffffu : (1u << nv) - 1u;
+                            const unsigned self = (unsigned)(k - m0);
+                            if (self < (unsigned)NB_CHUNK) keep &= ~(1u << self);
+                            ha &= hr & keep;
+                            hr &= keep & ~ha;   // radial only
+                            tot += __popc(ha) + __popc(hr);
+                            while (ha) {
+                                const int j = __ffs(ha) - 1;
+                                ha &= ha - 1u;
+                                if (sa + sro < M) col[(size_t)(sa++) * ld] = ((m0 + j) << 5) | code;
+                            }
+                            while (hr) {
+                                const int j = __ffs(hr) - 1;
+                                hr &= hr - 1u;
+                                if (sa + sro < M)
+                                    col[(size_t)(M - 1 - sro++) * ld] = ((m0 + j) << 5) | code;
+                            }
+                        }
+                    } else {
+                        for (int m = start[c2]; m < e; ++m) {
+                            const P4 q = pos4[m];
+                            const R dx = q.x - px, dy = q.y - py, dz = q.z - pz;
+                            const R r2 = dx * dx + dy * dy + dz * dz;
+                            const bool hit = r2 < rcR2 && m != k;
+                            const bool ang = r2 < rcA2;
+                            const bool room = sa + sro < M;
+                            if (hit && room)
+                                col[(size_t)(ang ? sa : M - 1 - sro) * ld] = (m << 5) | code;
+                            tot += hit;
+                            sa += hit && room && ang;
+                            sro += hit && room && !ang;
+                        }
                     }
                 }
             }

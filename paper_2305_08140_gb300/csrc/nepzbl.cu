@@ -228,7 +228,10 @@ static int ensure_atoms(nep_ctx* ctx, int n, int M)
     CK(cudaMalloc(&ctx->perm, sizeof(int) * ld));
     CK(cudaMalloc(&ctx->cell_sorted, sizeof(int) * ld));
     CK(cudaMalloc(&ctx->invperm, sizeof(int) * ld));
-    CK(cudaMalloc(&ctx->pos4, p4 * ld));
+    // NB_CHUNK - 1 entries of slack: the chunked neighbour search reads past
+    // the last atom (those reads are masked off)
+    CK(cudaMalloc(&ctx->pos4, p4 * (ld + NB_CHUNK)));
+    CK(cudaMemset(ctx->pos4, 0, p4 * (ld + NB_CHUNK)));
     CK(cudaMalloc(&ctx->rel4, p4 * ld));
     CK(cudaMalloc(&ctx->cnt, sizeof(int2) * ld));
     CK(cudaMalloc(&ctx->nbr, sizeof(int) * (size_t)ld * MM));
@@ -401,8 +404,11 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     rq.inv_rcR = P.inv_rcR;
     for (int t = 0; t < NR * KR; ++t) rq.hR[t] = P.hR[t];
     for (int t = 0; t < NR; ++t) rq.CR[t] = P.CR[t];
-    auto kn = g.tric ? (fuse_q ? k_neighbors<R, true, true> : k_neighbors<R, false, true>)
-                     : (fuse_q ? k_neighbors<R, true, false> : k_neighbors<R, false, false>);
+    // chunked candidate tests (pos4 holds NB_CHUNK - 1 readable entries past
+    // the last atom, see ensure_atoms)
+    auto kn = g.tric ? (fuse_q ? k_neighbors<R, true, true, true> : k_neighbors<R, false, true, true>)
+                     : (fuse_q ? k_neighbors<R, true, false, true>
+                               : k_neighbors<R, false, false, true>);
     kn<<<(n + 127) / 128, 128, 0, s>>>(
         g, (R)(rl * rl), (R)(ra * ra), (const typename V4<R>::T*)ctx->pos4, ctx->cell_sorted,
         ctx->start, ctx->nbr, ctx->cnt, ctx->status, ctx->status + 1, ctx->pairs, gate, rq,
