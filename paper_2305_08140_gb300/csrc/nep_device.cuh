@@ -465,7 +465,7 @@ struct RadCoef {
 // readable entries past the last atom; the bits of those are masked off.
 constexpr int NB_CHUNK = 16;
 template <typename R, bool WQ, bool TRIC = false, bool CH = false>
-__global__ void __launch_bounds__(128, CH ? 6 : 8) k_neighbors(Grid g, R rcR2, R rcA2,
+__global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                                                    const typename V4<R>::T* __restrict__ pos4,
                                                    const int* __restrict__ cell_sorted,
                                                    const int* __restrict__ start,
