@@ -494,29 +494,27 @@ def run_ours(args):
         nep64.close()
         del st64
 
-    # end to end through the public API with host buffers: each step copies
-    # x, v, F from pinned host memory, runs one MD step and reads x, v, F and E back
+    # end to end through the C ABI with host buffers (md_step_host): every step
+    # copies x, v, F and the species from pinned host memory, runs one MD step
+    # and copies x, v, F and the step's energies, virial and status back
     k_e2e = max(1, min(args.steps, 10))
-    nep.md(st, 1)                      # the 1-step graph, captured before timing
-    hx = st.xyz.cpu().pin_memory()
-    hv = st.vel.cpu().pin_memory()
-    hf = st.forces.cpu().pin_memory()
-    dx, dv, df = st.xyz, st.vel, st.forces
+    nep.set_option(N.NEP_OPT_TIMING, 0)
+    hst = N.MDState(st.xyz.cpu().pin_memory(), st.vel.cpu().pin_memory(), s.box, s.pbc,
+                    dt_max=1.0, types=st.types.cpu().pin_memory(),
+                    forces=st.forces.cpu().pin_memory())
+    nep.md_host(hst, 1, stream)        # device mirror allocated, 1-step graph captured
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(k_e2e):
-        dx.copy_(hx, non_blocking=True)
-        dv.copy_(hv, non_blocking=True)
-        df.copy_(hf, non_blocking=True)
-        nep.md(st, 1, stream)
-        hx.copy_(dx, non_blocking=True)
-        hv.copy_(dv, non_blocking=True)
-        hf.copy_(df, non_blocking=True)
-        torch.cuda.synchronize()
-        _ = st.potential_energy
+        nep.md_host(hst, 1, stream)
+        _ = hst.potential_energy
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": ws * n * k_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 9 * 8 * n,
-           "d2h_bytes_per_step": 9 * 8 * n + 8, "steps": k_e2e}
+    # per step: x, v, F (3 x 24 B) and species (4 B) per atom in plus the thermo
+    # block (20 doubles); x, v, F out plus status, pair counts, energy/virial and
+    # thermo (3 + 4 + 10 + 20 words)
+    e2e = {"value": ws * n * k_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 76 * n + 160,
+           "d2h_bytes_per_step": 72 * n + 268, "steps": k_e2e,
+           "call": "md_step_host (C ABI, host arrays)"}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.skip_cpu:

@@ -168,6 +168,17 @@ typedef struct nep_md_state {
  * each step; state->box is updated). */
 int md_step(nep_ctx* ctx, nep_md_state* state, int n_steps, void* stream);
 
+/* md_step with the state in HOST memory: xyz, vel, forces and types of
+ * `state` are host arrays (pinned or pageable; device memory is rejected with
+ * NEP_ERR_INVALID_ARG).  The call copies them to device buffers the context
+ * owns (allocated on the first call and when n_atoms grows; freed by
+ * nep_free), advances n_steps exactly as md_step (Sec. II.B), copies xyz, vel
+ * and forces back and updates the outputs of `state`; it returns after the
+ * copies have completed (the stream is synchronised).  forces are copied in
+ * only when forces_valid is set.  Errors as md_step; on an error the host
+ * arrays are left unchanged. */
+int md_step_host(nep_ctx* ctx, nep_md_state* state, int n_steps, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Cascade protocol (Sec. II.B): the atoms within 3 a0 of the box boundaries
  * are held at 300 K by a Nose-Hoover chain thermostat, the system is first

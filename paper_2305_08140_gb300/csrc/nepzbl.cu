@@ -75,6 +75,12 @@ struct nep_ctx {
     double* vpart = nullptr;
     int *count = nullptr, *start = nullptr, *scan_sums = nullptr;
     double* backup = nullptr;        // x, v, F copies for MD rollback
+    // device mirror of a host MD state (md_step_host)
+    double* hm_x = nullptr;
+    double* hm_v = nullptr;
+    double* hm_f = nullptr;
+    int32_t* hm_t = nullptr;
+    int64_t hm_cap = 0;
     double* thermo = nullptr;        // TH_N doubles
     double* thermo_backup = nullptr;
     double* result = nullptr;        // NPART doubles (E, W)
@@ -778,6 +784,7 @@ void nep_free(nep_ctx* ctx)
     free_dev(ctx->d_scaler);
     free_dev(ctx->nhc); free_dev(ctx->nhc_backup); free_dev(ctx->d_box); free_dev(ctx->pka_part);
     free_dev(ctx->pka_atom);
+    free_dev(ctx->hm_x); free_dev(ctx->hm_v); free_dev(ctx->hm_f); free_dev(ctx->hm_t);
     if (ctx->h_result) cudaFreeHost(ctx->h_result);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->h_pairs) cudaFreeHost(ctx->h_pairs);
@@ -1236,6 +1243,63 @@ int md_step(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
         st->potential_energy = ctx->h_result[0];
         for (int t = 0; t < 9; ++t) st->virial[t] = ctx->h_result[1 + t];
     }
+    return NEP_OK;
+}
+
+int md_step_host(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
+{
+    if (!ctx) return NEP_ERR_INVALID_ARG;
+    if (!st || n_steps < 0) return fail(ctx, NEP_ERR_INVALID_ARG, "bad state or step count");
+    const int64_t n = st->n_atoms;
+    if (n <= 0 || n >= (1 << 26)) return fail(ctx, NEP_ERR_INVALID_ARG, "n_atoms must be in [1, 2^26)");
+    const void* arrays[4] = {st->xyz, st->vel, st->forces, st->types};
+    const char* names[4] = {"xyz", "vel", "forces", "types"};
+    CK(cudaSetDevice(ctx->device));
+    for (int t = 0; t < 4; ++t) {
+        if (!arrays[t]) return fail(ctx, NEP_ERR_INVALID_ARG, "%s is NULL", names[t]);
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, arrays[t]) != cudaSuccess) {
+            cudaGetLastError();   // plain host memory unknown to CUDA: accepted
+        } else if (at.type == cudaMemoryTypeDevice) {
+            return fail(ctx, NEP_ERR_INVALID_ARG,
+                        "%s is device memory: md_step_host takes host arrays (md_step takes "
+                        "device arrays)", names[t]);
+        }
+    }
+    if (n > ctx->hm_cap) {
+        cudaDeviceSynchronize();
+        drop_graphs(ctx);   // graphs hold the old mirror's addresses
+        free_dev(ctx->hm_x); free_dev(ctx->hm_v); free_dev(ctx->hm_f); free_dev(ctx->hm_t);
+        ctx->hm_cap = 0;
+        CK(cudaMalloc(&ctx->hm_x, sizeof(double) * 3 * (size_t)n));
+        CK(cudaMalloc(&ctx->hm_v, sizeof(double) * 3 * (size_t)n));
+        CK(cudaMalloc(&ctx->hm_f, sizeof(double) * 3 * (size_t)n));
+        CK(cudaMalloc(&ctx->hm_t, sizeof(int32_t) * (size_t)n));
+        ctx->hm_cap = n;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t b3 = sizeof(double) * 3 * (size_t)n;
+    CK(cudaMemcpyAsync(ctx->hm_x, st->xyz, b3, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->hm_v, st->vel, b3, cudaMemcpyHostToDevice, s));
+    if (st->forces_valid) CK(cudaMemcpyAsync(ctx->hm_f, st->forces, b3, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->hm_t, st->types, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s));
+    nep_md_state d = *st;
+    d.xyz = ctx->hm_x;
+    d.vel = ctx->hm_v;
+    d.forces = ctx->hm_f;
+    d.types = ctx->hm_t;
+    int rc = md_step(ctx, &d, n_steps, stream);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(st->xyz, ctx->hm_x, b3, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(st->vel, ctx->hm_v, b3, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(st->forces, ctx->hm_f, b3, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    // outputs of the step (the arrays are the caller's again)
+    d.xyz = st->xyz;
+    d.vel = st->vel;
+    d.forces = st->forces;
+    d.types = st->types;
+    *st = d;
     return NEP_OK;
 }
 

@@ -29,7 +29,7 @@ NEP_OPT_GRAPH_CHUNK = 2
 NEP_OPT_NBR_CAPACITY = 3
 NEP_OPT_SKIN_MILLIANGSTROM = 4
 
-EXPORTED = ("nep_init", "nep_free", "nep_last_error", "nep_compute", "md_step",
+EXPORTED = ("nep_init", "nep_free", "nep_last_error", "nep_compute", "md_step", "md_step_host",
             "nep_get_stats", "nep_set_option", "nep_reset_stats", "nep_compute_static",
             "nep_set_params", "nep_batch_forward", "nep_batch_backward", "nep_batch_loss_grad",
             "nep_batch_autotune", "nep_population_loss", "nep_snes_generation",
@@ -121,6 +121,8 @@ def load(build: bool = True):
     L.nep_compute.restype = C.c_int
     L.md_step.argtypes = [vp, C.POINTER(NepMdState), C.c_int, vp]
     L.md_step.restype = C.c_int
+    L.md_step_host.argtypes = [vp, C.POINTER(NepMdState), C.c_int, vp]
+    L.md_step_host.restype = C.c_int
     L.nep_get_stats.argtypes = [vp, C.POINTER(NepStats)]
     L.nep_get_stats.restype = C.c_int
     L.nep_set_option.argtypes = [vp, C.c_int, C.c_int64]
@@ -263,6 +265,13 @@ class NEP:
 
     def md(self, state: "MDState", n_steps: int, stream=None):
         self._check(self.lib.md_step(self.ctx, C.byref(state.c), int(n_steps), _stream_ptr(stream)))
+        return state
+
+    def md_host(self, state: "MDState", n_steps: int, stream=None):
+        """md_step on a state whose tensors live in host memory (CPU tensors,
+        pinned or not): the library copies them in, steps and copies them back."""
+        self._check(self.lib.md_step_host(self.ctx, C.byref(state.c), int(n_steps),
+                                          _stream_ptr(stream)))
         return state
 
     def set_thermostat(self, temperature=None, tau=100.0, chain=4, group=None):

@@ -307,3 +307,50 @@ def test_md_skin_variable_timestep_clump_fp64():
     assert np.abs(_min_image(st.xyz.cpu().numpy().T - p, s.box, s.pbc)).max() < 1e-8
     assert m.stats()["list_builds_skin"] < 30
     m.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_md_step_host_buffers(precision):
+    """md_step_host with the state in (pinned and pageable) host memory: the
+    same trajectory as md_step on device memory over calls of one and several
+    steps -- bit for bit on the FP32 path (fixed-point force sums), to
+    rounding on the FP64 path (its double atomics sum in any order) -- and
+    the FP64 path also against the oracle."""
+    import torch
+    from paper_2305_08140_gb300 import nepzbl as N
+    s = I.small_box((6, 6, 7), sigma=0.1, seed=31)
+    s.vel = I.maxwell_boltzmann(np.random.default_rng(32), s.n, 600.0)
+    m = nep(precision)
+    dev = N.MDState(N.to_device_soa(s.pos), N.to_device_soa(s.vel), s.box, s.pbc, dt_max=1.0)
+    m.md(dev, 1)
+    m.md(dev, 4)
+    m.md(dev, 1)
+    x = torch.tensor(np.ascontiguousarray(s.pos.T), dtype=torch.float64).pin_memory()
+    v = torch.tensor(np.ascontiguousarray(s.vel.T), dtype=torch.float64)   # pageable
+    host = N.MDState(x, v, s.box, s.pbc, dt_max=1.0)
+    assert not host.xyz.is_cuda and not host.forces.is_cuda
+    m.md_host(host, 1)
+    m.md_host(host, 4)
+    m.md_host(host, 1)
+    assert host.step == dev.step == 6
+    same = (lambda a, b, tol: np.array_equal(a, b)) if precision == "fp32" else \
+        (lambda a, b, tol: np.max(np.abs(a - b)) <= tol)
+    assert same(host.xyz.numpy(), dev.xyz.cpu().numpy(), 1e-12)
+    assert same(host.vel.numpy(), dev.vel.cpu().numpy(), 1e-15)
+    assert same(host.forces.numpy(), dev.forces.cpu().numpy(), 1e-11)
+    assert same(np.array([host.potential_energy, host.kinetic_energy]),
+                np.array([dev.potential_energy, dev.kinetic_energy]), 1e-10)
+    if precision == "fp64":
+        p, vo, F, th = O.md(I.nep_model(1), s.pos, s.vel, s.box, s.pbc, s.mass, 1.0, 6)
+        assert np.abs(_min_image(host.xyz.numpy().T - p, s.box, s.pbc)).max() < 1e-9
+        assert np.abs(host.forces.numpy().T - F).max() < 1e-9
+        assert host.potential_energy == pytest.approx(th[-1, 2], abs=1e-8)
+
+
+def test_md_step_host_rejects_device_arrays():
+    from paper_2305_08140_gb300 import nepzbl as N
+    s = I.small_box((6, 6, 6), sigma=0.05, seed=33)
+    m = nep("fp32")
+    dev = N.MDState(N.to_device_soa(s.pos), N.to_device_soa(s.vel), s.box, s.pbc, dt_max=1.0)
+    with pytest.raises(N.NepError, match="md_step_host takes host arrays"):
+        m.md_host(dev, 1)
