@@ -30,7 +30,7 @@ constexpr double EV_AMU = 1.602176634e-19 / 1.66053906660e-27 * 1e-10;
 constexpr double KB_EV = 8.617333262e-5;
 constexpr double EV_A3_GPA = 160.21766208;
 // longest neighbour list (slots) the force kernel stages in shared memory
-constexpr int STAGE_MAX_SLOTS = 112;
+constexpr int STAGE_MAX_SLOTS = 32;
 
 thread_local std::string g_init_error;
 
