@@ -118,15 +118,13 @@ NEP_HD void cheb(R r, R inv_rc, R* T, R* dT, R& fc, R& dfc, R& dxdr)
 }
 
 // Real Schmidt harmonics R_lm at u (homogeneous polynomials; u need not be a
-// unit vector, then the values are R_lm(u) = |u|^l Y_lm(u/|u|)).
+// unit vector, then the values are R_lm(u) = |u|^l Y_lm(u/|u|)), in two
+// parts: l = 1, 2 (Y[0..7]) and l = 3, 4 (Y[8..23]), so that a caller can
+// consume the first part before forming the second.
 template <typename R>
-NEP_HD void harmonics(R x, R y, R z, R* Y)
+NEP_HD void harmonics_l12(R x, R y, R z, R* Y)
 {
-    const R s3 = R(1.7320508075688772), s6_4 = R(0.6123724356957945),
-            s15 = R(3.872983346207417), s15_2 = R(1.9364916731037085),
-            s10_4 = R(0.7905694150420949), s5_4 = R(0.5590169943749475),
-            s5_2 = R(1.118033988749895), s70_4 = R(2.091650066335189),
-            s35_8 = R(0.739509972887452), s35_2 = R(2.958039891549808);
+    const R s3 = R(1.7320508075688772);
     R x2 = x * x, y2 = y * y, z2 = z * z, rho2 = x2 + y2;
     R xy = x * y, xmy = x2 - y2;
     // l = 1
@@ -137,6 +135,19 @@ NEP_HD void harmonics(R x, R y, R z, R* Y)
     Y[5] = s3 * y * z;
     Y[6] = R(0.5) * s3 * xmy;
     Y[7] = s3 * xy;
+}
+
+// l = 3, 4: writes Y[8..23]
+template <typename R>
+NEP_HD void harmonics_l34(R x, R y, R z, R* Y)
+{
+    const R s6_4 = R(0.6123724356957945), s15 = R(3.872983346207417),
+            s15_2 = R(1.9364916731037085), s10_4 = R(0.7905694150420949),
+            s5_4 = R(0.5590169943749475), s5_2 = R(1.118033988749895),
+            s70_4 = R(2.091650066335189), s35_8 = R(0.739509972887452),
+            s35_2 = R(2.958039891549808);
+    R x2 = x * x, y2 = y * y, z2 = z * z, rho2 = x2 + y2;
+    R xy = x * y, xmy = x2 - y2;
     // l = 3
     R a3 = R(4) * z2 - rho2;
     Y[8] = z * (z2 - R(1.5) * rho2);
@@ -158,6 +169,13 @@ NEP_HD void harmonics(R x, R y, R z, R* Y)
     Y[21] = s70_4 * z * s3m;
     Y[22] = s35_8 * (xmy * xmy - R(4) * x2 * y2);
     Y[23] = s35_2 * xy * xmy;
+}
+
+template <typename R>
+NEP_HD void harmonics(R x, R y, R z, R* Y)
+{
+    harmonics_l12(x, y, z, Y);
+    harmonics_l34(x, y, z, Y);
 }
 
 // V = sum_lm G[lm] grad R_lm (u), the gradients of the homogeneous

@@ -17,6 +17,7 @@
 #include "../../include/nepzbl.h"
 #include "nep_batch.cuh"
 #include "nep_batch_launch.h"
+#include "nep_tmem.cuh"
 
 using namespace nepk;
 
@@ -31,6 +32,8 @@ constexpr double KB_EV = 8.617333262e-5;
 constexpr double EV_A3_GPA = 160.21766208;
 // longest neighbour list (slots) the force kernel stages in shared memory
 constexpr int STAGE_MAX_SLOTS = 32;
+// the one-species FP32 angular kernel keeps its per-atom angular state in Tensor Memory
+constexpr bool USE_TMEM_ANG = true;
 
 thread_local std::string g_init_error;
 
@@ -465,10 +468,24 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
                                       sizeof(int) * STAGE_MAX_SLOTS * TILE)));
         ctx->nep_smem_set[ks] = 1;
     }
-    kang<<<tiles, TILE, stage_bytes, s>>>(P, g, p4, lnbr, lcnt, ctx->perm, x, (const R*)ctx->qr,
-                                          (typename V4<R>::T*)ctx->br, fa, ctx->partials,
-                                          site_energy, ctx->status, stage_slots, coef);
-    count_launch(ctx);
+    bool on_tmem = false;
+    if constexpr (sizeof(R) == 4) {
+        if (!ms && USE_TMEM_ANG) {
+            // one species, FP32: the angular state in Tensor Memory
+            k_nep_ang_tm<<<tiles, TILE, stage_bytes, s>>>(
+                P, g, p4, lnbr, lcnt, ctx->perm, x, (const float*)ctx->qr, (float4*)ctx->br, fa,
+                ctx->partials, site_energy, ctx->status, stage_slots);
+            count_launch(ctx);
+            on_tmem = true;
+        }
+    }
+    if (!on_tmem) {
+        kang<<<tiles, TILE, stage_bytes, s>>>(P, g, p4, lnbr, lcnt, ctx->perm, x,
+                                              (const R*)ctx->qr, (typename V4<R>::T*)ctx->br, fa,
+                                              ctx->partials, site_energy, ctx->status,
+                                              stage_slots, coef);
+        count_launch(ctx);
+    }
     // radial pair forces (all pairs, small state)
     (ms ? k_radial_force<R, true> : k_radial_force<R, false>)<<<tiles, TILE, 0, s>>>(
         P, g, p4, lnbr, lcnt, (const typename V4<R>::T*)ctx->br, fa,
