@@ -57,11 +57,11 @@ FP32_LANES = 128
 #   per angular pair, force pass: Chebyshev with derivatives 40,
 #     g_n and g'_n 190, harmonics 60, G_lm and G'_lm 480, S 96,
 #     gradient polynomial contraction ~200, assembly 12                     -> 1078
-# DRAM bytes (read + write) of the two timed force kernels (k_nep_ang +
+# DRAM bytes (read + write) of the two timed force kernels (k_nep_ang_tm +
 # k_radial_force) per atom, from one ncu capture of the same build on the
 # 1,024,000-atom slab (profiles/force_kernels_ncu_full_slab_1024000.md):
-# 516.3 MB per launch pair; scaled by the atom count.
-TRAFFIC_PER_ATOM = 516.3e6 / 1.024e6
+# 517.3 MB per launch pair; scaled by the atom count.
+TRAFFIC_PER_ATOM = 517.3e6 / 1.024e6
 FLOP_ATOM = 4630
 FLOP_PAIR_R = 128 + 122
 FLOP_PAIR_A = 424 + 1078
@@ -543,8 +543,9 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk,
         "roofline": {"bound": "alu",
-                     "kernel": ("k_nep_ang + k_radial_force (angular descriptor, network, "
-                                "forces; radial descriptor summed in k_neighbors)" if q_fused
+                     "kernel": ("k_nep_ang_tm + k_radial_force (angular descriptor, network, "
+                                "forces, angular state in Tensor Memory; radial descriptor "
+                                "summed in k_neighbors)" if q_fused
                                 else "k_radial_q + k_nep_ang + k_radial_force"),
                      "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops,
