@@ -60,8 +60,8 @@ FP32_LANES = 128
 # DRAM bytes (read + write) of the two timed force kernels (k_nep_ang_tm +
 # k_radial_force) per atom, from one ncu capture of the same build on the
 # 1,024,000-atom slab (profiles/force_kernels_ncu_full_slab_1024000.md):
-# 517.3 MB per launch pair; scaled by the atom count.
-TRAFFIC_PER_ATOM = 517.3e6 / 1.024e6
+# 516.6 MB per launch pair; scaled by the atom count.
+TRAFFIC_PER_ATOM = 516.6e6 / 1.024e6
 FLOP_ATOM = 4630
 FLOP_PAIR_R = 128 + 122
 FLOP_PAIR_A = 424 + 1078

@@ -234,6 +234,10 @@ typedef struct nep_stats {
     int32_t radial_q_in_neighbor_kernel;  /* 1: the last evaluation summed the radial
                                              descriptor in the neighbour-list kernel (one
                                              species, lists rebuilt every step) */
+    int32_t angular_state_in_tmem;        /* 1: the last evaluation kept the angular
+                                             descriptor sums and adjoint in Tensor Memory
+                                             (FP32, one species, at most 48 angular
+                                             neighbours on every atom) */
 } nep_stats;
 
 int nep_get_stats(const nep_ctx* ctx, nep_stats* out);

@@ -1470,8 +1470,13 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
                                                   double* __restrict__ partials,
                                                   double* __restrict__ site_energy,
                                                   int* __restrict__ status, int stage_slots,
-                                                  const R* __restrict__ coef)
+                                                  const R* __restrict__ coef,
+                                                  const int* __restrict__ ang_max = nullptr,
+                                                  int ang_lim = 0)
 {
+    // with ang_max: this launch handles only evaluations with more than
+    // ang_lim angular neighbours on some atom (k_nep_ang_tm takes the others)
+    if (ang_max && *ang_max <= ang_lim) return;
     using A_ = Acc<R>;
     using P4 = typename V4<R>::T;
     __shared__ P4 s_off[27];

@@ -45,6 +45,19 @@ __device__ __forceinline__ void tm_ld8(uint32_t a, float* v)
 }
 
 __device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// wait::ld that also names the 24 registers it makes valid, so that no use of
+// them can be scheduled before it
+__device__ __forceinline__ void tm_wait_ld24(float* v)
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]),
+                   "+f"(v[6]), "+f"(v[7]), "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]),
+                   "+f"(v[12]), "+f"(v[13]), "+f"(v[14]), "+f"(v[15]), "+f"(v[16]),
+                   "+f"(v[17]), "+f"(v[18]), "+f"(v[19]), "+f"(v[20]), "+f"(v[21]),
+                   "+f"(v[22]), "+f"(v[23])
+                 :
+                 : "memory");
+}
 __device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tm_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -63,9 +76,13 @@ __device__ __forceinline__ void tm_st24(uint32_t tb, int n, const float* v)
     tm_st8(tb + (uint32_t)(n * NLM + 16), v + 16);
 }
 
-// force_pair_ang with the adjoint in Tensor Memory (warp-collective).
+// force_pair_ang with the adjoint in Tensor Memory (warp-collective).  buf[0]
+// holds radial channel 0, loaded before the call and not yet waited for;
+// with `prefetch` (warp-uniform) channel 0 is loaded again into buf[0] for
+// the next pair as soon as this pair's contraction is done.
 __device__ __forceinline__ void force_pair_ang_tm(const Model<float>& P, float r, float inv_r,
                                                   float ux, float uy, float uz, uint32_t tb,
+                                                  float (&buf)[2][NLM], bool prefetch,
                                                   float& fx, float& fy, float& fz)
 {
     float T[KA], dT[KA], fc, dfc, dxdr;
@@ -86,9 +103,7 @@ __device__ __forceinline__ void force_pair_ang_tm(const Model<float>& P, float r
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm) { G[lm] = 0.f; Dd[lm] = 0.f; }
     // channel n + 1 is loaded while channel n is used
-    float buf[2][NLM];
-    tm_ld24(tb, 0, buf[0]);
-    tm_wait_ld();
+    tm_wait_ld24(buf[0]);
 #pragma unroll
     for (int n = 0; n < NA; ++n) {
         if (n + 1 < NA) tm_ld24(tb, n + 1, buf[(n + 1) & 1]);
@@ -97,8 +112,9 @@ __device__ __forceinline__ void force_pair_ang_tm(const Model<float>& P, float r
             G[lm] += buf[n & 1][lm] * gn[n];
             Dd[lm] += buf[n & 1][lm] * dgn[n];
         }
-        if (n + 1 < NA) tm_wait_ld();
+        if (n + 1 < NA) tm_wait_ld24(buf[(n + 1) & 1]);
     }
+    if (prefetch) tm_ld24(tb, 0, buf[0]);   // the next pair's channel 0
     float Y[NLM];
     nepm::harmonics(ux, uy, uz, Y);
     float sang = 0.f;
@@ -116,15 +132,19 @@ __device__ __forceinline__ void force_pair_ang_tm(const Model<float>& P, float r
 
 // k_nep_ang (one species, FP32) with the angular state in Tensor Memory; same
 // arguments and outputs.  At most TM_COLS x 3 columns are held per SM, so the
-// allocation never waits.
+// allocation never waits.  It handles the evaluations whose largest angular
+// neighbour count (*ang_max, from the neighbour kernel) is at most ang_lim and
+// returns at once otherwise (before allocating), k_nep_ang taking those.
 __global__ void __launch_bounds__(TILE, 3)
     k_nep_ang_tm(const Model<float> P, const Grid g, const float4* __restrict__ pos4,
                  const int* __restrict__ nbr, const int2* __restrict__ cnt,
                  const int* __restrict__ perm, const double* __restrict__ x64,
                  const float* __restrict__ qr, float4* __restrict__ br,
                  long long* __restrict__ facc, double* __restrict__ partials,
-                 double* __restrict__ site_energy, int* __restrict__ status, int stage_slots)
+                 double* __restrict__ site_energy, int* __restrict__ status, int stage_slots,
+                 const int* __restrict__ ang_max, int ang_lim)
 {
+    if (*ang_max > ang_lim) return;   // whole grid: k_nep_ang runs instead
     using A_ = Acc<float>;
     __shared__ float4 s_off[27];
     __shared__ int s_max;
@@ -255,7 +275,7 @@ __global__ void __launch_bounds__(TILE, 3)
     for (int n = 0; n < NA; ++n) {
         float v[NLM];
         tm_ld24(tb, n, v);
-        tm_wait_ld();
+        tm_wait_ld24(v);
         float dq4[5];
         nepm::fourbody(&v[3], dq4);
         const float a4 = a[NR + LM * NA + n];
@@ -296,6 +316,8 @@ __global__ void __launch_bounds__(TILE, 3)
     const int nmax = __reduce_max_sync(0xffffffffu, na);
     int ent_n = na > 0 ? entry(0) : 0;
     float4 pj_n = na > 0 ? pos4[ent_n >> 5] : pi;
+    float buf[2][NLM];   // adjoint of two radial channels (see force_pair_ang_tm)
+    if (nmax > 0) tm_ld24(tb, 0, buf[0]);
     for (int s = 0; s < nmax; ++s) {
         const bool act = s < na;
         const int ent = ent_n;
@@ -313,7 +335,8 @@ __global__ void __launch_bounds__(TILE, 3)
         const float inv_r = nepm::nep_rsqrt(r2);
         const float r = r2 * inv_r;
         float fx, fy, fz;
-        force_pair_ang_tm(P, r, inv_r, dx * inv_r, dy * inv_r, dz * inv_r, tb, fx, fy, fz);
+        force_pair_ang_tm(P, r, inv_r, dx * inv_r, dy * inv_r, dz * inv_r, tb, buf, s + 1 < nmax,
+                          fx, fy, fz);
         if (in) {
             bad |= !isfinite(fx + fy + fz);
             long long cx = A_::conv(fx), cy = A_::conv(fy), cz = A_::conv(fz);

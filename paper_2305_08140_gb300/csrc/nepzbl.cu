@@ -33,7 +33,12 @@ constexpr double EV_A3_GPA = 160.21766208;
 // longest neighbour list (slots) the force kernel stages in shared memory
 constexpr int STAGE_MAX_SLOTS = 32;
 // the one-species FP32 angular kernel keeps its per-atom angular state in Tensor Memory
+// unless this evaluation has an atom with more than TMEM_MAX_ANG angular neighbours
+// (dense clumps, where the register kernel measured faster): both kernels are
+// launched and each returns at once unless the neighbour kernel's device-side
+// maximum selects it, so the choice depends on the data of this evaluation only
 constexpr bool USE_TMEM_ANG = true;
+constexpr int TMEM_MAX_ANG = 48;
 
 thread_local std::string g_init_error;
 
@@ -114,6 +119,8 @@ struct nep_ctx {
     int capture_timed = 0;
     int nep_smem_set[4] = {0, 0, 0, 0};
     int radial_q_fused = 0;          // last evaluation summed q in the neighbour kernel
+    int ang_tmem = 0;                // last evaluation ran the Tensor-Memory angular kernel
+    int ang_dispatch = 0;            // last evaluation launched both angular kernels
     // Nose-Hoover chain thermostat on a group, Berendsen barostat (MD)
     int nhc_on = 0;
     NhcParams nhc_p;
@@ -468,24 +475,24 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
                                       sizeof(int) * STAGE_MAX_SLOTS * TILE)));
         ctx->nep_smem_set[ks] = 1;
     }
-    bool on_tmem = false;
+    // status[2]: the largest angular neighbour count of this evaluation
+    const bool dispatch = sizeof(R) == 4 && !ms && USE_TMEM_ANG;
+    ctx->ang_dispatch = dispatch ? 1 : 0;
     if constexpr (sizeof(R) == 4) {
-        if (!ms && USE_TMEM_ANG) {
+        if (dispatch) {
             // one species, FP32: the angular state in Tensor Memory
             k_nep_ang_tm<<<tiles, TILE, stage_bytes, s>>>(
                 P, g, p4, lnbr, lcnt, ctx->perm, x, (const float*)ctx->qr, (float4*)ctx->br, fa,
-                ctx->partials, site_energy, ctx->status, stage_slots);
+                ctx->partials, site_energy, ctx->status, stage_slots, ctx->status + 2,
+                TMEM_MAX_ANG);
             count_launch(ctx);
-            on_tmem = true;
         }
     }
-    if (!on_tmem) {
-        kang<<<tiles, TILE, stage_bytes, s>>>(P, g, p4, lnbr, lcnt, ctx->perm, x,
-                                              (const R*)ctx->qr, (typename V4<R>::T*)ctx->br, fa,
-                                              ctx->partials, site_energy, ctx->status,
-                                              stage_slots, coef);
-        count_launch(ctx);
-    }
+    kang<<<tiles, TILE, stage_bytes, s>>>(P, g, p4, lnbr, lcnt, ctx->perm, x, (const R*)ctx->qr,
+                                          (typename V4<R>::T*)ctx->br, fa, ctx->partials,
+                                          site_energy, ctx->status, stage_slots, coef,
+                                          dispatch ? ctx->status + 2 : nullptr, TMEM_MAX_ANG);
+    count_launch(ctx);
     // radial pair forces (all pairs, small state)
     (ms ? k_radial_force<R, true> : k_radial_force<R, false>)<<<tiles, TILE, 0, s>>>(
         P, g, p4, lnbr, lcnt, (const typename V4<R>::T*)ctx->br, fa,
@@ -555,6 +562,7 @@ static int readback(nep_ctx* ctx, cudaStream_t s)
     CK(cudaStreamSynchronize(s));
     ctx->last_max_total = ctx->h_status[1];
     ctx->last_max_ang = ctx->h_status[2];
+    ctx->ang_tmem = ctx->ang_dispatch && ctx->h_status[2] <= TMEM_MAX_ANG ? 1 : 0;
     ctx->last_pairs_r = (long long)ctx->h_pairs[0];
     ctx->last_pairs_a = (long long)ctx->h_pairs[1];
     return NEP_OK;
@@ -868,6 +876,7 @@ int nep_get_stats(const nep_ctx* ctx, nep_stats* out)
         nb = 0;
     out->list_builds_skin = (int64_t)nb;
     out->radial_q_in_neighbor_kernel = ctx->radial_q_fused;
+    out->angular_state_in_tmem = ctx->ang_tmem;
     return NEP_OK;
 }
 

@@ -72,7 +72,7 @@ class NepStats(C.Structure):
                 ("pairs_angular", C.c_int64), ("max_nbr_radial", C.c_int32),
                 ("max_nbr_angular", C.c_int32), ("nbr_capacity", C.c_int32),
                 ("graph_chunk", C.c_int32), ("list_builds_skin", C.c_int64),
-                ("radial_q_in_neighbor_kernel", C.c_int32)]
+                ("radial_q_in_neighbor_kernel", C.c_int32), ("angular_state_in_tmem", C.c_int32)]
 
 
 class NepTargets(C.Structure):

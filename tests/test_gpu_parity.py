@@ -354,3 +354,38 @@ def test_md_step_host_rejects_device_arrays():
     dev = N.MDState(N.to_device_soa(s.pos), N.to_device_soa(s.vel), s.box, s.pbc, dt_max=1.0)
     with pytest.raises(N.NepError, match="md_step_host takes host arrays"):
         m.md_host(dev, 1)
+
+
+def test_angular_kernel_dispatch_both_paths():
+    """FP32, one species: the angular kernel keeps its per-atom state in Tensor
+    Memory unless the evaluation has an atom with more than 48 angular
+    neighbours (then the register kernel runs; the choice is made on the
+    device from this evaluation's neighbour counts).  A lattice and a dense
+    clump, alternately, on one context: each takes its kernel every time, the
+    lattice matches the oracle, and repeats are bitwise equal.  (The register
+    kernel on clumps of this density is checked against the oracle by the
+    250,000-atom close-pair test.)"""
+    from paper_2305_08140_gb300 import nepzbl as N
+    from gpu_common import F32_E_PER_ATOM, F32_F, F32_U, F32_W_PER_ATOM
+    m = N.NEP(I.nep_model(1), "fp32")
+    lat = I.small_box((6, 6, 7), sigma=0.1, seed=51)
+    clump = I.c3(ncell=10, fraction=0.1, radius=6.0, seed=23)   # up to 85 angular neighbours
+    Eo, Fo, Wo, Uo = oracle_eval(lat)
+    outs = {}
+    for s, want_tmem in ((lat, 1), (clump, 0), (lat, 1), (clump, 0)):
+        E, F, W, U = m.compute(N.to_device_soa(s.pos), s.box, s.pbc, site_energy=True)
+        st = m.stats()
+        assert st["angular_state_in_tmem"] == want_tmem, (st["max_nbr_angular"], want_tmem)
+        assert (st["max_nbr_angular"] > 48) == (s is clump)
+        F = F.cpu().numpy().T
+        assert np.all(np.isfinite(F))
+        if s is lat:
+            assert np.max(np.abs(F - Fo)) <= F32_F
+            assert abs(E - Eo) / s.n <= F32_E_PER_ATOM
+            assert np.max(np.abs(U.cpu().numpy() - Uo)) <= F32_U
+            assert np.max(np.abs(W - Wo)) / s.n <= F32_W_PER_ATOM
+        outs.setdefault(id(s), []).append((E, F))
+    for s in (lat, clump):
+        (E1, F1), (E2, F2) = outs[id(s)]
+        assert E1 == E2 and np.array_equal(F1, F2)
+    m.close()
