@@ -586,6 +586,50 @@ class MDState:
         return np.array(self.c.virial[:]).reshape(3, 3)
 
 
+def save_checkpoint(path, state: "MDState", params=None):
+    """Writes an MD state to ``path`` (numpy .npz): positions, velocities,
+    forces and species, the cell and periodic flags, dt_max and d_max, the
+    accumulated time, step count and last dt, whether the forces are valid,
+    and the SHA-256 of the model parameters when ``params`` is given.  A run
+    resumed from it with ``load_checkpoint`` (NVE, no thermostat or barostat)
+    continues exactly as the uninterrupted run would have; the Nose-Hoover
+    chain and barostat settings live in the context and are not saved."""
+    import hashlib
+    c = state.c
+    extra = {}
+    if params is not None:
+        extra["params_sha256"] = np.frombuffer(hashlib.sha256(
+            np.ascontiguousarray(params, dtype=np.float64).tobytes()).digest(), dtype=np.uint8)
+    np.savez(path, xyz=state.xyz.cpu().numpy(), vel=state.vel.cpu().numpy(),
+             forces=state.forces.cpu().numpy(), types=state.types.cpu().numpy(),
+             box=np.array(c.box[:]), pbc=np.array(c.pbc[:], dtype=np.int32),
+             dt=np.array([c.dt_max, c.d_max, c.time, c.dt_last]),
+             counters=np.array([c.step, c.forces_valid], dtype=np.int64), **extra)
+
+
+def load_checkpoint(path, device="cuda", params=None) -> "MDState":
+    """The MD state written by ``save_checkpoint``, on ``device``.  With
+    ``params``, their SHA-256 must match the one saved (ValueError otherwise)."""
+    import hashlib
+    import torch
+    z = np.load(path)
+    if params is not None:
+        h = hashlib.sha256(np.ascontiguousarray(params, dtype=np.float64).tobytes()).digest()
+        if "params_sha256" not in z or bytes(z["params_sha256"]) != h:
+            raise ValueError("checkpoint was written with other model parameters")
+    dt_max, d_max, t, dt_last = (float(v) for v in z["dt"])
+    step, forces_valid = (int(v) for v in z["counters"])
+    st = MDState(torch.from_numpy(z["xyz"]).to(device), torch.from_numpy(z["vel"]).to(device),
+                 z["box"].reshape(3, 3), z["pbc"], dt_max=dt_max, d_max=d_max,
+                 types=torch.from_numpy(z["types"]).to(device),
+                 forces=torch.from_numpy(z["forces"]).to(device))
+    st.c.forces_valid = forces_valid
+    st.c.time = t
+    st.c.step = step
+    st.c.dt_last = dt_last
+    return st
+
+
 def to_device_soa(a, device="cuda"):
     """(n, 3) numpy array -> (3, n) float64 CUDA tensor."""
     import torch
