@@ -7,8 +7,11 @@
 // (lane = thread, column n * 24 + lm), the descriptor sums A are written there
 // after the descriptor pass, turned into the adjoint in place after the
 // network, and read back per radial channel (three 8-column loads, double
-// buffered) inside the pair loop.  The arithmetic is that of k_nep_ang
-// (nep_device.cuh); only where the 120 values live differs.
+// buffered; a pair's first channel is loaded at the end of the previous pair)
+// inside the pair loop.  The arithmetic is that of k_nep_ang (nep_device.cuh)
+// except that the block's ZBL virial is summed in 2^-32 eV fixed point (order
+// independent) instead of FP64 per thread; otherwise only where the 120
+// values live differs.
 //
 // tcgen05.ld/st/alloc are warp-collective (.sync.aligned): every one of them
 // is executed by all 32 lanes of a warp together -- the pair loop runs to the
