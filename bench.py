@@ -36,9 +36,8 @@ WORKLOAD = ("8,192,000-atom bcc W slab (160x160x160 cells, a=3.165 A), periodic 
             "with 30 A vacuum each side, 300 K (seed 5), NVE dt=1 fs, random-init NEP-ZBL "
             "(seed 1: r_c 6/4 A, n_max 4/4, basis 8, l_max 4 + 4-body, 30 neurons, ZBL 1/2 A)")
 
-# FP32 issue rate of GB300 used as the ALU roofline: 152 SMs x 128 FP32 lanes
-# x 2 flop per FMA x SM clock.
-SMS = 152
+# FP32 issue rate used as the ALU roofline: SMs (read from the device) x 128
+# FP32 lanes x 2 flop per FMA x SM clock.
 FP32_LANES = 128
 
 # Algorithmic work of one force evaluation, per atom and per ordered pair.
@@ -57,20 +56,34 @@ FP32_LANES = 128
 #   per angular pair, force pass: Chebyshev with derivatives 40,
 #     g_n and g'_n 190, harmonics 60, G_lm and G'_lm 480, S 96,
 #     gradient polynomial contraction ~200, assembly 12                     -> 1078
-# DRAM bytes (read + write) of the two timed force kernels (k_nep_ang_tm +
-# k_radial_force) per atom, from one ncu capture of the same build on the
-# 1,024,000-atom slab (profiles/force_kernels_ncu_full_slab_1024000.md):
-# 516.6 MB per launch pair; scaled by the atom count.
-TRAFFIC_PER_ATOM = 516.6e6 / 1.024e6
 FLOP_ATOM = 4630
 FLOP_PAIR_R = 128 + 122
 FLOP_PAIR_A = 424 + 1078
-# Algorithmic DRAM bytes of the force kernel per atom and per ordered pair:
-# own position (16) + counts (8) + site energy/partials (~1) per atom; per
-# pair the neighbour entry read twice (8) and the 3 x 8-byte force update
-# (read-modify-write 48) -- the neighbour position reads hit L1/L2.
-BYTES_ATOM = 25
-BYTES_PAIR = 56
+
+# Measured DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) per
+# atom: of the two timed force kernels (k_nep_ang_tm + k_radial_force) per
+# launch pair, and of every kernel of one MD step, from captures of the
+# 1,024,000-atom slab (same geometry as the 8,192,000-atom slab at 80^3
+# cells); scaled by the atom count.  None while the kernels have changed since
+# the capture.  Source: profiles/dram_bytes_md_step_slab_1024000.md.
+DRAM_FORCE_PER_ATOM = None
+DRAM_STEP_PER_ATOM = None
+# Compulsory HBM bytes per atom-step of this design: every array a kernel of
+# the step needs read or written once by that kernel (neighbour records that
+# the caches serve are not counted):
+#   kick-drift x, v r/w + F, species read 124; binning x read, cell/slot/
+#   relative position write 48; scatter 12; cell finalize 48; neighbour
+#   search own position and cell read, lists (58 x 4 B) and counts, radial
+#   descriptor write 280; angular kernel counts, angular entries (14 x 4 B),
+#   position, q, index read, radial record write, own force accumulator 176;
+#   radial forces counts, list (58 x 4 B), own record read, force
+#   accumulator 288; accumulator clear 24; forces gather 52; second kick 76.
+BYTES_STEP_ALG = 124 + 48 + 12 + 48 + 280 + 176 + 288 + 24 + 52 + 76
+# L1/L2 gather bytes of the two force kernels (not DRAM): per atom its own
+# position and counts (25 B); per radial pair the list entry read twice (8 B)
+# and the neighbour's 48-byte record.
+GATHER_ATOM = 25
+GATHER_PAIR = 56
 
 
 def _measured_peaks():
@@ -330,7 +343,9 @@ def other_configs(dev):
     dt = (time.perf_counter() - t0) / reps
     out["c4_512_configs_loss_grad_fp32"] = {
         "value": b.N / dt, "unit": "atom-gradients/s", "ms_per_step": dt * 1e3,
-        "configs": b.S, "atoms": b.N, "loss": L, "autotune": {"threads": bt, "ctas_per_sm": per},
+        "configs": b.S, "atoms": b.N, "loss": L,
+        "autotune": {"threads": bt, "ctas_per_sm": per,
+                     "table": nep.batch_autotune_table()[0], "unit": "ms per fused launch"},
         "note": "host-timed synchronous API call (forward + loss + gradient)"}
     # one SNES generation of the paper's training (population 50, Sec. III.A) over the
     # same 512 configurations: candidates, the NEP loss of all 50 in one launch, update
@@ -427,17 +442,23 @@ def run_ours(args):
     x = N.to_device_soa(s.pos, dev)
     v = N.to_device_soa(s.vel, dev)
     st = N.MDState(x, v, s.box, s.pbc, dt_max=1.0)
-    nep.set_option(N.NEP_OPT_GRAPH_CHUNK, 25)
     stream = torch.cuda.current_stream()
 
+    # autotune (neighbour-search tiling, steps per graph) on this state, outside
+    # the timed region; the state is not advanced
+    tune = None
+    if not args.no_tune:
+        tune = nep.md_autotune(st, reps=2)
+    chunk = nep.stats()["graph_chunk"] if tune else 25
+    nep.set_option(N.NEP_OPT_GRAPH_CHUNK, chunk)
     # warm-up (includes the first force evaluation and graph capture)
     nep.md(st, max(args.warmup, 1))
     torch.cuda.synchronize()
     nep.set_option(N.NEP_OPT_TIMING, 1)
     # capture every graph length the timed run uses outside the timed region
-    nep.md(st, min(25, args.steps))
-    if args.steps % 25 and args.steps > 25:
-        nep.md(st, args.steps % 25)
+    nep.md(st, min(chunk, args.steps))
+    if args.steps % chunk and args.steps > chunk:
+        nep.md(st, args.steps % chunk)
     nep.reset_stats()
     torch.cuda.synchronize()
     if dist:
@@ -459,6 +480,7 @@ def run_ours(args):
 
     # roofline of the dominant kernel (the force kernel), timed inside the region
     peaks, peak_kind = _measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     k_ms = stats["timed_ms"] / max(stats["timed_launches"], 1)
     pr, pa = stats["pairs_radial"], stats["pairs_angular"]
     # when the neighbour-list kernel sums the radial descriptor, its 128 flop per
@@ -466,10 +488,13 @@ def run_ours(args):
     q_fused = bool(stats["radial_q_in_neighbor_kernel"])
     flop = FLOP_ATOM * n + (FLOP_PAIR_R - (128 if q_fused else 0)) * pr + FLOP_PAIR_A * pa
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tflops = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+    peak_tflops = sms * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
     achieved = flop / (k_ms * 1e-3) / 1e12
-    bytes_alg = BYTES_ATOM * n + BYTES_PAIR * pr
-    hbm_achieved = bytes_alg / (k_ms * 1e-3) / 1e9
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    # DRAM bytes of the timed kernels (ncu) over their live duration
+    traffic = DRAM_FORCE_PER_ATOM * n if (q_fused and DRAM_FORCE_PER_ATOM) else None
+    hbm_kernel = traffic / (k_ms * 1e-3) / 1e9 if traffic else None
+    gather_gbs = (GATHER_ATOM * n + GATHER_PAIR * pr) / (k_ms * 1e-3) / 1e9
     launches = stats["kernel_launches"]
 
     # FP64 path on the same workload (a few steps)
@@ -539,7 +564,12 @@ def run_ours(args):
                    f"PROFILING CASE {args.ncell}^3-cell slab, {n} atoms", "atoms": n, "precision": "fp32 descriptors/network/forces,"
                    " fp64 positions/integrator/energy/virial", "parallelism": "replicas" if ws > 1
                    else "single GPU", "l2": "inputs larger than L2 (state ~0.6 GB, lists ~3 GB)",
-                   "graph_chunk": 25},
+                   "graph_chunk": chunk},
+        "autotune": ({"tiling": {"kept": tune["tiling"][1], "table": tune["tiling"][0],
+                                 "unit": "ms per force evaluation"},
+                      "graph_chunk": {"kept": tune["graph_chunk"][1],
+                                      "table": tune["graph_chunk"][0],
+                                      "unit": "ms per MD step"}} if tune else None),
         "gpu_launches": int(launches),
         "clocks": clk,
         "roofline": {"bound": "alu",
@@ -549,16 +579,36 @@ def run_ours(args):
                                 else "k_radial_q + k_nep_ang + k_radial_force"),
                      "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops,
-                     "traffic": TRAFFIC_PER_ATOM * n if q_fused else None,
+                     "traffic": traffic,
                      "traffic_note": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the "
-                                      "timed kernels, 1,024,000-atom capture scaled by atoms"),
-                     "peak_kind": f"FP32 issue rate {SMS} SMs x {FP32_LANES} lanes x 2 x "
+                                      "timed kernels per launch pair, 1,024,000-atom capture "
+                                      "scaled by atoms; null while the kernels differ from the "
+                                      "capture"),
+                     "peak_kind": f"FP32 issue rate {sms} SMs x {FP32_LANES} lanes x 2 x "
                                   f"{sm_mhz:.0f} MHz (sm_max_mhz, {peak_kind})",
+                     "sm_count": sms,
                      "kernel_ms": k_ms, "flop_per_launch": flop,
-                     "hbm_achieved_gbs": hbm_achieved, "hbm_peak_gbs": peaks.get("hbm_gbs"),
-                     "hbm_frac": hbm_achieved / float(peaks.get("hbm_gbs", 6800.0)),
+                     "hbm_achieved_gbs": hbm_kernel, "hbm_peak_gbs": hbm_peak,
+                     "hbm_frac": hbm_kernel / hbm_peak if hbm_kernel else None,
+                     "hbm_note": "measured DRAM bytes of the timed kernels / their live "
+                                 "CUDA-event duration / measured copy bandwidth",
+                     "l1l2_gather_gbs": gather_gbs,
+                     "l1l2_gather_note": "bytes the force kernels gather through L1/L2 (own "
+                                         "position and counts 25 B per atom, 56 B per radial "
+                                         "pair), not DRAM",
                      "kernel_share": stats["timed_ms"] / ms if ms > 0 else None,
                      "pairs_radial": pr, "pairs_angular": pa},
+        "step_hbm": {
+            "bytes_per_atom_step": BYTES_STEP_ALG,
+            "achieved_gbs": BYTES_STEP_ALG * n * args.steps / (ms * 1e-3) / 1e9,
+            "frac": BYTES_STEP_ALG * n * args.steps / (ms * 1e-3) / 1e9 / hbm_peak,
+            "measured_bytes_per_atom_step": DRAM_STEP_PER_ATOM,
+            "measured_gbs": (DRAM_STEP_PER_ATOM * n * args.steps / (ms * 1e-3) / 1e9
+                             if DRAM_STEP_PER_ATOM else None),
+            "measured_frac": (DRAM_STEP_PER_ATOM * n * args.steps / (ms * 1e-3) / 1e9 / hbm_peak
+                              if DRAM_STEP_PER_ATOM else None),
+            "note": "whole MD step: compulsory bytes of this design's kernels (and ncu DRAM "
+                    "bytes of one step) x atoms / ms_per_step / measured copy bandwidth"},
         "fp64_path": fp64,
         "other_configs": others,
         "e2e": e2e,
@@ -578,6 +628,9 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-extras", action="store_true",
                     help="skip the measurements of the other workloads")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the MD autotuner (default options: 1 z slice, chunk 16, 25 steps "
+                         "per graph)")
     ap.add_argument("--ncell", type=int, default=160,
                     help="slab size in bcc cells per side (160 = the 8,192,000-atom workload; "
                          "smaller values only for profiling)")

@@ -179,6 +179,37 @@ int md_step(nep_ctx* ctx, nep_md_state* state, int n_steps, void* stream);
  * arrays are left unchanged. */
 int md_step_host(nep_ctx* ctx, nep_md_state* state, int n_steps, void* stream);
 
+/* Timings of the candidates of one tuning run (host struct, filled by the
+ * library).  Each candidate has two parameters a, b whose meaning the tuning
+ * call states, and the median of its timed repetitions in milliseconds. */
+typedef struct nep_tune_table {
+    int32_t n;            /* candidates timed (at most 32) */
+    int32_t a[32], b[32]; /* parameters of each candidate */
+    double ms[32];        /* median time of each candidate (ms) */
+    int32_t best;         /* index of the candidate kept */
+} nep_tune_table;
+
+/* Autotuner of the MD path (an engineering addition; the paper tunes
+ * nothing).  On the state's own atoms, box and species it times, with CUDA
+ * events on `stream`:
+ *   1. every neighbour-search tiling (NEP_OPT_NBR_SLICES 1, 2, 4, 8 x
+ *      NEP_OPT_NBR_CHUNK 4, 8, 16) by `reps` force evaluations each, written
+ *      into a scratch force array owned by the context; tiling table: a = z
+ *      slices, b = chunk width, ms per evaluation (triclinic cells: one
+ *      candidate, the fixed search);
+ *   2. unless a thermostat or barostat is set, the steps per captured graph
+ *      (NEP_OPT_GRAPH_CHUNK 10, 25, 50) by `reps` runs of 50 MD steps of a
+ *      copy of the state in context-owned device memory (after one untimed
+ *      run that captures the graphs); chunk table: a = steps per graph,
+ *      b = 0, ms per MD step;
+ * and keeps the fastest of each (median of the repetitions) as the
+ * context's options.  The caller's state (xyz, vel, forces, types: device
+ * memory) is read, never written.  reps in [1, 50]; either table pointer may
+ * be NULL.  The tiling choice does not change which pairs are found.
+ * Synchronous. */
+int nep_md_autotune(nep_ctx* ctx, const nep_md_state* state, int reps, void* stream,
+                    nep_tune_table* tiling, nep_tune_table* chunk);
+
 /* ---------------------------------------------------------------------------
  * Cascade protocol (Sec. II.B): the atoms within 3 a0 of the box boundaries
  * are held at 300 K by a Nose-Hoover chain thermostat, the system is first
@@ -238,6 +269,10 @@ typedef struct nep_stats {
                                              descriptor sums and adjoint in Tensor Memory
                                              (FP32, one species, at most 48 angular
                                              neighbours on every atom) */
+    int32_t angular_tmem_blocks_per_sm;   /* resident blocks per SM of that kernel (from
+                                             the occupancy check; 0: not usable) */
+    int32_t nbr_z_slices;                 /* NEP_OPT_NBR_SLICES in effect */
+    int32_t nbr_chunk;                    /* NEP_OPT_NBR_CHUNK in effect */
 } nep_stats;
 
 int nep_get_stats(const nep_ctx* ctx, nep_stats* out);
@@ -250,11 +285,19 @@ int nep_get_stats(const nep_ctx* ctx, nep_stats* out);
  * 0.001 A (0, the default, rebuilds the neighbour lists every step; > 0 builds
  * them with r_c + skin and rebuilds only after some atom moved more than
  * skin / 2 since the last build, which leaves every pair within r_c in the
- * lists). */
+ * lists); NEP_OPT_NBR_SLICES (1, 2, 4 or 8; default 1) and NEP_OPT_NBR_CHUNK
+ * (4, 8 or 16; default 16) tile the neighbour search of orthorhombic cells:
+ * the atoms of each cell are grouped into z slices so that only the slices
+ * within reach of an atom are searched, and candidates are tested in
+ * unrolled chunks of that width.  They change only the order of pairs within
+ * a cell's part of a list, never which pairs are found; nep_md_autotune
+ * picks them by timing.  Returns NEP_ERR_INVALID_ARG for other values. */
 #define NEP_OPT_TIMING               1
 #define NEP_OPT_GRAPH_CHUNK          2
 #define NEP_OPT_NBR_CAPACITY         3
 #define NEP_OPT_SKIN_MILLIANGSTROM   4
+#define NEP_OPT_NBR_SLICES           5
+#define NEP_OPT_NBR_CHUNK            6
 int nep_set_option(nep_ctx* ctx, int option, int64_t value);
 
 /* Resets the counters of nep_stats (launches, timing). */
@@ -343,10 +386,15 @@ int nep_batch_loss_grad(nep_ctx* ctx, const nep_batch* batch, const nep_targets*
 
 /* Times the loss-gradient launch on this batch for each candidate of threads
  * per CTA (atoms of one configuration processed side by side: 64, 128, 256)
- * and CTAs per SM (1, 2, 4) and keeps the fastest for later batched calls. */
+ * and CTAs per SM (1, 2, 4), the median of three launches each, and keeps the
+ * fastest for later batched calls. */
 int nep_batch_autotune(nep_ctx* ctx, const nep_batch* batch, const nep_targets* targets,
                        const nep_loss_weights* w, void* stream, int* best_threads,
                        int* best_per_sm);
+
+/* The timings of the last nep_batch_autotune on this context: a = threads per
+ * CTA, b = CTAs per SM, ms per fused launch. */
+int nep_batch_autotune_table(const nep_ctx* ctx, nep_tune_table* out);
 
 /* ---------------------------------------------------------------------------
  * Population training (the separable natural evolution strategy, SNES, that
@@ -410,10 +458,14 @@ int nep_snes_generation(nep_ctx* ctx, const nep_batch* batch, const nep_targets*
  *   Set-up: the first call on a device (with that device current) looks up
  *   the array's device address once and caches it; make that first call
  *   before any stream capture.
+ *   Device memory: xyz, types, forces and (when not NULL) site_energy must be
+ *   device memory; a host pointer in any of them gives NEP_ERR_INVALID_ARG
+ *   before any GPU work.
  *   Concurrency: all calls share the one array; calls whose GPU work overlaps
  *   (different streams, threads or processes' contexts on the same device
  *   within this process) race and give wrong results.  Each call clears what
- *   must start at zero and finishes with a stream synchronisation.
+ *   must start at zero, copies its energy and virial to the host and
+ *   synchronises the stream before it returns.
  * Errors are reported through nep_last_error(NULL). */
 int nep_compute_static(const nep_params* p, int64_t n_atoms, const double* xyz,
                        const double box[9], const int32_t* types, const int32_t pbc[3],

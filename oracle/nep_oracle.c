@@ -252,7 +252,7 @@ void orc_zbl(double r, double Zi, double Zj, double r1, double r2,
  * gA[3*na]) and U^NEP itself. */
 static double site_nep(const orc_model *m, int ti, int nr, const double *dR, const int *tR,
                        int na, const double *dA, const int *tA, double *q_out, double *gR,
-                       double *gA)
+                       double *gA, double *cond)
 {
     const int nR = m->nR, nA = m->nA, L = m->lmax, D = m->D, H = m->H;
     double *q = (double *)calloc((size_t)D, sizeof(double));
@@ -314,13 +314,30 @@ static double site_nep(const orc_model *m, int ti, int nr, const double *dR, con
     /* network: U = sum_mu w1_mu tanh(sum_nu w0_{mu nu} s_nu q_nu - b0_mu) - b1 */
     double U = -m->b1[0];
     double *dUdq = (double *)calloc((size_t)D, sizeof(double));
+    double hmax = 0.0, nsens = 0.0, tmag = fabs(m->b1[0]);
     for (int mu = 0; mu < H; ++mu) {
-        double h = -m->b0[mu];
-        for (int nu = 0; nu < D; ++nu) h += m->w0[mu * D + nu] * m->s[nu] * q[nu];
+        double h = -m->b0[mu], habs = 0.0;
+        for (int nu = 0; nu < D; ++nu) {
+            h += m->w0[mu * D + nu] * m->s[nu] * q[nu];
+            habs += fabs(m->w0[mu * D + nu] * m->s[nu] * q[nu]);
+        }
         double th = tanh(h);
         U += m->w1[mu] * th;
         double back = m->w1[mu] * (1.0 - th * th);
         for (int nu = 0; nu < D; ++nu) dUdq[nu] += back * m->w0[mu * D + nu] * m->s[nu];
+        if (habs > hmax) hmax = habs;
+        nsens += fabs(back) * habs;
+        tmag += fabs(m->w1[mu] * th);
+    }
+    /* conditioning of the site (test support, for rounding-error bounds):
+     * radial neighbour count, max_mu sum_nu |w0 s q| (the scale of the
+     * pre-activations' rounding), sum_mu |w1 (1 - t^2)| sum_nu |w0 s q| (the
+     * sensitivity of U to relative descriptor errors) and sum |terms of U| */
+    if (cond) {
+        cond[0] = (double)nr;
+        cond[1] = hmax;
+        cond[2] = nsens;
+        cond[3] = tmag;
     }
 
     if (gR) {
@@ -397,7 +414,7 @@ int orc_site(const int *ihp, const double *dhp, const double *params,
     if (ti < 0 || ti >= m.T) return ORC_ERR_ARG;
     for (int s = 0; s < nr; ++s) if (tR[s] < 0 || tR[s] >= m.T) return ORC_ERR_ARG;
     for (int s = 0; s < na; ++s) if (tA[s] < 0 || tA[s] >= m.T) return ORC_ERR_ARG;
-    *U = site_nep(&m, ti, nr, dR, tR, na, dA, tA, q, gR, gA);
+    *U = site_nep(&m, ti, nr, dR, tR, na, dA, tA, q, gR, gA, NULL);
     return ORC_OK;
 }
 
@@ -756,6 +773,7 @@ int orc_neighbor_counts(int N, const double *pos, const double *box, const int *
 typedef struct {
     orc_list R, A, Z;   /* radial (rcR), angular (rcA) and ZBL (zr2) lists */
     double U;           /* U_i (NEP + half of the ZBL pair terms) */
+    double cond[4];     /* conditioning of the site (see site_nep) */
 } orc_atom;
 
 /* Lists and site gradients of atom i. */
@@ -773,7 +791,7 @@ static int atom_eval(const orc_model *m, const orc_sys *S, const orc_grid *G, in
     if (!at->R.g || !at->A.g || !at->Z.g) return ORC_ERR_MEM;
     const int ti = sys_type(S, i);
     at->U = site_nep(m, ti, at->R.n, at->R.d, at->R.t, at->A.n, at->A.d, at->A.t, q, at->R.g,
-                     at->A.g);
+                     at->A.g, at->cond);
     for (int s = 0; s < at->Z.n; ++s) {
         const double *d = at->Z.d + 3 * s;
         double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
@@ -856,6 +874,77 @@ int orc_energy_forces_virial(const int *ihp, const double *dhp, const double *pa
     return efv(&m, &S, use_grid, E, F, W, U, NULL);
 }
 
+#define NSCALE 5   /* rounding-error scales per atom (orc_force_scales) */
+
+/* Magnitude of a pair gradient vector. */
+static double norm3(const double *g)
+{
+    return sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+}
+
+/* Rounding-error scales of every atom (test support; N x NSCALE):
+ *   [0] S: sum of |g| over the NEP pair terms that enter F_i (its own lists'
+ *       terms and its neighbours' terms pointing at it);
+ *   [1] Z: the same over the ZBL pair terms;
+ *   [2] W: the NEP pair terms' magnitudes weighted by the conditioning of
+ *       the site they come from, sum |g| sqrt(M_k) max_mu sum_nu
+ *       |w0_{mu nu} s_nu q_{k nu}| (k: the atom whose site energy the term
+ *       differentiates, M_k its radial neighbours): the scale of the error
+ *       that rounding of the descriptor sums passes through the adjoint;
+ *   [3] sqrt(M_i) sum_mu |w1_mu (1 - t_mu^2)| sum_nu |w0 s q_i|: the scale of
+ *       the site energy's response to that rounding;
+ *   [4] sum_mu |w1_mu t_mu| + |b1|: the magnitude of U_i^NEP's terms. */
+int orc_force_scales(const int *ihp, const double *dhp, const double *params,
+                     const double *scaler, int N, const double *pos, const int *types,
+                     const double *box, const int *pbc, int use_grid, double *sc)
+{
+    orc_model m;
+    if (model_init(&m, ihp, dhp, params, scaler) || N < 0) return ORC_ERR_ARG;
+    orc_sys Sy = {N, pos, {0, 0, 0}, {pbc[0], pbc[1], pbc[2]}, types, 0, {0}, {0}};
+    if (!sys_cell(&Sy, box)) return ORC_ERR_ARG;
+    if (!types_valid(&Sy, m.T)) return ORC_ERR_ARG;
+    orc_grid G;
+    memset(&G, 0, sizeof(G));
+    if (use_grid && grid_build(&Sy, m.rcR, &G)) return ORC_ERR_MEM;
+    orc_atom *atoms = (orc_atom *)calloc((size_t)(N > 0 ? N : 1), sizeof(orc_atom));
+    if (!atoms) { grid_free(&G); return ORC_ERR_MEM; }
+    int err = ORC_OK;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int i = 0; i < N; ++i) {
+        int e = atom_eval(&m, &Sy, &G, i, &atoms[i], NULL);
+        if (e) {
+#pragma omp critical
+            err = e;
+        }
+    }
+    memset(sc, 0, sizeof(double) * NSCALE * (size_t)N);
+    for (int i = 0; i < N && !err; ++i) {
+        const double ki = sqrt(atoms[i].cond[0]) * atoms[i].cond[1];
+        double *oi = sc + (size_t)NSCALE * i;
+        oi[3] = sqrt(atoms[i].cond[0]) * atoms[i].cond[2];
+        oi[4] = atoms[i].cond[3];
+        const orc_list *Ls[3] = {&atoms[i].R, &atoms[i].A, &atoms[i].Z};
+        for (int w = 0; w < 3; ++w) {
+            const int col = w < 2 ? 0 : 1;
+            for (int s = 0; s < Ls[w]->n; ++s) {
+                const int j = Ls[w]->j[s];
+                if (j == i) continue;   /* a self-image term cancels in F_i */
+                const double v = norm3(Ls[w]->g + 3 * s);
+                oi[col] += v;
+                sc[(size_t)NSCALE * j + col] += v;
+                if (col == 0) {   /* a term of atom i's site energy */
+                    oi[2] += v * ki;
+                    sc[(size_t)NSCALE * j + 2] += v * ki;
+                }
+            }
+        }
+    }
+    for (int i = 0; i < N; ++i) atom_free(&atoms[i]);
+    free(atoms);
+    grid_free(&G);
+    return err;
+}
+
 /* Unscaled descriptors q (N, D) of every atom. */
 int orc_descriptors(const int *ihp, const double *dhp, const double *params,
                     const double *scaler, int N, const double *pos, const int *types,
@@ -872,34 +961,41 @@ int orc_descriptors(const int *ihp, const double *dhp, const double *params,
 /* Forces and site energies of a subset of atoms idx[nidx] only (for sampled
  * comparisons on large systems):
  *   F_a = sum_{s in lists(a), j_s != a} g_{a,s} - sum_{k != a} sum_{t: j_t = a} g_{k,t}
- * where k runs over the distinct atoms in the radial neighbourhood of a. */
-int orc_forces_subset(const int *ihp, const double *dhp, const double *params,
-                      const double *scaler, int N, const double *pos, const int *types,
-                      const double *box, const int *pbc, int nidx, const int64_t *idx,
-                      double *F, double *U)
+ * where k runs over the distinct atoms in the radial neighbourhood of a.
+ * Optionally (sc not NULL, nidx x NSCALE) the scales of each listed atom's
+ * force and site energy for rounding-error bounds (see scales_of). */
+static int forces_subset(const int *ihp, const double *dhp, const double *params,
+                         const double *scaler, int N, const double *pos, const int *types,
+                         const double *box, const int *pbc, int nidx, const int64_t *idx,
+                         double *F, double *U, double *sc)
 {
     orc_model m;
     if (model_init(&m, ihp, dhp, params, scaler) || N < 0) return ORC_ERR_ARG;
-    orc_sys S = {N, pos, {0, 0, 0}, {pbc[0], pbc[1], pbc[2]}, types, 0, {0}, {0}};
-    if (!sys_cell(&S, box)) return ORC_ERR_ARG;
-    if (!types_valid(&S, m.T)) return ORC_ERR_ARG;
+    orc_sys Sy = {N, pos, {0, 0, 0}, {pbc[0], pbc[1], pbc[2]}, types, 0, {0}, {0}};
+    if (!sys_cell(&Sy, box)) return ORC_ERR_ARG;
+    if (!types_valid(&Sy, m.T)) return ORC_ERR_ARG;
     orc_grid G;
     memset(&G, 0, sizeof(G));
-    if (grid_build(&S, m.rcR, &G)) return ORC_ERR_MEM;
+    if (grid_build(&Sy, m.rcR, &G)) return ORC_ERR_MEM;
     int err = ORC_OK;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int t = 0; t < nidx; ++t) {
         int a = (int)idx[t];
-        double f[3] = {0, 0, 0};
+        double f[3] = {0, 0, 0}, sn = 0.0, sz = 0.0, sw = 0.0;
         orc_atom at;
-        int e = atom_eval(&m, &S, &G, a, &at, NULL);
+        int e = atom_eval(&m, &Sy, &G, a, &at, NULL);
         if (!e) {
             U[t] = at.U;
+            const double ka = sqrt(at.cond[0]) * at.cond[1];
             const orc_list *Ls[3] = {&at.R, &at.A, &at.Z};
             for (int w = 0; w < 3; ++w)
                 for (int s = 0; s < Ls[w]->n; ++s)
-                    if (Ls[w]->j[s] != a)
+                    if (Ls[w]->j[s] != a) {
                         for (int c = 0; c < 3; ++c) f[c] += Ls[w]->g[3 * s + c];
+                        const double v = norm3(Ls[w]->g + 3 * s);
+                        if (w < 2) { sn += v; sw += v * ka; }
+                        else sz += v;
+                    }
             /* distinct neighbours k != a */
             int nk = 0;
             int *ks = (int *)malloc(sizeof(int) * (size_t)(at.R.n + 1));
@@ -911,13 +1007,18 @@ int orc_forces_subset(const int *ihp, const double *dhp, const double *params,
             }
             for (int u = 0; u < nk && !e; ++u) {
                 orc_atom bk;
-                e = atom_eval(&m, &S, &G, ks[u], &bk, NULL);
+                e = atom_eval(&m, &Sy, &G, ks[u], &bk, NULL);
                 if (!e) {
+                    const double kk = sqrt(bk.cond[0]) * bk.cond[1];
                     const orc_list *Lk[3] = {&bk.R, &bk.A, &bk.Z};
                     for (int w = 0; w < 3; ++w)
                         for (int s = 0; s < Lk[w]->n; ++s)
-                            if (Lk[w]->j[s] == a)
+                            if (Lk[w]->j[s] == a) {
                                 for (int c = 0; c < 3; ++c) f[c] -= Lk[w]->g[3 * s + c];
+                                const double v = norm3(Lk[w]->g + 3 * s);
+                                if (w < 2) { sn += v; sw += v * kk; }
+                                else sz += v;
+                            }
                 }
                 atom_free(&bk);
             }
@@ -925,6 +1026,14 @@ int orc_forces_subset(const int *ihp, const double *dhp, const double *params,
         }
         atom_free(&at);
         for (int c = 0; c < 3; ++c) F[3 * t + c] = f[c];
+        if (sc) {
+            double *o = sc + (size_t)NSCALE * t;
+            o[0] = sn;
+            o[1] = sz;
+            o[2] = sw;
+            o[3] = sqrt(at.cond[0]) * at.cond[2];
+            o[4] = at.cond[3];
+        }
         if (e) {
 #pragma omp critical
             err = e;
@@ -932,6 +1041,25 @@ int orc_forces_subset(const int *ihp, const double *dhp, const double *params,
     }
     grid_free(&G);
     return err;
+}
+
+int orc_forces_subset(const int *ihp, const double *dhp, const double *params,
+                      const double *scaler, int N, const double *pos, const int *types,
+                      const double *box, const int *pbc, int nidx, const int64_t *idx,
+                      double *F, double *U)
+{
+    return forces_subset(ihp, dhp, params, scaler, N, pos, types, box, pbc, nidx, idx, F, U,
+                         NULL);
+}
+
+/* orc_forces_subset plus the rounding-error scales (nidx x NSCALE, see
+ * scales_of) of each listed atom. */
+int orc_forces_subset_scales(const int *ihp, const double *dhp, const double *params,
+                             const double *scaler, int N, const double *pos, const int *types,
+                             const double *box, const int *pbc, int nidx, const int64_t *idx,
+                             double *F, double *U, double *sc)
+{
+    return forces_subset(ihp, dhp, params, scaler, N, pos, types, box, pbc, nidx, idx, F, U, sc);
 }
 
 /* ---------------------------------------------------------------------------

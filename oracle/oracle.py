@@ -43,6 +43,9 @@ def lib():
         L.orc_descriptors.argtypes = [ip, dp, dp, dp, C.c_int, dp, ip, dp, ip, C.c_int, dp]
         L.orc_forces_subset.argtypes = [ip, dp, dp, dp, C.c_int, dp, ip, dp, ip, C.c_int,
                                         C.POINTER(C.c_int64), dp, dp]
+        L.orc_forces_subset_scales.argtypes = [ip, dp, dp, dp, C.c_int, dp, ip, dp, ip, C.c_int,
+                                               C.POINTER(C.c_int64), dp, dp, dp]
+        L.orc_force_scales.argtypes = [ip, dp, dp, dp, C.c_int, dp, ip, dp, ip, C.c_int, dp]
         L.orc_md.argtypes = [ip, dp, dp, dp, C.c_int, dp, dp, dp, C.c_int, ip, dp, ip,
                              dp, C.c_double, C.c_double, C.c_int, C.c_int, dp]
         L.orc_md_ext.argtypes = [ip, dp, dp, dp, C.c_int, dp, dp, dp, C.c_int, ip, dp, ip,
@@ -163,8 +166,14 @@ def descriptors(model, pos, box, pbc, use_grid=True, types=None):
     return q
 
 
-def forces_subset(model, pos, box, pbc, idx, types=None):
-    """Forces (len(idx), 3) and site energies (len(idx)) of the listed atoms."""
+# columns of the rounding-error scales (orc_force_scales in nep_oracle.c)
+SCALE_COLUMNS = ("S", "Z", "W", "SU", "TU")
+
+
+def forces_subset(model, pos, box, pbc, idx, types=None, scales=False):
+    """Forces (len(idx), 3) and site energies (len(idx)) of the listed atoms;
+    with ``scales`` also their rounding-error scales (len(idx), 5), columns
+    SCALE_COLUMNS (see force_scales)."""
     ihp, dhp = _hp(model)
     p = _f64(model.params)
     s = _f64(model.scaler)
@@ -173,11 +182,33 @@ def forces_subset(model, pos, box, pbc, idx, types=None):
     idx = np.ascontiguousarray(idx, dtype=np.int64)
     F = np.zeros((len(idx), 3))
     U = np.zeros(len(idx))
-    _check(lib().orc_forces_subset(_i(ihp), _d(dhp), _d(p), _d(s), pos.shape[0], _d(pos), _i(t),
-                                   _d(_box9(box)), _i(np.ascontiguousarray(pbc, dtype=np.int32)),
-                                   len(idx), idx.ctypes.data_as(C.POINTER(C.c_int64)),
-                                   _d(F), _d(U)), "forces_subset")
-    return F, U
+    sc = np.zeros((max(len(idx), 1), 5))
+    _check(lib().orc_forces_subset_scales(
+        _i(ihp), _d(dhp), _d(p), _d(s), pos.shape[0], _d(pos), _i(t), _d(_box9(box)),
+        _i(np.ascontiguousarray(pbc, dtype=np.int32)), len(idx),
+        idx.ctypes.data_as(C.POINTER(C.c_int64)), _d(F), _d(U), _d(sc)), "forces_subset")
+    return (F, U, sc[:len(idx)]) if scales else (F, U)
+
+
+def force_scales(model, pos, box, pbc, types=None, use_grid=True):
+    """Rounding-error scales of every atom, (N, 5), columns SCALE_COLUMNS:
+    S, the sum of the magnitudes |dU_i/dd_ij| of the NEP pair terms that enter
+    its force; Z, the same over the ZBL pair terms; W, the NEP terms'
+    magnitudes each weighted by sqrt(M_k) max_mu sum_nu |w0_{mu nu} s_nu
+    q_{k nu}| of the atom k whose site energy it differentiates (M_k radial
+    neighbours); SU, sqrt(M_i) sum_mu |w1_mu (1 - t_mu^2)| sum_nu |w0 s q_i|;
+    TU, sum_mu |w1_mu t_mu| + |b1|."""
+    ihp, dhp = _hp(model)
+    p = _f64(model.params)
+    s = _f64(model.scaler)
+    pos = _f64(pos)
+    n = pos.shape[0]
+    t = _types(types, n)
+    sc = np.zeros((max(n, 1), 5))
+    _check(lib().orc_force_scales(_i(ihp), _d(dhp), _d(p), _d(s), n, _d(pos), _i(t),
+                                  _d(_box9(box)), _i(np.ascontiguousarray(pbc, dtype=np.int32)),
+                                  int(use_grid), _d(sc)), "force_scales")
+    return sc[:n]
 
 
 def site(model, dR, dA, ti=0, tR=None, tA=None):

@@ -37,6 +37,10 @@ constexpr int C_RAD = 0, C_ANG = 52;   // radial / angular block offsets
 
 // status bits
 constexpr int ST_OVERFLOW = 1, ST_NONFINITE = 2, ST_FORCE_RANGE = 4, ST_BADTYPE = 8;
+// the evaluation has a pair closer than the outer ZBL radius (set by the
+// radial-descriptor pass of the FP32 path); the kernels without the ZBL and
+// close-pair branches then leave the evaluation to the ones with them
+constexpr int ST_CLOSE = 16;
 
 template <typename R> struct V4 { using T = float4; };
 template <> struct V4<double> { using T = double4_32a; };
@@ -74,6 +78,11 @@ struct Grid {
     // fields above are used and h, hinv are diagonal)
     int tric;
     double h[9], hinv[9];
+    // z sub-slices per cell (1, 2, 4 or 8; 1 for triclinic cells): the atoms of
+    // a cell are grouped by slice floor(z_rel zs / lc_z) (clamped), and
+    // start[] is indexed by sub-cell c * zs + slice, so that the neighbour
+    // search can take the part of a stencil cell within reach in z
+    int zs;
 };
 
 // Fractional coordinates s = x h^-1 (row vectors).
@@ -193,7 +202,12 @@ __global__ void k_bin_count(Grid g, const double* __restrict__ x, int* __restric
     }
     if (bad) atomicOr(status, ST_NONFINITE);
     int cell = (c[0] * g.nc[1] + c[1]) * g.nc[2] + c[2];
-    cell_of[i] = cell;
+    if (g.zs > 1) {
+        int t = __double2int_rd(r3[2] * (g.zs * g.inv_lc[2]));
+        t = t < 0 ? 0 : (t >= g.zs ? g.zs - 1 : t);
+        cell = cell * g.zs + t;
+    }
+    cell_of[i] = cell;   // sub-cell
     slot_of[i] = atomicAdd(&count[cell], 1);
     if (rel) {
         typename V4<R>::T q;
@@ -258,28 +272,33 @@ static __global__ void __launch_bounds__(SCAN_T) k_scan_blocks(const int* __rest
     if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
 }
 
-// one block: exclusive scan of up to SCAN_B block sums; writes out[n] = total
+// one block: exclusive scan of the nb block sums, SCAN_B at a time with a
+// running carry; writes out[n] = total
 static __global__ void __launch_bounds__(SCAN_T) k_scan_sums(int* __restrict__ sums, int nb,
                                                       int* __restrict__ out, int n,
                             const int* __restrict__ gate = nullptr)
 {
     if (gate && *gate == 0) return;   // lists still valid (Verlet skin)
     __shared__ int sh[32];
-    int base = threadIdx.x * SCAN_ITEMS;
-    int v[SCAN_ITEMS], sum = 0;
+    int carry = 0;
+    for (int b0 = 0; b0 < nb; b0 += SCAN_B) {
+        int base = b0 + threadIdx.x * SCAN_ITEMS;
+        int v[SCAN_ITEMS], sum = 0;
 #pragma unroll
-    for (int t = 0; t < SCAN_ITEMS; ++t) {
-        v[t] = (base + t < nb) ? sums[base + t] : 0;
-        sum += v[t];
-    }
-    int total;
-    int ex = block_excl_scan(sum, sh, total);
+        for (int t = 0; t < SCAN_ITEMS; ++t) {
+            v[t] = (base + t < nb) ? sums[base + t] : 0;
+            sum += v[t];
+        }
+        int total;
+        int ex = carry + block_excl_scan(sum, sh, total);
 #pragma unroll
-    for (int t = 0; t < SCAN_ITEMS; ++t) {
-        if (base + t < nb) sums[base + t] = ex;
-        ex += v[t];
+        for (int t = 0; t < SCAN_ITEMS; ++t) {
+            if (base + t < nb) sums[base + t] = ex;
+            ex += v[t];
+        }
+        carry += total;
     }
-    if (threadIdx.x == 0) out[n] = total;
+    if (threadIdx.x == 0) out[n] = carry;
 }
 
 static __global__ void k_scan_add(int* __restrict__ out, int n, const int* __restrict__ sums,
@@ -317,11 +336,15 @@ __global__ void k_cell_finalize(Grid g, int ncell, const int* __restrict__ start
     if (gate && *gate == 0) return;   // lists still valid (Verlet skin)
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
-    int b = start[c], e = start[c + 1];
-    for (int s = b + 1; s < e; ++s) {
-        int v = perm[s], t = s;
-        while (t > b && perm[t - 1] > v) { perm[t] = perm[t - 1]; --t; }
-        perm[t] = v;
+    const int zs = g.zs > 1 ? g.zs : 1;
+    int b = start[c * zs], e = start[(c + 1) * zs];
+    for (int u = 0; u < zs; ++u) {   // each z slice by caller index
+        const int bu = start[c * zs + u], eu = start[c * zs + u + 1];
+        for (int s = bu + 1; s < eu; ++s) {
+            int v = perm[s], t = s;
+            while (t > bu && perm[t - 1] > v) { perm[t] = perm[t - 1]; --t; }
+            perm[t] = v;
+        }
     }
     int cz = c % g.nc[2], cy = (c / g.nc[2]) % g.nc[1], cx = c / (g.nc[2] * g.nc[1]);
     int cc[3] = {cx, cy, cz};
@@ -379,7 +402,8 @@ __global__ void __launch_bounds__(256) k_cell_finalize_w(
     const int c = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (c >= ncell) return;   // whole warps leave together
-    const int b = start[c], e = start[c + 1], cnt = e - b;
+    const int zs = g.zs > 1 ? g.zs : 1;
+    const int b = start[c * zs], e = start[(c + 1) * zs], cnt = e - b;
     bool badtype = false;
     auto place = [&](int s, int i) {
         const typename V4<R>::T q = rel[i];
@@ -393,19 +417,28 @@ __global__ void __launch_bounds__(256) k_cell_finalize_w(
         if (invperm) invperm[i] = s;
     };
     if (cnt <= 32) {
+        // rank by (z slice, caller index): the slices are already contiguous
         const int v = lane < cnt ? perm[b + lane] : 0x7fffffff;
+        int sl = 0;
+        for (int u = 1; u < zs; ++u) sl += b + lane >= start[c * zs + u];
         int rank = 0;
-        for (int j = 0; j < cnt; ++j) rank += __shfl_sync(0xffffffffu, v, j) < v;
+        for (int j = 0; j < cnt; ++j) {
+            const int vj = __shfl_sync(0xffffffffu, v, j), sj = __shfl_sync(0xffffffffu, sl, j);
+            rank += sj < sl || (sj == sl && vj < v);
+        }
         if (lane < cnt) {
             perm[b + rank] = v;
             place(b + rank, v);
         }
     } else {
         if (lane == 0)
-            for (int s = b + 1; s < e; ++s) {
-                int v = perm[s], t = s;
-                while (t > b && perm[t - 1] > v) { perm[t] = perm[t - 1]; --t; }
-                perm[t] = v;
+            for (int u = 0; u < zs; ++u) {   // each z slice by caller index
+                const int bu = start[c * zs + u], eu = start[c * zs + u + 1];
+                for (int s = bu + 1; s < eu; ++s) {
+                    int v = perm[s], t = s;
+                    while (t > bu && perm[t - 1] > v) { perm[t] = perm[t - 1]; --t; }
+                    perm[t] = v;
+                }
             }
         __syncwarp();
         for (int s = b + lane; s < e; s += 32) place(s, perm[s]);
@@ -441,12 +474,53 @@ __device__ __forceinline__ void fill_stencil(typename V4<R>::T* tab, const Grid&
     __syncthreads();
 }
 
+// FP64 displacement x_j - x_i of two atoms given by caller index (minimum
+// image along the periodic directions).
+__device__ __forceinline__ void disp64(const Grid& g, const double* __restrict__ x64, int i, int j,
+                                       double (&d)[3])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double t = x64[(size_t)c * g.n + j] - x64[(size_t)c * g.n + i];
+        if (!g.tric && g.pbc[c]) t -= g.L[c] * rint(t * g.invL[c]);
+        d[c] = t;
+    }
+    if (g.tric) min_image_tric(g, d);
+}
+
+// Close pairs on the FP32 path.  The displacement formed from cell-relative
+// FP32 coordinates carries an absolute error of up to ~2e-6 A (three rounded
+// coordinates and two roundings of the sums, each <= half an ulp at < 8 A),
+// which is a relative error of ~7e-6 at r = 0.3 A, passed on to every NEP
+// pair term of the pair.  Pairs closer than the outer ZBL radius (rare
+// outside cascades) therefore take their displacement from the FP64
+// positions, rounded once to FP32 (relative error <= 2^-24 per component).
+// close2: the squared outer ZBL radius; k, m: cell-ordered slots of i and j.
+template <typename R>
+__device__ __forceinline__ void close_pair_fp64(R close2, const Grid& g,
+                                                const double* __restrict__ x64,
+                                                const int* __restrict__ perm, int k, int m, R& dx,
+                                                R& dy, R& dz, R& r2)
+{
+    if constexpr (sizeof(R) == 4) {
+        if (r2 < close2) {
+            double d[3];
+            disp64(g, x64, perm[k], perm[m], d);
+            dx = (R)d[0];
+            dy = (R)d[1];
+            dz = (R)d[2];
+            r2 = dx * dx + dy * dy + dz * dz;
+        }
+    }
+}
+
 // Radial basis coefficients for the neighbour kernel that also sums the
 // radial descriptor (one species).
 template <typename R>
 struct RadCoef {
     R inv_rcR;
     R hR[NR * KR], CR[NR];
+    R close2;   // squared outer ZBL radius (close pairs, see close_pair_fp64)
 };
 
 // WQ: also the radial descriptor q_n of every atom (one species, lists
@@ -458,13 +532,23 @@ struct RadCoef {
 // descriptor work inside the hit branch would run with most lanes idle).
 // TRIC: triclinic cells (stencil offsets are vectors; the orthorhombic
 // instantiation keeps per-axis offsets).
-// CH: the candidates of a stencil cell are tested in unrolled chunks of
-// NB_CHUNK that only set hit bits (angular, radial); the set bits are stored
-// afterwards in the same order (the lists are identical).  The chunk reads up
-// to NB_CHUNK - 1 positions past the cell, so pos4 must hold NB_CHUNK - 1
-// readable entries past the last atom; the bits of those are masked off.
+// CH: the candidates of a stencil cell are tested in unrolled chunks of CHW
+// that only set hit bits (angular, radial); the set bits are stored
+// afterwards in candidate order.  The chunk reads up to CHW - 1 positions
+// past the range, so pos4 must hold NB_CHUNK - 1 >= CHW - 1 readable entries
+// past the last atom; the bits of those are masked off.
+// Orthorhombic cells (CH): only the candidates that can be within reach are
+// tested.  A stencil column (ox, oy) whose nearest point is farther than the
+// list cutoff r_l in x/y is skipped; otherwise its z reach is
+// R = sqrt(r_l^2 - dx_min^2 - dy_min^2) (+ a 1e-3 A margin), and of each cell
+// of the column only the z slices (see Grid::zs) that overlap
+// [z_i - R, z_i + R] are tested.  The lateral bound uses the cell extents in
+// periodic directions only (atoms outside an open extent are clamped into
+// the edge cells); the z slices clamp the same way, so the windows are exact
+// in every case.  Every candidate left out is farther than r_l, so the lists
+// hold the same pairs for any zs and CHW (in slice order within a cell).
 constexpr int NB_CHUNK = 16;
-template <typename R, bool WQ, bool TRIC = false, bool CH = false>
+template <typename R, bool WQ, bool TRIC = false, bool CH = false, int CHW = NB_CHUNK>
 __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                                                    const typename V4<R>::T* __restrict__ pos4,
                                                    const int* __restrict__ cell_sorted,
@@ -474,7 +558,9 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                                                    int* __restrict__ maxc,
                                                    unsigned long long* __restrict__ pairs,
                                                    const int* __restrict__ gate,
-                                                   const RadCoef<R> rq, R* __restrict__ qr)
+                                                   const RadCoef<R> rq, R* __restrict__ qr,
+                                                   const int* __restrict__ perm,
+                                                   const double* __restrict__ x64)
 {
     using P4 = typename V4<R>::T;
     if (gate && *gate == 0) return;   // lists still valid (Verlet skin)
@@ -494,16 +580,33 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
         const int M = g.M;
         int* col = nbr + k;
         const size_t ld = (size_t)g.ld;
+        const int zs = TRIC ? 1 : (g.zs > 1 ? g.zs : 1);
+        const R zsl = (R)(zs * g.inv_lc[2]);   // slices per A along z
+        // reach tests with the list cutoff widened by 1e-3 A (far above the
+        // rounding of these FP32 bounds): no candidate within r_l is lost
+        const R rl_m = sqrt(rcR2) + R(1e-3), rl_m2 = rl_m * rl_m;
         for (int ox = -1; ox <= 1; ++ox) {
             int X = cx + ox;
             if (g.pbc[0]) { X += X < 0 ? ncx : 0; X -= X >= ncx ? ncx : 0; }
             else if (X < 0 || X >= ncx) continue;
             const R px0 = p.x - R(ox) * lx;
+            // nearest x of the column's atoms (periodic: inside [0, lx))
+            R dxm = R(0);
+            if (!TRIC && CH && g.pbc[0] && ox != 0)
+                dxm = ox > 0 ? lx - p.x : p.x;
+            dxm = dxm > R(0) ? dxm : R(0);
             for (int oy = -1; oy <= 1; ++oy) {
                 int Y = cy + oy;
                 if (g.pbc[1]) { Y += Y < 0 ? ncy : 0; Y -= Y >= ncy ? ncy : 0; }
                 else if (Y < 0 || Y >= ncy) continue;
                 const R py0 = p.y - R(oy) * ly;
+                R dym = R(0);
+                if (!TRIC && CH && g.pbc[1] && oy != 0)
+                    dym = oy > 0 ? ly - p.y : p.y;
+                dym = dym > R(0) ? dym : R(0);
+                const R reach2 = rl_m2 - dxm * dxm - dym * dym;
+                if (!TRIC && CH && reach2 <= R(0)) continue;   // column out of reach
+                const R reach = TRIC || !CH ? R(0) : sqrt(reach2);
                 const int rowXY = (X * ncy + Y) * ncz;
                 for (int oz = -1; oz <= 1; ++oz) {
                     int Z = cz + oz;
@@ -519,24 +622,41 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                     }
                     const int code = (ox + 1) * 9 + (oy + 1) * 3 + (oz + 1);
                     const int c2 = rowXY + Z;
-                    const int e = start[c2 + 1];
                     if constexpr (CH) {
-                        for (int m0 = start[c2]; m0 < e; m0 += NB_CHUNK) {
+                        // the cell's z slices within reach of pz (clamped: the
+                        // edge slices of a cell hold any atom beyond them)
+                        int t0 = 0, t1 = zs - 1;
+                        if (!TRIC && zs > 1) {
+                            const R zlo = pz - reach, zhi = pz + reach;
+                            // nothing within reach (atoms of periodic or
+                            // interior cells lie inside [0, lz))
+                            const bool inside = g.pbc[2] || (Z > 0 && Z < ncz - 1);
+                            if (inside && (zhi < R(0) || zlo >= lz)) continue;
+                            t0 = (int)floor(zlo * zsl);
+                            t1 = (int)floor(zhi * zsl);
+                            t0 = t0 < 0 ? 0 : (t0 >= zs ? zs - 1 : t0);
+                            t1 = t1 < 0 ? 0 : (t1 >= zs ? zs - 1 : t1);
+                        } else if (!TRIC && g.pbc[2]) {
+                            if (pz + reach < R(0) || pz - reach >= lz) continue;
+                        }
+                        const int e = start[c2 * zs + t1 + 1];
+                        for (int m0 = start[c2 * zs + t0]; m0 < e; m0 += CHW) {
                             const P4* q0 = pos4 + m0;
                             unsigned hr = 0u, ha = 0u;   // r < rc_R, r < rc_A
 #pragma unroll
-                            for (int j = 0; j < NB_CHUNK; ++j) {
+                            for (int j = 0; j < CHW; ++j) {
                                 const P4 q = q0[j];
                                 const R dx = q.x - px, dy = q.y - py, dz = q.z - pz;
                                 const R r2 = dx * dx + dy * dy + dz * dz;
                                 if (r2 < rcR2) hr |= 1u << j;
                                 if (r2 < rcA2) ha |= 1u << j;
                             }
-                            // this cell's atoms only, never the atom itself
+                            // this range's atoms only, never the atom itself
                             const int nv = e - m0;
-                            unsigned keep = nv >= NB_CHUNK ? 0xffffffffu : (1u << nv) - 1u;
+                            unsigned keep = nv >= CHW ? (CHW == 32 ? 0xffffffffu : (1u << CHW) - 1u)
+                                                      : (1u << nv) - 1u;
                             const unsigned self = (unsigned)(k - m0);
-                            if (self < (unsigned)NB_CHUNK) keep &= ~(1u << self);
+                            if (self < (unsigned)CHW) keep &= ~(1u << self);
                             ha &= hr & keep;
                             hr &= keep & ~ha;   // radial only
                             tot += __popc(ha) + __popc(hr);
@@ -553,7 +673,9 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                             }
                         }
                     } else {
-                        for (int m = start[c2]; m < e; ++m) {
+                        const int zsn = g.zs > 1 ? g.zs : 1;
+                        const int e = start[(c2 + 1) * zsn];
+                        for (int m = start[c2 * zsn]; m < e; ++m) {
                             const P4 q = pos4[m];
                             const R dx = q.x - px, dy = q.y - py, dz = q.z - pz;
                             const R r2 = dx * dx + dy * dy + dz * dz;
@@ -579,6 +701,7 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
             R Sb[KR];
 #pragma unroll
             for (int kk = 0; kk < KR; ++kk) Sb[kk] = R(0);
+            bool close = false;
             const int ns = sa + sro;
             auto slot = [&](int t) { return t < sa ? t : M - 1 - (t - sa); };
             int ent_n = ns > 0 ? col[(size_t)slot(0) * ld] : 0;
@@ -591,9 +714,11 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                 if (t + 1 < ns) pj_n = pos4[ent_n >> 5];
                 if (t + 2 < ns) ent_nn = col[(size_t)slot(t + 2) * ld];
                 const P4 off = s_off[ent & 31];
-                const R fx = pj.x - p.x + off.x, fy = pj.y - p.y + off.y, fz = pj.z - p.z + off.z;
-                const R f2 = fx * fx + fy * fy + fz * fz;
+                R fx = pj.x - p.x + off.x, fy = pj.y - p.y + off.y, fz = pj.z - p.z + off.z;
+                R f2 = fx * fx + fy * fy + fz * fz;
                 if (f2 < rcR2) {
+                    close |= f2 < rq.close2;
+                    close_pair_fp64<R>(rq.close2, g, x64, perm, k, ent >> 5, fx, fy, fz, f2);
                     const R rr = f2 * nepm::nep_rsqrt(f2);
                     R T[KR], dT[KR], fc, dfc, dxdr;
                     nepm::cheb<KR, false>(rr, rq.inv_rcR, T, dT, fc, dfc, dxdr);
@@ -608,6 +733,7 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                 for (int kk = 0; kk < KR; ++kk) acc += rq.hR[n * KR + kk] * Sb[kk];
                 qr[(size_t)n * ld + k] = acc;
             }
+            if (close) atomicOr(status, ST_CLOSE);
         }
     }
     // statistics: block maxima and pair sums
@@ -1147,8 +1273,9 @@ __global__ void __launch_bounds__(TILE) k_nep(const Model<R> P, const Grid g,
             if (s + 1 < total) pj_n = pos4[ent_n >> 5];
             if (s + 2 < total) ent_nn = entry(s + 2);
             const P4 off = s_off[ent & 31];
-            const R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
-            const R r2 = dx * dx + dy * dy + dz * dz;
+            R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
+            R r2 = dx * dx + dy * dy + dz * dz;
+            close_pair_fp64<R>(P.zbl_r2 * P.zbl_r2, g, x64, perm, k, ent >> 5, dx, dy, dz, r2);
             const R inv_r = nepm::nep_rsqrt(r2);
             const R r = r2 * inv_r;
             desc_pair<R>(P, dx, dy, dz, r, inv_r, s < na, Sb, A);
@@ -1177,8 +1304,9 @@ __global__ void __launch_bounds__(TILE) k_nep(const Model<R> P, const Grid g,
             if (s + 2 < total) ent_nn = entry(s + 2);
             const int m = ent >> 5;
             const P4 off = s_off[ent & 31];
-            const R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
-            const R r2 = dx * dx + dy * dy + dz * dz;
+            R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
+            R r2 = dx * dx + dy * dy + dz * dz;
+            close_pair_fp64<R>(P.zbl_r2 * P.zbl_r2, g, x64, perm, k, m, dx, dy, dz, r2);
             const R inv_r = nepm::nep_rsqrt(r2);
             const R r = r2 * inv_r;
             const R ux = dx * inv_r, uy = dy * inv_r, uz = dz * inv_r;
@@ -1295,7 +1423,10 @@ __global__ void __launch_bounds__(128) k_radial_q(const Model<R> P, const Grid g
                                                   R* __restrict__ qr,
                                                   int* __restrict__ act_nbr,
                                                   int2* __restrict__ act_cnt,
-                                                  const R* __restrict__ coef)
+                                                  const R* __restrict__ coef,
+                                                  const int* __restrict__ perm,
+                                                  const double* __restrict__ x64,
+                                                  int* __restrict__ status)
 {
     using P4 = typename V4<R>::T;
     constexpr int NTS = MS ? NT_MAX : 1;
@@ -1314,6 +1445,7 @@ __global__ void __launch_bounds__(128) k_radial_q(const Model<R> P, const Grid g
 #pragma unroll
         for (int kk = 0; kk < KR; ++kk) Sb[t][kk] = R(0);
     int a_na = 0, a_nro = 0;
+    bool close = false;
     // two-stage prefetch: entry s + 2 and position s + 1 in flight during pair s
     int ent_n = total > 0 ? nbr[(size_t)list_slot(0, na, M) * ld + k] : 0;
     int ent_nn = total > 1 ? nbr[(size_t)list_slot(1, na, M) * ld + k] : 0;
@@ -1325,13 +1457,15 @@ __global__ void __launch_bounds__(128) k_radial_q(const Model<R> P, const Grid g
         if (s + 1 < total) pj_n = pos4[ent_n >> 5];
         if (s + 2 < total) ent_nn = nbr[(size_t)list_slot(s + 2, na, M) * ld + k];
         const P4 off = s_off[ent & 31];
-        const R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
-        const R r2 = dx * dx + dy * dy + dz * dz;
+        R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
+        R r2 = dx * dx + dy * dy + dz * dz;
         if (r2 >= P.rcR2) continue;   // beyond r_c (lists built with a skin)
         if (act_nbr) {
             if (r2 < P.rcA2) act_nbr[(size_t)(a_na++) * ld + k] = ent;
             else act_nbr[(size_t)(M - 1 - a_nro++) * ld + k] = ent;
         }
+        close |= r2 < P.zbl_r2 * P.zbl_r2;
+        close_pair_fp64<R>(P.zbl_r2 * P.zbl_r2, g, x64, perm, k, ent >> 5, dx, dy, dz, r2);
         const R r = r2 * nepm::nep_rsqrt(r2);
         R Tk[KR], dT[KR], fc, dfc, dxdr;
         nepm::cheb<KR, false>(r, P.inv_rcR, Tk, dT, fc, dfc, dxdr);
@@ -1351,6 +1485,7 @@ __global__ void __launch_bounds__(128) k_radial_q(const Model<R> P, const Grid g
         }
     }
     if (act_cnt) act_cnt[k] = make_int2(a_na, a_nro);
+    if (close) atomicOr(status, ST_CLOSE);
     R q[NR];
     if constexpr (MS) {
         const int ti = (int)pi.w;
@@ -1475,8 +1610,9 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
                                                   int ang_lim = 0)
 {
     // with ang_max: this launch handles only evaluations with more than
-    // ang_lim angular neighbours on some atom (k_nep_ang_tm takes the others)
-    if (ang_max && *ang_max <= ang_lim) return;
+    // ang_lim angular neighbours on some atom or with a pair closer than the
+    // outer ZBL radius (k_nep_ang_tm takes the others)
+    if (ang_max && *ang_max <= ang_lim && !(*status & ST_CLOSE)) return;
     using A_ = Acc<R>;
     using P4 = typename V4<R>::T;
     __shared__ P4 s_off[27];
@@ -1530,9 +1666,10 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
                 pj_n = pos4[ent_n >> 5];
             }
             const P4 off = s_off[ent & 31];
-            const R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
-            const R r2 = dx * dx + dy * dy + dz * dz;
+            R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
+            R r2 = dx * dx + dy * dy + dz * dz;
             if (r2 >= P.rcA2) continue;   // beyond r_c^A (lists built with a skin)
+            close_pair_fp64<R>(P.zbl_r2 * P.zbl_r2, g, x64, perm, k, ent >> 5, dx, dy, dz, r2);
             const R inv_r = nepm::nep_rsqrt(r2);
             const R r = r2 * inv_r;
             R Tk[KA], dT[KA], fc, dfc, dxdr;
@@ -1620,9 +1757,10 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
             }
             const int m = ent >> 5;
             const P4 off = s_off[ent & 31];
-            const R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
-            const R r2 = dx * dx + dy * dy + dz * dz;
+            R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
+            R r2 = dx * dx + dy * dy + dz * dz;
             if (r2 >= P.rcA2) continue;
+            close_pair_fp64<R>(P.zbl_r2 * P.zbl_r2, g, x64, perm, k, m, dx, dy, dz, r2);
             const R inv_r = nepm::nep_rsqrt(r2);
             const R r = r2 * inv_r;
             R fx, fy, fz;
@@ -1692,18 +1830,25 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
 // bp[(k T + t) * 3] = (b_0..b_3), (b_4..b_7), (b_8, B0, 0, 0).
 // MS (several species): the pair (i, j) adds atom i's adjoint for neighbour
 // species t_j and atom j's for species t_i (bp[(k * T + t) * 3]).
-template <typename R, bool MS>
-__global__ void __launch_bounds__(TILE) k_radial_force(const Model<R> P, const Grid g,
+template <typename R, bool MS, bool CLOSE = true>
+__global__ void __launch_bounds__(TILE, sizeof(R) == 4 && !MS ? 7 : 1) k_radial_force(const Model<R> P, const Grid g,
                                                        const typename V4<R>::T* __restrict__ pos4,
                                                        const int* __restrict__ nbr,
                                                        const int2* __restrict__ cnt,
                                                        const typename V4<R>::T* __restrict__ bp,
                                                        typename Acc<R>::T* __restrict__ facc,
                                                        double* __restrict__ partials,
-                                                       int* __restrict__ status)
+                                                       int* __restrict__ status,
+                                                       const int* __restrict__ perm,
+                                                       const double* __restrict__ x64,
+                                                       bool dispatch = false)
 {
     using A_ = Acc<R>;
     using P4 = typename V4<R>::T;
+    // dispatch (FP32, one species): both instantiations are launched and the
+    // one without the close-pair branch takes the evaluations without close
+    // pairs
+    if (dispatch && (((*status & ST_CLOSE) != 0) != CLOSE)) return;
     __shared__ P4 s_off[27];
     fill_stencil<R>(s_off, g);
     const int k = blockIdx.x * TILE + threadIdx.x;
@@ -1736,9 +1881,11 @@ __global__ void __launch_bounds__(TILE) k_radial_force(const Model<R> P, const G
             }
             if (s + 2 < total) ent_nn = nbr[(size_t)list_slot(s + 2, na, M) * ld + k];
             const P4 off = s_off[ent & 31];
-            const R dx = rj0.x - ri0.x + off.x, dy = rj0.y - ri0.y + off.y, dz = rj0.z - ri0.z + off.z;
-            const R r2 = dx * dx + dy * dy + dz * dz;
+            R dx = rj0.x - ri0.x + off.x, dy = rj0.y - ri0.y + off.y, dz = rj0.z - ri0.z + off.z;
+            R r2 = dx * dx + dy * dy + dz * dz;
             if (r2 >= P.rcR2) continue;   // beyond r_c (lists built with a skin)
+            if constexpr (CLOSE)
+                close_pair_fp64<R>(P.zbl_r2 * P.zbl_r2, g, x64, perm, k, ent >> 5, dx, dy, dz, r2);
             const R inv_r = nepm::nep_rsqrt(r2);
             const R r = r2 * inv_r;
             R T[KR], dT[KR], fc, dfc, dxdr;
@@ -1799,9 +1946,10 @@ __global__ void __launch_bounds__(TILE) k_radial_force(const Model<R> P, const G
             }
             if (s + 2 < total) ent_nn = nbr[(size_t)list_slot(s + 2, na, M) * ld + k];
             const P4 off = s_off[ent & 31];
-            const R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
-            const R r2 = dx * dx + dy * dy + dz * dz;
+            R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
+            R r2 = dx * dx + dy * dy + dz * dz;
             if (r2 >= P.rcR2) continue;   // beyond r_c (lists built with a skin)
+            close_pair_fp64<R>(P.zbl_r2 * P.zbl_r2, g, x64, perm, k, ent >> 5, dx, dy, dz, r2);
             const R inv_r = nepm::nep_rsqrt(r2);
             const R r = r2 * inv_r;
             R T[KR], dT[KR], fc, dfc, dxdr;

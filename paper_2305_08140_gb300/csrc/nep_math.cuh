@@ -226,6 +226,100 @@ NEP_HD void harmonics_grad_dot(R x, R y, R z, const R* G, R& vx, R& vy, R& vz)
           s70_4 * (c3 * G[20] + s3m * G[21]);
 }
 
+// The harmonics and their gradient contraction in three groups of 8 indices
+// (group 0: lm 0-7 = l 1, 2; group 1: lm 8-15 = l 3 and the first l = 4;
+// group 2: lm 16-23), for callers that stream coefficients group by group:
+// harmonics_group<GR> writes Y[0..7] = R_lm for lm = 8 GR + 0..7, and
+// harmonics_grad_dot_group<GR> adds sum over the group's lm of Gg[lm - 8 GR]
+// grad R_lm(u) to v.  Summed over the three groups they equal harmonics and
+// harmonics_grad_dot (the same terms).
+template <int GR, typename R>
+NEP_HD void harmonics_group(R x, R y, R z, R* Y)
+{
+    if constexpr (GR == 0) {
+        harmonics_l12(x, y, z, Y);
+    } else {
+        const R s6_4 = R(0.6123724356957945), s15 = R(3.872983346207417),
+                s15_2 = R(1.9364916731037085), s10_4 = R(0.7905694150420949),
+                s5_4 = R(0.5590169943749475), s5_2 = R(1.118033988749895),
+                s70_4 = R(2.091650066335189), s35_8 = R(0.739509972887452),
+                s35_2 = R(2.958039891549808);
+        R x2 = x * x, y2 = y * y, z2 = z * z, rho2 = x2 + y2;
+        R xy = x * y, xmy = x2 - y2;
+        R c3 = x * (x2 - R(3) * y2), s3m = y * (R(3) * x2 - y2);
+        if constexpr (GR == 1) {   // as harmonics_l34, Y[8..15]
+            R a3 = R(4) * z2 - rho2;
+            Y[0] = z * (z2 - R(1.5) * rho2);
+            Y[1] = s6_4 * x * a3;
+            Y[2] = s6_4 * y * a3;
+            Y[3] = s15_2 * z * xmy;
+            Y[4] = s15 * xy * z;
+            Y[5] = s10_4 * c3;
+            Y[6] = s10_4 * s3m;
+            Y[7] = z2 * z2 - R(3) * z2 * rho2 + R(0.375) * rho2 * rho2;
+        } else {                   // Y[16..23]
+            R a4 = R(4) * z2 - R(3) * rho2, b4 = R(6) * z2 - rho2;
+            Y[0] = s10_4 * x * z * a4;
+            Y[1] = s10_4 * y * z * a4;
+            Y[2] = s5_4 * b4 * xmy;
+            Y[3] = s5_2 * b4 * xy;
+            Y[4] = s70_4 * z * c3;
+            Y[5] = s70_4 * z * s3m;
+            Y[6] = s35_8 * (xmy * xmy - R(4) * x2 * y2);
+            Y[7] = s35_2 * xy * xmy;
+        }
+    }
+}
+
+template <int GR, typename R>
+NEP_HD void harmonics_grad_dot_group(R x, R y, R z, const R* Gg, R& vx, R& vy, R& vz)
+{
+    const R s3 = R(1.7320508075688772), s6_4 = R(0.6123724356957945),
+            s15 = R(3.872983346207417), s15_2 = R(1.9364916731037085),
+            s10_4 = R(0.7905694150420949), s5 = R(2.23606797749979),
+            s5_2 = R(1.118033988749895), s70_4 = R(2.091650066335189),
+            s35_2 = R(2.958039891549808);
+    R x2 = x * x, y2 = y * y, z2 = z * z, rho2 = x2 + y2;
+    R xy = x * y, xz = x * z, yz = y * z, xmy = x2 - y2, xyz = xy * z;
+    if constexpr (GR == 0) {
+        const R* G = Gg;   // lm 0..7
+        vx += G[1];
+        vy += G[2];
+        vz += G[0];
+        vx += -x * G[3] + s3 * (z * G[4] + x * G[6] + y * G[7]);
+        vy += -y * G[3] + s3 * (z * G[5] - y * G[6] + x * G[7]);
+        vz += R(2) * z * G[3] + s3 * (x * G[4] + y * G[5]);
+    } else if constexpr (GR == 1) {
+        const R* G = Gg - 8;   // lm 8..15
+        vx += R(-3) * xz * G[8] + s6_4 * (R(4) * z2 - R(3) * x2 - y2) * G[9] -
+              s6_4 * R(2) * xy * G[10] + s15 * (xz * G[11] + yz * G[12]) +
+              s10_4 * R(3) * (xmy * G[13] + R(2) * xy * G[14]);
+        vy += R(-3) * yz * G[8] - s6_4 * R(2) * xy * G[9] +
+              s6_4 * (R(4) * z2 - x2 - R(3) * y2) * G[10] + s15 * (-yz * G[11] + xz * G[12]) +
+              s10_4 * R(3) * (R(-2) * xy * G[13] + xmy * G[14]);
+        vz += (R(3) * z2 - R(1.5) * rho2) * G[8] + s6_4 * R(8) * (xz * G[9] + yz * G[10]) +
+              s15_2 * xmy * G[11] + s15 * xy * G[12];
+        R t15 = R(1.5) * rho2 - R(6) * z2;
+        vx += x * t15 * G[15];
+        vy += y * t15 * G[15];
+        vz += (R(4) * z2 * z - R(6) * z * rho2) * G[15];
+    } else {
+        const R* G = Gg - 16;   // lm 16..23
+        R c3 = x * (x2 - R(3) * y2), s3m = y * (R(3) * x2 - y2);
+        vx += s10_4 * (z * (R(4) * z2 - R(9) * x2 - R(3) * y2) * G[16] - R(6) * xyz * G[17]) +
+              s5 * x * (R(3) * z2 - x2) * G[18] + s5_2 * y * (R(6) * z2 - R(3) * x2 - y2) * G[19] +
+              s70_4 * (R(3) * z * xmy * G[20] + R(6) * xyz * G[21]) +
+              s35_2 * (c3 * G[22] + s3m * G[23]);
+        vy += s10_4 * (R(-6) * xyz * G[16] + z * (R(4) * z2 - R(3) * x2 - R(9) * y2) * G[17]) -
+              s5 * y * (R(3) * z2 - y2) * G[18] + s5_2 * x * (R(6) * z2 - x2 - R(3) * y2) * G[19] +
+              s70_4 * (R(-6) * xyz * G[20] + R(3) * z * xmy * G[21]) +
+              s35_2 * (-s3m * G[22] + c3 * G[23]);
+        vz += s10_4 * R(3) * (R(4) * z2 - rho2) * (x * G[16] + y * G[17]) +
+              R(3) * s5 * z * xmy * G[18] + R(6) * s5 * xyz * G[19] +
+              s70_4 * (c3 * G[20] + s3m * G[21]);
+    }
+}
+
 // D[lm] = grad R_lm(u) . w, the directional derivatives of the homogeneous
 // polynomials above along w (each row is the gradient of harmonics_grad_dot
 // dotted with w).

@@ -4,14 +4,19 @@
 // The angular pair-force pass needs the atom's adjoint dU/dA_nlm (5 x 24
 // values) for every pair; held in registers it limits the kernel to two
 // blocks per SM.  Here each block allocates 128 columns of Tensor Memory
-// (lane = thread, column n * 24 + lm), the descriptor sums A are written there
-// after the descriptor pass, turned into the adjoint in place after the
-// network, and read back per radial channel (three 8-column loads, double
-// buffered; a pair's first channel is loaded at the end of the previous pair)
-// inside the pair loop.  The arithmetic is that of k_nep_ang (nep_device.cuh)
-// except that the block's ZBL virial is summed in 2^-32 eV fixed point (order
-// independent) instead of FP64 per thread; otherwise only where the 120
-// values live differs.
+// (lane = thread, column n * 24 + lm).  The descriptor sums A are formed in
+// two passes over the atom's angular pairs (radial channels 0-2, then 3-4, so
+// that at most 72 sums are held in registers), each pass storing its channels
+// to Tensor Memory; the network turns them into the adjoint in place; the
+// pair loop streams the adjoint back in 8-column groups (one group in flight
+// while the previous one is used).  At <= 128 registers per thread four
+// blocks fit per SM (16 warps), which is also the most the 512 columns of
+// Tensor Memory hold: the launch pads its dynamic shared memory so that no
+// fifth block can be resident.  The arithmetic is that of k_nep_ang
+// (nep_device.cuh) except that the angular force of a pair is contracted
+// channel by channel.  It carries no ZBL and no close-pair branch: an
+// evaluation with a pair inside the outer ZBL radius (a status bit of the
+// radial-descriptor pass) goes to k_nep_ang, as do dense clumps.
 //
 // tcgen05.ld/st/alloc are warp-collective (.sync.aligned): every one of them
 // is executed by all 32 lanes of a warp together -- the pair loop runs to the
@@ -61,6 +66,14 @@ __device__ __forceinline__ void tm_wait_ld24(float* v)
                  :
                  : "memory");
 }
+__device__ __forceinline__ void tm_wait_ld8(float* v)
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]),
+                   "+f"(v[6]), "+f"(v[7])
+                 :
+                 : "memory");
+}
 __device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tm_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -79,66 +92,177 @@ __device__ __forceinline__ void tm_st24(uint32_t tb, int n, const float* v)
     tm_st8(tb + (uint32_t)(n * NLM + 16), v + 16);
 }
 
-// force_pair_ang with the adjoint in Tensor Memory (warp-collective).  buf[0]
-// holds radial channel 0, loaded before the call and not yet waited for;
-// with `prefetch` (warp-uniform) channel 0 is loaded again into buf[0] for
-// the next pair as soon as this pair's contraction is done.
+// force_pair_ang with the adjoint in Tensor Memory (warp-collective).  The
+// adjoint is read in 15 groups of 8 columns, group-major: harmonic group GR
+// (lm 8 GR .. 8 GR + 7, see nepm::harmonics_group) of channels n = 0..4 in
+// turn (columns n * 24 + 8 GR), linear index c = 5 GR + n; buf[0] holds
+// c = 0 on entry, loaded and not yet waited for; c + 1 (into buf[(c+1) & 1])
+// is loaded while c is used.  Only the current group's harmonics Y_lm and
+// G_lm = sum_n a_nlm g_n are live: the tangential part sum_lm G_lm grad Y_lm
+// is added group by group, and the radial part
+//   S = sum_n [g_n' sum_lm a_nlm Y_lm - (g_n / r) sum_lm l a_nlm Y_lm]
+// is accumulated per channel (P_n, Q_n).  With `prefetch` (warp-uniform)
+// c = 0 is loaded again into buf[0] for the next pair once the last group
+// (c = 14, also in buf[0]) has been used.
 __device__ __forceinline__ void force_pair_ang_tm(const Model<float>& P, float r, float inv_r,
                                                   float ux, float uy, float uz, uint32_t tb,
-                                                  float (&buf)[2][NLM], bool prefetch,
+                                                  float (&buf)[2][8], bool prefetch,
                                                   float& fx, float& fy, float& fz)
 {
-    float T[KA], dT[KA], fc, dfc, dxdr;
-    nepm::cheb<KA, true>(r, P.inv_rcA, T, dT, fc, dfc, dxdr);
     float gn[NA], dgn[NA];
+    {
+        float T[KA], dT[KA], fc, dfc, dxdr;
+        nepm::cheb<KA, true>(r, P.inv_rcA, T, dT, fc, dfc, dxdr);
 #pragma unroll
-    for (int n = 0; n < NA; ++n) {
-        float a = P.CA[n], b = 0.f;
+        for (int n = 0; n < NA; ++n) {
+            float a = P.CA[n], b = 0.f;
 #pragma unroll
-        for (int kk = 0; kk < KA; ++kk) {
-            a += P.hA[n * KA + kk] * T[kk];
-            b += P.hA[n * KA + kk] * dT[kk];
+            for (int kk = 0; kk < KA; ++kk) {
+                a += P.hA[n * KA + kk] * T[kk];
+                b += P.hA[n * KA + kk] * dT[kk];
+            }
+            gn[n] = fc * a;
+            dgn[n] = dfc * a + fc * dxdr * b;
         }
-        gn[n] = fc * a;
-        dgn[n] = dfc * a + fc * dxdr * b;
     }
-    float G[NLM], Dd[NLM];
+    float Pn[NA], Qn[NA];
 #pragma unroll
-    for (int lm = 0; lm < NLM; ++lm) { G[lm] = 0.f; Dd[lm] = 0.f; }
-    // channel n + 1 is loaded while channel n is used
-    tm_wait_ld24(buf[0]);
+    for (int n = 0; n < NA; ++n) { Pn[n] = 0.f; Qn[n] = 0.f; }
+    float vx = 0.f, vy = 0.f, vz = 0.f;
 #pragma unroll
-    for (int n = 0; n < NA; ++n) {
-        if (n + 1 < NA) tm_ld24(tb, n + 1, buf[(n + 1) & 1]);
+    for (int GR = 0; GR < 3; ++GR) {
+        // copies of u that the compiler cannot see through (an empty volatile
+        // asm, ordered after the previous group's Tensor-Memory waits): the
+        // group's polynomials are formed here, not hoisted and kept live
+        float gx = ux, gy = uy, gz = uz;
+        asm volatile("" : "+f"(gx), "+f"(gy), "+f"(gz));
+        float Y[8], G[8];
+        if (GR == 0) nepm::harmonics_group<0>(gx, gy, gz, Y);
+        if (GR == 1) nepm::harmonics_group<1>(gx, gy, gz, Y);
+        if (GR == 2) nepm::harmonics_group<2>(gx, gy, gz, Y);
 #pragma unroll
-        for (int lm = 0; lm < NLM; ++lm) {
-            G[lm] += buf[n & 1][lm] * gn[n];
-            Dd[lm] += buf[n & 1][lm] * dgn[n];
+        for (int j = 0; j < 8; ++j) G[j] = 0.f;
+#pragma unroll
+        for (int n = 0; n < NA; ++n) {
+            const int c = GR * NA + n;
+            tm_wait_ld8(buf[c & 1]);
+            if (c + 1 < 3 * NA) {
+                const int n1 = (c + 1) % NA, g1 = (c + 1) / NA;
+                tm_ld8(tb + (uint32_t)(n1 * NLM + 8 * g1), buf[(c + 1) & 1]);
+            }
+            float sa = 0.f, sb = 0.f;   // sum a Y over the group's lower / upper l
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float v = buf[c & 1][j];
+                G[j] += v * gn[n];
+                // group 0: l = 1 (j < 3), 2; group 1: l = 3 (j < 7), 4; group 2: l = 4
+                const bool lower = GR == 0 ? j < 3 : (GR == 1 ? j < 7 : true);
+                if (lower) sa += v * Y[j];
+                else sb += v * Y[j];
+            }
+            const float la = GR == 0 ? 1.f : (GR == 1 ? 3.f : 4.f);
+            const float lb = GR == 0 ? 2.f : 4.f;
+            Pn[n] += sa + sb;
+            Qn[n] += la * sa + lb * sb;
         }
-        if (n + 1 < NA) tm_wait_ld24(buf[(n + 1) & 1]);
+        if (GR == 0) nepm::harmonics_grad_dot_group<0>(gx, gy, gz, G, vx, vy, vz);
+        if (GR == 1) nepm::harmonics_grad_dot_group<1>(gx, gy, gz, G, vx, vy, vz);
+        if (GR == 2) nepm::harmonics_grad_dot_group<2>(gx, gy, gz, G, vx, vy, vz);
     }
-    if (prefetch) tm_ld24(tb, 0, buf[0]);   // the next pair's channel 0
-    float Y[NLM];
-    nepm::harmonics(ux, uy, uz, Y);
+    // the next pair's c = 0: buf[0] held the last group (3 NA is odd), now used
+    if (prefetch) tm_ld8(tb, buf[0]);
     float sang = 0.f;
 #pragma unroll
-    for (int lm = 0; lm < NLM; ++lm) {
-        const int l = lm < 3 ? 1 : (lm < 8 ? 2 : (lm < 15 ? 3 : 4));
-        sang += (Dd[lm] - float(l) * inv_r * G[lm]) * Y[lm];
-    }
-    float vx, vy, vz;
-    nepm::harmonics_grad_dot(ux, uy, uz, G, vx, vy, vz);
+    for (int n = 0; n < NA; ++n) sang += dgn[n] * Pn[n] - inv_r * gn[n] * Qn[n];
     fx = sang * ux + vx * inv_r;
     fy = sang * uy + vy * inv_r;
     fz = sang * uz + vz * inv_r;
 }
 
+// Descriptor pass over the atom's angular pairs for radial channels
+// [N0, N1): A_nlm = sum_j g_n(r_ij) Y_lm(u_ij) in registers, then the
+// channel's part of the descriptor (q_nl = sum_m A_nlm^2, q_n^4b) to shared
+// memory (s_q[nu - NR][TILE], this thread's column) and the sums to Tensor
+// Memory (stores not waited for).
+template <int N0, int N1, typename Entry>
+__device__ __forceinline__ void ang_desc_pass(const Model<float>& P, const Grid& g,
+                                              const float4* __restrict__ pos4,
+                                              const float4* s_off, int na,
+                                              const float4 pi, Entry entry, uint32_t tb,
+                                              float* s_q)
+{
+    constexpr int NN = N1 - N0;
+    float A[NN][NLM];
+#pragma unroll
+    for (int n = 0; n < NN; ++n)
+#pragma unroll
+        for (int lm = 0; lm < NLM; ++lm) A[n][lm] = 0.f;
+    int ent_n = na > 0 ? entry(0) : 0;
+    float4 pj_n = na > 0 ? pos4[ent_n >> 5] : pi;
+    for (int s = 0; s < na; ++s) {
+        const int ent = ent_n;
+        const float4 pj = pj_n;
+        if (s + 1 < na) {
+            ent_n = entry(s + 1);
+            pj_n = pos4[ent_n >> 5];
+        }
+        const float4 off = s_off[ent & 31];
+        float dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
+        float r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 >= P.rcA2) continue;   // beyond r_c^A (lists built with a skin)
+        const float inv_r = nepm::nep_rsqrt(r2);
+        const float r = r2 * inv_r;
+        float Tk[KA], dT[KA], fc, dfc, dxdr;
+        nepm::cheb<KA, false>(r, P.inv_rcA, Tk, dT, fc, dfc, dxdr);
+        float gn[NN];
+#pragma unroll
+        for (int n = 0; n < NN; ++n) {
+            float acc = P.CA[N0 + n];
+#pragma unroll
+            for (int kk = 0; kk < KA; ++kk) acc += P.hA[(N0 + n) * KA + kk] * Tk[kk];
+            gn[n] = fc * acc;
+        }
+        const float ux = dx * inv_r, uy = dy * inv_r, uz = dz * inv_r;
+        float Y[NLM];
+        nepm::harmonics_l12(ux, uy, uz, Y);
+#pragma unroll
+        for (int n = 0; n < NN; ++n)
+#pragma unroll
+            for (int lm = 0; lm < 8; ++lm) A[n][lm] += gn[n] * Y[lm];
+        nepm::harmonics_l34(ux, uy, uz, Y);
+#pragma unroll
+        for (int n = 0; n < NN; ++n)
+#pragma unroll
+            for (int lm = 8; lm < NLM; ++lm) A[n][lm] += gn[n] * Y[lm];
+    }
+#pragma unroll
+    for (int n = 0; n < NN; ++n) {
+#pragma unroll
+        for (int l = 1; l <= LM; ++l) {
+            float v = 0.f;
+#pragma unroll
+            for (int lm = l * l - 1; lm < (l + 1) * (l + 1) - 1; ++lm) v += A[n][lm] * A[n][lm];
+            s_q[((l - 1) * NA + N0 + n) * TILE + threadIdx.x] = v;
+        }
+        s_q[(LM * NA + N0 + n) * TILE + threadIdx.x] = nepm::fourbody(&A[n][3], (float*)nullptr);
+        tm_st24(tb, N0 + n, A[n]);
+    }
+}
+
 // k_nep_ang (one species, FP32) with the angular state in Tensor Memory; same
-// arguments and outputs.  At most TM_COLS x 3 columns are held per SM, so the
-// allocation never waits.  It handles the evaluations whose largest angular
-// neighbour count (*ang_max, from the neighbour kernel) is at most ang_lim and
-// returns at once otherwise (before allocating), k_nep_ang taking those.
-__global__ void __launch_bounds__(TILE, 3)
+// arguments and outputs.  At most TM_BLOCKS_PER_SM blocks may be resident
+// (TM_BLOCKS_PER_SM x TM_COLS = 512 columns, so the allocation never waits):
+// the launch checks the occupancy and pads the dynamic shared memory to
+// enforce it.  It handles the evaluations whose largest angular neighbour
+// count (*ang_max, from the neighbour kernel) is at most ang_lim and returns
+// at once otherwise (before allocating), k_nep_ang taking those.
+constexpr int TM_BLOCKS_PER_SM = 4;
+// dynamic shared memory: [0, TM_SQ_OFF) staged angular entries (at most
+// STAGE_MAX_SLOTS per atom), then the angular descriptor [D - NR][TILE]
+constexpr int TM_STAGE_SLOTS = 32;
+constexpr size_t TM_SQ_OFF = sizeof(int) * TM_STAGE_SLOTS * TILE;
+constexpr size_t TM_DYN_MIN = TM_SQ_OFF + sizeof(float) * (D - NR) * TILE;
+__global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
     k_nep_ang_tm(const Model<float> P, const Grid g, const float4* __restrict__ pos4,
                  const int* __restrict__ nbr, const int2* __restrict__ cnt,
                  const int* __restrict__ perm, const double* __restrict__ x64,
@@ -147,12 +271,13 @@ __global__ void __launch_bounds__(TILE, 3)
                  double* __restrict__ site_energy, int* __restrict__ status, int stage_slots,
                  const int* __restrict__ ang_max, int ang_lim)
 {
-    if (*ang_max > ang_lim) return;   // whole grid: k_nep_ang runs instead
+    // whole grid: k_nep_ang runs instead (dense clumps; pairs inside the ZBL
+    // range, whose FP64 branches this kernel does not carry)
+    if (*ang_max > ang_lim || (*status & ST_CLOSE)) return;
     using A_ = Acc<float>;
     __shared__ float4 s_off[27];
     __shared__ int s_max;
     __shared__ uint32_t s_tmem;
-    __shared__ long long s_wz[9];   // ZBL virial of the block, fixed point (2^-32 eV)
     __shared__ __align__(16) float s_w[H * WROW];
     __shared__ double s_red[TILE / 32][NPART];
     extern __shared__ __align__(16) unsigned char s_dyn[];
@@ -165,7 +290,6 @@ __global__ void __launch_bounds__(TILE, 3)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (threadIdx.x == 0) s_max = 0;
-    if (threadIdx.x < 9) s_wz[threadIdx.x] = 0;
     fill_network_rows<float>(s_w, P);
     tm_fence_before();
     fill_stencil<float>(s_off, g);   // ends with __syncthreads
@@ -185,72 +309,17 @@ __global__ void __launch_bounds__(TILE, 3)
     };
     const float4 pi = valid ? pos4[k] : make_float4(0.f, 0.f, 0.f, 0.f);
 
-    // descriptor pass: A_nlm = sum_j g_n(r_ij) Y_lm(u_ij) in registers
-    float A[NA][NLM];
-#pragma unroll
-    for (int n = 0; n < NA; ++n)
-#pragma unroll
-        for (int lm = 0; lm < NLM; ++lm) A[n][lm] = 0.f;
-    {
-        int ent_n = na > 0 ? entry(0) : 0;
-        float4 pj_n = na > 0 ? pos4[ent_n >> 5] : pi;
-        for (int s = 0; s < na; ++s) {
-            const int ent = ent_n;
-            const float4 pj = pj_n;
-            if (s + 1 < na) {
-                ent_n = entry(s + 1);
-                pj_n = pos4[ent_n >> 5];
-            }
-            const float4 off = s_off[ent & 31];
-            const float dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 >= P.rcA2) continue;   // beyond r_c^A (lists built with a skin)
-            const float inv_r = nepm::nep_rsqrt(r2);
-            const float r = r2 * inv_r;
-            float Tk[KA], dT[KA], fc, dfc, dxdr;
-            nepm::cheb<KA, false>(r, P.inv_rcA, Tk, dT, fc, dfc, dxdr);
-            float gn[NA];
-#pragma unroll
-            for (int n = 0; n < NA; ++n) {
-                float acc = P.CA[n];
-#pragma unroll
-                for (int kk = 0; kk < KA; ++kk) acc += P.hA[n * KA + kk] * Tk[kk];
-                gn[n] = fc * acc;
-            }
-            const float ux = dx * inv_r, uy = dy * inv_r, uz = dz * inv_r;
-            float Y[NLM];
-            nepm::harmonics_l12(ux, uy, uz, Y);
-#pragma unroll
-            for (int n = 0; n < NA; ++n)
-#pragma unroll
-                for (int lm = 0; lm < 8; ++lm) A[n][lm] += gn[n] * Y[lm];
-            nepm::harmonics_l34(ux, uy, uz, Y);
-#pragma unroll
-            for (int n = 0; n < NA; ++n)
-#pragma unroll
-                for (int lm = 8; lm < NLM; ++lm) A[n][lm] += gn[n] * Y[lm];
-        }
-    }
-
-    // descriptor vector; A goes to Tensor Memory
+    // descriptor vector: angular part in two passes over the pairs (channels
+    // 0-2, 3-4; the sums A to Tensor Memory, q via shared memory), radial part
+    // from the neighbour kernel
+    float* s_q = reinterpret_cast<float*>(s_dyn + TM_SQ_OFF);
+    ang_desc_pass<0, 3>(P, g, pos4, s_off, na, pi, entry, tb, s_q);
+    ang_desc_pass<3, NA>(P, g, pos4, s_off, na, pi, entry, tb, s_q);
     float q[D];
 #pragma unroll
     for (int n = 0; n < NR; ++n) q[n] = valid ? qr[(size_t)n * ld + k] : 0.f;
 #pragma unroll
-    for (int l = 1; l <= LM; ++l) {
-        const int lo = l * l - 1, hi = (l + 1) * (l + 1) - 1;
-#pragma unroll
-        for (int n = 0; n < NA; ++n) {
-            float v = 0.f;
-#pragma unroll
-            for (int lm = lo; lm < hi; ++lm) v += A[n][lm] * A[n][lm];
-            q[NR + (l - 1) * NA + n] = v;
-        }
-    }
-#pragma unroll
-    for (int n = 0; n < NA; ++n) q[NR + LM * NA + n] = nepm::fourbody(&A[n][3], (float*)nullptr);
-#pragma unroll
-    for (int n = 0; n < NA; ++n) tm_st24(tb, n, A[n]);
+    for (int nu = NR; nu < D; ++nu) q[nu] = s_q[(nu - NR) * TILE + threadIdx.x];
     tm_wait_st();
 
     // network forward and backward (rolled over the hidden neurons, as
@@ -313,14 +382,13 @@ __global__ void __launch_bounds__(TILE, 3)
     float wv[9];
 #pragma unroll
     for (int t = 0; t < 9; ++t) wv[t] = 0.f;
-    double ez = 0.0;
     bool bad = !isfinite(U);
     const int i_caller = valid ? perm[k] : 0;
     const int nmax = __reduce_max_sync(0xffffffffu, na);
     int ent_n = na > 0 ? entry(0) : 0;
     float4 pj_n = na > 0 ? pos4[ent_n >> 5] : pi;
-    float buf[2][NLM];   // adjoint of two radial channels (see force_pair_ang_tm)
-    if (nmax > 0) tm_ld24(tb, 0, buf[0]);
+    float buf[2][8];   // two 8-column groups of the adjoint (see force_pair_ang_tm)
+    if (nmax > 0) tm_ld8(tb, buf[0]);
     for (int s = 0; s < nmax; ++s) {
         const bool act = s < na;
         const int ent = ent_n;
@@ -333,7 +401,7 @@ __global__ void __launch_bounds__(TILE, 3)
         const float4 off = s_off[ent & 31];
         float dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
         if (!act) { dx = 1.f; dy = 0.f; dz = 0.f; }   // placeholder pair, result unused
-        const float r2 = dx * dx + dy * dy + dz * dz;
+        float r2 = dx * dx + dy * dy + dz * dz;
         const bool in = act && r2 < P.rcA2;
         const float inv_r = nepm::nep_rsqrt(r2);
         const float r = r2 * inv_r;
@@ -342,34 +410,7 @@ __global__ void __launch_bounds__(TILE, 3)
                           fx, fy, fz);
         if (in) {
             bad |= !isfinite(fx + fy + fz);
-            long long cx = A_::conv(fx), cy = A_::conv(fy), cz = A_::conv(fz);
-            if (r < P.zbl_r2) {
-                const int j_caller = perm[m];
-                double d64[3];
-                for (int c = 0; c < 3; ++c) {
-                    double t = x64[c * g.n + j_caller] - x64[c * g.n + i_caller];
-                    if (!g.tric && g.pbc[c]) t -= g.L[c] * rint(t * g.invL[c]);
-                    d64[c] = t;
-                }
-                if (g.tric) min_image_tric(g, d64);
-                const double r64 = sqrt(d64[0] * d64[0] + d64[1] * d64[1] + d64[2] * d64[2]);
-                if (r64 < P.zbl_rr2) {
-                    double Uz, dUz;
-                    zbl_pair(r64, P.zbl_k, P.zbl_inv_a, P.zbl_r1, P.zbl_rr2, Uz, dUz);
-                    ez += 0.5 * Uz;
-                    const double c = 0.5 * dUz / r64;
-                    const double f3[3] = {c * d64[0], c * d64[1], c * d64[2]};
-                    cx += A_::convd(f3[0]);
-                    cy += A_::convd(f3[1]);
-                    cz += A_::convd(f3[2]);
-                    bad |= !isfinite(c);
-                    for (int a1 = 0; a1 < 3; ++a1)
-                        for (int b1 = 0; b1 < 3; ++b1)
-                            atomicAdd(reinterpret_cast<unsigned long long*>(&s_wz[3 * a1 + b1]),
-                                      static_cast<unsigned long long>(
-                                          A_::convd(-f3[a1] * d64[b1])));
-                }
-            }
+            const long long cx = A_::conv(fx), cy = A_::conv(fy), cz = A_::conv(fz);
             fi[0] += cx; fi[1] += cy; fi[2] += cz;
             A_::add(&facc[m], -cx);
             A_::add(&facc[ld + m], -cy);
@@ -384,13 +425,12 @@ __global__ void __launch_bounds__(TILE, 3)
         A_::add(&facc[k], fi[0]);
         A_::add(&facc[ld + k], fi[1]);
         A_::add(&facc[2 * ld + k], fi[2]);
-        e_site = (double)U + ez;
+        e_site = (double)U;
         if (site_energy) site_energy[i_caller] = e_site;
         if (bad) atomicOr(status, ST_NONFINITE);
     }
 
-    // block partials (fixed order): energy and NEP virial by shuffles, the
-    // ZBL virial from its fixed-point block sum
+    // block partials (fixed order): energy and virial by shuffles
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e_site += __shfl_xor_sync(0xffffffffu, e_site, o);
 #pragma unroll
@@ -408,7 +448,6 @@ __global__ void __launch_bounds__(TILE, 3)
         double sum = 0.0;
 #pragma unroll
         for (int wi = 0; wi < TILE / 32; ++wi) sum += s_red[wi][threadIdx.x];
-        if (threadIdx.x > 0) sum += A_::value(s_wz[threadIdx.x - 1]);
         partials[(size_t)blockIdx.x * NPART + threadIdx.x] = sum;
     }
     if (warp == 0) {

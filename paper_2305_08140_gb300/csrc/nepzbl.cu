@@ -121,6 +121,8 @@ struct nep_ctx {
     int radial_q_fused = 0;          // last evaluation summed q in the neighbour kernel
     int ang_tmem = 0;                // last evaluation ran the Tensor-Memory angular kernel
     int ang_dispatch = 0;            // last evaluation launched both angular kernels
+    int tm_dyn = -1;                 // k_nep_ang_tm dynamic shared memory (-1: not set)
+    int tm_blocks = 0;               // its resident blocks per SM
     // Nose-Hoover chain thermostat on a group, Berendsen barostat (MD)
     int nhc_on = 0;
     NhcParams nhc_p;
@@ -134,6 +136,10 @@ struct nep_ctx {
     double* pka_part = nullptr;           // [2 * blocks] nearest-atom search
     long long* pka_atom = nullptr;
     size_t pka_cap = 0;
+    // neighbour search tiling (orthorhombic cells): z slices per cell and
+    // candidates per unrolled chunk
+    int nbr_zs = 1;
+    int nbr_chw = 16;
     // Verlet skin for MD (0: rebuild every step)
     double skin = 0.0;
     double* xref = nullptr;          // positions at the last list build (3 x ld)
@@ -173,6 +179,7 @@ struct nep_ctx {
     int b_bt = 128;          // threads per CTA
     int b_per_sm = 0;        // CTAs per SM (0: as many as fit)
     int b_tuned = 0;
+    nep_tune_table b_table{};   // the last batched autotune
 };
 
 static int fail(nep_ctx* c, int code, const char* fmt, ...)
@@ -274,8 +281,8 @@ static int ensure_cells(nep_ctx* ctx, int ncell)
 {
     if (ncell <= ctx->ccap) return NEP_OK;
     int cap = ncell + ncell / 8 + 64;
-    if ((cap + SCAN_B - 1) / SCAN_B > SCAN_B)
-        return fail(ctx, NEP_ERR_BOX, "cell grid too large (%d cells)", ncell);
+    if (ncell > (1 << 27))
+        return fail(ctx, NEP_ERR_BOX, "cell grid too large (%d sub-cells)", ncell);
     cudaDeviceSynchronize();
     drop_graphs(ctx);
     free_dev(ctx->count); free_dev(ctx->start); free_dev(ctx->scan_sums);
@@ -341,7 +348,14 @@ static int make_grid(nep_ctx* ctx, int64_t n, const double box[9], const int32_t
     }
     g.n = (int)n;
     g.ntypes = ctx->ntypes;
+    g.zs = g.tric ? 1 : ctx->nbr_zs;
     return NEP_OK;
+}
+
+// Sub-cells of a grid (cells x z slices): the length of count[] and start[].
+static int sub_cells(const Grid& g)
+{
+    return g.nc[0] * g.nc[1] * g.nc[2] * (g.zs > 1 ? g.zs : 1);
 }
 
 static int check_device_ptr(nep_ctx* ctx, const void* p, const char* what)
@@ -358,6 +372,50 @@ static int check_device_ptr(nep_ctx* ctx, const void* p, const char* what)
     return NEP_OK;
 }
 
+// Dynamic shared memory of k_nep_ang_tm, set once per context: at least what
+// the kernel uses, padded until no more than TM_BLOCKS_PER_SM blocks can be
+// resident on an SM (each holds TM_COLS of the 512 Tensor Memory columns, so
+// a further block's allocation would wait for one of them to finish).
+// Returns 0 (and the register kernel takes every evaluation) when the kernel
+// cannot be made resident that way.
+static int tmem_dyn_bytes(nep_ctx* ctx)
+{
+    if (ctx->tm_dyn >= 0) return ctx->tm_dyn;
+    ctx->tm_dyn = 0;
+    int dev_max = 0;
+    if (cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_nep_ang_tm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             dev_max - 8192) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    for (size_t dyn = TM_DYN_MIN; dyn + 8192 <= (size_t)dev_max; dyn += 4096) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_nep_ang_tm, TILE, dyn) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        if (nb < 1) return 0;
+        if (nb <= TM_BLOCKS_PER_SM) {
+            ctx->tm_dyn = (int)dyn;
+            ctx->tm_blocks = nb;
+            return ctx->tm_dyn;
+        }
+    }
+    return 0;
+}
+
+// The orthorhombic neighbour-search kernel for a chunk width (4, 8, 16).
+template <typename R>
+static auto neighbor_kernel(bool fuse_q, int chw)
+{
+    if (chw == 4) return fuse_q ? k_neighbors<R, true, false, true, 4> : k_neighbors<R, false, false, true, 4>;
+    if (chw == 16) return fuse_q ? k_neighbors<R, true, false, true, 16> : k_neighbors<R, false, false, true, 16>;
+    return fuse_q ? k_neighbors<R, true, false, true, 8> : k_neighbors<R, false, false, true, 8>;
+}
+
 // Launches one force evaluation on stream s (no synchronisation).
 // Kernels: bin count, 3-kernel scan, scatter, cell finalize, neighbours,
 // force kernel, forces out, reduction.
@@ -371,6 +429,7 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     g.M = ctx->M;
     const int n = g.n;
     const int ncell = g.nc[0] * g.nc[1] * g.nc[2];
+    const int nsub = sub_cells(g);   // cells x z slices (count[], start[])
     const Model<R>* Pp;
     if constexpr (sizeof(R) == 4) Pp = &ctx->mf;
     else Pp = &ctx->md;
@@ -385,23 +444,23 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
         // rebuild only when an atom moved more than skin/2 since the last build
         k_skin_check<<<nb, tb, 0, s>>>(g, x, ctx->xref, 0.25 * sk * sk, gate);
         count_launch(ctx);
-        const int np = std::max(ncell + 1, 3 * n);
-        k_skin_rebuild_prep<<<(np + tb - 1) / tb, tb, 0, s>>>(ctx->count, ncell, x, ctx->xref,
+        const int np = std::max(nsub + 1, 3 * n);
+        k_skin_rebuild_prep<<<(np + tb - 1) / tb, tb, 0, s>>>(ctx->count, nsub, x, ctx->xref,
                                                              3 * n, gate, ctx->nrebuild);
         count_launch(ctx);
     } else {
-        CK(cudaMemsetAsync(ctx->count, 0, sizeof(int) * (size_t)(ncell + 1), s));
+        CK(cudaMemsetAsync(ctx->count, 0, sizeof(int) * (size_t)(nsub + 1), s));
         CK(cudaMemsetAsync(ctx->pairs, 0, sizeof(unsigned long long) * 2, s));
     }
     k_bin_count<R><<<nb, tb, 0, s>>>(g, x, ctx->cell_of, ctx->slot_of, ctx->count, ctx->status, gate,
                                      (typename V4<R>::T*)ctx->rel4);
     count_launch(ctx);
-    const int sb = (ncell + SCAN_B - 1) / SCAN_B;
-    k_scan_blocks<<<sb, SCAN_T, 0, s>>>(ctx->count, ncell, ctx->start, ctx->scan_sums, gate);
+    const int sb = (nsub + SCAN_B - 1) / SCAN_B;
+    k_scan_blocks<<<sb, SCAN_T, 0, s>>>(ctx->count, nsub, ctx->start, ctx->scan_sums, gate);
     count_launch(ctx);
-    k_scan_sums<<<1, SCAN_T, 0, s>>>(ctx->scan_sums, sb, ctx->start, ncell, gate);
+    k_scan_sums<<<1, SCAN_T, 0, s>>>(ctx->scan_sums, sb, ctx->start, nsub, gate);
     count_launch(ctx);
-    k_scan_add<<<(ncell + tb - 1) / tb, tb, 0, s>>>(ctx->start, ncell, ctx->scan_sums, gate);
+    k_scan_add<<<(nsub + tb - 1) / tb, tb, 0, s>>>(ctx->start, nsub, ctx->scan_sums, gate);
     count_launch(ctx);
     k_bin_scatter<<<nb, tb, 0, s>>>(n, ctx->cell_of, ctx->slot_of, ctx->start, ctx->perm, gate);
     count_launch(ctx);
@@ -420,15 +479,15 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     rq.inv_rcR = P.inv_rcR;
     for (int t = 0; t < NR * KR; ++t) rq.hR[t] = P.hR[t];
     for (int t = 0; t < NR; ++t) rq.CR[t] = P.CR[t];
+    rq.close2 = P.zbl_r2 * P.zbl_r2;
     // chunked candidate tests (pos4 holds NB_CHUNK - 1 readable entries past
     // the last atom, see ensure_atoms)
     auto kn = g.tric ? (fuse_q ? k_neighbors<R, true, true, true> : k_neighbors<R, false, true, true>)
-                     : (fuse_q ? k_neighbors<R, true, false, true>
-                               : k_neighbors<R, false, false, true>);
+                     : neighbor_kernel<R>(fuse_q, ctx->nbr_chw);
     kn<<<(n + 127) / 128, 128, 0, s>>>(
         g, (R)(rl * rl), (R)(ra * ra), (const typename V4<R>::T*)ctx->pos4, ctx->cell_sorted,
         ctx->start, ctx->nbr, ctx->cnt, ctx->status, ctx->status + 1, ctx->pairs, gate, rq,
-        (R*)ctx->qr);
+        (R*)ctx->qr, ctx->perm, x);
     count_launch(ctx);
     ctx->radial_q_fused = fuse_q ? 1 : 0;
     if (gate) {
@@ -459,7 +518,7 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     if (!fuse_q) {
         (ms ? k_radial_q<R, true> : k_radial_q<R, false>)<<<(n + 127) / 128, 128, 0, s>>>(
             P, g, p4, ctx->nbr, ctx->cnt, (R*)ctx->qr, gate ? ctx->nbr_act : nullptr,
-            gate ? ctx->cnt_act : nullptr, coef);
+            gate ? ctx->cnt_act : nullptr, coef, ctx->perm, x, ctx->status);
         count_launch(ctx);
     }
     // angular part, network, ZBL (the block's angular entries staged in shared
@@ -476,12 +535,12 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
         ctx->nep_smem_set[ks] = 1;
     }
     // status[2]: the largest angular neighbour count of this evaluation
-    const bool dispatch = sizeof(R) == 4 && !ms && USE_TMEM_ANG;
+    const bool dispatch = sizeof(R) == 4 && !ms && USE_TMEM_ANG && tmem_dyn_bytes(ctx) > 0;
     ctx->ang_dispatch = dispatch ? 1 : 0;
     if constexpr (sizeof(R) == 4) {
         if (dispatch) {
             // one species, FP32: the angular state in Tensor Memory
-            k_nep_ang_tm<<<tiles, TILE, stage_bytes, s>>>(
+            k_nep_ang_tm<<<tiles, TILE, (size_t)tmem_dyn_bytes(ctx), s>>>(
                 P, g, p4, lnbr, lcnt, ctx->perm, x, (const float*)ctx->qr, (float4*)ctx->br, fa,
                 ctx->partials, site_energy, ctx->status, stage_slots, ctx->status + 2,
                 TMEM_MAX_ANG);
@@ -493,11 +552,24 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
                                           site_energy, ctx->status, stage_slots, coef,
                                           dispatch ? ctx->status + 2 : nullptr, TMEM_MAX_ANG);
     count_launch(ctx);
-    // radial pair forces (all pairs, small state)
-    (ms ? k_radial_force<R, true> : k_radial_force<R, false>)<<<tiles, TILE, 0, s>>>(
-        P, g, p4, lnbr, lcnt, (const typename V4<R>::T*)ctx->br, fa,
-        ctx->partials + (size_t)tiles * NPART, ctx->status);
-    count_launch(ctx);
+    // radial pair forces (all pairs, small state); FP32 one species: the
+    // variant without the close-pair branch unless the evaluation has a pair
+    // inside the outer ZBL radius (both launched, each returns unless chosen)
+    if (sizeof(R) == 4 && !ms) {
+        k_radial_force<R, false, false><<<tiles, TILE, 0, s>>>(
+            P, g, p4, lnbr, lcnt, (const typename V4<R>::T*)ctx->br, fa,
+            ctx->partials + (size_t)tiles * NPART, ctx->status, ctx->perm, x, true);
+        count_launch(ctx);
+        k_radial_force<R, false, true><<<tiles, TILE, 0, s>>>(
+            P, g, p4, lnbr, lcnt, (const typename V4<R>::T*)ctx->br, fa,
+            ctx->partials + (size_t)tiles * NPART, ctx->status, ctx->perm, x, true);
+        count_launch(ctx);
+    } else {
+        (ms ? k_radial_force<R, true> : k_radial_force<R, false>)<<<tiles, TILE, 0, s>>>(
+            P, g, p4, lnbr, lcnt, (const typename V4<R>::T*)ctx->br, fa,
+            ctx->partials + (size_t)tiles * NPART, ctx->status, ctx->perm, x, false);
+        count_launch(ctx);
+    }
     if (timed_slot >= 0) {
         if (ctx->capturing)
             CK(cudaEventRecordWithFlags(ctx->events[2 * timed_slot + 1], s, cudaEventRecordExternal));
@@ -562,7 +634,8 @@ static int readback(nep_ctx* ctx, cudaStream_t s)
     CK(cudaStreamSynchronize(s));
     ctx->last_max_total = ctx->h_status[1];
     ctx->last_max_ang = ctx->h_status[2];
-    ctx->ang_tmem = ctx->ang_dispatch && ctx->h_status[2] <= TMEM_MAX_ANG ? 1 : 0;
+    ctx->ang_tmem = ctx->ang_dispatch && ctx->h_status[2] <= TMEM_MAX_ANG &&
+                    !(ctx->h_status[0] & ST_CLOSE) ? 1 : 0;
     ctx->last_pairs_r = (long long)ctx->h_pairs[0];
     ctx->last_pairs_a = (long long)ctx->h_pairs[1];
     return NEP_OK;
@@ -846,6 +919,18 @@ int nep_set_option(nep_ctx* ctx, int option, int64_t value)
             return ensure_atoms(ctx, ld, M);
         }
         return NEP_OK;
+    case NEP_OPT_NBR_SLICES:
+        if (value != 1 && value != 2 && value != 4 && value != 8)
+            return fail(ctx, NEP_ERR_INVALID_ARG, "z slices per cell must be 1, 2, 4 or 8");
+        ctx->nbr_zs = (int)value;
+        drop_graphs(ctx);
+        return NEP_OK;
+    case NEP_OPT_NBR_CHUNK:
+        if (value != 4 && value != 8 && value != 16)
+            return fail(ctx, NEP_ERR_INVALID_ARG, "candidate chunk must be 4, 8 or 16");
+        ctx->nbr_chw = (int)value;
+        drop_graphs(ctx);
+        return NEP_OK;
     case NEP_OPT_NBR_CAPACITY:
         if (value < 1 || value > 1000000) return fail(ctx, NEP_ERR_INVALID_ARG, "bad capacity");
         if (ctx->ld > 0) {
@@ -877,6 +962,9 @@ int nep_get_stats(const nep_ctx* ctx, nep_stats* out)
     out->list_builds_skin = (int64_t)nb;
     out->radial_q_in_neighbor_kernel = ctx->radial_q_fused;
     out->angular_state_in_tmem = ctx->ang_tmem;
+    out->angular_tmem_blocks_per_sm = ctx->tm_blocks;
+    out->nbr_z_slices = ctx->nbr_zs;
+    out->nbr_chunk = ctx->nbr_chw;
     return NEP_OK;
 }
 
@@ -893,8 +981,7 @@ int nep_reset_stats(nep_ctx* ctx)
 static int compute_with_retry(nep_ctx* ctx, const Grid& g, const double* x, const int32_t* types,
                               double* F, double* site_energy, cudaStream_t s)
 {
-    const int ncell = g.nc[0] * g.nc[1] * g.nc[2];
-    int rc = ensure_cells(ctx, ncell);
+    int rc = ensure_cells(ctx, sub_cells(g));
     if (rc) return rc;
     int M = ctx->M > 0 ? ctx->M : 96;
     for (int attempt = 0; attempt < 4; ++attempt) {
@@ -1070,7 +1157,7 @@ static int md_steps_barostat(nep_ctx* ctx, nep_md_state* st, int n_steps, cudaSt
         Grid g;
         int rc = make_grid(ctx, n, st->box, st->pbc, g);
         if (rc) return rc;
-        if ((rc = ensure_cells(ctx, g.nc[0] * g.nc[1] * g.nc[2]))) return rc;
+        if ((rc = ensure_cells(ctx, sub_cells(g)))) return rc;
         if ((rc = ensure_atoms(ctx, (int)n, ctx->M > 0 ? ctx->M : 96))) return rc;
         CK(cudaMemcpyAsync(ctx->backup, st->xyz, bytes, cudaMemcpyDeviceToDevice, s));
         CK(cudaMemcpyAsync(ctx->backup + 3 * n, st->vel, bytes, cudaMemcpyDeviceToDevice, s));
@@ -1152,7 +1239,7 @@ int md_step(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
         for (int t = 0; t < 9; ++t) st->virial[t] = ctx->h_result[1 + t];
     }
     {
-        int rc2 = ensure_cells(ctx, g.nc[0] * g.nc[1] * g.nc[2]);
+        int rc2 = ensure_cells(ctx, sub_cells(g));
         if (rc2) return rc2;
         int need = ctx->M > 0 ? ctx->M : 96;
         if (ctx->last_max_total > 0) {
@@ -1272,6 +1359,27 @@ int md_step(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
     return NEP_OK;
 }
 
+}  // extern "C"
+
+// Device mirror of an MD state (x, v, F, species) owned by the context: the
+// device side of md_step_host and the scratch state of nep_md_autotune.
+static int ensure_mirror(nep_ctx* ctx, int64_t n)
+{
+    if (n <= ctx->hm_cap) return NEP_OK;
+    cudaDeviceSynchronize();
+    drop_graphs(ctx);   // graphs hold the old mirror's addresses
+    free_dev(ctx->hm_x); free_dev(ctx->hm_v); free_dev(ctx->hm_f); free_dev(ctx->hm_t);
+    ctx->hm_cap = 0;
+    CK(cudaMalloc(&ctx->hm_x, sizeof(double) * 3 * (size_t)n));
+    CK(cudaMalloc(&ctx->hm_v, sizeof(double) * 3 * (size_t)n));
+    CK(cudaMalloc(&ctx->hm_f, sizeof(double) * 3 * (size_t)n));
+    CK(cudaMalloc(&ctx->hm_t, sizeof(int32_t) * (size_t)n));
+    ctx->hm_cap = n;
+    return NEP_OK;
+}
+
+extern "C" {
+
 int md_step_host(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
 {
     if (!ctx) return NEP_ERR_INVALID_ARG;
@@ -1292,17 +1400,8 @@ int md_step_host(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
                         "device arrays)", names[t]);
         }
     }
-    if (n > ctx->hm_cap) {
-        cudaDeviceSynchronize();
-        drop_graphs(ctx);   // graphs hold the old mirror's addresses
-        free_dev(ctx->hm_x); free_dev(ctx->hm_v); free_dev(ctx->hm_f); free_dev(ctx->hm_t);
-        ctx->hm_cap = 0;
-        CK(cudaMalloc(&ctx->hm_x, sizeof(double) * 3 * (size_t)n));
-        CK(cudaMalloc(&ctx->hm_v, sizeof(double) * 3 * (size_t)n));
-        CK(cudaMalloc(&ctx->hm_f, sizeof(double) * 3 * (size_t)n));
-        CK(cudaMalloc(&ctx->hm_t, sizeof(int32_t) * (size_t)n));
-        ctx->hm_cap = n;
-    }
+    int rc0 = ensure_mirror(ctx, n);
+    if (rc0) return rc0;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t b3 = sizeof(double) * 3 * (size_t)n;
     CK(cudaMemcpyAsync(ctx->hm_x, st->xyz, b3, cudaMemcpyHostToDevice, s));
@@ -1327,6 +1426,120 @@ int md_step_host(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
     d.types = st->types;
     *st = d;
     return NEP_OK;
+}
+
+// Median of a few timings.
+static double median_ms(std::vector<float> t)
+{
+    std::sort(t.begin(), t.end());
+    const size_t m = t.size();
+    return m == 0 ? 0.0 : (m % 2 ? t[m / 2] : 0.5 * ((double)t[m / 2 - 1] + t[m / 2]));
+}
+
+int nep_md_autotune(nep_ctx* ctx, const nep_md_state* st, int reps, void* stream,
+                    nep_tune_table* tiling, nep_tune_table* chunk)
+{
+    if (!ctx) return NEP_ERR_INVALID_ARG;
+    if (!st) return fail(ctx, NEP_ERR_INVALID_ARG, "NULL state");
+    const int64_t n = st->n_atoms;
+    if (n <= 0 || n >= (1 << 26)) return fail(ctx, NEP_ERR_INVALID_ARG, "n_atoms must be in [1, 2^26)");
+    if (reps < 1 || reps > 50) return fail(ctx, NEP_ERR_INVALID_ARG, "reps must be in [1, 50]");
+    int rc;
+    if ((rc = check_device_ptr(ctx, st->xyz, "xyz")) || (rc = check_device_ptr(ctx, st->vel, "vel")) ||
+        (rc = check_device_ptr(ctx, st->forces, "forces")) ||
+        (rc = check_device_ptr(ctx, st->types, "types")))
+        return rc;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = ensure_mirror(ctx, n))) return rc;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    nep_tune_table tt;
+    memset(&tt, 0, sizeof(tt));
+    // 1. neighbour-search tiling: force evaluations of the state's positions
+    //    (forces into the context's scratch state)
+    const int zss[4] = {1, 2, 4, 8}, chws[3] = {4, 8, 16};
+    const int zs0 = ctx->nbr_zs, chw0 = ctx->nbr_chw;
+    double best = 1e300;
+    int bz = zs0, bc = chw0;
+    for (int a = 0; a < 4 && !rc; ++a)
+        for (int b = 0; b < 3 && !rc; ++b) {
+            ctx->nbr_zs = zss[a];
+            ctx->nbr_chw = chws[b];
+            Grid g;
+            if ((rc = make_grid(ctx, n, st->box, st->pbc, g))) break;
+            if (g.tric && (a > 0 || b != 2)) continue;   // triclinic: one kernel
+            if ((rc = compute_with_retry(ctx, g, st->xyz, st->types, ctx->hm_f, nullptr, s))) break;
+            std::vector<float> t;
+            for (int r = 0; r < reps && !rc; ++r) {
+                CK(cudaEventRecord(e0, s));
+                rc = eval(ctx, g, st->xyz, st->types, ctx->hm_f, nullptr, s, -1);
+                CK(cudaEventRecord(e1, s));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                t.push_back(ms);
+            }
+            if (rc) break;
+            CK(cudaStreamSynchronize(s));
+            CK(cudaMemcpy(ctx->h_status, ctx->status, sizeof(int), cudaMemcpyDeviceToHost));
+            if (ctx->h_status[0] & ST_OVERFLOW) continue;   // capacity grew meanwhile
+            const double m = median_ms(t);
+            if (tt.n < 32) {
+                tt.a[tt.n] = zss[a]; tt.b[tt.n] = chws[b]; tt.ms[tt.n] = m;
+                if (m < best) { best = m; bz = zss[a]; bc = chws[b]; tt.best = tt.n; }
+                ++tt.n;
+            }
+        }
+    ctx->nbr_zs = rc ? zs0 : bz;
+    ctx->nbr_chw = rc ? chw0 : bc;
+    drop_graphs(ctx);
+    if (tiling) *tiling = tt;
+    // 2. steps per captured graph: 50 MD steps of a copy of the state for
+    //    each candidate (NVE only: a thermostat or barostat keeps its state in
+    //    the context, which trial steps would advance)
+    nep_tune_table tc;
+    memset(&tc, 0, sizeof(tc));
+    if (!rc && !ctx->nhc_on && !ctx->baro_on) {
+        const int chunks[3] = {10, 25, 50};
+        const int chunk0 = ctx->chunk;
+        const size_t b3 = sizeof(double) * 3 * (size_t)n;
+        double bestc = 1e300;
+        int bch = chunk0;
+        for (int c = 0; c < 3 && !rc; ++c) {
+            ctx->chunk = chunks[c];
+            nep_md_state d = *st;
+            d.xyz = ctx->hm_x; d.vel = ctx->hm_v; d.forces = ctx->hm_f; d.types = ctx->hm_t;
+            std::vector<float> t;
+            for (int r = 0; r <= reps && !rc; ++r) {   // r = 0: capture (not timed)
+                CK(cudaMemcpyAsync(ctx->hm_x, st->xyz, b3, cudaMemcpyDeviceToDevice, s));
+                CK(cudaMemcpyAsync(ctx->hm_v, st->vel, b3, cudaMemcpyDeviceToDevice, s));
+                CK(cudaMemcpyAsync(ctx->hm_f, st->forces, b3, cudaMemcpyDeviceToDevice, s));
+                CK(cudaMemcpyAsync(ctx->hm_t, st->types, sizeof(int32_t) * (size_t)n,
+                                   cudaMemcpyDeviceToDevice, s));
+                nep_md_state d2 = d;
+                CK(cudaEventRecord(e0, s));
+                rc = md_step(ctx, &d2, 50, stream);
+                CK(cudaEventRecord(e1, s));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (r > 0) t.push_back(ms / 50.0f);
+            }
+            if (rc) break;
+            const double m = median_ms(t);
+            tc.a[tc.n] = chunks[c]; tc.b[tc.n] = 0; tc.ms[tc.n] = m;
+            if (m < bestc) { bestc = m; bch = chunks[c]; tc.best = tc.n; }
+            ++tc.n;
+        }
+        ctx->chunk = rc ? chunk0 : bch;
+        drop_graphs(ctx);
+    }
+    if (chunk) *chunk = tc;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
 }
 
 }  // extern "C"
@@ -1613,12 +1826,14 @@ int nep_batch_autotune(nep_ctx* ctx, const nep_batch* batch, const nep_targets* 
     CK(cudaMalloc(&grad, sizeof(double) * n_params_for(ctx->ntypes)));
     const int bts[3] = {64, 128, 256};
     const int nbt = ctx->precision == NEP_FP32 ? 3 : 1;
-    float best = 1e30f;
+    double best = 1e300;
     int bb = ctx->b_bt, bs = ctx->b_per_sm;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     int rc = NEP_OK;
+    nep_tune_table tab;
+    memset(&tab, 0, sizeof(tab));
     for (int a = 0; a < nbt && !rc; ++a) {
         for (int per = 1; per <= 4 && !rc; per *= 2) {
             ctx->b_bt = ctx->precision == NEP_FP32 ? bts[a] : 128;
@@ -1627,15 +1842,27 @@ int nep_batch_autotune(nep_ctx* ctx, const nep_batch* batch, const nep_targets* 
             rc = nep_batch_loss_grad(ctx, batch, t, w, L, grad, nullptr, nullptr, nullptr,
                                      stream);   // warm-up
             if (rc) break;
-            cudaEventRecord(e0, s);
-            rc = nep_batch_loss_grad(ctx, batch, t, w, L, grad, nullptr, nullptr, nullptr, stream);
-            cudaEventRecord(e1, s);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (!rc && ms < best) { best = ms; bb = ctx->b_bt; bs = per; }
+            // median of three launches (one launch alone is too noisy to rank
+            // candidates a few per cent apart)
+            std::vector<float> tm;
+            for (int r = 0; r < 3 && !rc; ++r) {
+                cudaEventRecord(e0, s);
+                rc = nep_batch_loss_grad(ctx, batch, t, w, L, grad, nullptr, nullptr, nullptr,
+                                         stream);
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                tm.push_back(ms);
+            }
+            if (rc) break;
+            const double m = median_ms(tm);
+            tab.a[tab.n] = ctx->b_bt; tab.b[tab.n] = per; tab.ms[tab.n] = m;
+            if (m < best) { best = m; bb = ctx->b_bt; bs = per; tab.best = tab.n; }
+            ++tab.n;
         }
     }
+    ctx->b_table = tab;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(grad);
@@ -1645,6 +1872,13 @@ int nep_batch_autotune(nep_ctx* ctx, const nep_batch* batch, const nep_targets* 
     if (best_threads) *best_threads = bb;
     if (best_per_sm) *best_per_sm = bs;
     return rc;
+}
+
+int nep_batch_autotune_table(const nep_ctx* ctx, nep_tune_table* out)
+{
+    if (!ctx || !out) return NEP_ERR_INVALID_ARG;
+    *out = ctx->b_table;
+    return NEP_OK;
 }
 
 
@@ -1879,17 +2113,26 @@ extern "C" int nep_compute_static(const nep_params* p, int64_t n_atoms, const do
     g.ld = ST_MAX_ATOMS;
     g.M = ST_SLOTS;
     g.ntypes = 1;
+    g.zs = 1;
     if (n == 0) {
         *energy = 0.0;
         if (virial) for (int t = 0; t < 9; ++t) virial[t] = 0.0;
         return NEP_OK;
     }
-    for (const void* q : {(const void*)xyz, (const void*)types, (const void*)forces}) {
+    // site_energy is optional; when given, the kernels store to it, so it is
+    // checked like the required arrays
+    const void* dev_args[4] = {xyz, types, forces, site_energy};
+    const char* dev_names[4] = {"xyz", "types", "forces", "site_energy"};
+    for (int a = 0; a < 4; ++a) {
+        const void* q = dev_args[a];
+        if (a == 3 && !q) continue;
         cudaPointerAttributes at;
         if (!q || cudaPointerGetAttributes(&at, q) != cudaSuccess ||
             (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
             cudaGetLastError();
-            return fail(nullptr, NEP_ERR_INVALID_ARG, "inputs and outputs must be device memory");
+            return fail(nullptr, NEP_ERR_INVALID_ARG,
+                        "%s must be device memory (inputs and outputs are device arrays)",
+                        dev_names[a]);
         }
     }
     unsigned char* base = nullptr;
@@ -1932,7 +2175,7 @@ extern "C" int nep_compute_static(const nep_params* p, int64_t n_atoms, const do
     k_neighbors<float, false><<<(n + 127) / 128, 128, 0, s>>>(g, P.rcR2, P.rcA2, pos4, cell_sorted,
                                                              start, nbr, cnt, status, status + 1,
                                                              pairs, nullptr, RadCoef<float>{},
-                                                             nullptr);
+                                                             nullptr, perm, xyz);
     const int tiles = (n + TILE - 1) / TILE;
     k_nep<float><<<tiles, TILE, 0, s>>>(P, g, pos4, nbr, cnt, perm, xyz, facc, partials,
                                         site_energy, status, 0);

@@ -28,12 +28,15 @@ NEP_OPT_TIMING = 1
 NEP_OPT_GRAPH_CHUNK = 2
 NEP_OPT_NBR_CAPACITY = 3
 NEP_OPT_SKIN_MILLIANGSTROM = 4
+NEP_OPT_NBR_SLICES = 5
+NEP_OPT_NBR_CHUNK = 6
 
 EXPORTED = ("nep_init", "nep_free", "nep_last_error", "nep_compute", "md_step", "md_step_host",
             "nep_get_stats", "nep_set_option", "nep_reset_stats", "nep_compute_static",
             "nep_set_params", "nep_batch_forward", "nep_batch_backward", "nep_batch_loss_grad",
             "nep_batch_autotune", "nep_population_loss", "nep_snes_generation",
-            "nep_set_thermostat", "nep_set_barostat", "nep_pka")
+            "nep_set_thermostat", "nep_set_barostat", "nep_pka", "nep_md_autotune",
+            "nep_batch_autotune_table")
 
 
 class NepParams(C.Structure):
@@ -66,13 +69,26 @@ class NepBarostat(C.Structure):
     _fields_ = [("pressure", C.c_double), ("tau", C.c_double), ("compressibility", C.c_double)]
 
 
+class NepTuneTable(C.Structure):
+    _fields_ = [("n", C.c_int32), ("a", C.c_int32 * 32), ("b", C.c_int32 * 32),
+                ("ms", C.c_double * 32), ("best", C.c_int32)]
+
+    def rows(self, names):
+        """[{names[0]: a, names[1]: b, "ms": ms}, ...] and the kept row."""
+        rows = [{names[0]: self.a[i], names[1]: self.b[i], "ms": self.ms[i]}
+                for i in range(self.n)]
+        return rows, (rows[self.best] if self.n else None)
+
+
 class NepStats(C.Structure):
     _fields_ = [("kernel_launches", C.c_int64), ("timed_launches", C.c_int64),
                 ("timed_ms", C.c_double), ("pairs_radial", C.c_int64),
                 ("pairs_angular", C.c_int64), ("max_nbr_radial", C.c_int32),
                 ("max_nbr_angular", C.c_int32), ("nbr_capacity", C.c_int32),
                 ("graph_chunk", C.c_int32), ("list_builds_skin", C.c_int64),
-                ("radial_q_in_neighbor_kernel", C.c_int32), ("angular_state_in_tmem", C.c_int32)]
+                ("radial_q_in_neighbor_kernel", C.c_int32), ("angular_state_in_tmem", C.c_int32),
+                ("angular_tmem_blocks_per_sm", C.c_int32), ("nbr_z_slices", C.c_int32),
+                ("nbr_chunk", C.c_int32)]
 
 
 class NepTargets(C.Structure):
@@ -125,6 +141,11 @@ def load(build: bool = True):
     L.md_step_host.restype = C.c_int
     L.nep_get_stats.argtypes = [vp, C.POINTER(NepStats)]
     L.nep_get_stats.restype = C.c_int
+    L.nep_md_autotune.argtypes = [vp, C.POINTER(NepMdState), C.c_int, vp,
+                                  C.POINTER(NepTuneTable), C.POINTER(NepTuneTable)]
+    L.nep_md_autotune.restype = C.c_int
+    L.nep_batch_autotune_table.argtypes = [vp, C.POINTER(NepTuneTable)]
+    L.nep_batch_autotune_table.restype = C.c_int
     L.nep_set_option.argtypes = [vp, C.c_int, C.c_int64]
     L.nep_set_option.restype = C.c_int
     L.nep_reset_stats.argtypes = [vp]
@@ -409,6 +430,24 @@ class NEP:
                                                 C.byref(per)))
         return bt.value, per.value
 
+    def batch_autotune_table(self):
+        """Timings of the last batch_autotune: rows (threads, ctas_per_sm, ms)
+        and the kept row."""
+        tab = NepTuneTable()
+        self._check(self.lib.nep_batch_autotune_table(self.ctx, C.byref(tab)))
+        return tab.rows(("threads", "ctas_per_sm"))
+
+    def md_autotune(self, state: "MDState", reps: int = 3, stream=None):
+        """nep_md_autotune on an MD state (read, not advanced): times every
+        neighbour-search tiling and graph chunk and keeps the fastest.  Returns
+        {"tiling": (rows, kept), "graph_chunk": (rows, kept)}."""
+        tiling, chunk = NepTuneTable(), NepTuneTable()
+        self._check(self.lib.nep_md_autotune(self.ctx, C.byref(state.c), int(reps),
+                                             _stream_ptr(stream), C.byref(tiling),
+                                             C.byref(chunk)))
+        return {"tiling": tiling.rows(("z_slices", "chunk_width")),
+                "graph_chunk": chunk.rows(("steps_per_graph", "unused"))}
+
 
 # loss weights of the paper's training (Sec. III.A)
 PAPER_WEIGHTS = {"energy": 1.0, "force": 1.0, "virial": 0.1, "l1": 0.05, "l2": 0.05}
@@ -586,20 +625,39 @@ class MDState:
         return np.array(self.c.virial[:]).reshape(3, 3)
 
 
-def save_checkpoint(path, state: "MDState", params=None):
+def model_fingerprint(model) -> bytes:
+    """SHA-256 over everything that defines the potential of a NepModel: the
+    model sizes, the species (Z and mass), the cutoffs, the ZBL switch radii,
+    the flat parameters and the descriptor scaler.  Two models with the same
+    fingerprint give the same forces."""
+    import hashlib
+    h = hashlib.sha256()
+    sizes = np.array([model.n_max_radial, model.n_max_angular, model.basis_size_radial,
+                      model.basis_size_angular, model.l_max, model.use_4body, model.n_hidden,
+                      model.n_types], dtype=np.int64)
+    h.update(b"sizes"); h.update(sizes.tobytes())
+    h.update(b"z"); h.update(np.asarray(model.zs, dtype=np.int64).tobytes())
+    h.update(b"mass"); h.update(np.asarray(model.masses, dtype=np.float64).tobytes())
+    h.update(b"radii"); h.update(np.array([model.rc_radial, model.rc_angular, model.zbl_r_inner,
+                                           model.zbl_r_outer], dtype=np.float64).tobytes())
+    h.update(b"params"); h.update(np.ascontiguousarray(model.params, dtype=np.float64).tobytes())
+    h.update(b"scaler"); h.update(np.ascontiguousarray(model.scaler, dtype=np.float64).tobytes())
+    return h.digest()
+
+
+def save_checkpoint(path, state: "MDState", model=None):
     """Writes an MD state to ``path`` (numpy .npz): positions, velocities,
     forces and species, the cell and periodic flags, dt_max and d_max, the
     accumulated time, step count and last dt, whether the forces are valid,
-    and the SHA-256 of the model parameters when ``params`` is given.  A run
-    resumed from it with ``load_checkpoint`` (NVE, no thermostat or barostat)
-    continues exactly as the uninterrupted run would have; the Nose-Hoover
-    chain and barostat settings live in the context and are not saved."""
-    import hashlib
+    and, when ``model`` (a NepModel) is given, its ``model_fingerprint``.  A
+    run resumed from it with ``load_checkpoint`` (NVE, no thermostat or
+    barostat) continues exactly as the uninterrupted run would have; the
+    Nose-Hoover chain and barostat settings live in the context and are not
+    saved."""
     c = state.c
     extra = {}
-    if params is not None:
-        extra["params_sha256"] = np.frombuffer(hashlib.sha256(
-            np.ascontiguousarray(params, dtype=np.float64).tobytes()).digest(), dtype=np.uint8)
+    if model is not None:
+        extra["model_sha256"] = np.frombuffer(model_fingerprint(model), dtype=np.uint8)
     np.savez(path, xyz=state.xyz.cpu().numpy(), vel=state.vel.cpu().numpy(),
              forces=state.forces.cpu().numpy(), types=state.types.cpu().numpy(),
              box=np.array(c.box[:]), pbc=np.array(c.pbc[:], dtype=np.int32),
@@ -607,16 +665,17 @@ def save_checkpoint(path, state: "MDState", params=None):
              counters=np.array([c.step, c.forces_valid], dtype=np.int64), **extra)
 
 
-def load_checkpoint(path, device="cuda", params=None) -> "MDState":
+def load_checkpoint(path, device="cuda", model=None) -> "MDState":
     """The MD state written by ``save_checkpoint``, on ``device``.  With
-    ``params``, their SHA-256 must match the one saved (ValueError otherwise)."""
-    import hashlib
+    ``model``, its fingerprint must match the one saved (ValueError
+    otherwise): a state saved under another potential -- other parameters,
+    scaler, cutoffs, ZBL radii, species or sizes -- would not continue the
+    saved trajectory."""
     import torch
     z = np.load(path)
-    if params is not None:
-        h = hashlib.sha256(np.ascontiguousarray(params, dtype=np.float64).tobytes()).digest()
-        if "params_sha256" not in z or bytes(z["params_sha256"]) != h:
-            raise ValueError("checkpoint was written with other model parameters")
+    if model is not None:
+        if "model_sha256" not in z or bytes(z["model_sha256"]) != model_fingerprint(model):
+            raise ValueError("checkpoint was written with another model")
     dt_max, d_max, t, dt_last = (float(v) for v in z["dt"])
     step, forces_valid = (int(v) for v in z["counters"])
     st = MDState(torch.from_numpy(z["xyz"]).to(device), torch.from_numpy(z["vel"]).to(device),

@@ -40,3 +40,15 @@ extern "C" void h_fourbody_hvp(const double* A2, const double* Ad, double* out)
     nepm::sym_anticomm<double>(T, Td, S);
     nepm::fourbody_map<double>(S, out);
 }
+
+// grouped harmonics and gradient contraction, summed over the three groups
+extern "C" void h_harmonics_groups(const double* u, const double* G, double* Y, double* v)
+{
+    nepm::harmonics_group<0, double>(u[0], u[1], u[2], Y);
+    nepm::harmonics_group<1, double>(u[0], u[1], u[2], Y + 8);
+    nepm::harmonics_group<2, double>(u[0], u[1], u[2], Y + 16);
+    v[0] = v[1] = v[2] = 0.0;
+    nepm::harmonics_grad_dot_group<0, double>(u[0], u[1], u[2], G, v[0], v[1], v[2]);
+    nepm::harmonics_grad_dot_group<1, double>(u[0], u[1], u[2], G + 8, v[0], v[1], v[2]);
+    nepm::harmonics_grad_dot_group<2, double>(u[0], u[1], u[2], G + 16, v[0], v[1], v[2]);
+}

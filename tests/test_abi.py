@@ -38,9 +38,9 @@ def test_struct_layouts_match_header():
     import tempfile
     from paper_2305_08140_gb300 import nepzbl as N
     prog = ('#include <stdio.h>\n#include "nepzbl.h"\nint main(void){printf('
-            '"%zu %zu %zu %zu %zu %zu\\n", sizeof(nep_params), sizeof(nep_md_state), '
+            '"%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(nep_params), sizeof(nep_md_state), '
             'sizeof(nep_stats), sizeof(nep_batch), sizeof(nep_targets), '
-            'sizeof(nep_loss_weights));return 0;}\n')
+            'sizeof(nep_loss_weights), sizeof(nep_tune_table));return 0;}\n')
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "t.c")
         exe = os.path.join(d, "t")
@@ -48,7 +48,8 @@ def test_struct_layouts_match_header():
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", exe, c])
         sizes = [int(v) for v in subprocess.check_output([exe]).split()]
     assert sizes == [C.sizeof(N.NepParams), C.sizeof(N.NepMdState), C.sizeof(N.NepStats),
-                     C.sizeof(N.NepBatch), C.sizeof(N.NepTargets), C.sizeof(N.NepLossWeights)]
+                     C.sizeof(N.NepBatch), C.sizeof(N.NepTargets), C.sizeof(N.NepLossWeights),
+                     C.sizeof(N.NepTuneTable)]
 
 
 def test_init_without_gpu_fails_cleanly():

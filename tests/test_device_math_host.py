@@ -142,3 +142,24 @@ def test_fourbody_hessian_vector_product(lib):
     lib.h_fourbody(_p(A2 + h * Ad), _p(gp))
     lib.h_fourbody(_p(A2 - h * Ad), _p(gm))
     np.testing.assert_allclose(out, (gp - gm) / (2 * h), rtol=1e-7, atol=1e-9)
+
+
+def test_grouped_harmonics_equal_the_full_forms(lib):
+    """The three 8-index groups of harmonics and of the gradient contraction
+    (used when coefficients stream in group by group) give exactly the full
+    harmonics and the full contraction, and the contraction is the gradient
+    of sum_lm G_lm R_lm (central differences)."""
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        u = rng.normal(size=3)
+        G = rng.normal(size=24)
+        Yg, vg = np.zeros(24), np.zeros(3)
+        lib.h_harmonics_groups(_p(u), _p(G), _p(Yg), _p(vg))
+        np.testing.assert_allclose(Yg, Y(lib, u), rtol=1e-14, atol=1e-14)
+        v = np.zeros(3)
+        lib.h_harmonics_grad_dot(*[float(t) for t in u], _p(G), _p(v))
+        np.testing.assert_allclose(vg, v, rtol=1e-13, atol=1e-13)
+        h = 1e-6
+        fd = np.array([(G @ Y(lib, u + h * e) - G @ Y(lib, u - h * e)) / (2 * h)
+                       for e in np.eye(3)])
+        np.testing.assert_allclose(vg, fd, rtol=1e-7, atol=1e-7)

@@ -65,19 +65,31 @@ def _small_configs(k, seed=4):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_batch_forward_matches_oracle(precision):
-    structs = I.c4(24)
+def test_batch_forward_matches_oracle_all_512(precision):
+    """The full 512-configuration batch (~116k atoms, one persistent launch):
+    every configuration's energy and virial and every atom's force against the
+    oracle, element by element."""
+    structs = I.c4()
+    assert len(structs) == 512
     nep, b = _gpu(structs, precision)
-    E, F = nep.batch_forward(b)
+    E, F, W = nep.batch_forward(b, virials=True)
     E = E.cpu().numpy()
     F = F.cpu().numpy().T
-    Eo, Fo = _oracle_EF(I.nep_model(1), structs)
+    W = W.cpu().numpy()
     tf = 1e-4 if precision == "fp32" else 1e-9
     te = 1e-6 if precision == "fp32" else 1e-11
+    tw = 2e-5 if precision == "fp32" else 1e-10
+    worst = [0.0, 0.0, 0.0]
     for c, s in enumerate(structs):
+        Eo, Fo, Wo, _ = O.energy_forces_virial(I.nep_model(1), s.pos, s.box, s.pbc)
         a, z = b.offsets[c], b.offsets[c + 1]
-        assert abs(E[c] - Eo[c]) / s.n <= te, (c, E[c], Eo[c])
-        assert np.max(np.abs(F[a:z] - Fo[c])) <= tf, (c, np.max(np.abs(F[a:z] - Fo[c])))
+        de, df, dw = abs(E[c] - Eo) / s.n, np.max(np.abs(F[a:z] - Fo)), np.max(np.abs(W[c] - Wo)) / s.n
+        worst = [max(worst[0], de), max(worst[1], df), max(worst[2], dw)]
+        assert de <= te, (c, E[c], Eo)
+        assert df <= tf, (c, df)
+        assert dw <= tw, (c, W[c], Wo)
+    print(f"512 configurations: max |dE|/N {worst[0]:.2e}, max |dF| {worst[1]:.2e}, "
+          f"max |dW|/N {worst[2]:.2e}")
     nep.close()
 
 
@@ -116,6 +128,14 @@ def test_c4_512_configurations_loss_and_sampled_gradient():
     g = g.cpu().numpy()
     Lo = _oracle_loss(model, model.params, structs, Et, Ft)
     assert L == pytest.approx(Lo, rel=1e-5)
+    # the fused launch's own energies and forces, every configuration
+    Eo, Fo = _oracle_EF(model, structs)
+    E = E.cpu().numpy()
+    F = F.cpu().numpy().T
+    for c, s in enumerate(structs):
+        a, z = b.offsets[c], b.offsets[c + 1]
+        assert abs(E[c] - Eo[c]) / s.n <= 1e-6, (c, E[c], Eo[c])
+        assert np.max(np.abs(F[a:z] - Fo[c])) <= 1e-4, c
     rng = np.random.default_rng(7)
     H, D = 30, 30
     idx = np.concatenate([rng.choice(H * D, 6, replace=False), H * D + rng.choice(30, 3),

@@ -1,8 +1,8 @@
 """Checkpoint and resume of an MD state (binding level, numpy .npz): a run
 resumed from a checkpoint in a fresh context continues bit for bit like the
 uninterrupted run (FP32 path: fixed-point force sums, deterministic kernels),
-with a fixed and with a variable time step; a checkpoint written with other
-model parameters is refused."""
+with a fixed and with a variable time step; a checkpoint written with another
+model is refused."""
 import numpy as np
 import pytest
 
@@ -22,11 +22,11 @@ def test_resume_is_bitwise_equal(tmp_path, d_max):
                    d_max=d_max)
     a.md(st, 7)
     path = str(tmp_path / "state.npz")
-    N.save_checkpoint(path, st, params=model.params)
+    N.save_checkpoint(path, st, model=model)
     a.md(st, 9)
     a.close()
     b = N.NEP(model, "fp32")
-    r = N.load_checkpoint(path, params=model.params)
+    r = N.load_checkpoint(path, model=model)
     assert r.step == 7 and r.c.forces_valid == 1
     b.md(r, 9)
     assert r.step == st.step == 16 and r.time == st.time
@@ -34,6 +34,8 @@ def test_resume_is_bitwise_equal(tmp_path, d_max):
         assert torch.equal(getattr(r, name), getattr(st, name)), name
     assert r.potential_energy == st.potential_energy
     assert r.kinetic_energy == st.kinetic_energy
+    other = I.nep_model(1)
+    other.params = np.asarray(model.params) * (1.0 + 1e-12)
     with pytest.raises(ValueError):
-        N.load_checkpoint(path, params=np.asarray(model.params) * (1.0 + 1e-12))
+        N.load_checkpoint(path, model=other)
     b.close()

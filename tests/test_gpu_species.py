@@ -8,7 +8,8 @@ from oracle import oracle as O
 from paper_2305_08140_gb300 import inputs as I
 
 from gpu_common import (F32_E_PER_ATOM, F32_F, F32_U, F32_W_PER_ATOM, F64_E_PER_ATOM, F64_F,
-                        F64_U, F64_W_PER_ATOM)
+                        F64_U, F64_W_PER_ATOM, check_forces, check_sites, force_bound,
+                        site_bound)
 
 pytestmark = pytest.mark.gpu
 
@@ -35,7 +36,7 @@ def _types_dev(s):
     return torch.tensor(s.types, dtype=torch.int32, device="cuda")
 
 
-def _parity(s, species, precision, rel_force=0.0):
+def _parity(s, species, precision, scaled=False):
     from paper_2305_08140_gb300 import nepzbl as N
     E, F, W, U = _nep(species, precision).compute(N.to_device_soa(s.pos), s.box, s.pbc,
                                                   types=_types_dev(s), site_energy=True)
@@ -43,14 +44,13 @@ def _parity(s, species, precision, rel_force=0.0):
     U = U.cpu().numpy()
     Eo, Fo, Wo, Uo = O.energy_forces_virial(_model(species), s.pos, s.box, s.pbc, types=s.types)
     if precision == "fp32":
-        tf, te, tu, tw = F32_F, F32_E_PER_ATOM, F32_U, F32_W_PER_ATOM
+        te, tw = F32_E_PER_ATOM, F32_W_PER_ATOM
     else:
-        tf, te, tu, tw = F64_F, F64_E_PER_ATOM, F64_U, F64_W_PER_ATOM
-    bound = tf + rel_force * np.linalg.norm(Fo, axis=1, keepdims=True)
-    dF = np.abs(F - Fo)
-    assert np.all(dF <= bound), (dF.max(), np.unravel_index(np.argmax(dF - bound), dF.shape))
+        te, tw = F64_E_PER_ATOM, F64_W_PER_ATOM
+    sc = O.force_scales(_model(species), s.pos, s.box, s.pbc, types=s.types) if scaled else None
+    check_forces(F, Fo, force_bound(precision, sc))
     assert abs(E - Eo) / s.n <= te, (E, Eo)
-    assert np.max(np.abs(U - Uo)) <= tu + rel_force * np.max(np.abs(Uo))
+    check_sites(U, Uo, site_bound(precision, Uo, sc))
     assert np.max(np.abs(W - Wo)) / s.n <= tw, (W, Wo)
     return E, F, Eo, Fo
 
@@ -67,7 +67,7 @@ def _wmo_box(ncell=(10, 10, 10), seed=301, sigma=0.08, close=True):
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_w_mo_alloy_2000_atoms(precision):
-    _parity(_wmo_box(), WMO, precision, rel_force=1e-6 if precision == "fp32" else 1e-12)
+    _parity(_wmo_box(), WMO, precision, scaled=True)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])

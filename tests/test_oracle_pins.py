@@ -415,6 +415,59 @@ def test_forces_subset_matches_full():
     np.testing.assert_allclose(Fs, F, rtol=1e-10, atol=1e-12)
 
 
+def test_force_scales_dimers_triangle_and_linearity():
+    """Rounding-error scales of each atom: the pair-term magnitude sum S is |F|
+    for a symmetric dimer (NEP only at 3 A), Z is |F| with the network off at
+    1.2 A (ZBL only); S + Z >= |F_i| for every atom of a disordered periodic
+    box (triangle inequality); S is linear in the output weights w1 while the
+    network scales follow their closed forms (W = S max_mu sum |w0 s q| for
+    the dimer, SU linear in w1, TU = sum |w1 t| + |b1|); the subset routine
+    gives the same values."""
+    box = np.array([30.0, 30.0, 30.0])
+    pos = np.array([[10.0, 10.0, 10.0], [13.0, 10.0, 10.0]])
+    E, F, W, U = O.energy_forces_virial(MODEL, pos, box, [0, 0, 0], use_grid=False)
+    sc = O.force_scales(MODEL, pos, box, [0, 0, 0], use_grid=False)
+    np.testing.assert_allclose(sc[:, 0], np.linalg.norm(F, axis=1), rtol=1e-12)
+    assert np.all(sc[:, 1] == 0)
+    # network scales of one site from its descriptor (closed forms)
+    H, D = MODEL.n_hidden, MODEL.dim
+    P = MODEL.params
+    w0 = P[:H * D].reshape(H, D) * MODEL.scaler[None, :]
+    b0, w1, b1 = P[H * D:H * D + H], P[H * D + H:H * D + 2 * H], P[H * D + 2 * H]
+    q = O.descriptors(MODEL, pos, box, [0, 0, 0], use_grid=False)[0]
+    habs = np.abs(w0 * q[None, :]).sum(1)
+    t = np.tanh(w0 @ q - b0)
+    # W: both terms of atom 0's force come from sites with one radial neighbour
+    np.testing.assert_allclose(sc[0, 2], sc[0, 0] * habs.max(), rtol=1e-12)
+    np.testing.assert_allclose(sc[0, 3], np.sum(np.abs(w1 * (1 - t * t)) * habs), rtol=1e-12)
+    np.testing.assert_allclose(sc[0, 4], np.sum(np.abs(w1 * t)) + abs(b1), rtol=1e-12)
+    m = I.nep_model(1)
+    m.params = np.zeros_like(m.params)
+    pos[1, 0] = 11.2
+    E, F, W, U = O.energy_forces_virial(m, pos, box, [0, 0, 0], use_grid=False)
+    sc = O.force_scales(m, pos, box, [0, 0, 0], use_grid=False)
+    assert np.all(sc[:, 0] == 0)
+    np.testing.assert_allclose(sc[:, 1], abs(O.zbl(1.2)[1]), rtol=1e-12)
+    np.testing.assert_allclose(sc[:, 1], np.linalg.norm(F, axis=1), rtol=1e-12)
+    s = I.c3(ncell=6, fraction=0.05, radius=4.0, seed=5)
+    E, F, W, U = O.energy_forces_virial(MODEL, s.pos, s.box, s.pbc)
+    sc = O.force_scales(MODEL, s.pos, s.box, s.pbc)
+    assert np.all(sc[:, 0] + sc[:, 1] >= np.linalg.norm(F, axis=1) * (1 - 1e-12))
+    assert np.any(sc[:, 1] > 0) and np.all(sc[:, 0] > 0)
+    assert np.all(sc[:, 2] > 0) and np.all(sc[:, 4] > 0)
+    m = I.nep_model(1)
+    m.params = MODEL.params.copy()
+    m.params[H * D + H:H * D + 2 * H] *= -2.5     # w1
+    sc2 = O.force_scales(m, s.pos, s.box, s.pbc)
+    np.testing.assert_allclose(sc2[:, 0], 2.5 * sc[:, 0], rtol=1e-10)
+    np.testing.assert_allclose(sc2[:, 1], sc[:, 1], rtol=1e-12)
+    np.testing.assert_allclose(sc2[:, 2], 2.5 * sc[:, 2], rtol=1e-10)
+    np.testing.assert_allclose(sc2[:, 3], 2.5 * sc[:, 3], rtol=1e-10)
+    idx = np.array([0, 7, s.n // 2, s.n - 1])
+    Fs, Us, scs = O.forces_subset(MODEL, s.pos, s.box, s.pbc, idx, scales=True)
+    np.testing.assert_allclose(scs, sc[idx], rtol=1e-11)
+
+
 # --- MD ---------------------------------------------------------------------------
 
 def _tiny_md_system():

@@ -97,3 +97,32 @@ def test_static_scratch_rejects_too_many_atoms():
                                 C.byref(E), C.c_void_p(dummy.data_ptr()), None, None, None)
     assert rc == N.NEP_ERR_INVALID_ARG
     assert "8192" in lib.nep_last_error(None).decode()
+
+
+def test_static_scratch_rejects_host_site_energy():
+    """A host array passed as site_energy is refused before any GPU work (the
+    kernels would store to it): NEP_ERR_INVALID_ARG, naming the argument.  No
+    kernel runs on the bad pointer, and a valid call afterwards still works."""
+    import torch
+    from paper_2305_08140_gb300 import nepzbl as N
+    lib = N.load()
+    model = I.nep_model(1)
+    p, keep = _params_struct(model)
+    s = I.small_box((6, 6, 7), sigma=0.1, seed=63)
+    x = N.to_device_soa(s.pos)
+    types = torch.zeros(s.n, dtype=torch.int32, device="cuda")
+    F = torch.zeros((3, s.n), dtype=torch.float64, device="cuda")
+    U_host = np.zeros(s.n)
+    box = np.ascontiguousarray(np.diag(s.box).reshape(9))
+    E = C.c_double()
+    rc = lib.nep_compute_static(C.byref(p), s.n, C.c_void_p(x.data_ptr()),
+                                box.ctypes.data_as(C.POINTER(C.c_double)),
+                                C.c_void_p(types.data_ptr()), (C.c_int32 * 3)(*s.pbc),
+                                C.byref(E), C.c_void_p(F.data_ptr()), None,
+                                C.c_void_p(U_host.ctypes.data),
+                                C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == N.NEP_ERR_INVALID_ARG
+    assert "site_energy" in lib.nep_last_error(None).decode()
+    assert np.all(U_host == 0.0)
+    E1, F1, W1, U1 = _static_eval(lib, p, s)
+    assert np.all(np.isfinite(F1)) and np.isfinite(E1)
