@@ -618,6 +618,52 @@ def run_ours(args):
     return 0
 
 
+def run_profile_case(args):
+    """One workload, a few repetitions, no JSON line: the command that ncu
+    captures for the kernels outside the MD step (one kernel per capture).
+      c4_loss     512 configurations, fused forward + loss + gradient (k_batch)
+      c4_pop      the NEP loss of a population of 50 over the 512 configurations
+                  (k_batch_pop)
+      c2_fp64     one plain-FP64 force evaluation of the 128,000-atom crystal
+                  (k_nep_ang<double>, k_radial_force<double>)
+    """
+    import torch
+    from paper_2305_08140_gb300 import nepzbl as N
+    dev = torch.device("cuda", 0)
+    model = I.nep_model(1)
+    reps = max(args.steps, 1)
+    if args.profile_case in ("c4_loss", "c4_pop"):
+        structs = I.c4()
+        b = N.Batch(structs, dev)
+        tgt = N.NEP(I.nep_model(101), "fp32")
+        Et, Ft, W9 = tgt.batch_forward(b, virials=True)
+        tgt.close()
+        nep = N.NEP(model, "fp32")
+        if args.profile_case == "c4_loss":
+            for _ in range(reps):
+                nep.batch_loss_grad(b, Et, Ft)
+        else:
+            Wt = W9.reshape(b.S, 9)[:, [0, 4, 8, 5, 6, 1]].contiguous()
+            g = torch.Generator(device=dev)
+            g.manual_seed(7)
+            theta = torch.tensor(model.params, dtype=torch.float64, device=dev)
+            thetas = theta[None, :] + 0.01 * torch.randn((50, theta.numel()), generator=g,
+                                                          dtype=torch.float64, device=dev)
+            for _ in range(reps):
+                N.population_loss(nep, b, thetas, Et, Ft, Wt)
+        nep.close()
+    elif args.profile_case == "c2_fp64":
+        s = I.displaced(I.c2(), 0.05, 41)
+        nep = N.NEP(model, "fp64")
+        x = N.to_device_soa(s.pos, dev)
+        for _ in range(reps):
+            nep.compute(x, s.box, s.pbc)
+        nep.close()
+    torch.cuda.synchronize()
+    print(f"profile case {args.profile_case}: {reps} repetitions done")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -634,9 +680,13 @@ def main():
     ap.add_argument("--ncell", type=int, default=160,
                     help="slab size in bcc cells per side (160 = the 8,192,000-atom workload; "
                          "smaller values only for profiling)")
+    ap.add_argument("--profile-case", choices=["c4_loss", "c4_pop", "c2_fp64"], default=None,
+                    help="run one other workload --steps times without timing (for ncu)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.profile_case:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

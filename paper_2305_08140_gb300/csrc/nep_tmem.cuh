@@ -78,6 +78,13 @@ __device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sy
 __device__ __forceinline__ void tm_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// Packed FP32 pairs (sm_100 and later: one FFMA2 instruction does two
+// correctly rounded FMAs, so the issue-bound loops below take half the
+// instructions for the same arithmetic).
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
 // the 24 values of radial channel n of this thread's lane
 __device__ __forceinline__ void tm_ld24(uint32_t tb, int n, float* v)
 {
@@ -115,14 +122,13 @@ __device__ __forceinline__ void force_pair_ang_tm(const Model<float>& P, float r
         nepm::cheb<KA, true>(r, P.inv_rcA, T, dT, fc, dfc, dxdr);
 #pragma unroll
         for (int n = 0; n < NA; ++n) {
-            float a = P.CA[n], b = 0.f;
+            // (sum_k h_nk T_k + C_n, sum_k h_nk T'_k) as one packed pair
+            float2 ab = f2(P.CA[n], 0.f);
 #pragma unroll
-            for (int kk = 0; kk < KA; ++kk) {
-                a += P.hA[n * KA + kk] * T[kk];
-                b += P.hA[n * KA + kk] * dT[kk];
-            }
-            gn[n] = fc * a;
-            dgn[n] = dfc * a + fc * dxdr * b;
+            for (int kk = 0; kk < KA; ++kk)
+                ab = fma2(f2(P.hA[n * KA + kk], P.hA[n * KA + kk]), f2(T[kk], dT[kk]), ab);
+            gn[n] = fc * ab.x;
+            dgn[n] = dfc * ab.x + fc * dxdr * ab.y;
         }
     }
     float Pn[NA], Qn[NA];
@@ -136,12 +142,13 @@ __device__ __forceinline__ void force_pair_ang_tm(const Model<float>& P, float r
         // group's polynomials are formed here, not hoisted and kept live
         float gx = ux, gy = uy, gz = uz;
         asm volatile("" : "+f"(gx), "+f"(gy), "+f"(gz));
-        float Y[8], G[8];
+        float Y[8];
         if (GR == 0) nepm::harmonics_group<0>(gx, gy, gz, Y);
         if (GR == 1) nepm::harmonics_group<1>(gx, gy, gz, Y);
         if (GR == 2) nepm::harmonics_group<2>(gx, gy, gz, Y);
+        float2 G2[4];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) G[j] = 0.f;
+        for (int p = 0; p < 4; ++p) G2[p] = f2(0.f, 0.f);
 #pragma unroll
         for (int n = 0; n < NA; ++n) {
             const int c = GR * NA + n;
@@ -150,21 +157,35 @@ __device__ __forceinline__ void force_pair_ang_tm(const Model<float>& P, float r
                 const int n1 = (c + 1) % NA, g1 = (c + 1) / NA;
                 tm_ld8(tb + (uint32_t)(n1 * NLM + 8 * g1), buf[(c + 1) & 1]);
             }
-            float sa = 0.f, sb = 0.f;   // sum a Y over the group's lower / upper l
+            const float* v = buf[c & 1];
+            const float2 gg = f2(gn[n], gn[n]);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const float v = buf[c & 1][j];
-                G[j] += v * gn[n];
-                // group 0: l = 1 (j < 3), 2; group 1: l = 3 (j < 7), 4; group 2: l = 4
-                const bool lower = GR == 0 ? j < 3 : (GR == 1 ? j < 7 : true);
-                if (lower) sa += v * Y[j];
-                else sb += v * Y[j];
+            for (int p = 0; p < 4; ++p) G2[p] = fma2(f2(v[2 * p], v[2 * p + 1]), gg, G2[p]);
+            // sum a Y over the group's lower and upper l (group 0: l = 1 for
+            // j < 3, else 2; group 1: l = 3 for j < 7, else 4; group 2: l = 4):
+            // pairs (0,1) and (4,5)+(6,7) are whole, pair (2,3) (group 0) or
+            // (6,7) (group 1) splits
+            float sa, sb;
+            const float2 t01 = mul2(f2(v[0], v[1]), f2(Y[0], Y[1]));
+            const float2 t23 = mul2(f2(v[2], v[3]), f2(Y[2], Y[3]));
+            const float2 t45 = mul2(f2(v[4], v[5]), f2(Y[4], Y[5]));
+            const float2 t67 = mul2(f2(v[6], v[7]), f2(Y[6], Y[7]));
+            if (GR == 0) {
+                sa = (t01.x + t01.y) + t23.x;
+                sb = (t23.y + t45.x) + (t45.y + (t67.x + t67.y));
+            } else if (GR == 1) {
+                sa = ((t01.x + t01.y) + (t23.x + t23.y)) + ((t45.x + t45.y) + t67.x);
+                sb = t67.y;
+            } else {
+                sa = 0.f;
+                sb = ((t01.x + t01.y) + (t23.x + t23.y)) + ((t45.x + t45.y) + (t67.x + t67.y));
             }
-            const float la = GR == 0 ? 1.f : (GR == 1 ? 3.f : 4.f);
+            const float la = GR == 0 ? 1.f : 3.f;
             const float lb = GR == 0 ? 2.f : 4.f;
             Pn[n] += sa + sb;
             Qn[n] += la * sa + lb * sb;
         }
+        const float G[8] = {G2[0].x, G2[0].y, G2[1].x, G2[1].y, G2[2].x, G2[2].y, G2[3].x, G2[3].y};
         if (GR == 0) nepm::harmonics_grad_dot_group<0>(gx, gy, gz, G, vx, vy, vz);
         if (GR == 1) nepm::harmonics_grad_dot_group<1>(gx, gy, gz, G, vx, vy, vz);
         if (GR == 2) nepm::harmonics_grad_dot_group<2>(gx, gy, gz, G, vx, vy, vz);
@@ -192,11 +213,11 @@ __device__ __forceinline__ void ang_desc_pass(const Model<float>& P, const Grid&
                                               float* s_q)
 {
     constexpr int NN = N1 - N0;
-    float A[NN][NLM];
+    float2 A[NN][NLM / 2];   // A_nlm in packed pairs (lm, lm + 1)
 #pragma unroll
     for (int n = 0; n < NN; ++n)
 #pragma unroll
-        for (int lm = 0; lm < NLM; ++lm) A[n][lm] = 0.f;
+        for (int p = 0; p < NLM / 2; ++p) A[n][p] = f2(0.f, 0.f);
     int ent_n = na > 0 ? entry(0) : 0;
     float4 pj_n = na > 0 ? pos4[ent_n >> 5] : pi;
     for (int s = 0; s < na; ++s) {
@@ -228,24 +249,29 @@ __device__ __forceinline__ void ang_desc_pass(const Model<float>& P, const Grid&
 #pragma unroll
         for (int n = 0; n < NN; ++n)
 #pragma unroll
-            for (int lm = 0; lm < 8; ++lm) A[n][lm] += gn[n] * Y[lm];
+            for (int p = 0; p < 4; ++p)
+                A[n][p] = fma2(f2(gn[n], gn[n]), f2(Y[2 * p], Y[2 * p + 1]), A[n][p]);
         nepm::harmonics_l34(ux, uy, uz, Y);
 #pragma unroll
         for (int n = 0; n < NN; ++n)
 #pragma unroll
-            for (int lm = 8; lm < NLM; ++lm) A[n][lm] += gn[n] * Y[lm];
+            for (int p = 4; p < NLM / 2; ++p)
+                A[n][p] = fma2(f2(gn[n], gn[n]), f2(Y[2 * p], Y[2 * p + 1]), A[n][p]);
     }
 #pragma unroll
     for (int n = 0; n < NN; ++n) {
+        float An[NLM];
+#pragma unroll
+        for (int p = 0; p < NLM / 2; ++p) { An[2 * p] = A[n][p].x; An[2 * p + 1] = A[n][p].y; }
 #pragma unroll
         for (int l = 1; l <= LM; ++l) {
             float v = 0.f;
 #pragma unroll
-            for (int lm = l * l - 1; lm < (l + 1) * (l + 1) - 1; ++lm) v += A[n][lm] * A[n][lm];
+            for (int lm = l * l - 1; lm < (l + 1) * (l + 1) - 1; ++lm) v += An[lm] * An[lm];
             s_q[((l - 1) * NA + N0 + n) * TILE + threadIdx.x] = v;
         }
-        s_q[(LM * NA + N0 + n) * TILE + threadIdx.x] = nepm::fourbody(&A[n][3], (float*)nullptr);
-        tm_st24(tb, N0 + n, A[n]);
+        s_q[(LM * NA + N0 + n) * TILE + threadIdx.x] = nepm::fourbody(&An[3], (float*)nullptr);
+        tm_st24(tb, N0 + n, An);
     }
 }
 
@@ -324,23 +350,29 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
 
     // network forward and backward (rolled over the hidden neurons, as
     // network_adjoint_core_rolled)
-    float a[D];
+    // (packed pairs of descriptor components: the pre-activation is the sum of
+    // an even and an odd partial sum)
+    float2 a2[D / 2];
 #pragma unroll
-    for (int nu = 0; nu < D; ++nu) a[nu] = 0.f;
+    for (int p = 0; p < D / 2; ++p) a2[p] = f2(0.f, 0.f);
     float U = -P.b1;
 #pragma unroll 1
     for (int mu = 0; mu < H; ++mu) {
         float w[WROW];
         load_row<float>(s_w + mu * WROW, w);
-        float h = -w[D];
+        float2 h2 = f2(-w[D], 0.f);
 #pragma unroll
-        for (int nu = 0; nu < D; ++nu) h += w[nu] * q[nu];
+        for (int p = 0; p < D / 2; ++p) h2 = fma2(f2(w[2 * p], w[2 * p + 1]), f2(q[2 * p], q[2 * p + 1]), h2);
+        const float h = h2.x + h2.y;
         const float t = tanhf(h);
         U += w[D + 1] * t;
         const float gm = w[D + 1] * (1.f - t * t);
 #pragma unroll
-        for (int nu = 0; nu < D; ++nu) a[nu] += gm * w[nu];
+        for (int p = 0; p < D / 2; ++p) a2[p] = fma2(f2(gm, gm), f2(w[2 * p], w[2 * p + 1]), a2[p]);
     }
+    float a[D];
+#pragma unroll
+    for (int p = 0; p < D / 2; ++p) { a[2 * p] = a2[p].x; a[2 * p + 1] = a2[p].y; }
     // adjoint dU/dA_nlm in Tensor Memory, channel by channel (4-body term
     // folded into l = 2)
 #pragma unroll
