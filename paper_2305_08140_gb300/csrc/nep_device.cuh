@@ -722,8 +722,21 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                     const R rr = f2 * nepm::nep_rsqrt(f2);
                     R T[KR], dT[KR], fc, dfc, dxdr;
                     nepm::cheb<KR, false>(rr, rq.inv_rcR, T, dT, fc, dfc, dxdr);
+                    if constexpr (sizeof(R) == 4) {
+                        // packed pairs: one FFMA2 per two basis functions
 #pragma unroll
-                    for (int kk = 0; kk < KR; ++kk) Sb[kk] += fc * T[kk];
+                        for (int kk = 0; kk + 1 < KR; kk += 2) {
+                            const float2 t = __ffma2_rn(make_float2(fc, fc),
+                                                        make_float2(T[kk], T[kk + 1]),
+                                                        make_float2(Sb[kk], Sb[kk + 1]));
+                            Sb[kk] = t.x;
+                            Sb[kk + 1] = t.y;
+                        }
+                        Sb[KR - 1] += fc * T[KR - 1];
+                    } else {
+#pragma unroll
+                        for (int kk = 0; kk < KR; ++kk) Sb[kk] += fc * T[kk];
+                    }
                 }
             }
 #pragma unroll
@@ -1890,22 +1903,39 @@ __global__ void __launch_bounds__(TILE, sizeof(R) == 4 && !MS ? 7 : 1) k_radial_
             const R r = r2 * inv_r;
             R T[KR], dT[KR], fc, dfc, dxdr;
             nepm::cheb<KR, true>(r, P.inv_rcR, T, dT, fc, dfc, dxdr);
-            const R b[KR] = {ri1.x + rj1.x, ri1.y + rj1.y, ri1.z + rj1.z, ri1.w + rj1.w,
-                             ri2.x + rj2.x, ri2.y + rj2.y, ri2.z + rj2.z, ri2.w + rj2.w,
-                             ri0.w + rj0.w};
-            R s1 = b[0], s2 = R(0);
+            R s1, s2;
+            if constexpr (sizeof(R) == 4) {
+                // packed pairs (one FFMA2 per k: (s1, s2) += b_k (T_k, T'_k))
+                float2 ss = __fadd2_rn(make_float2(ri1.x, 0.f), make_float2(rj1.x, 0.f));
+                const float bk[KR - 1] = {ri1.y + rj1.y, ri1.z + rj1.z, ri1.w + rj1.w,
+                                          ri2.x + rj2.x, ri2.y + rj2.y, ri2.z + rj2.z,
+                                          ri2.w + rj2.w, ri0.w + rj0.w};
 #pragma unroll
-            for (int kk = 1; kk < KR; ++kk) {
-                s1 += b[kk] * T[kk];
-                s2 += b[kk] * dT[kk];
+                for (int kk = 1; kk < KR; ++kk)
+                    ss = __ffma2_rn(make_float2(bk[kk - 1], bk[kk - 1]),
+                                    make_float2(T[kk], dT[kk]), ss);
+                s1 = ss.x;
+                s2 = ss.y;
+            } else {
+                const R b[KR] = {ri1.x + rj1.x, ri1.y + rj1.y, ri1.z + rj1.z, ri1.w + rj1.w,
+                                 ri2.x + rj2.x, ri2.y + rj2.y, ri2.z + rj2.z, ri2.w + rj2.w,
+                                 ri0.w + rj0.w};
+                s1 = b[0];
+                s2 = R(0);
+#pragma unroll
+                for (int kk = 1; kk < KR; ++kk) {
+                    s1 += b[kk] * T[kk];
+                    s2 += b[kk] * dT[kk];
+                }
             }
             const R fs = (dfc * s1 + fc * dxdr * s2) * inv_r;   // (f_ij - f_ji) = fs d
             const R gx = fs * dx, gy = fs * dy, gz = fs * dz;
             fx += gx; fy += gy; fz += gz;
-            w[0] -= gx * dx; w[1] -= gx * dy; w[2] -= gx * dz;
-            w[3] -= gy * dx; w[4] -= gy * dy; w[5] -= gy * dz;
-            w[6] -= gz * dx; w[7] -= gz * dy; w[8] -= gz * dz;
+            // fs d (x) d is symmetric: six products (expanded after the loop)
+            w[0] -= gx * dx; w[4] -= gy * dy; w[8] -= gz * dz;
+            w[1] -= gx * dy; w[2] -= gx * dz; w[5] -= gy * dz;
         }
+        w[3] = w[1]; w[6] = w[2]; w[7] = w[5];
         if (!isfinite(fx + fy + fz)) atomicOr(status, ST_NONFINITE);
         A_::add(&facc[k], A_::conv(fx));
         A_::add(&facc[ld + k], A_::conv(fy));
