@@ -204,6 +204,9 @@ __device__ __forceinline__ int species_at(const typename V4<R>::T& p)
 
 // MS: coefficients of every pair from its species block (pair_coef); the
 // radial descriptor and radial force per pair instead of through basis sums.
+// atoms per R partial of the per-configuration gradient sums
+constexpr int GSUM_BLK = 16;
+
 template <typename R, bool MS = false>
 __device__ __forceinline__ double batch_atom_forward(const Model<R>& P, const Batch& b,
                                                      long long a0, int i,
@@ -271,6 +274,11 @@ __device__ __forceinline__ double batch_atom_forward(const Model<R>& P, const Ba
     }
     double ez = 0.0;
     typename A_::T fi[3] = {0, 0, 0};
+    // this atom's NEP virial in R (the narrow FP64 pipe of this GPU made the
+    // per-pair FP64 sums the launch's bottleneck); the rare ZBL pairs in FP64
+    R wr[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) wr[t] = R(0);
     bad |= !isfinite(U);
     for (int s = 0; s < tot; ++s) {
         const int ent = b.nbr[(size_t)slot_of(s, na, nro, M) * b.ntot + col];
@@ -305,9 +313,13 @@ __device__ __forceinline__ double batch_atom_forward(const Model<R>& P, const Ba
         }
         bad |= !isfinite(fx + fy + fz);
         typename A_::T cx = A_::conv(fx), cy = A_::conv(fy), cz = A_::conv(fz);
-        const double d64[3] = {(double)g.dx, (double)g.dy, (double)g.dz};
-        double f64[3] = {(double)fx, (double)fy, (double)fz};
+        const R fp[3] = {fx, fy, fz}, dp[3] = {g.dx, g.dy, g.dz};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) wr[3 * a + c] -= fp[a] * dp[c];
         if (s < na && g.r < P.zbl_r2) {
+            const double d64[3] = {(double)g.dx, (double)g.dy, (double)g.dz};
             const double r64 = sqrt(d64[0] * d64[0] + d64[1] * d64[1] + d64[2] * d64[2]);
             if (r64 < P.zbl_rr2) {
                 double Uz, dUz;
@@ -319,15 +331,12 @@ __device__ __forceinline__ double batch_atom_forward(const Model<R>& P, const Ba
                 cx += A_::convd(c * d64[0]);
                 cy += A_::convd(c * d64[1]);
                 cz += A_::convd(c * d64[2]);
-                f64[0] += c * d64[0];
-                f64[1] += c * d64[1];
-                f64[2] += c * d64[2];
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) w[3 * a + e] -= c * d64[a] * d64[e];
             }
         }
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) w[3 * a + c] -= f64[a] * d64[c];
         fi[0] += cx; fi[1] += cy; fi[2] += cz;
         A_::add(&sF[0][g.j], -cx);
         A_::add(&sF[1][g.j], -cy);
@@ -336,6 +345,8 @@ __device__ __forceinline__ double batch_atom_forward(const Model<R>& P, const Ba
     A_::add(&sF[0][i], fi[0]);
     A_::add(&sF[1][i], fi[1]);
     A_::add(&sF[2][i], fi[2]);
+#pragma unroll
+    for (int t = 0; t < 9; ++t) w[t] += (double)wr[t];
     return (double)U + ez;
 }
 
@@ -718,19 +729,39 @@ __global__ void __launch_bounds__(BT) k_batch(const Model<R> P, const Batch b)
             const R* scr = (const R*)b.scr;
             for (int e = threadIdx.x; e < H * D + 2 * H + 1; e += BT) {
                 double acc = 0.0;
+                // sums over the atoms: R partials over GSUM_BLK atoms, FP64
+                // across the partials (few FP64 instructions; the per-atom
+                // products are R anyway)
                 if (e < H * D) {
                     const int mu = e / D, nu = e % D;
-                    for (int i = 0; i < N; ++i) {
-                        const R* row = scr + (size_t)(a0 + i) * BSTRIDE;
-                        acc += (double)row[BS_U + mu] * (double)row[BS_Q + nu] -
-                               (double)row[BS_V + mu] * (double)row[BS_QD + nu];
+                    for (int i0 = 0; i0 < N; i0 += GSUM_BLK) {
+                        const int i1 = i0 + GSUM_BLK < N ? i0 + GSUM_BLK : N;
+                        R part = R(0);
+                        for (int i = i0; i < i1; ++i) {
+                            const R* row = scr + (size_t)(a0 + i) * BSTRIDE;
+                            part += row[BS_U + mu] * row[BS_Q + nu];
+                            part -= row[BS_V + mu] * row[BS_QD + nu];
+                        }
+                        acc += (double)part;
                     }
                     // W = w0 * s: chain to w0 through the scaler folded into P.w0
                     acc *= (double)P.sc[nu];
                 } else if (e < OFF_W1) {
-                    for (int i = 0; i < N; ++i) acc -= (double)scr[(size_t)(a0 + i) * BSTRIDE + BS_U + (e - OFF_B0)];
+                    for (int i0 = 0; i0 < N; i0 += GSUM_BLK) {
+                        const int i1 = i0 + GSUM_BLK < N ? i0 + GSUM_BLK : N;
+                        R part = R(0);
+                        for (int i = i0; i < i1; ++i)
+                            part += scr[(size_t)(a0 + i) * BSTRIDE + BS_U + (e - OFF_B0)];
+                        acc -= (double)part;
+                    }
                 } else if (e < OFF_B1) {
-                    for (int i = 0; i < N; ++i) acc += (double)scr[(size_t)(a0 + i) * BSTRIDE + BS_GW1 + (e - OFF_W1)];
+                    for (int i0 = 0; i0 < N; i0 += GSUM_BLK) {
+                        const int i1 = i0 + GSUM_BLK < N ? i0 + GSUM_BLK : N;
+                        R part = R(0);
+                        for (int i = i0; i < i1; ++i)
+                            part += scr[(size_t)(a0 + i) * BSTRIDE + BS_GW1 + (e - OFF_W1)];
+                        acc += (double)part;
+                    }
                 } else {
                     acc = -eps * N;
                 }
