@@ -61,13 +61,14 @@ FLOP_PAIR_R = 128 + 122
 FLOP_PAIR_A = 424 + 1078
 
 # Measured DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) per
-# atom: of the two timed force kernels (k_nep_ang_tm + k_radial_force) per
-# launch pair, and of every kernel of one MD step, from captures of the
-# 1,024,000-atom slab (same geometry as the 8,192,000-atom slab at 80^3
-# cells); scaled by the atom count.  None while the kernels have changed since
-# the capture.  Source: profiles/dram_bytes_md_step_slab_1024000.md.
-DRAM_FORCE_PER_ATOM = None
-DRAM_STEP_PER_ATOM = None
+# atom: of the two timed force kernels (k_nep_ang_tm + both k_radial_force
+# launches) per evaluation, and of every kernel of one MD step, from a
+# one-pass capture of the 8,192,000-atom slab itself; used for that workload
+# (scaled by the atom count for others).  Set to None when the kernels change
+# until they are captured again.  Source:
+# profiles/dram_bytes_md_step_slab_8192000.md.
+DRAM_FORCE_PER_ATOM = 534.2
+DRAM_STEP_PER_ATOM = 1287.0
 # Compulsory HBM bytes per atom-step of this design: every array a kernel of
 # the step needs read or written once by that kernel (neighbour records that
 # the caches serve are not counted):
@@ -581,9 +582,9 @@ def run_ours(args):
                      "frac": achieved / peak_tflops,
                      "traffic": traffic,
                      "traffic_note": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the "
-                                      "timed kernels per launch pair, 1,024,000-atom capture "
-                                      "scaled by atoms; null while the kernels differ from the "
-                                      "capture"),
+                                      "timed kernels per evaluation, one-pass capture of the "
+                                      "8,192,000-atom slab (scaled by atoms for other sizes); "
+                                      "null while the kernels differ from the capture"),
                      "peak_kind": f"FP32 issue rate {sms} SMs x {FP32_LANES} lanes x 2 x "
                                   f"{sm_mhz:.0f} MHz (sm_max_mhz, {peak_kind})",
                      "sm_count": sms,
