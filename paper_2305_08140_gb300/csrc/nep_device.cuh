@@ -1773,7 +1773,17 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
             R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
             R r2 = dx * dx + dy * dy + dz * dz;
             if (r2 >= P.rcA2) continue;
-            close_pair_fp64<R>(P.zbl_r2 * P.zbl_r2, g, x64, perm, k, m, dx, dy, dz, r2);
+            // close pair (FP32 path): the FP64 displacement, formed once for the
+            // NEP terms (rounded, see close_pair_fp64) and the ZBL term
+            double d64[3];
+            const bool close = sizeof(R) == 4 && r2 < P.zbl_r2 * P.zbl_r2;
+            if (close) {
+                disp64(g, x64, i_caller, perm[m], d64);
+                dx = (R)d64[0];
+                dy = (R)d64[1];
+                dz = (R)d64[2];
+                r2 = dx * dx + dy * dy + dz * dz;
+            }
             const R inv_r = nepm::nep_rsqrt(r2);
             const R r = r2 * inv_r;
             R fx, fy, fz;
@@ -1783,15 +1793,8 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
             bad |= !isfinite(fx + fy + fz);
             typename A_::T cx = A_::conv(fx), cy = A_::conv(fy), cz = A_::conv(fz);
             if (r < P.zbl_r2) {
-                double d64[3];
                 if (sizeof(R) == 4) {
-                    const int j_caller = perm[m];
-                    for (int a = 0; a < 3; ++a) {
-                        double t = x64[a * g.n + j_caller] - x64[a * g.n + i_caller];
-                        if (!g.tric && g.pbc[a]) t -= g.L[a] * rint(t * g.invL[a]);
-                        d64[a] = t;
-                    }
-                    if (g.tric) min_image_tric(g, d64);
+                    if (!close) disp64(g, x64, i_caller, perm[m], d64);
                 } else {
                     d64[0] = (double)dx; d64[1] = (double)dy; d64[2] = (double)dz;
                 }
