@@ -320,15 +320,6 @@ static __global__ void k_bin_scatter(int n, const int* __restrict__ cell_of,
     perm[start[cell_of[i]] + slot_of[i]] = i;
 }
 
-// Paired layout of the cell-relative positions for the FP32 neighbour search:
-// atoms 2p and 2p + 1 share 8 floats (x_2p, x_2p+1, y_2p, y_2p+1, z_2p,
-// z_2p+1, -, -), so that one 16-byte and one 8-byte load give two candidates'
-// coordinates as packed pairs for the FP32x2 instructions.
-__host__ __device__ __forceinline__ size_t pos2_index(int k)
-{
-    return (size_t)(k >> 1) * 8 + (k & 1);
-}
-
 // One thread per cell: order the cell's atoms by caller index (so everything
 // downstream is independent of the atomic slot order) and write their
 // cell-relative positions.
@@ -405,8 +396,7 @@ __global__ void __launch_bounds__(256) k_cell_finalize_w(
     Grid g, int ncell, const int* __restrict__ start, int* __restrict__ perm,
     const int32_t* __restrict__ types, typename V4<R>::T* __restrict__ pos4,
     int* __restrict__ cell_sorted, int* __restrict__ status, const int* __restrict__ gate,
-    int* __restrict__ invperm, const typename V4<R>::T* __restrict__ rel,
-    float* __restrict__ pos2 = nullptr)
+    int* __restrict__ invperm, const typename V4<R>::T* __restrict__ rel)
 {
     if (gate && *gate == 0) return;   // lists still valid (Verlet skin)
     const int c = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
@@ -423,12 +413,6 @@ __global__ void __launch_bounds__(256) k_cell_finalize_w(
         if (t < 0 || t >= g.ntypes) { badtype = true; t = 0; }
         o.w = (R)t;
         pos4[s] = o;
-        if (pos2) {   // the same position in the paired layout (see pos2_index)
-            float* q2 = pos2 + pos2_index(s);
-            q2[0] = (float)q.x;
-            q2[2] = (float)q.y;
-            q2[4] = (float)q.z;
-        }
         cell_sorted[s] = c;
         if (invperm) invperm[i] = s;
     };
@@ -576,8 +560,7 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                                                    const int* __restrict__ gate,
                                                    const RadCoef<R> rq, R* __restrict__ qr,
                                                    const int* __restrict__ perm,
-                                                   const double* __restrict__ x64,
-                                                   const float* __restrict__ pos2)
+                                                   const double* __restrict__ x64)
 {
     using P4 = typename V4<R>::T;
     if (gate && *gate == 0) return;   // lists still valid (Verlet skin)
@@ -657,49 +640,21 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                             if (pz + reach < R(0) || pz - reach >= lz) continue;
                         }
                         const int e = start[c2 * zs + t1 + 1];
-                        const int m_lo = start[c2 * zs + t0];
-                        // FP32: candidates in packed pairs from the paired layout
-                        // (chunks start at an even slot; a leading odd slot is
-                        // masked); otherwise one by one from pos4
-                        constexpr bool PAIRS = sizeof(R) == 4 && !TRIC;
-                        for (int m0 = PAIRS ? (m_lo & ~1) : m_lo; m0 < e; m0 += CHW) {
+                        for (int m0 = start[c2 * zs + t0]; m0 < e; m0 += CHW) {
+                            const P4* q0 = pos4 + m0;
                             unsigned hr = 0u, ha = 0u;   // r < rc_R, r < rc_A
-                            if constexpr (PAIRS) {
-                                const float2 npx = make_float2(-(float)px, -(float)px),
-                                             npy = make_float2(-(float)py, -(float)py),
-                                             npz = make_float2(-(float)pz, -(float)pz);
-                                const float* q0 = pos2 + pos2_index(m0);
 #pragma unroll
-                                for (int j = 0; j < CHW; j += 2) {
-                                    const float4 xy = *reinterpret_cast<const float4*>(q0 + 4 * j);
-                                    const float2 zz = *reinterpret_cast<const float2*>(q0 + 4 * j + 4);
-                                    const float2 dx = __fadd2_rn(make_float2(xy.x, xy.y), npx);
-                                    const float2 dy = __fadd2_rn(make_float2(xy.z, xy.w), npy);
-                                    const float2 dz = __fadd2_rn(zz, npz);
-                                    float2 r2 = __fmul2_rn(dx, dx);
-                                    r2 = __ffma2_rn(dy, dy, r2);
-                                    r2 = __ffma2_rn(dz, dz, r2);
-                                    if (r2.x < rcR2) hr |= 1u << j;
-                                    if (r2.x < rcA2) ha |= 1u << j;
-                                    if (r2.y < rcR2) hr |= 2u << j;
-                                    if (r2.y < rcA2) ha |= 2u << j;
-                                }
-                            } else {
-                                const P4* q0 = pos4 + m0;
-#pragma unroll
-                                for (int j = 0; j < CHW; ++j) {
-                                    const P4 q = q0[j];
-                                    const R dx = q.x - px, dy = q.y - py, dz = q.z - pz;
-                                    const R r2 = dx * dx + dy * dy + dz * dz;
-                                    if (r2 < rcR2) hr |= 1u << j;
-                                    if (r2 < rcA2) ha |= 1u << j;
-                                }
+                            for (int j = 0; j < CHW; ++j) {
+                                const P4 q = q0[j];
+                                const R dx = q.x - px, dy = q.y - py, dz = q.z - pz;
+                                const R r2 = dx * dx + dy * dy + dz * dz;
+                                if (r2 < rcR2) hr |= 1u << j;
+                                if (r2 < rcA2) ha |= 1u << j;
                             }
                             // this range's atoms only, never the atom itself
                             const int nv = e - m0;
                             unsigned keep = nv >= CHW ? (CHW == 32 ? 0xffffffffu : (1u << CHW) - 1u)
                                                       : (1u << nv) - 1u;
-                            if (m0 < m_lo) keep &= ~1u;   // the leading odd slot
                             const unsigned self = (unsigned)(k - m0);
                             if (self < (unsigned)CHW) keep &= ~(1u << self);
                             ha &= hr & keep;

@@ -72,7 +72,6 @@ struct nep_ctx {
     int *cell_of = nullptr, *slot_of = nullptr, *perm = nullptr, *cell_sorted = nullptr;
     int* invperm = nullptr;          // caller index -> cell-ordered slot
     void* pos4 = nullptr;
-    float* pos2 = nullptr;           // FP32: pos4 in the paired layout (pos2_index)
     void* rel4 = nullptr;            // cell-relative position by caller index (binning)
     int2* cnt = nullptr;
     int* nbr = nullptr;
@@ -226,7 +225,7 @@ static void free_scratch(nep_ctx* ctx)
 {
     drop_graphs(ctx);
     free_dev(ctx->cell_of); free_dev(ctx->slot_of); free_dev(ctx->perm);
-    free_dev(ctx->cell_sorted); free_dev(ctx->invperm); free_dev(ctx->pos4); free_dev(ctx->pos2); free_dev(ctx->rel4); free_dev(ctx->cnt); free_dev(ctx->nbr);
+    free_dev(ctx->cell_sorted); free_dev(ctx->invperm); free_dev(ctx->pos4); free_dev(ctx->rel4); free_dev(ctx->cnt); free_dev(ctx->nbr);
     free_dev(ctx->facc); free_dev(ctx->partials); free_dev(ctx->partials2);
     free_dev(ctx->qr); free_dev(ctx->br); free_dev(ctx->xref); free_dev(ctx->nbr_act);
     free_dev(ctx->cnt_act);
@@ -256,13 +255,6 @@ static int ensure_atoms(nep_ctx* ctx, int n, int M)
     // the last atom (those reads are masked off)
     CK(cudaMalloc(&ctx->pos4, p4 * (ld + NB_CHUNK)));
     CK(cudaMemset(ctx->pos4, 0, p4 * (ld + NB_CHUNK)));
-    if (ctx->precision == NEP_FP32) {
-        // the paired layout for the FP32 search (8 floats per two atoms), with
-        // the same slack
-        const size_t f2 = pos2_index(ld + NB_CHUNK + 2) + 8;
-        CK(cudaMalloc(&ctx->pos2, sizeof(float) * f2));
-        CK(cudaMemset(ctx->pos2, 0, sizeof(float) * f2));
-    }
     CK(cudaMalloc(&ctx->rel4, p4 * ld));
     CK(cudaMalloc(&ctx->cnt, sizeof(int2) * ld));
     CK(cudaMalloc(&ctx->nbr, sizeof(int) * (size_t)ld * MM));
@@ -475,8 +467,7 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     // one warp per cell (the positions relative to the cells from k_bin_count)
     k_cell_finalize_w<R><<<(int)(((size_t)ncell * 32 + 255) / 256), 256, 0, s>>>(
         g, ncell, ctx->start, ctx->perm, types, (typename V4<R>::T*)ctx->pos4, ctx->cell_sorted,
-        ctx->status, gate, ctx->invperm, (const typename V4<R>::T*)ctx->rel4,
-        g.tric ? nullptr : ctx->pos2);
+        ctx->status, gate, ctx->invperm, (const typename V4<R>::T*)ctx->rel4);
     count_launch(ctx);
     // one species, lists rebuilt every step, FP32: the neighbour kernel also
     // sums the radial descriptor (no separate radial-descriptor pass); the
@@ -496,7 +487,7 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     kn<<<(n + 127) / 128, 128, 0, s>>>(
         g, (R)(rl * rl), (R)(ra * ra), (const typename V4<R>::T*)ctx->pos4, ctx->cell_sorted,
         ctx->start, ctx->nbr, ctx->cnt, ctx->status, ctx->status + 1, ctx->pairs, gate, rq,
-        (R*)ctx->qr, ctx->perm, x, ctx->pos2);
+        (R*)ctx->qr, ctx->perm, x);
     count_launch(ctx);
     ctx->radial_q_fused = fuse_q ? 1 : 0;
     if (gate) {
@@ -2184,7 +2175,7 @@ extern "C" int nep_compute_static(const nep_params* p, int64_t n_atoms, const do
     k_neighbors<float, false><<<(n + 127) / 128, 128, 0, s>>>(g, P.rcR2, P.rcA2, pos4, cell_sorted,
                                                              start, nbr, cnt, status, status + 1,
                                                              pairs, nullptr, RadCoef<float>{},
-                                                             nullptr, perm, xyz, nullptr);
+                                                             nullptr, perm, xyz);
     const int tiles = (n + TILE - 1) / TILE;
     k_nep<float><<<tiles, TILE, 0, s>>>(P, g, pos4, nbr, cnt, perm, xyz, facc, partials,
                                         site_energy, status, 0);
