@@ -1640,10 +1640,15 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
         for (int t = threadIdx.x; t < T * T * CSTR; t += TILE) s_coef[t] = coef[t];
     }
     __shared__ __align__(16) R s_w[H * WROW];
-    if (threadIdx.x == 0) s_max = 0;
     fill_network_rows<R>(s_w, P);
     fill_stencil<R>(s_off, g);
-    const int k = blockIdx.x * TILE + threadIdx.x;
+    // one tile of TILE cell-ordered atoms per iteration (one iteration per
+    // block unless the launch uses fewer blocks than tiles)
+    const int ntiles = (g.n + TILE - 1) / TILE;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    if (threadIdx.x == 0) s_max = 0;
+    __syncthreads();
+    const int k = tile * TILE + threadIdx.x;
     const size_t ld = (size_t)g.ld;
     const int na = k < g.n ? cnt[k].x : 0;
     atomicMax(&s_max, na);
@@ -1833,7 +1838,9 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
         if (site_energy) site_energy[i_caller] = e_site;
         if (bad) atomicOr(status, ST_NONFINITE);
     }
-    tile_partials<R>(e_site, w, wz, has_zbl, partials + (size_t)blockIdx.x * NPART);
+    tile_partials<R>(e_site, w, wz, has_zbl, partials + (size_t)tile * NPART);
+    __syncthreads();   // the staged entries and shared sums are reused by the next tile
+    }
 }
 
 // Radial pair forces by gathering: with the radial adjoint of both atoms,
@@ -1867,7 +1874,11 @@ __global__ void __launch_bounds__(TILE, sizeof(R) == 4 && !MS ? 7 : 1) k_radial_
     if (dispatch && (((*status & ST_CLOSE) != 0) != CLOSE)) return;
     __shared__ P4 s_off[27];
     fill_stencil<R>(s_off, g);
-    const int k = blockIdx.x * TILE + threadIdx.x;
+    // one tile of TILE cell-ordered atoms per iteration (one iteration per
+    // block unless the launch uses fewer blocks than tiles)
+    const int ntiles = (g.n + TILE - 1) / TILE;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int k = tile * TILE + threadIdx.x;
     const size_t ld = (size_t)g.ld;
     R w[9];
     double wz[9];
@@ -2010,7 +2021,9 @@ __global__ void __launch_bounds__(TILE, sizeof(R) == 4 && !MS ? 7 : 1) k_radial_
 #pragma unroll
         for (int t = 0; t < 9; ++t) w[t] *= R(0.5);
     }
-    tile_partials<R>(0.0, w, wz, false, partials + (size_t)blockIdx.x * NPART);
+    tile_partials<R>(0.0, w, wz, false, partials + (size_t)tile * NPART);
+    __syncthreads();   // tile_partials' shared sums are reused by the next tile
+    }
 }
 
 // Forces back to caller order (FP64), one thread per caller index: the
@@ -2195,10 +2208,12 @@ __global__ void __launch_bounds__(256) k_kick_thermo(int n, MassTab mt,
                                                      double* __restrict__ part)
 {
     constexpr bool half_kick = HALF, tensor = TENSOR;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
     double v2 = 0.0, va[3] = {0.0, 0.0, 0.0};
     long long vmb = 0;   // bit pattern of max |v|^2
-    if (i < n) {
+    // grid-stride over the atoms (the grid is a few blocks per SM, so that
+    // k_thermo_step reduces a few hundred partials, not one per 256 atoms);
+    // each thread's atoms are summed in a fixed order
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int t = species_of(mt, types, i);
         double vm = 0.0, vv[3];
 #pragma unroll
@@ -2211,11 +2226,12 @@ __global__ void __launch_bounds__(256) k_kick_thermo(int n, MassTab mt,
             }
             vm += vv[a] * vv[a];
         }
-        v2 = mt.m[t] * vm;
-        vmb = __double_as_longlong(vm);
+        v2 += mt.m[t] * vm;
+        const long long b = __double_as_longlong(vm);
+        vmb = b > vmb ? b : vmb;
         if constexpr (tensor)
 #pragma unroll
-            for (int a = 0; a < 3; ++a) va[a] = mt.m[t] * vv[a] * vv[a];
+            for (int a = 0; a < 3; ++a) va[a] += mt.m[t] * vv[a] * vv[a];
     }
     __shared__ double sh[KT_PART][8];
     if constexpr (LOWSUM) {

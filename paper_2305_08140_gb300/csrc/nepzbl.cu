@@ -53,6 +53,7 @@ struct GraphEntry {
 struct nep_ctx {
     int precision = NEP_FP32;
     int device = 0;
+    int sm_count = 0;                // multiprocessors of the device
     Model<float> mf;
     Model<double> md;
     nep_params hp;                   // hyperparameters, Z and masses (pointers cleared)
@@ -547,7 +548,10 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
             count_launch(ctx);
         }
     }
-    kang<<<tiles, TILE, stage_bytes, s>>>(P, g, p4, lnbr, lcnt, ctx->perm, x, (const R*)ctx->qr,
+    // with the dispatch the register kernel rarely runs on lattices: a grid of a
+    // few blocks per SM, looping over the tiles, makes its early return cheap
+    const int ang_grid = dispatch && tiles > 4 * ctx->sm_count ? 4 * ctx->sm_count : tiles;
+    kang<<<ang_grid, TILE, stage_bytes, s>>>(P, g, p4, lnbr, lcnt, ctx->perm, x, (const R*)ctx->qr,
                                           (typename V4<R>::T*)ctx->br, fa, ctx->partials,
                                           site_energy, ctx->status, stage_slots, coef,
                                           dispatch ? ctx->status + 2 : nullptr, TMEM_MAX_ANG);
@@ -560,7 +564,10 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
             P, g, p4, lnbr, lcnt, (const typename V4<R>::T*)ctx->br, fa,
             ctx->partials + (size_t)tiles * NPART, ctx->status, ctx->perm, x, true);
         count_launch(ctx);
-        k_radial_force<R, false, true><<<tiles, TILE, 0, s>>>(
+        // (the close-pair variant rarely runs: a grid of a few blocks per SM,
+        // looping over the tiles, makes its early return cheap)
+        const int close_grid = tiles < 4 * ctx->sm_count ? tiles : 4 * ctx->sm_count;
+        k_radial_force<R, false, true><<<close_grid > 0 ? close_grid : 1, TILE, 0, s>>>(
             P, g, p4, lnbr, lcnt, (const typename V4<R>::T*)ctx->br, fa,
             ctx->partials + (size_t)tiles * NPART, ctx->status, ctx->perm, x, true);
         count_launch(ctx);
@@ -828,6 +835,8 @@ int nep_init(const nep_params* p, int precision, nep_ctx** out)
         ctx->mt.acc[t] = EV_AMU / m;
     }
     cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->thermo, sizeof(double) * TH_N);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->thermo_backup, sizeof(double) * TH_N);
@@ -1073,6 +1082,14 @@ static auto kick_thermo_kernel(const nep_ctx* ctx, int half_kick, int tensor)
 // One velocity-Verlet step on stream s:
 //   [NHC(dt/2)] v += dt/2 F/m, x += dt v; F(x); v += dt/2 F/m [NHC(dt/2)];
 //   kinetic energy, max |v| and the next dt.
+// Blocks of k_kick_thermo (grid-stride): four per SM at most, so that the
+// single-block k_thermo_step reduces a few hundred partials.
+static int kick_blocks(const nep_ctx* ctx, int n)
+{
+    const int full = (n + 255) / 256, cap = 4 * (ctx->sm_count > 0 ? ctx->sm_count : 152);
+    return full < cap ? (full > 0 ? full : 1) : cap;
+}
+
 static int enqueue_step(nep_ctx* ctx, const Grid& g, nep_md_state* st, cudaStream_t s, int slot)
 {
     const int n = g.n;
@@ -1084,18 +1101,19 @@ static int enqueue_step(nep_ctx* ctx, const Grid& g, nep_md_state* st, cudaStrea
     int* gate = ctx->skin > 0.0 && !ctx->baro_on ? ctx->gate : nullptr;
     int rc = eval(ctx, g, st->xyz, st->types, st->forces, nullptr, s, slot, gate);
     if (rc) return rc;
-    kick_thermo_kernel(ctx, 1, ctx->baro_on)<<<nb, tb, 0, s>>>(n, ctx->mt, st->types, ctx->thermo,
-                                                               st->vel, st->forces, ctx->vpart);
+    const int nkt = kick_blocks(ctx, n);
+    kick_thermo_kernel(ctx, 1, ctx->baro_on)<<<nkt, tb, 0, s>>>(n, ctx->mt, st->types, ctx->thermo,
+                                                                st->vel, st->forces, ctx->vpart);
     count_launch(ctx);
     if (ctx->nhc_on) {
         enqueue_nhc(ctx, n, st->types, st->vel, s);
         // kinetic energy and speeds after the thermostat's scaling
-        kick_thermo_kernel(ctx, 0, ctx->baro_on)<<<nb, tb, 0, s>>>(n, ctx->mt, st->types,
-                                                                   ctx->thermo, st->vel,
-                                                                   st->forces, ctx->vpart);
+        kick_thermo_kernel(ctx, 0, ctx->baro_on)<<<nkt, tb, 0, s>>>(n, ctx->mt, st->types,
+                                                                    ctx->thermo, st->vel,
+                                                                    st->forces, ctx->vpart);
         count_launch(ctx);
     }
-    k_thermo_step<<<1, 256, 0, s>>>(ctx->vpart, nb, EV_AMU, ctx->thermo, 1, ctx->mt, gate);
+    k_thermo_step<<<1, 256, 0, s>>>(ctx->vpart, nkt, EV_AMU, ctx->thermo, 1, ctx->mt, gate);
     count_launch(ctx);
     return NEP_OK;
 }
@@ -1269,11 +1287,12 @@ int md_step(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
     th[TH_DTLAST] = st->dt_last;
     CK(cudaMemcpyAsync(ctx->thermo, th, sizeof(th), cudaMemcpyHostToDevice, s));
     {
-        const int tb = 256, nb = (int)((n + tb - 1) / tb);
-        kick_thermo_kernel(ctx, 0, ctx->baro_on)<<<nb, tb, 0, s>>>(
+        const int tb = 256;
+        kick_thermo_kernel(ctx, 0, ctx->baro_on)<<<kick_blocks(ctx, (int)n), tb, 0, s>>>(
             (int)n, ctx->mt, st->types, ctx->thermo, st->vel, st->forces, ctx->vpart);
         count_launch(ctx);
-        k_thermo_step<<<1, 256, 0, s>>>(ctx->vpart, nb, EV_AMU, ctx->thermo, 0, ctx->mt);
+        k_thermo_step<<<1, 256, 0, s>>>(ctx->vpart, kick_blocks(ctx, (int)n), EV_AMU, ctx->thermo,
+                                        0, ctx->mt);
         count_launch(ctx);
         if (ctx->nhc_on && ctx->nhc_counted != (int)n) {
             k_group_count<<<1, 256, 0, s>>>((int)n, ctx->nhc_group, ctx->nhc);
