@@ -453,23 +453,45 @@ __global__ void __launch_bounds__(256) k_cell_finalize_w(
 // The 27 stencil offsets (cell-edge multiples) of the neighbour codes, in
 // shared memory; filled by the first 27 threads of the block.
 template <typename R>
+__device__ __forceinline__ typename V4<R>::T stencil_entry(int code, const Grid& g)
+{
+    int a = code / 9, b = (code / 3) % 3, c = code % 3;
+    typename V4<R>::T o;
+    if (g.tric) {
+        o.x = (R)stencil_off_tric(g, a - 1, b - 1, c - 1, 0);
+        o.y = (R)stencil_off_tric(g, a - 1, b - 1, c - 1, 1);
+        o.z = (R)stencil_off_tric(g, a - 1, b - 1, c - 1, 2);
+    } else {
+        o.x = (R)((a - 1) * g.lc[0]);
+        o.y = (R)((b - 1) * g.lc[1]);
+        o.z = (R)((c - 1) * g.lc[2]);
+    }
+    o.w = R(0);
+    return o;
+}
+template <typename R>
 __device__ __forceinline__ void fill_stencil(typename V4<R>::T* tab, const Grid& g)
 {
+    if (threadIdx.x < 27) tab[threadIdx.x] = stencil_entry<R>(threadIdx.x, g);
+    __syncthreads();
+}
+
+// The same offsets split by component (three 27-entry arrays, the same
+// values).  A warp's lookups with arbitrary codes then touch 27 distinct
+// banks per component (one shared-memory wavefront each), where 16-byte
+// entries, one per code, conflict (~6 wavefronts per warp-wide lookup).
+template <typename R>
+struct StencilSplit {
+    R x[27], y[27], z[27];
+};
+template <typename R>
+__device__ __forceinline__ void fill_stencil_split(StencilSplit<R>& t, const Grid& g)
+{
     if (threadIdx.x < 27) {
-        int code = threadIdx.x;
-        int a = code / 9, b = (code / 3) % 3, c = code % 3;
-        typename V4<R>::T o;
-        if (g.tric) {
-            o.x = (R)stencil_off_tric(g, a - 1, b - 1, c - 1, 0);
-            o.y = (R)stencil_off_tric(g, a - 1, b - 1, c - 1, 1);
-            o.z = (R)stencil_off_tric(g, a - 1, b - 1, c - 1, 2);
-        } else {
-            o.x = (R)((a - 1) * g.lc[0]);
-            o.y = (R)((b - 1) * g.lc[1]);
-            o.z = (R)((c - 1) * g.lc[2]);
-        }
-        o.w = R(0);
-        tab[code] = o;
+        const typename V4<R>::T o = stencil_entry<R>(threadIdx.x, g);
+        t.x[threadIdx.x] = o.x;
+        t.y[threadIdx.x] = o.y;
+        t.z[threadIdx.x] = o.z;
     }
     __syncthreads();
 }
@@ -1872,8 +1894,8 @@ __global__ void __launch_bounds__(TILE, sizeof(R) == 4 && !MS ? 7 : 1) k_radial_
     // one without the close-pair branch takes the evaluations without close
     // pairs
     if (dispatch && (((*status & ST_CLOSE) != 0) != CLOSE)) return;
-    __shared__ P4 s_off[27];
-    fill_stencil<R>(s_off, g);
+    __shared__ StencilSplit<R> s_off;
+    fill_stencil_split<R>(s_off, g);
     // one tile of TILE cell-ordered atoms per iteration (one iteration per
     // block unless the launch uses fewer blocks than tiles)
     const int ntiles = (g.n + TILE - 1) / TILE;
@@ -1907,8 +1929,9 @@ __global__ void __launch_bounds__(TILE, sizeof(R) == 4 && !MS ? 7 : 1) k_radial_
                 rj0_n = bp[3 * m1]; rj1_n = bp[3 * m1 + 1]; rj2_n = bp[3 * m1 + 2];
             }
             if (s + 2 < total) ent_nn = nbr[(size_t)list_slot(s + 2, na, M) * ld + k];
-            const P4 off = s_off[ent & 31];
-            R dx = rj0.x - ri0.x + off.x, dy = rj0.y - ri0.y + off.y, dz = rj0.z - ri0.z + off.z;
+            const int code = ent & 31;
+            R dx = rj0.x - ri0.x + s_off.x[code], dy = rj0.y - ri0.y + s_off.y[code],
+              dz = rj0.z - ri0.z + s_off.z[code];
             R r2 = dx * dx + dy * dy + dz * dz;
             if (r2 >= P.rcR2) continue;   // beyond r_c (lists built with a skin)
             if constexpr (CLOSE)
@@ -1989,8 +2012,9 @@ __global__ void __launch_bounds__(TILE, sizeof(R) == 4 && !MS ? 7 : 1) k_radial_
                 bi0 = bp[3 * mi]; bi1 = bp[3 * mi + 1]; bi2 = bp[3 * mi + 2];
             }
             if (s + 2 < total) ent_nn = nbr[(size_t)list_slot(s + 2, na, M) * ld + k];
-            const P4 off = s_off[ent & 31];
-            R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
+            const int code = ent & 31;
+            R dx = pj.x - pi.x + s_off.x[code], dy = pj.y - pi.y + s_off.y[code],
+              dz = pj.z - pi.z + s_off.z[code];
             R r2 = dx * dx + dy * dy + dz * dz;
             if (r2 >= P.rcR2) continue;   // beyond r_c (lists built with a skin)
             close_pair_fp64<R>(P.zbl_r2 * P.zbl_r2, g, x64, perm, k, ent >> 5, dx, dy, dz, r2);

@@ -105,12 +105,13 @@ __device__ __forceinline__ void tm_st24(uint32_t tb, int n, const float* v)
 // turn (columns n * 24 + 8 GR), linear index c = 5 GR + n; buf[0] holds
 // c = 0 on entry, loaded and not yet waited for; c + 1 (into buf[(c+1) & 1])
 // is loaded while c is used.  Only the current group's harmonics Y_lm and
-// G_lm = sum_n a_nlm g_n are live: the tangential part sum_lm G_lm grad Y_lm
-// is added group by group, and the radial part
-//   S = sum_n [g_n' sum_lm a_nlm Y_lm - (g_n / r) sum_lm l a_nlm Y_lm]
-// is accumulated per channel (P_n, Q_n).  With `prefetch` (warp-uniform)
-// c = 0 is loaded again into buf[0] for the next pair once the last group
-// (c = 14, also in buf[0]) has been used.
+// the channel sums G_lm = sum_n a_nlm g_n, H_lm = sum_n a_nlm g_n' are live:
+// the tangential part sum_lm G_lm grad Y_lm and the radial part
+//   S = sum_lm Y_lm (H_lm - (l / r) G_lm)
+// are added group by group (the same sum as sum_n [g_n' sum_lm a_nlm Y_lm -
+// (g_n / r) sum_lm l a_nlm Y_lm], in fewer operations).  With `prefetch`
+// (warp-uniform) c = 0 is loaded again into buf[0] for the next pair once the
+// last group (c = 14, also in buf[0]) has been used.
 __device__ __forceinline__ void force_pair_ang_tm(const Model<float>& P, float r, float inv_r,
                                                   float ux, float uy, float uz, uint32_t tb,
                                                   float (&buf)[2][8], bool prefetch,
@@ -131,9 +132,9 @@ __device__ __forceinline__ void force_pair_ang_tm(const Model<float>& P, float r
             dgn[n] = dfc * ab.x + fc * dxdr * ab.y;
         }
     }
-    float Pn[NA], Qn[NA];
-#pragma unroll
-    for (int n = 0; n < NA; ++n) { Pn[n] = 0.f; Qn[n] = 0.f; }
+    // -l / r for l = 1..4
+    const float m1 = -inv_r, m2 = -2.f * inv_r, m3 = -3.f * inv_r, m4 = -4.f * inv_r;
+    float sang = 0.f;
     float vx = 0.f, vy = 0.f, vz = 0.f;
 #pragma unroll
     for (int GR = 0; GR < 3; ++GR) {
@@ -146,9 +147,9 @@ __device__ __forceinline__ void force_pair_ang_tm(const Model<float>& P, float r
         if (GR == 0) nepm::harmonics_group<0>(gx, gy, gz, Y);
         if (GR == 1) nepm::harmonics_group<1>(gx, gy, gz, Y);
         if (GR == 2) nepm::harmonics_group<2>(gx, gy, gz, Y);
-        float2 G2[4];
+        float2 G2[4], H2[4];
 #pragma unroll
-        for (int p = 0; p < 4; ++p) G2[p] = f2(0.f, 0.f);
+        for (int p = 0; p < 4; ++p) { G2[p] = f2(0.f, 0.f); H2[p] = f2(0.f, 0.f); }
 #pragma unroll
         for (int n = 0; n < NA; ++n) {
             const int c = GR * NA + n;
@@ -158,33 +159,24 @@ __device__ __forceinline__ void force_pair_ang_tm(const Model<float>& P, float r
                 tm_ld8(tb + (uint32_t)(n1 * NLM + 8 * g1), buf[(c + 1) & 1]);
             }
             const float* v = buf[c & 1];
-            const float2 gg = f2(gn[n], gn[n]);
+            const float2 gg = f2(gn[n], gn[n]), hh = f2(dgn[n], dgn[n]);
 #pragma unroll
-            for (int p = 0; p < 4; ++p) G2[p] = fma2(f2(v[2 * p], v[2 * p + 1]), gg, G2[p]);
-            // sum a Y over the group's lower and upper l (group 0: l = 1 for
-            // j < 3, else 2; group 1: l = 3 for j < 7, else 4; group 2: l = 4):
-            // pairs (0,1) and (4,5)+(6,7) are whole, pair (2,3) (group 0) or
-            // (6,7) (group 1) splits
-            float sa, sb;
-            const float2 t01 = mul2(f2(v[0], v[1]), f2(Y[0], Y[1]));
-            const float2 t23 = mul2(f2(v[2], v[3]), f2(Y[2], Y[3]));
-            const float2 t45 = mul2(f2(v[4], v[5]), f2(Y[4], Y[5]));
-            const float2 t67 = mul2(f2(v[6], v[7]), f2(Y[6], Y[7]));
-            if (GR == 0) {
-                sa = (t01.x + t01.y) + t23.x;
-                sb = (t23.y + t45.x) + (t45.y + (t67.x + t67.y));
-            } else if (GR == 1) {
-                sa = ((t01.x + t01.y) + (t23.x + t23.y)) + ((t45.x + t45.y) + t67.x);
-                sb = t67.y;
-            } else {
-                sa = 0.f;
-                sb = ((t01.x + t01.y) + (t23.x + t23.y)) + ((t45.x + t45.y) + (t67.x + t67.y));
+            for (int p = 0; p < 4; ++p) {
+                const float2 v2 = f2(v[2 * p], v[2 * p + 1]);
+                G2[p] = fma2(v2, gg, G2[p]);
+                H2[p] = fma2(v2, hh, H2[p]);
             }
-            const float la = GR == 0 ? 1.f : 3.f;
-            const float lb = GR == 0 ? 2.f : 4.f;
-            Pn[n] += sa + sb;
-            Qn[n] += la * sa + lb * sb;
         }
+        // radial part of the group; the degree l of each lm (group 0: l = 1
+        // for lm < 3, else 2; group 1: l = 3 for lm < 15, else 4; group 2: 4)
+        const float2 L[4] = {GR == 0 ? f2(m1, m1) : (GR == 1 ? f2(m3, m3) : f2(m4, m4)),
+                             GR == 0 ? f2(m1, m2) : (GR == 1 ? f2(m3, m3) : f2(m4, m4)),
+                             GR == 0 ? f2(m2, m2) : (GR == 1 ? f2(m3, m3) : f2(m4, m4)),
+                             GR == 0 ? f2(m2, m2) : (GR == 1 ? f2(m3, m4) : f2(m4, m4))};
+        float2 s2 = mul2(f2(Y[0], Y[1]), fma2(L[0], G2[0], H2[0]));
+#pragma unroll
+        for (int p = 1; p < 4; ++p) s2 = fma2(f2(Y[2 * p], Y[2 * p + 1]), fma2(L[p], G2[p], H2[p]), s2);
+        sang += s2.x + s2.y;
         const float G[8] = {G2[0].x, G2[0].y, G2[1].x, G2[1].y, G2[2].x, G2[2].y, G2[3].x, G2[3].y};
         if (GR == 0) nepm::harmonics_grad_dot_group<0>(gx, gy, gz, G, vx, vy, vz);
         if (GR == 1) nepm::harmonics_grad_dot_group<1>(gx, gy, gz, G, vx, vy, vz);
@@ -192,9 +184,6 @@ __device__ __forceinline__ void force_pair_ang_tm(const Model<float>& P, float r
     }
     // the next pair's c = 0: buf[0] held the last group (3 NA is odd), now used
     if (prefetch) tm_ld8(tb, buf[0]);
-    float sang = 0.f;
-#pragma unroll
-    for (int n = 0; n < NA; ++n) sang += dgn[n] * Pn[n] - inv_r * gn[n] * Qn[n];
     fx = sang * ux + vx * inv_r;
     fy = sang * uy + vy * inv_r;
     fz = sang * uz + vz * inv_r;
