@@ -5,9 +5,10 @@
 // values) for every pair; held in registers it limits the kernel to two
 // blocks per SM.  Here each block allocates 128 columns of Tensor Memory
 // (lane = thread, column n * 24 + lm).  The descriptor sums A are formed in
-// two passes over the atom's angular pairs (radial channels 0-2, then 3-4, so
-// that at most 72 sums are held in registers), each pass storing its channels
-// to Tensor Memory; the network turns them into the adjoint in place; the
+// one pass over the atom's angular pairs: radial channels 0-2 in registers (72
+// sums, stored to Tensor Memory at the end), channels 3-4 accumulated in their
+// Tensor-Memory columns (read, updated and written back per pair); the
+// network turns them into the adjoint in place; the
 // pair loop streams the adjoint back in 8-column groups (one group in flight
 // while the previous one is used).  At <= 128 registers per thread four
 // blocks fit per SM (16 warps), which is also the most the 512 columns of
@@ -189,78 +190,123 @@ __device__ __forceinline__ void force_pair_ang_tm(const Model<float>& P, float r
     fz = sang * uz + vz * inv_r;
 }
 
-// Descriptor pass over the atom's angular pairs for radial channels
-// [N0, N1): A_nlm = sum_j g_n(r_ij) Y_lm(u_ij) in registers, then the
-// channel's part of the descriptor (q_nl = sum_m A_nlm^2, q_n^4b) to shared
-// memory (s_q[nu - NR][TILE], this thread's column) and the sums to Tensor
+// A_nlm += g v for the 8 columns at a (this lane's Tensor-Memory row): loaded,
+// updated and stored back (warp-collective; the store is not waited for).
+__device__ __forceinline__ void tm_rmw8(uint32_t a, float g, const float* Y)
+{
+    float v[8];
+    tm_ld8(a, v);
+    tm_wait_ld8(v);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const float2 t = fma2(f2(g, g), f2(Y[2 * p], Y[2 * p + 1]), f2(v[2 * p], v[2 * p + 1]));
+        v[2 * p] = t.x;
+        v[2 * p + 1] = t.y;
+    }
+    tm_st8(a, v);
+}
+
+// The descriptor sums A_nlm = sum_j g_n(r_ij) Y_lm(u_ij) over the atom's
+// angular pairs in one pass: radial channels 0-2 in registers (72 sums),
+// channels 3-4 in their Tensor-Memory columns, read, updated and written back
+// per pair and harmonic group (lm 0-7, 8-15, 16-23).  The Tensor-Memory
+// accesses are warp-collective, so the loop runs to the warp's largest pair
+// count (nmax), a lane's missing pairs adding zero.  Then each channel's part
+// of the descriptor (q_nl = sum_m A_nlm^2, q_n^4b) to shared memory
+// (s_q[nu - NR][TILE], this thread's column) and channels 0-2 to Tensor
 // Memory (stores not waited for).
-template <int N0, int N1, typename Entry>
-__device__ __forceinline__ void ang_desc_pass(const Model<float>& P, const Grid& g,
-                                              const float4* __restrict__ pos4,
-                                              const float4* s_off, int na,
+template <typename Entry>
+__device__ __forceinline__ void ang_desc_sums(const Model<float>& P, const float4* __restrict__ pos4,
+                                              const StencilSplit<float>& s_off, int na, int nmax,
                                               const float4 pi, Entry entry, uint32_t tb,
                                               float* s_q)
 {
-    constexpr int NN = N1 - N0;
+    constexpr int NN = 3;   // channels in registers
     float2 A[NN][NLM / 2];   // A_nlm in packed pairs (lm, lm + 1)
 #pragma unroll
     for (int n = 0; n < NN; ++n)
 #pragma unroll
         for (int p = 0; p < NLM / 2; ++p) A[n][p] = f2(0.f, 0.f);
+    {
+        float z[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) z[t] = 0.f;
+#pragma unroll
+        for (int c = NN * NLM; c < NA * NLM; c += 8) tm_st8(tb + (uint32_t)c, z);
+    }
     int ent_n = na > 0 ? entry(0) : 0;
     float4 pj_n = na > 0 ? pos4[ent_n >> 5] : pi;
-    for (int s = 0; s < na; ++s) {
+    for (int s = 0; s < nmax; ++s) {
+        const bool act = s < na;
         const int ent = ent_n;
         const float4 pj = pj_n;
         if (s + 1 < na) {
             ent_n = entry(s + 1);
             pj_n = pos4[ent_n >> 5];
         }
-        const float4 off = s_off[ent & 31];
-        float dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
-        float r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 >= P.rcA2) continue;   // beyond r_c^A (lists built with a skin)
+        const int code = ent & 31;
+        float dx = pj.x - pi.x + s_off.x[code], dy = pj.y - pi.y + s_off.y[code],
+              dz = pj.z - pi.z + s_off.z[code];
+        if (!act) { dx = 1.f; dy = 0.f; dz = 0.f; }   // placeholder pair, adds zero
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        // beyond r_c^A (lists built with a skin) or a placeholder: g_n = 0
+        const bool in = act && r2 < P.rcA2;
         const float inv_r = nepm::nep_rsqrt(r2);
         const float r = r2 * inv_r;
         float Tk[KA], dT[KA], fc, dfc, dxdr;
         nepm::cheb<KA, false>(r, P.inv_rcA, Tk, dT, fc, dfc, dxdr);
-        float gn[NN];
+        const float fcm = in ? fc : 0.f;
+        float gn[NA];
 #pragma unroll
-        for (int n = 0; n < NN; ++n) {
-            float acc = P.CA[N0 + n];
+        for (int n = 0; n < NA; ++n) {
+            float acc = P.CA[n];
 #pragma unroll
-            for (int kk = 0; kk < KA; ++kk) acc += P.hA[(N0 + n) * KA + kk] * Tk[kk];
-            gn[n] = fc * acc;
+            for (int kk = 0; kk < KA; ++kk) acc += P.hA[n * KA + kk] * Tk[kk];
+            gn[n] = fcm * acc;
         }
         const float ux = dx * inv_r, uy = dy * inv_r, uz = dz * inv_r;
-        float Y[NLM];
-        nepm::harmonics_l12(ux, uy, uz, Y);
+        // the previous pair's stores to the channel 3-4 columns are complete
+        // before they are read again
+        tm_wait_st();
 #pragma unroll
-        for (int n = 0; n < NN; ++n)
+        for (int GR = 0; GR < 3; ++GR) {
+            float gx = ux, gy = uy, gz = uz;
+            asm volatile("" : "+f"(gx), "+f"(gy), "+f"(gz));
+            float Y[8];
+            if (GR == 0) nepm::harmonics_group<0>(gx, gy, gz, Y);
+            if (GR == 1) nepm::harmonics_group<1>(gx, gy, gz, Y);
+            if (GR == 2) nepm::harmonics_group<2>(gx, gy, gz, Y);
 #pragma unroll
-            for (int p = 0; p < 4; ++p)
-                A[n][p] = fma2(f2(gn[n], gn[n]), f2(Y[2 * p], Y[2 * p + 1]), A[n][p]);
-        nepm::harmonics_l34(ux, uy, uz, Y);
+            for (int n = 0; n < NN; ++n)
 #pragma unroll
-        for (int n = 0; n < NN; ++n)
+                for (int p = 0; p < 4; ++p)
+                    A[n][4 * GR + p] = fma2(f2(gn[n], gn[n]), f2(Y[2 * p], Y[2 * p + 1]),
+                                            A[n][4 * GR + p]);
 #pragma unroll
-            for (int p = 4; p < NLM / 2; ++p)
-                A[n][p] = fma2(f2(gn[n], gn[n]), f2(Y[2 * p], Y[2 * p + 1]), A[n][p]);
+            for (int n = NN; n < NA; ++n) tm_rmw8(tb + (uint32_t)(n * NLM + 8 * GR), gn[n], Y);
+        }
     }
+    // channels 3-4: the final sums back from Tensor Memory
+    tm_wait_st();
 #pragma unroll
-    for (int n = 0; n < NN; ++n) {
+    for (int n = 0; n < NA; ++n) {
         float An[NLM];
+        if (n < NN) {
 #pragma unroll
-        for (int p = 0; p < NLM / 2; ++p) { An[2 * p] = A[n][p].x; An[2 * p + 1] = A[n][p].y; }
+            for (int p = 0; p < NLM / 2; ++p) { An[2 * p] = A[n][p].x; An[2 * p + 1] = A[n][p].y; }
+        } else {
+            tm_ld24(tb, n, An);
+            tm_wait_ld24(An);
+        }
 #pragma unroll
         for (int l = 1; l <= LM; ++l) {
             float v = 0.f;
 #pragma unroll
             for (int lm = l * l - 1; lm < (l + 1) * (l + 1) - 1; ++lm) v += An[lm] * An[lm];
-            s_q[((l - 1) * NA + N0 + n) * TILE + threadIdx.x] = v;
+            s_q[((l - 1) * NA + n) * TILE + threadIdx.x] = v;
         }
-        s_q[(LM * NA + N0 + n) * TILE + threadIdx.x] = nepm::fourbody(&An[3], (float*)nullptr);
-        tm_st24(tb, N0 + n, An);
+        s_q[(LM * NA + n) * TILE + threadIdx.x] = nepm::fourbody(&An[3], (float*)nullptr);
+        if (n < NN) tm_st24(tb, n, An);
     }
 }
 
@@ -290,7 +336,7 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
     // range, whose FP64 branches this kernel does not carry)
     if (*ang_max > ang_lim || (*status & ST_CLOSE)) return;
     using A_ = Acc<float>;
-    __shared__ float4 s_off[27];
+    __shared__ StencilSplit<float> s_off;
     __shared__ int s_max;
     __shared__ uint32_t s_tmem;
     __shared__ __align__(16) float s_w[H * WROW];
@@ -307,7 +353,7 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
     if (threadIdx.x == 0) s_max = 0;
     fill_network_rows<float>(s_w, P);
     tm_fence_before();
-    fill_stencil<float>(s_off, g);   // ends with __syncthreads
+    fill_stencil_split<float>(s_off, g);   // ends with __syncthreads
     tm_fence_after();
     const uint32_t tb = s_tmem + ((uint32_t)(warp * 32) << 16);   // this warp's 32 lanes
     const int k = blockIdx.x * TILE + threadIdx.x;
@@ -324,12 +370,12 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
     };
     const float4 pi = valid ? pos4[k] : make_float4(0.f, 0.f, 0.f, 0.f);
 
-    // descriptor vector: angular part in two passes over the pairs (channels
-    // 0-2, 3-4; the sums A to Tensor Memory, q via shared memory), radial part
-    // from the neighbour kernel
+    // descriptor vector: angular part in one pass over the pairs (the sums A
+    // to Tensor Memory, q via shared memory), radial part from the neighbour
+    // kernel
     float* s_q = reinterpret_cast<float*>(s_dyn + TM_SQ_OFF);
-    ang_desc_pass<0, 3>(P, g, pos4, s_off, na, pi, entry, tb, s_q);
-    ang_desc_pass<3, NA>(P, g, pos4, s_off, na, pi, entry, tb, s_q);
+    const int nmax = __reduce_max_sync(0xffffffffu, na);
+    ang_desc_sums(P, pos4, s_off, na, nmax, pi, entry, tb, s_q);
     float q[D];
 #pragma unroll
     for (int n = 0; n < NR; ++n) q[n] = valid ? qr[(size_t)n * ld + k] : 0.f;
@@ -405,7 +451,6 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
     for (int t = 0; t < 9; ++t) wv[t] = 0.f;
     bool bad = !isfinite(U);
     const int i_caller = valid ? perm[k] : 0;
-    const int nmax = __reduce_max_sync(0xffffffffu, na);
     int ent_n = na > 0 ? entry(0) : 0;
     float4 pj_n = na > 0 ? pos4[ent_n >> 5] : pi;
     float buf[2][8];   // two 8-column groups of the adjoint (see force_pair_ang_tm)
@@ -419,8 +464,9 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
             pj_n = pos4[ent_n >> 5];
         }
         const int m = ent >> 5;
-        const float4 off = s_off[ent & 31];
-        float dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
+        const int code = ent & 31;
+        float dx = pj.x - pi.x + s_off.x[code], dy = pj.y - pi.y + s_off.y[code],
+              dz = pj.z - pi.z + s_off.z[code];
         if (!act) { dx = 1.f; dy = 0.f; dz = 0.f; }   // placeholder pair, result unused
         float r2 = dx * dx + dy * dy + dz * dz;
         const bool in = act && r2 < P.rcA2;
