@@ -598,7 +598,12 @@ def run_ours(args):
                                          "position and counts 25 B per atom, 56 B per radial "
                                          "pair), not DRAM",
                      "kernel_share": stats["timed_ms"] / ms if ms > 0 else None,
-                     "pairs_radial": pr, "pairs_angular": pa},
+                     "pairs_radial": pr, "pairs_angular": pa,
+                     # tiles of 128 atoms of the last graph chunk, and those that
+                     # held a dense clump and ran in the register angular kernel (the
+                     # rest kept their angular state in Tensor Memory)
+                     "angular_tiles": stats["angular_tiles"],
+                     "angular_tiles_register": stats["angular_tiles_register"]},
         "step_hbm": {
             "bytes_per_atom_step": BYTES_STEP_ALG,
             "achieved_gbs": BYTES_STEP_ALG * n * args.steps / (ms * 1e-3) / 1e9,

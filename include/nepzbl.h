@@ -265,14 +265,23 @@ typedef struct nep_stats {
     int32_t radial_q_in_neighbor_kernel;  /* 1: the last evaluation summed the radial
                                              descriptor in the neighbour-list kernel (one
                                              species, lists rebuilt every step) */
-    int32_t angular_state_in_tmem;        /* 1: the last evaluation kept the angular
-                                             descriptor sums and adjoint in Tensor Memory
-                                             (FP32, one species, at most 48 angular
-                                             neighbours on every atom) */
+    int32_t angular_state_in_tmem;        /* 1: the last evaluation (or MD graph chunk)
+                                             kept the angular descriptor sums and adjoint
+                                             of some of its atoms in Tensor Memory (FP32,
+                                             one species: the tiles of 128 cell-ordered
+                                             atoms with at most 48 angular neighbours on
+                                             every atom and no pair inside the outer ZBL
+                                             radius) */
     int32_t angular_tmem_blocks_per_sm;   /* resident blocks per SM of that kernel (from
                                              the occupancy check; 0: not usable) */
     int32_t nbr_z_slices;                 /* NEP_OPT_NBR_SLICES in effect */
     int32_t nbr_chunk;                    /* NEP_OPT_NBR_CHUNK in effect */
+    int64_t angular_tiles;                /* tiles of 128 cell-ordered atoms in the last
+                                             evaluation (MD: summed over the last graph
+                                             chunk's steps) */
+    int64_t angular_tiles_register;       /* of those, the tiles the register angular
+                                             kernel took (all of them for FP64 or several
+                                             species) */
 } nep_stats;
 
 int nep_get_stats(const nep_ctx* ctx, nep_stats* out);

@@ -17,7 +17,8 @@
 //                  pair p = t_i * T + t_j: radial h (c/2) [0, 45), C [45, 50),
 //                  angular h [52, 97), C [97, 102)
 //   br[(k * T + t) * 3]  radial adjoint of atom k contracted with the
-//                  coefficients of neighbour species t (b_0..b_8, B0, 0, 0)
+//                  coefficients of neighbour species t (b_0..b_8, B0, 0, 0);
+//                  one species: the record of atom k (see rec_store)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -38,9 +39,29 @@ constexpr int C_RAD = 0, C_ANG = 52;   // radial / angular block offsets
 // status bits
 constexpr int ST_OVERFLOW = 1, ST_NONFINITE = 2, ST_FORCE_RANGE = 4, ST_BADTYPE = 8;
 // the evaluation has a pair closer than the outer ZBL radius (set by the
-// radial-descriptor pass of the FP32 path); the kernels without the ZBL and
-// close-pair branches then leave the evaluation to the ones with them
+// radial-descriptor pass of the FP32 path)
 constexpr int ST_CLOSE = 16;
+
+// Per-tile kernel choice (FP32, one species).  The radial-descriptor pass
+// (k_neighbors' second pass, or k_radial_q with a Verlet skin; blocks of TILE
+// atoms, so block b is tile b) ORs into tflag[tile]: TILE_CLOSE when an atom of
+// the tile has a pair closer than the outer ZBL radius, TILE_DENSE when one has
+// more than TILE_ANG_LIM angular neighbours.  The angular kernel without the
+// ZBL and close-pair branches (k_nep_ang_tm) takes the tiles with neither bit,
+// the register kernel k_nep_ang the others; the radial-force instantiation
+// without the close-pair branch the tiles without TILE_CLOSE.  Each tile is
+// done by exactly one kernel of each pair, so its forces and partial sums are
+// those of the kernel that would do the whole evaluation.
+constexpr int TILE_CLOSE = 1, TILE_DENSE = 2;
+constexpr int TILE_ANG_LIM = 48;
+// Behind the ntiles flags, tflag[ntiles] counts the flagged tiles and
+// tflag[ntiles + 1 + i] lists them (in the order they were first flagged; the
+// kernels that take few tiles loop over this list, and every tile's result is
+// the same whichever block takes it).
+__device__ __forceinline__ void tile_mark(int* __restrict__ tflag, int ntiles, int tile, int bits)
+{
+    if (atomicOr(&tflag[tile], bits) == 0) tflag[ntiles + 1 + atomicAdd(&tflag[ntiles], 1)] = tile;
+}
 
 template <typename R> struct V4 { using T = float4; };
 template <> struct V4<double> { using T = double4_32a; };
@@ -582,7 +603,8 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                                                    const int* __restrict__ gate,
                                                    const RadCoef<R> rq, R* __restrict__ qr,
                                                    const int* __restrict__ perm,
-                                                   const double* __restrict__ x64)
+                                                   const double* __restrict__ x64,
+                                                   int* __restrict__ tflag = nullptr)
 {
     using P4 = typename V4<R>::T;
     if (gate && *gate == 0) return;   // lists still valid (Verlet skin)
@@ -769,6 +791,9 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                 qr[(size_t)n * ld + k] = acc;
             }
             if (close) atomicOr(status, ST_CLOSE);
+            // this tile's kernel choice (blocks of TILE atoms: block = tile)
+            const int bits = (close ? TILE_CLOSE : 0) | (sa > TILE_ANG_LIM ? TILE_DENSE : 0);
+            if (tflag && bits) tile_mark(tflag, (g.n + TILE - 1) / TILE, blockIdx.x, bits);
         }
     }
     // statistics: block maxima and pair sums
@@ -907,6 +932,17 @@ template <> struct Acc<double> {
     __device__ static __forceinline__ double value(double v) { return v; }
 };
 
+// The FP32 one-species radial record of atom k (position and radial adjoint,
+// written by the angular kernels, gathered per neighbour by k_radial_force):
+// rec[3k] = (x, y, z, b_8), rec[3k + 1] = (b_0 + B0, b_1, b_2, b_3),
+// rec[3k + 2] = (b_4..b_7).
+__device__ __forceinline__ void rec_store(float4* __restrict__ rec, size_t k, const float4 r0,
+                                          const float4 r1, const float4 r2)
+{
+    rec[3 * k] = r0;
+    rec[3 * k + 1] = r1;
+    rec[3 * k + 2] = r2;
+}
 // ZBL pair term of Eq. 2-4 with the Tersoff switch, in FP64: U and dU/dr.
 __device__ __forceinline__ void zbl_pair(double r, double k, double inv_a, double r1, double r2,
                                          double& U, double& dU)
@@ -1461,7 +1497,8 @@ __global__ void __launch_bounds__(128) k_radial_q(const Model<R> P, const Grid g
                                                   const R* __restrict__ coef,
                                                   const int* __restrict__ perm,
                                                   const double* __restrict__ x64,
-                                                  int* __restrict__ status)
+                                                  int* __restrict__ status,
+                                                  int* __restrict__ tflag = nullptr)
 {
     using P4 = typename V4<R>::T;
     constexpr int NTS = MS ? NT_MAX : 1;
@@ -1521,6 +1558,12 @@ __global__ void __launch_bounds__(128) k_radial_q(const Model<R> P, const Grid g
     }
     if (act_cnt) act_cnt[k] = make_int2(a_na, a_nro);
     if (close) atomicOr(status, ST_CLOSE);
+    if (tflag) {
+        // this tile's kernel choice (blocks of TILE atoms: block = tile)
+        const int bits = (close ? TILE_CLOSE : 0) |
+                         ((act_cnt ? a_na : na) > TILE_ANG_LIM ? TILE_DENSE : 0);
+        if (bits) tile_mark(tflag, (g.n + TILE - 1) / TILE, blockIdx.x, bits);
+    }
     R q[NR];
     if constexpr (MS) {
         const int ti = (int)pi.w;
@@ -1641,13 +1684,12 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
                                                   double* __restrict__ site_energy,
                                                   int* __restrict__ status, int stage_slots,
                                                   const R* __restrict__ coef,
-                                                  const int* __restrict__ ang_max = nullptr,
-                                                  int ang_lim = 0)
+                                                  const int* __restrict__ tflag = nullptr,
+                                                  int* __restrict__ ntiles_done = nullptr,
+                                                  int tmask = 0)
 {
-    // with ang_max: this launch handles only evaluations with more than
-    // ang_lim angular neighbours on some atom or with a pair closer than the
-    // outer ZBL radius (k_nep_ang_tm takes the others)
-    if (ang_max && *ang_max <= ang_lim && !(*status & ST_CLOSE)) return;
+    // with tflag: this launch takes only the tiles with a bit of tmask in their
+    // flag (k_nep_ang_tm takes the others) and counts them
     using A_ = Acc<R>;
     using P4 = typename V4<R>::T;
     __shared__ P4 s_off[27];
@@ -1667,7 +1709,14 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
     // one tile of TILE cell-ordered atoms per iteration (one iteration per
     // block unless the launch uses fewer blocks than tiles)
     const int ntiles = (g.n + TILE - 1) / TILE;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // with tflag: the listed tiles (see tile_mark)
+    const int nlist = tflag ? tflag[ntiles] : ntiles;
+    for (int it = blockIdx.x; it < nlist; it += gridDim.x) {
+    const int tile = tflag ? tflag[ntiles + 1 + it] : it;
+    if (tflag) {
+        if (!(tflag[tile] & tmask)) continue;   // the whole block: the flag is the tile's
+        if (threadIdx.x == 0) atomicAdd(ntiles_done, 1);
+    }
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
     const int k = tile * TILE + threadIdx.x;
@@ -1886,20 +1935,23 @@ __global__ void __launch_bounds__(TILE, sizeof(R) == 4 && !MS ? 7 : 1) k_radial_
                                                        int* __restrict__ status,
                                                        const int* __restrict__ perm,
                                                        const double* __restrict__ x64,
-                                                       bool dispatch = false)
+                                                       const int* __restrict__ tflag = nullptr)
 {
     using A_ = Acc<R>;
     using P4 = typename V4<R>::T;
-    // dispatch (FP32, one species): both instantiations are launched and the
-    // one without the close-pair branch takes the evaluations without close
-    // pairs
-    if (dispatch && (((*status & ST_CLOSE) != 0) != CLOSE)) return;
+    // with tflag (FP32, one species): both instantiations are launched, the
+    // one without the close-pair branch takes the tiles without TILE_CLOSE
     __shared__ StencilSplit<R> s_off;
     fill_stencil_split<R>(s_off, g);
     // one tile of TILE cell-ordered atoms per iteration (one iteration per
     // block unless the launch uses fewer blocks than tiles)
     const int ntiles = (g.n + TILE - 1) / TILE;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // with tflag, the close-pair variant takes the listed tiles (see tile_mark)
+    const bool listed = tflag && CLOSE;
+    const int nlist = listed ? tflag[ntiles] : ntiles;
+    for (int it = blockIdx.x; it < nlist; it += gridDim.x) {
+    const int tile = listed ? tflag[ntiles + 1 + it] : it;
+    if (tflag && (((tflag[tile] & TILE_CLOSE) != 0) != CLOSE)) continue;   // whole block
     const int k = tile * TILE + threadIdx.x;
     const size_t ld = (size_t)g.ld;
     R w[9];
@@ -1911,23 +1963,22 @@ __global__ void __launch_bounds__(TILE, sizeof(R) == 4 && !MS ? 7 : 1) k_radial_
         // in one record written by the angular kernel)
         const int2 c2 = cnt[k];
         const int na = c2.x, total = c2.x + c2.y, M = g.M;
-        const P4 ri0 = bp[3 * (size_t)k], ri1 = bp[3 * (size_t)k + 1], ri2 = bp[3 * (size_t)k + 2];
+        // the record of atom m (see rec_store)
+        auto record = [&](size_t m, P4& r0, P4& r1, P4& r2) {
+            r0 = bp[3 * m]; r1 = bp[3 * m + 1]; r2 = bp[3 * m + 2];
+        };
+        P4 ri0, ri1, ri2;
+        record((size_t)k, ri0, ri1, ri2);
         R fx = R(0), fy = R(0), fz = R(0);
         int ent_n = total > 0 ? nbr[(size_t)list_slot(0, na, M) * ld + k] : 0;
         int ent_nn = total > 1 ? nbr[(size_t)list_slot(1, na, M) * ld + k] : 0;
         P4 rj0_n = ri0, rj1_n = ri1, rj2_n = ri2;
-        if (total > 0) {
-            const size_t m0 = (size_t)(ent_n >> 5);
-            rj0_n = bp[3 * m0]; rj1_n = bp[3 * m0 + 1]; rj2_n = bp[3 * m0 + 2];
-        }
+        if (total > 0) record((size_t)(ent_n >> 5), rj0_n, rj1_n, rj2_n);
         for (int s = 0; s < total; ++s) {
             const int ent = ent_n;
             const P4 rj0 = rj0_n, rj1 = rj1_n, rj2 = rj2_n;
             ent_n = ent_nn;
-            if (s + 1 < total) {
-                const size_t m1 = (size_t)(ent_n >> 5);
-                rj0_n = bp[3 * m1]; rj1_n = bp[3 * m1 + 1]; rj2_n = bp[3 * m1 + 2];
-            }
+            if (s + 1 < total) record((size_t)(ent_n >> 5), rj0_n, rj1_n, rj2_n);
             if (s + 2 < total) ent_nn = nbr[(size_t)list_slot(s + 2, na, M) * ld + k];
             const int code = ent & 31;
             R dx = rj0.x - ri0.x + s_off.x[code], dy = rj0.y - ri0.y + s_off.y[code],

@@ -214,12 +214,16 @@ __device__ __forceinline__ void tm_rmw8(uint32_t a, float g, const float* Y)
 // count (nmax), a lane's missing pairs adding zero.  Then each channel's part
 // of the descriptor (q_nl = sum_m A_nlm^2, q_n^4b) to shared memory
 // (s_q[nu - NR][TILE], this thread's column) and channels 0-2 to Tensor
-// Memory (stores not waited for).
-template <typename Entry>
+// Memory (stores not waited for).  CLOSE: pairs inside the outer ZBL radius
+// take their displacement from the FP64 positions (close_pair_fp64; g, x64,
+// perm and this atom's slot k serve it).
+template <bool CLOSE, typename Entry>
 __device__ __forceinline__ void ang_desc_sums(const Model<float>& P, const float4* __restrict__ pos4,
                                               const StencilSplit<float>& s_off, int na, int nmax,
                                               const float4 pi, Entry entry, uint32_t tb,
-                                              float* s_q)
+                                              float* s_q, const Grid& g,
+                                              const double* __restrict__ x64,
+                                              const int* __restrict__ perm, int k)
 {
     constexpr int NN = 3;   // channels in registers
     float2 A[NN][NLM / 2];   // A_nlm in packed pairs (lm, lm + 1)
@@ -247,8 +251,10 @@ __device__ __forceinline__ void ang_desc_sums(const Model<float>& P, const float
         const int code = ent & 31;
         float dx = pj.x - pi.x + s_off.x[code], dy = pj.y - pi.y + s_off.y[code],
               dz = pj.z - pi.z + s_off.z[code];
-        if (!act) { dx = 1.f; dy = 0.f; dz = 0.f; }   // placeholder pair, adds zero
-        const float r2 = dx * dx + dy * dy + dz * dz;
+        float r2 = dx * dx + dy * dy + dz * dz;
+        if (CLOSE && act)
+            close_pair_fp64<float>(P.zbl_r2 * P.zbl_r2, g, x64, perm, k, ent >> 5, dx, dy, dz, r2);
+        if (!act) { dx = 1.f; dy = 0.f; dz = 0.f; r2 = 1.f; }   // placeholder pair, adds zero
         // beyond r_c^A (lists built with a skin) or a placeholder: g_n = 0
         const bool in = act && r2 < P.rcA2;
         const float inv_r = nepm::nep_rsqrt(r2);
@@ -314,15 +320,23 @@ __device__ __forceinline__ void ang_desc_sums(const Model<float>& P, const float
 // arguments and outputs.  At most TM_BLOCKS_PER_SM blocks may be resident
 // (TM_BLOCKS_PER_SM x TM_COLS = 512 columns, so the allocation never waits):
 // the launch checks the occupancy and pads the dynamic shared memory to
-// enforce it.  It handles the evaluations whose largest angular neighbour
-// count (*ang_max, from the neighbour kernel) is at most ang_lim and returns
-// at once otherwise (before allocating), k_nep_ang taking those.
+// enforce it.  It takes the tiles whose flag in tflag (from the
+// radial-descriptor pass) is 0 (CLOSE = false) or exactly TILE_CLOSE (CLOSE =
+// true: pairs inside the outer ZBL radius, whose displacements come from the
+// FP64 positions and whose ZBL term is added in FP64, as in k_nep_ang);
+// k_nep_ang takes the dense tiles.  One tile per block with a grid of all
+// tiles, or a loop over the tiles with a shorter grid; a block without a tile
+// of its own returns before allocating.
 constexpr int TM_BLOCKS_PER_SM = 4;
 // dynamic shared memory: [0, TM_SQ_OFF) staged angular entries (at most
-// STAGE_MAX_SLOTS per atom), then the angular descriptor [D - NR][TILE]
+// STAGE_MAX_SLOTS per atom), then the angular descriptor [D - NR][TILE]; with
+// CLOSE also the ZBL virial of every atom [9][TILE] (double)
 constexpr int TM_STAGE_SLOTS = 32;
 constexpr size_t TM_SQ_OFF = sizeof(int) * TM_STAGE_SLOTS * TILE;
 constexpr size_t TM_DYN_MIN = TM_SQ_OFF + sizeof(float) * (D - NR) * TILE;
+constexpr size_t TM_WZ_OFF = (TM_DYN_MIN + 15) / 16 * 16;
+constexpr size_t TM_DYN_MIN_CLOSE = TM_WZ_OFF + sizeof(double) * 9 * TILE;
+template <bool CLOSE>
 __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
     k_nep_ang_tm(const Model<float> P, const Grid g, const float4* __restrict__ pos4,
                  const int* __restrict__ nbr, const int2* __restrict__ cnt,
@@ -330,11 +344,14 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
                  const float* __restrict__ qr, float4* __restrict__ br,
                  long long* __restrict__ facc, double* __restrict__ partials,
                  double* __restrict__ site_energy, int* __restrict__ status, int stage_slots,
-                 const int* __restrict__ ang_max, int ang_lim)
+                 const int* __restrict__ tflag)
 {
-    // whole grid: k_nep_ang runs instead (dense clumps; pairs inside the ZBL
-    // range, whose FP64 branches this kernel does not carry)
-    if (*ang_max > ang_lim || (*status & ST_CLOSE)) return;
+    const int want = CLOSE ? TILE_CLOSE : 0;
+    const int ntiles = (g.n + TILE - 1) / TILE;
+    // CLOSE: the listed tiles (see tile_mark); otherwise every tile
+    const int nlist = CLOSE ? tflag[ntiles] : ntiles;
+    if (blockIdx.x >= nlist) return;   // no tile for this block
+    if (!CLOSE && gridDim.x >= ntiles && tflag[blockIdx.x] != want) return;   // before allocating
     using A_ = Acc<float>;
     __shared__ StencilSplit<float> s_off;
     __shared__ int s_max;
@@ -343,6 +360,7 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
     __shared__ double s_red[TILE / 32][NPART];
     extern __shared__ __align__(16) unsigned char s_dyn[];
     int* s_ent = reinterpret_cast<int*>(s_dyn);
+    double* s_wz = reinterpret_cast<double*>(s_dyn + TM_WZ_OFF);   // CLOSE only
     const int warp = threadIdx.x >> 5;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -350,15 +368,19 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (threadIdx.x == 0) s_max = 0;
     fill_network_rows<float>(s_w, P);
     tm_fence_before();
     fill_stencil_split<float>(s_off, g);   // ends with __syncthreads
     tm_fence_after();
     const uint32_t tb = s_tmem + ((uint32_t)(warp * 32) << 16);   // this warp's 32 lanes
-    const int k = blockIdx.x * TILE + threadIdx.x;
-    const bool valid = k < g.n;
     const size_t ld = (size_t)g.ld;
+    for (int it = blockIdx.x; it < nlist; it += gridDim.x) {
+    const int tile = CLOSE ? tflag[ntiles + 1 + it] : it;
+    if (tflag[tile] != want) continue;   // the whole block
+    if (threadIdx.x == 0) s_max = 0;
+    __syncthreads();   // also: the previous tile's shared data is no longer read
+    const int k = tile * TILE + threadIdx.x;
+    const bool valid = k < g.n;
     const int na = valid ? cnt[k].x : 0;
     atomicMax(&s_max, na);
     __syncthreads();
@@ -369,13 +391,17 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
         return staged ? s_ent[s * TILE + threadIdx.x] : nbr[(size_t)s * ld + k];
     };
     const float4 pi = valid ? pos4[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    if constexpr (CLOSE) {
+#pragma unroll
+        for (int t = 0; t < 9; ++t) s_wz[t * TILE + threadIdx.x] = 0.0;
+    }
 
     // descriptor vector: angular part in one pass over the pairs (the sums A
     // to Tensor Memory, q via shared memory), radial part from the neighbour
     // kernel
     float* s_q = reinterpret_cast<float*>(s_dyn + TM_SQ_OFF);
     const int nmax = __reduce_max_sync(0xffffffffu, na);
-    ang_desc_sums(P, pos4, s_off, na, nmax, pi, entry, tb, s_q);
+    ang_desc_sums<CLOSE>(P, pos4, s_off, na, nmax, pi, entry, tb, s_q, g, x64, perm, k);
     float q[D];
 #pragma unroll
     for (int n = 0; n < NR; ++n) q[n] = valid ? qr[(size_t)n * ld + k] : 0.f;
@@ -427,8 +453,7 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
         tm_st24(tb, n, v);
     }
     tm_wait_st();
-    // the record the radial-force kernel gathers per neighbour:
-    // (x, y, z, b_8), (b_0 + B0, b_1, b_2, b_3), (b_4..b_7)
+    // the record the radial-force kernel gathers per neighbour (rec_store)
     if (valid) {
         float bR[KR], B0 = 0.f;
 #pragma unroll
@@ -439,9 +464,9 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
 #pragma unroll
             for (int kk = 0; kk < KR; ++kk) bR[kk] += a[nu] * P.hR[nu * KR + kk];
         }
-        br[3 * (size_t)k] = make_float4(pi.x, pi.y, pi.z, bR[8]);
-        br[3 * (size_t)k + 1] = make_float4(bR[0] + B0, bR[1], bR[2], bR[3]);
-        br[3 * (size_t)k + 2] = make_float4(bR[4], bR[5], bR[6], bR[7]);
+        rec_store(br, (size_t)k, make_float4(pi.x, pi.y, pi.z, bR[8]),
+                  make_float4(bR[0] + B0, bR[1], bR[2], bR[3]),
+                  make_float4(bR[4], bR[5], bR[6], bR[7]));
     }
 
     // pair-force pass: every lane runs to the warp's largest pair count
@@ -449,6 +474,7 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
     float wv[9];
 #pragma unroll
     for (int t = 0; t < 9; ++t) wv[t] = 0.f;
+    double ez = 0.0;   // CLOSE: half the ZBL energy of the atom's pairs
     bool bad = !isfinite(U);
     const int i_caller = valid ? perm[k] : 0;
     int ent_n = na > 0 ? entry(0) : 0;
@@ -467,8 +493,20 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
         const int code = ent & 31;
         float dx = pj.x - pi.x + s_off.x[code], dy = pj.y - pi.y + s_off.y[code],
               dz = pj.z - pi.z + s_off.z[code];
-        if (!act) { dx = 1.f; dy = 0.f; dz = 0.f; }   // placeholder pair, result unused
         float r2 = dx * dx + dy * dy + dz * dz;
+        // CLOSE: a pair inside the outer ZBL radius takes the FP64
+        // displacement, formed once for the NEP terms (rounded, as
+        // close_pair_fp64) and the ZBL term
+        double d64[3];
+        const bool close = CLOSE && act && r2 < P.zbl_r2 * P.zbl_r2;
+        if (close) {
+            disp64(g, x64, i_caller, perm[m], d64);
+            dx = (float)d64[0];
+            dy = (float)d64[1];
+            dz = (float)d64[2];
+            r2 = dx * dx + dy * dy + dz * dz;
+        }
+        if (!act) { dx = 1.f; dy = 0.f; dz = 0.f; r2 = 1.f; }   // placeholder pair, result unused
         const bool in = act && r2 < P.rcA2;
         const float inv_r = nepm::nep_rsqrt(r2);
         const float r = r2 * inv_r;
@@ -477,7 +515,27 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
                           fx, fy, fz);
         if (in) {
             bad |= !isfinite(fx + fy + fz);
-            const long long cx = A_::conv(fx), cy = A_::conv(fy), cz = A_::conv(fz);
+            long long cx = A_::conv(fx), cy = A_::conv(fy), cz = A_::conv(fz);
+            if (CLOSE && r < P.zbl_r2) {
+                if (!close) disp64(g, x64, i_caller, perm[m], d64);
+                const double r64 = sqrt(d64[0] * d64[0] + d64[1] * d64[1] + d64[2] * d64[2]);
+                if (r64 < P.zbl_rr2) {
+                    double Uz, dUz;
+                    zbl_pair(r64, P.zbl_k, P.zbl_inv_a, P.zbl_r1, P.zbl_rr2, Uz, dUz);
+                    ez += 0.5 * Uz;
+                    const double c = 0.5 * dUz / r64;
+                    const double f3[3] = {c * d64[0], c * d64[1], c * d64[2]};
+                    cx += A_::convd(f3[0]);
+                    cy += A_::convd(f3[1]);
+                    cz += A_::convd(f3[2]);
+                    bad |= !isfinite(c);
+#pragma unroll
+                    for (int a3 = 0; a3 < 3; ++a3)
+#pragma unroll
+                        for (int b3 = 0; b3 < 3; ++b3)
+                            s_wz[(3 * a3 + b3) * TILE + threadIdx.x] -= f3[a3] * d64[b3];
+                }
+            }
             fi[0] += cx; fi[1] += cy; fi[2] += cz;
             A_::add(&facc[m], -cx);
             A_::add(&facc[ld + m], -cy);
@@ -492,22 +550,33 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
         A_::add(&facc[k], fi[0]);
         A_::add(&facc[ld + k], fi[1]);
         A_::add(&facc[2 * ld + k], fi[2]);
-        e_site = (double)U;
+        e_site = (double)U + ez;
         if (site_energy) site_energy[i_caller] = e_site;
         if (bad) atomicOr(status, ST_NONFINITE);
     }
 
-    // block partials (fixed order): energy and virial by shuffles
+    // block partials (fixed order): energy and virial by shuffles (the FP64
+    // ZBL virial of CLOSE tiles on its own, then added)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e_site += __shfl_xor_sync(0xffffffffu, e_site, o);
 #pragma unroll
     for (int t = 0; t < 9; ++t)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) wv[t] += __shfl_xor_sync(0xffffffffu, wv[t], o);
+    double wzs[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        wzs[t] = 0.0;
+        if constexpr (CLOSE) {
+            wzs[t] = s_wz[t * TILE + threadIdx.x];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) wzs[t] += __shfl_xor_sync(0xffffffffu, wzs[t], o);
+        }
+    }
     if ((threadIdx.x & 31) == 0) {
         s_red[warp][0] = e_site;
 #pragma unroll
-        for (int t = 0; t < 9; ++t) s_red[warp][1 + t] = (double)wv[t];
+        for (int t = 0; t < 9; ++t) s_red[warp][1 + t] = (double)wv[t] + wzs[t];
     }
     tm_fence_before();
     __syncthreads();
@@ -515,8 +584,9 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
         double sum = 0.0;
 #pragma unroll
         for (int wi = 0; wi < TILE / 32; ++wi) sum += s_red[wi][threadIdx.x];
-        partials[(size_t)blockIdx.x * NPART + threadIdx.x] = sum;
+        partials[(size_t)tile * NPART + threadIdx.x] = sum;
     }
+    }   // tile loop
     if (warp == 0) {
         tm_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"

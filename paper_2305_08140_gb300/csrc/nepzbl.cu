@@ -33,12 +33,15 @@ constexpr double EV_A3_GPA = 160.21766208;
 // longest neighbour list (slots) the force kernel stages in shared memory
 constexpr int STAGE_MAX_SLOTS = 32;
 // the one-species FP32 angular kernel keeps its per-atom angular state in Tensor Memory
-// unless this evaluation has an atom with more than TMEM_MAX_ANG angular neighbours
-// (dense clumps, where the register kernel measured faster): both kernels are
-// launched and each returns at once unless the neighbour kernel's device-side
-// maximum selects it, so the choice depends on the data of this evaluation only
+// except in the tiles (TILE atoms) with an atom of more than TMEM_MAX_ANG angular
+// neighbours (dense clumps, where the register kernel measured faster) or with a
+// pair inside the outer ZBL radius: both kernels are launched and each takes the
+// tiles the radial-descriptor pass marked for it, so the choice depends on the
+// data of this evaluation only
 constexpr bool USE_TMEM_ANG = true;
-constexpr int TMEM_MAX_ANG = 48;
+constexpr int TMEM_MAX_ANG = TILE_ANG_LIM;
+// device status words of a context
+constexpr int NSTATUS = 4;
 
 thread_local std::string g_init_error;
 
@@ -93,11 +96,13 @@ struct nep_ctx {
     double* thermo = nullptr;        // TH_N doubles
     double* thermo_backup = nullptr;
     double* result = nullptr;        // NPART doubles (E, W)
-    int* status = nullptr;           // [0] status bits, [1..2] max counts
+    int* status = nullptr;           // [0] status bits, [1..2] max counts, [3] tiles
+                                     // of the register angular kernel (dispatch)
+    int* tflag = nullptr;            // per-tile kernel choice (TILE_CLOSE, TILE_DENSE)
     unsigned long long* pairs = nullptr;
     // pinned host mirrors
     double* h_result = nullptr;      // NPART + TH_N
-    int* h_status = nullptr;         // 3
+    int* h_status = nullptr;         // NSTATUS
     unsigned long long* h_pairs = nullptr;
 
     cudaStream_t cap_stream = nullptr;
@@ -121,9 +126,12 @@ struct nep_ctx {
     int nep_smem_set[4] = {0, 0, 0, 0};
     int radial_q_fused = 0;          // last evaluation summed q in the neighbour kernel
     int ang_tmem = 0;                // last evaluation ran the Tensor-Memory angular kernel
+    int last_tiles = 0;              // tiles (TILE atoms) of the last evaluation
+    long long ang_tiles = 0, ang_reg_tiles = 0;   // of the last call / graph chunk
     int ang_dispatch = 0;            // last evaluation launched both angular kernels
     int tm_dyn = -1;                 // k_nep_ang_tm dynamic shared memory (-1: not set)
     int tm_blocks = 0;               // its resident blocks per SM
+    int tm_dyn_close = -1, tm_blocks_close = 0;   // the same for k_nep_ang_tm<true>
     // Nose-Hoover chain thermostat on a group, Berendsen barostat (MD)
     int nhc_on = 0;
     NhcParams nhc_p;
@@ -227,7 +235,7 @@ static void free_scratch(nep_ctx* ctx)
     drop_graphs(ctx);
     free_dev(ctx->cell_of); free_dev(ctx->slot_of); free_dev(ctx->perm);
     free_dev(ctx->cell_sorted); free_dev(ctx->invperm); free_dev(ctx->pos4); free_dev(ctx->rel4); free_dev(ctx->cnt); free_dev(ctx->nbr);
-    free_dev(ctx->facc); free_dev(ctx->partials); free_dev(ctx->partials2);
+    free_dev(ctx->facc); free_dev(ctx->partials); free_dev(ctx->partials2); free_dev(ctx->tflag);
     free_dev(ctx->qr); free_dev(ctx->br); free_dev(ctx->xref); free_dev(ctx->nbr_act);
     free_dev(ctx->cnt_act);
     free_dev(ctx->vpart); free_dev(ctx->backup);
@@ -262,6 +270,7 @@ static int ensure_atoms(nep_ctx* ctx, int n, int M)
     CK(cudaMalloc(&ctx->facc, acc * 3 * (size_t)ld));
     CK(cudaMemset(ctx->facc, 0, acc * 3 * (size_t)ld));
     CK(cudaMalloc(&ctx->partials, sizeof(double) * NPART * 2 * (size_t)tiles));
+    CK(cudaMalloc(&ctx->tflag, sizeof(int) * (2 * (size_t)tiles + 1)));   // flags, count, list
     const size_t rsz = ctx->precision == NEP_FP32 ? sizeof(float) : sizeof(double);
     CK(cudaMalloc(&ctx->qr, rsz * NR * (size_t)ld));
     CK(cudaMalloc(&ctx->br, rsz * 12 * (size_t)ctx->ntypes * ld));
@@ -373,39 +382,49 @@ static int check_device_ptr(nep_ctx* ctx, const void* p, const char* what)
     return NEP_OK;
 }
 
-// Dynamic shared memory of k_nep_ang_tm, set once per context: at least what
-// the kernel uses, padded until no more than TM_BLOCKS_PER_SM blocks can be
-// resident on an SM (each holds TM_COLS of the 512 Tensor Memory columns, so
-// a further block's allocation would wait for one of them to finish).
-// Returns 0 (and the register kernel takes every evaluation) when the kernel
-// cannot be made resident that way.
-static int tmem_dyn_bytes(nep_ctx* ctx)
+// Dynamic shared memory of k_nep_ang_tm<CLOSE>, set once per context: at
+// least what the kernel uses, padded until no more than TM_BLOCKS_PER_SM
+// blocks can be resident on an SM (each holds TM_COLS of the 512 Tensor Memory
+// columns, so a further block's allocation would wait for one of them to
+// finish).  Returns 0 when the kernel cannot be made resident that way (then
+// the register kernel takes its tiles).
+template <bool CLOSE>
+static int tmem_dyn_for(nep_ctx* ctx, int& dyn_out, int& blocks_out)
 {
-    if (ctx->tm_dyn >= 0) return ctx->tm_dyn;
-    ctx->tm_dyn = 0;
+    if (dyn_out >= 0) return dyn_out;
+    dyn_out = 0;
     int dev_max = 0;
     if (cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device) !=
             cudaSuccess ||
-        cudaFuncSetAttribute(k_nep_ang_tm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_nep_ang_tm<CLOSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              dev_max - 8192) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
-    for (size_t dyn = TM_DYN_MIN; dyn + 8192 <= (size_t)dev_max; dyn += 4096) {
+    const size_t lo = CLOSE ? TM_DYN_MIN_CLOSE : TM_DYN_MIN;
+    for (size_t dyn = lo; dyn + 8192 <= (size_t)dev_max; dyn += 4096) {
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_nep_ang_tm, TILE, dyn) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_nep_ang_tm<CLOSE>, TILE, dyn) !=
             cudaSuccess) {
             cudaGetLastError();
             return 0;
         }
         if (nb < 1) return 0;
         if (nb <= TM_BLOCKS_PER_SM) {
-            ctx->tm_dyn = (int)dyn;
-            ctx->tm_blocks = nb;
-            return ctx->tm_dyn;
+            dyn_out = (int)dyn;
+            blocks_out = nb;
+            return dyn_out;
         }
     }
     return 0;
+}
+static int tmem_dyn_bytes(nep_ctx* ctx)
+{
+    return tmem_dyn_for<false>(ctx, ctx->tm_dyn, ctx->tm_blocks);
+}
+static int tmem_dyn_bytes_close(nep_ctx* ctx)
+{
+    return tmem_dyn_for<true>(ctx, ctx->tm_dyn_close, ctx->tm_blocks_close);
 }
 
 // The orthorhombic neighbour-search kernel for a chunk width (4, 8, 16).
@@ -481,6 +500,14 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     for (int t = 0; t < NR * KR; ++t) rq.hR[t] = P.hR[t];
     for (int t = 0; t < NR; ++t) rq.CR[t] = P.CR[t];
     rq.close2 = P.zbl_r2 * P.zbl_r2;
+    // FP32, one species: the kernels that carry no close-pair (and no ZBL)
+    // branch are chosen tile by tile; the radial-descriptor pass (here or in
+    // k_radial_q) marks the tiles in tflag (blocks of TILE atoms = tiles)
+    const bool tiled = sizeof(R) == 4 && !ms;
+    const bool dispatch = tiled && USE_TMEM_ANG && tmem_dyn_bytes(ctx) > 0;
+    const int tiles = (n + TILE - 1) / TILE;
+    int* tfl = tiled ? ctx->tflag : nullptr;
+    if (tiled) CK(cudaMemsetAsync(ctx->tflag, 0, sizeof(int) * ((size_t)tiles + 1), s));
     // chunked candidate tests (pos4 holds NB_CHUNK - 1 readable entries past
     // the last atom, see ensure_atoms)
     auto kn = g.tric ? (fuse_q ? k_neighbors<R, true, true, true> : k_neighbors<R, false, true, true>)
@@ -488,7 +515,7 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     kn<<<(n + 127) / 128, 128, 0, s>>>(
         g, (R)(rl * rl), (R)(ra * ra), (const typename V4<R>::T*)ctx->pos4, ctx->cell_sorted,
         ctx->start, ctx->nbr, ctx->cnt, ctx->status, ctx->status + 1, ctx->pairs, gate, rq,
-        (R*)ctx->qr, ctx->perm, x);
+        (R*)ctx->qr, ctx->perm, x, fuse_q ? tfl : nullptr);
     count_launch(ctx);
     ctx->radial_q_fused = fuse_q ? 1 : 0;
     if (gate) {
@@ -497,7 +524,6 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
                                            (typename V4<R>::T*)ctx->pos4);
         count_launch(ctx);
     }
-    const int tiles = (n + TILE - 1) / TILE;
     // force accumulators start at zero (the forces are gathered out of them)
     CK(cudaMemsetAsync(ctx->facc, 0, sizeof(typename Acc<R>::T) * 3 * (size_t)ctx->ld, s));
     // the force kernels are timed together when timing is on
@@ -519,7 +545,7 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     if (!fuse_q) {
         (ms ? k_radial_q<R, true> : k_radial_q<R, false>)<<<(n + 127) / 128, 128, 0, s>>>(
             P, g, p4, ctx->nbr, ctx->cnt, (R*)ctx->qr, gate ? ctx->nbr_act : nullptr,
-            gate ? ctx->cnt_act : nullptr, coef, ctx->perm, x, ctx->status);
+            gate ? ctx->cnt_act : nullptr, coef, ctx->perm, x, ctx->status, tfl);
         count_launch(ctx);
     }
     // angular part, network, ZBL (the block's angular entries staged in shared
@@ -535,16 +561,27 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
                                       sizeof(int) * STAGE_MAX_SLOTS * TILE)));
         ctx->nep_smem_set[ks] = 1;
     }
-    // status[2]: the largest angular neighbour count of this evaluation
-    const bool dispatch = sizeof(R) == 4 && !ms && USE_TMEM_ANG && tmem_dyn_bytes(ctx) > 0;
     ctx->ang_dispatch = dispatch ? 1 : 0;
+    ctx->last_tiles = tiles;
+    // tiles with a close pair: the Tensor-Memory kernel with the close-pair
+    // and ZBL branches when it can be made resident, else the register kernel
+    const bool tm_close = dispatch && tmem_dyn_bytes_close(ctx) > 0;
     if constexpr (sizeof(R) == 4) {
         if (dispatch) {
             // one species, FP32: the angular state in Tensor Memory
-            k_nep_ang_tm<<<tiles, TILE, (size_t)tmem_dyn_bytes(ctx), s>>>(
+            k_nep_ang_tm<false><<<tiles, TILE, (size_t)tmem_dyn_bytes(ctx), s>>>(
                 P, g, p4, lnbr, lcnt, ctx->perm, x, (const float*)ctx->qr, (float4*)ctx->br, fa,
-                ctx->partials, site_energy, ctx->status, stage_slots, ctx->status + 2,
-                TMEM_MAX_ANG);
+                ctx->partials, site_energy, ctx->status, stage_slots, ctx->tflag);
+            count_launch(ctx);
+        }
+        if (tm_close) {
+            // (few tiles have close pairs: a grid of a few blocks per SM loops
+            // over the tiles and takes those)
+            const int cg = tiles < TM_BLOCKS_PER_SM * ctx->sm_count ? tiles
+                                                                     : TM_BLOCKS_PER_SM * ctx->sm_count;
+            k_nep_ang_tm<true><<<cg, TILE, (size_t)tmem_dyn_bytes_close(ctx), s>>>(
+                P, g, p4, lnbr, lcnt, ctx->perm, x, (const float*)ctx->qr, (float4*)ctx->br, fa,
+                ctx->partials, site_energy, ctx->status, stage_slots, ctx->tflag);
             count_launch(ctx);
         }
     }
@@ -554,27 +591,28 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     kang<<<ang_grid, TILE, stage_bytes, s>>>(P, g, p4, lnbr, lcnt, ctx->perm, x, (const R*)ctx->qr,
                                           (typename V4<R>::T*)ctx->br, fa, ctx->partials,
                                           site_energy, ctx->status, stage_slots, coef,
-                                          dispatch ? ctx->status + 2 : nullptr, TMEM_MAX_ANG);
+                                          dispatch ? ctx->tflag : nullptr, ctx->status + 3,
+                                          tm_close ? TILE_DENSE : TILE_DENSE | TILE_CLOSE);
     count_launch(ctx);
     // radial pair forces (all pairs, small state); FP32 one species: the
-    // variant without the close-pair branch unless the evaluation has a pair
-    // inside the outer ZBL radius (both launched, each returns unless chosen)
-    if (sizeof(R) == 4 && !ms) {
+    // variant without the close-pair branch on the tiles without a pair inside
+    // the outer ZBL radius, the other on the rest (both launched)
+    if (tiled) {
         k_radial_force<R, false, false><<<tiles, TILE, 0, s>>>(
             P, g, p4, lnbr, lcnt, (const typename V4<R>::T*)ctx->br, fa,
-            ctx->partials + (size_t)tiles * NPART, ctx->status, ctx->perm, x, true);
+            ctx->partials + (size_t)tiles * NPART, ctx->status, ctx->perm, x, tfl);
         count_launch(ctx);
-        // (the close-pair variant rarely runs: a grid of a few blocks per SM,
-        // looping over the tiles, makes its early return cheap)
+        // (the close-pair variant rarely has tiles: a grid of a few blocks per
+        // SM, looping over the tiles, makes its pass over the flags cheap)
         const int close_grid = tiles < 4 * ctx->sm_count ? tiles : 4 * ctx->sm_count;
         k_radial_force<R, false, true><<<close_grid > 0 ? close_grid : 1, TILE, 0, s>>>(
             P, g, p4, lnbr, lcnt, (const typename V4<R>::T*)ctx->br, fa,
-            ctx->partials + (size_t)tiles * NPART, ctx->status, ctx->perm, x, true);
+            ctx->partials + (size_t)tiles * NPART, ctx->status, ctx->perm, x, tfl);
         count_launch(ctx);
     } else {
         (ms ? k_radial_force<R, true> : k_radial_force<R, false>)<<<tiles, TILE, 0, s>>>(
             P, g, p4, lnbr, lcnt, (const typename V4<R>::T*)ctx->br, fa,
-            ctx->partials + (size_t)tiles * NPART, ctx->status, ctx->perm, x, false);
+            ctx->partials + (size_t)tiles * NPART, ctx->status, ctx->perm, x, nullptr);
         count_launch(ctx);
     }
     if (timed_slot >= 0) {
@@ -630,9 +668,9 @@ static int collect_timing(nep_ctx* ctx, int count)
 }
 
 // Reads status, counters and results to pinned host memory and waits.
-static int readback(nep_ctx* ctx, cudaStream_t s)
+static int readback(nep_ctx* ctx, cudaStream_t s, int evals = 1)
 {
-    CK(cudaMemcpyAsync(ctx->h_status, ctx->status, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->h_status, ctx->status, sizeof(int) * NSTATUS, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(ctx->h_pairs, ctx->pairs, sizeof(unsigned long long) * 2,
                        cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(ctx->h_result, ctx->result, sizeof(double) * NPART, cudaMemcpyDeviceToHost, s));
@@ -641,8 +679,10 @@ static int readback(nep_ctx* ctx, cudaStream_t s)
     CK(cudaStreamSynchronize(s));
     ctx->last_max_total = ctx->h_status[1];
     ctx->last_max_ang = ctx->h_status[2];
-    ctx->ang_tmem = ctx->ang_dispatch && ctx->h_status[2] <= TMEM_MAX_ANG &&
-                    !(ctx->h_status[0] & ST_CLOSE) ? 1 : 0;
+    // angular tiles of these evaluations, and those the register kernel took
+    ctx->ang_tiles = (long long)ctx->last_tiles * evals;
+    ctx->ang_reg_tiles = ctx->ang_dispatch ? ctx->h_status[3] : ctx->ang_tiles;
+    ctx->ang_tmem = ctx->ang_dispatch && ctx->ang_reg_tiles < ctx->ang_tiles ? 1 : 0;
     ctx->last_pairs_r = (long long)ctx->h_pairs[0];
     ctx->last_pairs_a = (long long)ctx->h_pairs[1];
     return NEP_OK;
@@ -841,16 +881,16 @@ int nep_init(const nep_params* p, int precision, nep_ctx** out)
     if (e == cudaSuccess) e = cudaMalloc(&ctx->thermo, sizeof(double) * TH_N);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->thermo_backup, sizeof(double) * TH_N);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->result, sizeof(double) * NPART);
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->status, sizeof(int) * 3);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->status, sizeof(int) * NSTATUS);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->pairs, sizeof(unsigned long long) * 2);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->gate, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->nrebuild, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(ctx->nrebuild, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_result, sizeof(double) * (NPART + TH_N));
-    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_status, sizeof(int) * 3);
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_status, sizeof(int) * NSTATUS);
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_pairs, sizeof(unsigned long long) * 2);
     if (e == cudaSuccess) e = cudaMemset(ctx->thermo, 0, sizeof(double) * TH_N);
-    if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(int) * 3);
+    if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(int) * NSTATUS);
     if (e != cudaSuccess) {
         int rc = fail(nullptr, NEP_ERR_CUDA, "CUDA setup failed: %s", cudaGetErrorString(e));
         nep_free(ctx);
@@ -974,6 +1014,8 @@ int nep_get_stats(const nep_ctx* ctx, nep_stats* out)
     out->angular_tmem_blocks_per_sm = ctx->tm_blocks;
     out->nbr_z_slices = ctx->nbr_zs;
     out->nbr_chunk = ctx->nbr_chw;
+    out->angular_tiles = ctx->ang_tiles;
+    out->angular_tiles_register = ctx->ang_reg_tiles;
     return NEP_OK;
 }
 
@@ -996,7 +1038,7 @@ static int compute_with_retry(nep_ctx* ctx, const Grid& g, const double* x, cons
     for (int attempt = 0; attempt < 4; ++attempt) {
         rc = ensure_atoms(ctx, g.n, M);
         if (rc) return rc;
-        CK(cudaMemsetAsync(ctx->status, 0, sizeof(int) * 3, s));
+        CK(cudaMemsetAsync(ctx->status, 0, sizeof(int) * NSTATUS, s));
         int slot = -1;
         if (ctx->timing) {
             rc = ensure_events(ctx, 1);
@@ -1185,7 +1227,7 @@ static int md_steps_barostat(nep_ctx* ctx, nep_md_state* st, int n_steps, cudaSt
         if (ctx->nhc_on)
             CK(cudaMemcpyAsync(ctx->nhc_backup, ctx->nhc, sizeof(double) * NHC_N,
                                cudaMemcpyDeviceToDevice, s));
-        CK(cudaMemsetAsync(ctx->status, 0, sizeof(int) * 3, s));
+        CK(cudaMemsetAsync(ctx->status, 0, sizeof(int) * NSTATUS, s));
         g.ld = ctx->ld;
         g.M = ctx->M;
         if ((rc = enqueue_step(ctx, g, st, s, -1))) return rc;
@@ -1328,7 +1370,7 @@ int md_step(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
         if (ctx->nhc_on)
             CK(cudaMemcpyAsync(ctx->nhc_backup, ctx->nhc, sizeof(double) * NHC_N,
                                cudaMemcpyDeviceToDevice, s));
-        CK(cudaMemsetAsync(ctx->status, 0, sizeof(int) * 3, s));
+        CK(cudaMemsetAsync(ctx->status, 0, sizeof(int) * NSTATUS, s));
         if (ctx->skin > 0.0 && force_rebuild) {
             const int one = 1;
             CK(cudaMemcpyAsync(ctx->gate, &one, sizeof(int), cudaMemcpyHostToDevice, s));
@@ -1336,7 +1378,7 @@ int md_step(nep_ctx* ctx, nep_md_state* st, int n_steps, void* stream)
         }
         CK(cudaGraphLaunch(it->second.exec, s));
         ctx->launches += it->second.kernels;
-        rc = readback(ctx, s);
+        rc = readback(ctx, s, len);
         if (rc) return rc;
         if (ctx->h_status[0] & ST_BADTYPE)
             return fail(ctx, NEP_ERR_INVALID_ARG, "species index out of range [0, %d)",
@@ -1688,10 +1730,10 @@ static int batch_launch(nep_ctx* ctx, Batch& b, int mode, double* grad, cudaStre
                                         : batch_blocks_per_sm(ctx->precision, mode, bt);
         int grid = std::min(b.S, std::max(1, per_sm * sms));
         CK(cudaMemsetAsync(ctx->b_queue, 0, sizeof(int), s));
-        CK(cudaMemsetAsync(ctx->status, 0, sizeof(int) * 3, s));
+        CK(cudaMemsetAsync(ctx->status, 0, sizeof(int) * NSTATUS, s));
         CK(launch_batch(ctx->precision, mode, bt, grid, ctx->mf, ctx->md, b, grad, s));
         ctx->launches += (mode == MODE_BACKWARD || mode == MODE_LOSS) ? 2 : 1;
-        CK(cudaMemcpyAsync(ctx->h_status, ctx->status, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(ctx->h_status, ctx->status, sizeof(int) * NSTATUS, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (ctx->h_status[0] & ST_OVERFLOW) {
             // keep the batch description: reallocation must not lose offsets/boxes/order
@@ -1937,7 +1979,7 @@ static int population_eval(nep_ctx* ctx, const nep_batch* batch, const nep_targe
     const long long items = (long long)n_pop * b.S;
     const int grid = (int)std::min<long long>(items, (long long)population_blocks_per_sm(ctx->precision) * sms);
     CK(cudaMemsetAsync(ctx->b_queue, 0, sizeof(int), s));
-    CK(cudaMemsetAsync(ctx->status, 0, sizeof(int) * 3, s));
+    CK(cudaMemsetAsync(ctx->status, 0, sizeof(int) * NSTATUS, s));
     if (b.T > 1) {
         const size_t rsz = ctx->precision == NEP_FP32 ? sizeof(float) : sizeof(double);
         if ((rc = grow(ctx, &ctx->p_tables, ctx->p_tables_cap,
@@ -1949,7 +1991,7 @@ static int population_eval(nep_ctx* ctx, const nep_batch* batch, const nep_targe
     CK(launch_population_loss(n_pop, ctx->p_out, thetas, b.S, b.ntot, (double)nv, w->energy,
                               w->force, w->virial, w->l1, w->l2, losses, b.np, s));
     ctx->launches += 3;
-    CK(cudaMemcpyAsync(ctx->h_status, ctx->status, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->h_status, ctx->status, sizeof(int) * NSTATUS, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (ctx->h_status[0] & ST_BADTYPE)
         return fail(ctx, NEP_ERR_INVALID_ARG, "species index out of range [0, %d)", ctx->ntypes);

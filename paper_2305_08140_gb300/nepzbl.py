@@ -88,7 +88,8 @@ class NepStats(C.Structure):
                 ("graph_chunk", C.c_int32), ("list_builds_skin", C.c_int64),
                 ("radial_q_in_neighbor_kernel", C.c_int32), ("angular_state_in_tmem", C.c_int32),
                 ("angular_tmem_blocks_per_sm", C.c_int32), ("nbr_z_slices", C.c_int32),
-                ("nbr_chunk", C.c_int32)]
+                ("nbr_chunk", C.c_int32), ("angular_tiles", C.c_int64),
+                ("angular_tiles_register", C.c_int64)]
 
 
 class NepTargets(C.Structure):

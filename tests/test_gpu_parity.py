@@ -367,13 +367,13 @@ def test_md_step_host_rejects_device_arrays():
 
 def test_angular_kernel_dispatch_both_paths():
     """FP32, one species: the angular kernel keeps its per-atom state in Tensor
-    Memory unless the evaluation has an atom with more than 48 angular
-    neighbours (then the register kernel runs; the choice is made on the
-    device from this evaluation's neighbour counts).  A lattice and a dense
-    clump, alternately, on one context: each takes its kernel every time, the
-    lattice matches the oracle, and repeats are bitwise equal.  (The register
-    kernel on clumps of this density is checked against the oracle by the
-    250,000-atom close-pair test.)"""
+    Memory except in the tiles (128 cell-ordered atoms) with an atom of more
+    than 48 angular neighbours or a pair inside the outer ZBL radius, which the
+    register kernel takes (the choice is made on the device, tile by tile, from
+    this evaluation's neighbour pass).  A lattice and a dense clump in a
+    lattice, alternately, on one context: the lattice runs wholly in Tensor
+    Memory, the clump's box in both kernels; both match the oracle (the clump
+    with the per-atom rounding bounds) and repeats are bitwise equal."""
     from paper_2305_08140_gb300 import nepzbl as N
     from gpu_common import F32_E_PER_ATOM, F32_F, F32_W_PER_ATOM, check_sites, site_bound
     m = N.NEP(I.nep_model(1), "fp32")
@@ -381,10 +381,16 @@ def test_angular_kernel_dispatch_both_paths():
     clump = I.c3(ncell=10, fraction=0.1, radius=6.0, seed=23)   # up to 85 angular neighbours
     Eo, Fo, Wo, Uo = oracle_eval(lat)
     outs = {}
-    for s, want_tmem in ((lat, 1), (clump, 0), (lat, 1), (clump, 0)):
+    for s in (lat, clump, lat, clump):
         E, F, W, U = m.compute(N.to_device_soa(s.pos), s.box, s.pbc, site_energy=True)
         st = m.stats()
-        assert st["angular_state_in_tmem"] == want_tmem, (st["max_nbr_angular"], want_tmem)
+        tiles = (s.n + 127) // 128
+        assert st["angular_tiles"] == tiles
+        assert st["angular_state_in_tmem"] == 1
+        if s is lat:
+            assert st["angular_tiles_register"] == 0
+        else:
+            assert 0 < st["angular_tiles_register"] < tiles, st["angular_tiles_register"]
         assert (st["max_nbr_angular"] > 48) == (s is clump)
         F = F.cpu().numpy().T
         assert np.all(np.isfinite(F))
@@ -398,6 +404,8 @@ def test_angular_kernel_dispatch_both_paths():
         (E1, F1), (E2, F2) = outs[id(s)]
         assert E1 == E2 and np.array_equal(F1, F2)
     m.close()
+    # the clump, its tiles split between the two kernels, against the oracle
+    assert_parity(clump, "fp32", scaled=True)
 
 
 @pytest.mark.parametrize("precision,skin", [("fp32", 0), ("fp64", 0), ("fp32", 500)])
