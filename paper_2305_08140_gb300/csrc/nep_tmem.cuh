@@ -374,7 +374,9 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
     tm_fence_after();
     const uint32_t tb = s_tmem + ((uint32_t)(warp * 32) << 16);   // this warp's 32 lanes
     const size_t ld = (size_t)g.ld;
-    for (int it = blockIdx.x; it < nlist; it += gridDim.x) {
+    // (without CLOSE the grid covers the tiles: one iteration)
+    const int it_end = CLOSE ? nlist : (int)blockIdx.x + 1;
+    for (int it = blockIdx.x; it < it_end; it += CLOSE ? gridDim.x : 1) {
     const int tile = CLOSE ? tflag[ntiles + 1 + it] : it;
     if (tflag[tile] != want) continue;   // the whole block
     if (threadIdx.x == 0) s_max = 0;
@@ -391,10 +393,6 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
         return staged ? s_ent[s * TILE + threadIdx.x] : nbr[(size_t)s * ld + k];
     };
     const float4 pi = valid ? pos4[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-    if constexpr (CLOSE) {
-#pragma unroll
-        for (int t = 0; t < 9; ++t) s_wz[t * TILE + threadIdx.x] = 0.0;
-    }
 
     // descriptor vector: angular part in one pass over the pairs (the sums A
     // to Tensor Memory, q via shared memory), radial part from the neighbour
@@ -475,6 +473,7 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
 #pragma unroll
     for (int t = 0; t < 9; ++t) wv[t] = 0.f;
     double ez = 0.0;   // CLOSE: half the ZBL energy of the atom's pairs
+    unsigned long long zmask = 0;   // CLOSE: pairs (slots < 64) with a ZBL term
     bool bad = !isfinite(U);
     const int i_caller = valid ? perm[k] : 0;
     int ent_n = na > 0 ? entry(0) : 0;
@@ -515,27 +514,9 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
                           fx, fy, fz);
         if (in) {
             bad |= !isfinite(fx + fy + fz);
-            long long cx = A_::conv(fx), cy = A_::conv(fy), cz = A_::conv(fz);
-            if (CLOSE && r < P.zbl_r2) {
-                if (!close) disp64(g, x64, i_caller, perm[m], d64);
-                const double r64 = sqrt(d64[0] * d64[0] + d64[1] * d64[1] + d64[2] * d64[2]);
-                if (r64 < P.zbl_rr2) {
-                    double Uz, dUz;
-                    zbl_pair(r64, P.zbl_k, P.zbl_inv_a, P.zbl_r1, P.zbl_rr2, Uz, dUz);
-                    ez += 0.5 * Uz;
-                    const double c = 0.5 * dUz / r64;
-                    const double f3[3] = {c * d64[0], c * d64[1], c * d64[2]};
-                    cx += A_::convd(f3[0]);
-                    cy += A_::convd(f3[1]);
-                    cz += A_::convd(f3[2]);
-                    bad |= !isfinite(c);
-#pragma unroll
-                    for (int a3 = 0; a3 < 3; ++a3)
-#pragma unroll
-                        for (int b3 = 0; b3 < 3; ++b3)
-                            s_wz[(3 * a3 + b3) * TILE + threadIdx.x] -= f3[a3] * d64[b3];
-                }
-            }
+            const long long cx = A_::conv(fx), cy = A_::conv(fy), cz = A_::conv(fz);
+            // the ZBL term of a pair inside the outer radius: after the loop
+            if (CLOSE && r < P.zbl_r2) zmask |= 1ull << s;
             fi[0] += cx; fi[1] += cy; fi[2] += cz;
             A_::add(&facc[m], -cx);
             A_::add(&facc[ld + m], -cy);
@@ -544,6 +525,43 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
             wv[3] -= fy * dx; wv[4] -= fy * dy; wv[5] -= fy * dz;
             wv[6] -= fz * dx; wv[7] -= fz * dy; wv[8] -= fz * dz;
         }
+    }
+    if constexpr (CLOSE) {
+        // ZBL terms (Eq. 2-4, FP64) of the pairs marked in the pair loop (a
+        // tile here has at most TILE_ANG_LIM angular neighbours per atom, so
+        // their slots are below 64), each converted and added on its own, as
+        // in k_nep_ang; the FP64 virial of the atom to shared memory
+        double wz[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) wz[t] = 0.0;
+        while (zmask) {
+            const int sz = __ffsll((long long)zmask) - 1;
+            zmask &= zmask - 1;
+            const int m = entry(sz) >> 5;
+            double d64[3];
+            disp64(g, x64, i_caller, perm[m], d64);
+            const double r64 = sqrt(d64[0] * d64[0] + d64[1] * d64[1] + d64[2] * d64[2]);
+            if (r64 < P.zbl_rr2) {
+                double Uz, dUz;
+                zbl_pair(r64, P.zbl_k, P.zbl_inv_a, P.zbl_r1, P.zbl_rr2, Uz, dUz);
+                ez += 0.5 * Uz;
+                const double c = 0.5 * dUz / r64;
+                const double f3[3] = {c * d64[0], c * d64[1], c * d64[2]};
+                const long long zx = A_::convd(f3[0]), zy = A_::convd(f3[1]),
+                                zz = A_::convd(f3[2]);
+                fi[0] += zx; fi[1] += zy; fi[2] += zz;
+                A_::add(&facc[m], -zx);
+                A_::add(&facc[ld + m], -zy);
+                A_::add(&facc[2 * ld + m], -zz);
+                bad |= !isfinite(c);
+#pragma unroll
+                for (int a3 = 0; a3 < 3; ++a3)
+#pragma unroll
+                    for (int b3 = 0; b3 < 3; ++b3) wz[3 * a3 + b3] -= f3[a3] * d64[b3];
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 9; ++t) s_wz[t * TILE + threadIdx.x] = wz[t];
     }
     double e_site = 0.0;
     if (valid) {
