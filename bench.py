@@ -68,7 +68,7 @@ FLOP_PAIR_A = 424 + 1078
 # until they are captured again.  Source:
 # profiles/dram_bytes_md_step_slab_8192000.md.
 DRAM_FORCE_PER_ATOM = 534.2
-DRAM_STEP_PER_ATOM = 1287.0
+DRAM_STEP_PER_ATOM = 1275.9
 # Compulsory HBM bytes per atom-step of this design: every array a kernel of
 # the step needs read or written once by that kernel (neighbour records that
 # the caches serve are not counted):

@@ -703,17 +703,36 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                             if (self < (unsigned)CHW) keep &= ~(1u << self);
                             ha &= hr & keep;
                             hr &= keep & ~ha;   // radial only
-                            tot += __popc(ha) + __popc(hr);
-                            while (ha) {
-                                const int j = __ffs(ha) - 1;
-                                ha &= ha - 1u;
-                                if (sa + sro < M) col[(size_t)(sa++) * ld] = ((m0 + j) << 5) | code;
-                            }
-                            while (hr) {
-                                const int j = __ffs(hr) - 1;
-                                hr &= hr - 1u;
-                                if (sa + sro < M)
-                                    col[(size_t)(M - 1 - sro++) * ld] = ((m0 + j) << 5) | code;
+                            const int na_c = __popc(ha), nr_c = __popc(hr);
+                            tot += na_c + nr_c;
+                            const int base = (m0 << 5) | code;   // entry of candidate j: base + 32 j
+                            if (sa + sro + na_c + nr_c <= M) {
+                                // room for all of them: no test per hit
+                                int* pa = col + (size_t)sa * ld;
+                                while (ha) {
+                                    *pa = base + ((__ffs(ha) - 1) << 5);
+                                    ha &= ha - 1u;
+                                    pa += ld;
+                                }
+                                int* pr = col + (size_t)(M - 1 - sro) * ld;
+                                while (hr) {
+                                    *pr = base + ((__ffs(hr) - 1) << 5);
+                                    hr &= hr - 1u;
+                                    pr -= ld;
+                                }
+                                sa += na_c;
+                                sro += nr_c;
+                            } else {
+                                while (ha) {
+                                    const int j = __ffs(ha) - 1;
+                                    ha &= ha - 1u;
+                                    if (sa + sro < M) col[(size_t)(sa++) * ld] = base + (j << 5);
+                                }
+                                while (hr) {
+                                    const int j = __ffs(hr) - 1;
+                                    hr &= hr - 1u;
+                                    if (sa + sro < M) col[(size_t)(M - 1 - sro++) * ld] = base + (j << 5);
+                                }
                             }
                         }
                     } else {
