@@ -113,11 +113,14 @@ __device__ __forceinline__ void tm_st24(uint32_t tb, int n, const float* v)
 // (g_n / r) sum_lm l a_nlm Y_lm], in fewer operations).  With `prefetch`
 // (warp-uniform) c = 0 is loaded again into buf[0] for the next pair once the
 // last group (c = 14, also in buf[0]) has been used.
+template <bool MS = false>
 __device__ __forceinline__ void force_pair_ang_tm(const Model<float>& P, float r, float inv_r,
                                                   float ux, float uy, float uz, uint32_t tb,
                                                   float (&buf)[2][8], bool prefetch,
-                                                  float& fx, float& fy, float& fz)
+                                                  float& fx, float& fy, float& fz,
+                                                  const float* cs = nullptr)
 {
+    // MS: cs = the pair's angular coefficients (h [0, 45), C [45, 50))
     float gn[NA], dgn[NA];
     {
         float T[KA], dT[KA], fc, dfc, dxdr;
@@ -125,10 +128,12 @@ __device__ __forceinline__ void force_pair_ang_tm(const Model<float>& P, float r
 #pragma unroll
         for (int n = 0; n < NA; ++n) {
             // (sum_k h_nk T_k + C_n, sum_k h_nk T'_k) as one packed pair
-            float2 ab = f2(P.CA[n], 0.f);
+            float2 ab = f2(MS ? cs[NA * KA + n] : P.CA[n], 0.f);
 #pragma unroll
-            for (int kk = 0; kk < KA; ++kk)
-                ab = fma2(f2(P.hA[n * KA + kk], P.hA[n * KA + kk]), f2(T[kk], dT[kk]), ab);
+            for (int kk = 0; kk < KA; ++kk) {
+                const float h = MS ? cs[n * KA + kk] : P.hA[n * KA + kk];
+                ab = fma2(f2(h, h), f2(T[kk], dT[kk]), ab);
+            }
             gn[n] = fc * ab.x;
             dgn[n] = dfc * ab.x + fc * dxdr * ab.y;
         }
@@ -217,14 +222,16 @@ __device__ __forceinline__ void tm_rmw8(uint32_t a, float g, const float* Y)
 // Memory (stores not waited for).  CLOSE: pairs inside the outer ZBL radius
 // take their displacement from the FP64 positions (close_pair_fp64; g, x64,
 // perm and this atom's slot k serve it).
-template <bool CLOSE, typename Entry>
+template <bool CLOSE, bool MS, typename Entry>
 __device__ __forceinline__ void ang_desc_sums(const Model<float>& P, const float4* __restrict__ pos4,
                                               const StencilSplit<float>& s_off, int na, int nmax,
                                               const float4 pi, Entry entry, uint32_t tb,
                                               float* s_q, const Grid& g,
                                               const double* __restrict__ x64,
-                                              const int* __restrict__ perm, int k)
+                                              const int* __restrict__ perm, int k,
+                                              const float* s_coef, int ti, int T)
 {
+    // MS: the pair's angular coefficients from the table in shared memory
     constexpr int NN = 3;   // channels in registers
     float2 A[NN][NLM / 2];   // A_nlm in packed pairs (lm, lm + 1)
 #pragma unroll
@@ -262,12 +269,13 @@ __device__ __forceinline__ void ang_desc_sums(const Model<float>& P, const float
         float Tk[KA], dT[KA], fc, dfc, dxdr;
         nepm::cheb<KA, false>(r, P.inv_rcA, Tk, dT, fc, dfc, dxdr);
         const float fcm = in ? fc : 0.f;
+        const float* cs = MS ? s_coef + ((size_t)ti * T + (int)pj.w) * CSTR + C_ANG : nullptr;
         float gn[NA];
 #pragma unroll
         for (int n = 0; n < NA; ++n) {
-            float acc = P.CA[n];
+            float acc = MS ? cs[NA * KA + n] : P.CA[n];
 #pragma unroll
-            for (int kk = 0; kk < KA; ++kk) acc += P.hA[n * KA + kk] * Tk[kk];
+            for (int kk = 0; kk < KA; ++kk) acc += (MS ? cs[n * KA + kk] : P.hA[n * KA + kk]) * Tk[kk];
             gn[n] = fcm * acc;
         }
         const float ux = dx * inv_r, uy = dy * inv_r, uz = dz * inv_r;
@@ -316,8 +324,11 @@ __device__ __forceinline__ void ang_desc_sums(const Model<float>& P, const float
     }
 }
 
-// k_nep_ang (one species, FP32) with the angular state in Tensor Memory; same
-// arguments and outputs.  At most TM_BLOCKS_PER_SM blocks may be resident
+// k_nep_ang (FP32) with the angular state in Tensor Memory; same arguments and
+// outputs.  MS (several species): the pair coefficients come from the table
+// coef ([T * T][CSTR], copied to shared memory), the record of atom k is one
+// radial adjoint per neighbour species t (br[(k T + t) * 3], as k_nep_ang
+// writes it), the ZBL parameters are the pair's.  At most TM_BLOCKS_PER_SM blocks may be resident
 // (TM_BLOCKS_PER_SM x TM_COLS = 512 columns, so the allocation never waits):
 // the launch checks the occupancy and pads the dynamic shared memory to
 // enforce it.  It takes the tiles whose flag in tflag (from the
@@ -336,7 +347,19 @@ constexpr size_t TM_SQ_OFF = sizeof(int) * TM_STAGE_SLOTS * TILE;
 constexpr size_t TM_DYN_MIN = TM_SQ_OFF + sizeof(float) * (D - NR) * TILE;
 constexpr size_t TM_WZ_OFF = (TM_DYN_MIN + 15) / 16 * 16;
 constexpr size_t TM_DYN_MIN_CLOSE = TM_WZ_OFF + sizeof(double) * 9 * TILE;
-template <bool CLOSE>
+// MS: the pair coefficient table after the regions above (at most NT_MAX^2 pairs)
+constexpr size_t TM_COEF_BYTES = sizeof(float) * NT_MAX * NT_MAX * CSTR;
+template <bool CLOSE, bool MS>
+__host__ __device__ constexpr size_t tm_coef_off()
+{
+    return CLOSE ? TM_DYN_MIN_CLOSE : (TM_DYN_MIN + 15) / 16 * 16;
+}
+template <bool CLOSE, bool MS>
+__host__ __device__ constexpr size_t tm_dyn_min()
+{
+    return tm_coef_off<CLOSE, MS>() + (MS ? TM_COEF_BYTES : 0);
+}
+template <bool CLOSE, bool MS>
 __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
     k_nep_ang_tm(const Model<float> P, const Grid g, const float4* __restrict__ pos4,
                  const int* __restrict__ nbr, const int2* __restrict__ cnt,
@@ -344,7 +367,7 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
                  const float* __restrict__ qr, float4* __restrict__ br,
                  long long* __restrict__ facc, double* __restrict__ partials,
                  double* __restrict__ site_energy, int* __restrict__ status, int stage_slots,
-                 const int* __restrict__ tflag)
+                 const int* __restrict__ tflag, const float* __restrict__ coef)
 {
     const int want = CLOSE ? TILE_CLOSE : 0;
     const int ntiles = (g.n + TILE - 1) / TILE;
@@ -361,6 +384,11 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
     extern __shared__ __align__(16) unsigned char s_dyn[];
     int* s_ent = reinterpret_cast<int*>(s_dyn);
     double* s_wz = reinterpret_cast<double*>(s_dyn + TM_WZ_OFF);   // CLOSE only
+    float* s_coef = reinterpret_cast<float*>(s_dyn + tm_coef_off<CLOSE, MS>());   // MS only
+    const int T = MS ? P.ntypes : 1;
+    if constexpr (MS) {
+        for (int t = threadIdx.x; t < T * T * CSTR; t += TILE) s_coef[t] = coef[t];
+    }
     const int warp = threadIdx.x >> 5;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -393,13 +421,15 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
         return staged ? s_ent[s * TILE + threadIdx.x] : nbr[(size_t)s * ld + k];
     };
     const float4 pi = valid ? pos4[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int ti = MS ? (int)pi.w : 0;
 
     // descriptor vector: angular part in one pass over the pairs (the sums A
     // to Tensor Memory, q via shared memory), radial part from the neighbour
     // kernel
     float* s_q = reinterpret_cast<float*>(s_dyn + TM_SQ_OFF);
     const int nmax = __reduce_max_sync(0xffffffffu, na);
-    ang_desc_sums<CLOSE>(P, pos4, s_off, na, nmax, pi, entry, tb, s_q, g, x64, perm, k);
+    ang_desc_sums<CLOSE, MS>(P, pos4, s_off, na, nmax, pi, entry, tb, s_q, g, x64, perm, k,
+                             s_coef, ti, T);
     float q[D];
 #pragma unroll
     for (int n = 0; n < NR; ++n) q[n] = valid ? qr[(size_t)n * ld + k] : 0.f;
@@ -451,20 +481,33 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
         tm_st24(tb, n, v);
     }
     tm_wait_st();
-    // the record the radial-force kernel gathers per neighbour (rec_store)
+    // the record the radial-force kernel gathers per neighbour (rec_store); MS:
+    // per neighbour species t, (b_0..b_3), (b_4..b_7), (b_8, B0, 0, 0)
     if (valid) {
-        float bR[KR], B0 = 0.f;
+#pragma unroll 1
+        for (int t = 0; t < T; ++t) {
+            const float* c = MS ? s_coef + ((size_t)ti * T + t) * CSTR + C_RAD : nullptr;
+            float bR[KR], B0 = 0.f;
 #pragma unroll
-        for (int kk = 0; kk < KR; ++kk) bR[kk] = 0.f;
+            for (int kk = 0; kk < KR; ++kk) bR[kk] = 0.f;
 #pragma unroll
-        for (int nu = 0; nu < NR; ++nu) {
-            B0 += a[nu] * P.CR[nu];
+            for (int nu = 0; nu < NR; ++nu) {
+                B0 += a[nu] * (MS ? c[NR * KR + nu] : P.CR[nu]);
 #pragma unroll
-            for (int kk = 0; kk < KR; ++kk) bR[kk] += a[nu] * P.hR[nu * KR + kk];
+                for (int kk = 0; kk < KR; ++kk)
+                    bR[kk] += a[nu] * (MS ? c[nu * KR + kk] : P.hR[nu * KR + kk]);
+            }
+            if constexpr (MS) {
+                const size_t slot = (size_t)k * T + t;
+                br[3 * slot] = make_float4(bR[0], bR[1], bR[2], bR[3]);
+                br[3 * slot + 1] = make_float4(bR[4], bR[5], bR[6], bR[7]);
+                br[3 * slot + 2] = make_float4(bR[8], B0, 0.f, 0.f);
+            } else {
+                rec_store(br, (size_t)k, make_float4(pi.x, pi.y, pi.z, bR[8]),
+                          make_float4(bR[0] + B0, bR[1], bR[2], bR[3]),
+                          make_float4(bR[4], bR[5], bR[6], bR[7]));
+            }
         }
-        rec_store(br, (size_t)k, make_float4(pi.x, pi.y, pi.z, bR[8]),
-                  make_float4(bR[0] + B0, bR[1], bR[2], bR[3]),
-                  make_float4(bR[4], bR[5], bR[6], bR[7]));
     }
 
     // pair-force pass: every lane runs to the warp's largest pair count
@@ -510,8 +553,9 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
         const float inv_r = nepm::nep_rsqrt(r2);
         const float r = r2 * inv_r;
         float fx, fy, fz;
-        force_pair_ang_tm(P, r, inv_r, dx * inv_r, dy * inv_r, dz * inv_r, tb, buf, s + 1 < nmax,
-                          fx, fy, fz);
+        force_pair_ang_tm<MS>(P, r, inv_r, dx * inv_r, dy * inv_r, dz * inv_r, tb, buf,
+                              s + 1 < nmax, fx, fy, fz,
+                              MS ? s_coef + ((size_t)ti * T + (int)pj.w) * CSTR + C_ANG : nullptr);
         if (in) {
             bad |= !isfinite(fx + fy + fz);
             const long long cx = A_::conv(fx), cy = A_::conv(fy), cz = A_::conv(fz);
@@ -543,7 +587,9 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
             const double r64 = sqrt(d64[0] * d64[0] + d64[1] * d64[1] + d64[2] * d64[2]);
             if (r64 < P.zbl_rr2) {
                 double Uz, dUz;
-                zbl_pair(r64, P.zbl_k, P.zbl_inv_a, P.zbl_r1, P.zbl_rr2, Uz, dUz);
+                const int pz = MS ? ti * T + (int)pos4[m].w : 0;
+                zbl_pair(r64, MS ? P.zbl_kp[pz] : P.zbl_k, MS ? P.zbl_inv_ap[pz] : P.zbl_inv_a,
+                         P.zbl_r1, P.zbl_rr2, Uz, dUz);
                 ez += 0.5 * Uz;
                 const double c = 0.5 * dUz / r64;
                 const double f3[3] = {c * d64[0], c * d64[1], c * d64[2]};

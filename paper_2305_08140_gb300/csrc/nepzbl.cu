@@ -131,7 +131,8 @@ struct nep_ctx {
     int ang_dispatch = 0;            // last evaluation launched both angular kernels
     int tm_dyn = -1;                 // k_nep_ang_tm dynamic shared memory (-1: not set)
     int tm_blocks = 0;               // its resident blocks per SM
-    int tm_dyn_close = -1, tm_blocks_close = 0;   // the same for k_nep_ang_tm<true>
+    int tm_dyn_close = -1, tm_blocks_close = 0;   // the same for k_nep_ang_tm<true, false>
+    int tm_dyn_ms[2] = {-1, -1}, tm_blocks_ms[2] = {0, 0};   // <false / true, true>
     // Nose-Hoover chain thermostat on a group, Berendsen barostat (MD)
     int nhc_on = 0;
     NhcParams nhc_p;
@@ -382,13 +383,13 @@ static int check_device_ptr(nep_ctx* ctx, const void* p, const char* what)
     return NEP_OK;
 }
 
-// Dynamic shared memory of k_nep_ang_tm<CLOSE>, set once per context: at
+// Dynamic shared memory of k_nep_ang_tm<CLOSE, MS>, set once per context: at
 // least what the kernel uses, padded until no more than TM_BLOCKS_PER_SM
 // blocks can be resident on an SM (each holds TM_COLS of the 512 Tensor Memory
 // columns, so a further block's allocation would wait for one of them to
 // finish).  Returns 0 when the kernel cannot be made resident that way (then
 // the register kernel takes its tiles).
-template <bool CLOSE>
+template <bool CLOSE, bool MS>
 static int tmem_dyn_for(nep_ctx* ctx, int& dyn_out, int& blocks_out)
 {
     if (dyn_out >= 0) return dyn_out;
@@ -396,15 +397,15 @@ static int tmem_dyn_for(nep_ctx* ctx, int& dyn_out, int& blocks_out)
     int dev_max = 0;
     if (cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device) !=
             cudaSuccess ||
-        cudaFuncSetAttribute(k_nep_ang_tm<CLOSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_nep_ang_tm<CLOSE, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              dev_max - 8192) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
-    const size_t lo = CLOSE ? TM_DYN_MIN_CLOSE : TM_DYN_MIN;
+    const size_t lo = tm_dyn_min<CLOSE, MS>();
     for (size_t dyn = lo; dyn + 8192 <= (size_t)dev_max; dyn += 4096) {
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_nep_ang_tm<CLOSE>, TILE, dyn) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_nep_ang_tm<CLOSE, MS>, TILE, dyn) !=
             cudaSuccess) {
             cudaGetLastError();
             return 0;
@@ -418,13 +419,15 @@ static int tmem_dyn_for(nep_ctx* ctx, int& dyn_out, int& blocks_out)
     }
     return 0;
 }
-static int tmem_dyn_bytes(nep_ctx* ctx)
+static int tmem_dyn_bytes(nep_ctx* ctx, bool ms = false)
 {
-    return tmem_dyn_for<false>(ctx, ctx->tm_dyn, ctx->tm_blocks);
+    return ms ? tmem_dyn_for<false, true>(ctx, ctx->tm_dyn_ms[0], ctx->tm_blocks_ms[0])
+              : tmem_dyn_for<false, false>(ctx, ctx->tm_dyn, ctx->tm_blocks);
 }
-static int tmem_dyn_bytes_close(nep_ctx* ctx)
+static int tmem_dyn_bytes_close(nep_ctx* ctx, bool ms = false)
 {
-    return tmem_dyn_for<true>(ctx, ctx->tm_dyn_close, ctx->tm_blocks_close);
+    return ms ? tmem_dyn_for<true, true>(ctx, ctx->tm_dyn_ms[1], ctx->tm_blocks_ms[1])
+              : tmem_dyn_for<true, false>(ctx, ctx->tm_dyn_close, ctx->tm_blocks_close);
 }
 
 // The orthorhombic neighbour-search kernel for a chunk width (4, 8, 16).
@@ -500,11 +503,11 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     for (int t = 0; t < NR * KR; ++t) rq.hR[t] = P.hR[t];
     for (int t = 0; t < NR; ++t) rq.CR[t] = P.CR[t];
     rq.close2 = P.zbl_r2 * P.zbl_r2;
-    // FP32, one species: the kernels that carry no close-pair (and no ZBL)
-    // branch are chosen tile by tile; the radial-descriptor pass (here or in
+    // FP32: the angular kernels (and, with one species, the radial-force
+    // kernels) are chosen tile by tile; the radial-descriptor pass (here or in
     // k_radial_q) marks the tiles in tflag (blocks of TILE atoms = tiles)
-    const bool tiled = sizeof(R) == 4 && !ms;
-    const bool dispatch = tiled && USE_TMEM_ANG && tmem_dyn_bytes(ctx) > 0;
+    const bool tiled = sizeof(R) == 4;
+    const bool dispatch = tiled && USE_TMEM_ANG && tmem_dyn_bytes(ctx, ms) > 0;
     const int tiles = (n + TILE - 1) / TILE;
     int* tfl = tiled ? ctx->tflag : nullptr;
     if (tiled) CK(cudaMemsetAsync(ctx->tflag, 0, sizeof(int) * ((size_t)tiles + 1), s));
@@ -565,23 +568,26 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     ctx->last_tiles = tiles;
     // tiles with a close pair: the Tensor-Memory kernel with the close-pair
     // and ZBL branches when it can be made resident, else the register kernel
-    const bool tm_close = dispatch && tmem_dyn_bytes_close(ctx) > 0;
+    const bool tm_close = dispatch && tmem_dyn_bytes_close(ctx, ms) > 0;
     if constexpr (sizeof(R) == 4) {
+        // (few tiles have close pairs: a grid of a few blocks per SM loops over
+        // the listed tiles and takes those)
+        const int cg = tiles < TM_BLOCKS_PER_SM * ctx->sm_count ? tiles
+                                                                 : TM_BLOCKS_PER_SM * ctx->sm_count;
+        const float* cf = ctx->coef_f;
         if (dispatch) {
-            // one species, FP32: the angular state in Tensor Memory
-            k_nep_ang_tm<false><<<tiles, TILE, (size_t)tmem_dyn_bytes(ctx), s>>>(
-                P, g, p4, lnbr, lcnt, ctx->perm, x, (const float*)ctx->qr, (float4*)ctx->br, fa,
-                ctx->partials, site_energy, ctx->status, stage_slots, ctx->tflag);
+            // FP32: the angular state in Tensor Memory
+            (ms ? k_nep_ang_tm<false, true> : k_nep_ang_tm<false, false>)
+                <<<tiles, TILE, (size_t)tmem_dyn_bytes(ctx, ms), s>>>(
+                    P, g, p4, lnbr, lcnt, ctx->perm, x, (const float*)ctx->qr, (float4*)ctx->br,
+                    fa, ctx->partials, site_energy, ctx->status, stage_slots, ctx->tflag, cf);
             count_launch(ctx);
         }
         if (tm_close) {
-            // (few tiles have close pairs: a grid of a few blocks per SM loops
-            // over the tiles and takes those)
-            const int cg = tiles < TM_BLOCKS_PER_SM * ctx->sm_count ? tiles
-                                                                     : TM_BLOCKS_PER_SM * ctx->sm_count;
-            k_nep_ang_tm<true><<<cg, TILE, (size_t)tmem_dyn_bytes_close(ctx), s>>>(
-                P, g, p4, lnbr, lcnt, ctx->perm, x, (const float*)ctx->qr, (float4*)ctx->br, fa,
-                ctx->partials, site_energy, ctx->status, stage_slots, ctx->tflag);
+            (ms ? k_nep_ang_tm<true, true> : k_nep_ang_tm<true, false>)
+                <<<cg, TILE, (size_t)tmem_dyn_bytes_close(ctx, ms), s>>>(
+                    P, g, p4, lnbr, lcnt, ctx->perm, x, (const float*)ctx->qr, (float4*)ctx->br,
+                    fa, ctx->partials, site_energy, ctx->status, stage_slots, ctx->tflag, cf);
             count_launch(ctx);
         }
     }
@@ -597,7 +603,7 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     // radial pair forces (all pairs, small state); FP32 one species: the
     // variant without the close-pair branch on the tiles without a pair inside
     // the outer ZBL radius, the other on the rest (both launched)
-    if (tiled) {
+    if (tiled && !ms) {
         k_radial_force<R, false, false><<<tiles, TILE, 0, s>>>(
             P, g, p4, lnbr, lcnt, (const typename V4<R>::T*)ctx->br, fa,
             ctx->partials + (size_t)tiles * NPART, ctx->status, ctx->perm, x, tfl);
