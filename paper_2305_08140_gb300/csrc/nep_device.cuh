@@ -1962,6 +1962,10 @@ __global__ void __launch_bounds__(TILE, sizeof(R) == 4 && !MS ? 7 : 1) k_radial_
     // one without the close-pair branch takes the tiles without TILE_CLOSE
     __shared__ StencilSplit<R> s_off;
     fill_stencil_split<R>(s_off, g);
+    // FP32, several species: the atom's own adjoints in shared memory (a
+    // gathered 16-byte load per neighbour each otherwise)
+    constexpr bool OWN = MS && sizeof(R) == 4;
+    __shared__ P4 s_own[OWN ? NT_MAX * 3 * TILE : 1];
     // one tile of TILE cell-ordered atoms per iteration (one iteration per
     // block unless the launch uses fewer blocks than tiles)
     const int ntiles = (g.n + TILE - 1) / TILE;
@@ -2057,6 +2061,14 @@ __global__ void __launch_bounds__(TILE, sizeof(R) == 4 && !MS ? 7 : 1) k_radial_
         const int T = MS ? P.ntypes : 1;
         const int ti = MS ? (int)pi.w : 0;
         P4 bi0 = bp[3 * (size_t)k], bi1 = bp[3 * (size_t)k + 1], bi2 = bp[3 * (size_t)k + 2];
+        if constexpr (OWN) {
+            // this atom's adjoints for every neighbour species, in this thread's
+            // column of shared memory (read by this thread only)
+            for (int t = 0; t < T; ++t)
+#pragma unroll
+                for (int p = 0; p < 3; ++p)
+                    s_own[(t * 3 + p) * TILE + threadIdx.x] = bp[3 * ((size_t)k * T + t) + p];
+        }
         R fx = R(0), fy = R(0), fz = R(0);
         // two-stage prefetch: entry s + 2, position and adjoint s + 1 in flight
         int ent_n = total > 0 ? nbr[(size_t)list_slot(0, na, M) * ld + k] : 0;
@@ -2076,7 +2088,11 @@ __global__ void __launch_bounds__(TILE, sizeof(R) == 4 && !MS ? 7 : 1) k_radial_
                 pj_n = pos4[ent_n >> 5];
                 bj0_n = bp[3 * m1]; bj1_n = bp[3 * m1 + 1]; bj2_n = bp[3 * m1 + 2];
             }
-            if constexpr (MS) {
+            if constexpr (OWN) {
+                // this atom's adjoint for the neighbour's species
+                const int o = (int)pj.w * 3 * TILE + threadIdx.x;
+                bi0 = s_own[o]; bi1 = s_own[o + TILE]; bi2 = s_own[o + 2 * TILE];
+            } else if constexpr (MS) {
                 // this atom's adjoint for the neighbour's species (L1-resident)
                 const size_t mi = (size_t)k * T + (int)pj.w;
                 bi0 = bp[3 * mi]; bi1 = bp[3 * mi + 1]; bi2 = bp[3 * mi + 2];
