@@ -219,6 +219,52 @@ def test_network_matches_numpy():
     assert U == pytest.approx(ref, rel=1e-13)
 
 
+def test_network_special_weights_dimer_closed_form():
+    """A network that reads only the radial descriptor: w0[mu, nu(mu)] = a_mu
+    with nu(mu) = (mu + 2) mod n_R for the first n_R neurons and 0 elsewhere,
+    so the site energy of each atom of a dimer at r (outside the ZBL range,
+    one neighbour) is sum_mu w1_mu tanh(a_mu s_nu q_nu(r) - b0_mu)
+    + sum_rest w1 tanh(-b0) - b1
+    with q(r) = c_R f(r) (the pinned radial basis).  E = 2 U_site, U_site per
+    atom, and F = -dE/dr (central differences of that closed form).  Catches a
+    missing descriptor scaler, a sign of b0 or b1, a transposed w0."""
+    H, D = MODEL.n_hidden, MODEL.dim
+    nR, KR = 5, 9
+    p = MODEL.params.copy()
+    w0 = np.zeros((H, D))
+    a = np.array([0.7, -1.3, 0.4, 2.1, -0.9])
+    nu = (np.arange(nR) + 2) % nR
+    for mu in range(nR):
+        w0[mu, nu[mu]] = a[mu]
+    b0 = np.linspace(-0.6, 0.8, H)
+    w1 = np.linspace(0.9, -0.5, H)
+    b1 = 0.37
+    p[:H * D] = w0.ravel()
+    p[H * D:H * D + H] = b0
+    p[H * D + H:H * D + 2 * H] = w1
+    p[H * D + 2 * H] = b1
+    cR = p[H * D + 2 * H + 1:H * D + 2 * H + 1 + nR * KR].reshape(nR, KR)
+    s = np.asarray(MODEL.scaler)
+
+    def U_closed(r):
+        q = cR @ O.basis(r, 6.0, KR)[0]
+        h = -b0.copy()
+        h[:nR] += a * s[nu] * q[nu]
+        return float(w1 @ np.tanh(h) - b1)
+
+    box = [40.0, 40.0, 40.0]
+    for r in (2.6, 3.7, 5.2):
+        pos = np.array([[10.0, 11.0, 12.0], [10.0, 11.0, 12.0 + r]])
+        E, F, W, U = O.energy_forces_virial(MODEL, pos, box, [0, 0, 0], params=p)
+        u = U_closed(r)
+        np.testing.assert_allclose(U, [u, u], rtol=1e-12, atol=1e-12)
+        assert E == pytest.approx(2 * u, rel=1e-12, abs=1e-12)
+        h = 1e-5
+        dEdr = 2 * (U_closed(r + h) - U_closed(r - h)) / (2 * h)
+        np.testing.assert_allclose(F[1], [0.0, 0.0, -dEdr], atol=1e-7)
+        np.testing.assert_allclose(F[0], -F[1], atol=1e-12)
+
+
 def test_site_invariances():
     d = _random_env(10, seed=7)
     dR = np.vstack([d, _random_env(25, 4.0, 5.99, seed=8)])
