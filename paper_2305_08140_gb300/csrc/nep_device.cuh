@@ -2016,17 +2016,23 @@ __global__ void __launch_bounds__(TILE, sizeof(R) == 4 && !MS ? 7 : 1) k_radial_
             nepm::cheb<KR, true>(r, P.inv_rcR, T, dT, fc, dfc, dxdr);
             R s1, s2;
             if constexpr (sizeof(R) == 4) {
-                // packed pairs (one FFMA2 per k: (s1, s2) += b_k (T_k, T'_k))
-                float2 ss = __fadd2_rn(make_float2(ri1.x, 0.f), make_float2(rj1.x, 0.f));
-                const float bk[KR - 1] = {ri1.y + rj1.y, ri1.z + rj1.z, ri1.w + rj1.w,
-                                          ri2.x + rj2.x, ri2.y + rj2.y, ri2.z + rj2.z,
-                                          ri2.w + rj2.w, ri0.w + rj0.w};
-#pragma unroll
-                for (int kk = 1; kk < KR; ++kk)
-                    ss = __ffma2_rn(make_float2(bk[kk - 1], bk[kk - 1]),
-                                    make_float2(T[kk], dT[kk]), ss);
-                s1 = ss.x;
-                s2 = ss.y;
+                // packed pairs of adjacent k: (b_k, b_k+1) (T_k, T_k+1) and
+                // (b_k, b_k+1) (T'_k, T'_k+1), with T_0 = 1, T'_0 = 0, T'_1 = 1
+                const float2 b01 = __fadd2_rn(make_float2(ri1.x, ri1.y), make_float2(rj1.x, rj1.y));
+                const float2 b23 = __fadd2_rn(make_float2(ri1.z, ri1.w), make_float2(rj1.z, rj1.w));
+                const float2 b45 = __fadd2_rn(make_float2(ri2.x, ri2.y), make_float2(rj2.x, rj2.y));
+                const float2 b67 = __fadd2_rn(make_float2(ri2.z, ri2.w), make_float2(rj2.z, rj2.w));
+                const float b8 = ri0.w + rj0.w;
+                float2 a1 = __fmul2_rn(b01, make_float2(1.f, T[1]));
+                a1 = __ffma2_rn(b23, make_float2(T[2], T[3]), a1);
+                a1 = __ffma2_rn(b45, make_float2(T[4], T[5]), a1);
+                a1 = __ffma2_rn(b67, make_float2(T[6], T[7]), a1);
+                float2 a2 = make_float2(0.f, b01.y);
+                a2 = __ffma2_rn(b23, make_float2(dT[2], dT[3]), a2);
+                a2 = __ffma2_rn(b45, make_float2(dT[4], dT[5]), a2);
+                a2 = __ffma2_rn(b67, make_float2(dT[6], dT[7]), a2);
+                s1 = (a1.x + a1.y) + b8 * T[8];
+                s2 = (a2.x + a2.y) + b8 * dT[8];
             } else {
                 const R b[KR] = {ri1.x + rj1.x, ri1.y + rj1.y, ri1.z + rj1.z, ri1.w + rj1.w,
                                  ri2.x + rj2.x, ri2.y + rj2.y, ri2.z + rj2.z, ri2.w + rj2.w,
