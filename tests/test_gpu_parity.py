@@ -276,6 +276,36 @@ def test_md_variable_timestep_fp64():
     assert np.abs(_min_image(xg - p, s.box, s.pbc)).max() < 1e-8
 
 
+def test_md_clump_fp32_tiles_split_between_kernels():
+    """FP32 MD of a lattice holding a dense clump (pairs down to ~0.3 A): every
+    step splits the tiles of 128 atoms between the plain Tensor-Memory angular
+    kernel, its close-pair variant and the register kernel (tiles with more
+    than 48 angular neighbours on an atom).  20 steps with variable dt
+    (0.01 A per step) follow the oracle's trajectory; a second run on a fresh
+    context repeats the first bitwise."""
+    from paper_2305_08140_gb300 import nepzbl as N
+    s = I.c3(ncell=10, fraction=0.1, radius=6.0, seed=23)   # up to 85 angular neighbours
+    runs = []
+    for _ in range(2):
+        m = N.NEP(I.nep_model(1), "fp32")
+        m.set_option(N.NEP_OPT_GRAPH_CHUNK, 6)
+        st = N.MDState(N.to_device_soa(s.pos), N.to_device_soa(s.vel), s.box, s.pbc,
+                       dt_max=1.0, d_max=0.01)
+        m.md(st, 20)
+        runs.append((st.xyz.cpu().numpy().T.copy(), st.vel.cpu().numpy().T.copy(), st.time,
+                     st.potential_energy, m.stats()))
+        m.close()
+    x1, v1, t1, e1, st1 = runs[0]
+    x2, v2, t2, e2, _ = runs[1]
+    assert np.array_equal(x1, x2) and np.array_equal(v1, v2) and t1 == t2 and e1 == e2
+    # the register kernel took the dense tiles, Tensor Memory the others
+    assert 0 < st1["angular_tiles_register"] < st1["angular_tiles"], st1
+    assert st1["angular_state_in_tmem"] == 1
+    p, v, F, th = O.md(I.nep_model(1), s.pos, s.vel, s.box, s.pbc, s.mass, 1.0, 20, d_max=0.01)
+    assert t1 == pytest.approx(th[:, 1].sum(), rel=1e-6)
+    assert np.abs(_min_image(x1 - p, s.box, s.pbc)).max() < 1e-6
+
+
 # ---------------------------------------------------------------------------
 # Verlet skin: lists built with r_c + skin and reused; same trajectories
 # ---------------------------------------------------------------------------

@@ -68,6 +68,11 @@ def _wmo_box(ncell=(10, 10, 10), seed=301, sigma=0.08, close=True):
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_w_mo_alloy_2000_atoms(precision):
     _parity(_wmo_box(), WMO, precision, scaled=True)
+    if precision == "fp32":
+        # the several-species angular state in Tensor Memory (its close-pair
+        # variant on the tiles holding the unlike close pairs)
+        st = _nep(WMO, precision).stats()
+        assert st["angular_state_in_tmem"] == 1 and st["angular_tiles_register"] == 0, st
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
