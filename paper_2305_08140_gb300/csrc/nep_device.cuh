@@ -38,18 +38,17 @@ constexpr int C_RAD = 0, C_ANG = 52;   // radial / angular block offsets
 
 // status bits
 constexpr int ST_OVERFLOW = 1, ST_NONFINITE = 2, ST_FORCE_RANGE = 4, ST_BADTYPE = 8;
-// the evaluation has a pair closer than the outer ZBL radius (set by the
-// radial-descriptor pass of the FP32 path)
-constexpr int ST_CLOSE = 16;
 
-// Per-tile kernel choice (FP32, one species).  The radial-descriptor pass
-// (k_neighbors' second pass, or k_radial_q with a Verlet skin; blocks of TILE
-// atoms, so block b is tile b) ORs into tflag[tile]: TILE_CLOSE when an atom of
-// the tile has a pair closer than the outer ZBL radius, TILE_DENSE when one has
-// more than TILE_ANG_LIM angular neighbours.  The angular kernel without the
-// ZBL and close-pair branches (k_nep_ang_tm) takes the tiles with neither bit,
-// the register kernel k_nep_ang the others; the radial-force instantiation
-// without the close-pair branch the tiles without TILE_CLOSE.  Each tile is
+// Per-tile kernel choice (FP32).  The radial-descriptor pass (k_neighbors'
+// second pass, or k_radial_q with several species or a Verlet skin; blocks of
+// TILE atoms, so block b is tile b) ORs into tflag[tile]: TILE_CLOSE when an
+// atom of the tile has a pair closer than the outer ZBL radius, TILE_DENSE
+// when one has more than TILE_ANG_LIM angular neighbours.  The Tensor-Memory
+// angular kernel without the ZBL and close-pair branches (k_nep_ang_tm<false>)
+// takes the tiles with neither bit, its close-pair variant the tiles with
+// TILE_CLOSE alone, the register kernel k_nep_ang the dense ones; with one
+// species the radial-force instantiation without the close-pair branch takes
+// the tiles without TILE_CLOSE, the other the rest.  Each tile is
 // done by exactly one kernel of each pair, so its forces and partial sums are
 // those of the kernel that would do the whole evaluation.
 constexpr int TILE_CLOSE = 1, TILE_DENSE = 2;
@@ -809,7 +808,6 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                 for (int kk = 0; kk < KR; ++kk) acc += rq.hR[n * KR + kk] * Sb[kk];
                 qr[(size_t)n * ld + k] = acc;
             }
-            if (close) atomicOr(status, ST_CLOSE);
             // this tile's kernel choice (blocks of TILE atoms: block = tile)
             const int bits = (close ? TILE_CLOSE : 0) | (sa > TILE_ANG_LIM ? TILE_DENSE : 0);
             if (tflag && bits) tile_mark(tflag, (g.n + TILE - 1) / TILE, blockIdx.x, bits);
@@ -1576,7 +1574,6 @@ __global__ void __launch_bounds__(128) k_radial_q(const Model<R> P, const Grid g
         }
     }
     if (act_cnt) act_cnt[k] = make_int2(a_na, a_nro);
-    if (close) atomicOr(status, ST_CLOSE);
     if (tflag) {
         // this tile's kernel choice (blocks of TILE atoms: block = tile)
         const int bits = (close ? TILE_CLOSE : 0) |
