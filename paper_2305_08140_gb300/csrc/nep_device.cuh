@@ -590,8 +590,11 @@ struct RadCoef {
 // in every case.  Every candidate left out is farther than r_l, so the lists
 // hold the same pairs for any zs and CHW (in slice order within a cell).
 constexpr int NB_CHUNK = 16;
-template <typename R, bool WQ, bool TRIC = false, bool CH = false, int CHW = NB_CHUNK>
-__global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
+// MSW > 0 (with WQ, several species): the basis sums per neighbour species,
+// MSW >= T slots, and q_n = sum_t [C_n(t_i, t) Sb_t,0 + sum_k h_nk(t_i, t) Sb_t,k]
+// with the pair coefficients from coefR ([T * T][CSTR], radial block).
+template <typename R, bool WQ, bool TRIC = false, bool CH = false, int CHW = NB_CHUNK, int MSW = 0>
+__global__ void __launch_bounds__(128, MSW ? 6 : 8) k_neighbors(Grid g, R rcR2, R rcA2,
                                                    const typename V4<R>::T* __restrict__ pos4,
                                                    const int* __restrict__ cell_sorted,
                                                    const int* __restrict__ start,
@@ -603,7 +606,8 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                                                    const RadCoef<R> rq, R* __restrict__ qr,
                                                    const int* __restrict__ perm,
                                                    const double* __restrict__ x64,
-                                                   int* __restrict__ tflag = nullptr)
+                                                   int* __restrict__ tflag = nullptr,
+                                                   const R* __restrict__ coefR = nullptr)
 {
     using P4 = typename V4<R>::T;
     if (gate && *gate == 0) return;   // lists still valid (Verlet skin)
@@ -763,6 +767,12 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
             R Sb[KR];
 #pragma unroll
             for (int kk = 0; kk < KR; ++kk) Sb[kk] = R(0);
+            constexpr int NS = MSW > 0 ? MSW : 1;
+            R Sm[NS][KR];   // several species: per neighbour species
+#pragma unroll
+            for (int t = 0; t < NS; ++t)
+#pragma unroll
+                for (int kk = 0; kk < KR; ++kk) Sm[t][kk] = R(0);
             bool close = false;
             const int ns = sa + sro;
             auto slot = [&](int t) { return t < sa ? t : M - 1 - (t - sa); };
@@ -784,7 +794,15 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                     const R rr = f2 * nepm::nep_rsqrt(f2);
                     R T[KR], dT[KR], fc, dfc, dxdr;
                     nepm::cheb<KR, false>(rr, rq.inv_rcR, T, dT, fc, dfc, dxdr);
-                    if constexpr (sizeof(R) == 4) {
+                    if constexpr (MSW > 0) {
+                        const int tj = (int)pj.w;
+#pragma unroll
+                        for (int t = 0; t < NS; ++t) {
+                            const R wt = tj == t ? fc : R(0);
+#pragma unroll
+                            for (int kk = 0; kk < KR; ++kk) Sm[t][kk] += wt * T[kk];
+                        }
+                    } else if constexpr (sizeof(R) == 4) {
                         // packed pairs: one FFMA2 per two basis functions
 #pragma unroll
                         for (int kk = 0; kk + 1 < KR; kk += 2) {
@@ -801,12 +819,34 @@ __global__ void __launch_bounds__(128, 8) k_neighbors(Grid g, R rcR2, R rcA2,
                     }
                 }
             }
+            if constexpr (MSW > 0) {
+                const int T = g.ntypes, ti = (int)p.w;
+                R q[NR];
 #pragma unroll
-            for (int n = 0; n < NR; ++n) {
-                R acc = rq.CR[n] * Sb[0];
+                for (int n = 0; n < NR; ++n) q[n] = R(0);
 #pragma unroll
-                for (int kk = 0; kk < KR; ++kk) acc += rq.hR[n * KR + kk] * Sb[kk];
-                qr[(size_t)n * ld + k] = acc;
+                for (int t = 0; t < NS; ++t) {
+                    if (t < T) {
+                        const R* c = coefR + ((size_t)ti * T + t) * CSTR + C_RAD;
+#pragma unroll
+                        for (int n = 0; n < NR; ++n) {
+                            R acc = c[NR * KR + n] * Sm[t][0];
+#pragma unroll
+                            for (int kk = 0; kk < KR; ++kk) acc += c[n * KR + kk] * Sm[t][kk];
+                            q[n] += acc;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int n = 0; n < NR; ++n) qr[(size_t)n * ld + k] = q[n];
+            } else {
+#pragma unroll
+                for (int n = 0; n < NR; ++n) {
+                    R acc = rq.CR[n] * Sb[0];
+#pragma unroll
+                    for (int kk = 0; kk < KR; ++kk) acc += rq.hR[n * KR + kk] * Sb[kk];
+                    qr[(size_t)n * ld + k] = acc;
+                }
             }
             // this tile's kernel choice (blocks of TILE atoms: block = tile)
             const int bits = (close ? TILE_CLOSE : 0) | (sa > TILE_ANG_LIM ? TILE_DENSE : 0);

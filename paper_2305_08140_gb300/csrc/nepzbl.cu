@@ -497,7 +497,9 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     // FP64 path keeps the separate pass (FP64 arithmetic in the divergent hit
     // branch of the search costs more than the pass)
     const bool ms = ctx->ntypes > 1;
-    const bool fuse_q = !ms && !gate && sizeof(R) == 4;
+    // (several species: the orthorhombic search with chunks of 16, basis sums
+    // per neighbour species)
+    const bool fuse_q = !gate && sizeof(R) == 4 && (!ms || (!g.tric && ctx->nbr_chw == 16));
     RadCoef<R> rq;
     rq.inv_rcR = P.inv_rcR;
     for (int t = 0; t < NR * KR; ++t) rq.hR[t] = P.hR[t];
@@ -515,10 +517,16 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     // the last atom, see ensure_atoms)
     auto kn = g.tric ? (fuse_q ? k_neighbors<R, true, true, true> : k_neighbors<R, false, true, true>)
                      : neighbor_kernel<R>(fuse_q, ctx->nbr_chw);
+    if (fuse_q && ms)
+        kn = ctx->ntypes <= 2 ? k_neighbors<R, true, false, true, 16, 2>
+                              : k_neighbors<R, true, false, true, 16, 4>;
+    const R* coefR;
+    if constexpr (sizeof(R) == 4) coefR = ctx->coef_f;
+    else coefR = ctx->coef_d;
     kn<<<(n + 127) / 128, 128, 0, s>>>(
         g, (R)(rl * rl), (R)(ra * ra), (const typename V4<R>::T*)ctx->pos4, ctx->cell_sorted,
         ctx->start, ctx->nbr, ctx->cnt, ctx->status, ctx->status + 1, ctx->pairs, gate, rq,
-        (R*)ctx->qr, ctx->perm, x, fuse_q ? tfl : nullptr);
+        (R*)ctx->qr, ctx->perm, x, fuse_q ? tfl : nullptr, ms ? coefR : nullptr);
     count_launch(ctx);
     ctx->radial_q_fused = fuse_q ? 1 : 0;
     if (gate) {
