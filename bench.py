@@ -632,6 +632,10 @@ def run_profile_case(args):
                   (k_batch_pop)
       c2_fp64     one plain-FP64 force evaluation of the 128,000-atom crystal
                   (k_nep_ang<double>, k_radial_force<double>)
+      wmo_md      MD of the 8,192,000-atom slab as a 50/50 W-Mo alloy: 3 steps,
+                  then graph chunks of 5 (the several-species kernels)
+      c3_md       MD of the 250,000-atom crystal with a dense clump, variable dt
+                  (0.01 A per step): 3 steps, then graph chunks of 5
     """
     import torch
     from paper_2305_08140_gb300 import nepzbl as N
@@ -657,6 +661,29 @@ def run_profile_case(args):
                                                           dtype=torch.float64, device=dev)
             for _ in range(reps):
                 N.population_loss(nep, b, thetas, Et, Ft, Wt)
+        nep.close()
+    elif args.profile_case == "c3_md":
+        s = I.c3()
+        nep = N.NEP(model, "fp32")
+        st = N.MDState(N.to_device_soa(s.pos, dev), N.to_device_soa(s.vel, dev), s.box, s.pbc,
+                       dt_max=1.0, d_max=0.01)
+        nep.set_option(N.NEP_OPT_GRAPH_CHUNK, 5)
+        nep.md(st, 3)
+        for _ in range(reps):
+            nep.md(st, 5)
+        torch.cuda.synchronize()
+        nep.close()
+    elif args.profile_case == "wmo_md":
+        s = I.alloy(I.c5(), [0.5, 0.5], seed=305)
+        nep = N.NEP(I.nep_model(301, species=("W", "Mo")), "fp32")
+        types = torch.tensor(s.types, dtype=torch.int32, device=dev)
+        st = N.MDState(N.to_device_soa(s.pos, dev), N.to_device_soa(s.vel, dev), s.box, s.pbc,
+                       dt_max=1.0, types=types)
+        nep.set_option(N.NEP_OPT_GRAPH_CHUNK, 5)
+        nep.md(st, 3)
+        for _ in range(reps):
+            nep.md(st, 5)
+        torch.cuda.synchronize()
         nep.close()
     elif args.profile_case == "c2_fp64":
         s = I.displaced(I.c2(), 0.05, 41)
@@ -686,7 +713,7 @@ def main():
     ap.add_argument("--ncell", type=int, default=160,
                     help="slab size in bcc cells per side (160 = the 8,192,000-atom workload; "
                          "smaller values only for profiling)")
-    ap.add_argument("--profile-case", choices=["c4_loss", "c4_pop", "c2_fp64"], default=None,
+    ap.add_argument("--profile-case", choices=["c4_loss", "c4_pop", "c2_fp64", "wmo_md", "c3_md"], default=None,
                     help="run one other workload --steps times without timing (for ncu)")
     args = ap.parse_args()
     if args.warmup < 3:
