@@ -1722,10 +1722,173 @@ __device__ __forceinline__ void tile_partials(double e_site, R (&w)[9], double (
     }
 }
 
+// Close pairs in the register kernel (FP32 path).  A warp runs every pair
+// slot for all 32 lanes, and FP64 arithmetic runs at a small fraction of the
+// FP32 rate on this part, so an FP64 displacement or ZBL term taken inline
+// costs the warp a full FP64 sequence in each slot in which any lane has a
+// close pair; in a dense clump (~13 of ~100 angular pairs inside 2 A) that is
+// nearly every slot.  Instead each atom lists its close pairs (up to CQ; more
+// are taken inline) and the warp does their FP64 work with one pair per lane:
+//   before the descriptor pass: the FP64 displacement of each listed pair,
+//     rounded once to FP32 (as close_pair_fp64), read back in both passes;
+//   after the pair-force pass: the ZBL term (Eq. 2-4) of each listed pair
+//     inside the outer radius; the lane that evaluates it adds the
+//     neighbour's share of the force, the atom's own lane then adds its
+//     energy, force and FP64 virial in slot order, so every sum is the one of
+//     the inline form, in the same order.
+constexpr int CQ = 32;
+// dynamic shared memory of the register kernel behind the staged entries:
+// the close-pair lists [CQ][TILE] float4, the ZBL results [9][TILE] double
+// and the per-warp prefix counts [TILE] int
+constexpr size_t CQ_BYTES = sizeof(float4) * CQ * TILE + sizeof(double) * 9 * TILE + sizeof(int) * TILE;
+
+// The per-lane list lengths of the warp's lanes in mask (lanes 0..nact-1:
+// the atoms of a tile that exist) as an inclusive prefix in inc[0..nact-1]
+// (the warp's own entries); returns the warp's total.
+__device__ __forceinline__ int warp_list_prefix(int cnt, int* __restrict__ inc, unsigned mask)
+{
+    const int lane = threadIdx.x & 31;
+    int v = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(mask, v, o);
+        if (lane >= o) v += t;
+    }
+    inc[lane] = v;
+    __syncwarp(mask);
+    return __shfl_sync(mask, v, 31 - __clz(mask));
+}
+
+// The lane owning entry e of the warp's lists (inc as above, nact lanes) and
+// the entry's index c within that lane's list.
+__device__ __forceinline__ int warp_entry_owner(const int* __restrict__ inc, int nact, int e, int& c)
+{
+    int lo = 0, hi = nact - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (inc[mid] > e) hi = mid;
+        else lo = mid + 1;
+    }
+    c = e - (lo > 0 ? inc[lo - 1] : 0);
+    return lo;
+}
+
+// cd[c * TILE + t] = (dx, dy, dz, slot) of the c-th listed pair of the
+// block's atom t: on entry the slot (int bits), on return also the FP64
+// displacement rounded to FP32.  Collective over the lanes in mask (see
+// warp_list_prefix); nc = this lane's count.
+__device__ __forceinline__ void close_refine_warp(const Grid& g, const double* __restrict__ x64,
+                                                  const int* __restrict__ perm,
+                                                  const int* __restrict__ s_ent, bool staged,
+                                                  const int* __restrict__ nbr, size_t ld,
+                                                  int tile, float4* __restrict__ cd,
+                                                  int* __restrict__ inc, int nc, unsigned mask)
+{
+    const int total = warp_list_prefix(nc, inc, mask);
+    const int lane = threadIdx.x & 31, wb = threadIdx.x & ~31, nact = __popc(mask);
+    for (int e = lane; e < total; e += nact) {
+        int c;
+        const int t = wb + warp_entry_owner(inc, nact, e, c);
+        const int ko = tile * TILE + t;
+        float4 v = cd[c * TILE + t];
+        const int s = __float_as_int(v.w);
+        const int ent = staged ? s_ent[s * TILE + t] : nbr[(size_t)s * ld + ko];
+        double d[3];
+        disp64(g, x64, perm[ko], perm[ent >> 5], d);
+        v.x = (float)d[0];
+        v.y = (float)d[1];
+        v.z = (float)d[2];
+        cd[c * TILE + t] = v;
+    }
+    __syncwarp(mask);
+}
+
+// The ZBL terms of the listed pairs: cd[c * TILE + t].w = neighbour m (int
+// bits) of the c-th pair of atom t with r < outer radius; zr [9][TILE]
+// doubles of scratch.  Collective over the lanes in mask; nz = this lane's
+// count; ez, fi, wz, bad, has_zbl are this lane's atom's sums, continued as
+// the inline form would.
+template <bool MS>
+__device__ __forceinline__ void zbl_warp(const Model<float>& P, const Grid& g,
+                                         const double* __restrict__ x64,
+                                         const int* __restrict__ perm,
+                                         const float4* __restrict__ pos4,
+                                         long long* __restrict__ facc, size_t ld, int tile,
+                                         const float4* __restrict__ cd, double* __restrict__ zr,
+                                         int* __restrict__ inc, int nz, unsigned mask,
+                                         double& ez, long long (&fi)[3], double (&wz)[9],
+                                         bool& bad, bool& has_zbl)
+{
+    using A_ = Acc<float>;
+    const int total = warp_list_prefix(nz, inc, mask);
+    const int lane = threadIdx.x & 31, wb = threadIdx.x & ~31, nact = __popc(mask);
+    const int start = inc[lane] - nz;
+    for (int b0 = 0; b0 < total; b0 += nact) {
+        const int e = b0 + lane;
+        if (e < total) {
+            int c;
+            const int t = wb + warp_entry_owner(inc, nact, e, c);
+            const int ko = tile * TILE + t;
+            const int m = __float_as_int(cd[c * TILE + t].w);
+            double d64[3];
+            disp64(g, x64, perm[ko], perm[m], d64);
+            const double r64 = sqrt(d64[0] * d64[0] + d64[1] * d64[1] + d64[2] * d64[2]);
+            double in = 0.0, uh = 0.0, cc = 0.0, f3[3] = {0.0, 0.0, 0.0};
+            if (r64 < P.zbl_rr2) {
+                double Uz, dUz;
+                const int pz = MS ? (int)pos4[ko].w * P.ntypes + (int)pos4[m].w : 0;
+                zbl_pair(r64, MS ? P.zbl_kp[pz] : P.zbl_k, MS ? P.zbl_inv_ap[pz] : P.zbl_inv_a,
+                         P.zbl_r1, P.zbl_rr2, Uz, dUz);
+                in = 1.0;
+                uh = 0.5 * Uz;
+                cc = 0.5 * dUz / r64;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) f3[a] = cc * d64[a];
+                A_::add(&facc[m], -A_::convd(f3[0]));
+                A_::add(&facc[ld + m], -A_::convd(f3[1]));
+                A_::add(&facc[2 * ld + m], -A_::convd(f3[2]));
+            }
+            zr[threadIdx.x] = in;
+            zr[TILE + threadIdx.x] = uh;
+            zr[2 * TILE + threadIdx.x] = cc;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                zr[(3 + a) * TILE + threadIdx.x] = f3[a];
+                zr[(6 + a) * TILE + threadIdx.x] = d64[a];
+            }
+        }
+        __syncwarp(mask);
+        // this lane's entries among the batch, in slot order
+        const int lo = start > b0 ? start : b0;
+        const int hi = start + nz < b0 + nact ? start + nz : b0 + nact;
+        for (int e2 = lo; e2 < hi; ++e2) {
+            const int q = wb + (e2 - b0);
+            if (zr[q] != 0.0) {
+                ez += zr[TILE + q];
+                const double cc = zr[2 * TILE + q];
+                const double f3[3] = {zr[3 * TILE + q], zr[4 * TILE + q], zr[5 * TILE + q]};
+                const double d64[3] = {zr[6 * TILE + q], zr[7 * TILE + q], zr[8 * TILE + q]};
+                fi[0] += A_::convd(f3[0]);
+                fi[1] += A_::convd(f3[1]);
+                fi[2] += A_::convd(f3[2]);
+                bad |= !isfinite(cc);
+                has_zbl = true;
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) wz[3 * a + b] -= f3[a] * d64[b];
+            }
+        }
+        __syncwarp(mask);
+    }
+}
+
 // MS (several species): the coefficient table of all ordered species pairs
 // is copied to shared memory ahead of the staged entries; each angular pair
 // reads its own block, and the radial adjoint is written once per neighbour
 // species (br[(k * T + t) * 3]).
+// FP32: the close pairs' FP64 work warp-wide (see CQ) in shared memory
+// behind the staged entries.
 template <typename R, bool MS>
 __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g,
                                                   const typename V4<R>::T* __restrict__ pos4,
@@ -1751,11 +1914,15 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
     __shared__ P4 s_off[27];
     __shared__ int s_max;
     // dynamic: [T * T * CSTR] coefficients (MS only), then [stage_slots][TILE]
-    // angular entries
+    // angular entries, then (FP32) the close-pair lists (see CQ)
     extern __shared__ __align__(16) unsigned char s_dyn[];
     const int T = MS ? P.ntypes : 1;
     R* s_coef = reinterpret_cast<R*>(s_dyn);
     int* s_ent = reinterpret_cast<int*>(s_dyn + (MS ? sizeof(R) * T * T * CSTR : 0));
+    constexpr bool CW = sizeof(R) == 4;   // close pairs warp-wide
+    float4* s_cd = reinterpret_cast<float4*>(s_ent + (size_t)stage_slots * TILE);
+    double* s_zr = reinterpret_cast<double*>(s_cd + CQ * TILE);
+    int* s_inc = reinterpret_cast<int*>(s_zr + 9 * TILE) + (threadIdx.x & ~31);
     if constexpr (MS) {
         for (int t = threadIdx.x; t < T * T * CSTR; t += TILE) s_coef[t] = coef[t];
     }
@@ -1789,6 +1956,7 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
     bool has_zbl = false;
 #pragma unroll
     for (int t = 0; t < 9; ++t) { w[t] = R(0); wz[t] = 0.0; }
+    const unsigned vmask = __ballot_sync(0xffffffffu, k < g.n);   // a prefix of the warp
 
     if (k < g.n) {
         const P4 pi = pos4[k];
@@ -1796,6 +1964,40 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
         auto entry = [&](int s) -> int {
             return staged ? s_ent[s * TILE + threadIdx.x] : nbr[(size_t)s * ld + k];
         };
+        // FP32: the slots of this atom's close pairs (r^2 below the squared
+        // outer ZBL radius, in the passes' own FP32 form), the first CQ listed
+        // with their FP64 displacements (warp-wide, see CQ); from slot s_inl
+        // on (more than CQ) the passes refine close pairs inline
+        int ncq = 0, s_inl = 0x7fffffff;
+        if constexpr (CW) {
+            int nc = 0;
+            int ent_c = na > 0 ? entry(0) : 0;
+            P4 pj_c = na > 0 ? pos4[ent_c >> 5] : pi;
+            for (int s = 0; s < na; ++s) {
+                const int ent = ent_c;
+                const P4 pj = pj_c;
+                if (s + 1 < na) {
+                    ent_c = entry(s + 1);
+                    pj_c = pos4[ent_c >> 5];
+                }
+                const P4 off = s_off[ent & 31];
+                const R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
+                const R r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 < P.zbl_r2 * P.zbl_r2) {
+                    if (nc < CQ) s_cd[nc * TILE + threadIdx.x] = make_float4(0.f, 0.f, 0.f, __int_as_float(s));
+                    else if (nc == CQ) s_inl = s;
+                    ++nc;
+                }
+            }
+            ncq = nc < CQ ? nc : CQ;
+            close_refine_warp(g, x64, perm, s_ent, staged, nbr, ld, tile, s_cd, s_inc, ncq, vmask);
+        }
+        // the next listed close pair (its slot; -1: none left)
+        int ci = 0;
+        auto listed_slot = [&](int c) -> int {
+            return c < ncq ? __float_as_int(s_cd[c * TILE + threadIdx.x].w) : -1;
+        };
+        int next_s = CW ? listed_slot(0) : -1;
         R A[NA][NLM];
 #pragma unroll
         for (int n = 0; n < NA; ++n)
@@ -1813,8 +2015,17 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
             const P4 off = s_off[ent & 31];
             R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
             R r2 = dx * dx + dy * dy + dz * dz;
+            bool listed = false;
+            if (CW && s == next_s) {
+                const float4 v = s_cd[ci * TILE + threadIdx.x];
+                dx = v.x; dy = v.y; dz = v.z;
+                r2 = dx * dx + dy * dy + dz * dz;
+                listed = true;
+                next_s = listed_slot(++ci);
+            }
             if (r2 >= P.rcA2) continue;   // beyond r_c^A (lists built with a skin)
-            close_pair_fp64<R>(P.zbl_r2 * P.zbl_r2, g, x64, perm, k, ent >> 5, dx, dy, dz, r2);
+            if (!CW || (!listed && s >= s_inl))
+                close_pair_fp64<R>(P.zbl_r2 * P.zbl_r2, g, x64, perm, k, ent >> 5, dx, dy, dz, r2);
             const R inv_r = nepm::nep_rsqrt(r2);
             const R r = r2 * inv_r;
             R Tk[KA], dT[KA], fc, dfc, dxdr;
@@ -1893,6 +2104,11 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
         const int i_caller = perm[k];
         ent_n = na > 0 ? entry(0) : 0;
         pj_n = na > 0 ? pos4[ent_n >> 5] : pi;
+        // listed close pairs again in slot order; those with a ZBL term are
+        // queued in the consumed list entries (nz <= ci) for zbl_warp
+        ci = 0;
+        next_s = CW ? listed_slot(0) : -1;
+        int nz = 0;
         for (int s = 0; s < na; ++s) {
             const int ent = ent_n;
             const P4 pj = pj_n;
@@ -1904,11 +2120,21 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
             const P4 off = s_off[ent & 31];
             R dx = pj.x - pi.x + off.x, dy = pj.y - pi.y + off.y, dz = pj.z - pi.z + off.z;
             R r2 = dx * dx + dy * dy + dz * dz;
+            bool listed = false;
+            if (CW && s == next_s) {
+                const float4 v = s_cd[ci * TILE + threadIdx.x];
+                dx = v.x; dy = v.y; dz = v.z;
+                r2 = dx * dx + dy * dy + dz * dz;
+                listed = true;
+                next_s = listed_slot(++ci);
+            }
             if (r2 >= P.rcA2) continue;
-            // close pair (FP32 path): the FP64 displacement, formed once for the
-            // NEP terms (rounded, see close_pair_fp64) and the ZBL term
+            // close pair (FP32 path) not listed: the FP64 displacement, formed
+            // once for the NEP terms (rounded, see close_pair_fp64) and the ZBL
+            // term
             double d64[3];
-            const bool close = sizeof(R) == 4 && r2 < P.zbl_r2 * P.zbl_r2;
+            const bool close = sizeof(R) == 4 && !listed && (!CW || s >= s_inl) &&
+                               r2 < P.zbl_r2 * P.zbl_r2;
             if (close) {
                 disp64(g, x64, i_caller, perm[m], d64);
                 dx = (R)d64[0];
@@ -1924,7 +2150,10 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
                                  : nullptr);
             bad |= !isfinite(fx + fy + fz);
             typename A_::T cx = A_::conv(fx), cy = A_::conv(fy), cz = A_::conv(fz);
-            if (r < P.zbl_r2) {
+            if (CW && listed && r < P.zbl_r2) {
+                s_cd[nz * TILE + threadIdx.x].w = __int_as_float(m);
+                ++nz;
+            } else if (r < P.zbl_r2) {
                 if (sizeof(R) == 4) {
                     if (!close) disp64(g, x64, i_caller, perm[m], d64);
                 } else {
@@ -1958,6 +2187,9 @@ __global__ void __launch_bounds__(TILE) k_nep_ang(const Model<R> P, const Grid g
             w[3] -= fy * dx; w[4] -= fy * dy; w[5] -= fy * dz;
             w[6] -= fz * dx; w[7] -= fz * dy; w[8] -= fz * dz;
         }
+        if constexpr (CW)
+            zbl_warp<MS>(P, g, x64, perm, pos4, facc, ld, tile, s_cd, s_zr, s_inc, nz, vmask, ez,
+                         fi, wz, bad, has_zbl);
         A_::add(&facc[k], fi[0]);
         A_::add(&facc[ld + k], fi[1]);
         A_::add(&facc[2 * ld + k], fi[2]);

@@ -563,13 +563,16 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
     // memory when they fit; with several species the pair coefficients first)
     const int stage_slots = ctx->M < STAGE_MAX_SLOTS ? ctx->M : STAGE_MAX_SLOTS;
     const size_t coef_bytes = ms ? sizeof(R) * (size_t)ctx->ntypes * ctx->ntypes * CSTR : 0;
-    const size_t stage_bytes = coef_bytes + sizeof(int) * (size_t)stage_slots * TILE;
+    // (FP32: the close-pair lists behind them, see CQ)
+    const size_t stage_bytes = coef_bytes + sizeof(int) * (size_t)stage_slots * TILE +
+                               (sizeof(R) == 4 ? CQ_BYTES : 0);
     auto kang = ms ? k_nep_ang<R, true> : k_nep_ang<R, false>;
     const int ks = (sizeof(R) == 4 ? 0 : 2) + (ms ? 1 : 0);
     if (!ctx->nep_smem_set[ks]) {
         CK(cudaFuncSetAttribute(kang, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(sizeof(R) * NT_MAX * NT_MAX * CSTR +
-                                      sizeof(int) * STAGE_MAX_SLOTS * TILE)));
+                                      sizeof(int) * STAGE_MAX_SLOTS * TILE +
+                                      (sizeof(R) == 4 ? CQ_BYTES : 0))));
         ctx->nep_smem_set[ks] = 1;
     }
     ctx->ang_dispatch = dispatch ? 1 : 0;
