@@ -517,6 +517,7 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
     for (int t = 0; t < 9; ++t) wv[t] = 0.f;
     double ez = 0.0;   // CLOSE: half the ZBL energy of the atom's pairs
     unsigned long long zmask = 0;   // CLOSE: pairs (slots < 64) with a ZBL term
+    bool zhad = false;              // CLOSE: a ZBL term was added
     bool bad = !isfinite(U);
     const int i_caller = valid ? perm[k] : 0;
     int ent_n = na > 0 ? entry(0) : 0;
@@ -600,6 +601,7 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
                 A_::add(&facc[ld + m], -zy);
                 A_::add(&facc[2 * ld + m], -zz);
                 bad |= !isfinite(c);
+                zhad = true;
 #pragma unroll
                 for (int a3 = 0; a3 < 3; ++a3)
 #pragma unroll
@@ -620,7 +622,8 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
     }
 
     // block partials (fixed order): energy and virial by shuffles (the FP64
-    // ZBL virial of CLOSE tiles on its own, then added)
+    // ZBL virial of CLOSE tiles on its own, then added; skipped, as the sums of
+    // zeros it would give, by warps without a ZBL term: FP64 adds are slow here)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e_site += __shfl_xor_sync(0xffffffffu, e_site, o);
 #pragma unroll
@@ -629,9 +632,10 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
         for (int o = 16; o > 0; o >>= 1) wv[t] += __shfl_xor_sync(0xffffffffu, wv[t], o);
     double wzs[9];
 #pragma unroll
-    for (int t = 0; t < 9; ++t) {
-        wzs[t] = 0.0;
-        if constexpr (CLOSE) {
+    for (int t = 0; t < 9; ++t) wzs[t] = 0.0;
+    if (CLOSE && __any_sync(0xffffffffu, zhad)) {
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
             wzs[t] = s_wz[t * TILE + threadIdx.x];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) wzs[t] += __shfl_xor_sync(0xffffffffu, wzs[t], o);
