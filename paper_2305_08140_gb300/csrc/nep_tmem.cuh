@@ -212,6 +212,16 @@ __device__ __forceinline__ void tm_rmw8(uint32_t a, float g, const float* Y)
 }
 
 // The descriptor sums A_nlm = sum_j g_n(r_ij) Y_lm(u_ij) over the atom's
+// CLOSE variant: pairs whose FP32 r^2 is below the squared outer ZBL radius,
+// widened by 10^-5 so that every pair whose FP32 distance r^2 rsqrt(r^2) can
+// fall below that radius (rsqrtf: 2 ulp) is among them; they take the FP64
+// displacement (close_pair_fp64 refines below the radius itself: pairs in
+// the margin, at the ZBL switch's zero, are refined as well).
+__device__ __forceinline__ bool close_deferred(const Model<float>& P, float r2)
+{
+    return r2 < P.zbl_r2 * P.zbl_r2 * 1.00001f;
+}
+
 // angular pairs in one pass: radial channels 0-2 in registers (72 sums),
 // channels 3-4 in their Tensor-Memory columns, read, updated and written back
 // per pair and harmonic group (lm 0-7, 8-15, 16-23).  The Tensor-Memory
@@ -220,8 +230,11 @@ __device__ __forceinline__ void tm_rmw8(uint32_t a, float g, const float* Y)
 // of the descriptor (q_nl = sum_m A_nlm^2, q_n^4b) to shared memory
 // (s_q[nu - NR][TILE], this thread's column) and channels 0-2 to Tensor
 // Memory (stores not waited for).  CLOSE: pairs inside the outer ZBL radius
-// take their displacement from the FP64 positions (close_pair_fp64; g, x64,
-// perm and this atom's slot k serve it).
+// (close_deferred) take their displacement from the FP64 positions (as
+// close_pair_fp64; g, x64, perm and this atom's slot k serve it); they are
+// left out of the pass (cmask: their slots) and added after it, one per lane
+// and iteration, so that the FP64 work runs once per deferred pair of the
+// busiest lane instead of in every slot in which some lane has one.
 template <bool CLOSE, bool MS, typename Entry>
 __device__ __forceinline__ void ang_desc_sums(const Model<float>& P, const float4* __restrict__ pos4,
                                               const StencilSplit<float>& s_off, int na, int nmax,
@@ -245,23 +258,10 @@ __device__ __forceinline__ void ang_desc_sums(const Model<float>& P, const float
 #pragma unroll
         for (int c = NN * NLM; c < NA * NLM; c += 8) tm_st8(tb + (uint32_t)c, z);
     }
-    int ent_n = na > 0 ? entry(0) : 0;
-    float4 pj_n = na > 0 ? pos4[ent_n >> 5] : pi;
-    for (int s = 0; s < nmax; ++s) {
-        const bool act = s < na;
-        const int ent = ent_n;
-        const float4 pj = pj_n;
-        if (s + 1 < na) {
-            ent_n = entry(s + 1);
-            pj_n = pos4[ent_n >> 5];
-        }
-        const int code = ent & 31;
-        float dx = pj.x - pi.x + s_off.x[code], dy = pj.y - pi.y + s_off.y[code],
-              dz = pj.z - pi.z + s_off.z[code];
-        float r2 = dx * dx + dy * dy + dz * dz;
-        if (CLOSE && act)
-            close_pair_fp64<float>(P.zbl_r2 * P.zbl_r2, g, x64, perm, k, ent >> 5, dx, dy, dz, r2);
-        if (!act) { dx = 1.f; dy = 0.f; dz = 0.f; r2 = 1.f; }   // placeholder pair, adds zero
+    // one pair (act = false: a placeholder that adds zero); collective over
+    // the warp (the channel 3-4 columns)
+    auto add_pair = [&](float dx, float dy, float dz, float r2, bool act, float tj) {
+        if (!act) { dx = 1.f; dy = 0.f; dz = 0.f; r2 = 1.f; }
         // beyond r_c^A (lists built with a skin) or a placeholder: g_n = 0
         const bool in = act && r2 < P.rcA2;
         const float inv_r = nepm::nep_rsqrt(r2);
@@ -269,7 +269,7 @@ __device__ __forceinline__ void ang_desc_sums(const Model<float>& P, const float
         float Tk[KA], dT[KA], fc, dfc, dxdr;
         nepm::cheb<KA, false>(r, P.inv_rcA, Tk, dT, fc, dfc, dxdr);
         const float fcm = in ? fc : 0.f;
-        const float* cs = MS ? s_coef + ((size_t)ti * T + (int)pj.w) * CSTR + C_ANG : nullptr;
+        const float* cs = MS ? s_coef + ((size_t)ti * T + (int)tj) * CSTR + C_ANG : nullptr;
         float gn[NA];
 #pragma unroll
         for (int n = 0; n < NA; ++n) {
@@ -298,6 +298,46 @@ __device__ __forceinline__ void ang_desc_sums(const Model<float>& P, const float
                                             A[n][4 * GR + p]);
 #pragma unroll
             for (int n = NN; n < NA; ++n) tm_rmw8(tb + (uint32_t)(n * NLM + 8 * GR), gn[n], Y);
+        }
+    };
+    unsigned long long cmask = 0;   // CLOSE: deferred slots (< 64: at most TILE_ANG_LIM pairs)
+    int ent_n = na > 0 ? entry(0) : 0;
+    float4 pj_n = na > 0 ? pos4[ent_n >> 5] : pi;
+    for (int s = 0; s < nmax; ++s) {
+        const bool act = s < na;
+        const int ent = ent_n;
+        const float4 pj = pj_n;
+        if (s + 1 < na) {
+            ent_n = entry(s + 1);
+            pj_n = pos4[ent_n >> 5];
+        }
+        const int code = ent & 31;
+        const float dx = pj.x - pi.x + s_off.x[code], dy = pj.y - pi.y + s_off.y[code],
+                    dz = pj.z - pi.z + s_off.z[code];
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const bool defer = CLOSE && act && close_deferred(P, r2);
+        if (defer) cmask |= 1ull << s;
+        add_pair(dx, dy, dz, r2, act && !defer, pj.w);
+    }
+    if constexpr (CLOSE) {
+        // the deferred pairs with their FP64 displacements
+        const int cm = __reduce_max_sync(0xffffffffu, __popcll(cmask));
+        const int kc = perm[k < g.n ? k : 0];
+        for (int j = 0; j < cm; ++j) {
+            const bool act = cmask != 0;
+            float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f, tj = 0.f;
+            if (act) {
+                const int ent = entry(__ffsll((long long)cmask) - 1);
+                cmask &= cmask - 1;
+                double d[3];
+                disp64(g, x64, kc, perm[ent >> 5], d);
+                dx = (float)d[0];
+                dy = (float)d[1];
+                dz = (float)d[2];
+                r2 = dx * dx + dy * dy + dz * dz;
+                if constexpr (MS) tj = pos4[ent >> 5].w;
+            }
+            add_pair(dx, dy, dz, r2, act, tj);
         }
     }
     // channels 3-4: the final sums back from Tensor Memory
@@ -516,13 +556,39 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
 #pragma unroll
     for (int t = 0; t < 9; ++t) wv[t] = 0.f;
     double ez = 0.0;   // CLOSE: half the ZBL energy of the atom's pairs
-    unsigned long long zmask = 0;   // CLOSE: pairs (slots < 64) with a ZBL term
     bool zhad = false;              // CLOSE: a ZBL term was added
     bool bad = !isfinite(U);
     const int i_caller = valid ? perm[k] : 0;
+    float buf[2][8];   // two 8-column groups of the adjoint (see force_pair_ang_tm)
+    // one pair (act = false: a placeholder, result unused); collective over
+    // the warp (the adjoint columns); more: prefetch for a next pair
+    auto force_pair = [&](float dx, float dy, float dz, float r2, bool act, int m, float tj,
+                          bool more) -> bool {
+        if (!act) { dx = 1.f; dy = 0.f; dz = 0.f; r2 = 1.f; }
+        const bool in = act && r2 < P.rcA2;
+        const float inv_r = nepm::nep_rsqrt(r2);
+        const float r = r2 * inv_r;
+        float fx, fy, fz;
+        force_pair_ang_tm<MS>(P, r, inv_r, dx * inv_r, dy * inv_r, dz * inv_r, tb, buf, more,
+                              fx, fy, fz,
+                              MS ? s_coef + ((size_t)ti * T + (int)tj) * CSTR + C_ANG : nullptr);
+        if (in) {
+            bad |= !isfinite(fx + fy + fz);
+            const long long cx = A_::conv(fx), cy = A_::conv(fy), cz = A_::conv(fz);
+            fi[0] += cx; fi[1] += cy; fi[2] += cz;
+            A_::add(&facc[m], -cx);
+            A_::add(&facc[ld + m], -cy);
+            A_::add(&facc[2 * ld + m], -cz);
+            wv[0] -= fx * dx; wv[1] -= fx * dy; wv[2] -= fx * dz;
+            wv[3] -= fy * dx; wv[4] -= fy * dy; wv[5] -= fy * dz;
+            wv[6] -= fz * dx; wv[7] -= fz * dy; wv[8] -= fz * dz;
+        }
+        return in && r < P.zbl_r2;
+    };
+    // CLOSE: the pairs deferred as in ang_desc_sums (slots < 64)
+    unsigned long long cmask = 0;
     int ent_n = na > 0 ? entry(0) : 0;
     float4 pj_n = na > 0 ? pos4[ent_n >> 5] : pi;
-    float buf[2][8];   // two 8-column groups of the adjoint (see force_pair_ang_tm)
     if (nmax > 0) tm_ld8(tb, buf[0]);
     for (int s = 0; s < nmax; ++s) {
         const bool act = s < na;
@@ -532,80 +598,62 @@ __global__ void __launch_bounds__(TILE, TM_BLOCKS_PER_SM)
             ent_n = entry(s + 1);
             pj_n = pos4[ent_n >> 5];
         }
-        const int m = ent >> 5;
         const int code = ent & 31;
-        float dx = pj.x - pi.x + s_off.x[code], dy = pj.y - pi.y + s_off.y[code],
-              dz = pj.z - pi.z + s_off.z[code];
-        float r2 = dx * dx + dy * dy + dz * dz;
-        // CLOSE: a pair inside the outer ZBL radius takes the FP64
-        // displacement, formed once for the NEP terms (rounded, as
-        // close_pair_fp64) and the ZBL term
-        double d64[3];
-        const bool close = CLOSE && act && r2 < P.zbl_r2 * P.zbl_r2;
-        if (close) {
-            disp64(g, x64, i_caller, perm[m], d64);
-            dx = (float)d64[0];
-            dy = (float)d64[1];
-            dz = (float)d64[2];
-            r2 = dx * dx + dy * dy + dz * dz;
-        }
-        if (!act) { dx = 1.f; dy = 0.f; dz = 0.f; r2 = 1.f; }   // placeholder pair, result unused
-        const bool in = act && r2 < P.rcA2;
-        const float inv_r = nepm::nep_rsqrt(r2);
-        const float r = r2 * inv_r;
-        float fx, fy, fz;
-        force_pair_ang_tm<MS>(P, r, inv_r, dx * inv_r, dy * inv_r, dz * inv_r, tb, buf,
-                              s + 1 < nmax, fx, fy, fz,
-                              MS ? s_coef + ((size_t)ti * T + (int)pj.w) * CSTR + C_ANG : nullptr);
-        if (in) {
-            bad |= !isfinite(fx + fy + fz);
-            const long long cx = A_::conv(fx), cy = A_::conv(fy), cz = A_::conv(fz);
-            // the ZBL term of a pair inside the outer radius: after the loop
-            if (CLOSE && r < P.zbl_r2) zmask |= 1ull << s;
-            fi[0] += cx; fi[1] += cy; fi[2] += cz;
-            A_::add(&facc[m], -cx);
-            A_::add(&facc[ld + m], -cy);
-            A_::add(&facc[2 * ld + m], -cz);
-            wv[0] -= fx * dx; wv[1] -= fx * dy; wv[2] -= fx * dz;
-            wv[3] -= fy * dx; wv[4] -= fy * dy; wv[5] -= fy * dz;
-            wv[6] -= fz * dx; wv[7] -= fz * dy; wv[8] -= fz * dz;
-        }
+        const float dx = pj.x - pi.x + s_off.x[code], dy = pj.y - pi.y + s_off.y[code],
+                    dz = pj.z - pi.z + s_off.z[code];
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const bool defer = CLOSE && act && close_deferred(P, r2);
+        if (defer) cmask |= 1ull << s;
+        force_pair(dx, dy, dz, r2, act && !defer, ent >> 5, pj.w, s + 1 < nmax);
     }
     if constexpr (CLOSE) {
-        // ZBL terms (Eq. 2-4, FP64) of the pairs marked in the pair loop (a
-        // tile here has at most TILE_ANG_LIM angular neighbours per atom, so
-        // their slots are below 64), each converted and added on its own, as
+        // the deferred pairs: the FP64 displacement, formed once for the NEP
+        // terms (rounded, as close_pair_fp64) and the ZBL term (Eq. 2-4,
+        // FP64), in slot order; each term converted and added on its own, as
         // in k_nep_ang; the FP64 virial of the atom to shared memory
         double wz[9];
 #pragma unroll
         for (int t = 0; t < 9; ++t) wz[t] = 0.0;
-        while (zmask) {
-            const int sz = __ffsll((long long)zmask) - 1;
-            zmask &= zmask - 1;
-            const int m = entry(sz) >> 5;
-            double d64[3];
-            disp64(g, x64, i_caller, perm[m], d64);
-            const double r64 = sqrt(d64[0] * d64[0] + d64[1] * d64[1] + d64[2] * d64[2]);
-            if (r64 < P.zbl_rr2) {
-                double Uz, dUz;
-                const int pz = MS ? ti * T + (int)pos4[m].w : 0;
-                zbl_pair(r64, MS ? P.zbl_kp[pz] : P.zbl_k, MS ? P.zbl_inv_ap[pz] : P.zbl_inv_a,
-                         P.zbl_r1, P.zbl_rr2, Uz, dUz);
-                ez += 0.5 * Uz;
-                const double c = 0.5 * dUz / r64;
-                const double f3[3] = {c * d64[0], c * d64[1], c * d64[2]};
-                const long long zx = A_::convd(f3[0]), zy = A_::convd(f3[1]),
-                                zz = A_::convd(f3[2]);
-                fi[0] += zx; fi[1] += zy; fi[2] += zz;
-                A_::add(&facc[m], -zx);
-                A_::add(&facc[ld + m], -zy);
-                A_::add(&facc[2 * ld + m], -zz);
-                bad |= !isfinite(c);
-                zhad = true;
+        const int cm = __reduce_max_sync(0xffffffffu, __popcll(cmask));
+        if (cm > 0) tm_ld8(tb, buf[0]);
+        for (int j = 0; j < cm; ++j) {
+            const bool act = cmask != 0;
+            float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f, tj = 0.f;
+            double d64[3] = {0.0, 0.0, 0.0};
+            int m = 0;
+            if (act) {
+                m = entry(__ffsll((long long)cmask) - 1) >> 5;
+                cmask &= cmask - 1;
+                disp64(g, x64, i_caller, perm[m], d64);
+                dx = (float)d64[0];
+                dy = (float)d64[1];
+                dz = (float)d64[2];
+                r2 = dx * dx + dy * dy + dz * dz;
+                if constexpr (MS) tj = pos4[m].w;
+            }
+            if (force_pair(dx, dy, dz, r2, act, m, tj, j + 1 < cm)) {
+                const double r64 = sqrt(d64[0] * d64[0] + d64[1] * d64[1] + d64[2] * d64[2]);
+                if (r64 < P.zbl_rr2) {
+                    double Uz, dUz;
+                    const int pz = MS ? ti * T + (int)tj : 0;
+                    zbl_pair(r64, MS ? P.zbl_kp[pz] : P.zbl_k, MS ? P.zbl_inv_ap[pz] : P.zbl_inv_a,
+                             P.zbl_r1, P.zbl_rr2, Uz, dUz);
+                    ez += 0.5 * Uz;
+                    const double c = 0.5 * dUz / r64;
+                    const double f3[3] = {c * d64[0], c * d64[1], c * d64[2]};
+                    const long long zx = A_::convd(f3[0]), zy = A_::convd(f3[1]),
+                                    zz = A_::convd(f3[2]);
+                    fi[0] += zx; fi[1] += zy; fi[2] += zz;
+                    A_::add(&facc[m], -zx);
+                    A_::add(&facc[ld + m], -zy);
+                    A_::add(&facc[2 * ld + m], -zz);
+                    bad |= !isfinite(c);
+                    zhad = true;
 #pragma unroll
-                for (int a3 = 0; a3 < 3; ++a3)
+                    for (int a3 = 0; a3 < 3; ++a3)
 #pragma unroll
-                    for (int b3 = 0; b3 < 3; ++b3) wz[3 * a3 + b3] -= f3[a3] * d64[b3];
+                        for (int b3 = 0; b3 < 3; ++b3) wz[3 * a3 + b3] -= f3[a3] * d64[b3];
+                }
             }
         }
 #pragma unroll

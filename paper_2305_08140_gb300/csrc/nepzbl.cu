@@ -132,6 +132,7 @@ struct nep_ctx {
     int tm_dyn = -1;                 // k_nep_ang_tm dynamic shared memory (-1: not set)
     int tm_blocks = 0;               // its resident blocks per SM
     int tm_dyn_close = -1, tm_blocks_close = 0;   // the same for k_nep_ang_tm<true, false>
+    int rf_close_blocks = 0;         // resident blocks per SM of k_radial_force<float, false, true>
     int tm_dyn_ms[2] = {-1, -1}, tm_blocks_ms[2] = {0, 0};   // <false / true, true>
     // Nose-Hoover chain thermostat on a group, Berendsen barostat (MD)
     int nhc_on = 0;
@@ -619,9 +620,21 @@ static int launch_eval(nep_ctx* ctx, const Grid& g0, const double* x, const int3
             P, g, p4, lnbr, lcnt, (const typename V4<R>::T*)ctx->br, fa,
             ctx->partials + (size_t)tiles * NPART, ctx->status, ctx->perm, x, tfl);
         count_launch(ctx);
-        // (the close-pair variant rarely has tiles: a grid of a few blocks per
-        // SM, looping over the tiles, makes its pass over the flags cheap)
-        const int close_grid = tiles < 4 * ctx->sm_count ? tiles : 4 * ctx->sm_count;
+        // (the close-pair variant loops over the listed tiles on a grid of as
+        // many blocks as are resident at once: cheap when the list is empty,
+        // at full occupancy when it is long)
+        if (ctx->rf_close_blocks == 0) {
+            int nb = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_radial_force<R, false, true>,
+                                                              TILE, 0) != cudaSuccess ||
+                nb < 1) {
+                cudaGetLastError();
+                nb = 4;
+            }
+            ctx->rf_close_blocks = nb;
+        }
+        const int close_cap = ctx->rf_close_blocks * ctx->sm_count;
+        const int close_grid = tiles < close_cap ? tiles : close_cap;
         k_radial_force<R, false, true><<<close_grid > 0 ? close_grid : 1, TILE, 0, s>>>(
             P, g, p4, lnbr, lcnt, (const typename V4<R>::T*)ctx->br, fa,
             ctx->partials + (size_t)tiles * NPART, ctx->status, ctx->perm, x, tfl);
