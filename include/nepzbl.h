@@ -280,8 +280,10 @@ typedef struct nep_stats {
                                              evaluation (MD: summed over the last graph
                                              chunk's steps) */
     int64_t angular_tiles_register;       /* of those, the tiles the register angular
-                                             kernel took (all of them for FP64 or several
-                                             species) */
+                                             kernel took: FP32, the tiles with an atom of
+                                             more than 48 angular neighbours (and those
+                                             with a close pair when the Tensor-Memory
+                                             kernel cannot be resident); FP64, all */
 } nep_stats;
 
 int nep_get_stats(const nep_ctx* ctx, nep_stats* out);
