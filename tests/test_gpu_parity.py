@@ -40,6 +40,21 @@ def test_close_pairs_zbl_clump(precision):
     assert_parity(s, precision, scaled=True)
 
 
+def test_close_pair_list_overflow_tight_cluster():
+    """FP32: more pairs inside the outer ZBL radius on one atom than the register
+    kernel lists per atom (32; their FP64 displacements and ZBL terms are done
+    warp-wide, later ones inline): 130 atoms moved into a 3.2 A sphere of a
+    432-atom crystal (pairs down to 0.45 A, up to 40 inside 2 A on an atom),
+    against the oracle with the per-atom bounds."""
+    s = I.c3(ncell=6, fraction=0.3, radius=3.2, min_sep=0.45, seed=29)
+    d = s.pos[:, None, :] - s.pos[None, :, :]
+    d -= s.box * np.round(d / s.box)
+    r = np.sqrt((d ** 2).sum(-1))
+    np.fill_diagonal(r, np.inf)
+    assert (r < 2.0).sum(1).max() > 32
+    assert_parity(s, "fp32", scaled=True)
+
+
 def test_single_atom_and_dimer():
     s = I.Structure(np.array([[3.0, 4.0, 5.0]]), np.array([20.0, 20.0, 20.0]),
                     np.array([1, 1, 1], np.int32), np.zeros(1, np.int32))
