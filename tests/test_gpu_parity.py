@@ -45,14 +45,28 @@ def test_close_pair_list_overflow_tight_cluster():
     kernel lists per atom (32; their FP64 displacements and ZBL terms are done
     warp-wide, later ones inline): 130 atoms moved into a 3.2 A sphere of a
     432-atom crystal (pairs down to 0.45 A, up to 40 inside 2 A on an atom),
-    against the oracle with the per-atom bounds."""
+    against the oracle with the per-atom bounds.  The virial (~6e5 eV here) is
+    held to the flat per-atom bound plus the modelled rounding of every atom's
+    NEP pair forces (its force bound above the flat part) times the radial
+    cutoff, the longest lever arm a pair term has: the same pair forces enter
+    the virial as -1/2 sum d_ij (x) f_ij."""
+    from gpu_common import F32_W_PER_ATOM
     s = I.c3(ncell=6, fraction=0.3, radius=3.2, min_sep=0.45, seed=29)
     d = s.pos[:, None, :] - s.pos[None, :, :]
     d -= s.box * np.round(d / s.box)
     r = np.sqrt((d ** 2).sum(-1))
     np.fill_diagonal(r, np.inf)
     assert (r < 2.0).sum(1).max() > 32
-    assert_parity(s, "fp32", scaled=True)
+    E, F, W, U = gpu_eval(s, "fp32")
+    Eo, Fo, Wo, Uo = oracle_eval(s)
+    model = I.nep_model(1)
+    sc = O.force_scales(model, s.pos, s.box, s.pbc)
+    bF = force_bound("fp32", sc)
+    check_forces(F, Fo, bF)
+    assert abs(E - Eo) / s.n <= F32_E_PER_ATOM, (E, Eo)
+    check_sites(U, Uo, site_bound("fp32", Uo, sc))
+    bW = s.n * F32_W_PER_ATOM + model.rc_radial * float(np.sum(bF - F32_F))
+    assert np.max(np.abs(W - Wo)) <= bW, (np.max(np.abs(W - Wo)), bW)
 
 
 def test_single_atom_and_dimer():
